@@ -1,0 +1,279 @@
+"""FP64 CPU oracle of the catalog path -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never calls it, and it
+shares no code with the CUDA library.  The arithmetic lives in ``ipp_oracle.c``
+(plain C, FP64, one function per step of the paper); this module only builds
+it with gcc and marshals numpy arrays.
+
+Parity status per function is recorded at the top of ``ipp_oracle.c`` and in
+the design notes: every function here is pinned by a ``-m "not gpu"`` test.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ipp_oracle.c")
+_HDR = os.path.join(_HERE, "ipp_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FLAG_EDGE = 1
+FLAG_WIN_NOT_CONVERGED = 2
+FLAG_ANN_FEW = 4
+FLAG_FIT_MAXITER = 8
+FLAG_FIT_SINGULAR = 16
+FLAG_FIT_BAD_SIGMA = 32
+
+EST_SIGMA, EST_MEDIAN, EST_MEAN, EST_FACTORS = 0, 1, 2, 3
+PSF_MOFFAT, PSF_GAUSS = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (no fused multiply-add)."""
+    stale = (not os.path.exists(_LIB)) or any(
+        os.path.getmtime(f) > os.path.getmtime(_LIB) for f in (_SRC, _HDR))
+    if force or stale:
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+               _SRC, "-o", _LIB + ".tmp", "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class BgParams(C.Structure):
+    _fields_ = [("mesh_w", C.c_int32), ("mesh_h", C.c_int32),
+                ("filter_w", C.c_int32), ("filter_h", C.c_int32),
+                ("maxiters", C.c_int32), ("min_valid", C.c_int32),
+                ("estimator", C.c_int32), ("pad_", C.c_int32),
+                ("nsigma", C.c_double), ("median_factor", C.c_double),
+                ("mean_factor", C.c_double)]
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+            L.orc_calibrate.argtypes = [vp, i64, i64, i64, vp, d, vp, vp]
+            L.orc_mesh_stats.argtypes = [vp, i64, i64, i64, vp, C.POINTER(BgParams), vp, vp, vp, vp, vp]
+            L.orc_mesh_fill_filter.argtypes = [vp, vp, vp, i64, i64, i32, i32, vp, vp]
+            L.orc_keys_weight.argtypes = [d]
+            L.orc_keys_weight.restype = d
+            L.orc_interp_map.argtypes = [vp, i64, i64, i32, i32, i64, i64, vp]
+            L.orc_bg_subtract.argtypes = [vp, i64, i64, i64, vp, i64, i64, i32, i32, vp, vp]
+            L.orc_threshold.argtypes = [vp, i64, i64, vp, i64, i64, i32, i32, d, d, vp]
+            L.orc_label.argtypes = [vp, vp, i64, i64, i32, vp, i64] + [vp] * 10
+            L.orc_label.restype = i64
+            L.orc_centroid.argtypes = [vp, i64, i64, i64, vp, vp, d, i32, d, vp, vp, vp, vp]
+            L.orc_overlap.argtypes = [d] * 7
+            L.orc_overlap.restype = d
+            L.orc_aperture.argtypes = [vp, i64, i64, i64, vp, vp, d, d, d, i32, vp, vp, vp, vp, vp]
+            L.orc_psf_model.argtypes = [vp, i32, i32, d, vp, vp]
+            L.orc_psf_fit.argtypes = [vp, i64, i32, vp, vp, i32, d, i32, d, vp, vp, vp, vp]
+            L.orc_psf_init.argtypes = [vp, i32, vp]
+            _lib = L
+    return _lib
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+# ------------------------------------------------------------------ c0
+def calibrate(raw, flat, bias=500.0, bias_map=None):
+    raw = np.ascontiguousarray(raw, dtype=np.uint16)
+    H, W = raw.shape
+    out = np.empty((H, W), np.float32)
+    bm = None if bias_map is None else _f32(bias_map)
+    rc = lib().orc_calibrate(_p(raw), W, H, W, _p(bm), float(bias), _p(_f32(flat)), _p(out))
+    assert rc == 0
+    return out
+
+
+# ------------------------------------------------------------- c1-c3
+def bg_params(mesh=64, mesh_h=None, filter_size=3, maxiters=10, min_valid=100,
+              nsigma=3.0, estimator=EST_SIGMA, median_factor=2.5, mean_factor=1.5):
+    return BgParams(mesh, mesh_h or mesh, filter_size, filter_size, maxiters, min_valid,
+                    estimator, 0, nsigma, median_factor, mean_factor)
+
+
+def mesh_stats(img, mask=None, **kw):
+    img = _f32(img)
+    H, W = img.shape
+    p = bg_params(**kw)
+    nx, ny = -(-W // p.mesh_w), -(-H // p.mesh_h)
+    rb, rr = np.zeros((ny, nx)), np.zeros((ny, nx))
+    valid, niter = np.zeros((ny, nx), np.int32), np.zeros((ny, nx), np.int32)
+    margin = np.zeros((ny, nx))
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    rc = lib().orc_mesh_stats(_p(img), W, H, W, _p(m), C.byref(p), _p(rb), _p(rr),
+                              _p(valid), _p(niter), _p(margin))
+    assert rc == 0
+    return dict(raw_bkg=rb, raw_rms=rr, valid=valid, niter=niter, margin=margin)
+
+
+def fill_filter(raw_bkg, raw_rms, valid, filter_size=3):
+    ny, nx = raw_bkg.shape
+    b, r = np.zeros((ny, nx)), np.zeros((ny, nx))
+    rc = lib().orc_mesh_fill_filter(_p(np.ascontiguousarray(raw_bkg, np.float64)),
+                                    _p(np.ascontiguousarray(raw_rms, np.float64)),
+                                    _p(np.ascontiguousarray(valid, np.int32)),
+                                    nx, ny, filter_size, filter_size, _p(b), _p(r))
+    if rc != 0:
+        raise ValueError("no valid mesh")
+    return b, r
+
+
+def bg_estimate(img, mask=None, **kw):
+    """Sec. 2.2.2 mesh background: returns filtered (bkg, rms) as float32 grids
+    and the unfiltered statistics."""
+    st = mesh_stats(img, mask, **kw)
+    fs = kw.get("filter_size", 3)
+    b, r = fill_filter(st["raw_bkg"], st["raw_rms"], st["valid"], fs)
+    return b.astype(np.float32), r.astype(np.float32), st
+
+
+def keys_weight(s):
+    return lib().orc_keys_weight(float(s))
+
+
+def interp_map(mesh, mesh_w, W, H, mesh_h=None):
+    mesh = _f32(mesh)
+    ny, nx = mesh.shape
+    out = np.zeros((H, W))
+    rc = lib().orc_interp_map(_p(mesh), nx, ny, mesh_w, mesh_h or mesh_w, W, H, _p(out))
+    assert rc == 0
+    return out
+
+
+def bg_subtract(img, mesh_bkg, mesh_w, mesh_h=None):
+    img, mesh_bkg = _f32(img), _f32(mesh_bkg)
+    H, W = img.shape
+    ny, nx = mesh_bkg.shape
+    sub, bmap = np.empty((H, W), np.float32), np.empty((H, W), np.float32)
+    rc = lib().orc_bg_subtract(_p(img), W, H, W, _p(mesh_bkg), nx, ny, mesh_w,
+                               mesh_h or mesh_w, _p(sub), _p(bmap))
+    assert rc == 0
+    return sub, bmap
+
+
+def threshold(sub, mesh_rms, mesh_w, k=1.5, thresh_abs=0.0, mesh_h=None):
+    sub, mesh_rms = _f32(sub), _f32(mesh_rms)
+    H, W = sub.shape
+    ny, nx = mesh_rms.shape
+    m = np.zeros((H, W), np.uint8)
+    rc = lib().orc_threshold(_p(sub), W, H, _p(mesh_rms), nx, ny, mesh_w, mesh_h or mesh_w,
+                             float(k), float(thresh_abs), _p(m))
+    assert rc == 0
+    return m
+
+
+# ------------------------------------------------------------- c6-c7
+def label(mask, sub, min_area=5, max_src=None):
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    sub = _f32(sub)
+    H, W = mask.shape
+    labels = np.zeros((H, W), np.int32)
+    cap = max_src if max_src is not None else max(1, (H * W) // max(1, min_area) + 1)
+    cap = int(min(cap, H * W + 1))
+    st = dict(area=np.zeros(cap, np.int32), first=np.zeros(cap, np.int64),
+              xmin=np.zeros(cap, np.int32), xmax=np.zeros(cap, np.int32),
+              ymin=np.zeros(cap, np.int32), ymax=np.zeros(cap, np.int32),
+              peak=np.zeros(cap), sum=np.zeros(cap), xbar=np.zeros(cap), ybar=np.zeros(cap))
+    order = ["area", "first", "xmin", "xmax", "ymin", "ymax", "peak", "sum", "xbar", "ybar"]
+    K = lib().orc_label(_p(mask), _p(sub), W, H, min_area, _p(labels), cap,
+                        *[_p(st[k]) for k in order])
+    n = min(K, cap)
+    return labels, int(K), {k: v[:n] for k, v in st.items()}
+
+
+# ---------------------------------------------------------------- c8
+def centroid(sub, x0, y0, fwhm_win=3.0, max_iter=16, tol2=1e-8):
+    sub = _f32(sub)
+    H, W = sub.shape
+    x0, y0 = _f32(x0), _f32(y0)
+    n = len(x0)
+    x, y = np.zeros(n), np.zeros(n)
+    it, fl = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    lib().orc_centroid(_p(sub), W, H, n, _p(x0), _p(y0), float(fwhm_win), int(max_iter),
+                       float(tol2), _p(x), _p(y), _p(it), _p(fl))
+    return x, y, it, fl
+
+
+# --------------------------------------------------------------- c9-c11
+def overlap(cx, cy, r, x0, x1, y0, y1):
+    return lib().orc_overlap(float(cx), float(cy), float(r), float(x0), float(x1),
+                             float(y0), float(y1))
+
+
+def aperture(sub, x, y, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann=10):
+    sub = _f32(sub)
+    H, W = sub.shape
+    x, y = _f32(x), _f32(y)
+    n = len(x)
+    out = dict(flux=np.zeros(n), sky=np.zeros(n), area=np.zeros(n),
+               n_ann=np.zeros(n, np.int32), flags=np.zeros(n, np.int32))
+    lib().orc_aperture(_p(sub), W, H, n, _p(x), _p(y), float(r_ap), float(r_in), float(r_out),
+                       int(min_ann), _p(out["flux"]), _p(out["sky"]), _p(out["area"]),
+                       _p(out["n_ann"]), _p(out["flags"]))
+    return out
+
+
+# -------------------------------------------------------------- c12-c13
+def psf_model(p7, S=15, model=PSF_MOFFAT, beta=2.5, jac=True):
+    p7 = np.ascontiguousarray(p7, dtype=np.float64)
+    m = np.zeros(S * S)
+    J = np.zeros((S * S, 7)) if jac else None
+    lib().orc_psf_model(_p(p7), S, model, float(beta), _p(m), _p(J))
+    return (m.reshape(S, S), J) if jac else m.reshape(S, S)
+
+
+def psf_init(stamp):
+    st = _f32(stamp)
+    S = st.shape[-1]
+    p = np.zeros(7)
+    lib().orc_psf_init(_p(st), S, _p(p))
+    return p
+
+
+def psf_fit(stamps, init=None, weights=None, model=PSF_MOFFAT, beta=2.5, max_iter=50,
+            lambda0=1e-3):
+    stamps = _f32(stamps)
+    N, S = stamps.shape[0], stamps.shape[-1]
+    ini = None if init is None else _f32(init)
+    w = None if weights is None else _f32(weights)
+    out = dict(params=np.zeros((N, 7)), chi2=np.zeros(N), iters=np.zeros(N, np.int32),
+               flags=np.zeros(N, np.int32))
+    lib().orc_psf_fit(_p(stamps), N, S, _p(w), _p(ini), model, float(beta), int(max_iter),
+                      float(lambda0), _p(out["params"]), _p(out["chi2"]), _p(out["iters"]),
+                      _p(out["flags"]))
+    return out
+
+
+# ----------------------------------------------------------- whole path
+def catalog(img, mesh=64, filter_size=3, k=1.5, min_area=5, fwhm_win=3.0,
+            r_ap=5.0, r_in=8.0, r_out=12.0, mask_in=None):
+    """The whole per-frame path a1..a6 on one float32 frame."""
+    bkg, rms, st = bg_estimate(img, mesh=mesh, filter_size=filter_size)
+    sub, _ = bg_subtract(img, bkg, mesh)
+    m = threshold(sub, rms, mesh, k) if mask_in is None else mask_in
+    labels, K, stats = label(m, sub, min_area)
+    x, y, it, cfl = centroid(sub, stats["xbar"].astype(np.float32),
+                             stats["ybar"].astype(np.float32), fwhm_win)
+    ph = aperture(sub, x.astype(np.float32), y.astype(np.float32), r_ap, r_in, r_out)
+    return dict(bkg=bkg, rms=rms, mesh_stats=st, sub=sub, mask=m, labels=labels, K=K,
+                stats=stats, x=x, y=y, cen_iter=it, cen_flags=cfl, **ph)
