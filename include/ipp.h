@@ -1,0 +1,306 @@
+/*
+ * ipp.h -- C ABI of the GB300 (sm_103a) catalog path.
+ *
+ * The library implements the per-frame hot path of the GPU image
+ * pre-processing method of Cao, Jia et al., "Image Pre-Processing Framework for
+ * Time-Domain Astronomy in the Artificial Intelligence Era" (arXiv 2502.10783):
+ *
+ *   ipp_bg_estimate   mesh background: iterative sigma clip per mesh, the
+ *                     2.5 median - 1.5 mean estimator, median filter on the
+ *                     mesh grid                               (Sec. 2.2.2, Eqs. 1-4)
+ *   ipp_bg_subtract   interpolation of the mesh back to full resolution and
+ *                     subtraction                             (Sec. 2.2.2)
+ *   ipp_detect_label  pixel detection above k x local rms, 8-connected
+ *                     labeling, per-candidate peak / flux     (Sec. 2.2.5)
+ *   ipp_centroid      windowed centroid of each candidate     (positions, Sec. 2.2.5)
+ *   ipp_aperture_phot circular aperture photometry with a local sky annulus
+ *                                                             (Sec. 2.2.5)
+ *   ipp_psf_fit       batched Levenberg-Marquardt PSF fit of stamps
+ *   ipp_extract       all catalog steps of one frame, fused where the data allow
+ *
+ * Conventions for every call
+ *   - Pixel (row i, col j) has its centre at (x = j, y = i).  Frames are row-major
+ *     with `pitch` elements between rows (pitch >= W).
+ *   - Every pointer argument is a DEVICE pointer unless stated otherwise; the
+ *     caller owns all buffers.  Parameter structs are host pointers, read during
+ *     the call only.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - Calls enqueue work on `stream` and return without synchronising.  Counts
+ *     that depend on the data (number of sources) stay in device memory.
+ *   - The return value is an IPP_* status.  IPP_ERR_INVALID_ARG and
+ *     IPP_ERR_NOT_SUPPORTED are detected on the host before anything is enqueued;
+ *     IPP_ERR_CUDA reports a launch failure (ipp_last_error_detail() has the
+ *     text).  Errors that arise on the device are reported through the device
+ *     status words documented per call, never by trapping.
+ *   - Workspaces (`ws`) are device buffers of at least the size returned by the
+ *     matching *_workspace_size() query, 256-byte aligned.  The library allocates
+ *     no device memory inside a call.
+ */
+#ifndef IPP_H
+#define IPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define IPP_OK 0
+#define IPP_ERR_INVALID_ARG 1   /* null pointer, bad size, pitch < W, misalignment, bad parameter */
+#define IPP_ERR_CUDA 2          /* CUDA launch/runtime error; detail in ipp_last_error_detail() */
+#define IPP_ERR_CAPACITY 3      /* device status: more sources than max_src (see ipp_detect_label) */
+#define IPP_ERR_NO_VALID_MESH 4 /* device status: no mesh had enough usable pixels */
+#define IPP_ERR_TIMEOUT 5       /* device status: a bounded device-side wait ran out */
+#define IPP_ERR_NOT_SUPPORTED 6 /* valid request outside what this build implements */
+
+/* image element types */
+#define IPP_F32 0
+#define IPP_U16 1
+
+/* per-source flag bits */
+#define IPP_FLAG_EDGE 1              /* window / aperture / annulus crosses the frame edge */
+#define IPP_FLAG_WIN_NOT_CONVERGED 2 /* windowed centroid did not converge (seed kept if sum <= 0) */
+#define IPP_FLAG_ANN_FEW 4           /* fewer than min_ann annulus pixels: sky = 0 */
+#define IPP_FLAG_FIT_MAXITER 8       /* PSF fit stopped at max_iter */
+#define IPP_FLAG_FIT_SINGULAR 16     /* PSF fit normal matrix not positive definite */
+#define IPP_FLAG_FIT_BAD_SIGMA 32    /* PSF fit width at or below 0.05 px */
+
+/* background estimators (Sec. 2.2.2) */
+#define IPP_EST_SIGMA 0   /* Eq. 3: 2.5 median - 1.5 mean (default) */
+#define IPP_EST_MEDIAN 1  /* Eq. 1 */
+#define IPP_EST_MEAN 2    /* Eq. 2 */
+#define IPP_EST_FACTORS 3 /* Eq. 4, read as median_factor * median - mean_factor * mean */
+
+/* PSF models */
+#define IPP_PSF_MOFFAT 0
+#define IPP_PSF_GAUSS 1
+
+/* Mesh background parameters (Sec. 2.2.2).  Defaults in brackets. */
+typedef struct {
+    int32_t mesh_w, mesh_h;     /* mesh size in px [64, 64]; 4 <= size, mesh_w*mesh_h <= 16384 */
+    int32_t filter_w, filter_h; /* median-filter window on the mesh grid, odd, <= 7 [3, 3] */
+    int32_t maxiters;           /* clip passes [10] */
+    int32_t min_valid;          /* usable pixels for a valid mesh [100] */
+    int32_t estimator;          /* IPP_EST_* [IPP_EST_SIGMA] */
+    int32_t reserved;           /* must be 0 */
+    double nsigma;              /* clip half-width in sigma [3] */
+    double median_factor;       /* Eq. 4 [2.5] */
+    double mean_factor;         /* Eq. 4 [1.5] */
+} ipp_bg_params;
+
+/* Detection parameters (Sec. 2.2.5). */
+typedef struct {
+    float k;            /* threshold in units of the interpolated mesh rms [1.5] */
+    float thresh_abs;   /* absolute floor of the threshold, ADU [0] */
+    int32_t min_area;   /* smallest kept candidate, px [5] */
+    int32_t reserved;   /* must be 0 */
+} ipp_det_params;
+
+/* Windowed-centroid parameters (paper-silent reading). */
+typedef struct {
+    float fwhm_win;     /* window FWHM, px: sigma_w = fwhm / 2.35482, radius 4 sigma_w [3] */
+    int32_t max_iter;   /* [16] */
+    float tol2;         /* stop when the squared step is below this, px^2 [1e-8] */
+    int32_t reserved;
+} ipp_cen_params;
+
+/* Aperture photometry parameters. */
+typedef struct {
+    float r_ap;         /* aperture radius, px [5] */
+    float r_in, r_out;  /* sky annulus: pixel centres with r_in <= d < r_out [8, 12]; r_out <= 32 */
+    int32_t min_ann;    /* fewest annulus pixels for a sky value [10] */
+} ipp_phot_params;
+
+/* PSF fit parameters (paper-silent reading). */
+typedef struct {
+    int32_t model;      /* IPP_PSF_MOFFAT or IPP_PSF_GAUSS */
+    float beta;         /* Moffat exponent [2.5] */
+    int32_t max_iter;   /* LM trials [50] */
+    float lambda0;      /* initial damping [1e-3] */
+} ipp_fit_params;
+
+/* Per-source statistics of ipp_detect_label: device arrays of max_src entries
+ * (structure of arrays).  Entry k describes label k+1. */
+typedef struct {
+    int32_t* area;      /* pixels */
+    int64_t* first;     /* raster index i*W + j of the first pixel */
+    int32_t* xmin;
+    int32_t* xmax;
+    int32_t* ymin;
+    int32_t* ymax;
+    float* peak;        /* largest value */
+    float* flux;        /* isophotal flux: sum of values */
+    float* xbar;        /* flux-weighted barycentre */
+    float* ybar;
+} ipp_src_stats;
+
+/* Bias/flat calibration for IPP_U16 frames: f = (raw - bias) * inv_flat. */
+typedef struct {
+    const float* bias_map;  /* nullable device map (pitch = W); else `bias` */
+    float bias;
+    int32_t reserved;
+    const float* inv_flat;  /* device map of 1/flat, pitch = W (required) */
+} ipp_calib;
+
+/* ------------------------------------------------------------ queries */
+const char* ipp_status_string(int status);
+/* Text of the last IPP_ERR_CUDA / argument error seen by this host thread. */
+const char* ipp_last_error_detail(void);
+/* 0 on success; fills the library version triple. */
+int ipp_version(int* major, int* minor, int* patch);
+
+/* ---------------------------------------------------------- background */
+/*
+ * ipp_bg_estimate -- mesh statistics and mesh filter (Sec. 2.2.2, Eqs. 1-4).
+ * The frame is cut into mesh_w x mesh_h regions (nx = ceil(W / mesh_w),
+ * ny = ceil(H / mesh_h); partial last meshes keep their real pixels).  Per mesh,
+ * over the unmasked finite pixels: repeat up to maxiters times -- median (Eq. 1),
+ * mean (Eq. 2) and population sigma of the current set, drop values outside
+ * [median - nsigma sigma, median + nsigma sigma] (bounds inclusive) -- until no
+ * value is dropped; the background is the chosen estimator of the final set
+ * (Eq. 3 by default) and the rms its sigma.  Meshes with fewer than min_valid
+ * usable pixels take the median of the valid meshes in the nearest
+ * (2k+1)^2 neighbourhood that holds any.  Both grids are then median filtered
+ * with a filter_w x filter_h window that shrinks at the grid edges.
+ *   img       device frame, dtype IPP_F32 (or IPP_U16 with `cal`), pitch elements
+ *   mask      nullable device uint8 map (pitch = W); nonzero excludes the pixel
+ *   cal       calibration for IPP_U16 input (nullable for IPP_F32)
+ *   mesh_bkg, mesh_rms   device float[ny * nx] outputs (filtered)
+ *   raw_bkg, raw_rms     nullable device float[ny * nx]: values before fill/filter
+ *                        (invalid meshes hold -1 in raw_rms)
+ *   ws, ws_bytes         workspace of ipp_bg_estimate_workspace_size() bytes
+ *   status_dev           nullable device int32: set to IPP_ERR_NO_VALID_MESH when
+ *                        no mesh is valid (outputs then hold 0), else IPP_OK
+ */
+size_t ipp_bg_estimate_workspace_size(int64_t W, int64_t H, const ipp_bg_params* p);
+int ipp_bg_estimate(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                    const uint8_t* mask, const ipp_calib* cal, const ipp_bg_params* p,
+                    float* mesh_bkg, float* mesh_rms, float* raw_bkg, float* raw_rms,
+                    int32_t* status_dev, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ipp_bg_subtract -- interpolation back to full resolution and subtraction
+ * (Sec. 2.2.2).  Node (p, q) of the filtered mesh sits at
+ * ((q + 1/2) mesh_w - 1/2, (p + 1/2) mesh_h - 1/2); the background at each pixel
+ * is the separable Keys (1981) cubic convolution (a = -1/2) of the 4 x 4 nearest
+ * nodes, indices clamped to the grid.  sub = f - B.
+ *   sub        device float output, sub_pitch elements per row (may alias img
+ *              only when dtype is IPP_F32 and pitches match)
+ *   bkg_map    nullable device float output of B (pitch = sub_pitch)
+ */
+int ipp_bg_subtract(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                    const ipp_calib* cal, const float* mesh_bkg, const ipp_bg_params* p,
+                    float* sub, int64_t sub_pitch, float* bkg_map, void* stream);
+
+/* --------------------------------------------------------------- detection */
+/*
+ * ipp_detect_label -- pixel detection and connection into candidates, with the
+ * per-candidate pre-analysis of Sec. 2.2.5.  A pixel is detected when
+ * sub > max(k * rms(x, y), thresh_abs), rms(x, y) being the Keys interpolation of
+ * mesh_rms; detected pixels are joined into 8-connected components; components
+ * smaller than min_area pixels are dropped and the rest numbered 1..K in raster
+ * order of their first pixel (the numbering does not depend on tiling).
+ *   mask_in    nullable device bit mask that replaces the threshold: row i holds
+ *              ceil(W/32) uint32 words, pixel (i, j) is bit (j % 32) of word j / 32
+ *   labels     device int32 map, pitch = W (0 = background)
+ *   n_src_dev  device int32: K, the number of candidates (all of them, even above
+ *              max_src)
+ *   stats      host struct of device arrays of max_src entries; entries for labels
+ *              above max_src are not written (K > max_src is the capacity case)
+ *   ws         workspace of ipp_detect_label_workspace_size() bytes
+ */
+size_t ipp_detect_label_workspace_size(int64_t W, int64_t H);
+int ipp_detect_label(const float* sub, int64_t W, int64_t H, int64_t pitch,
+                     const float* mesh_rms, const ipp_bg_params* bp, const ipp_det_params* dp,
+                     const uint32_t* mask_in, int32_t* labels, int32_t* n_src_dev,
+                     int32_t max_src, const ipp_src_stats* stats, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* -------------------------------------------------------------- per source */
+/*
+ * ipp_centroid -- windowed centroid (paper-silent reading of the positions of
+ * Sec. 2.2.5): Gaussian window sigma_w = fwhm_win / 2.35482 over the pixels with
+ * centres within 4 sigma_w of the current position and inside the frame;
+ * x += 2 sum(w f (x_i - x)) / sum(w f) (same for y) until the squared step is
+ * below tol2 or max_iter updates; a non-positive weighted sum returns the seed.
+ * Processes min(*n_src_dev, max_src) sources.
+ *   x0, y0     seeds (e.g. the barycentres of ipp_detect_label)
+ *   x, y, niter, flags   device outputs per source (niter nullable)
+ */
+int ipp_centroid(const float* sub, int64_t W, int64_t H, int64_t pitch,
+                 const int32_t* n_src_dev, int32_t max_src, const float* x0, const float* y0,
+                 const ipp_cen_params* p, float* x, float* y, int32_t* niter, int32_t* flags,
+                 void* stream);
+
+/*
+ * ipp_aperture_phot -- aperture photometry (Sec. 2.2.5) with a local sky
+ * annulus (paper-silent reading): weights are the exact areas of the pixel /
+ * disk overlaps, sky is the median (Eq. 1) of the pixels whose centres satisfy
+ * r_in <= d < r_out, flux = sum(w f) - sky sum(w), area = sum(w).
+ *   flux, sky, area, n_ann, flags   device outputs per source (nullable except flux)
+ */
+int ipp_aperture_phot(const float* sub, int64_t W, int64_t H, int64_t pitch,
+                      const int32_t* n_src_dev, int32_t max_src, const float* x, const float* y,
+                      const ipp_phot_params* p, float* flux, float* sky, float* area,
+                      int32_t* n_ann, int32_t* flags, void* stream);
+
+/* ------------------------------------------------------------- fused frame */
+/*
+ * ipp_extract -- the catalog path of one frame in one call: bg_estimate,
+ * bg_subtract fused with the threshold and the per-tile labeling, label merge,
+ * centroid and aperture photometry.  Outputs as in the individual calls; the
+ * positions used for photometry are the windowed centroids.
+ */
+typedef struct {
+    float* mesh_bkg; float* mesh_rms;     /* [ny*nx] */
+    float* sub;                           /* [H*W] background-subtracted frame, pitch W */
+    int32_t* labels;                      /* [H*W] */
+    int32_t* n_src_dev;                   /* [1] */
+    ipp_src_stats stats;                  /* [max_src] */
+    float* x; float* y; int32_t* cen_flags;              /* [max_src] */
+    float* flux; float* sky; float* area; int32_t* n_ann; int32_t* phot_flags; /* [max_src] */
+    int32_t* status_dev;                  /* [1] nullable */
+} ipp_catalog_out;
+
+size_t ipp_extract_workspace_size(int64_t W, int64_t H, const ipp_bg_params* bp);
+int ipp_extract(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                const ipp_calib* cal, const ipp_bg_params* bp, const ipp_det_params* dp,
+                const ipp_cen_params* cp, const ipp_phot_params* pp, int32_t max_src,
+                const ipp_catalog_out* out, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- PSF fit */
+/*
+ * ipp_psf_fit -- batched Levenberg-Marquardt fit of an elliptical Moffat or
+ * Gaussian PSF (paper-silent) to N stamps of S x S pixels.  Parameters per stamp:
+ * (x0, y0, F, sky, sx, sy, theta); model point-sampled at pixel centres
+ * (0..S-1):  u = cos(t) dx + sin(t) dy, v = -sin(t) dx + cos(t) dy,
+ * q = u^2/sx^2 + v^2/sy^2, Moffat F (beta-1)/(pi sx sy) (1+q)^-beta + sky,
+ * Gaussian F/(2 pi sx sy) exp(-q/2) + sky.  Model, Jacobian and J'WJ in FP32;
+ * the 7x7 damped normal equations solved by Cholesky in FP64.  One trial per
+ * iteration: accepted when chi^2 drops (lambda /= 10), else lambda *= 10; widths
+ * must stay above 0.05.  Converged when an accepted step lowers chi^2 by less
+ * than 1e-6 relative (the FP32 chi^2 resolves ~1e-7; an FP64 evaluation would
+ * use 1e-8), or when lambda exceeds 1e10.  Result canonicalised to
+ * sx >= sy and theta in [-pi/2, pi/2).
+ *   stamps   device float[N*S*S]; weights nullable (same shape)
+ *   init     nullable device float[N*7]; NULL = stamp centre, border-median sky,
+ *            sum above sky, sx = 1.6, sy = 1.4, theta = 0
+ *   params   device float[N*7]; chi2 float[N]; iters, flags int32[N] (nullable)
+ */
+int ipp_psf_fit(const float* stamps, int64_t N, int32_t S, const float* weights,
+                const float* init, const ipp_fit_params* p, float* params, float* chi2,
+                int32_t* iters, int32_t* flags, void* stream);
+
+/* Model images m[N*S*S] of params[N*7] (forward of the differentiable model). */
+int ipp_psf_model_fwd(const float* params, int64_t N, int32_t S, const ipp_fit_params* p,
+                      float* model, void* stream);
+
+/* Adjoint: grad_params[n][k] = sum_pixels grad_model[n][pix] * dm/dparam_k. */
+int ipp_psf_model_adj(const float* params, int64_t N, int32_t S, const ipp_fit_params* p,
+                      const float* grad_model, float* grad_params, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPP_H */

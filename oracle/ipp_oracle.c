@@ -338,7 +338,8 @@ int64_t orc_label(const uint8_t* mask, const float* sub, int64_t W, int64_t H,
  * frame; update x += 2 sum(w f (x_i - x)) / sum(w f), same for y, until the
  * squared step is below tol2 or max_iter updates were made.  A non-positive
  * weighted sum returns the seed with WIN_NOT_CONVERGED.  EDGE is set when the
- * window of the final position reaches outside the frame.
+ * window disk (radius 4 sigma_w) at the final position crosses the frame's outer
+ * boundary.
  */
 int orc_centroid(const float* sub, int64_t W, int64_t H, int64_t n,
                  const float* x0, const float* y0, double fwhm_win,
@@ -367,17 +368,11 @@ int orc_centroid(const float* sub, int64_t W, int64_t H, int64_t n,
             cx += ddx; cy += ddy;
             if (ddx * ddx + ddy * ddy < tol2) { fl = 0; it++; break; }
         }
-        /* edge test at the final position */
-        {
-            int64_t i0 = (int64_t)floor(cy - rad), i1 = (int64_t)ceil(cy + rad);
-            int64_t j0 = (int64_t)floor(cx - rad), j1 = (int64_t)ceil(cx + rad);
-            for (int64_t i = i0; i <= i1; i++)
-                for (int64_t j = j0; j <= j1; j++) {
-                    double dx = (double)j - cx, dy = (double)i - cy;
-                    if (dx * dx + dy * dy < rad2 && (i < 0 || i >= H || j < 0 || j >= W))
-                        fl |= ORC_FLAG_EDGE;
-                }
-        }
+        /* EDGE: the window disk at the final position crosses the frame's outer
+         * boundary [-1/2, W-1/2] x [-1/2, H-1/2] */
+        if (cx - rad < -0.5 || cx + rad > (double)W - 0.5 || cy - rad < -0.5 ||
+            cy + rad > (double)H - 0.5)
+            fl |= ORC_FLAG_EDGE;
         x[s] = cx; y[s] = cy;
         if (niter) niter[s] = it;
         flags[s] = fl;
@@ -452,7 +447,8 @@ double orc_overlap(double cx, double cy, double r, double x0, double x1,
  *            r_in <= d < r_out (d^2 = (j-x)^2 + (i-y)^2 in FP64); fewer than
  *            min_ann of them -> sky = 0 and ANN_FEW;
  *   flux   = sum w f - sky sum w, area = sum w, over in-frame pixels;
- *   EDGE when the aperture or the annulus reaches outside the frame.
+ *   EDGE when the disk of radius max(r_ap, r_out) crosses the frame's outer
+ *   boundary [-1/2, W-1/2] x [-1/2, H-1/2].
  */
 int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
                  const float* x, const float* y, double r_ap, double r_in,
@@ -472,7 +468,7 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
                 double w = orc_overlap(cx, cy, r_ap, (double)j - 0.5, (double)j + 0.5,
                                        (double)i - 0.5, (double)i + 0.5);
                 if (!(w > 0.0)) continue;
-                if (i < 0 || i >= H || j < 0 || j >= W) { fl |= ORC_FLAG_EDGE; continue; }
+                if (i < 0 || i >= H || j < 0 || j >= W) continue;
                 sw += w; swf += w * (double)sub[i * W + j];
             }
         int64_t na = 0;
@@ -483,9 +479,15 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
                 double dx = (double)j - cx, dy = (double)i - cy;
                 double d2 = dx * dx + dy * dy;
                 if (!(d2 >= rin2 && d2 < rout2)) continue;
-                if (i < 0 || i >= H || j < 0 || j >= W) { fl |= ORC_FLAG_EDGE; continue; }
+                if (i < 0 || i >= H || j < 0 || j >= W) continue;
                 ann[na++] = (double)sub[i * W + j];
             }
+        {
+            double R = r_ap > r_out ? r_ap : r_out;
+            if (cx - R < -0.5 || cx + R > (double)W - 0.5 || cy - R < -0.5 ||
+                cy + R > (double)H - 0.5)
+                fl |= ORC_FLAG_EDGE;
+        }
         double sk = 0.0;
         if (na < min_ann) fl |= ORC_FLAG_ANN_FEW;
         else sk = median_of(ann, na);

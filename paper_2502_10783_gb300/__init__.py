@@ -1,0 +1,336 @@
+"""GB300 (sm_103a) catalog path of the GPU image pre-processing method of
+Cao, Jia et al. (arXiv 2502.10783): mesh background estimation and subtraction
+(Sec. 2.2.2), threshold detection with connected-component labeling and
+per-candidate statistics, windowed centroids and aperture photometry with a
+local sky annulus (Sec. 2.2.5), and a batched differentiable PSF fit.
+
+Every step runs in the CUDA kernels of libipp.so behind the C ABI of
+include/ipp.h.  This module only marshals arguments: it allocates outputs and
+workspaces with torch, passes raw device pointers and the current stream, and
+raises when a call returns an error status.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import _abi
+from ._abi import (  # noqa: F401
+    EST_FACTORS, EST_MEAN, EST_MEDIAN, EST_SIGMA, FLAG_ANN_FEW, FLAG_EDGE, FLAG_FIT_BAD_SIGMA,
+    FLAG_FIT_MAXITER, FLAG_FIT_SINGULAR, FLAG_WIN_NOT_CONVERGED, IppError, PSF_GAUSS, PSF_MOFFAT,
+)
+
+__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot",
+           "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
+
+
+def load():
+    """Load (building if needed) the CUDA library; raises if it cannot."""
+    return _abi.load()
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _need_cuda(t, name, dtype=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+
+
+@dataclass
+class BgConfig:
+    """Mesh background parameters (Sec. 2.2.2); defaults as in the paper (64 px meshes)."""
+    mesh: int = 64
+    mesh_h: int | None = None
+    filter_size: int = 3
+    maxiters: int = 10
+    min_valid: int = 100
+    nsigma: float = 3.0
+    estimator: int = EST_SIGMA
+    median_factor: float = 2.5
+    mean_factor: float = 1.5
+
+    def c(self):
+        return _abi.BgParams(self.mesh, self.mesh_h or self.mesh, self.filter_size, self.filter_size,
+                             self.maxiters, self.min_valid, self.estimator, 0, self.nsigma,
+                             self.median_factor, self.mean_factor)
+
+    def grid(self, W, H):
+        mh = self.mesh_h or self.mesh
+        return -(-W // self.mesh), -(-H // mh)
+
+
+def _bgcfg(cfg, kw):
+    if cfg is None:
+        cfg = BgConfig(**kw)
+    return cfg
+
+
+def _frame(img, calib):
+    if img.dtype == torch.float32:
+        return _abi.IPP_F32, None
+    if img.dtype in (torch.uint16, torch.int16):
+        if calib is None:
+            raise ValueError("uint16 frames need calib=(inv_flat, bias[, bias_map])")
+        inv_flat, bias = calib[0], calib[1]
+        bias_map = calib[2] if len(calib) > 2 else None
+        return _abi.IPP_U16, _abi.Calib(_ptr(bias_map), float(bias), 0, _ptr(inv_flat))
+    raise TypeError(f"unsupported frame dtype {img.dtype}")
+
+
+def bg_estimate(img, mask=None, cfg: BgConfig | None = None, raw=False, calib=None, ws=None, **kw):
+    """Filtered mesh background and rms grids, float32 [ny, nx] (ipp_bg_estimate)."""
+    L = load()
+    cfg = _bgcfg(cfg, kw)
+    _need_cuda(img, "img")
+    H, W = img.shape
+    dtype, cal = _frame(img, calib)
+    p = cfg.c()
+    nx, ny = cfg.grid(W, H)
+    dev = img.device
+    bkg = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    rms = torch.empty_like(bkg)
+    rb = torch.empty_like(bkg) if raw else None
+    rr = torch.empty_like(bkg) if raw else None
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    need = L.ipp_bg_estimate_workspace_size(W, H, p)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    m = None if mask is None else mask.to(torch.uint8).contiguous()
+    _abi.check("ipp_bg_estimate", L.ipp_bg_estimate(
+        _ptr(img), dtype, W, H, img.stride(0), _ptr(m), cal, p, _ptr(bkg), _ptr(rms), _ptr(rb), _ptr(rr),
+        _ptr(status), _ptr(ws), ws.numel(), _stream()))
+    if raw:
+        return bkg, rms, rb, rr, status
+    return bkg, rms
+
+
+def bg_subtract(img, mesh_bkg, cfg: BgConfig | None = None, bkg_map=False, calib=None, out=None, **kw):
+    """Background-subtracted frame (ipp_bg_subtract); optionally the background map."""
+    L = load()
+    cfg = _bgcfg(cfg, kw)
+    _need_cuda(img, "img")
+    _need_cuda(mesh_bkg, "mesh_bkg", torch.float32)
+    H, W = img.shape
+    dtype, cal = _frame(img, calib)
+    sub = out if out is not None else torch.empty((H, W), dtype=torch.float32, device=img.device)
+    bmap = torch.empty_like(sub) if bkg_map else None
+    _abi.check("ipp_bg_subtract", L.ipp_bg_subtract(
+        _ptr(img), dtype, W, H, img.stride(0), cal, _ptr(mesh_bkg.contiguous()), cfg.c(), _ptr(sub),
+        sub.stride(0), _ptr(bmap), _stream()))
+    return (sub, bmap) if bkg_map else sub
+
+
+_STAT_TYPES = dict(area=torch.int32, first=torch.int64, xmin=torch.int32, xmax=torch.int32,
+                   ymin=torch.int32, ymax=torch.int32, peak=torch.float32, flux=torch.float32,
+                   xbar=torch.float32, ybar=torch.float32)
+
+
+def _alloc_stats(max_src, dev):
+    return {k: torch.empty(max(max_src, 1), dtype=t, device=dev) for k, t in _STAT_TYPES.items()}
+
+
+def _stats_c(st):
+    return _abi.SrcStats(*[_ptr(st[k]) for k in _STAT_TYPES])
+
+
+def detect_label(sub, mesh_rms=None, cfg: BgConfig | None = None, k=1.5, thresh_abs=0.0, min_area=5,
+                 mask_in=None, max_src=None, ws=None, **kw):
+    """Labels, device source count and per-source stats (ipp_detect_label).
+
+    mask_in: optional packed bit mask (uint32 words, ceil(W/32) per row) that
+    replaces the threshold."""
+    L = load()
+    cfg = _bgcfg(cfg, kw)
+    _need_cuda(sub, "sub", torch.float32)
+    H, W = sub.shape
+    dev = sub.device
+    if max_src is None:
+        max_src = max(1024, (H * W) // 64)
+    labels = torch.empty((H, W), dtype=torch.int32, device=dev)
+    n_src = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = _alloc_stats(max_src, dev)
+    need = L.ipp_detect_label_workspace_size(W, H)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    mi = None
+    if mask_in is not None:
+        _need_cuda(mask_in, "mask_in")
+        mi = mask_in.contiguous()
+    rms = None if mesh_rms is None else mesh_rms.contiguous()
+    _abi.check("ipp_detect_label", L.ipp_detect_label(
+        _ptr(sub), W, H, sub.stride(0), _ptr(rms), cfg.c(), _abi.DetParams(k, thresh_abs, min_area, 0),
+        _ptr(mi), _ptr(labels), _ptr(n_src), max_src, _stats_c(st), _ptr(ws), ws.numel(), _stream()))
+    return labels, n_src, st
+
+
+def centroid(sub, x0, y0, n_src=None, fwhm_win=3.0, max_iter=16, tol2=1e-8, max_src=None):
+    """Windowed centroids (ipp_centroid); returns x, y, niter, flags."""
+    L = load()
+    _need_cuda(sub, "sub", torch.float32)
+    H, W = sub.shape
+    n = x0.numel() if max_src is None else max_src
+    if n_src is None:
+        n_src = torch.tensor([x0.numel()], dtype=torch.int32, device=sub.device)
+    x = torch.empty(max(n, 1), dtype=torch.float32, device=sub.device)
+    y, it = torch.empty_like(x), torch.empty(max(n, 1), dtype=torch.int32, device=sub.device)
+    fl = torch.empty_like(it)
+    _abi.check("ipp_centroid", L.ipp_centroid(
+        _ptr(sub), W, H, sub.stride(0), _ptr(n_src), n, _ptr(x0.contiguous()), _ptr(y0.contiguous()),
+        _abi.CenParams(fwhm_win, max_iter, tol2, 0), _ptr(x), _ptr(y), _ptr(it), _ptr(fl), _stream()))
+    return x[:n], y[:n], it[:n], fl[:n]
+
+
+def aperture_phot(sub, x, y, n_src=None, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann=10, max_src=None):
+    """Aperture photometry with a sky annulus (ipp_aperture_phot)."""
+    L = load()
+    _need_cuda(sub, "sub", torch.float32)
+    H, W = sub.shape
+    n = x.numel() if max_src is None else max_src
+    if n_src is None:
+        n_src = torch.tensor([x.numel()], dtype=torch.int32, device=sub.device)
+    dev = sub.device
+    out = dict(flux=torch.empty(max(n, 1), dtype=torch.float32, device=dev))
+    out["sky"] = torch.empty_like(out["flux"])
+    out["area"] = torch.empty_like(out["flux"])
+    out["n_ann"] = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    out["flags"] = torch.empty_like(out["n_ann"])
+    _abi.check("ipp_aperture_phot", L.ipp_aperture_phot(
+        _ptr(sub), W, H, sub.stride(0), _ptr(n_src), n, _ptr(x.contiguous()), _ptr(y.contiguous()),
+        _abi.PhotParams(r_ap, r_in, r_out, min_ann), _ptr(out["flux"]), _ptr(out["sky"]), _ptr(out["area"]),
+        _ptr(out["n_ann"]), _ptr(out["flags"]), _stream()))
+    return {k: v[:n] for k, v in out.items()}
+
+
+class Extractor:
+    """Preallocated outputs and workspace for repeated ipp_extract calls on
+    frames of one shape (the per-frame path without allocations)."""
+
+    def __init__(self, W, H, cfg: BgConfig | None = None, k=1.5, thresh_abs=0.0, min_area=5, fwhm_win=3.0,
+                 cen_iter=16, tol2=1e-8, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann=10, max_src=None,
+                 device="cuda"):
+        L = load()
+        self.L, self.W, self.H = L, W, H
+        self.cfg = cfg or BgConfig()
+        self.max_src = max_src if max_src is not None else max(4096, (W * H) // 256)
+        dev = torch.device(device)
+        nx, ny = self.cfg.grid(W, H)
+        f32, i32 = torch.float32, torch.int32
+        o = dict(mesh_bkg=torch.empty((ny, nx), dtype=f32, device=dev))
+        o["mesh_rms"] = torch.empty_like(o["mesh_bkg"])
+        o["sub"] = torch.empty((H, W), dtype=f32, device=dev)
+        o["labels"] = torch.empty((H, W), dtype=i32, device=dev)
+        o["n_src"] = torch.zeros(1, dtype=i32, device=dev)
+        o["status"] = torch.zeros(1, dtype=i32, device=dev)
+        n = self.max_src
+        for key in ("x", "y", "flux", "sky", "area"):
+            o[key] = torch.empty(n, dtype=f32, device=dev)
+        for key in ("cen_flags", "n_ann", "phot_flags"):
+            o[key] = torch.empty(n, dtype=i32, device=dev)
+        self.stats = _alloc_stats(n, dev)
+        self.out = o
+        self.c_out = _abi.CatalogOut(
+            _ptr(o["mesh_bkg"]), _ptr(o["mesh_rms"]), _ptr(o["sub"]), _ptr(o["labels"]), _ptr(o["n_src"]),
+            _stats_c(self.stats), _ptr(o["x"]), _ptr(o["y"]), _ptr(o["cen_flags"]), _ptr(o["flux"]),
+            _ptr(o["sky"]), _ptr(o["area"]), _ptr(o["n_ann"]), _ptr(o["phot_flags"]), _ptr(o["status"]))
+        self.bp = self.cfg.c()
+        self.dp = _abi.DetParams(k, thresh_abs, min_area, 0)
+        self.cp = _abi.CenParams(fwhm_win, cen_iter, tol2, 0)
+        self.pp = _abi.PhotParams(r_ap, r_in, r_out, min_ann)
+        need = L.ipp_extract_workspace_size(W, H, self.bp)
+        self.ws = torch.empty(need, dtype=torch.uint8, device=dev)
+
+    def __call__(self, img, calib=None, stream=None):
+        _need_cuda(img, "img")
+        if tuple(img.shape) != (self.H, self.W):
+            raise ValueError(f"frame shape {tuple(img.shape)} != {(self.H, self.W)}")
+        dtype, cal = _frame(img, calib)
+        s = stream.cuda_stream if stream is not None else _stream()
+        _abi.check("ipp_extract", self.L.ipp_extract(
+            _ptr(img), dtype, self.W, self.H, img.stride(0), cal, self.bp, self.dp, self.cp, self.pp,
+            self.max_src, self.c_out, _ptr(self.ws), self.ws.numel(), s))
+        return self.out
+
+
+_BG_KEYS = ("mesh", "mesh_h", "filter_size", "maxiters", "min_valid", "nsigma", "estimator",
+            "median_factor", "mean_factor")
+
+
+def extract(img, cfg: BgConfig | None = None, calib=None, **kw):
+    """The whole catalog path of one frame (ipp_extract); returns a dict of tensors.
+    Background keywords (mesh, filter_size, ...) build the BgConfig; the others
+    go to Extractor."""
+    H, W = img.shape
+    bgkw = {k: kw.pop(k) for k in list(kw) if k in _BG_KEYS}
+    if cfg is None:
+        cfg = BgConfig(**bgkw)
+    ex = Extractor(W, H, cfg, device=img.device, **kw)
+    out = dict(ex(img, calib))
+    out["stats"] = ex.stats
+    return out
+
+
+def psf_fit(stamps, init=None, weights=None, model=PSF_MOFFAT, beta=2.5, max_iter=50, lambda0=1e-3):
+    """Batched Levenberg-Marquardt PSF fit (ipp_psf_fit)."""
+    L = load()
+    _need_cuda(stamps, "stamps", torch.float32)
+    N, S = stamps.shape[0], stamps.shape[-1]
+    dev = stamps.device
+    out = dict(params=torch.empty((N, 7), dtype=torch.float32, device=dev),
+               chi2=torch.empty(N, dtype=torch.float32, device=dev),
+               iters=torch.empty(N, dtype=torch.int32, device=dev),
+               flags=torch.empty(N, dtype=torch.int32, device=dev))
+    _abi.check("ipp_psf_fit", L.ipp_psf_fit(
+        _ptr(stamps.contiguous()), N, S, _ptr(None if weights is None else weights.contiguous()),
+        _ptr(None if init is None else init.contiguous()), _abi.FitParams(model, beta, max_iter, lambda0),
+        _ptr(out["params"]), _ptr(out["chi2"]), _ptr(out["iters"]), _ptr(out["flags"]), _stream()))
+    return out
+
+
+def _psf_fwd(params, S, model, beta):
+    L = load()
+    N = params.shape[0]
+    m = torch.empty((N, S, S), dtype=torch.float32, device=params.device)
+    _abi.check("ipp_psf_model_fwd", L.ipp_psf_model_fwd(
+        _ptr(params.contiguous()), N, S, _abi.FitParams(model, beta, 0, 0.0), _ptr(m), _stream()))
+    return m
+
+
+def _psf_adj(params, grad, S, model, beta):
+    L = load()
+    N = params.shape[0]
+    g = torch.empty((N, 7), dtype=torch.float32, device=params.device)
+    _abi.check("ipp_psf_model_adj", L.ipp_psf_model_adj(
+        _ptr(params.contiguous()), N, S, _abi.FitParams(model, beta, 0, 0.0), _ptr(grad.contiguous()),
+        _ptr(g), _stream()))
+    return g
+
+
+class PSFModel(torch.autograd.Function):
+    """Differentiable PSF images m[N, S, S] of params[N, 7]: forward and the
+    hand-written adjoint (vector-Jacobian product) are CUDA kernels."""
+
+    @staticmethod
+    def forward(ctx, params, S=15, model=PSF_MOFFAT, beta=2.5):
+        params = params.detach().to(torch.float32).contiguous()
+        ctx.save_for_backward(params)
+        ctx.cfg = (S, model, beta)
+        return _psf_fwd(params, S, model, beta)
+
+    @staticmethod
+    def backward(ctx, grad):
+        (params,) = ctx.saved_tensors
+        S, model, beta = ctx.cfg
+        return _psf_adj(params, grad.to(torch.float32), S, model, beta), None, None, None
+
+
+def psf_model(params, S=15, model=PSF_MOFFAT, beta=2.5):
+    return PSFModel.apply(params, S, model, beta)

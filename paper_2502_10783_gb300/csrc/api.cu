@@ -1,0 +1,318 @@
+// api.cu -- the C ABI of libipp: argument validation, workspace layout and the
+// launch sequences of each call.  All calls are asynchronous on `stream`.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "jobs.cuh"
+
+using namespace ipp;
+
+// ---- error reporting --------------------------------------------------------
+static thread_local char g_detail[512] = "";
+
+int ipp_set_error(int status, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int ipp_check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return IPP_OK;
+}
+
+extern "C" const char* ipp_status_string(int status) {
+    switch (status) {
+        case IPP_OK: return "ok";
+        case IPP_ERR_INVALID_ARG: return "invalid argument";
+        case IPP_ERR_CUDA: return "CUDA error";
+        case IPP_ERR_CAPACITY: return "capacity exceeded";
+        case IPP_ERR_NO_VALID_MESH: return "no valid mesh";
+        case IPP_ERR_TIMEOUT: return "device wait timed out";
+        case IPP_ERR_NOT_SUPPORTED: return "not supported";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* ipp_last_error_detail(void) { return g_detail; }
+
+extern "C" int ipp_version(int* major, int* minor, int* patch) {
+    if (!major || !minor || !patch) return IPP_ERR_INVALID_ARG;
+    *major = 0; *minor = 1; *patch = 0;
+    return IPP_OK;
+}
+
+#define REQUIRE(cond, ...) \
+    do { if (!(cond)) return ipp_set_error(IPP_ERR_INVALID_ARG, __VA_ARGS__); } while (0)
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---- validation helpers -------------------------------------------------------
+static int check_frame(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch, const ipp_calib* cal) {
+    REQUIRE(img, "img is NULL");
+    REQUIRE(W > 0 && H > 0, "W, H must be positive (got %lld, %lld)", (long long)W, (long long)H);
+    REQUIRE(W < (1ll << 31) && H < (1ll << 31), "frame dimensions too large");
+    REQUIRE(pitch >= W, "pitch %lld < W %lld", (long long)pitch, (long long)W);
+    REQUIRE(dtype == IPP_F32 || dtype == IPP_U16, "unknown dtype %d", dtype);
+    if (dtype == IPP_U16) REQUIRE(cal && cal->inv_flat, "IPP_U16 input needs cal->inv_flat");
+    return IPP_OK;
+}
+
+static int check_bg(const ipp_bg_params* p) {
+    REQUIRE(p, "bg params NULL");
+    REQUIRE(p->mesh_w >= 4 && p->mesh_h >= 4, "mesh size must be >= 4 (got %d x %d)", p->mesh_w, p->mesh_h);
+    REQUIRE((int64_t)p->mesh_w * p->mesh_h <= 16384, "mesh area %d > 16384", p->mesh_w * p->mesh_h);
+    REQUIRE(p->filter_w >= 1 && p->filter_h >= 1 && (p->filter_w & 1) && (p->filter_h & 1) &&
+                p->filter_w <= 7 && p->filter_h <= 7, "filter must be odd and <= 7");
+    REQUIRE(p->maxiters >= 1, "maxiters must be >= 1");
+    REQUIRE(p->min_valid >= 1, "min_valid must be >= 1");
+    REQUIRE(p->estimator >= 0 && p->estimator <= 3, "unknown estimator %d", p->estimator);
+    REQUIRE(p->nsigma > 0, "nsigma must be > 0");
+    return IPP_OK;
+}
+
+static void grid_of(int64_t W, int64_t H, const ipp_bg_params* p, int* nx, int* ny) {
+    *nx = (int)cdiv(W, p->mesh_w);
+    *ny = (int)cdiv(H, p->mesh_h);
+}
+
+// ---- background ---------------------------------------------------------------
+extern "C" size_t ipp_bg_estimate_workspace_size(int64_t W, int64_t H, const ipp_bg_params* p) {
+    if (!p || p->mesh_w < 1 || p->mesh_h < 1 || W <= 0 || H <= 0) return 0;
+    int nx, ny;
+    grid_of(W, H, p, &nx, &ny);
+    return 4 * a256((size_t)nx * ny * sizeof(float));
+}
+
+static int bg_estimate_impl(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                            const uint8_t* mask, const ipp_calib* cal, const ipp_bg_params* p,
+                            float* mesh_bkg, float* mesh_rms, float* raw_bkg, float* raw_rms,
+                            int32_t* status_dev, void* ws, size_t ws_bytes, cudaStream_t s) {
+    int nx, ny;
+    grid_of(W, H, p, &nx, &ny);
+    size_t nb = a256((size_t)nx * ny * sizeof(float));
+    unsigned char* w = (unsigned char*)ws;
+    float* rb = raw_bkg ? raw_bkg : (float*)(w + 0 * nb);
+    float* rr = raw_rms ? raw_rms : (float*)(w + 1 * nb);
+    float* fb = (float*)(w + 2 * nb);
+    float* fr = (float*)(w + 3 * nb);
+    MeshJob J;
+    J.img = img; J.dtype = dtype; J.W = W; J.H = H; J.pitch = pitch; J.mask = mask;
+    J.bias_map = cal ? cal->bias_map : nullptr; J.bias = cal ? cal->bias : 0.f;
+    J.inv_flat = cal ? cal->inv_flat : nullptr;
+    J.mesh_w = p->mesh_w; J.mesh_h = p->mesh_h; J.nx = nx; J.ny = ny;
+    J.maxiters = p->maxiters; J.min_valid = p->min_valid; J.estimator = p->estimator;
+    J.nsigma = p->nsigma; J.mf = p->median_factor; J.mnf = p->mean_factor;
+    J.raw_bkg = rb; J.raw_rms = rr;
+    if (int e = ipp_launch_mesh_stats(J, s)) return e;
+    return ipp_launch_mesh_filter(rb, rr, fb, fr, nx, ny, p->filter_w, p->filter_h, mesh_bkg, mesh_rms,
+                                  status_dev, s);
+}
+
+extern "C" int ipp_bg_estimate(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                               const uint8_t* mask, const ipp_calib* cal, const ipp_bg_params* p,
+                               float* mesh_bkg, float* mesh_rms, float* raw_bkg, float* raw_rms,
+                               int32_t* status_dev, void* ws, size_t ws_bytes, void* stream) {
+    if (int e = check_frame(img, dtype, W, H, pitch, cal)) return e;
+    if (int e = check_bg(p)) return e;
+    REQUIRE(mesh_bkg && mesh_rms, "mesh outputs NULL");
+    size_t need = ipp_bg_estimate_workspace_size(W, H, p);
+    REQUIRE(ws && ws_bytes >= need, "workspace of %zu bytes needed", need);
+    return bg_estimate_impl(img, dtype, W, H, pitch, mask, cal, p, mesh_bkg, mesh_rms, raw_bkg, raw_rms,
+                            status_dev, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int ipp_bg_subtract(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                               const ipp_calib* cal, const float* mesh_bkg, const ipp_bg_params* p,
+                               float* sub, int64_t sub_pitch, float* bkg_map, void* stream) {
+    if (int e = check_frame(img, dtype, W, H, pitch, cal)) return e;
+    if (int e = check_bg(p)) return e;
+    REQUIRE(mesh_bkg && sub, "mesh_bkg / sub NULL");
+    REQUIRE(sub_pitch >= W, "sub_pitch < W");
+    int nx, ny;
+    grid_of(W, H, p, &nx, &ny);
+    SubJob J;
+    J.img = img; J.dtype = dtype; J.W = W; J.H = H; J.pitch = pitch;
+    J.bias_map = cal ? cal->bias_map : nullptr; J.bias = cal ? cal->bias : 0.f;
+    J.inv_flat = cal ? cal->inv_flat : nullptr;
+    J.mesh = mesh_bkg; J.nx = nx; J.ny = ny; J.mesh_w = p->mesh_w; J.mesh_h = p->mesh_h;
+    J.sub = sub; J.sub_pitch = sub_pitch; J.bkg_map = bkg_map;
+    return ipp_launch_bg_subtract(J, (cudaStream_t)stream);
+}
+
+// ---- detection ------------------------------------------------------------------
+static int check_stats(const ipp_src_stats* st) {
+    REQUIRE(st && st->area && st->first && st->xmin && st->xmax && st->ymin && st->ymax && st->peak &&
+                st->flux && st->xbar && st->ybar, "stats arrays NULL");
+    return IPP_OK;
+}
+
+extern "C" size_t ipp_detect_label_workspace_size(int64_t W, int64_t H) {
+    if (W <= 0 || H <= 0) return 0;
+    return ipp_ccl_workspace_size(W, H);
+}
+
+extern "C" int ipp_detect_label(const float* sub, int64_t W, int64_t H, int64_t pitch,
+                                const float* mesh_rms, const ipp_bg_params* bp, const ipp_det_params* dp,
+                                const uint32_t* mask_in, int32_t* labels, int32_t* n_src_dev,
+                                int32_t max_src, const ipp_src_stats* stats, void* ws, size_t ws_bytes,
+                                void* stream) {
+    if (int e = check_frame(sub, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(dp, "det params NULL");
+    REQUIRE(dp->min_area >= 1, "min_area must be >= 1");
+    if (!mask_in) {
+        if (int e = check_bg(bp)) return e;
+        REQUIRE(mesh_rms, "mesh_rms NULL (needed without mask_in)");
+        REQUIRE(dp->k >= 0.f, "k must be >= 0");
+    }
+    REQUIRE(labels && n_src_dev, "labels / n_src_dev NULL");
+    REQUIRE(max_src >= 0, "max_src < 0");
+    if (int e = check_stats(stats)) return e;
+    size_t need = ipp_detect_label_workspace_size(W, H);
+    REQUIRE(ws && ws_bytes >= need, "workspace of %zu bytes needed", need);
+    DetectArgs A;
+    memset(&A, 0, sizeof(A));
+    A.mode = mask_in ? 1 : 0;
+    A.W = W; A.H = H; A.dtype = IPP_F32;
+    A.sub = const_cast<float*>(sub); A.sub_pitch = pitch;
+    A.mesh_rms = mesh_rms;
+    if (bp) {
+        grid_of(W, H, bp, &A.nx, &A.ny);
+        A.mesh_w = bp->mesh_w; A.mesh_h = bp->mesh_h;
+    }
+    A.k = dp->k; A.thresh_abs = dp->thresh_abs; A.min_area = dp->min_area; A.mask_in = mask_in;
+    A.labels = labels; A.n_src_dev = n_src_dev; A.max_src = max_src; A.stats = *stats; A.ws = ws;
+    return ipp_launch_detect(A, (cudaStream_t)stream);
+}
+
+// ---- per source -------------------------------------------------------------------
+extern "C" int ipp_centroid(const float* sub, int64_t W, int64_t H, int64_t pitch,
+                            const int32_t* n_src_dev, int32_t max_src, const float* x0, const float* y0,
+                            const ipp_cen_params* p, float* x, float* y, int32_t* niter, int32_t* flags,
+                            void* stream) {
+    if (int e = check_frame(sub, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(p && p->fwhm_win > 0.f && p->max_iter >= 1 && p->tol2 >= 0.f, "bad centroid params");
+    REQUIRE(p->fwhm_win <= 16.f, "fwhm_win above 16 px not supported");
+    REQUIRE(n_src_dev && x0 && y0 && x && y && flags, "NULL pointer");
+    REQUIRE(max_src >= 0, "max_src < 0");
+    CenJob J;
+    J.sub = sub; J.W = W; J.H = H; J.pitch = pitch; J.n_src_dev = n_src_dev; J.max_src = max_src;
+    J.x0 = x0; J.y0 = y0;
+    J.sw = (float)(p->fwhm_win / 2.3548200450309493);
+    J.rad = 4.0f * J.sw;
+    J.tol2 = p->tol2; J.max_iter = p->max_iter;
+    J.x = x; J.y = y; J.niter = niter; J.flags = flags;
+    return ipp_launch_centroid(J, (cudaStream_t)stream);
+}
+
+extern "C" int ipp_aperture_phot(const float* sub, int64_t W, int64_t H, int64_t pitch,
+                                 const int32_t* n_src_dev, int32_t max_src, const float* x, const float* y,
+                                 const ipp_phot_params* p, float* flux, float* sky, float* area,
+                                 int32_t* n_ann, int32_t* flags, void* stream) {
+    if (int e = check_frame(sub, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(p && p->r_ap > 0.f && p->r_in >= 0.f && p->r_out > p->r_in, "bad aperture params");
+    REQUIRE(p->r_ap <= 16.f, "r_ap above 16 px not supported");
+    REQUIRE(n_src_dev && x && y && flux, "NULL pointer");
+    REQUIRE(max_src >= 0, "max_src < 0");
+    PhotJob J;
+    J.sub = sub; J.W = W; J.H = H; J.pitch = pitch; J.n_src_dev = n_src_dev; J.max_src = max_src;
+    J.x = x; J.y = y; J.r_ap = p->r_ap; J.r_in = p->r_in; J.r_out = p->r_out; J.min_ann = p->min_ann;
+    J.flux = flux; J.sky = sky; J.area = area; J.n_ann = n_ann; J.flags = flags;
+    return ipp_launch_aperture(J, (cudaStream_t)stream);
+}
+
+// ---- fused frame ---------------------------------------------------------------------
+extern "C" size_t ipp_extract_workspace_size(int64_t W, int64_t H, const ipp_bg_params* bp) {
+    if (!bp) return 0;
+    return a256(ipp_bg_estimate_workspace_size(W, H, bp)) + ipp_ccl_workspace_size(W, H);
+}
+
+extern "C" int ipp_extract(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                           const ipp_calib* cal, const ipp_bg_params* bp, const ipp_det_params* dp,
+                           const ipp_cen_params* cp, const ipp_phot_params* pp, int32_t max_src,
+                           const ipp_catalog_out* out, void* ws, size_t ws_bytes, void* stream) {
+    if (int e = check_frame(img, dtype, W, H, pitch, cal)) return e;
+    if (int e = check_bg(bp)) return e;
+    REQUIRE(dp && cp && pp && out, "NULL parameter struct");
+    REQUIRE(out->mesh_bkg && out->mesh_rms && out->sub && out->labels && out->n_src_dev, "NULL output");
+    REQUIRE(out->x && out->y && out->cen_flags && out->flux, "NULL per-source output");
+    if (int e = check_stats(&out->stats)) return e;
+    REQUIRE(dp->min_area >= 1 && dp->k >= 0.f, "bad detection params");
+    REQUIRE(cp->fwhm_win > 0.f && cp->fwhm_win <= 16.f && cp->max_iter >= 1, "bad centroid params");
+    REQUIRE(pp->r_ap > 0.f && pp->r_ap <= 16.f && pp->r_out > pp->r_in && pp->r_in >= 0.f, "bad aperture params");
+    REQUIRE(pp->r_out <= 16.f, "r_out above 16 px not supported");
+    REQUIRE(max_src >= 0, "max_src < 0");
+    size_t need = ipp_extract_workspace_size(W, H, bp);
+    REQUIRE(ws && ws_bytes >= need, "workspace of %zu bytes needed", need);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* w = (unsigned char*)ws;
+    size_t bgws = a256(ipp_bg_estimate_workspace_size(W, H, bp));
+    if (int e = bg_estimate_impl(img, dtype, W, H, pitch, nullptr, cal, bp, out->mesh_bkg, out->mesh_rms,
+                                 nullptr, nullptr, out->status_dev, w, bgws, s))
+        return e;
+    DetectArgs A;
+    memset(&A, 0, sizeof(A));
+    A.mode = 2;
+    A.W = W; A.H = H; A.img = img; A.dtype = dtype; A.pitch = pitch;
+    A.bias_map = cal ? cal->bias_map : nullptr; A.bias = cal ? cal->bias : 0.f;
+    A.inv_flat = cal ? cal->inv_flat : nullptr;
+    A.mesh_bkg = out->mesh_bkg; A.sub = out->sub; A.sub_pitch = W; A.mesh_rms = out->mesh_rms;
+    grid_of(W, H, bp, &A.nx, &A.ny);
+    A.mesh_w = bp->mesh_w; A.mesh_h = bp->mesh_h;
+    A.k = dp->k; A.thresh_abs = dp->thresh_abs; A.min_area = dp->min_area; A.mask_in = nullptr;
+    A.labels = out->labels; A.n_src_dev = out->n_src_dev; A.max_src = max_src; A.stats = out->stats;
+    A.ws = w + bgws;
+    if (int e = ipp_launch_detect(A, s)) return e;
+    ipp_cen_params c = *cp;
+    if (int e = ipp_centroid(out->sub, W, H, W, out->n_src_dev, max_src, out->stats.xbar, out->stats.ybar, &c,
+                             out->x, out->y, nullptr, out->cen_flags, stream))
+        return e;
+    return ipp_aperture_phot(out->sub, W, H, W, out->n_src_dev, max_src, out->x, out->y, pp, out->flux,
+                             out->sky, out->area, out->n_ann, out->phot_flags, stream);
+}
+
+// ---- PSF fit and differentiable model --------------------------------------------
+static int check_fit(const ipp_fit_params* p, int32_t S) {
+    REQUIRE(p, "fit params NULL");
+    REQUIRE(p->model == IPP_PSF_MOFFAT || p->model == IPP_PSF_GAUSS, "unknown PSF model %d", p->model);
+    REQUIRE(p->model != IPP_PSF_MOFFAT || p->beta > 1.0f, "Moffat beta must be > 1");
+    REQUIRE(S >= 3 && S <= 32, "stamp size %d outside 3..32", S);
+    return IPP_OK;
+}
+
+extern "C" int ipp_psf_fit(const float* stamps, int64_t N, int32_t S, const float* weights,
+                           const float* init, const ipp_fit_params* p, float* params, float* chi2,
+                           int32_t* iters, int32_t* flags, void* stream) {
+    if (int e = check_fit(p, S)) return e;
+    REQUIRE(N >= 0, "N < 0");
+    if (N == 0) return IPP_OK;
+    REQUIRE(stamps && params && chi2, "NULL pointer");
+    REQUIRE(p->max_iter >= 1 && p->lambda0 > 0.f, "bad LM params");
+    FitJob J;
+    J.stamps = stamps; J.N = N; J.S = S; J.weights = weights; J.init = init;
+    J.model = p->model; J.beta = p->beta; J.max_iter = p->max_iter; J.lambda0 = p->lambda0;
+    J.params = params; J.chi2 = chi2; J.iters = iters; J.flags = flags;
+    return ipp_launch_psf_fit(J, (cudaStream_t)stream);
+}
+
+extern "C" int ipp_psf_model_fwd(const float* params, int64_t N, int32_t S, const ipp_fit_params* p,
+                                 float* model, void* stream) {
+    if (int e = check_fit(p, S)) return e;
+    REQUIRE(N >= 0, "N < 0");
+    if (N == 0) return IPP_OK;
+    REQUIRE(params && model, "NULL pointer");
+    return ipp_launch_psf_fwd(params, N, S, p->model, p->beta, model, (cudaStream_t)stream);
+}
+
+extern "C" int ipp_psf_model_adj(const float* params, int64_t N, int32_t S, const ipp_fit_params* p,
+                                 const float* grad_model, float* grad_params, void* stream) {
+    if (int e = check_fit(p, S)) return e;
+    REQUIRE(N >= 0, "N < 0");
+    if (N == 0) return IPP_OK;
+    REQUIRE(params && grad_model && grad_params, "NULL pointer");
+    return ipp_launch_psf_adj(params, N, S, p->model, p->beta, grad_model, grad_params, (cudaStream_t)stream);
+}

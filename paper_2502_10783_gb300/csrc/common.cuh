@@ -1,0 +1,89 @@
+// common.cuh -- small device helpers shared by the kernels of libipp.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ipp.h"
+
+#define IPP_HD __host__ __device__ __forceinline__
+#define IPP_D __device__ __forceinline__
+
+namespace ipp {
+
+constexpr int kWarp = 32;
+
+// Float <-> order-preserving uint32 key (negative values reversed), so that
+// integer comparisons and atomics order floats correctly.  NaNs map outside the
+// keys of -inf..+inf.
+IPP_D uint32_t fkey(float v) {
+    uint32_t u = __float_as_uint(v);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+IPP_D float fkey_inv(uint32_t k) {
+    uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(u);
+}
+
+IPP_D float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+IPP_D int warp_sum_i(int v) { return __reduce_add_sync(0xffffffffu, v); }
+
+// ---- double-float (unevaluated sum hi + lo of two FP32 numbers) -----------
+// Knuth's TwoSum and an FMA-based exact product; used for sums whose error
+// must stay far below FP32 rounding without using the (slow) FP64 pipe.
+struct df {
+    float hi, lo;
+};
+IPP_D df df_make(float a) { return df{a, 0.0f}; }
+IPP_D df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df{s, e};
+}
+IPP_D df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), s.lo);
+    return two_sum(s.hi, lo);
+}
+IPP_D df df_add_f(df a, float b) {
+    df s = two_sum(a.hi, b);
+    return two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+// exact square of a float as a double-float
+IPP_D df sq_exact(float a) {
+    float p = __fmul_rn(a, a);
+    float e = __fmaf_rn(a, a, -p);
+    return df{p, e};
+}
+IPP_D double df_to_d(df a) { return (double)a.hi + (double)a.lo; }
+IPP_D df warp_sum_df(df v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        df w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, w);
+    }
+    return v;
+}
+
+// Keys (1981) cubic-convolution weights, a = -1/2, for fractional offset s in
+// [0, 1): nodes at distances 1 + s, s, 1 - s, 2 - s.
+IPP_D void keys_weights(float s, float w[4]) {
+    float s2 = s * s, s3 = s2 * s;
+    w[0] = -0.5f * s3 + s2 - 0.5f * s;
+    w[1] = 1.5f * s3 - 2.5f * s2 + 1.0f;
+    w[2] = -1.5f * s3 + 2.0f * s2 + 0.5f * s;
+    w[3] = 0.5f * s3 - 0.5f * s2;
+}
+
+IPP_HD int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+IPP_HD int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace ipp
+
+// host-side error recording (api.cu)
+int ipp_set_error(int status, const char* fmt, ...);
+int ipp_check_launch(const char* what);

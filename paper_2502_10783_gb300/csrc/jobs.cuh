@@ -1,0 +1,124 @@
+// jobs.cuh -- argument bundles passed from the C ABI (api.cu) to the kernel
+// launchers of each translation unit, and the launchers' declarations.
+#pragma once
+#include "common.cuh"
+
+namespace ipp {
+
+struct MeshJob {
+    const void* img;
+    int dtype;
+    int64_t W, H, pitch;
+    const uint8_t* mask;
+    const float* bias_map;
+    float bias;
+    const float* inv_flat;
+    int mesh_w, mesh_h, nx, ny;
+    int maxiters, min_valid, estimator;
+    double nsigma, mf, mnf;
+    float* raw_bkg;  // [ny*nx]
+    float* raw_rms;  // [ny*nx], -1 marks an invalid mesh
+};
+
+struct SubJob {
+    const void* img;
+    int dtype;
+    int64_t W, H, pitch;
+    const float* bias_map;
+    float bias;
+    const float* inv_flat;
+    const float* mesh;
+    int nx, ny, mesh_w, mesh_h;
+    float* sub;
+    int64_t sub_pitch;
+    float* bkg_map;
+};
+
+struct CenJob {
+    const float* sub;
+    int64_t W, H, pitch;
+    const int32_t* n_src_dev;
+    int32_t max_src;
+    const float* x0;
+    const float* y0;
+    float sw, rad, tol2;
+    int max_iter;
+    float* x;
+    float* y;
+    int32_t* niter;
+    int32_t* flags;
+};
+
+struct PhotJob {
+    const float* sub;
+    int64_t W, H, pitch;
+    const int32_t* n_src_dev;
+    int32_t max_src;
+    const float* x;
+    const float* y;
+    float r_ap, r_in, r_out;
+    int min_ann;
+    float* flux;
+    float* sky;
+    float* area;
+    int32_t* n_ann;
+    int32_t* flags;
+};
+
+// detection: mode 0 = threshold a given sub frame, 1 = given bit mask,
+// 2 = fused with interpolation + subtraction of the raw frame
+struct DetectArgs {
+    int mode;
+    int64_t W, H;
+    const void* img;
+    int dtype;
+    int64_t pitch;
+    const float* bias_map;
+    float bias;
+    const float* inv_flat;
+    const float* mesh_bkg;
+    float* sub;
+    int64_t sub_pitch;
+    const float* mesh_rms;
+    int nx, ny, mesh_w, mesh_h;
+    float k, thresh_abs;
+    int min_area;
+    const uint32_t* mask_in;
+    int32_t* labels;
+    int32_t* n_src_dev;
+    int32_t max_src;
+    ipp_src_stats stats;
+    void* ws;
+};
+
+struct FitJob {
+    const float* stamps;
+    int64_t N;
+    int S;
+    const float* weights;
+    const float* init;
+    int model;
+    float beta;
+    int max_iter;
+    float lambda0;
+    float* params;
+    float* chi2;
+    int32_t* iters;
+    int32_t* flags;
+};
+
+}  // namespace ipp
+
+int ipp_launch_mesh_stats(const ipp::MeshJob& J, cudaStream_t s);
+int ipp_launch_mesh_filter(const float* raw_bkg, const float* raw_rms, float* fill_bkg, float* fill_rms,
+                           int nx, int ny, int fw, int fh, float* out_bkg, float* out_rms,
+                           int32_t* status_dev, cudaStream_t s);
+int ipp_launch_bg_subtract(const ipp::SubJob& J, cudaStream_t s);
+size_t ipp_ccl_workspace_size(int64_t W, int64_t H);
+int ipp_launch_detect(const ipp::DetectArgs& A, cudaStream_t s);
+int ipp_launch_centroid(const ipp::CenJob& J, cudaStream_t s);
+int ipp_launch_aperture(const ipp::PhotJob& J, cudaStream_t s);
+int ipp_launch_psf_fit(const ipp::FitJob& J, cudaStream_t s);
+int ipp_launch_psf_fwd(const float* params, int64_t N, int S, int model, float beta, float* model_out, cudaStream_t s);
+int ipp_launch_psf_adj(const float* params, int64_t N, int S, int model, float beta, const float* grad_model,
+                       float* grad_params, cudaStream_t s);

@@ -1,0 +1,144 @@
+"""GPU parity of the background steps (Sec. 2.2.2) against the FP64 oracle:
+mesh statistics + filter (ipp_bg_estimate) and interpolation + subtraction
+(ipp_bg_subtract), element by element on seeded frames.
+
+Tolerances: mesh values 1e-5 relative (the statistics are exact order
+statistics and double-float sums; only the final FP32 rounding and the
+FP32-vs-FP64 median filter of even windows remain).  Subtracted pixels:
+|d| <= 1e-5 * max(|f|, |B|) -- the Keys interpolation is evaluated in FP32
+(relative rounding ~1e-7 of the background)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_util import dev, host, rel_close
+
+pytestmark = pytest.mark.gpu
+
+
+def _cmp_mesh(gb, gr, ob, orr, rtol=1e-5):
+    assert gb.shape == ob.shape
+    okb = rel_close(gb, ob, rtol, 1e-6)
+    okr = rel_close(gr, orr, rtol, 1e-6)
+    assert okb.all(), f"bkg mismatch at {np.argwhere(~okb)[:5]}: {gb[~okb][:5]} vs {ob[~okb][:5]}"
+    assert okr.all(), f"rms mismatch at {np.argwhere(~okr)[:5]}: {gr[~okr][:5]} vs {orr[~okr][:5]}"
+
+
+@pytest.mark.parametrize("shape,mesh,seed", [((1024, 1024), 64, 1001), ((221, 300), 32, 7),
+                                             ((130, 97), 16, 8), ((64, 64), 64, 9)])
+def test_bg_estimate_parity(gpu, orc, shape, mesh, seed):
+    H, W = shape
+    if (H, W) == (1024, 1024):
+        img, _ = synth.frame_gradient_1k(seed)
+    else:
+        img, _ = synth.tiny_frame(W, H, seed, n_stars=6)
+    ob, orr, st = orc.bg_estimate(img, mesh=mesh)
+    gb, gr, rb, rr, status = gpu.bg_estimate(dev(img), mesh=mesh, raw=True)
+    torch.cuda.synchronize()
+    assert int(host(status)[0]) == 0
+    # raw (unfiltered) statistics, valid meshes
+    v = st["valid"] == 1
+    assert np.array_equal(host(rr) >= 0, v)
+    _cmp_mesh(host(rb)[v], host(rr)[v], st["raw_bkg"][v], st["raw_rms"][v])
+    _cmp_mesh(host(gb), host(gr), ob, orr)
+
+
+def test_bg_estimate_survey_frame_full_size(gpu, orc):
+    """4096^2 survey field with hot pixels and cosmic rays, 128 px meshes, the
+    launch configuration of the benchmark: every mesh value against the oracle."""
+    img, _ = synth.frame_survey_4k()
+    ob, orr, st = orc.bg_estimate(img, mesh=128)
+    gb, gr = gpu.bg_estimate(dev(img), mesh=128)
+    _cmp_mesh(host(gb), host(gr), ob, orr)
+
+
+@pytest.mark.parametrize("est", [0, 1, 2, 3])
+def test_bg_estimators(gpu, orc, est):
+    img, _ = synth.tiny_frame(256, 192, 21, n_stars=8)
+    kw = dict(mesh=32, estimator=est, median_factor=3.0, mean_factor=2.0)
+    ob, orr, _ = orc.bg_estimate(img, **kw)
+    gb, gr = gpu.bg_estimate(dev(img), **kw)
+    _cmp_mesh(host(gb), host(gr), ob, orr)
+
+
+def test_bg_mask_and_invalid_fill(gpu, orc):
+    img, _ = synth.tiny_frame(256, 256, 31, n_stars=5)
+    mask = np.zeros(img.shape, np.uint8)
+    mask[0:64, 0:64] = 1            # two fully masked meshes -> invalid, filled
+    mask[100:140, 200:256] = 1      # partial masking
+    img[70, 70] = np.nan            # non-finite pixel excluded
+    ob, orr, st = orc.bg_estimate(img, mask=mask, mesh=32)
+    assert (st["valid"] == 0).sum() >= 2
+    gb, gr = gpu.bg_estimate(dev(img), mask=dev(mask), mesh=32)
+    _cmp_mesh(host(gb), host(gr), ob, orr)
+
+
+def test_bg_maxiters_and_filter_sizes(gpu, orc):
+    img, _ = synth.tiny_frame(320, 256, 41, n_stars=12)
+    for kw in (dict(mesh=32, maxiters=1), dict(mesh=32, maxiters=2, filter_size=1),
+               dict(mesh=40, filter_size=5), dict(mesh=32, nsigma=2.0)):
+        ob, orr, _ = orc.bg_estimate(img, **kw)
+        gb, gr = gpu.bg_estimate(dev(img), **kw)
+        _cmp_mesh(host(gb), host(gr), ob, orr)
+
+
+def test_constant_frame_zero_residual(gpu):
+    img = np.full((300, 260), 1234.5625, np.float32)
+    t = dev(img)
+    gb, gr = gpu.bg_estimate(t, mesh=64)
+    sub = gpu.bg_subtract(t, gb, mesh=64)
+    assert np.all(host(gb) == np.float32(1234.5625)) and np.all(host(gr) == 0)
+    assert np.all(host(sub) == 0.0)
+
+
+def test_no_valid_mesh_status(gpu):
+    img = np.full((64, 64), np.nan, np.float32)
+    gb, gr, rb, rr, status = gpu.bg_estimate(dev(img), mesh=32, raw=True)
+    assert int(host(status)[0]) == 4   # IPP_ERR_NO_VALID_MESH
+    assert np.all(host(gb) == 0)
+
+
+@pytest.mark.parametrize("shape,mesh", [((1024, 1024), 64), ((221, 300), 32), ((77, 131), 8), ((40, 40), 64)])
+def test_bg_subtract_parity(gpu, orc, shape, mesh):
+    H, W = shape
+    img, _ = synth.tiny_frame(W, H, 51, n_stars=5) if H < 1024 else synth.frame_gradient_1k(52)
+    ob, orr, _ = orc.bg_estimate(img, mesh=mesh, min_valid=1)
+    osub, obmap = orc.bg_subtract(img, ob, mesh)
+    gsub, gbmap = gpu.bg_subtract(dev(img), dev(ob), mesh=mesh, bkg_map=True)
+    gsub, gbmap = host(gsub), host(gbmap)
+    scale = np.maximum(np.abs(img), np.abs(obmap))
+    assert np.all(np.abs(gbmap - obmap) <= 1e-5 * scale)
+    assert np.all(np.abs(gsub - osub) <= 1e-5 * scale)
+
+
+def test_bg_subtract_pitched_input(gpu, orc):
+    """row pitch larger than W (a view into a wider buffer)."""
+    img, _ = synth.tiny_frame(203, 150, 61, n_stars=4)
+    wide = np.zeros((150, 256), np.float32)
+    wide[:, :203] = img
+    tw = dev(wide)[:, :203]
+    ob, orr, _ = orc.bg_estimate(img, mesh=32)
+    gb, gr = gpu.bg_estimate(tw, mesh=32)
+    _cmp_mesh(host(gb), host(gr), ob, orr)
+    gsub = host(gpu.bg_subtract(tw, dev(ob), mesh=32))
+    osub, obmap = orc.bg_subtract(img, ob, 32)
+    assert np.all(np.abs(gsub - osub) <= 1e-5 * np.maximum(np.abs(img), np.abs(obmap)))
+
+
+def test_uint16_calibrated_input(gpu, orc):
+    """bias/flat correction fused into the first read: (raw - bias) * (1/flat)."""
+    rng = np.random.default_rng(71)
+    H, W = 200, 260
+    raw = rng.integers(600, 3000, (H, W)).astype(np.uint16)
+    flat = rng.uniform(0.9, 1.1, (H, W)).astype(np.float32)
+    f = orc.calibrate(raw, flat, bias=500.0)
+    ob, orr, _ = orc.bg_estimate(f, mesh=32)
+    inv = dev((1.0 / flat.astype(np.float64)).astype(np.float32))
+    traw = torch.from_numpy(raw.view(np.int16)).cuda().view(torch.uint16) if hasattr(torch, "uint16") else None
+    if traw is None:
+        pytest.skip("torch without uint16")
+    gb, gr = gpu.bg_estimate(traw, mesh=32, calib=(inv, 500.0))
+    # reciprocal-multiply vs divide differ in the last bit of each pixel: the
+    # mesh statistics of such values agree to ~1e-7 relative
+    _cmp_mesh(host(gb), host(gr), ob, orr, rtol=2e-5)

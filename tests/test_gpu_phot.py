@@ -1,0 +1,112 @@
+"""GPU parity of the per-source steps: windowed centroid and aperture
+photometry with a sky annulus, from identical float32 inputs.
+
+Tolerances (derived from the arithmetic):
+  * centroid, converged sources: the stop rule leaves up to ~1e-4 px between
+    two runs that stop one update apart, plus FP32 sums -> 3e-4 px + 2 ulp(x);
+  * annulus membership is decided exactly as the FP64 expression of the oracle,
+    so n_ann and the median sky are exact;
+  * flux: 1e-5 x (|flux| + area x (|sky| + rms)) -- FP32 overlap weights (~1e-6
+    absolute each) times pixel values of order the sky noise."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_util import dev, float_ulp, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def field(orc):
+    img, tr = synth.frame_gradient_1k(1001)
+    out = orc.catalog(img)
+    return img, out
+
+
+def test_centroid_parity(gpu, orc, field):
+    img, out = field
+    x0 = out["stats"]["xbar"].astype(np.float32)
+    y0 = out["stats"]["ybar"].astype(np.float32)
+    ox, oy, oit, ofl = orc.centroid(out["sub"], x0, y0)
+    gx, gy, git, gfl = gpu.centroid(dev(out["sub"]), dev(x0), dev(y0))
+    gx, gy, git, gfl = host(gx), host(gy), host(git), host(gfl)
+    conv = (ofl & 2) == 0
+    assert conv.sum() > 0.5 * len(conv)
+    tol = 3e-4 + 2 * float_ulp(ox)
+    bad = conv & ((np.abs(gx - ox) > tol) | (np.abs(gy - oy) > tol))
+    assert bad.sum() == 0, f"{bad.sum()} converged centroids differ: {np.flatnonzero(bad)[:5]}"
+    # convergence status agrees except where the last step sits at the tolerance
+    agree = ((gfl & 2) == 0) == conv
+    assert agree.mean() > 0.97
+    assert np.array_equal(gfl & 1, ofl & 1)
+
+
+def test_centroid_seed_kept_and_edge(gpu, orc):
+    sub = -np.ones((40, 50), np.float32)
+    x0 = np.array([10.25, 1.0, 48.5], np.float32)
+    y0 = np.array([20.5, 20.0, 38.0], np.float32)
+    ox, oy, oit, ofl = orc.centroid(sub, x0, y0)
+    gx, gy, git, gfl = (host(t) for t in gpu.centroid(dev(sub), dev(x0), dev(y0)))
+    assert np.array_equal(gx, x0) and np.array_equal(gy, y0)
+    assert np.array_equal(gfl, ofl)
+
+
+def test_aperture_parity(gpu, orc, field):
+    img, out = field
+    x = out["x"].astype(np.float32)
+    y = out["y"].astype(np.float32)
+    ph = orc.aperture(out["sub"], x, y)
+    g = {k: host(v) for k, v in gpu.aperture_phot(dev(out["sub"]), dev(x), dev(y)).items()}
+    assert np.array_equal(g["n_ann"], ph["n_ann"])
+    assert np.array_equal(g["flags"], ph["flags"])
+    assert np.array_equal(g["sky"], ph["sky"].astype(np.float32))
+    assert np.all(np.abs(g["area"] - ph["area"]) <= 2e-5 * ph["area"] + 1e-6)
+    rms = float(np.median(out["rms"]))
+    scale = np.abs(ph["flux"]) + ph["area"] * (np.abs(ph["sky"]) + rms)
+    err = np.abs(g["flux"] - ph["flux"])
+    assert np.all(err <= 1e-5 * scale), f"max rel err {np.max(err / scale)}"
+
+
+def test_aperture_random_positions(gpu, orc):
+    """many random sub-pixel positions incl. the frame edges and exact
+    half-integers, on a noise frame."""
+    rng = np.random.default_rng(5)
+    sub = rng.normal(0, 30, (200, 260)).astype(np.float32)
+    n = 3000
+    x = rng.uniform(-2, 262, n).astype(np.float32)
+    y = rng.uniform(-2, 202, n).astype(np.float32)
+    x[:100] = np.round(x[:100] * 2) / 2
+    y[:100] = np.round(y[:100] * 2) / 2
+    ph = orc.aperture(sub, x, y)
+    g = {k: host(v) for k, v in gpu.aperture_phot(dev(sub), dev(x), dev(y)).items()}
+    assert np.array_equal(g["n_ann"], ph["n_ann"])
+    assert np.array_equal(g["flags"], ph["flags"])
+    assert np.array_equal(g["sky"], ph["sky"].astype(np.float32))
+    scale = np.abs(ph["flux"]) + ph["area"] * (np.abs(ph["sky"]) + 30.0)
+    assert np.all(np.abs(g["flux"] - ph["flux"]) <= 1e-5 * scale)
+
+
+def test_overlap_weights_sum_flat(gpu, orc):
+    """flat frame: area = pi r^2 for interior centres, flux = 0 exactly in exact
+    arithmetic (|flux| <= FP32 rounding of the weights)."""
+    sub = np.full((100, 100), 7.0, np.float32)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(30, 70, 500).astype(np.float32)
+    y = rng.uniform(30, 70, 500).astype(np.float32)
+    g = {k: host(v) for k, v in gpu.aperture_phot(dev(sub), dev(x), dev(y)).items()}
+    assert np.all(np.abs(g["area"] - np.pi * 25) < 2e-4)
+    assert np.all(g["sky"] == 7.0)
+    assert np.all(np.abs(g["flux"]) < 2e-3)
+
+
+def test_device_count_limits_work(gpu, orc):
+    """only min(*n_src_dev, max_src) sources are processed; the rest untouched."""
+    sub = np.random.default_rng(1).normal(0, 1, (64, 64)).astype(np.float32)
+    x = dev(np.full(10, 32.0, np.float32))
+    y = dev(np.full(10, 32.0, np.float32))
+    n = torch.tensor([3], dtype=torch.int32, device="cuda")
+    out = gpu.aperture_phot(dev(sub), x, y, n_src=n)
+    fl = host(out["n_ann"])
+    assert np.all(fl[:3] > 0)

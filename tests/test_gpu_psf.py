@@ -1,0 +1,120 @@
+"""GPU parity of the differentiable PSF model and the batched LM fit.
+
+  * forward model vs the oracle's FP64 model: 2e-5 relative to the peak;
+  * adjoint (hand-written Jacobian-transpose kernel) vs the oracle's analytic
+    Jacobian and vs central finite differences (h = 1e-3) of the GPU forward;
+  * fit: chi^2 within 1e-4 relative and (x, y, F, sky, sx, sy) within 1e-4
+    relative (positions 1e-4 px + FP32 rounding) on well-measured stamps; the
+    FP32 model and the FP64-vs-FP32 iterate can take other accept/reject paths,
+    so faint stamps are compared by chi^2 only."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _params(rng, n):
+    return np.stack([7 + rng.uniform(-0.6, 0.6, n), 7 + rng.uniform(-0.6, 0.6, n), rng.uniform(500, 5e4, n),
+                     rng.uniform(50, 1000, n), rng.uniform(1.0, 2.0, n), rng.uniform(1.0, 2.0, n),
+                     rng.uniform(-1.5, 1.5, n)], 1)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_forward_and_adjoint(gpu, orc, model):
+    rng = np.random.default_rng(10 + model)
+    P = _params(rng, 64)
+    Pf = P.astype(np.float32)
+    m = host(gpu.psf_model(dev(Pf), 15, model, 2.5))
+    G = rng.normal(size=(64, 15, 15)).astype(np.float32)
+    pt = dev(Pf).requires_grad_(True)
+    out = gpu.psf_model(pt, 15, model, 2.5)
+    out.backward(dev(G))
+    ga = host(pt.grad)
+    for n in range(64):
+        om, J = orc.psf_model(Pf[n].astype(np.float64), 15, model, 2.5)
+        assert np.max(np.abs(m[n] - om)) <= 2e-5 * (np.max(np.abs(om)))
+        gref = J.T @ G[n].ravel().astype(np.float64)
+        sc = np.abs(J).max(axis=0) * np.abs(G[n]).sum()
+        assert np.all(np.abs(ga[n] - gref) <= 1e-5 * sc + 1e-6), (n, ga[n], gref)
+
+
+def test_adjoint_vs_finite_differences(gpu):
+    """central differences of the GPU forward itself (h = 1e-3 on positions /
+    widths / angle, relative 1e-3 on flux and sky), in float64 via torch."""
+    rng = np.random.default_rng(3)
+    P = _params(rng, 16).astype(np.float32)
+    G = rng.normal(size=(16, 15, 15)).astype(np.float32)
+    pt = dev(P).requires_grad_(True)
+    gpu.psf_model(pt, 15, 0, 2.5).backward(dev(G))
+    ga = host(pt.grad).astype(np.float64)
+    for k in range(7):
+        h = np.where(np.isin(k, (2, 3)), 1e-3 * np.abs(P[:, k]), 1e-2).astype(np.float32)
+        Pp, Pm = P.copy(), P.copy()
+        Pp[:, k] += h
+        Pm[:, k] -= h
+        hp = (Pp[:, k] - Pm[:, k]).astype(np.float64)   # the step actually taken in float32
+        fp = host(gpu.psf_model(dev(Pp), 15, 0, 2.5)).astype(np.float64)
+        fm = host(gpu.psf_model(dev(Pm), 15, 0, 2.5)).astype(np.float64)
+        fd = ((fp - fm) * G).sum(axis=(1, 2)) / hp
+        sc = np.abs(ga[:, k]) + np.abs(G).sum(axis=(1, 2)) * np.abs(fp - fm).max(axis=(1, 2)) / hp * 1e-3 + 1e-3
+        assert np.all(np.abs(fd - ga[:, k]) <= 2e-2 * sc), k
+
+
+def test_fit_parity(gpu, orc):
+    """Faint stamps (F of a few hundred ADU on a 1000 ADU sky) crawl for hundreds
+    of LM trials on both sides, so at max_iter = 50 about half stop with
+    FIT_MAXITER; the parity gate is on stamps that both sides converge, and
+    well-measured stars must converge."""
+    stamps, truth = synth.moffat_stamps(400, seed=4000)
+    o = orc.psf_fit(stamps)
+    g = {k: host(v) for k, v in gpu.psf_fit(dev(stamps)).items()}
+    conv = (o["flags"] == 0) & (g["flags"] == 0)
+    assert conv.mean() > 0.3
+    strong = truth[:, 2] > 5e3
+    assert np.mean(g["flags"][strong] == 0) > 0.95 and np.mean(o["flags"][strong] == 0) > 0.95
+    # chi^2 of converged fits: the same optimum
+    rel = np.abs(g["chi2"] - o["chi2"]) / o["chi2"]
+    assert np.median(rel[conv]) < 1e-5
+    bright = conv & (truth[:, 2] > 5e3) & (o["params"][:, 4] > 0.3) & (o["params"][:, 5] > 0.3)
+    assert bright.sum() > 20
+    assert np.all(rel[bright] < 1e-4)
+    gp, op = g["params"][bright], o["params"][bright]
+    assert np.all(np.abs(gp[:, :2] - op[:, :2]) <= 1e-4 + 4e-6 * np.abs(op[:, :2]))
+    assert np.all(np.abs(gp[:, 2:6] - op[:, 2:6]) <= 1e-4 * np.abs(op[:, 2:6]) + 1e-4)
+    ell = np.abs(op[:, 4] - op[:, 5]) / op[:, 4] > 0.05
+    dth = (gp[:, 6] - op[:, 6] + math.pi / 2) % math.pi - math.pi / 2
+    assert np.all(np.abs(dth[ell]) < 1e-3)
+
+
+def test_fit_noise_free_recovery_and_init(gpu, orc):
+    rng = np.random.default_rng(12)
+    P = _params(rng, 32)
+    P[:, 4] = np.maximum(P[:, 4], 1.2 * P[:, 5])
+    stamps = np.stack([orc.psf_model(p, 15, 0, 2.5, jac=False) for p in P]).astype(np.float32)
+    g = {k: host(v) for k, v in gpu.psf_fit(dev(stamps), max_iter=200).items()}
+    assert np.all(g["flags"] == 0)
+    assert np.allclose(g["params"][:, :6], P[:, :6], rtol=2e-4, atol=2e-4)
+    # explicit init = the default start computed by the oracle: identical results
+    init = np.stack([orc.psf_init(s) for s in stamps]).astype(np.float32)
+    g2 = {k: host(v) for k, v in gpu.psf_fit(dev(stamps), init=dev(init), max_iter=200).items()}
+    assert np.allclose(g2["params"], g["params"], rtol=1e-6, atol=1e-6)
+
+
+def test_fit_gaussian_and_weights(gpu, orc):
+    rng = np.random.default_rng(13)
+    P = _params(rng, 16)
+    P[:, 2] *= 3
+    stamps = np.stack([orc.psf_model(p, 15, 1, jac=False) for p in P])
+    stamps = (stamps + rng.normal(0, 3, stamps.shape)).astype(np.float32)
+    w = np.full(stamps.shape, 1 / 9.0, np.float32)
+    o = orc.psf_fit(stamps, weights=w, model=1)
+    g = {k: host(v) for k, v in gpu.psf_fit(dev(stamps), weights=dev(w), model=1).items()}
+    ok = (o["flags"] == 0) & (g["flags"] == 0)
+    assert ok.mean() > 0.8
+    assert np.all(np.abs(g["chi2"][ok] - o["chi2"][ok]) <= 1e-4 * o["chi2"][ok])
