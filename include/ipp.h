@@ -180,6 +180,31 @@ int ipp_bg_estimate(const void* img, int dtype, int64_t W, int64_t H, int64_t pi
                     int32_t* status_dev, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * ipp_bg_estimate_noalloc -- ipp_bg_estimate for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this is an interface choice.
+ * Some callers must not call cudaMalloc once they run -- real-time pipelines
+ * with a device-memory budget fixed at start-up, or code called back from
+ * another framework, where an allocation may synchronise the device or break
+ * that framework's memory accounting.  This variant takes no workspace: its
+ * scratch is a device array inside the library of IPP_BG_NOALLOC_MAX_MESHES
+ * nodes x 4 floats (256 KiB), which every GPU that loads the library keeps until
+ * the process exits.  The caller still passes the frame and the output grids.
+ *   - Same arguments and results as ipp_bg_estimate, minus raw_* and ws.
+ *   - A mesh grid larger than IPP_BG_NOALLOC_MAX_MESHES nodes is rejected with
+ *     IPP_ERR_NOT_SUPPORTED (nothing is enqueued).
+ *   - The first call on a device looks up the scratch address on that device;
+ *     make that first call before any stream capture.
+ *   - All calls on a device share the one scratch array: calls whose work can
+ *     overlap on the GPU (different streams without ordering) race and give
+ *     wrong results.  Calls ordered on one stream are fine.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define IPP_BG_NOALLOC_MAX_MESHES 16384
+int ipp_bg_estimate_noalloc(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                            const uint8_t* mask, const ipp_calib* cal, const ipp_bg_params* p,
+                            float* mesh_bkg, float* mesh_rms, int32_t* status_dev, void* stream);
+
+/*
  * ipp_bg_subtract -- interpolation back to full resolution and subtraction
  * (Sec. 2.2.2).  Node (p, q) of the filtered mesh sits at
  * ((q + 1/2) mesh_w - 1/2, (p + 1/2) mesh_h - 1/2); the background at each pixel

@@ -66,6 +66,8 @@ PROTOTYPES = {
     "ipp_bg_estimate_workspace_size": ([i64, i64, C.POINTER(BgParams)], sz),
     "ipp_bg_estimate": ([vp, i32, i64, i64, i64, vp, C.POINTER(Calib), C.POINTER(BgParams), vp, vp, vp, vp,
                          vp, vp, sz, vp], i32),
+    "ipp_bg_estimate_noalloc": ([vp, i32, i64, i64, i64, vp, C.POINTER(Calib), C.POINTER(BgParams), vp, vp, vp,
+                                 vp], i32),
     "ipp_bg_subtract": ([vp, i32, i64, i64, i64, C.POINTER(Calib), vp, C.POINTER(BgParams), vp, i64, vp, vp],
                         i32),
     "ipp_detect_label_workspace_size": ([i64, i64], sz),
