@@ -2,13 +2,15 @@
 // clip, invalid-mesh fill and mesh median filter, interpolation + subtraction.
 //
 // k_mesh_stats: one CTA (512 threads) per mesh.  The mesh is read once from HBM
-// into registers; a histogram over a window around the mean turns it into a
-// bin-sorted copy in shared memory, with per-bin sums.  Every clip pass then
-// costs O(pixels in the two boundary bins + the median bin) instead of O(mesh):
-// counts and sums of full bins come from prefix sums, the exact order
-// statistics from the small slice that holds them.  Sums are kept in
-// double-float (pairs of FP32) and combined in FP64, so the clip bounds agree
-// with an FP64 evaluation to ~1e-12 relative.
+// into registers.  A histogram over a window around the mean (refined around
+// the median when outliers made it coarse) turns the mesh into a bin-sorted copy
+// in shared memory.  The sums of the whole set are taken once, exactly: values
+// inside the window as int64 fixed point (a power-of-two scale no coarser than
+// their own spacing), the few outside it in double-float.  Every clip pass then only
+// touches the values it removes (the tails, bin by bin) and the bins holding
+// the median order statistics, so a pass costs O(removed + median bin), not
+// O(mesh), and the bounds agree with an FP64 evaluation to ~1e-13.  Scalar FP64
+// work (moments, bounds) runs on one thread: the FP64 pipe is narrow.
 #include <math.h>
 
 #include "jobs.cuh"
@@ -19,25 +21,23 @@ constexpr int MS_THREADS = 512;
 constexpr int MS_WARPS = MS_THREADS / kWarp;
 constexpr int MS_NB = 1024;          // window bins 1..MS_NB; 0 = below, MS_NB+1 = above
 constexpr int MS_NBT = MS_NB + 2;
-constexpr int MS_RANKCOUNT_MAX = 1024;  // slices up to this size: select by rank counting
-
+constexpr int MS_SCALE_BITS = 14;    // fixed point: d_int = (v - c*) * 2^(14 - e), bw = 2^e
 
 struct MeshShared {
     uint32_t hcnt[MS_NBT];
     uint32_t hstart[MS_NBT + 1];
-    uint32_t hfill[MS_NBT];
-    float d1[MS_NBT];  // per-bin sum of (v - bin centre); reused as radix scratch
-    float d2[MS_NBT];  // per-bin sum of (v - bin centre)^2
-    float2 P1[MS_NBT + 1];  // double-float prefix over window bins of sum(v - c*)
-    float2 P2[MS_NBT + 1];  // ... of sum (v - c*)^2
-    // reductions / broadcasts
-    float2 red1[MS_WARPS], red2[MS_WARPS];
-    int redi[MS_WARPS * 2];
-    float redf[MS_WARPS * 2];
+    uint32_t hfill[MS_NBT];   // scatter cursors; reused as radix-select histogram
+    uint32_t radix[2048];
+    uint32_t sorted_bits[(MS_NBT + 31) / 32];  // bins whose slice is already sorted
+    long long redl[MS_WARPS * 2];
+    float4 redo[MS_WARPS];
+    int redi[MS_WARPS * 3];
+    float redf[MS_WARPS * 3];
     double bc_d[8];
+    long long bc_l[4];
     int bc_i[8];
     float bc_f[4];
-    uint32_t bc_u[4];
+    uint32_t bc_u[2];
 };
 
 // Bin of a value: monotone in v (FP subtraction and the power-of-two scaling
@@ -48,175 +48,141 @@ __device__ __forceinline__ int bin_of(float v, float cstar, float inv_bw) {
     return (int)t + MS_NB / 2 + 1;
 }
 
-__device__ __forceinline__ df two_prod(float a, float b) {
-    float p = __fmul_rn(a, b);
-    return df{p, __fmaf_rn(a, b, -p)};
-}
-__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
-
-// Block-wide sum of (count, df, df); result valid in all threads.
-struct Red3 {
-    int n;
-    double s1, s2;
+// Sums of a set of values relative to c*: in-window values in int64 fixed
+// point (scale 2^-fx, exact for values no finer than that), the values of the two
+// end bins (outliers) in double-float (pairs of FP32, ~48-bit mantissa) so that
+// no FP64 instruction is needed per element.
+struct Sums {
+    long long i1, i2;
+    df o1, o2;
 };
-__device__ Red3 block_red3(MeshShared& S, int n, df a, df b) {
+
+__device__ __forceinline__ void sums_add(Sums& a, float v, int b, float cstar, float fxs) {
+    if (b >= 1 && b <= MS_NB) {
+        const int d = __float2int_rn((v - cstar) * fxs);
+        a.i1 += d;
+        a.i2 += (long long)d * d;
+    } else {
+        const df d = two_sum(v, -cstar);
+        df q = sq_exact(d.hi);
+        q = df_add_f(q, __fmul_rn(2.0f * d.hi, d.lo));
+        a.o1 = df_add(a.o1, d);
+        a.o2 = df_add(a.o2, q);
+    }
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide reduction of (Sums, three counts).  The totals are left in
+// S.redl[0..1] (int64 sums), S.bc_d[0..1] (outlier sums, FP64, converted once by
+// thread 0) and S.bc_i[0..2]; every thread gets the counts back.
+__device__ void block_reduce(MeshShared& S, const Sums& s, int c[3]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    n = warp_sum_i(n);
-    a = warp_sum_df(a);
-    b = warp_sum_df(b);
+    const long long a = warp_sum_ll(s.i1), b = warp_sum_ll(s.i2);
+    const bool anyo = __any_sync(0xffffffffu, s.o1.hi != 0.f || s.o2.hi != 0.f);
+    const df x = anyo ? warp_sum_df(s.o1) : df{0.f, 0.f};
+    const df y = anyo ? warp_sum_df(s.o2) : df{0.f, 0.f};
+    const int c0 = warp_sum_i(c[0]), c1 = warp_sum_i(c[1]), c2 = warp_sum_i(c[2]);
     __syncthreads();
     if (lane == 0) {
-        S.redi[warp] = n;
-        S.red1[warp] = make_float2(a.hi, a.lo);
-        S.red2[warp] = make_float2(b.hi, b.lo);
+        S.redl[warp] = a; S.redl[MS_WARPS + warp] = b;
+        S.redo[warp] = make_float4(x.hi, x.lo, y.hi, y.lo);
+        S.redi[warp] = c0; S.redi[MS_WARPS + warp] = c1; S.redi[2 * MS_WARPS + warp] = c2;
     }
     __syncthreads();
     if (warp == 0) {
-        int nn = lane < MS_WARPS ? S.redi[lane] : 0;
-        df aa = lane < MS_WARPS ? df{S.red1[lane].x, S.red1[lane].y} : df{0.f, 0.f};
-        df bb = lane < MS_WARPS ? df{S.red2[lane].x, S.red2[lane].y} : df{0.f, 0.f};
-        nn = warp_sum_i(nn);
-        aa = warp_sum_df(aa);
-        bb = warp_sum_df(bb);
+        const bool in = lane < MS_WARPS;
+        const long long aa = warp_sum_ll(in ? S.redl[lane] : 0), bb = warp_sum_ll(in ? S.redl[MS_WARPS + lane] : 0);
+        const float4 o = in ? S.redo[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const df xx = warp_sum_df(df{o.x, o.y}), yy = warp_sum_df(df{o.z, o.w});
+        const int k0 = warp_sum_i(in ? S.redi[lane] : 0), k1 = warp_sum_i(in ? S.redi[MS_WARPS + lane] : 0);
+        const int k2 = warp_sum_i(in ? S.redi[2 * MS_WARPS + lane] : 0);
         if (lane == 0) {
-            S.bc_i[0] = nn;
-            S.bc_d[0] = df_to_d(aa);
-            S.bc_d[1] = df_to_d(bb);
+            S.redl[0] = aa; S.redl[1] = bb;
+            S.bc_d[0] = df_to_d(xx); S.bc_d[1] = df_to_d(yy);
+            S.bc_i[0] = k0; S.bc_i[1] = k1; S.bc_i[2] = k2;
         }
     }
     __syncthreads();
-    Red3 r{S.bc_i[0], S.bc_d[0], S.bc_d[1]};
+    c[0] = S.bc_i[0]; c[1] = S.bc_i[1]; c[2] = S.bc_i[2];
     __syncthreads();
-    return r;
 }
 
-// Count, sum(v - c*) and sum((v - c*)^2) of the set {v : lo <= v <= hi} (kept
-// set of a clip pass), plus the kept counts of its two boundary bins.
-struct SetStats {
-    int n;
-    double a1, a2;  // relative to c*
-    int bl, bh;     // boundary bins
-    int nbl, nbh;   // kept elements in slices bl and bh (nbh = 0 when bl == bh)
-};
-
-__device__ SetStats set_stats(MeshShared& S, const float* sval, float lo, float hi, float cstar,
-                              float inv_bw) {
-    SetStats st;
-    st.bl = (lo == -INFINITY) ? 0 : bin_of(lo, cstar, inv_bw);
-    st.bh = (hi == INFINITY) ? MS_NB + 1 : bin_of(hi, cstar, inv_bw);
-    // explicit part: the boundary slices
-    int cl = 0, ch = 0;
-    df e1{0.f, 0.f}, e2{0.f, 0.f};
-    {
-        int s0 = S.hstart[st.bl], s1 = S.hstart[st.bl + 1];
-        for (int k = s0 + (int)threadIdx.x; k < s1; k += MS_THREADS) {
-            float v = sval[k];
-            if (v >= lo && v <= hi) {
-                cl++;
-                df d = two_sum(v, -cstar);
-                e1 = df_add(e1, d);
-                df q = sq_exact(d.hi);
-                q = df_add_f(q, __fmul_rn(2.0f * d.hi, d.lo));
-                e2 = df_add(e2, q);
-            }
+// Sort the slice of bin b in place, once: every element computes its rank
+// (ties by position) and is written there.  Slices longer than the block are
+// left unsorted (they are selected by radix passes).
+__device__ bool ensure_sorted(MeshShared& S, float* sval, int b) {
+    if ((S.sorted_bits[b >> 5] >> (b & 31)) & 1u) return true;
+    const int s0 = S.hstart[b], s1 = S.hstart[b + 1], m = s1 - s0;
+    if (m > MS_THREADS) return false;
+    float v = 0.f;
+    int rank = 0;
+    if ((int)threadIdx.x < m) {
+        v = sval[s0 + threadIdx.x];
+        for (int u = s0; u < s1; u++) {
+            const float x = sval[u];
+            rank += (x < v) || (x == v && u < s0 + (int)threadIdx.x);
         }
     }
-    if (st.bh != st.bl) {
-        int s0 = S.hstart[st.bh], s1 = S.hstart[st.bh + 1];
-        for (int k = s0 + (int)threadIdx.x; k < s1; k += MS_THREADS) {
-            float v = sval[k];
-            if (v >= lo && v <= hi) {
-                ch++;
-                df d = two_sum(v, -cstar);
-                e1 = df_add(e1, d);
-                df q = sq_exact(d.hi);
-                q = df_add_f(q, __fmul_rn(2.0f * d.hi, d.lo));
-                e2 = df_add(e2, q);
-            }
-        }
-    }
-    // counts of the two boundary slices, reduced separately
-    {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        int a = warp_sum_i(cl), b = warp_sum_i(ch);
-        if (lane == 0) { S.redi[warp] = a; S.redi[MS_WARPS + warp] = b; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int x = 0, y = 0;
-            for (int w = 0; w < MS_WARPS; w++) { x += S.redi[w]; y += S.redi[MS_WARPS + w]; }
-            S.bc_i[4] = x;
-            S.bc_i[5] = y;
-        }
-        __syncthreads();
-        st.nbl = S.bc_i[4];
-        st.nbh = S.bc_i[5];
-        __syncthreads();
-    }
-    Red3 r = block_red3(S, cl + ch, e1, e2);
-    st.n = r.n;
-    st.a1 = r.s1;
-    st.a2 = r.s2;
-    if (st.bh > st.bl + 1) {  // full window bins strictly between
-        st.n += (int)(S.hstart[st.bh] - S.hstart[st.bl + 1]);
-        float2 p1h = S.P1[st.bh], p1l = S.P1[st.bl + 1];
-        float2 p2h = S.P2[st.bh], p2l = S.P2[st.bl + 1];
-        st.a1 += ((double)p1h.x + (double)p1h.y) - ((double)p1l.x + (double)p1l.y);
-        st.a2 += ((double)p2h.x + (double)p2h.y) - ((double)p2l.x + (double)p2l.y);
-    }
-    return st;
+    __syncthreads();
+    if ((int)threadIdx.x < m) sval[s0 + rank] = v;
+    if (threadIdx.x == 0) S.sorted_bits[b >> 5] |= 1u << (b & 31);
+    __syncthreads();
+    return true;
 }
 
-// r-th smallest (0-based) of the elements of slice [s0, s1) that lie in
-// [lo, hi].  Rank counting with ties broken by position for small slices; an
-// 11-bit radix select over the order-preserving keys otherwise.
-__device__ float select_in_slice(MeshShared& S, const float* sval, int s0, int s1, float lo,
-                                 float hi, int r) {
-    const int m = s1 - s0;
-    if (m <= MS_RANKCOUNT_MAX) {
-        for (int k = s0 + (int)threadIdx.x; k < s1; k += MS_THREADS) {
-            float v = sval[k];
-            if (!(v >= lo && v <= hi)) continue;
-            int rank = 0;
-            for (int u = s0; u < s1; u++) {
-                float x = sval[u];
-                bool in = (x >= lo && x <= hi);
-                rank += in && (x < v || (x == v && u < k));
-            }
-            if (rank == r) S.bc_f[0] = v;
-        }
-        __syncthreads();
-        float res = S.bc_f[0];
-        __syncthreads();
-        return res;
+// r-th smallest (0-based) of the elements of bin b's slice that lie in [lo, hi].
+// A sorted slice keeps its elements of [lo, hi] contiguous: a binary search for
+// the first one and an index.  Otherwise an 11/11/10-bit radix select over the
+// order-preserving keys.
+__device__ float select_in_bin(MeshShared& S, float* sval, int b, float lo, float hi, int r) {
+    const int s0 = S.hstart[b], s1 = S.hstart[b + 1];
+    if (ensure_sorted(S, sval, b)) {
+        int a = s0, e = s1;  // first element >= lo
+        while (a < e) { const int m = (a + e) >> 1; if (sval[m] < lo) a = m + 1; else e = m; }
+        return sval[a + r];
     }
-    // radix select, 3 passes of 11/11/10 bits over keys
-    uint32_t* hist = reinterpret_cast<uint32_t*>(S.d1);  // 2 * MS_NBT >= 2048 words
     uint32_t prefix = 0, pmask = 0;
     int rr = r;
     const int shifts[3] = {21, 10, 0};
     const int widths[3] = {11, 11, 10};
     for (int pass = 0; pass < 3; pass++) {
         const int sh = shifts[pass], nb = 1 << widths[pass];
-        for (int k = threadIdx.x; k < nb; k += MS_THREADS) hist[k] = 0;
+        for (int k = threadIdx.x; k < nb; k += MS_THREADS) S.radix[k] = 0;
         __syncthreads();
         for (int k = s0 + (int)threadIdx.x; k < s1; k += MS_THREADS) {
-            float v = sval[k];
+            const float v = sval[k];
             if (!(v >= lo && v <= hi)) continue;
-            uint32_t key = fkey(v);
+            const uint32_t key = fkey(v);
             if ((key & pmask) != prefix) continue;
-            atomicAdd(&hist[(key >> sh) & (nb - 1)], 1u);
+            atomicAdd(&S.radix[(key >> sh) & (nb - 1)], 1u);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int acc = 0, d = 0;
-            for (d = 0; d < nb; d++) {
-                int c = (int)hist[d];
-                if (rr < acc + c) break;
-                acc += c;
+        if (threadIdx.x < 32) {  // one warp finds the digit: scan of nb counts
+            const int lane = threadIdx.x, per = nb / 32;
+            int tot = 0;
+            for (int d = lane * per; d < (lane + 1) * per; d++) tot += (int)S.radix[d];
+            int inc = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
             }
-            if (d >= nb) d = nb - 1;  // unreachable for a valid rank
-            S.bc_u[0] = (uint32_t)d;
-            S.bc_i[6] = rr - acc;
+            const int before = inc - tot;
+            if (rr >= before && rr < inc) {
+                int acc = before, d = lane * per;
+                for (; d < (lane + 1) * per; d++) {
+                    int c = (int)S.radix[d];
+                    if (rr < acc + c) break;
+                    acc += c;
+                }
+                S.bc_u[0] = (uint32_t)d;
+                S.bc_i[6] = rr - acc;
+            }
         }
         __syncthreads();
         prefix |= S.bc_u[0] << sh;
@@ -227,34 +193,54 @@ __device__ float select_in_slice(MeshShared& S, const float* sval, int s0, int s
     return fkey_inv(prefix);
 }
 
-// Median (Eq. 1) of the kept set described by st.
-__device__ double set_median(MeshShared& S, const float* sval, const SetStats& st, float lo,
-                             float hi) {
-    const int full = (st.bh > st.bl + 1) ? (int)(S.hstart[st.bh] - S.hstart[st.bl + 1]) : 0;
-    float vals[2];
-    int ks[2] = {(st.n - 1) / 2, st.n / 2};
+// State of the kept set [lo, hi] of a clip pass.
+struct KeptSet {
+    float lo, hi;
+    int bl, bh;     // bins of lo and hi
+    int nbl, nbh;   // kept elements in slices bl and bh (nbh unused when bl == bh)
+    int n;
+};
+
+// The two middle order statistics x_k0, x_k1 (k0 = (n-1)/2, k1 = n/2) of the
+// kept set; Eq. 1's median is their mean.
+__device__ void kept_middle(MeshShared& S, float* sval, const KeptSet& K, float vals[2]) {
+    const int ks[2] = {(K.n - 1) / 2, K.n / 2};
+    const int full = (K.bh > K.bl + 1) ? (int)(S.hstart[K.bh] - S.hstart[K.bl + 1]) : 0;
+    const int nbl = (K.bl == K.bh) ? K.n : K.nbl;
     for (int q = 0; q < 2; q++) {
         if (q == 1 && ks[1] == ks[0]) { vals[1] = vals[0]; break; }
-        int k = ks[q];
-        int s0, s1, r;
-        if (k < st.nbl) {
-            s0 = S.hstart[st.bl]; s1 = S.hstart[st.bl + 1]; r = k;
-        } else if (k - st.nbl < full) {
-            int kk = k - st.nbl;
-            // bin b in (bl, bh) with hstart[b] - base <= kk < hstart[b+1] - base
-            uint32_t base = S.hstart[st.bl + 1];
-            int a = st.bl + 1, b = st.bh - 1;
+        const int k = ks[q];
+        int bin, r;
+        if (k < nbl) {
+            bin = K.bl; r = k;
+        } else if (k - nbl < full) {
+            const int kk = k - nbl;
+            const uint32_t base = S.hstart[K.bl + 1];
+            int a = K.bl + 1, b = K.bh - 1;
             while (a < b) {
-                int mid = (a + b + 1) >> 1;
+                const int mid = (a + b + 1) >> 1;
                 if ((int)(S.hstart[mid] - base) <= kk) a = mid; else b = mid - 1;
             }
-            s0 = S.hstart[a]; s1 = S.hstart[a + 1]; r = kk - (int)(S.hstart[a] - base);
+            bin = a; r = kk - (int)(S.hstart[a] - base);
         } else {
-            s0 = S.hstart[st.bh]; s1 = S.hstart[st.bh + 1]; r = k - st.nbl - full;
+            bin = K.bh; r = k - nbl - full;
         }
-        vals[q] = select_in_slice(S, sval, s0, s1, lo, hi, r);
+        vals[q] = select_in_bin(S, sval, bin, K.lo, K.hi, r);
     }
-    return 0.5 * ((double)vals[0] + (double)vals[1]);
+}
+
+// Scalar FP64 statistics of the kept set (one thread): mean and population sigma.
+struct KeptSums {
+    long long i1, i2;
+    double o1, o2;
+};
+__device__ __forceinline__ void kept_stats(const KeptSums& t, int n, float cstar, double unit, double* mu,
+                                           double* sd) {
+    const double s1 = (double)t.i1 * unit + t.o1;
+    const double s2 = (double)t.i2 * unit * unit + t.o2;
+    const double m1 = s1 / n;
+    *mu = (double)cstar + m1;
+    *sd = sqrt(fmax(s2 / n - m1 * m1, 0.0));
 }
 
 template <int PPT>
@@ -262,6 +248,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2) k_mesh_stats(MeshJob J) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MeshShared& S = *reinterpret_cast<MeshShared*>(smem_raw);
     float* sval = reinterpret_cast<float*>(smem_raw + sizeof(MeshShared));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     const int mesh = blockIdx.x;
     const int mx = mesh % J.nx, my = mesh / J.nx;
@@ -270,24 +257,26 @@ __global__ void __launch_bounds__(MS_THREADS, 2) k_mesh_stats(MeshJob J) {
     const int he = (int)min((int64_t)J.mesh_h, J.H - y0);
     const int slots = J.mesh_w * J.mesh_h;
 
-    // ---- load (one HBM read of the mesh), exact double-float sums ----------
+    // ---- load (the one HBM read of the mesh); approximate moments ------------
     float v[PPT];
     int n_loc = 0;
-    df s1{0.f, 0.f}, s2{0.f, 0.f};
-    float vmin = INFINITY, vmax = -INFINITY;
+    float piv = 0.f, s = 0.f, q = 0.f, vmin = INFINITY, vmax = -INFINITY;
+    // element e = threadIdx.x + k * 512 of the mesh sits at (r, c); both advance
+    // by fixed steps with k, so no division inside the loop
+    const int dr = MS_THREADS / J.mesh_w, dc = MS_THREADS - dr * J.mesh_w;
+    int r = threadIdx.x / J.mesh_w, c = threadIdx.x - r * J.mesh_w;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
-        int e = threadIdx.x + k * MS_THREADS;
+        const int e = threadIdx.x + k * MS_THREADS;
         float x = __int_as_float(0x7fc00000);  // NaN = not usable
         if (e < slots) {
-            int r = e / J.mesh_w, c = e - r * J.mesh_w;
             if (r < he && c < we) {
-                int64_t yy = y0 + r, xx = x0 + c;
+                const int64_t yy = y0 + r, xx = x0 + c;
                 if (J.dtype == IPP_F32) {
                     x = __ldg(reinterpret_cast<const float*>(J.img) + yy * J.pitch + xx);
                 } else {
-                    float raw = (float)__ldg(reinterpret_cast<const uint16_t*>(J.img) + yy * J.pitch + xx);
-                    float b = J.bias_map ? __ldg(J.bias_map + yy * J.W + xx) : J.bias;
+                    const float raw = (float)__ldg(reinterpret_cast<const uint16_t*>(J.img) + yy * J.pitch + xx);
+                    const float b = J.bias_map ? __ldg(J.bias_map + yy * J.W + xx) : J.bias;
                     x = (raw - b) * __ldg(J.inv_flat + yy * J.W + xx);
                 }
                 if (J.mask && J.mask[yy * J.W + xx]) x = __int_as_float(0x7fc00000);
@@ -295,34 +284,70 @@ __global__ void __launch_bounds__(MS_THREADS, 2) k_mesh_stats(MeshJob J) {
             }
         }
         v[k] = x;
+        r += dr;
+        c += dc;
+        if (c >= J.mesh_w) { c -= J.mesh_w; r++; }
         if (x == x) {
+            if (n_loc == 0) piv = x;
             n_loc++;
-            s1 = df_add_f(s1, x);
-            s2 = df_add(s2, sq_exact(x));
+            const float d = x - piv;
+            s += d;
+            q = fmaf(d, d, q);
             vmin = fminf(vmin, x);
             vmax = fmaxf(vmax, x);
         }
     }
-    {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // merge (n, mean, M2) across the block (Chan et al.); FP32 is enough here:
+    // these moments only place the histogram window
+    float mean = n_loc ? piv + s / n_loc : 0.f;
+    float m2 = n_loc ? fmaxf(q - s * s / n_loc, 0.f) : 0.f;
+    float cnt = (float)n_loc;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-            vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        const float nb = __shfl_xor_sync(0xffffffffu, cnt, o);
+        const float mb = __shfl_xor_sync(0xffffffffu, mean, o);
+        const float qb = __shfl_xor_sync(0xffffffffu, m2, o);
+        const float nt = cnt + nb;
+        if (nt > 0.f) {
+            const float dl = mb - mean;
+            mean = mean + dl * (nb / nt);
+            m2 = m2 + qb + dl * dl * (cnt * nb / nt);
         }
-        if (lane == 0) { S.redf[warp] = vmin; S.redf[MS_WARPS + warp] = vmax; }
+        cnt = nt;
+        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     }
-    Red3 tot = block_red3(S, n_loc, s1, s2);  // contains __syncthreads
-    if (threadIdx.x == 0) {
-        float a = INFINITY, b = -INFINITY;
-        for (int w = 0; w < MS_WARPS; w++) { a = fminf(a, S.redf[w]); b = fmaxf(b, S.redf[MS_WARPS + w]); }
-        S.bc_f[1] = a;
-        S.bc_f[2] = b;
+    if (lane == 0) {
+        S.redf[warp] = cnt; S.redf[MS_WARPS + warp] = mean; S.redf[2 * MS_WARPS + warp] = m2;
+        S.redi[warp] = __float_as_int(vmin); S.redi[MS_WARPS + warp] = __float_as_int(vmax);
     }
     __syncthreads();
-    vmin = S.bc_f[1];
-    vmax = S.bc_f[2];
-    const int n0 = tot.n;
+    if (threadIdx.x == 0) {
+        float c = 0.f, mu = 0.f, mm = 0.f, a = INFINITY, b = -INFINITY;
+        for (int w = 0; w < MS_WARPS; w++) {
+            const float nb = S.redf[w], mb = S.redf[MS_WARPS + w], qb = S.redf[2 * MS_WARPS + w];
+            const float nt = c + nb;
+            if (nt > 0.f) {
+                const float dl = mb - mu;
+                mu = mu + dl * (nb / nt);
+                mm = mm + qb + dl * dl * (c * nb / nt);
+            }
+            c = nt;
+            a = fminf(a, __int_as_float(S.redi[w]));
+            b = fmaxf(b, __int_as_float(S.redi[MS_WARPS + w]));
+        }
+        S.bc_i[0] = (int)c;
+        S.bc_f[0] = mu;
+        S.bc_f[1] = c > 0.f ? sqrtf(mm / c) : 0.f;
+        S.bc_f[2] = a;
+        S.bc_f[3] = b;
+    }
+    __syncthreads();
+    const int n0 = S.bc_i[0];
+    const float mu0 = S.bc_f[0], sd0 = S.bc_f[1];
+    vmin = S.bc_f[2];
+    vmax = S.bc_f[3];
+    __syncthreads();
 
     if (n0 < J.min_valid || n0 == 0) {
         if (threadIdx.x == 0) { J.raw_bkg[mesh] = 0.f; J.raw_rms[mesh] = -1.f; }
@@ -330,7 +355,8 @@ __global__ void __launch_bounds__(MS_THREADS, 2) k_mesh_stats(MeshJob J) {
     }
     if (vmin == vmax) {  // constant mesh: every statistic is that value, sigma 0
         if (threadIdx.x == 0) {
-            double c = (double)vmin, bk;
+            const double c = (double)vmin;
+            double bk;
             switch (J.estimator) {
                 case IPP_EST_MEDIAN: case IPP_EST_MEAN: bk = c; break;
                 case IPP_EST_FACTORS: bk = J.mf * c - J.mnf * c; break;
@@ -342,22 +368,20 @@ __global__ void __launch_bounds__(MS_THREADS, 2) k_mesh_stats(MeshJob J) {
         return;
     }
 
-    // ---- histogram window ---------------------------------------------------
-    // Width NB*bw in [10 sigma0, 20 sigma0), bw a power of two, centre c* a
-    // multiple of bw near the mean; refined once around the median bin when
-    // outliers made it coarse.
+    // ---- histogram window: bw = 2^e, width NB*bw in (4, 8] sigma0, centre c* a
+    // multiple of bw near the mean; refined once around the median bin when it
+    // is crowded (outliers inflate sigma0).  Values outside the window land in
+    // the two end bins, whose slices are handled element by element. ---------
+    int e;
     float cstar, bw, inv_bw;
     {
-        double mu0 = tot.s1 / n0;
-        double var0 = tot.s2 / n0 - mu0 * mu0;
-        double sd0 = sqrt(fmax(var0, 0.0));
-        double span = fmax(10.0 * sd0, (double)(vmax - vmin) * 1e-6);
-        span = fmax(span, fabs(mu0) * 1e-6 + 1e-30);
-        int e = (int)ceil(log2(span / MS_NB));
-        e = max(min(e, 100), -120);
+        float span = fmaxf(8.0f * sd0, (vmax - vmin) * 1e-6f);
+        span = fmaxf(span, fabsf(mu0) * 1e-6f + 1e-30f);
+        e = (int)floorf(log2f(span / MS_NB));
+        e = max(min(e, 100), -110);
         bw = ldexpf(1.0f, e);
         inv_bw = ldexpf(1.0f, -e);
-        cstar = rintf((float)mu0 * inv_bw) * bw;
+        cstar = rintf(mu0 * inv_bw) * bw;
     }
     for (int round = 0; round < 2; round++) {
         for (int k = threadIdx.x; k < MS_NBT; k += MS_THREADS) S.hcnt[k] = 0;
@@ -366,160 +390,152 @@ __global__ void __launch_bounds__(MS_THREADS, 2) k_mesh_stats(MeshJob J) {
         for (int k = 0; k < PPT; k++)
             if (v[k] == v[k]) atomicAdd(&S.hcnt[bin_of(v[k], cstar, inv_bw)], 1u);
         __syncthreads();
-        if (round == 1) break;
-        // robust width from the 16th / 84th percentile bins; refine when the
-        // median bin is crowded and the window could be at least 8x finer
-        if (threadIdx.x == 0) {
-            int acc = 0, b16 = -1, b50 = -1, b84 = -1;
-            int k16 = (int)(0.1587 * n0), k50 = n0 / 2, k84 = (int)(0.8413 * n0);
-            for (int b = 0; b < MS_NBT; b++) {
-                acc += (int)S.hcnt[b];
-                if (b16 < 0 && acc > k16) b16 = b;
-                if (b50 < 0 && acc > k50) b50 = b;
-                if (b84 < 0 && acc > k84) b84 = b;
+        if (threadIdx.x < 32) {  // exclusive scan of the counts (one warp)
+            constexpr int PER = (MS_NBT + 31) / 32;
+            const int b0 = lane * PER;
+            int acc = 0;
+            for (int b = b0; b < min(b0 + PER, MS_NBT); b++) acc += (int)S.hcnt[b];
+            int inc = acc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
             }
+            int run = inc - acc;
+            for (int b = b0; b < min(b0 + PER, MS_NBT); b++) {
+                S.hstart[b] = (uint32_t)run;
+                run += (int)S.hcnt[b];
+            }
+            if (lane == 31) S.hstart[MS_NBT] = (uint32_t)inc;
+        }
+        __syncthreads();
+        if (round == 1) break;
+        if (threadIdx.x == 0) {
+            // bins holding the 15.87 / 50 / 84.13 percentiles (binary search)
+            auto bin_at = [&](int k) {
+                int a = 0, b = MS_NBT - 1;
+                while (a < b) {
+                    const int mid = (a + b + 1) >> 1;
+                    if ((int)S.hstart[mid] <= k) a = mid; else b = mid - 1;
+                }
+                return a;
+            };
+            const int b16 = bin_at((int)(0.1587f * n0)), b50 = bin_at(n0 / 2), b84 = bin_at((int)(0.8413f * n0));
             int refine = 0;
             float nc = cstar, nbw = bw, ninv = inv_bw;
-            if (b50 >= 1 && b50 <= MS_NB && S.hcnt[b50] > 96 && b16 >= 1 && b84 <= MS_NB) {
-                double sr = 0.5 * (double)(b84 - b16 + 1) * bw;
-                double span = 10.0 * sr;
-                int e = (int)ceil(log2(span / MS_NB));
-                float cand = ldexpf(1.0f, e);
-                if (cand * 8.0f <= bw) {
+            int ne = e;
+            if (b50 >= 1 && b50 <= MS_NB && S.hcnt[b50] > 64) {
+                // window of about +-4 sigma_r: the median bins then hold ~n/100 values
+                const float sr = fmaxf(0.5f * (float)(b84 - b16 + 1) * bw, bw * 0.5f);
+                int e2 = (int)floorf(log2f(8.0f * sr / MS_NB));
+                e2 = max(e2, -110);
+                if (e2 < e) {
                     refine = 1;
-                    nbw = cand;
-                    ninv = ldexpf(1.0f, -e);
-                    float centre = cstar + ((float)(b50 - MS_NB / 2 - 1) + 0.5f) * bw;
+                    ne = e2;
+                    nbw = ldexpf(1.0f, e2);
+                    ninv = ldexpf(1.0f, -e2);
+                    const float centre = cstar + ((float)(b50 - MS_NB / 2 - 1) + 0.5f) * bw;
                     nc = rintf(centre * ninv) * nbw;
                 }
             }
             S.bc_i[7] = refine;
+            S.bc_i[5] = ne;
             S.bc_f[0] = nc;
             S.bc_f[1] = nbw;
             S.bc_f[2] = ninv;
         }
         __syncthreads();
-        int refine = S.bc_i[7];
+        const int refine = S.bc_i[7];
+        e = S.bc_i[5];
         cstar = S.bc_f[0];
         bw = S.bc_f[1];
         inv_bw = S.bc_f[2];
         __syncthreads();
         if (!refine) break;
     }
-
-    // ---- exclusive scan of the bin counts (one warp) -------------------------
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        constexpr int PER = (MS_NBT + 31) / 32;
-        int b0 = lane * PER, acc = 0;
-        for (int b = b0; b < min(b0 + PER, MS_NBT); b++) acc += (int)S.hcnt[b];
-        int inc = acc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
-        }
-        int run = inc - acc;
-        for (int b = b0; b < min(b0 + PER, MS_NBT); b++) {
-            S.hstart[b] = (uint32_t)run;
-            run += (int)S.hcnt[b];
-        }
-        if (lane == 31) S.hstart[MS_NBT] = (uint32_t)inc;
-    }
-    for (int k = threadIdx.x; k < MS_NBT; k += MS_THREADS) {
-        S.hfill[k] = 0;
-        S.d1[k] = 0.f;
-        S.d2[k] = 0.f;
-    }
+    for (int k = threadIdx.x; k < MS_NBT; k += MS_THREADS) S.hfill[k] = 0;
+    for (int k = threadIdx.x; k < (MS_NBT + 31) / 32; k += MS_THREADS) S.sorted_bits[k] = 0;
     __syncthreads();
 
-    // ---- scatter into bin order; per-bin sums of offsets from the bin centre
+    // ---- scatter into bin order + exact sums of the whole set ----------------
+    const float fxs = ldexpf(1.0f, MS_SCALE_BITS - e);           // fixed-point scale
+    const double unit = ldexp(1.0, e - MS_SCALE_BITS);
+    {
+        Sums tot{0, 0, df{0.f, 0.f}, df{0.f, 0.f}};
 #pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        float x = v[k];
-        if (x == x) {
-            int b = bin_of(x, cstar, inv_bw);
-            uint32_t pos = S.hstart[b] + atomicAdd(&S.hfill[b], 1u);
-            sval[pos] = x;
-            if (b >= 1 && b <= MS_NB) {
-                float cb = cstar + ((float)(b - MS_NB / 2 - 1) + 0.5f) * bw;
-                float d = x - cb;
-                atomicAdd(&S.d1[b], d);
-                atomicAdd(&S.d2[b], d * d);
+        for (int k = 0; k < PPT; k++) {
+            const float x = v[k];
+            if (x == x) {
+                const int b = bin_of(x, cstar, inv_bw);
+                sval[S.hstart[b] + atomicAdd(&S.hfill[b], 1u)] = x;
+                sums_add(tot, x, b, cstar, fxs);
             }
         }
+        int cz[3] = {0, 0, 0};
+        block_reduce(S, tot, cz);  // also orders the scatter before any read of sval
     }
-    __syncthreads();
+    // the running sums of the kept set live in thread 0; all scalar FP64 work
+    // happens there and is broadcast through shared memory
+    KeptSums ks{0, 0, 0.0, 0.0};
+    if (threadIdx.x == 0) ks = KeptSums{S.redl[0], S.redl[1], S.bc_d[0], S.bc_d[1]};
 
-    // ---- prefix over window bins of sums relative to c* (one warp, df) ------
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        constexpr int PER = (MS_NB + 31) / 32;
-        int b0 = 1 + lane * PER;
-        df t1{0.f, 0.f}, t2{0.f, 0.f};
-        for (int b = b0; b < min(b0 + PER, MS_NB + 1); b++) {
-            float nb = (float)S.hcnt[b];
-            float ob = ((float)(b - MS_NB / 2 - 1) + 0.5f) * bw;  // exact: bw power of 2
-            float d1b = S.d1[b], d2b = S.d2[b];
-            df x1 = df_add_f(two_prod(nb, ob), d1b);
-            df x2 = two_prod(nb, ob * ob);
-            x2 = df_add(x2, two_prod(2.0f * ob, d1b));
-            x2 = df_add_f(x2, d2b);
-            t1 = df_add(t1, x1);
-            t2 = df_add(t2, x2);
-        }
-        df i1 = t1, i2 = t2;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            df u1{__shfl_up_sync(0xffffffffu, i1.hi, o), __shfl_up_sync(0xffffffffu, i1.lo, o)};
-            df u2{__shfl_up_sync(0xffffffffu, i2.hi, o), __shfl_up_sync(0xffffffffu, i2.lo, o)};
-            if (lane >= o) { i1 = df_add(i1, u1); i2 = df_add(i2, u2); }
-        }
-        df r1 = df_add(i1, df_neg(t1)), r2 = df_add(i2, df_neg(t2));  // exclusive
-        for (int b = b0; b < min(b0 + PER, MS_NB + 1); b++) {
-            S.P1[b] = make_float2(r1.hi, r1.lo);
-            S.P2[b] = make_float2(r2.hi, r2.lo);
-            float nb = (float)S.hcnt[b];
-            float ob = ((float)(b - MS_NB / 2 - 1) + 0.5f) * bw;
-            float d1b = S.d1[b], d2b = S.d2[b];
-            df x1 = df_add_f(two_prod(nb, ob), d1b);
-            df x2 = two_prod(nb, ob * ob);
-            x2 = df_add(x2, two_prod(2.0f * ob, d1b));
-            x2 = df_add_f(x2, d2b);
-            r1 = df_add(r1, x1);
-            r2 = df_add(r2, x2);
-        }
-        if (lane == 31) {
-            S.P1[MS_NB + 1] = make_float2(r1.hi, r1.lo);
-            S.P2[MS_NB + 1] = make_float2(r2.hi, r2.lo);
-        }
-    }
-    __syncthreads();
-
-    // ---- clip passes -----------------------------------------------------------
-    float lo = -INFINITY, hi = INFINITY;
-    SetStats st = set_stats(S, sval, lo, hi, cstar, inv_bw);
-    double med = 0.0, mu = 0.0, sd = 0.0;
+    // ---- clip passes --------------------------------------------------------------
+    KeptSet K;
+    K.lo = -INFINITY; K.hi = INFINITY; K.bl = 0; K.bh = MS_NB + 1;
+    K.nbl = (int)S.hcnt[0]; K.nbh = (int)S.hcnt[MS_NB + 1];
+    K.n = n0;
+    double med = 0.0, mu = 0.0, sd = 0.0;  // meaningful in thread 0 only
     bool done = false;
     for (int it = 0; it < J.maxiters; it++) {
-        mu = (double)cstar + st.a1 / st.n;
-        double m1 = st.a1 / st.n;
-        sd = sqrt(fmax(st.a2 / st.n - m1 * m1, 0.0));
-        med = set_median(S, sval, st, lo, hi);
-        double blo = med - J.nsigma * sd, bhi = med + J.nsigma * sd;
-        float nlo = fmaxf(lo, __double2float_ru(blo));
-        float nhi = fminf(hi, __double2float_rd(bhi));
-        SetStats st2 = set_stats(S, sval, nlo, nhi, cstar, inv_bw);
-        if (st2.n == st.n || st2.n == 0) { done = true; break; }
-        lo = nlo;
-        hi = nhi;
-        st = st2;
+        float mid[2];
+        kept_middle(S, sval, K, mid);
+        if (threadIdx.x == 0) {
+            kept_stats(ks, K.n, cstar, unit, &mu, &sd);
+            med = 0.5 * ((double)mid[0] + (double)mid[1]);
+            const double blo = __dsub_rn(med, __dmul_rn(J.nsigma, sd));
+            const double bhi = __dadd_rn(med, __dmul_rn(J.nsigma, sd));
+            S.bc_f[0] = fmaxf(K.lo, __double2float_ru(blo));
+            S.bc_f[1] = fminf(K.hi, __double2float_rd(bhi));
+        }
+        __syncthreads();
+        const float nlo = S.bc_f[0], nhi = S.bc_f[1];
+        const int nbl_bin = bin_of(nlo, cstar, inv_bw), nbh_bin = bin_of(nhi, cstar, inv_bw);
+        // values removed by this pass lie in bins [bl, nbl_bin] and [nbh_bin, bh]
+        Sums rem{0, 0, df{0.f, 0.f}, df{0.f, 0.f}};
+        int c[3] = {0, 0, 0};  // removed, kept in new bin bl, kept in new bin bh
+        {
+            const int a0 = S.hstart[K.bl], a1 = S.hstart[nbl_bin + 1];
+            for (int k = a0 + (int)threadIdx.x; k < a1; k += MS_THREADS) {
+                const float x = sval[k];
+                if (!(x >= K.lo && x <= K.hi)) continue;
+                if (x < nlo || x > nhi) { c[0]++; sums_add(rem, x, bin_of(x, cstar, inv_bw), cstar, fxs); }
+                else if (k >= (int)S.hstart[nbl_bin]) c[1]++;
+            }
+            const int b0 = S.hstart[max(nbh_bin, nbl_bin + 1)], b1 = S.hstart[K.bh + 1];
+            for (int k = b0 + (int)threadIdx.x; k < b1; k += MS_THREADS) {
+                const float x = sval[k];
+                if (!(x >= K.lo && x <= K.hi)) continue;
+                if (x < nlo || x > nhi) { c[0]++; sums_add(rem, x, bin_of(x, cstar, inv_bw), cstar, fxs); }
+                else if (k < (int)S.hstart[nbh_bin + 1] && nbh_bin != nbl_bin) c[2]++;
+            }
+        }
+        block_reduce(S, rem, c);
+        if (c[0] == 0) { done = true; break; }   // no value dropped: the set is stable
+        if (c[0] >= K.n) { done = true; break; } // cannot happen (see header); keep the set
+        if (threadIdx.x == 0) {
+            ks.i1 -= S.redl[0]; ks.i2 -= S.redl[1]; ks.o1 -= S.bc_d[0]; ks.o2 -= S.bc_d[1];
+        }
+        K.lo = nlo; K.hi = nhi; K.bl = nbl_bin; K.bh = nbh_bin;
+        K.nbl = c[1]; K.nbh = c[2];
+        K.n -= c[0];
     }
     if (!done) {
-        mu = (double)cstar + st.a1 / st.n;
-        double m1 = st.a1 / st.n;
-        sd = sqrt(fmax(st.a2 / st.n - m1 * m1, 0.0));
-        med = set_median(S, sval, st, lo, hi);
+        float mid[2];
+        kept_middle(S, sval, K, mid);
+        if (threadIdx.x == 0) {
+            kept_stats(ks, K.n, cstar, unit, &mu, &sd);
+            med = 0.5 * ((double)mid[0] + (double)mid[1]);
+        }
     }
     if (threadIdx.x == 0) {
         double bk;
@@ -535,29 +551,29 @@ __global__ void __launch_bounds__(MS_THREADS, 2) k_mesh_stats(MeshJob J) {
 }
 
 // ---------------------------------------------------------------------------
-// Invalid-mesh fill and median filter on the mesh grid (one CTA; the grid is
-// small).  An invalid node takes the median of the valid nodes in the smallest
-// (2k+1)^2 neighbourhood holding any; then each node becomes the median of the
-// in-bounds nodes of its fw x fh window.
-constexpr int MF_THREADS = 1024;
+// Invalid-mesh fill and median filter on the mesh grid.  An invalid node takes
+// the median of the valid nodes in the smallest (2k+1)^2 neighbourhood holding
+// any; each node then becomes the median of the in-bounds (filled) nodes of its
+// fw x fh window.  One thread per node; the fill of an invalid neighbour is
+// recomputed where needed (invalid meshes are rare).
+constexpr int MF_THREADS = 256;
 
-// median (Eq. 1) of the values of `src` at the valid nodes of a window, found
-// by rank counting (windows are small)
-__device__ float window_median(const float* src, const float* valid_rms, int nx, int ny, int p0,
-                               int p1, int q0, int q1, int cnt) {
-    int k0 = (cnt - 1) / 2, k1 = cnt / 2;
+// median (Eq. 1) of src over the valid nodes of a window, by rank counting
+__device__ float window_median_valid(const float* src, const float* raw_rms, int nx, int p0, int p1, int q0,
+                                     int q1, int cnt) {
+    const int k0 = (cnt - 1) / 2, k1 = cnt / 2;
     float a = 0.f, b = 0.f;
     for (int p = p0; p <= p1; p++)
         for (int q = q0; q <= q1; q++) {
-            int id = p * nx + q;
-            if (valid_rms && valid_rms[id] < 0.f) continue;
-            float x = src[id];
+            const int id = p * nx + q;
+            if (raw_rms[id] < 0.f) continue;
+            const float x = src[id];
             int less = 0, leq = 0;
             for (int pp = p0; pp <= p1; pp++)
                 for (int qq = q0; qq <= q1; qq++) {
-                    int j = pp * nx + qq;
-                    if (valid_rms && valid_rms[j] < 0.f) continue;
-                    float y = src[j];
+                    const int j = pp * nx + qq;
+                    if (raw_rms[j] < 0.f) continue;
+                    const float y = src[j];
                     less += y < x;
                     leq += y <= x;
                 }
@@ -567,51 +583,57 @@ __device__ float window_median(const float* src, const float* valid_rms, int nx,
     return (float)(0.5 * ((double)a + (double)b));
 }
 
-__global__ void __launch_bounds__(MF_THREADS) k_mesh_fill_filter(
-    const float* raw_bkg, const float* raw_rms, float* fill_bkg, float* fill_rms, int nx, int ny,
-    int fw, int fh, float* out_bkg, float* out_rms, int32_t* status_dev) {
-    __shared__ int nvalid;
-    if (threadIdx.x == 0) nvalid = 0;
-    __syncthreads();
-    const int nn = nx * ny;
-    int c = 0;
-    for (int id = threadIdx.x; id < nn; id += MF_THREADS) c += raw_rms[id] >= 0.f;
-    atomicAdd(&nvalid, c);
-    __syncthreads();
-    if (nvalid == 0) {
-        for (int id = threadIdx.x; id < nn; id += MF_THREADS) { out_bkg[id] = 0.f; out_rms[id] = 0.f; }
-        if (threadIdx.x == 0 && status_dev) *status_dev = IPP_ERR_NO_VALID_MESH;
+// filled value of node (p, q) of src; false when the grid has no valid node
+__device__ bool filled_value(const float* src, const float* raw_rms, int nx, int ny, int p, int q, float* out) {
+    const int id = p * nx + q;
+    if (raw_rms[id] >= 0.f) { *out = src[id]; return true; }
+    for (int k = 1; k <= max(nx, ny); k++) {
+        const int p0 = max(p - k, 0), p1 = min(p + k, ny - 1), q0 = max(q - k, 0), q1 = min(q + k, nx - 1);
+        int cnt = 0;
+        for (int pp = p0; pp <= p1; pp++)
+            for (int qq = q0; qq <= q1; qq++) cnt += raw_rms[pp * nx + qq] >= 0.f;
+        if (cnt > 0) {
+            *out = window_median_valid(src, raw_rms, nx, p0, p1, q0, q1, cnt);
+            return true;
+        }
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(MF_THREADS) k_mesh_filter(const float* raw_bkg, const float* raw_rms, int nx,
+                                                            int ny, int fw, int fh, float* out_bkg,
+                                                            float* out_rms, int32_t* status_dev) {
+    const int id = blockIdx.x * MF_THREADS + threadIdx.x;
+    if (id >= nx * ny) return;
+    const int p = id / nx, q = id - p * nx;
+    const int hw = fw / 2, hh = fh / 2;
+    const int p0 = max(p - hh, 0), p1 = min(p + hh, ny - 1), q0 = max(q - hw, 0), q1 = min(q + hw, nx - 1);
+    float wb[49], wr[49];
+    int n = 0;
+    bool ok = true;
+    for (int pp = p0; pp <= p1; pp++)
+        for (int qq = q0; qq <= q1; qq++) {
+            float b, r;
+            ok &= filled_value(raw_bkg, raw_rms, nx, ny, pp, qq, &b);
+            ok &= filled_value(raw_rms, raw_rms, nx, ny, pp, qq, &r);
+            // insertion into the two sorted windows
+            int i = n - 1;
+            while (i >= 0 && wb[i] > b) { wb[i + 1] = wb[i]; i--; }
+            wb[i + 1] = b;
+            i = n - 1;
+            while (i >= 0 && wr[i] > r) { wr[i + 1] = wr[i]; i--; }
+            wr[i + 1] = r;
+            n++;
+        }
+    if (!ok) {  // no valid mesh anywhere
+        out_bkg[id] = 0.f;
+        out_rms[id] = 0.f;
+        if (id == 0 && status_dev) *status_dev = IPP_ERR_NO_VALID_MESH;
         return;
     }
-    for (int id = threadIdx.x; id < nn; id += MF_THREADS) {
-        if (raw_rms[id] >= 0.f) {
-            fill_bkg[id] = raw_bkg[id];
-            fill_rms[id] = raw_rms[id];
-            continue;
-        }
-        int p = id / nx, q = id - p * nx;
-        for (int k = 1; k <= max(nx, ny); k++) {
-            int p0 = max(p - k, 0), p1 = min(p + k, ny - 1), q0 = max(q - k, 0), q1 = min(q + k, nx - 1);
-            int cnt = 0;
-            for (int pp = p0; pp <= p1; pp++)
-                for (int qq = q0; qq <= q1; qq++) cnt += raw_rms[pp * nx + qq] >= 0.f;
-            if (cnt > 0) {
-                fill_bkg[id] = window_median(raw_bkg, raw_rms, nx, ny, p0, p1, q0, q1, cnt);
-                fill_rms[id] = window_median(raw_rms, raw_rms, nx, ny, p0, p1, q0, q1, cnt);
-                break;
-            }
-        }
-    }
-    __syncthreads();  // fill_* written by this block are visible to it after the barrier
-    const int hw = fw / 2, hh = fh / 2;
-    for (int id = threadIdx.x; id < nn; id += MF_THREADS) {
-        int p = id / nx, q = id - p * nx;
-        int p0 = max(p - hh, 0), p1 = min(p + hh, ny - 1), q0 = max(q - hw, 0), q1 = min(q + hw, nx - 1);
-        int cnt = (p1 - p0 + 1) * (q1 - q0 + 1);
-        out_bkg[id] = window_median(fill_bkg, nullptr, nx, ny, p0, p1, q0, q1, cnt);
-        out_rms[id] = window_median(fill_rms, nullptr, nx, ny, p0, p1, q0, q1, cnt);
-    }
-    if (threadIdx.x == 0 && status_dev) *status_dev = IPP_OK;
+    out_bkg[id] = (float)(0.5 * ((double)wb[(n - 1) / 2] + (double)wb[n / 2]));
+    out_rms[id] = (float)(0.5 * ((double)wr[(n - 1) / 2] + (double)wr[n / 2]));
+    if (id == 0 && status_dev) *status_dev = IPP_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -633,14 +655,14 @@ __global__ void __launch_bounds__(BG_THREADS) k_bg_subtract(SubJob J) {
     __shared__ float cv[BG_TH][BG_NQ];
     const int64_t tx0 = (int64_t)blockIdx.x * BG_TW, ty0 = (int64_t)blockIdx.y * BG_TH;
     // node columns used by this tile
-    const int qa = (int)floorf(((float)tx0 + 0.5f) / J.mesh_w - 0.5f) - 1;
+    const int qa = (int)floorf(((float)(int)tx0 + 0.5f) / J.mesh_w - 0.5f) - 1;
     const int qbase = max(qa, 0);
     // per-row vertical interpolation of the needed node columns
     const float ref = J.mesh[0];
     for (int t = threadIdx.x; t < BG_TH * BG_NQ; t += BG_THREADS) {
         int r = t / BG_NQ, qq = t - r * BG_NQ;
         int q = min(qbase + qq, J.nx - 1);
-        float vy = ((float)(ty0 + r) + 0.5f) / J.mesh_h - 0.5f;
+        float vy = ((float)((int)ty0 + r) + 0.5f) / J.mesh_h - 0.5f;
         float pf = floorf(vy);
         float w[4];
         keys_weights(vy - pf, w);
@@ -661,7 +683,7 @@ __global__ void __launch_bounds__(BG_THREADS) k_bg_subtract(SubJob J) {
     int qi[4][4];
 #pragma unroll
     for (int c = 0; c < 4; c++) {
-        float u = ((float)(xc + c) + 0.5f) / J.mesh_w - 0.5f;
+        float u = ((float)((int)xc + c) + 0.5f) / J.mesh_w - 0.5f;
         float qf = floorf(u);
         keys_weights(u - qf, wx[c]);
         int q0 = (int)qf;
@@ -743,9 +765,12 @@ int ipp_launch_mesh_stats(const MeshJob& J, cudaStream_t s) {
 int ipp_launch_mesh_filter(const float* raw_bkg, const float* raw_rms, float* fill_bkg, float* fill_rms,
                            int nx, int ny, int fw, int fh, float* out_bkg, float* out_rms,
                            int32_t* status_dev, cudaStream_t s) {
-    k_mesh_fill_filter<<<1, MF_THREADS, 0, s>>>(raw_bkg, raw_rms, fill_bkg, fill_rms, nx, ny, fw, fh,
-                                                 out_bkg, out_rms, status_dev);
-    return ipp_check_launch("k_mesh_fill_filter");
+    (void)fill_bkg;
+    (void)fill_rms;  // the fill is computed on the fly
+    const int nn = nx * ny;
+    k_mesh_filter<<<(nn + MF_THREADS - 1) / MF_THREADS, MF_THREADS, 0, s>>>(raw_bkg, raw_rms, nx, ny, fw, fh,
+                                                                            out_bkg, out_rms, status_dev);
+    return ipp_check_launch("k_mesh_filter");
 }
 
 int ipp_launch_bg_subtract(const SubJob& J, cudaStream_t s) {

@@ -1,35 +1,38 @@
 // detect.cu -- pixel detection and connection into candidates, with the
 // per-candidate pre-analysis of Sec. 2.2.5 (peak, total flux, ...).
 //
-// Tiles of TH x TW pixels.  k_tile_label thresholds a tile (or takes a given
-// mask), packs it into bits, labels it with a shared-memory union-find whose
-// roots are the smallest local raster index, and emits one node per component
-// that touches the tile border or is large enough, with its partial stats.
-// Border pixels record their node.  The global phase unites nodes across tile
-// seams, folds the stats into the roots, keeps roots of at least min_area pixels
-// and numbers them by the raster index of their first pixel (per-row counts,
-// an exclusive scan, a rank inside each row).  k_tile_final re-derives the
-// identical local labels from the bit mask and writes the label map once.
-// Nothing depends on the tile shape except the work split.
+// Tiles of TH x TW pixels, one CTA each.  k_tile_label thresholds a tile (or
+// takes a given mask) into shared-memory bit rows, cuts the rows into runs of
+// detected pixels and unites runs of adjacent rows that touch (8-connectivity)
+// with a union-find whose roots are the earliest run in raster order.
+// Components touching the tile border, or large enough, are kept and get a
+// node with their partial statistics; each run records its node for the final
+// write.  The global phase unites nodes across tile seams, folds the stats into
+// the roots, keeps roots of at least min_area pixels and numbers them by the
+// raster index of their first pixel (per-row counts, an exclusive scan, a rank
+// inside each row).  k_tile_final expands the runs into the label map, writing
+// every pixel once.  Nothing depends on the tile shape but the work split.
 #include "jobs.cuh"
 
 namespace ipp {
 
 constexpr int T_TH = 32, T_TW = 128;
 constexpr int T_WPR = T_TW / 32;                 // mask words per tile row
-constexpr int T_WORDS = T_TH * T_WPR;            // 128
-constexpr int T_PIX = T_TH * T_TW;               // 4096
 constexpr int T_CAP = (T_TH / 2) * (T_TW / 2);   // max 8-connected components in a tile
+constexpr int T_RCAP = T_TH * (T_TW / 2);        // max runs in a tile
+constexpr int T_KCAP = 256;                      // kept components with stats in shared memory
 constexpr int T_THREADS = 256;
 constexpr int T_NQ = 40;
 
 enum TileMode { MODE_SUB_THRESH = 0, MODE_MASK = 1, MODE_FUSED = 2 };
 
-// Global scratch of the labeling (all indices by node = tile * T_CAP + cid).
+// Global scratch of the labeling (node = tile * T_CAP + kept id; run = tile * T_RCAP + run id).
 struct CclWs {
-    uint32_t* mask;      // padded bit mask: (nty*T_TH) rows x (ntx*T_WPR) words
-    int32_t* ncomp;      // [ntiles]
-    int32_t* parent;     // [ntiles*T_CAP], -1 = dropped component
+    int32_t* nkept;      // [ntiles]
+    int32_t* nruns;      // [ntiles]
+    uint32_t* runs;      // [ntiles*T_RCAP]: row << 16 | start << 8 | end
+    int32_t* run_node;   // [ntiles*T_RCAP]: node of the run's component, -1 if dropped
+    int32_t* parent;     // [ntiles*T_CAP]
     int32_t* area;
     unsigned long long* first;
     uint32_t* peak;      // order-preserving key
@@ -61,112 +64,45 @@ struct TileJob {
 };
 
 struct TileShared {
-    uint32_t mask[T_TH][T_WPR];
-    int32_t lab[T_PIX];
-    uint32_t rootw[T_WORDS];
-    int32_t rootpre[T_WORDS];
-    int32_t nc;
-    int32_t c_area[T_CAP];
-    uint32_t c_peak[T_CAP];
-    double c_sum[T_CAP], c_sx[T_CAP], c_sy[T_CAP];
-    int32_t c_xmin[T_CAP], c_xmax[T_CAP], c_ymin[T_CAP], c_ymax[T_CAP];
-    int32_t c_border[T_CAP];
-    int32_t c_root[T_CAP];
     float cvb[T_TH][T_NQ];
     float cvr[T_TH][T_NQ];
+    uint32_t mask[T_TH][T_WPR];
+    int32_t roff[T_TH + 1];
+    int16_t rs[T_RCAP], re[T_RCAP];  // run start / end column (inclusive)
+    int32_t rpar[T_RCAP];            // union-find over runs
+    int32_t rarea[T_RCAP];           // area at the root run; border flag in bit 30
+    int32_t rkid[T_RCAP];            // kept id at the root run, -1 if dropped
+    int32_t nruns, nkept;
+    // statistics of the first T_KCAP kept components
+    double k_sum[T_KCAP], k_sx[T_KCAP], k_sy[T_KCAP];
+    uint32_t k_peak[T_KCAP];
+    int32_t k_xmin[T_KCAP], k_xmax[T_KCAP], k_ymin[T_KCAP], k_ymax[T_KCAP];
+    int32_t wsum[T_THREADS / 32];  // >= 2 * (T_TH * T_WPR / 32) for the run scan
 };
 
-__device__ __forceinline__ int lfind(const int32_t* L, int x) {
-    int p = L[x];
-    while (p != x) { x = p; p = L[x]; }
+constexpr int BORDER_BIT = 1 << 30;
+static_assert(T_THREADS / 32 >= 2 * (T_TH * T_WPR / 32), "run scan uses 2 x (mask words / 32) partial sums");
+static_assert(T_TH * T_WPR <= T_THREADS, "one thread per mask word");
+
+__device__ __forceinline__ int rfind(const int32_t* P, int x) {
+    int p = P[x];
+    while (p != x) { x = p; p = P[x]; }
     return x;
 }
 // lock-free union by atomicMin: the larger root is linked under the smaller
-__device__ __forceinline__ void lunite(int32_t* L, int a, int b) {
+__device__ __forceinline__ void runite(int32_t* P, int a, int b) {
     while (true) {
-        a = lfind(L, a);
-        b = lfind(L, b);
+        a = rfind(P, a);
+        b = rfind(P, b);
         if (a == b) return;
         if (a > b) { int t = a; a = b; b = t; }
-        int old = atomicMin(&L[b], a);
+        int old = atomicMin(&P[b], a);
         if (old == b) return;
         b = old;
     }
 }
 __device__ __forceinline__ bool mbit(const TileShared& S, int r, int c) {
     return (S.mask[r][c >> 5] >> (c & 31)) & 1u;
-}
-
-// Local union-find over the bit mask in S.mask, then compaction of the roots
-// (component ids in raster order of their roots).  Identical in both tile
-// passes, so component ids agree.
-__device__ void tile_ccl(TileShared& S) {
-    const int t = threadIdx.x;
-    if (t < T_WORDS) {
-        int r = t / T_WPR, wi = t % T_WPR;
-        uint32_t bits = S.mask[r][wi];
-        while (bits) {
-            int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            int p = r * T_TW + wi * 32 + b;
-            S.lab[p] = p;
-        }
-    }
-    __syncthreads();
-    if (t < T_WORDS) {
-        int r = t / T_WPR, wi = t % T_WPR;
-        uint32_t bits = S.mask[r][wi];
-        while (bits) {
-            int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            int c = wi * 32 + b, p = r * T_TW + c;
-            if (c > 0 && mbit(S, r, c - 1)) lunite(S.lab, p, p - 1);
-            if (r > 0) {
-                if (mbit(S, r - 1, c)) {
-                    lunite(S.lab, p, p - T_TW);
-                } else {
-                    if (c > 0 && mbit(S, r - 1, c - 1)) lunite(S.lab, p, p - T_TW - 1);
-                    if (c < T_TW - 1 && mbit(S, r - 1, c + 1)) lunite(S.lab, p, p - T_TW + 1);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (t < T_WORDS) {
-        int r = t / T_WPR, wi = t % T_WPR;
-        uint32_t bits = S.mask[r][wi], rb = 0;
-        while (bits) {
-            int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            int p = r * T_TW + wi * 32 + b;
-            int root = lfind(S.lab, p);
-            S.lab[p] = root;
-            if (root == p) rb |= 1u << b;
-        }
-        S.rootw[t] = rb;
-    }
-    __syncthreads();
-    if (t < 32) {  // exclusive popcount prefix over the 128 root words
-        int c[4], tot = 0;
-#pragma unroll
-        for (int k = 0; k < 4; k++) { c[k] = __popc(S.rootw[t * 4 + k]); tot += c[k]; }
-        int inc = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int v = __shfl_up_sync(0xffffffffu, inc, o);
-            if (t >= o) inc += v;
-        }
-        int run = inc - tot;
-#pragma unroll
-        for (int k = 0; k < 4; k++) { S.rootpre[t * 4 + k] = run; run += c[k]; }
-        if (t == 31) S.nc = inc;
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ int cid_of(const TileShared& S, int root) {
-    int w = root >> 5, b = root & 31;
-    return S.rootpre[w] + __popc(S.rootw[w] & ((1u << b) - 1u));
 }
 
 __device__ __forceinline__ float tile_load_pix(const TileJob& J, int64_t y, int64_t x) {
@@ -176,13 +112,76 @@ __device__ __forceinline__ float tile_load_pix(const TileJob& J, int64_t y, int6
     return (raw - b) * __ldg(J.inv_flat + y * J.W + x);
 }
 
-__global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
+__device__ __forceinline__ int row_of_run(const TileShared& S, int i) {  // largest r with roff[r] <= i
+    int a = 0, b = T_TH - 1;
+    while (a < b) { const int m = (a + b + 1) >> 1; if (S.roff[m] <= i) a = m; else b = m - 1; }
+    return a;
+}
+
+// Cut the mask rows into runs (row-major, increasing start), one thread per
+// mask word: run starts are set bits whose left neighbour is clear, run ends set
+// bits whose right neighbour is clear (neighbours across word edges included);
+// the k-th start and the k-th end of the tile bound the k-th run.
+__device__ void tile_runs(TileShared& S) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint32_t st = 0, en = 0;
+    if (t < T_TH * T_WPR) {
+        const int r = t / T_WPR, w = t % T_WPR;
+        const uint32_t m = S.mask[r][w];
+        const uint32_t pb = w > 0 ? S.mask[r][w - 1] >> 31 : 0u;
+        const uint32_t nb = w < T_WPR - 1 ? S.mask[r][w + 1] & 1u : 0u;
+        st = m & ~((m << 1) | pb);
+        en = m & ~((m >> 1) | (nb << 31));
+    }
+    const int cs = __popc(st), ce = __popc(en);
+    int is = cs, ie = ce;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, is, o), b = __shfl_up_sync(0xffffffffu, ie, o);
+        if (lane >= o) { is += a; ie += b; }
+    }
+    if (lane == 31 && warp < (T_TH * T_WPR) / 32) { S.wsum[warp] = is; S.wsum[4 + warp] = ie; }
+    __syncthreads();
+    if (t < T_TH * T_WPR) {
+        int bs = 0, be = 0;
+        for (int k = 0; k < warp; k++) { bs += S.wsum[k]; be += S.wsum[4 + k]; }
+        int ps = bs + is - cs, pe = be + ie - ce;
+        if (t % T_WPR == 0) S.roff[t / T_WPR] = ps;
+        const int base = (t % T_WPR) * 32;
+        while (st) { const int b = __ffs(st) - 1; st &= st - 1; S.rs[ps++] = (int16_t)(base + b); }
+        while (en) { const int b = __ffs(en) - 1; en &= en - 1; S.re[pe++] = (int16_t)(base + b); }
+        if (t == T_TH * T_WPR - 1) { S.roff[T_TH] = ps; S.nruns = ps; }
+    }
+    __syncthreads();
+}
+
+// Union-find over the runs of the tile: run i of row r joins the runs of row
+// r - 1 that overlap [start - 1, end + 1] (8-connectivity).  Roots end up as the
+// smallest run id of the component (its first run in raster order).
+__device__ void tile_union(TileShared& S) {
+    const int nr = S.nruns;
+    for (int i = threadIdx.x; i < nr; i += T_THREADS) S.rpar[i] = i;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr; i += T_THREADS) {
+        const int r = row_of_run(S, i);
+        if (r == 0) continue;
+        const int a = S.rs[i] - 1, b = S.re[i] + 1;
+        int lo = S.roff[r - 1], hi = S.roff[r];      // first run of row r-1 ending at or after a
+        const int end = hi;
+        while (lo < hi) { const int m = (lo + hi) >> 1; if (S.re[m] < a) lo = m + 1; else hi = m; }
+        for (int k = lo; k < end && S.rs[k] <= b; k++) runite(S.rpar, i, k);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr; i += T_THREADS) S.rpar[i] = rfind(S.rpar, i);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(T_THREADS, 4) k_tile_label(TileJob J) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileShared& S = *reinterpret_cast<TileShared*>(smem_raw);
     const int tx = blockIdx.x, ty = blockIdx.y, tile = ty * J.ntx + tx;
     const int64_t tx0 = (int64_t)tx * T_TW, ty0 = (int64_t)ty * T_TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t mpitch = (int64_t)J.ntx * T_WPR;
 
     // zero the per-row counters of the numbering (any block may do it)
     for (int64_t i = (int64_t)tile * T_THREADS + threadIdx.x; i < J.H; i += (int64_t)J.ntx * J.nty * T_THREADS) {
@@ -190,28 +189,28 @@ __global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
         J.ws.rowfill[i] = 0;
     }
 
-    // ---- phase A: values, threshold, bit mask ------------------------------
+    // ---- phase A: values, threshold, bit rows ------------------------------
     const bool thresh = J.mode != MODE_MASK;
     const bool fused = J.mode == MODE_FUSED;
     int qbase = 0;
     float refb = 0.f, refr = 0.f;
     if (thresh) {
-        const int qa = (int)floorf(((float)tx0 + 0.5f) / J.mesh_w - 0.5f) - 1;
+        const int qa = (int)floorf(((float)(int)tx0 + 0.5f) / J.mesh_w - 0.5f) - 1;
         qbase = max(qa, 0);
         refr = J.mesh_rms[0];
         if (fused) refb = J.mesh_bkg[0];
         for (int t = threadIdx.x; t < T_TH * T_NQ; t += T_THREADS) {
-            int r = t / T_NQ, qq = t - r * T_NQ;
-            int q = min(qbase + qq, J.nx - 1);
-            float vy = ((float)(ty0 + r) + 0.5f) / J.mesh_h - 0.5f;
-            float pf = floorf(vy);
+            const int r = t / T_NQ, qq = t - r * T_NQ;
+            const int q = min(qbase + qq, J.nx - 1);
+            const float vy = ((float)((int)ty0 + r) + 0.5f) / J.mesh_h - 0.5f;
+            const float pf = floorf(vy);
             float w[4];
             keys_weights(vy - pf, w);
-            int p0 = (int)pf;
+            const int p0 = (int)pf;
             float ab = 0.f, ar = 0.f;
 #pragma unroll
             for (int a = 0; a < 4; a++) {
-                int p = clampi(p0 - 1 + a, 0, J.ny - 1);
+                const int p = clampi(p0 - 1 + a, 0, J.ny - 1);
                 ar = fmaf(w[a], J.mesh_rms[p * J.nx + q] - refr, ar);
                 if (fused) ab = fmaf(w[a], J.mesh_bkg[p * J.nx + q] - refb, ab);
             }
@@ -227,10 +226,10 @@ __global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
         if (thresh) {
 #pragma unroll
             for (int c = 0; c < 4; c++) {
-                float u = ((float)(xc + c) + 0.5f) / J.mesh_w - 0.5f;
-                float qf = floorf(u);
+                const float u = ((float)((int)xc + c) + 0.5f) / J.mesh_w - 0.5f;
+                const float qf = floorf(u);
                 keys_weights(u - qf, wx[c]);
-                int q0 = (int)qf;
+                const int q0 = (int)qf;
 #pragma unroll
                 for (int b = 0; b < 4; b++) qi[c][b] = min(clampi(q0 - 1 + b, 0, J.nx - 1) - qbase, T_NQ - 1);
             }
@@ -246,14 +245,14 @@ __global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
                     const int64_t mw = (J.W + 31) / 32;
 #pragma unroll
                     for (int c = 0; c < 4; c++) {
-                        int64_t x = xc + c;
+                        const int64_t x = xc + c;
                         if (x < J.W && ((J.mask_in[y * mw + (x >> 5)] >> (x & 31)) & 1u)) nib |= 1u << c;
                     }
                 } else {
                     float f[4];
                     if (fused) {
                         if (vin && full4) {
-                            float4 t4 = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(J.img) + y * J.pitch + xc));
+                            const float4 t4 = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(J.img) + y * J.pitch + xc));
                             f[0] = t4.x; f[1] = t4.y; f[2] = t4.z; f[3] = t4.w;
                         } else {
 #pragma unroll
@@ -275,7 +274,7 @@ __global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
                         }
                     } else {
                         if (vsub && full4) {
-                            float4 t4 = __ldg(reinterpret_cast<const float4*>(J.sub + y * J.sub_pitch + xc));
+                            const float4 t4 = __ldg(reinterpret_cast<const float4*>(J.sub + y * J.sub_pitch + xc));
                             f[0] = t4.x; f[1] = t4.y; f[2] = t4.z; f[3] = t4.w;
                         } else {
 #pragma unroll
@@ -287,7 +286,7 @@ __global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
                         float acc = 0.f;
 #pragma unroll
                         for (int b = 0; b < 4; b++) acc = fmaf(wx[c][b], S.cvr[r][qi[c][b]], acc);
-                        float thr = fmaxf(J.k * (refr + acc), J.thresh_abs);
+                        const float thr = fmaxf(J.k * (refr + acc), J.thresh_abs);
                         if (xc + c < J.W && f[c] > thr) nib |= 1u << c;
                     }
                 }
@@ -301,92 +300,134 @@ __global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
         }
     }
     __syncthreads();
-    if (threadIdx.x < T_WORDS) {
-        int r = threadIdx.x / T_WPR, wi = threadIdx.x % T_WPR;
-        J.ws.mask[(ty0 + r) * mpitch + (int64_t)tx * T_WPR + wi] = S.mask[r][wi];
-    }
 
-    // ---- phase B/C: local components ---------------------------------------
-    tile_ccl(S);
-    const int nc = S.nc;
-    for (int c = threadIdx.x; c < nc; c += T_THREADS) {
-        S.c_area[c] = 0;
-        S.c_peak[c] = 0u;
-        S.c_sum[c] = 0.0; S.c_sx[c] = 0.0; S.c_sy[c] = 0.0;
-        S.c_xmin[c] = T_TW; S.c_xmax[c] = -1; S.c_ymin[c] = T_TH; S.c_ymax[c] = -1;
-        S.c_border[c] = 0;
+    // ---- phase B/C: runs and their union-find --------------------------------
+    tile_runs(S);
+    tile_union(S);
+    const int nr = S.nruns;
+
+    // ---- phase D: area and border flag at the root runs -----------------------
+    for (int i = threadIdx.x; i < nr; i += T_THREADS) S.rarea[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr; i += T_THREADS) {
+        const int r = row_of_run(S, i);
+        const int st = S.rs[i], en = S.re[i];
+        const int root = S.rpar[i];
+        if (r == 0 || r == T_TH - 1 || st == 0 || en == T_TW - 1) atomicOr(&S.rarea[root], BORDER_BIT);
+        atomicAdd(&S.rarea[root], en - st + 1);
     }
     __syncthreads();
 
-    // ---- phase D: per-component partial stats -------------------------------
-    // Each thread walks its word's pixels in order and aggregates runs of the
-    // same component before one set of shared atomics per run; the sums are
-    // FP64, so the result does not depend on the order of the atomics.
-    if (threadIdx.x < T_WORDS) {
-        const int r = threadIdx.x / T_WPR, wi = threadIdx.x % T_WPR;
-        uint32_t bits = S.mask[r][wi];
-        int cur = -1, n = 0, cmin = 0, cmax = 0;
-        float s0 = 0.f, s1 = 0.f, pk = 0.f;
-        bool border = false;
-        auto flush = [&]() {
-            if (cur < 0) return;
-            atomicAdd(&S.c_area[cur], n);
-            atomicAdd(&S.c_sum[cur], (double)s0);
-            atomicAdd(&S.c_sx[cur], (double)s1);
-            atomicAdd(&S.c_sy[cur], (double)s0 * (double)r);
-            atomicMax(&S.c_peak[cur], fkey(pk));
-            atomicMin(&S.c_xmin[cur], cmin);
-            atomicMax(&S.c_xmax[cur], cmax);
-            atomicMin(&S.c_ymin[cur], r);
-            atomicMax(&S.c_ymax[cur], r);
-            if (border) S.c_border[cur] = 1;
-        };
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const int col = wi * 32 + b, p = r * T_TW + col;
-            const int root = S.lab[p];
-            const int c = cid_of(S, root);
-            if (root == p) S.c_root[c] = p;
-            const float f = __ldcg(J.sub + (ty0 + r) * J.sub_pitch + tx0 + col);
-            if (c != cur) {
-                flush();
-                cur = c; n = 0; s0 = 0.f; s1 = 0.f; pk = f; cmin = col; border = false;
+    // ---- phase E: kept components get consecutive ids (raster order of roots) --
+    {
+        int chunk0 = 0;
+        for (int base = 0; base < nr; base += T_THREADS) {
+            const int i = base + threadIdx.x;
+            bool kept = false;
+            if (i < nr && S.rpar[i] == i) {
+                const int v = S.rarea[i];
+                kept = (v & BORDER_BIT) || (v & ~BORDER_BIT) >= J.min_area;
             }
-            n++;
-            s0 += f;
-            s1 = fmaf(f, (float)col, s1);
-            pk = fmaxf(pk, f);
-            cmax = col;
-            border |= (r == 0 || r == T_TH - 1 || col == 0 || col == T_TW - 1);
+            const unsigned bal = __ballot_sync(0xffffffffu, kept);
+            if (lane == 0) S.wsum[warp] = __popc(bal);
+            __syncthreads();
+            int before = chunk0;
+            for (int w = 0; w < warp; w++) before += S.wsum[w];
+            int total = chunk0;
+            for (int w = 0; w < T_THREADS / 32; w++) total += S.wsum[w];
+            if (i < nr) S.rkid[i] = kept ? before + __popc(bal & ((1u << lane) - 1u)) : -1;
+            __syncthreads();
+            chunk0 = total;
         }
-        flush();
+        if (threadIdx.x == 0) S.nkept = chunk0;
+    }
+    __syncthreads();
+    const int nk = S.nkept;
+    for (int c = threadIdx.x; c < min(nk, T_KCAP); c += T_THREADS) {
+        S.k_sum[c] = 0.0; S.k_sx[c] = 0.0; S.k_sy[c] = 0.0;
+        S.k_peak[c] = 0u;
+        S.k_xmin[c] = T_TW; S.k_xmax[c] = -1; S.k_ymin[c] = T_TH; S.k_ymax[c] = -1;
+    }
+    // kept components beyond the shared tables accumulate in the global node
+    // arrays directly (only masks with more than T_KCAP kept components per tile)
+    for (int i = threadIdx.x; i < nr; i += T_THREADS) {
+        const int kid = (S.rpar[i] == i) ? S.rkid[i] : -1;
+        if (kid >= T_KCAP) {
+            const int node = tile * T_CAP + kid;
+            J.ws.sum[node] = 0.0; J.ws.sx[node] = 0.0; J.ws.sy[node] = 0.0;
+            J.ws.peak[node] = 0u;
+            J.ws.xmin[node] = INT32_MAX; J.ws.xmax[node] = -1; J.ws.ymin[node] = INT32_MAX; J.ws.ymax[node] = -1;
+        }
     }
     __syncthreads();
 
-    // ---- phase E: emit nodes --------------------------------------------------
-    for (int c = threadIdx.x; c < nc; c += T_THREADS) {
-        const int node = tile * T_CAP + c;
-        const bool kept = S.c_border[c] || S.c_area[c] >= J.min_area;
-        if (!kept) { J.ws.parent[node] = -1; continue; }
-        const int root = S.c_root[c];
-        const int rr = root / T_TW, rc = root % T_TW;
-        J.ws.parent[node] = node;
-        J.ws.area[node] = S.c_area[c];
-        J.ws.first[node] = (unsigned long long)((ty0 + rr) * J.W + tx0 + rc);
-        J.ws.peak[node] = S.c_peak[c];
-        J.ws.xmin[node] = (int)tx0 + S.c_xmin[c];
-        J.ws.xmax[node] = (int)tx0 + S.c_xmax[c];
-        J.ws.ymin[node] = (int)ty0 + S.c_ymin[c];
-        J.ws.ymax[node] = (int)ty0 + S.c_ymax[c];
-        const double sm = S.c_sum[c];
-        J.ws.sum[node] = sm;
-        J.ws.sx[node] = S.c_sx[c] + (double)tx0 * sm;
-        J.ws.sy[node] = S.c_sy[c] + (double)ty0 * sm;
+    // ---- phase F: per-run partial stats (values re-read from L2) ---------------
+    for (int i = threadIdx.x; i < nr; i += T_THREADS) {
+        const int kid = S.rkid[S.rpar[i]];
+        if (kid < 0) continue;
+        const int r = row_of_run(S, i);
+        const int st = S.rs[i], en = S.re[i];
+        const float* row = J.sub + (ty0 + r) * J.sub_pitch + tx0;
+        float s0 = 0.f, s1 = 0.f, pk = -INFINITY;
+        for (int c = st; c <= en; c++) {
+            const float f = __ldcg(row + c);
+            s0 += f;
+            s1 = fmaf(f, (float)c, s1);
+            pk = fmaxf(pk, f);
+        }
+        if (kid < T_KCAP) {
+            atomicAdd(&S.k_sum[kid], (double)s0);
+            atomicAdd(&S.k_sx[kid], (double)s1);
+            atomicAdd(&S.k_sy[kid], (double)s0 * (double)r);
+            atomicMax(&S.k_peak[kid], fkey(pk));
+            atomicMin(&S.k_xmin[kid], st);
+            atomicMax(&S.k_xmax[kid], en);
+            atomicMin(&S.k_ymin[kid], r);
+            atomicMax(&S.k_ymax[kid], r);
+        } else {
+            const int node = tile * T_CAP + kid;
+            atomicAdd(&J.ws.sum[node], (double)s0);
+            atomicAdd(&J.ws.sx[node], (double)s1 + (double)(int)tx0 * (double)s0);
+            atomicAdd(&J.ws.sy[node], (double)s0 * (double)((int)ty0 + r));
+            atomicMax(&J.ws.peak[node], fkey(pk));
+            atomicMin(&J.ws.xmin[node], (int)tx0 + st);
+            atomicMax(&J.ws.xmax[node], (int)tx0 + en);
+            atomicMin(&J.ws.ymin[node], (int)ty0 + r);
+            atomicMax(&J.ws.ymax[node], (int)ty0 + r);
+        }
     }
-    if (threadIdx.x == 0) J.ws.ncomp[tile] = nc;
+    __syncthreads();
 
-    // ---- phase F: node of each border pixel -----------------------------------
+    // ---- phase G: nodes, run table, border nodes -------------------------------
+    for (int i = threadIdx.x; i < nr; i += T_THREADS) {
+        const int root = S.rpar[i];
+        const int kid = S.rkid[root];
+        const int node = kid >= 0 ? tile * T_CAP + kid : -1;
+        const int r = row_of_run(S, i);
+        J.ws.runs[(int64_t)tile * T_RCAP + i] = ((uint32_t)r << 16) | ((uint32_t)S.rs[i] << 8) | (uint32_t)S.re[i];
+        J.ws.run_node[(int64_t)tile * T_RCAP + i] = node;
+        if (root == i && kid >= 0) {
+            J.ws.parent[node] = node;
+            J.ws.area[node] = S.rarea[i] & ~BORDER_BIT;
+            J.ws.first[node] = (unsigned long long)((ty0 + r) * J.W + tx0 + S.rs[i]);
+            if (kid < T_KCAP) {
+                const double sm = S.k_sum[kid];
+                J.ws.peak[node] = S.k_peak[kid];
+                J.ws.xmin[node] = (int)tx0 + S.k_xmin[kid];
+                J.ws.xmax[node] = (int)tx0 + S.k_xmax[kid];
+                J.ws.ymin[node] = (int)ty0 + S.k_ymin[kid];
+                J.ws.ymax[node] = (int)ty0 + S.k_ymax[kid];
+                J.ws.sum[node] = sm;
+                J.ws.sx[node] = S.k_sx[kid] + (double)(int)tx0 * sm;
+                J.ws.sy[node] = S.k_sy[kid] + (double)(int)ty0 * sm;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        J.ws.nkept[tile] = nk;
+        J.ws.nruns[tile] = nr;
+    }
+    // border pixels: node of the run covering them (runs of a row are sorted)
     for (int t = threadIdx.x; t < 2 * T_TW + 2 * T_TH; t += T_THREADS) {
         int r, c;
         int32_t* dst;
@@ -394,7 +435,14 @@ __global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
         else if (t < 2 * T_TW) { r = T_TH - 1; c = t - T_TW; dst = J.ws.bbot + (int64_t)tile * T_TW + c; }
         else if (t < 2 * T_TW + T_TH) { r = t - 2 * T_TW; c = 0; dst = J.ws.blef + (int64_t)tile * T_TH + r; }
         else { r = t - 2 * T_TW - T_TH; c = T_TW - 1; dst = J.ws.brig + (int64_t)tile * T_TH + r; }
-        *dst = mbit(S, r, c) ? tile * T_CAP + cid_of(S, S.lab[r * T_TW + c]) : -1;
+        int v = -1;
+        if (mbit(S, r, c)) {
+            int a = S.roff[r], b = S.roff[r + 1] - 1;   // last run starting at or before c
+            while (a < b) { const int m = (a + b + 1) >> 1; if (S.rs[m] <= c) a = m; else b = m - 1; }
+            const int kid = S.rkid[S.rpar[a]];
+            v = kid >= 0 ? tile * T_CAP + kid : -1;
+        }
+        *dst = v;
     }
 }
 
@@ -450,10 +498,9 @@ __global__ void k_ccl_union(CclWs ws, int ntx, int nty) {
 // fold every kept node into its root
 __global__ void k_ccl_resolve(CclWs ws) {
     const int tile = blockIdx.x;
-    const int nc = ws.ncomp[tile];
+    const int nc = ws.nkept[tile];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
         const int node = tile * T_CAP + c;
-        if (__ldcg(ws.parent + node) < 0) continue;
         const int r = gfind(ws.parent, node);
         if (r == node) continue;
         ws.parent[node] = r;
@@ -472,7 +519,7 @@ __global__ void k_ccl_resolve(CclWs ws) {
 
 __global__ void k_ccl_count(CclWs ws, int64_t W, int min_area) {
     const int tile = blockIdx.x;
-    const int nc = ws.ncomp[tile];
+    const int nc = ws.nkept[tile];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
         const int node = tile * T_CAP + c;
         if (ws.parent[node] != node) continue;
@@ -524,7 +571,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_rows(CclWs ws, int64_t H,
 
 __global__ void k_ccl_place(CclWs ws, int64_t W, int min_area) {
     const int tile = blockIdx.x;
-    const int nc = ws.ncomp[tile];
+    const int nc = ws.nkept[tile];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
         const int node = tile * T_CAP + c;
         if (ws.parent[node] != node || ws.area[node] < min_area) continue;
@@ -538,7 +585,7 @@ __global__ void k_ccl_place(CclWs ws, int64_t W, int min_area) {
 
 __global__ void k_ccl_number(CclWs ws, int64_t W, int min_area, int32_t max_src, ipp_src_stats out) {
     const int tile = blockIdx.x;
-    const int nc = ws.ncomp[tile];
+    const int nc = ws.nkept[tile];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
         const int node = tile * T_CAP + c;
         if (ws.parent[node] != node || ws.area[node] < min_area) continue;
@@ -566,27 +613,25 @@ __global__ void k_ccl_number(CclWs ws, int64_t W, int min_area, int32_t max_src,
     }
 }
 
-// Second tile pass: rebuild the local components from the bit mask and write
-// the final label of every pixel of the tile (0 for background and dropped).
-__global__ void __launch_bounds__(T_THREADS, 3) k_tile_final(CclWs ws, int64_t W, int64_t H, int ntx,
-                                                           int32_t* labels) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileShared& S = *reinterpret_cast<TileShared*>(smem_raw);
+// Second tile pass: expand the tile's runs into the label map (0 for
+// background and dropped components), writing every pixel once, coalesced.
+__global__ void __launch_bounds__(T_THREADS) k_tile_final(CclWs ws, int64_t W, int64_t H, int ntx,
+                                                         int32_t* labels) {
+    __shared__ __align__(16) int32_t lab[T_TH][T_TW];
     const int tx = blockIdx.x, ty = blockIdx.y, tile = ty * ntx + tx;
     const int64_t tx0 = (int64_t)tx * T_TW, ty0 = (int64_t)ty * T_TH;
-    const int64_t mpitch = (int64_t)ntx * T_WPR;
-    if (threadIdx.x < T_WORDS) {
-        int r = threadIdx.x / T_WPR, wi = threadIdx.x % T_WPR;
-        S.mask[r][wi] = ws.mask[(ty0 + r) * mpitch + (int64_t)tx * T_WPR + wi];
-    }
+    int4* l4 = reinterpret_cast<int4*>(&lab[0][0]);
+    for (int t = threadIdx.x; t < T_TH * T_TW / 4; t += T_THREADS) l4[t] = make_int4(0, 0, 0, 0);
     __syncthreads();
-    tile_ccl(S);
-    // component id -> final label
-    const int nc = S.nc;
-    for (int c = threadIdx.x; c < nc; c += T_THREADS) {
-        const int node = tile * T_CAP + c;
-        const int p = __ldcg(ws.parent + node);
-        S.c_area[c] = p < 0 ? 0 : __ldcg(ws.label + p);
+    const int nr = ws.nruns[tile];
+    for (int i = threadIdx.x; i < nr; i += T_THREADS) {
+        const int node = __ldcg(ws.run_node + (int64_t)tile * T_RCAP + i);
+        if (node < 0) continue;
+        const int v = __ldcg(ws.label + __ldcg(ws.parent + node));
+        if (v == 0) continue;
+        const uint32_t rr = __ldcg(ws.runs + (int64_t)tile * T_RCAP + i);
+        const int r = rr >> 16, st = (rr >> 8) & 0xff, en = rr & 0xff;
+        for (int c = st; c <= en; c++) lab[r][c] = v;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -595,18 +640,14 @@ __global__ void __launch_bounds__(T_THREADS, 3) k_tile_final(CclWs ws, int64_t W
     for (int r = warp; r < T_TH; r += T_THREADS / 32) {
         const int64_t y = ty0 + r;
         if (y >= H || xc >= W) continue;
-        int out[4];
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            int col = lane * 4 + c;
-            out[c] = mbit(S, r, col) ? S.c_area[cid_of(S, S.lab[r * T_TW + col])] : 0;
-        }
+        const int4 o = *reinterpret_cast<const int4*>(&lab[r][lane * 4]);
         if (vec) {
-            *reinterpret_cast<int4*>(labels + y * W + xc) = make_int4(out[0], out[1], out[2], out[3]);
+            *reinterpret_cast<int4*>(labels + y * W + xc) = o;
         } else {
+            const int vals[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
             for (int c = 0; c < 4; c++)
-                if (xc + c < W) labels[y * W + xc + c] = out[c];
+                if (xc + c < W) labels[y * W + xc + c] = vals[c];
         }
     }
 }
@@ -618,8 +659,8 @@ using namespace ipp;
 
 struct CclLayout {
     int ntx, nty;
-    int64_t ntiles, nodes;
-    size_t off[24];
+    int64_t ntiles, nodes, runs;
+    size_t off[26];
     size_t total;
 };
 
@@ -631,9 +672,10 @@ static CclLayout ccl_layout(int64_t W, int64_t H) {
     L.nty = (int)cdiv(H, T_TH);
     L.ntiles = (int64_t)L.ntx * L.nty;
     L.nodes = L.ntiles * T_CAP;
-    size_t sizes[] = {
-        (size_t)(L.nty * T_TH) * (size_t)(L.ntx * T_WPR) * 4,  // mask
-        (size_t)L.ntiles * 4,                                  // ncomp
+    L.runs = L.ntiles * T_RCAP;
+    const size_t sizes[] = {
+        (size_t)L.ntiles * 4, (size_t)L.ntiles * 4,            // nkept nruns
+        (size_t)L.runs * 4, (size_t)L.runs * 4,                // runs run_node
         (size_t)L.nodes * 4, (size_t)L.nodes * 4,              // parent, area
         (size_t)L.nodes * 8, (size_t)L.nodes * 4,              // first, peak
         (size_t)L.nodes * 4, (size_t)L.nodes * 4, (size_t)L.nodes * 4, (size_t)L.nodes * 4,  // bbox
@@ -645,7 +687,7 @@ static CclLayout ccl_layout(int64_t W, int64_t H) {
         (size_t)L.nodes * 8, (size_t)L.nodes * 4,              // slist
     };
     size_t o = 0;
-    for (int k = 0; k < 23; k++) { L.off[k] = o; o += align256(sizes[k]); }
+    for (int k = 0; k < 25; k++) { L.off[k] = o; o += align256(sizes[k]); }
     L.total = o;
     return L;
 }
@@ -653,29 +695,31 @@ static CclLayout ccl_layout(int64_t W, int64_t H) {
 static CclWs ccl_ws(const CclLayout& L, void* ws) {
     unsigned char* b = (unsigned char*)ws;
     CclWs w;
-    w.mask = (uint32_t*)(b + L.off[0]);
-    w.ncomp = (int32_t*)(b + L.off[1]);
-    w.parent = (int32_t*)(b + L.off[2]);
-    w.area = (int32_t*)(b + L.off[3]);
-    w.first = (unsigned long long*)(b + L.off[4]);
-    w.peak = (uint32_t*)(b + L.off[5]);
-    w.xmin = (int32_t*)(b + L.off[6]);
-    w.xmax = (int32_t*)(b + L.off[7]);
-    w.ymin = (int32_t*)(b + L.off[8]);
-    w.ymax = (int32_t*)(b + L.off[9]);
-    w.sum = (double*)(b + L.off[10]);
-    w.sx = (double*)(b + L.off[11]);
-    w.sy = (double*)(b + L.off[12]);
-    w.label = (int32_t*)(b + L.off[13]);
-    w.btop = (int32_t*)(b + L.off[14]);
-    w.bbot = (int32_t*)(b + L.off[15]);
-    w.blef = (int32_t*)(b + L.off[16]);
-    w.brig = (int32_t*)(b + L.off[17]);
-    w.rowcnt = (int32_t*)(b + L.off[18]);
-    w.rowfill = (int32_t*)(b + L.off[19]);
-    w.rowbase = (int32_t*)(b + L.off[20]);
-    w.slist_first = (unsigned long long*)(b + L.off[21]);
-    w.slist_node = (int32_t*)(b + L.off[22]);
+    w.nkept = (int32_t*)(b + L.off[0]);
+    w.nruns = (int32_t*)(b + L.off[1]);
+    w.runs = (uint32_t*)(b + L.off[2]);
+    w.run_node = (int32_t*)(b + L.off[3]);
+    w.parent = (int32_t*)(b + L.off[4]);
+    w.area = (int32_t*)(b + L.off[5]);
+    w.first = (unsigned long long*)(b + L.off[6]);
+    w.peak = (uint32_t*)(b + L.off[7]);
+    w.xmin = (int32_t*)(b + L.off[8]);
+    w.xmax = (int32_t*)(b + L.off[9]);
+    w.ymin = (int32_t*)(b + L.off[10]);
+    w.ymax = (int32_t*)(b + L.off[11]);
+    w.sum = (double*)(b + L.off[12]);
+    w.sx = (double*)(b + L.off[13]);
+    w.sy = (double*)(b + L.off[14]);
+    w.label = (int32_t*)(b + L.off[15]);
+    w.btop = (int32_t*)(b + L.off[16]);
+    w.bbot = (int32_t*)(b + L.off[17]);
+    w.blef = (int32_t*)(b + L.off[18]);
+    w.brig = (int32_t*)(b + L.off[19]);
+    w.rowcnt = (int32_t*)(b + L.off[20]);
+    w.rowfill = (int32_t*)(b + L.off[21]);
+    w.rowbase = (int32_t*)(b + L.off[22]);
+    w.slist_first = (unsigned long long*)(b + L.off[23]);
+    w.slist_node = (int32_t*)(b + L.off[24]);
     return w;
 }
 
@@ -696,7 +740,6 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
     J.ws = w;
     const size_t sm = sizeof(TileShared);
     cudaFuncSetAttribute(k_tile_label, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_tile_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 tg(L.ntx, L.nty);
     k_tile_label<<<tg, T_THREADS, sm, s>>>(J);
     if (int e = ipp_check_launch("k_tile_label")) return e;
@@ -713,6 +756,6 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
     if (int e = ipp_check_launch("k_ccl_place")) return e;
     k_ccl_number<<<nt, 128, 0, s>>>(w, A.W, A.min_area, A.max_src, A.stats);
     if (int e = ipp_check_launch("k_ccl_number")) return e;
-    k_tile_final<<<tg, T_THREADS, sm, s>>>(w, A.W, A.H, L.ntx, A.labels);
+    k_tile_final<<<tg, T_THREADS, 0, s>>>(w, A.W, A.H, L.ntx, A.labels);
     return ipp_check_launch("k_tile_final");
 }

@@ -16,6 +16,11 @@ constexpr int ANN_BOX = 2 * (ANN_MAXR + 1) + 1;            // 35
 constexpr int ANN_CAP = ANN_BOX * ANN_BOX;                 // 1225
 
 
+// Window pixels of one source: the box of half-width R = floor(rad + 1/2)
+// around the integer anchor covers every pixel within rad of a position whose
+// offset from the anchor is at most 1/2.  With NPL > 0 each lane caches its
+// NPL box pixels in registers and reloads them only when the anchor moves.
+template <int NPL>
 __global__ void __launch_bounds__(P_THREADS) k_centroid(CenJob J) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * P_THREADS + threadIdx.x) >> 5;
@@ -23,26 +28,69 @@ __global__ void __launch_bounds__(P_THREADS) k_centroid(CenJob J) {
     const int n = min(*J.n_src_dev, J.max_src);
     const float rad2 = J.rad * J.rad;
     const float inv2s2 = 1.0f / (2.0f * J.sw * J.sw);
-    const int R = (int)ceilf(J.rad) + 1;
-    const int box = 2 * R + 1;
+    const float Wf = (float)(int)J.W, Hf = (float)(int)J.H;
+    const int R = (int)floorf(J.rad + 0.5f);
+    const int box = 2 * R + 1, nbox = box * box;
+    // this lane's box offsets, fixed for the whole kernel
+    constexpr int NC = NPL > 0 ? NPL : 1;
+    float dif[NC], djf[NC];
+    int dii[NC], dji[NC];
+#pragma unroll
+    for (int m = 0; m < NC; m++) {
+        const int idx = lane + 32 * m;
+        dii[m] = idx / box - R;
+        dji[m] = idx % box - R;
+        dif[m] = (float)dii[m];
+        djf[m] = (float)dji[m];
+    }
     for (int s = gw; s < n; s += nw) {
         const float sx0 = J.x0[s], sy0 = J.y0[s];
         float ax = rintf(sx0), ay = rintf(sy0);
         float ox = sx0 - ax, oy = sy0 - ay;
         int fl = IPP_FLAG_WIN_NOT_CONVERGED, it;
+        float cache[NC];
+        uint32_t valid = 0;
+        float cax = NAN, cay = NAN;  // anchor of the cached pixels
         for (it = 0; it < J.max_iter; it++) {
             float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-            const int64_t ia = (int64_t)ay, ja = (int64_t)ax;
-            for (int idx = lane; idx < box * box; idx += 32) {
-                int di = idx / box - R, dj = idx % box - R;
-                float dx = (float)dj - ox, dy = (float)di - oy;
-                float d2 = fmaf(dx, dx, dy * dy);
-                int64_t i = ia + di, j = ja + dj;
-                if (d2 < rad2 && i >= 0 && i < J.H && j >= 0 && j < J.W) {
-                    float w = expf(-d2 * inv2s2) * __ldg(J.sub + i * J.pitch + j);
-                    s0 += w;
-                    s1 = fmaf(w, dx, s1);
-                    s2 = fmaf(w, dy, s2);
+            if (NPL > 0) {
+                if (ax != cax || ay != cay) {  // (re)load the box around the anchor
+                    const int64_t ia = (int)ay, ja = (int)ax;
+                    valid = 0;
+#pragma unroll
+                    for (int m = 0; m < NC; m++) {
+                        const int64_t i = ia + dii[m], j = ja + dji[m];
+                        const bool ok = (lane + 32 * m < nbox) && i >= 0 && i < J.H && j >= 0 && j < J.W;
+                        cache[m] = ok ? __ldg(J.sub + i * J.pitch + j) : 0.f;
+                        valid |= (uint32_t)ok << m;
+                    }
+                    cax = ax;
+                    cay = ay;
+                }
+#pragma unroll
+                for (int m = 0; m < NC; m++) {
+                    const float dx = djf[m] - ox, dy = dif[m] - oy;
+                    const float d2 = fmaf(dx, dx, dy * dy);
+                    if (((valid >> m) & 1u) && d2 < rad2) {
+                        const float w = __expf(-d2 * inv2s2) * cache[m];
+                        s0 += w;
+                        s1 = fmaf(w, dx, s1);
+                        s2 = fmaf(w, dy, s2);
+                    }
+                }
+            } else {
+                const int64_t ia = (int)ay, ja = (int)ax;
+                for (int idx = lane; idx < nbox; idx += 32) {
+                    const int di = idx / box - R, dj = idx % box - R;
+                    const float dx = (float)dj - ox, dy = (float)di - oy;
+                    const float d2 = fmaf(dx, dx, dy * dy);
+                    const int64_t i = ia + di, j = ja + dj;
+                    if (d2 < rad2 && i >= 0 && i < J.H && j >= 0 && j < J.W) {
+                        const float w = __expf(-d2 * inv2s2) * __ldg(J.sub + i * J.pitch + j);
+                        s0 += w;
+                        s1 = fmaf(w, dx, s1);
+                        s2 = fmaf(w, dy, s2);
+                    }
                 }
             }
             s0 = warp_sum(s0);
@@ -53,17 +101,16 @@ __global__ void __launch_bounds__(P_THREADS) k_centroid(CenJob J) {
                 it++;
                 break;
             }
-            float ddx = 2.0f * s1 / s0, ddy = 2.0f * s2 / s0;
+            const float ddx = 2.0f * s1 / s0, ddy = 2.0f * s2 / s0;
             ox += ddx;
             oy += ddy;
-            float rx = rintf(ox), ry = rintf(oy);  // re-anchor: |offset| <= 1/2
+            const float rx = rintf(ox), ry = rintf(oy);  // re-anchor: |offset| <= 1/2
             ax += rx; ox -= rx;
             ay += ry; oy -= ry;
             if (ddx * ddx + ddy * ddy < J.tol2) { fl = 0; it++; break; }
         }
         const float xf = ax + ox, yf = ay + oy;
-        if (xf - J.rad < -0.5f || xf + J.rad > (float)J.W - 0.5f || yf - J.rad < -0.5f ||
-            yf + J.rad > (float)J.H - 0.5f)
+        if (xf - J.rad < -0.5f || xf + J.rad > Wf - 0.5f || yf - J.rad < -0.5f || yf + J.rad > Hf - 0.5f)
             fl |= IPP_FLAG_EDGE;
         if (lane == 0) {
             J.x[s] = xf;
@@ -156,15 +203,109 @@ __device__ __forceinline__ bool in_annulus(float dx, float dy, int64_t i, int64_
     return e2 >= rin2d && e2 < rout2d;
 }
 
+// Median (Eq. 1) of the na values buf[0..na) held by one warp's shared buffer,
+// exact.  Both middle order statistics x_k0, x_k1 (k0 = (na-1)/2, k1 = na/2)
+// minimise sum |x - m|, so they lie within one standard deviation of the mean:
+// the search starts from [mean - sd, mean + sd] (checked by counting, else the
+// full range), halves the value interval while both ranks stay on one side, and
+// finishes with a rank count over the at most 32 values left in the interval.
+__device__ float warp_median(const float* buf, int na, float* cand, int lane) {
+    const int k0 = (na - 1) / 2, k1 = na / 2;
+    float s = 0.f, q = 0.f, mn = INFINITY, mx = -INFINITY;
+    for (int t = lane; t < na; t += 32) {
+        const float v = buf[t];
+        s += v;
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+    }
+    s = warp_sum(s);
+    const float mean = s / na;
+    for (int t = lane; t < na; t += 32) { const float d = buf[t] - mean; q = fmaf(d, d, q); }
+    q = warp_sum(q);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const float sd = sqrtf(q / na);
+    auto count_lt = [&](float x) {
+        int c = 0;
+        for (int t = lane; t < na; t += 32) c += buf[t] < x;
+        return __reduce_add_sync(0xffffffffu, c);
+    };
+    auto count_le = [&](float x) {
+        int c = 0;
+        for (int t = lane; t < na; t += 32) c += buf[t] <= x;
+        return __reduce_add_sync(0xffffffffu, c);
+    };
+    // invariant: c_lt = #(v < L) <= k0 and k1 < c_le = #(v <= U)
+    float L = fmaxf(mn, mean - sd * 1.001f - 1e-30f), U = fminf(mx, mean + sd * 1.001f + 1e-30f);
+    int c_lt = count_lt(L), c_le = count_le(U);
+    if (!(c_lt <= k0 && k1 < c_le)) { L = mn; U = mx; c_lt = 0; c_le = na; }
+    for (int step = 0; step < 64 && c_le - c_lt > 32 && L < U; step++) {
+        const float M = 0.5f * (L + U);
+        if (!(M > L && M <= U)) break;
+        const int c_m = count_lt(M);
+        if (k1 < c_m) { U = nextafterf(M, -INFINITY); c_le = c_m; }
+        else if (k0 >= c_m) { L = M; c_lt = c_m; }
+        else {  // x_k0 < M <= x_k1: the two neighbours of M
+            float a = -INFINITY, b = INFINITY;
+            for (int t = lane; t < na; t += 32) {
+                const float v = buf[t];
+                if (v < M) a = fmaxf(a, v); else b = fminf(b, v);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+                b = fminf(b, __shfl_xor_sync(0xffffffffu, b, o));
+            }
+            return (float)(0.5 * ((double)a + (double)b));
+        }
+    }
+    if (!(L < U)) return L;  // all values of the interval are equal
+    if (c_le - c_lt > 32) {  // L and U adjacent floats: only the two values L and U are left
+        const int cl = count_le(L);
+        const float v0 = k0 < cl ? L : U, v1 = k1 < cl ? L : U;
+        return (float)(0.5 * ((double)v0 + (double)v1));
+    }
+    // gather the values of [L, U] (at most 32 when the loop ends normally)
+    int nc = 0;
+    for (int base = 0; base < na; base += 32) {
+        const int t = base + lane;
+        const bool in = t < na && buf[t] >= L && buf[t] <= U;
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        const int pos = nc + __popc(bal & ((1u << lane) - 1u));
+        if (in && pos < 32) cand[pos] = buf[t];
+        nc += __popc(bal);
+    }
+    __syncwarp();
+    nc = min(nc, 32);
+    const float mine = lane < nc ? cand[lane] : INFINITY;
+    int rank = 0;
+    for (int u = 0; u < nc; u++) {
+        const float x = cand[u];
+        rank += (x < mine) || (x == mine && u < lane);
+    }
+    const int r0 = k0 - c_lt, r1 = k1 - c_lt;
+    const unsigned b0 = __ballot_sync(0xffffffffu, lane < nc && rank == r0);
+    const unsigned b1 = __ballot_sync(0xffffffffu, lane < nc && rank == r1);
+    const float v0 = __shfl_sync(0xffffffffu, mine, b0 ? __ffs(b0) - 1 : 0);
+    const float v1 = __shfl_sync(0xffffffffu, mine, b1 ? __ffs(b1) - 1 : 0);
+    __syncwarp();
+    return (float)(0.5 * ((double)v0 + (double)v1));
+}
+
 __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
     __shared__ float ann[P_WARPS][ANN_CAP];
+    __shared__ float cand[P_WARPS][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = (blockIdx.x * P_THREADS + threadIdx.x) >> 5;
     const int nw = (gridDim.x * P_THREADS) >> 5;
     const int n = min(*J.n_src_dev, J.max_src);
     float* buf = ann[wib];
-    const int R1 = (int)ceilf(J.r_ap + 0.5f), box1 = 2 * R1 + 1;
-    const int R2 = (int)ceilf(J.r_out) + 1, box2 = 2 * R2 + 1;
+    const float Wf = (float)(int)J.W, Hf = (float)(int)J.H;
+    const int R1 = (int)ceilf(J.r_ap + 1.0f) - 1, box1 = 2 * R1 + 1;  // pixels reaching within r_ap
+    const int R2 = (int)floorf(J.r_out + 0.5f), box2 = 2 * R2 + 1;  // centres within r_out of any offset <= 1/2
     const double rin2d = __dmul_rn((double)J.r_in, (double)J.r_in);
     const double rout2d = __dmul_rn((double)J.r_out, (double)J.r_out);
     const float rin2 = (float)rin2d, rout2 = (float)rout2d;
@@ -172,39 +313,52 @@ __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
         const float x = J.x[s], y = J.y[s];
         const float ax = rintf(x), ay = rintf(y);
         const float ox = x - ax, oy = y - ay;
-        const int64_t ia = (int64_t)ay, ja = (int64_t)ax;
+        const int64_t ia = (int)ay, ja = (int)ax;
         // aperture sum with exact overlap weights
         float sw = 0.f, swf = 0.f;
-        for (int idx = lane; idx < box1 * box1; idx += 32) {
-            int di = idx / box1 - R1, dj = idx % box1 - R1;
-            int64_t i = ia + di, j = ja + dj;
-            if (i < 0 || i >= J.H || j < 0 || j >= J.W) continue;
-            float w = circle_pixel_area(ox - (float)dj, oy - (float)di, J.r_ap);
-            if (w > 0.f) {
-                sw += w;
-                swf = fmaf(w, __ldg(J.sub + i * J.pitch + j), swf);
+        {
+            int di = lane / box1 - R1, dj = lane % box1 - R1;
+            const int sdi = 32 / box1, sdj = 32 % box1;
+            for (int idx = lane; idx < box1 * box1; idx += 32) {
+                const int64_t i = ia + di, j = ja + dj;
+                if (i >= 0 && i < J.H && j >= 0 && j < J.W) {
+                    const float w = circle_pixel_area(ox - (float)dj, oy - (float)di, J.r_ap);
+                    if (w > 0.f) {
+                        sw += w;
+                        swf = fmaf(w, __ldg(J.sub + i * J.pitch + j), swf);
+                    }
+                }
+                di += sdi;
+                dj += sdj;
+                if (dj > R1) { dj -= box1; di++; }
             }
         }
         sw = warp_sum(sw);
         swf = warp_sum(swf);
         // annulus values into the warp's buffer
         int na = 0;
-        for (int base = 0; base < box2 * box2; base += 32) {
-            int idx = base + lane;
-            bool take = false;
-            float v = 0.f;
-            if (idx < box2 * box2) {
-                int di = idx / box2 - R2, dj = idx % box2 - R2;
-                int64_t i = ia + di, j = ja + dj;
-                if (i >= 0 && i < J.H && j >= 0 && j < J.W &&
-                    in_annulus((float)dj - ox, (float)di - oy, i, j, x, y, rin2, rout2, rin2d, rout2d)) {
-                    take = true;
-                    v = __ldg(J.sub + i * J.pitch + j);
+        {
+            int di = lane / box2 - R2, dj = lane % box2 - R2;
+            const int sdi = 32 / box2, sdj = 32 % box2;
+            for (int base = 0; base < box2 * box2; base += 32) {
+                const int idx = base + lane;
+                bool take = false;
+                float v = 0.f;
+                if (idx < box2 * box2) {
+                    const int64_t i = ia + di, j = ja + dj;
+                    if (i >= 0 && i < J.H && j >= 0 && j < J.W &&
+                        in_annulus((float)dj - ox, (float)di - oy, i, j, x, y, rin2, rout2, rin2d, rout2d)) {
+                        take = true;
+                        v = __ldg(J.sub + i * J.pitch + j);
+                    }
                 }
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                if (take) buf[na + __popc(bal & ((1u << lane) - 1u))] = v;
+                na += __popc(bal);
+                di += sdi;
+                dj += sdj;
+                if (dj > R2) { dj -= box2; di++; }
             }
-            unsigned bal = __ballot_sync(0xffffffffu, take);
-            if (take) buf[na + __popc(bal & ((1u << lane) - 1u))] = v;
-            na += __popc(bal);
         }
         __syncwarp();
         float skyv = 0.f;
@@ -212,32 +366,11 @@ __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
         if (na < J.min_ann) {
             fl |= IPP_FLAG_ANN_FEW;
         } else {
-            // median (Eq. 1) by bisection over order-preserving keys
-            const int k0 = (na - 1) / 2, k1 = na / 2;
-            uint32_t lo = 0u, hi = 0xffffffffu;
-            while (lo < hi) {
-                uint32_t mid = lo + ((hi - lo) >> 1);
-                int c = 0;
-                for (int t = lane; t < na; t += 32) c += fkey(buf[t]) <= mid;
-                c = __reduce_add_sync(0xffffffffu, c);
-                if (c > k0) hi = mid; else lo = mid + 1;
-            }
-            const uint32_t ka = lo;
-            int cle = 0;
-            uint32_t nxt = 0xffffffffu;
-            for (int t = lane; t < na; t += 32) {
-                uint32_t kk = fkey(buf[t]);
-                cle += kk <= ka;
-                if (kk > ka && kk < nxt) nxt = kk;
-            }
-            cle = __reduce_add_sync(0xffffffffu, cle);
-            nxt = __reduce_min_sync(0xffffffffu, nxt);
-            const uint32_t kb = (cle > k1) ? ka : nxt;
-            skyv = (float)(0.5 * ((double)fkey_inv(ka) + (double)fkey_inv(kb)));
+            skyv = warp_median(buf, na, cand[wib], lane);
         }
         __syncwarp();
         const float Rm = fmaxf(J.r_ap, J.r_out);
-        if (x - Rm < -0.5f || x + Rm > (float)J.W - 0.5f || y - Rm < -0.5f || y + Rm > (float)J.H - 0.5f)
+        if (x - Rm < -0.5f || x + Rm > Wf - 0.5f || y - Rm < -0.5f || y + Rm > Hf - 0.5f)
             fl |= IPP_FLAG_EDGE;
         if (lane == 0) {
             J.flux[s] = swf - skyv * sw;
@@ -261,7 +394,11 @@ static int persistent_blocks(cudaStream_t) {
 }
 
 int ipp_launch_centroid(const CenJob& J, cudaStream_t s) {
-    k_centroid<<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
+    const int R = (int)floorf(J.rad + 0.5f);
+    const int nbox = (2 * R + 1) * (2 * R + 1);
+    if (nbox <= 32 * 4) k_centroid<4><<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
+    else if (nbox <= 32 * 8) k_centroid<8><<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
+    else k_centroid<0><<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
     return ipp_check_launch("k_centroid");
 }
 
