@@ -2,16 +2,19 @@
 // per-candidate pre-analysis of Sec. 2.2.5 (peak, total flux, ...).
 //
 // Tiles of TH x TW pixels, one CTA each.  k_tile_label thresholds a tile (or
-// takes a given mask) into shared-memory bit rows, cuts the rows into runs of
+// takes a given mask) into shared-memory bit rows (keeping the tile's values
+// there for the statistics), cuts the rows into runs of
 // detected pixels and unites runs of adjacent rows that touch (8-connectivity)
 // with a union-find whose roots are the earliest run in raster order.
 // Components touching the tile border, or large enough, are kept and get a
 // node with their partial statistics; each run records its node for the final
 // write.  The global phase unites nodes across tile seams, folds the stats into
 // the roots, keeps roots of at least min_area pixels and numbers them by the
-// raster index of their first pixel (per-row counts, an exclusive scan, a rank
-// inside each row).  k_tile_final expands the runs into the label map, writing
+// raster index of their first pixel (survivors bucketed by tile row; a block per
+// tile row ranks its bucket and adds the counts of earlier tile rows).  k_tile_final expands the runs into the label map, writing
 // every pixel once.  Nothing depends on the tile shape but the work split.
+#include <algorithm>
+
 #include "jobs.cuh"
 
 namespace ipp {
@@ -41,8 +44,11 @@ struct CclWs {
     int32_t* label;
     int32_t* btop; int32_t* bbot;    // [ntiles*T_TW]
     int32_t* blef; int32_t* brig;    // [ntiles*T_TH]
-    int32_t* rowcnt; int32_t* rowfill; int32_t* rowbase;  // [H], [H], [H+1]
-    unsigned long long* slist_first; int32_t* slist_node;  // [ntiles*T_CAP]
+    int32_t* counters;   // [0] kept nodes listed (zeroed by the host before the tile pass)
+    int32_t* trcnt;      // [nty] surviving components per tile row (zeroed with counters)
+    int32_t* klist;      // [ntiles*T_CAP] kept node ids, in no particular order
+    unsigned long long* bfirst; int32_t* bnode;  // per tile row: [nty][ntx*T_CAP] survivors
+    int32_t bcap;        // capacity of one tile row's bucket = ntx * T_CAP
 };
 
 struct TileJob {
@@ -66,6 +72,7 @@ struct TileJob {
 struct TileShared {
     float cvb[T_TH][T_NQ];
     float cvr[T_TH][T_NQ];
+    float val[T_TH][T_TW];           // the tile's background-subtracted values
     uint32_t mask[T_TH][T_WPR];
     int32_t roff[T_TH + 1];
     int16_t rs[T_RCAP], re[T_RCAP];  // run start / end column (inclusive)
@@ -176,18 +183,12 @@ __device__ void tile_union(TileShared& S) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(T_THREADS, 4) k_tile_label(TileJob J) {
+__global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileShared& S = *reinterpret_cast<TileShared*>(smem_raw);
     const int tx = blockIdx.x, ty = blockIdx.y, tile = ty * J.ntx + tx;
     const int64_t tx0 = (int64_t)tx * T_TW, ty0 = (int64_t)ty * T_TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    // zero the per-row counters of the numbering (any block may do it)
-    for (int64_t i = (int64_t)tile * T_THREADS + threadIdx.x; i < J.H; i += (int64_t)J.ntx * J.nty * T_THREADS) {
-        J.ws.rowcnt[i] = 0;
-        J.ws.rowfill[i] = 0;
-    }
 
     // ---- phase A: values, threshold, bit rows ------------------------------
     const bool thresh = J.mode != MODE_MASK;
@@ -196,11 +197,13 @@ __global__ void __launch_bounds__(T_THREADS, 4) k_tile_label(TileJob J) {
     float refb = 0.f, refr = 0.f;
     if (thresh) {
         const int qa = (int)floorf(((float)(int)tx0 + 0.5f) / J.mesh_w - 0.5f) - 1;
+        const int qz = (int)floorf(((float)((int)tx0 + T_TW - 1) + 0.5f) / J.mesh_w - 0.5f) + 2;
         qbase = max(qa, 0);
+        const int nq = min(min(qz, J.nx - 1) - qbase + 1, T_NQ);  // node columns this tile reads
         refr = J.mesh_rms[0];
         if (fused) refb = J.mesh_bkg[0];
-        for (int t = threadIdx.x; t < T_TH * T_NQ; t += T_THREADS) {
-            const int r = t / T_NQ, qq = t - r * T_NQ;
+        for (int t = threadIdx.x; t < T_TH * nq; t += T_THREADS) {
+            const int r = t / nq, qq = t - r * nq;
             const int q = min(qbase + qq, J.nx - 1);
             const float vy = ((float)((int)ty0 + r) + 0.5f) / J.mesh_h - 0.5f;
             const float pf = floorf(vy);
@@ -237,48 +240,75 @@ __global__ void __launch_bounds__(T_THREADS, 4) k_tile_label(TileJob J) {
         const bool vin = (J.pitch % 4 == 0) && (((uintptr_t)J.img & 15) == 0) && J.dtype == IPP_F32;
         const bool vsub = (J.sub_pitch % 4 == 0) && (((uintptr_t)J.sub & 15) == 0);
         const bool full4 = xc + 4 <= J.W;
-        for (int r = warp; r < T_TH; r += T_THREADS / 32) {
+        // the warp's rows: all loads first (several in flight per thread), then
+        // the arithmetic; values go to shared memory for the stats phase
+        constexpr int RPW = T_TH / (T_THREADS / 32);  // rows per warp
+        float f[RPW][4];
+        uint32_t mbits[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; q++) {
+            const int r = warp + q * (T_THREADS / 32);
+            const int64_t y = ty0 + r;
+            mbits[q] = 0;
+#pragma unroll
+            for (int c = 0; c < 4; c++) f[q][c] = 0.f;
+            if (y >= J.H || xc >= J.W) continue;
+            if (J.mode == MODE_MASK) {
+                const int64_t mw = (J.W + 31) / 32;
+                const uint32_t word = __ldg(J.mask_in + y * mw + (xc >> 5));
+                mbits[q] = (word >> (xc & 31)) & 0xfu;
+                if (vsub && full4) {
+                    const float4 t4 = __ldg(reinterpret_cast<const float4*>(J.sub + y * J.sub_pitch + xc));
+                    f[q][0] = t4.x; f[q][1] = t4.y; f[q][2] = t4.z; f[q][3] = t4.w;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? __ldg(J.sub + y * J.sub_pitch + xc + c) : 0.f;
+                }
+            } else if (fused) {
+                if (vin && full4) {
+                    const float4 t4 = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(J.img) + y * J.pitch + xc));
+                    f[q][0] = t4.x; f[q][1] = t4.y; f[q][2] = t4.z; f[q][3] = t4.w;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? tile_load_pix(J, y, xc + c) : 0.f;
+                }
+            } else {
+                if (vsub && full4) {
+                    const float4 t4 = __ldg(reinterpret_cast<const float4*>(J.sub + y * J.sub_pitch + xc));
+                    f[q][0] = t4.x; f[q][1] = t4.y; f[q][2] = t4.z; f[q][3] = t4.w;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? __ldg(J.sub + y * J.sub_pitch + xc + c) : 0.f;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; q++) {
+            const int r = warp + q * (T_THREADS / 32);
             const int64_t y = ty0 + r;
             uint32_t nib = 0;
             if (y < J.H && xc < J.W) {
                 if (J.mode == MODE_MASK) {
-                    const int64_t mw = (J.W + 31) / 32;
+                    // pixels beyond W were masked by the caller's padding bits: drop them
 #pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        const int64_t x = xc + c;
-                        if (x < J.W && ((J.mask_in[y * mw + (x >> 5)] >> (x & 31)) & 1u)) nib |= 1u << c;
-                    }
+                    for (int c = 0; c < 4; c++)
+                        if (xc + c < J.W && ((mbits[q] >> c) & 1u)) nib |= 1u << c;
                 } else {
-                    float f[4];
                     if (fused) {
-                        if (vin && full4) {
-                            const float4 t4 = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(J.img) + y * J.pitch + xc));
-                            f[0] = t4.x; f[1] = t4.y; f[2] = t4.z; f[3] = t4.w;
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 4; c++) f[c] = (xc + c < J.W) ? tile_load_pix(J, y, xc + c) : 0.f;
-                        }
 #pragma unroll
                         for (int c = 0; c < 4; c++) {
                             float acc = 0.f;
 #pragma unroll
                             for (int b = 0; b < 4; b++) acc = fmaf(wx[c][b], S.cvb[r][qi[c][b]], acc);
-                            f[c] = f[c] - (refb + acc);
+                            f[q][c] = f[q][c] - (refb + acc);
                         }
                         if (vsub && full4) {
-                            *reinterpret_cast<float4*>(J.sub + y * J.sub_pitch + xc) = make_float4(f[0], f[1], f[2], f[3]);
+                            *reinterpret_cast<float4*>(J.sub + y * J.sub_pitch + xc) =
+                                make_float4(f[q][0], f[q][1], f[q][2], f[q][3]);
                         } else {
 #pragma unroll
                             for (int c = 0; c < 4; c++)
-                                if (xc + c < J.W) J.sub[y * J.sub_pitch + xc + c] = f[c];
-                        }
-                    } else {
-                        if (vsub && full4) {
-                            const float4 t4 = __ldg(reinterpret_cast<const float4*>(J.sub + y * J.sub_pitch + xc));
-                            f[0] = t4.x; f[1] = t4.y; f[2] = t4.z; f[3] = t4.w;
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 4; c++) f[c] = (xc + c < J.W) ? __ldg(J.sub + y * J.sub_pitch + xc + c) : 0.f;
+                                if (xc + c < J.W) J.sub[y * J.sub_pitch + xc + c] = f[q][c];
                         }
                     }
 #pragma unroll
@@ -287,10 +317,11 @@ __global__ void __launch_bounds__(T_THREADS, 4) k_tile_label(TileJob J) {
 #pragma unroll
                         for (int b = 0; b < 4; b++) acc = fmaf(wx[c][b], S.cvr[r][qi[c][b]], acc);
                         const float thr = fmaxf(J.k * (refr + acc), J.thresh_abs);
-                        if (xc + c < J.W && f[c] > thr) nib |= 1u << c;
+                        if (xc + c < J.W && f[q][c] > thr) nib |= 1u << c;
                     }
                 }
             }
+            *reinterpret_cast<float4*>(&S.val[r][lane * 4]) = make_float4(f[q][0], f[q][1], f[q][2], f[q][3]);
             // 8 lanes x 4 bits -> one 32-bit word
             uint32_t wv = nib << (4 * (lane & 7));
             wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
@@ -367,10 +398,9 @@ __global__ void __launch_bounds__(T_THREADS, 4) k_tile_label(TileJob J) {
         if (kid < 0) continue;
         const int r = row_of_run(S, i);
         const int st = S.rs[i], en = S.re[i];
-        const float* row = J.sub + (ty0 + r) * J.sub_pitch + tx0;
         float s0 = 0.f, s1 = 0.f, pk = -INFINITY;
         for (int c = st; c <= en; c++) {
-            const float f = __ldcg(row + c);
+            const float f = S.val[r][c];
             s0 += f;
             s1 = fmaf(f, (float)c, s1);
             pk = fmaxf(pk, f);
@@ -426,7 +456,10 @@ __global__ void __launch_bounds__(T_THREADS, 4) k_tile_label(TileJob J) {
     if (threadIdx.x == 0) {
         J.ws.nkept[tile] = nk;
         J.ws.nruns[tile] = nr;
+        S.nkept = nk > 0 ? atomicAdd(&J.ws.counters[0], nk) : 0;  // base of this tile in klist
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += T_THREADS) J.ws.klist[S.nkept + k] = tile * T_CAP + k;
     // border pixels: node of the run covering them (runs of a row are sorted)
     for (int t = threadIdx.x; t < 2 * T_TW + 2 * T_TH; t += T_THREADS) {
         int r, c;
@@ -495,12 +528,11 @@ __global__ void k_ccl_union(CclWs ws, int ntx, int nty) {
     }
 }
 
-// fold every kept node into its root
+// fold every kept node into its root (grid-stride over the kept-node list)
 __global__ void k_ccl_resolve(CclWs ws) {
-    const int tile = blockIdx.x;
-    const int nc = ws.nkept[tile];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const int node = tile * T_CAP + c;
+    const int n = __ldcg(ws.counters);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int node = ws.klist[t];
         const int r = gfind(ws.parent, node);
         if (r == node) continue;
         ws.parent[node] = r;
@@ -517,84 +549,48 @@ __global__ void k_ccl_resolve(CclWs ws) {
     }
 }
 
-__global__ void k_ccl_count(CclWs ws, int64_t W, int min_area) {
-    const int tile = blockIdx.x;
-    const int nc = ws.nkept[tile];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const int node = tile * T_CAP + c;
+// roots of at least min_area pixels go to the bucket of the tile row holding
+// their first pixel; the others get label 0
+__global__ void k_ccl_survive(CclWs ws, int64_t W, int min_area) {
+    const int n = __ldcg(ws.counters);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int node = ws.klist[t];
         if (ws.parent[node] != node) continue;
-        if (ws.area[node] >= min_area) atomicAdd(&ws.rowcnt[ws.first[node] / W], 1);
-        else ws.label[node] = 0;
+        if (ws.area[node] < min_area) { ws.label[node] = 0; continue; }
+        const unsigned long long f = ws.first[node];
+        const int tr = (int)((int64_t)(f / (unsigned long long)W) / T_TH);
+        const int slot = atomicAdd(&ws.trcnt[tr], 1);
+        ws.bfirst[(int64_t)tr * ws.bcap + slot] = f;
+        ws.bnode[(int64_t)tr * ws.bcap + slot] = node;
     }
 }
 
-constexpr int SCAN_THREADS = 1024;
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_rows(CclWs ws, int64_t H, int32_t* n_src_dev) {
-    __shared__ int wsum[SCAN_THREADS / 32];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
+// One block per tile row: label = (survivors of earlier tile rows) + (position
+// of the first pixel in this tile row's sorted bucket) + 1, i.e. raster order of
+// first pixels.  The bucket is sorted in shared memory by a bitonic network on
+// (first pixel, node) pairs; buckets beyond NB_SMEM entries fall back to ranking
+// by counting over global memory (only for pathological masks).
+constexpr int NB_THREADS = 512, NB_SMEM = 8192;
+constexpr size_t NB_DYN_SMEM = (size_t)NB_SMEM * (sizeof(unsigned long long) + sizeof(int));
+__global__ void __launch_bounds__(NB_THREADS) k_ccl_number(CclWs ws, int nty, int32_t max_src,
+                                                           ipp_src_stats out, int32_t* n_src_dev) {
+    extern __shared__ __align__(16) unsigned char nb_smem[];
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(nb_smem);
+    int* sn = reinterpret_cast<int*>(nb_smem + (size_t)NB_SMEM * sizeof(unsigned long long));
+    __shared__ int red[NB_THREADS / 32];
+    const int tr = blockIdx.x;
+    int base = 0;
+    for (int t = threadIdx.x; t < tr; t += NB_THREADS) base += __ldcg(ws.trcnt + t);
+    base = __reduce_add_sync(0xffffffffu, base);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = base;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t base = 0; base < H; base += SCAN_THREADS) {
-        int64_t i = base + threadIdx.x;
-        int v = i < H ? ws.rowcnt[i] : 0;
-        int inc = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
-        }
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            int s = wsum[lane];
-            int si = s;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int t = __shfl_up_sync(0xffffffffu, si, o);
-                if (lane >= o) si += t;
-            }
-            wsum[lane] = si - s;
-        }
-        __syncthreads();
-        int excl = carry + wsum[warp] + inc - v;
-        if (i < H) ws.rowbase[i] = excl;
-        __syncthreads();
-        if (threadIdx.x == SCAN_THREADS - 1) carry = excl + v;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        ws.rowbase[H] = carry;
-        *n_src_dev = carry;
-    }
-}
-
-__global__ void k_ccl_place(CclWs ws, int64_t W, int min_area) {
-    const int tile = blockIdx.x;
-    const int nc = ws.nkept[tile];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const int node = tile * T_CAP + c;
-        if (ws.parent[node] != node || ws.area[node] < min_area) continue;
-        const unsigned long long f = ws.first[node];
-        const int64_t row = (int64_t)(f / (unsigned long long)W);
-        const int slot = ws.rowbase[row] + atomicAdd(&ws.rowfill[row], 1);
-        ws.slist_first[slot] = f;
-        ws.slist_node[slot] = node;
-    }
-}
-
-__global__ void k_ccl_number(CclWs ws, int64_t W, int min_area, int32_t max_src, ipp_src_stats out) {
-    const int tile = blockIdx.x;
-    const int nc = ws.nkept[tile];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const int node = tile * T_CAP + c;
-        if (ws.parent[node] != node || ws.area[node] < min_area) continue;
-        const unsigned long long f = ws.first[node];
-        const int64_t row = (int64_t)(f / (unsigned long long)W);
-        const int s0 = ws.rowbase[row], s1 = ws.rowbase[row] + ws.rowcnt[row];
-        int rank = 0;
-        for (int s = s0; s < s1; s++) rank += ws.slist_first[s] < f;
-        const int lab = s0 + rank + 1;
+    base = 0;
+    for (int w = 0; w < NB_THREADS / 32; w++) base += red[w];
+    const int n = __ldcg(ws.trcnt + tr);
+    if (tr == nty - 1 && threadIdx.x == 0) *n_src_dev = base + n;
+    const unsigned long long* bf = ws.bfirst + (int64_t)tr * ws.bcap;
+    const int32_t* bn = ws.bnode + (int64_t)tr * ws.bcap;
+    auto emit = [&](int node, unsigned long long f, int lab) {
         ws.label[node] = lab;
         if (lab <= max_src) {
             const int k = lab - 1;
@@ -609,6 +605,39 @@ __global__ void k_ccl_number(CclWs ws, int64_t W, int min_area, int32_t max_src,
             out.flux[k] = (float)sm;
             out.xbar[k] = (float)(ws.sx[node] / sm);
             out.ybar[k] = (float)(ws.sy[node] / sm);
+        }
+    };
+    if (n <= NB_SMEM) {
+        int np = 1;
+        while (np < n) np <<= 1;
+        for (int i = threadIdx.x; i < np; i += NB_THREADS) {
+            sk[i] = i < n ? __ldcg(bf + i) : ~0ull;
+            sn[i] = i < n ? __ldcg(bn + i) : -1;
+        }
+        __syncthreads();
+        for (int k = 2; k <= np; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < np; i += NB_THREADS) {
+                    const int p = i ^ j;
+                    if (p > i) {
+                        const bool asc = (i & k) == 0;
+                        const unsigned long long a = sk[i], b = sk[p];
+                        if ((a > b) == asc) {
+                            sk[i] = b; sk[p] = a;
+                            const int t = sn[i]; sn[i] = sn[p]; sn[p] = t;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < n; i += NB_THREADS) emit(sn[i], sk[i], base + i + 1);
+    } else {
+        for (int i = threadIdx.x; i < n; i += NB_THREADS) {
+            const unsigned long long f = __ldcg(bf + i);
+            int rank = 0;
+            for (int j = 0; j < n; j++) rank += __ldcg(bf + j) < f;
+            emit(__ldcg(bn + i), f, base + rank + 1);
         }
     }
 }
@@ -683,11 +712,12 @@ static CclLayout ccl_layout(int64_t W, int64_t H) {
         (size_t)L.nodes * 4,                                   // label
         (size_t)L.ntiles * T_TW * 4, (size_t)L.ntiles * T_TW * 4,  // btop bbot
         (size_t)L.ntiles * T_TH * 4, (size_t)L.ntiles * T_TH * 4,  // blef brig
-        (size_t)H * 4, (size_t)H * 4, (size_t)(H + 1) * 4,     // rowcnt rowfill rowbase
-        (size_t)L.nodes * 8, (size_t)L.nodes * 4,              // slist
+        (size_t)(L.nty + 8) * 4,                               // counters + trcnt
+        (size_t)L.nodes * 4,                                   // klist
+        (size_t)L.nodes * 8, (size_t)L.nodes * 4,              // bucket first / node
     };
     size_t o = 0;
-    for (int k = 0; k < 25; k++) { L.off[k] = o; o += align256(sizes[k]); }
+    for (int k = 0; k < 24; k++) { L.off[k] = o; o += align256(sizes[k]); }
     L.total = o;
     return L;
 }
@@ -715,11 +745,12 @@ static CclWs ccl_ws(const CclLayout& L, void* ws) {
     w.bbot = (int32_t*)(b + L.off[17]);
     w.blef = (int32_t*)(b + L.off[18]);
     w.brig = (int32_t*)(b + L.off[19]);
-    w.rowcnt = (int32_t*)(b + L.off[20]);
-    w.rowfill = (int32_t*)(b + L.off[21]);
-    w.rowbase = (int32_t*)(b + L.off[22]);
-    w.slist_first = (unsigned long long*)(b + L.off[23]);
-    w.slist_node = (int32_t*)(b + L.off[24]);
+    w.counters = (int32_t*)(b + L.off[20]);
+    w.trcnt = w.counters + 8;
+    w.klist = (int32_t*)(b + L.off[21]);
+    w.bfirst = (unsigned long long*)(b + L.off[22]);
+    w.bnode = (int32_t*)(b + L.off[23]);
+    w.bcap = L.ntx * T_CAP;
     return w;
 }
 
@@ -741,20 +772,22 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
     const size_t sm = sizeof(TileShared);
     cudaFuncSetAttribute(k_tile_label, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 tg(L.ntx, L.nty);
+    // the kept-node counter and the per-tile-row counts start at zero
+    if (cudaMemsetAsync(w.counters, 0, (size_t)(L.nty + 8) * 4, s) != cudaSuccess) return ipp_check_launch("memset");
     k_tile_label<<<tg, T_THREADS, sm, s>>>(J);
     if (int e = ipp_check_launch("k_tile_label")) return e;
     k_ccl_union<<<tg, 128, 0, s>>>(w, L.ntx, L.nty);
     if (int e = ipp_check_launch("k_ccl_union")) return e;
-    const unsigned nt = (unsigned)L.ntiles;
-    k_ccl_resolve<<<nt, 128, 0, s>>>(w);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned pg = (unsigned)std::max(sms, 1) * 8;  // persistent grid over the kept nodes
+    k_ccl_resolve<<<pg, 256, 0, s>>>(w);
     if (int e = ipp_check_launch("k_ccl_resolve")) return e;
-    k_ccl_count<<<nt, 128, 0, s>>>(w, A.W, A.min_area);
-    if (int e = ipp_check_launch("k_ccl_count")) return e;
-    k_scan_rows<<<1, SCAN_THREADS, 0, s>>>(w, A.H, A.n_src_dev);
-    if (int e = ipp_check_launch("k_scan_rows")) return e;
-    k_ccl_place<<<nt, 128, 0, s>>>(w, A.W, A.min_area);
-    if (int e = ipp_check_launch("k_ccl_place")) return e;
-    k_ccl_number<<<nt, 128, 0, s>>>(w, A.W, A.min_area, A.max_src, A.stats);
+    k_ccl_survive<<<pg, 256, 0, s>>>(w, A.W, A.min_area);
+    if (int e = ipp_check_launch("k_ccl_survive")) return e;
+    cudaFuncSetAttribute(k_ccl_number, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NB_DYN_SMEM);
+    k_ccl_number<<<L.nty, NB_THREADS, NB_DYN_SMEM, s>>>(w, L.nty, A.max_src, A.stats, A.n_src_dev);
     if (int e = ipp_check_launch("k_ccl_number")) return e;
     k_tile_final<<<tg, T_THREADS, 0, s>>>(w, A.W, A.H, L.ntx, A.labels);
     return ipp_check_launch("k_tile_final");
