@@ -15,6 +15,7 @@
  *   ipp_centroid      windowed centroid of each candidate     (positions, Sec. 2.2.5)
  *   ipp_aperture_phot circular aperture photometry with a local sky annulus
  *                                                             (Sec. 2.2.5)
+ *   ipp_stamp_cut     S x S stamps at the measured positions (input of the fit)
  *   ipp_psf_fit       batched Levenberg-Marquardt PSF fit of stamps
  *   ipp_extract       all catalog steps of one frame, fused where the data allow
  *
@@ -269,6 +270,28 @@ int ipp_aperture_phot(const float* sub, int64_t W, int64_t H, int64_t pitch,
                       const int32_t* n_src_dev, int32_t max_src, const float* x, const float* y,
                       const ipp_phot_params* p, float* flux, float* sky, float* area,
                       int32_t* n_ann, int32_t* flags, void* stream);
+
+/*
+ * ipp_stamp_cut -- S x S stamps of the subtracted frame around each source, the
+ * input of the PSF fit (the paper fits no PSF; this cut is part of that
+ * paper-silent reading of Sec. 2.2.5's photometry).  For source s < min(*n_src_dev,
+ * max_src) the stamp origin is ox = floor(x[s] + 1/2) - S/2, oy = floor(y[s] + 1/2)
+ * - S/2 (round half up, S odd, integer division), and stamp pixel (r, c) is frame
+ * pixel (row oy + r, column ox + c).  Stamp pixels outside the frame are 0 with
+ * weight 0 and the source gets IPP_FLAG_EDGE; inside pixels have weight 1.  A
+ * position that is not finite or lies more than 2^30 px outside the frame gives a
+ * stamp of zeros with weight 0, origin (0, 0) and IPP_FLAG_EDGE.
+ *   S        odd, 3 <= S <= 63
+ *   stamps   device float[max_src * S * S], source-major, rows of S (only the first
+ *            n stamps are written)
+ *   weights  nullable device float[max_src * S * S]
+ *   origin   nullable device int32[max_src * 2]: (ox, oy) per source
+ *   flags    nullable device int32[max_src]: written (0 or IPP_FLAG_EDGE), not or-ed
+ */
+int ipp_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch,
+                  const int32_t* n_src_dev, int32_t max_src, const float* x, const float* y,
+                  int32_t S, float* stamps, float* weights, int32_t* origin, int32_t* flags,
+                  void* stream);
 
 /* ------------------------------------------------------------- fused frame */
 /*

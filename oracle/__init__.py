@@ -82,6 +82,7 @@ def lib():
             L.orc_overlap.argtypes = [d] * 7
             L.orc_overlap.restype = d
             L.orc_aperture.argtypes = [vp, i64, i64, i64, vp, vp, d, d, d, i32, vp, vp, vp, vp, vp]
+            L.orc_stamp_cut.argtypes = [vp, i64, i64, i64, vp, vp, i32, vp, vp, vp, vp]
             L.orc_psf_model.argtypes = [vp, i32, i32, d, vp, vp]
             L.orc_psf_fit.argtypes = [vp, i64, i32, vp, vp, i32, d, i32, d, vp, vp, vp, vp]
             L.orc_psf_init.argtypes = [vp, i32, vp]
@@ -230,6 +231,20 @@ def aperture(sub, x, y, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann=10):
     lib().orc_aperture(_p(sub), W, H, n, _p(x), _p(y), float(r_ap), float(r_in), float(r_out),
                        int(min_ann), _p(out["flux"]), _p(out["sky"]), _p(out["area"]),
                        _p(out["n_ann"]), _p(out["flags"]))
+    return out
+
+
+def stamp_cut(sub, x, y, S=15):
+    sub = _f32(sub)
+    H, W = sub.shape
+    x, y = _f32(x), _f32(y)
+    n = len(x)
+    out = dict(stamps=np.zeros((n, S, S), np.float32), weights=np.zeros((n, S, S), np.float32),
+               origin=np.zeros((n, 2), np.int32), flags=np.zeros(n, np.int32))
+    rc = lib().orc_stamp_cut(_p(sub), W, H, n, _p(x), _p(y), int(S), _p(out["stamps"]), _p(out["weights"]),
+                             _p(out["origin"]), _p(out["flags"]))
+    if rc:
+        raise ValueError(f"orc_stamp_cut: status {rc}")
     return out
 
 

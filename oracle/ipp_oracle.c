@@ -498,6 +498,42 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
     return ORC_OK;
 }
 
+/* ----------------------------------------------------------- stamps ---- */
+/* The stamp of a source is the S x S block of the subtracted frame centred on
+ * the pixel nearest to its position, ties rounded up: centre column
+ * floor(x + 1/2), computed in FP64 where x + 1/2 is exact for every float x.
+ * Pixels beyond the frame are 0 and get weight 0; a stamp that needs any of
+ * them is flagged EDGE.  A non-finite position, or one more than 2^30 px
+ * outside the frame, gives an all-zero stamp at origin (0, 0), flagged EDGE. */
+int orc_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t n,
+                  const float* x, const float* y, int32_t S, float* stamps,
+                  float* weights, int32_t* origin, int32_t* flags) {
+    if (!sub || W <= 0 || H <= 0 || n < 0 || S < 3 || S % 2 == 0) return ORC_INVALID_ARG;
+    int64_t half = S / 2;
+    double lim = 1073741824.0 + (double)(W > H ? W : H);
+    for (int64_t s = 0; s < n; s++) {
+        double xs = x[s], ys = y[s];
+        int ok = isfinite(xs) && isfinite(ys) && fabs(xs) < lim && fabs(ys) < lim;
+        int64_t ox = 0, oy = 0;
+        if (ok) {
+            ox = (int64_t)floor(xs + 0.5) - half;
+            oy = (int64_t)floor(ys + 0.5) - half;
+        }
+        int edge = !ok;
+        for (int64_t r = 0; r < S; r++)
+            for (int64_t c = 0; c < S; c++) {
+                int64_t fy = oy + r, fx = ox + c, k = (s * S + r) * S + c;
+                int in = ok && fy >= 0 && fy < H && fx >= 0 && fx < W;
+                if (!in) edge = 1;
+                stamps[k] = in ? sub[fy * W + fx] : 0.0f;
+                if (weights) weights[k] = in ? 1.0f : 0.0f;
+            }
+        if (origin) { origin[2 * s] = (int32_t)ox; origin[2 * s + 1] = (int32_t)oy; }
+        if (flags) flags[s] = edge ? ORC_FLAG_EDGE : 0;
+    }
+    return ORC_OK;
+}
+
 /* --------------------------------------------------------------- c12 ---- */
 /*
  * PSF model (paper-silent), point-sampled at the pixel centres of an S x S

@@ -90,6 +90,12 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
                  double r_out, int32_t min_ann, double* flux, double* sky,
                  double* area, int32_t* n_ann, int32_t* flags);
 
+/* Stamp cut (paper-silent; input of the PSF fit): S x S stamp whose centre pixel
+ * is (floor(x + 1/2), floor(y + 1/2)); out-of-frame pixels 0 with weight 0. */
+int orc_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t n,
+                  const float* x, const float* y, int32_t S, float* stamps,
+                  float* weights, int32_t* origin, int32_t* flags);
+
 /* PSF model (paper-silent reading): params = x0, y0, F, sky, sx, sy, theta */
 #define ORC_PSF_MOFFAT 0
 #define ORC_PSF_GAUSS 1

@@ -21,7 +21,7 @@ from ._abi import (  # noqa: F401
     FLAG_FIT_MAXITER, FLAG_FIT_SINGULAR, FLAG_WIN_NOT_CONVERGED, IppError, PSF_GAUSS, PSF_MOFFAT,
 )
 
-__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot",
+__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "stamp_cut",
            "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
 
 
@@ -207,6 +207,27 @@ def aperture_phot(sub, x, y, n_src=None, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann
         _ptr(sub), W, H, sub.stride(0), _ptr(n_src), n, _ptr(x.contiguous()), _ptr(y.contiguous()),
         _abi.PhotParams(r_ap, r_in, r_out, min_ann), _ptr(out["flux"]), _ptr(out["sky"]), _ptr(out["area"]),
         _ptr(out["n_ann"]), _ptr(out["flags"]), _stream()))
+    return {k: v[:n] for k, v in out.items()}
+
+
+def stamp_cut(sub, x, y, n_src=None, S=15, max_src=None):
+    """S x S stamps around the positions, weights (0 off the frame), origins and
+    EDGE flags (ipp_stamp_cut): the input of psf_fit."""
+    L = load()
+    _need_cuda(sub, "sub", torch.float32)
+    H, W = sub.shape
+    n = x.numel() if max_src is None else max_src
+    if n_src is None:
+        n_src = torch.tensor([x.numel()], dtype=torch.int32, device=sub.device)
+    dev = sub.device
+    m = max(n, 1)
+    out = dict(stamps=torch.empty((m, S, S), dtype=torch.float32, device=dev))
+    out["weights"] = torch.empty_like(out["stamps"])
+    out["origin"] = torch.empty((m, 2), dtype=torch.int32, device=dev)
+    out["flags"] = torch.empty(m, dtype=torch.int32, device=dev)
+    _abi.check("ipp_stamp_cut", L.ipp_stamp_cut(
+        _ptr(sub), W, H, sub.stride(0), _ptr(n_src), n, _ptr(x.contiguous()), _ptr(y.contiguous()), S,
+        _ptr(out["stamps"]), _ptr(out["weights"]), _ptr(out["origin"]), _ptr(out["flags"]), _stream()))
     return {k: v[:n] for k, v in out.items()}
 
 

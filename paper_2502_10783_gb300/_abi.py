@@ -76,6 +76,7 @@ PROTOTYPES = {
     "ipp_centroid": ([vp, i64, i64, i64, vp, i32, vp, vp, C.POINTER(CenParams), vp, vp, vp, vp, vp], i32),
     "ipp_aperture_phot": ([vp, i64, i64, i64, vp, i32, vp, vp, C.POINTER(PhotParams), vp, vp, vp, vp, vp, vp],
                           i32),
+    "ipp_stamp_cut": ([vp, i64, i64, i64, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp], i32),
     "ipp_extract_workspace_size": ([i64, i64, C.POINTER(BgParams)], sz),
     "ipp_extract": ([vp, i32, i64, i64, i64, C.POINTER(Calib), C.POINTER(BgParams), C.POINTER(DetParams),
                      C.POINTER(CenParams), C.POINTER(PhotParams), i32, C.POINTER(CatalogOut), vp, sz, vp], i32),

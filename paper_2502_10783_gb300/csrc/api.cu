@@ -225,6 +225,17 @@ extern "C" int ipp_aperture_phot(const float* sub, int64_t W, int64_t H, int64_t
     return ipp_launch_aperture(J, (cudaStream_t)stream);
 }
 
+extern "C" int ipp_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, const int32_t* n_src_dev,
+                             int32_t max_src, const float* x, const float* y, int32_t S, float* stamps,
+                             float* weights, int32_t* origin, int32_t* flags, void* stream) {
+    if (int e = check_frame(sub, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(S >= 3 && S <= 63 && (S & 1), "stamp size S must be odd, 3..63");
+    REQUIRE(n_src_dev && x && y && stamps, "NULL pointer");
+    REQUIRE(max_src >= 0, "max_src < 0");
+    return ipp_launch_stamp_cut(sub, W, H, pitch, n_src_dev, max_src, x, y, S, stamps, weights, origin, flags,
+                                (cudaStream_t)stream);
+}
+
 // ---- fused frame ---------------------------------------------------------------------
 extern "C" size_t ipp_extract_workspace_size(int64_t W, int64_t H, const ipp_bg_params* bp) {
     if (!bp) return 0;

@@ -1,46 +1,61 @@
 // bg.cu -- mesh background (Sec. 2.2.2, Eqs. 1-4): per-mesh iterative sigma
 // clip, invalid-mesh fill and mesh median filter, interpolation + subtraction.
 //
-// k_mesh_stats: one CTA (512 threads) per mesh.  The mesh is read once from HBM
-// into registers.  A histogram over a window around the mean (refined around
-// the median when outliers made it coarse) turns the mesh into a bin-sorted copy
-// in shared memory.  The sums of the whole set are taken once, exactly: values
-// inside the window as int64 fixed point (a power-of-two scale no coarser than
-// their own spacing), the few outside it in double-float.  Every clip pass then only
-// touches the values it removes (the tails, bin by bin) and the bins holding
-// the median order statistics, so a pass costs O(removed + median bin), not
-// O(mesh), and the bounds agree with an FP64 evaluation to ~1e-13.  Scalar FP64
-// work (moments, bounds) runs on one thread: the FP64 pipe is narrow.
+// k_mesh_stats: one 128-thread CTA per mesh with ~31 KB of shared memory, so
+// seven meshes run on each SM and a 4096^2 frame of 128 px meshes is a single
+// wave.  The mesh is not held on chip.  Warp 0 first sorts a 256-value sample
+// to place a histogram window (bins of ~1/64-1/128 robust sigma, outliers in
+// two end bins).  Read 1 (HBM, float4) builds the histogram and the exact sums
+// of the whole set relative to the window centre -- in-window values as int64
+// fixed point (a power-of-two scale no coarser than their own spacing), the
+// few outside the window in double-float.  A window that missed or is too
+// coarse is re-placed with one more read.  The last read (L2) keeps, bin-sorted
+// in shared memory, only the values a clip pass can touch: the tails beyond ~2
+// robust sigma, where the bounds fall, and a band of bins around the median
+// (sorted in parallel before the passes start).  A pass then touches only the
+// values it removes and the median bins, so it costs O(removed + median bin),
+// and its statistics are formed in double-float on one lane (the FP64 pipe of
+// this GPU is narrow).  A pass that needs a bin that was not stored (bounds
+// inside the core, a median outside the band) reads the mesh again for that
+// pass: same result, more traffic.
 #include <math.h>
 
 #include "jobs.cuh"
 
 namespace ipp {
 
-constexpr int MS_THREADS = 512;
+constexpr int MS_THREADS = 128;
 constexpr int MS_WARPS = MS_THREADS / kWarp;
 constexpr int MS_NB = 1024;          // window bins 1..MS_NB; 0 = below, MS_NB+1 = above
 constexpr int MS_NBT = MS_NB + 2;
 constexpr int MS_SCALE_BITS = 14;    // fixed point: d_int = (v - c*) * 2^(14 - e), bw = 2^e
+constexpr int MS_STORE = 2880;       // stored values: tails + median band
+constexpr int MS_GCAP = 512;         // gathered values of unstored median bins
+constexpr int MS_BAND = 8;           // median band half-width in bins (at most)
+constexpr int MS_CHUNK = 8;          // loads in flight per thread
+constexpr int MS_WARPSORT_MAX = 256;
+
+// slots of MeshShared::bc_i
+enum { BI_STATE = 0, BI_MODE, BI_KBL, BI_KBH, BI_GL, BI_GH, BI_GCNT, BI_NEED, BI_RB0, BI_RR0, BI_RB1, BI_RR1,
+       BI_DIGIT, BI_REM, BI_N0, BI_REFINE, BI_E, BI_CL, BI_ML, BI_MH, BI_CH, BI_SBAD, BI_COUNT };
+enum { ST_STOP = 0, ST_SCAN = 1, ST_GATHER = 2, ST_RADIX = 3 };
 
 struct MeshShared {
-    uint32_t hcnt[MS_NBT];
-    uint32_t hstart[MS_NBT + 1];
-    uint32_t hfill[MS_NBT];   // scatter cursors; reused as radix-select histogram
-    uint32_t radix[2048];
-    uint32_t sorted_bits[(MS_NBT + 31) / 32];  // bins whose slice is already sorted
+    uint32_t hbuf[2 * MS_NBT];      // counts | scatter cursors; radix histogram after the scatter
+    uint32_t hstart[MS_NBT + 1];    // exclusive prefix of the counts
+    uint32_t sstart[MS_NBT + 1];    // exclusive prefix of the stored counts
+    uint32_t sorted_bits[(MS_NBT + 31) / 32];  // stored bins whose slice is already sorted
+    float store[MS_STORE];
+    float gbuf[MS_GCAP];
     long long redl[MS_WARPS * 2];
     float4 redo[MS_WARPS];
     int redi[MS_WARPS * 3];
     float redf[MS_WARPS * 3];
-    double bc_d[8];
-    long long bc_l[4];
     long long ks_i[2];   // running sums of the kept set (clip loop, warp 0 lane 0)
-    double ks_o[2];
-    double st[3];        // median, mean, sigma of the kept set
-    int bc_i[8];
-    float bc_f[4];
-    uint32_t bc_u[2];
+    df ks_o[2];
+    df st[3];            // median, mean, sigma of the kept set
+    float bc_f[8];
+    int bc_i[BI_COUNT];
 };
 
 // Bin of a value: monotone in v (FP subtraction and the power-of-two scaling
@@ -49,6 +64,92 @@ __device__ __forceinline__ int bin_of(float v, float cstar, float inv_bw) {
     float t = floorf((v - cstar) * inv_bw);
     t = fmaxf(fminf(t, (float)(MS_NB / 2)), (float)(-MS_NB / 2 - 1));
     return (int)t + MS_NB / 2 + 1;
+}
+
+// Where a mesh lives and how its values are formed (calibrated when raw u16).
+struct MeshGeom {
+    const void* img;
+    int dtype;
+    int64_t pitch, W;
+    const uint8_t* mask;
+    const float* bias_map;
+    float bias;
+    const float* inv_flat;
+    int64_t x0, y0;
+    int mw, we, he, slots;
+    bool vec;  // f32, unmasked, 16-byte aligned rows, we % 4 == 0: float4 reads
+};
+
+// Value of mesh pixel (r, c) (inside the mesh's frame region); false when the
+// pixel is masked or not finite.
+__device__ __forceinline__ bool mesh_value_at(const MeshGeom& G, int r, int c, float* out) {
+    const int64_t yy = G.y0 + r, xx = G.x0 + c;
+    float x;
+    if (G.dtype == IPP_F32) {
+        x = __ldg(reinterpret_cast<const float*>(G.img) + yy * G.pitch + xx);
+    } else {
+        const float raw = (float)__ldg(reinterpret_cast<const uint16_t*>(G.img) + yy * G.pitch + xx);
+        const float b = G.bias_map ? __ldg(G.bias_map + yy * G.W + xx) : G.bias;
+        x = (raw - b) * __ldg(G.inv_flat + yy * G.W + xx);
+    }
+    *out = x;
+    return !(G.mask && G.mask[yy * G.W + xx]) && isfinite(x);
+}
+
+// Calls f(v) for every usable value of the mesh that this thread owns.  Vector
+// path: float4 quads of the mesh's frame region, quad e4 = threadIdx.x + k *
+// MS_THREADS; scalar path: element e = threadIdx.x + k * MS_THREADS of the
+// mw x mh slots (row e / mw, column e % mw).  A chunk of loads is issued before
+// any is used: addresses are clamped into the mesh and slots beyond it are
+// skipped afterwards.  Every call forms the values with the same arithmetic, so
+// re-reads see identical values.
+template <class F>
+__device__ __forceinline__ void mesh_for_each(const MeshGeom& G, F&& f) {
+    if (G.vec) {
+        constexpr int VCH = 4;
+        const int qpr = G.we >> 2, nq = G.he * qpr;
+        const float4* base = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(G.img) + G.y0 * G.pitch +
+                                                             G.x0);
+        const int64_t p4 = G.pitch >> 2;
+        const int dr = MS_THREADS / qpr, dc = MS_THREADS - dr * qpr;
+        int r = threadIdx.x / qpr, c = threadIdx.x - r * qpr;
+        for (int e0 = threadIdx.x; e0 < nq; e0 += VCH * MS_THREADS) {
+            float4 q[VCH];
+#pragma unroll
+            for (int j = 0; j < VCH; j++) {
+                q[j] = __ldg(base + (int64_t)min(r, G.he - 1) * p4 + c);
+                r += dr;
+                c += dc;
+                if (c >= qpr) { c -= qpr; r++; }
+            }
+#pragma unroll
+            for (int j = 0; j < VCH; j++) {
+                if (e0 + j * MS_THREADS >= nq) continue;
+                if (isfinite(q[j].x)) f(q[j].x);
+                if (isfinite(q[j].y)) f(q[j].y);
+                if (isfinite(q[j].z)) f(q[j].z);
+                if (isfinite(q[j].w)) f(q[j].w);
+            }
+        }
+        return;
+    }
+    const int dr = MS_THREADS / G.mw, dc = MS_THREADS - dr * G.mw;
+    int r = threadIdx.x / G.mw, c = threadIdx.x - r * G.mw;
+    for (int e0 = threadIdx.x; e0 < G.slots; e0 += MS_CHUNK * MS_THREADS) {
+        float v[MS_CHUNK];
+        bool ok[MS_CHUNK];
+#pragma unroll
+        for (int j = 0; j < MS_CHUNK; j++) {
+            const bool in = e0 + j * MS_THREADS < G.slots && r < G.he && c < G.we;
+            ok[j] = mesh_value_at(G, min(r, G.he - 1), min(c, G.we - 1), &v[j]) && in;
+            r += dr;
+            c += dc;
+            if (c >= G.mw) { c -= G.mw; r++; }
+        }
+#pragma unroll
+        for (int j = 0; j < MS_CHUNK; j++)
+            if (ok[j]) f(v[j]);
+    }
 }
 
 // Sums of a set of values relative to c*: in-window values in int64 fixed
@@ -97,19 +198,34 @@ __device__ __forceinline__ void warp_partial(MeshShared& S, const Sums& s, const
     }
 }
 
-// Warp 0 only, after a barrier: totals of the per-warp partials.  Counts in
-// every lane; sums (int64 and the outlier sums as FP64) valid in lane 0.
+// Warp 0 only, after a barrier: totals of the per-warp partials (lanes
+// 0..MS_WARPS-1 hold one each; lane 0 ends with the totals).  Counts are
+// broadcast to every lane; the sums (int64, outlier sums as double-float) are
+// valid in lane 0.
 __device__ __forceinline__ void warp0_totals(const MeshShared& S, int lane, int c[3], long long* i1, long long* i2,
-                                             double* o1, double* o2) {
+                                             df* o1, df* o2) {
     const bool in = lane < MS_WARPS;
-    *i1 = warp_sum_ll(in ? S.redl[lane] : 0);
-    *i2 = warp_sum_ll(in ? S.redl[MS_WARPS + lane] : 0);
+    long long a = in ? S.redl[lane] : 0, b = in ? S.redl[MS_WARPS + lane] : 0;
     const float4 o = in ? S.redo[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const df xx = warp_sum_df(df{o.x, o.y}), yy = warp_sum_df(df{o.z, o.w});
-    c[0] = warp_sum_i(in ? S.redi[lane] : 0);
-    c[1] = warp_sum_i(in ? S.redi[MS_WARPS + lane] : 0);
-    c[2] = warp_sum_i(in ? S.redi[2 * MS_WARPS + lane] : 0);
-    if (lane == 0) { *o1 = df_to_d(xx); *o2 = df_to_d(yy); }
+    df x{o.x, o.y}, y{o.z, o.w};
+    int c0 = in ? S.redi[lane] : 0, c1 = in ? S.redi[MS_WARPS + lane] : 0, c2 = in ? S.redi[2 * MS_WARPS + lane] : 0;
+#pragma unroll
+    for (int off = MS_WARPS / 2; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
+        x = df_add(x, df{__shfl_xor_sync(0xffffffffu, x.hi, off), __shfl_xor_sync(0xffffffffu, x.lo, off)});
+        y = df_add(y, df{__shfl_xor_sync(0xffffffffu, y.hi, off), __shfl_xor_sync(0xffffffffu, y.lo, off)});
+        c0 += __shfl_xor_sync(0xffffffffu, c0, off);
+        c1 += __shfl_xor_sync(0xffffffffu, c1, off);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, off);
+    }
+    c[0] = __shfl_sync(0xffffffffu, c0, 0);
+    c[1] = __shfl_sync(0xffffffffu, c1, 0);
+    c[2] = __shfl_sync(0xffffffffu, c2, 0);
+    *i1 = a;
+    *i2 = b;
+    *o1 = x;
+    *o2 = y;
 }
 
 // Bitonic sort of 32*E values held E per lane (value index E*lane + j),
@@ -162,42 +278,41 @@ __device__ __forceinline__ void warp_sort_slice(float* sval, int s0, int m, int 
     __syncwarp();
 }
 
-// Warp 0 only: sort bin b's slice in place once (slices up to 256 values).
-__device__ void warp_ensure_sorted(MeshShared& S, float* sval, int b, int lane) {
+// Warp 0 only: sort stored bin b's slice in place once (slices up to 256 values).
+__device__ void warp_ensure_sorted(MeshShared& S, int b, int lane) {
     if ((S.sorted_bits[b >> 5] >> (b & 31)) & 1u) return;
-    const int s0 = S.hstart[b], m = (int)S.hstart[b + 1] - s0;
-    if (m <= 32) warp_sort_slice<1>(sval, s0, m, lane);
-    else if (m <= 64) warp_sort_slice<2>(sval, s0, m, lane);
-    else if (m <= 128) warp_sort_slice<4>(sval, s0, m, lane);
-    else warp_sort_slice<8>(sval, s0, m, lane);
-    if (lane == 0) S.sorted_bits[b >> 5] |= 1u << (b & 31);
+    const int s0 = S.sstart[b], m = (int)S.sstart[b + 1] - s0;
+    if (m <= 32) warp_sort_slice<1>(S.store, s0, m, lane);
+    else if (m <= 64) warp_sort_slice<2>(S.store, s0, m, lane);
+    else if (m <= 128) warp_sort_slice<4>(S.store, s0, m, lane);
+    else warp_sort_slice<8>(S.store, s0, m, lane);
+    if (lane == 0) atomicOr(&S.sorted_bits[b >> 5], 1u << (b & 31));
     __syncwarp();
 }
 
-constexpr int MS_WARPSORT_MAX = 256;
-
-// Warp 0 only: r-th smallest of the elements of slice [s0, s1) within [lo, hi]
-// for slices too long to sort: 11/11/10-bit radix passes over the
-// order-preserving keys with the histogram in shared memory.
-__device__ float warp_radix_select(MeshShared& S, const float* sval, int s0, int s1, float lo, float hi, int r,
-                                   int lane) {
+// Warp 0 only: r-th smallest of the values of buf[s0, s1) that lie in [lo, hi]
+// and, when bsel >= 0, fall in bin bsel: 11/11/10-bit radix passes over the
+// order-preserving keys, histogram in S.hbuf (free after the scatter).
+__device__ float warp_radix_select(MeshShared& S, const float* buf, int s0, int s1, float lo, float hi, int bsel,
+                                   float cstar, float inv_bw, int r, int lane) {
     uint32_t prefix = 0, pmask = 0;
     int rr = r;
     for (int pass = 0; pass < 3; pass++) {
         const int sh = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
         const int nb = pass == 2 ? 1024 : 2048, per = nb / 32;
-        for (int k = lane; k < nb; k += 32) S.radix[k] = 0;
+        for (int k = lane; k < nb; k += 32) S.hbuf[k] = 0;
         __syncwarp();
         for (int k = s0 + lane; k < s1; k += 32) {
-            const float v = sval[k];
+            const float v = buf[k];
             if (!(v >= lo && v <= hi)) continue;
+            if (bsel >= 0 && bin_of(v, cstar, inv_bw) != bsel) continue;
             const uint32_t key = fkey(v);
             if ((key & pmask) != prefix) continue;
-            atomicAdd(&S.radix[(key >> sh) & (nb - 1)], 1u);
+            atomicAdd(&S.hbuf[(key >> sh) & (nb - 1)], 1u);
         }
         __syncwarp();
         int tot = 0;
-        for (int d = lane * per; d < (lane + 1) * per; d++) tot += (int)S.radix[d];
+        for (int d = lane * per; d < (lane + 1) * per; d++) tot += (int)S.hbuf[d];
         int inc = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -209,7 +324,7 @@ __device__ float warp_radix_select(MeshShared& S, const float* sval, int s0, int
         if (rr >= before && rr < inc) {
             int acc = before, d = lane * per;
             for (; d < (lane + 1) * per; d++) {
-                const int c = (int)S.radix[d];
+                const int c = (int)S.hbuf[d];
                 if (rr < acc + c) break;
                 acc += c;
             }
@@ -228,16 +343,66 @@ __device__ float warp_radix_select(MeshShared& S, const float* sval, int s0, int
     return fkey_inv(prefix);
 }
 
+// Block-wide: the same selection over the values of the mesh itself (global
+// re-reads), for a median bin holding more values than the gather buffer.
+__device__ float block_radix_select_global(MeshShared& S, const MeshGeom& G, float lo, float hi, int bsel,
+                                           float cstar, float inv_bw, int r) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t prefix = 0, pmask = 0;
+    int rr = r;
+    for (int pass = 0; pass < 3; pass++) {
+        const int sh = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
+        const int nb = pass == 2 ? 1024 : 2048, per = nb / 32;
+        for (int k = threadIdx.x; k < nb; k += MS_THREADS) S.hbuf[k] = 0;
+        __syncthreads();
+        mesh_for_each(G, [&](float v) {
+            if (!(v >= lo && v <= hi) || bin_of(v, cstar, inv_bw) != bsel) return;
+            const uint32_t key = fkey(v);
+            if ((key & pmask) == prefix) atomicAdd(&S.hbuf[(key >> sh) & (nb - 1)], 1u);
+        });
+        __syncthreads();
+        if (warp == 0) {
+            int tot = 0;
+            for (int d = lane * per; d < (lane + 1) * per; d++) tot += (int)S.hbuf[d];
+            int inc = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const int before = inc - tot;
+            if (rr >= before && rr < inc) {
+                int acc = before, d = lane * per;
+                for (; d < (lane + 1) * per; d++) {
+                    const int c = (int)S.hbuf[d];
+                    if (rr < acc + c) break;
+                    acc += c;
+                }
+                S.bc_i[BI_DIGIT] = d;
+                S.bc_i[BI_REM] = rr - acc;
+            }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)S.bc_i[BI_DIGIT] << sh;
+        pmask |= (uint32_t)(nb - 1) << sh;
+        rr = S.bc_i[BI_REM];
+        __syncthreads();
+    }
+    return fkey_inv(prefix);
+}
+
 // State of the kept set [lo, hi] of a clip pass.
 struct KeptSet {
     float lo, hi;
     int bl, bh;     // bins of lo and hi
-    int nbl, nbh;   // kept elements in slices bl and bh (nbh unused when bl == bh)
+    int nbl, nbh;   // kept elements in bins bl and bh (nbh unused when bl == bh)
     int n;
 };
 
-// Bin and rank (among the kept values of that bin) of the k-th smallest kept value.
-__device__ __forceinline__ void kept_locate(const MeshShared& S, const KeptSet& K, int k, int* bin, int* r) {
+// Warp 0 only: bin and rank (among the kept values of that bin) of the k-th
+// smallest kept value.  The bin search probes 32 bins per step (ballot), so
+// it takes two or three steps over the 1026 bins.
+__device__ __forceinline__ void kept_locate(const MeshShared& S, const KeptSet& K, int k, int lane, int* bin, int* r) {
     const int full = (K.bh > K.bl + 1) ? (int)(S.hstart[K.bh] - S.hstart[K.bl + 1]) : 0;
     const int nbl = (K.bl == K.bh) ? K.n : K.nbl;
     if (k < nbl) {
@@ -245,10 +410,15 @@ __device__ __forceinline__ void kept_locate(const MeshShared& S, const KeptSet& 
     } else if (k - nbl < full) {
         const int kk = k - nbl;
         const uint32_t base = S.hstart[K.bl + 1];
-        int a = K.bl + 1, b = K.bh - 1;
-        while (a < b) {
-            const int mid = (a + b + 1) >> 1;
-            if ((int)(S.hstart[mid] - base) <= kk) a = mid; else b = mid - 1;
+        // largest a in [K.bl + 1, K.bh) with hstart[a] - base <= kk (true at K.bl + 1)
+        int a = K.bl + 1, e = K.bh;
+        while (e - a > 1) {
+            const int step = (e - a + 31) >> 5;
+            const int p = a + lane * step;
+            const unsigned m = __ballot_sync(0xffffffffu, p < e && (int)(S.hstart[p] - base) <= kk);
+            const int na = a + (31 - __clz(m)) * step;
+            e = min(na + step, e);
+            a = na;
         }
         *bin = a; *r = kk - (int)(S.hstart[a] - base);
     } else {
@@ -256,181 +426,284 @@ __device__ __forceinline__ void kept_locate(const MeshShared& S, const KeptSet& 
     }
 }
 
-// Warp 0 only: the two middle order statistics x_k0, x_k1 (k0 = (n-1)/2,
-// k1 = n/2) of the kept set; Eq. 1's median is their mean.  Bins of up to
-// MS_WARPSORT_MAX values are sorted once per mesh and indexed; longer ones are
-// selected by radix passes.
-__device__ void kept_middle(MeshShared& S, float* sval, const KeptSet& K, float vals[2], int lane) {
-    for (int q = 0; q < 2; q++) {
-        const int kq = q == 0 ? (K.n - 1) / 2 : K.n / 2;
-        if (q == 1 && kq == (K.n - 1) / 2) { vals[1] = vals[0]; break; }
-        int b, r;
-        kept_locate(S, K, kq, &b, &r);
-        const int s0 = S.hstart[b], s1 = S.hstart[b + 1];
-        const bool sorted = (S.sorted_bits[b >> 5] >> (b & 31)) & 1u;
-        if (sorted || s1 - s0 <= MS_WARPSORT_MAX) {
-            warp_ensure_sorted(S, sval, b, lane);
-            int a = s0, e = s1;  // first value >= lo in the sorted slice
-            while (a < e) { const int m = (a + e) >> 1; if (sval[m] < K.lo) a = m + 1; else e = m; }
-            vals[q] = sval[a + r];
-        } else {
-            vals[q] = warp_radix_select(S, sval, s0, s1, K.lo, K.hi, r, lane);
-        }
+// Which bins the scatter stored: [0, cl], [ml, mh] and [ch, MS_NB+1].
+struct Stored {
+    int cl, ml, mh, ch;
+    __device__ __forceinline__ bool bin(int b) const { return b <= cl || b >= ch || (b >= ml && b <= mh); }
+    __device__ __forceinline__ bool range(int a, int b) const {  // every bin of [a, b]; empty ranges are
+        return a > b || b <= cl || a >= ch || (a >= ml && b <= mh);
+    }
+};
+
+// ---- scalar statistics of the kept set (one thread) --------------------------
+// Double-float arithmetic on the FP32 pipe (~48-bit significands, relative
+// error ~1e-14): the FP64 pipe of this GPU is narrow and its latency sits on
+// the serial path of every clip pass.  Windows so fine or so coarse that the
+// scaled sums would leave the FP32 range (|e| > 40) take the FP64 branch.
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_scale(df a, float p2) { return df{a.hi * p2, a.lo * p2}; }  // p2 a power of two
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return two_sum(p, e);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return two_sum(p, e);
+}
+__device__ __forceinline__ df df_div(df a, df b) {  // one correction step after the FP32 quotient
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const df r = df_sub(a, df_mul_f(b, q1));
+    return two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+__device__ __forceinline__ df df_sqrt(df a) {  // one Newton step after the FP32 root
+    if (!(a.hi > 0.f)) return df{0.f, 0.f};
+    const float r = __fsqrt_rn(a.hi);
+    const df d = df_sub(a, sq_exact(r));
+    return two_sum(r, __fdiv_rn(d.hi, 2.0f * r));
+}
+// exact split of an int64 into three pieces of at most 21 bits
+__device__ __forceinline__ df df_from_i64(long long i) {
+    const float c2 = (float)(int)(i >> 42);
+    const float c1 = (float)(int)((i >> 21) & 0x1fffff);
+    const float c0 = (float)(int)(i & 0x1fffff);
+    return df_add_f(two_sum(c2 * 4398046511104.0f, c1 * 2097152.0f), c0);
+}
+__device__ __forceinline__ df df_from_d(double d) {
+    const float h = __double2float_rn(d);
+    return df{h, __double2float_rn(d - (double)h)};
+}
+// smallest float >= hi + lo, largest float <= hi + lo (|lo| <= ulp(hi) / 2)
+__device__ __forceinline__ float df_to_float_ru(df a) { return a.lo > 0.f ? nextafterf(a.hi, INFINITY) : a.hi; }
+__device__ __forceinline__ float df_to_float_rd(df a) { return a.lo < 0.f ? nextafterf(a.hi, -INFINITY) : a.hi; }
+
+// mean and population sigma of the kept set from its sums relative to c*:
+// s1 = i1 * unit + o1, s2 = i2 * unit^2 + o2, unit = 2^(e - MS_SCALE_BITS)
+__device__ __forceinline__ void kept_stats(long long i1, long long i2, df o1, df o2, int n, float cstar, int e,
+                                           df* mu, df* sd) {
+    if (e >= -40 && e <= 40) {
+        const float u = ldexpf(1.0f, e - MS_SCALE_BITS);
+        const df s1 = df_add(df_scale(df_from_i64(i1), u), o1);
+        const df s2 = df_add(df_scale(df_scale(df_from_i64(i2), u), u), o2);
+        const df rn = df_div(df{1.0f, 0.0f}, df{(float)n, 0.0f});
+        const df m1 = df_mul(s1, rn);
+        *mu = df_add_f(m1, cstar);
+        *sd = df_sqrt(df_sub(df_mul(s2, rn), df_mul(m1, m1)));
+    } else {
+        const double unit = ldexp(1.0, e - MS_SCALE_BITS);
+        const double s1 = (double)i1 * unit + df_to_d(o1);
+        const double s2 = (double)i2 * unit * unit + df_to_d(o2);
+        const double m1 = s1 / n;
+        *mu = df_from_d((double)cstar + m1);
+        *sd = df_from_d(sqrt(fmax(s2 / n - m1 * m1, 0.0)));
     }
 }
 
-// Scalar FP64 statistics of the kept set (one thread): mean and population sigma.
-struct KeptSums {
-    long long i1, i2;
-    double o1, o2;
-};
-__device__ __forceinline__ void kept_stats(const KeptSums& t, int n, float cstar, double unit, double* mu,
-                                           double* sd) {
-    const double s1 = (double)t.i1 * unit + t.o1;
-    const double s2 = (double)t.i2 * unit * unit + t.o2;
-    const double m1 = s1 / n;
-    *mu = (double)cstar + m1;
-    *sd = sqrt(fmax(s2 / n - m1 * m1, 0.0));
+// Warp 0 only: exclusive prefix of the histogram counts into S.hstart, and the
+// bins holding the order statistics kq[0..2] (broadcast to every lane).
+__device__ __forceinline__ void warp0_scan_counts(MeshShared& S, int lane, const int kq[3], int bq[3]) {
+    constexpr int PER = (MS_NBT + 31) / 32;
+    const int b0 = lane * PER, b1 = min(b0 + PER, MS_NBT);
+    int acc = 0;
+    for (int b = b0; b < b1; b++) acc += (int)S.hbuf[b];
+    int inc = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    int run = inc - acc;
+    int loc[3] = {0, 0, 0};
+    unsigned hit = 0;
+    for (int b = b0; b < b1; b++) {
+        const int h = (int)S.hbuf[b];
+        S.hstart[b] = (uint32_t)run;
+#pragma unroll
+        for (int t = 0; t < 3; t++)
+            if (kq[t] >= run && kq[t] < run + h) { loc[t] = b; hit |= 1u << t; }
+        run += h;
+    }
+    if (lane == 31) S.hstart[MS_NBT] = (uint32_t)inc;
+#pragma unroll
+    for (int t = 0; t < 3; t++) {
+        const unsigned who = __ballot_sync(0xffffffffu, (hit >> t) & 1u);
+        bq[t] = __shfl_sync(0xffffffffu, loc[t], who ? __ffs(who) - 1 : 0);
+    }
+    __syncwarp();
 }
 
-template <int PPT>
-__global__ void __launch_bounds__(MS_THREADS, 2) k_mesh_stats(MeshJob J) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    MeshShared& S = *reinterpret_cast<MeshShared*>(smem_raw);
-    float* sval = reinterpret_cast<float*>(smem_raw + sizeof(MeshShared));
+// Warp 0 only: value of rank r (among kept values) in bin b, when it is on chip:
+// a stored slice (sorted once, or radix-selected when long) or the gathered
+// bins [gl, gh].  Returns false when neither holds bin b.
+__device__ bool warp_value_of(MeshShared& S, const Stored& St, int b, int r, const KeptSet& K, float cstar,
+                              float inv_bw, int lane, float* out) {
+    if (St.bin(b)) {
+        const int s0 = S.sstart[b], s1 = S.sstart[b + 1];
+        const bool sorted = (S.sorted_bits[b >> 5] >> (b & 31)) & 1u;
+        if (sorted || s1 - s0 <= MS_WARPSORT_MAX) {
+            warp_ensure_sorted(S, b, lane);
+            int a = s0;
+            if (b == K.bl) {  // first value >= lo in the sorted slice (bins inside the kept range are whole)
+                int e = s1;
+                while (a < e) { const int m = (a + e) >> 1; if (S.store[m] < K.lo) a = m + 1; else e = m; }
+            }
+            *out = S.store[min(a + r, s1 - 1)];
+        } else {
+            *out = warp_radix_select(S, S.store, s0, s1, K.lo, K.hi, -1, cstar, inv_bw, r, lane);
+        }
+        return true;
+    }
+    if (b >= S.bc_i[BI_GL] && b <= S.bc_i[BI_GH]) {
+        *out = warp_radix_select(S, S.gbuf, 0, min(S.bc_i[BI_GCNT], MS_GCAP), K.lo, K.hi, b, cstar, inv_bw, r,
+                                 lane);
+        return true;
+    }
+    return false;
+}
+
+// Warp 0 only: statistics of the current kept set from its two middle order
+// statistics, and the bounds of the next pass (published for every warp).
+// Returns the next state: ST_SCAN, or ST_STOP after the last allowed pass.
+__device__ int warp0_finish(MeshShared& S, const MeshJob& J, const Stored& St, const KeptSet& K, float mid0,
+                            float mid1, int it, float cstar, int e, float inv_bw, df nsig, int lane, float* plo,
+                            float* phi) {
+    if (lane == 0) {
+        df mu, sd;
+        kept_stats(S.ks_i[0], S.ks_i[1], S.ks_o[0], S.ks_o[1], K.n, cstar, e, &mu, &sd);
+        const df m2 = two_sum(mid0, mid1);
+        S.st[0] = df{0.5f * m2.hi, 0.5f * m2.lo};
+        S.st[1] = mu;
+        S.st[2] = sd;
+    }
+    if (it == J.maxiters) return ST_STOP;  // statistics of the set left after maxiters passes
+    if (lane == 0) {
+        const df ks = df_mul(nsig, S.st[2]);
+        *plo = fmaxf(K.lo, df_to_float_ru(df_sub(S.st[0], ks)));
+        *phi = fminf(K.hi, df_to_float_rd(df_add(S.st[0], ks)));
+    }
+    *plo = __shfl_sync(0xffffffffu, *plo, 0);
+    *phi = __shfl_sync(0xffffffffu, *phi, 0);
+    const int nbl = bin_of(*plo, cstar, inv_bw), nbh = bin_of(*phi, cstar, inv_bw);
+    const bool on_chip = St.range(K.bl, nbl) && St.range(max(nbh, nbl + 1), K.bh);
+    if (lane == 0) {
+        S.bc_f[0] = *plo; S.bc_f[1] = *phi; S.bc_f[2] = K.lo; S.bc_f[3] = K.hi;
+        S.bc_i[BI_KBL] = K.bl; S.bc_i[BI_KBH] = K.bh;
+        S.bc_i[BI_MODE] = on_chip;
+    }
+    return ST_SCAN;
+}
+
+__global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
+    __shared__ MeshShared S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     const int mesh = blockIdx.x;
     const int mx = mesh % J.nx, my = mesh / J.nx;
-    const int64_t x0 = (int64_t)mx * J.mesh_w, y0 = (int64_t)my * J.mesh_h;
-    const int we = (int)min((int64_t)J.mesh_w, J.W - x0);
-    const int he = (int)min((int64_t)J.mesh_h, J.H - y0);
-    const int slots = J.mesh_w * J.mesh_h;
+    MeshGeom G;
+    G.img = J.img; G.dtype = J.dtype; G.pitch = J.pitch; G.W = J.W; G.mask = J.mask;
+    G.bias_map = J.bias_map; G.bias = J.bias; G.inv_flat = J.inv_flat;
+    G.x0 = (int64_t)mx * J.mesh_w; G.y0 = (int64_t)my * J.mesh_h;
+    G.mw = J.mesh_w;
+    G.we = (int)min((int64_t)J.mesh_w, J.W - G.x0);
+    G.he = (int)min((int64_t)J.mesh_h, J.H - G.y0);
+    G.slots = J.mesh_w * J.mesh_h;
+    G.vec = J.dtype == IPP_F32 && !J.mask && (J.pitch & 3) == 0 && (G.we & 3) == 0 &&
+            ((reinterpret_cast<uintptr_t>(J.img) + (uintptr_t)((G.y0 * J.pitch + G.x0) * 4)) & 15) == 0;
 
-    // ---- load (the one HBM read of the mesh); approximate moments ------------
-    // element e = threadIdx.x + k * 512 of the mesh sits at (r, c); both advance
-    // by fixed steps with k, so no division inside the loop
-    float v[PPT];
-    const int dr = MS_THREADS / J.mesh_w, dc = MS_THREADS - dr * J.mesh_w;
-    const float qnan = __int_as_float(0x7fc00000);  // NaN = not usable
-    if (J.dtype == IPP_F32) {
-        // every load is issued before any is used: addresses are clamped into
-        // the mesh and the out-of-mesh slots are blanked afterwards
-        const float* base = reinterpret_cast<const float*>(J.img) + y0 * J.pitch + x0;
-        uint32_t inside = 0;
-        int r = threadIdx.x / J.mesh_w, c = threadIdx.x - r * J.mesh_w;
-        const float* rowp = base + (int64_t)min(r, he - 1) * J.pitch;
+    // ---- histogram window from a sample: warp 0 sorts 256 values spread over
+    // the mesh; bw = 2^e with NB*bw in (8, 16] robust sigma, centre c* a
+    // multiple of bw near the sample median.  Values outside the window land in the two
+    // end bins, whose slices are handled element by element. ----------------
+    if (warp == 0) {
+        float a[8];
+        int nv = 0;
 #pragma unroll
-        for (int k = 0; k < PPT; k++) {
-            const int e = threadIdx.x + k * MS_THREADS;
-            inside |= (uint32_t)(e < slots && r < he && c < we) << k;
-            v[k] = __ldg(rowp + min(c, we - 1));
-            const int r0 = r;
-            r += dr;
-            c += dc;
-            if (c >= J.mesh_w) { c -= J.mesh_w; r++; }
-            rowp += (int64_t)(min(r, he - 1) - min(r0, he - 1)) * J.pitch;
+        for (int j = 0; j < 8; j++) {
+            const int k = lane + 32 * j;
+            const int r = (int)(((int64_t)k * G.he) >> 8), c = (int)(((int64_t)k * 61 + 7) % G.we);
+            float x;
+            a[j] = mesh_value_at(G, r, c, &x) ? x : INFINITY;
+            nv += a[j] != INFINITY;
         }
+        nv = warp_sum_i(nv);
+        warp_bitonic<8>(a, lane);
 #pragma unroll
-        for (int k = 0; k < PPT; k++)
-            if (!((inside >> k) & 1u) || !isfinite(v[k])) v[k] = qnan;
-        if (J.mask) {
-            r = threadIdx.x / J.mesh_w;
-            c = threadIdx.x - r * J.mesh_w;
-#pragma unroll
-            for (int k = 0; k < PPT; k++) {
-                if (v[k] == v[k] && J.mask[(y0 + r) * J.W + x0 + c]) v[k] = qnan;
-                r += dr;
-                c += dc;
-                if (c >= J.mesh_w) { c -= J.mesh_w; r++; }
+        for (int j = 0; j < 8; j++) S.gbuf[8 * lane + j] = a[j];
+        __syncwarp();
+        if (lane == 0) {
+            int e = 0;
+            float cs = 0.f;
+            if (nv >= 16) {
+                const float p16 = S.gbuf[(int)(0.1587f * nv)], p50 = S.gbuf[nv / 2], p84 = S.gbuf[(int)(0.8413f * nv)];
+                float span = fmaxf(8.0f * (p84 - p16), (S.gbuf[nv - 1] - S.gbuf[0]) * 1e-6f);
+                span = fmaxf(span, fabsf(p50) * 1e-6f + 1e-30f);
+                e = max(min((int)floorf(log2f(span / MS_NB)), 100), -110);
+                cs = rintf(p50 * ldexpf(1.0f, -e)) * ldexpf(1.0f, e);
             }
-        }
-    } else {
-        int r = threadIdx.x / J.mesh_w, c = threadIdx.x - r * J.mesh_w;
-#pragma unroll
-        for (int k = 0; k < PPT; k++) {
-            const int e = threadIdx.x + k * MS_THREADS;
-            float x = qnan;
-            if (e < slots && r < he && c < we) {
-                const int64_t yy = y0 + r, xx = x0 + c;
-                const float raw = (float)__ldg(reinterpret_cast<const uint16_t*>(J.img) + yy * J.pitch + xx);
-                const float b = J.bias_map ? __ldg(J.bias_map + yy * J.W + xx) : J.bias;
-                x = (raw - b) * __ldg(J.inv_flat + yy * J.W + xx);
-                if (J.mask && J.mask[yy * J.W + xx]) x = qnan;
-                if (!isfinite(x)) x = qnan;
-            }
-            v[k] = x;
-            r += dr;
-            c += dc;
-            if (c >= J.mesh_w) { c -= J.mesh_w; r++; }
+            S.bc_i[BI_SBAD] = nv < 16;  // too few usable samples: the window is re-placed after read 1
+            S.bc_i[BI_E] = e;
+            S.bc_f[4] = cs;
         }
     }
-    int n_loc = 0;
-    float piv = 0.f, s = 0.f, q = 0.f, vmin = INFINITY, vmax = -INFINITY;
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        const float x = v[k];
-        if (x == x) {
-            if (n_loc == 0) piv = x;
+    for (int k = threadIdx.x; k < MS_NBT; k += MS_THREADS) S.hbuf[k] = 0;
+    __syncthreads();
+    int e = S.bc_i[BI_E];
+    float cstar = S.bc_f[4], bw = ldexpf(1.0f, e), inv_bw = ldexpf(1.0f, -e);
+
+    // ---- read 1 (HBM): histogram in that window, exact sums relative to its
+    // centre, count, min, max ----------------------------------------------------
+    Sums tot{0, 0, df{0.f, 0.f}, df{0.f, 0.f}};
+    {
+        const float fxs0 = ldexpf(1.0f, MS_SCALE_BITS - e);
+        int n_loc = 0;
+        float vmin = INFINITY, vmax = -INFINITY;
+        mesh_for_each(G, [&](float x) {
+            const int b = bin_of(x, cstar, inv_bw);
+            atomicAdd(&S.hbuf[b], 1u);
+            sums_add(tot, x, b, cstar, fxs0);
             n_loc++;
-            const float d = x - piv;
-            s += d;
-            q = fmaf(d, d, q);
             vmin = fminf(vmin, x);
             vmax = fmaxf(vmax, x);
-        }
-    }
-    // merge (n, mean, M2) across the block (Chan et al.); FP32 is enough here:
-    // these moments only place the histogram window
-    float mean = n_loc ? piv + s / n_loc : 0.f;
-    float m2 = n_loc ? fmaxf(q - s * s / n_loc, 0.f) : 0.f;
-    float cnt = (float)n_loc;
+        });
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float nb = __shfl_xor_sync(0xffffffffu, cnt, o);
-        const float mb = __shfl_xor_sync(0xffffffffu, mean, o);
-        const float qb = __shfl_xor_sync(0xffffffffu, m2, o);
-        const float nt = cnt + nb;
-        if (nt > 0.f) {
-            const float dl = mb - mean;
-            mean = mean + dl * (nb / nt);
-            m2 = m2 + qb + dl * dl * (cnt * nb / nt);
+        for (int o = 16; o > 0; o >>= 1) {
+            vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+            vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         }
-        cnt = nt;
-        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        const int cn[3] = {n_loc, 0, 0};
+        warp_partial(S, tot, cn, lane, warp);
+        if (lane == 0) { S.redf[warp] = vmin; S.redf[MS_WARPS + warp] = vmax; }
     }
-    if (lane == 0) {
-        S.redf[warp] = cnt; S.redf[MS_WARPS + warp] = mean; S.redf[2 * MS_WARPS + warp] = m2;
-        S.redi[warp] = __float_as_int(vmin); S.redi[MS_WARPS + warp] = __float_as_int(vmax);
-    }
-    for (int k = threadIdx.x; k < MS_NBT; k += MS_THREADS) S.hcnt[k] = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float c = 0.f, mu = 0.f, mm = 0.f, a = INFINITY, b = -INFINITY;
-        for (int w = 0; w < MS_WARPS; w++) {
-            const float nb = S.redf[w], mb = S.redf[MS_WARPS + w], qb = S.redf[2 * MS_WARPS + w];
-            const float nt = c + nb;
-            if (nt > 0.f) {
-                const float dl = mb - mu;
-                mu = mu + dl * (nb / nt);
-                mm = mm + qb + dl * dl * (c * nb / nt);
+    float mu0 = 0.f, sd0 = 0.f;  // mean and sigma of the mesh (warp 0; used only to re-place a missed window)
+    if (warp == 0) {
+        int c[3];
+        long long i1, i2;
+        df o1, o2;
+        warp0_totals(S, lane, c, &i1, &i2, &o1, &o2);
+        if (lane == 0) {
+            float a = INFINITY, b = -INFINITY;
+            for (int w = 0; w < MS_WARPS; w++) { a = fminf(a, S.redf[w]); b = fmaxf(b, S.redf[MS_WARPS + w]); }
+            S.bc_i[BI_N0] = c[0];
+            S.bc_f[2] = a;
+            S.bc_f[3] = b;
+            if (c[0] > 0) {
+                const double unit0 = ldexp(1.0, e - MS_SCALE_BITS);
+                const double m1 = ((double)i1 * unit0 + df_to_d(o1)) / c[0];
+                const double var = ((double)i2 * unit0 * unit0 + df_to_d(o2)) / c[0] - m1 * m1;
+                mu0 = (float)((double)cstar + m1);
+                sd0 = (float)sqrt(fmax(var, 0.0));
             }
-            c = nt;
-            a = fminf(a, __int_as_float(S.redi[w]));
-            b = fmaxf(b, __int_as_float(S.redi[MS_WARPS + w]));
         }
-        S.bc_i[0] = (int)c;
-        S.bc_f[0] = mu;
-        S.bc_f[1] = c > 0.f ? sqrtf(mm / c) : 0.f;
-        S.bc_f[2] = a;
-        S.bc_f[3] = b;
     }
     __syncthreads();
-    const int n0 = S.bc_i[0];
-    const float mu0 = S.bc_f[0], sd0 = S.bc_f[1];
-    vmin = S.bc_f[2];
-    vmax = S.bc_f[3];
+    const int n0 = S.bc_i[BI_N0];
+    const float vmin = S.bc_f[2], vmax = S.bc_f[3];
 
     if (n0 < J.min_valid || n0 == 0) {
         if (threadIdx.x == 0) { J.raw_bkg[mesh] = 0.f; J.raw_rms[mesh] = -1.f; }
@@ -451,159 +724,177 @@ __global__ void __launch_bounds__(MS_THREADS, 2) k_mesh_stats(MeshJob J) {
         return;
     }
 
-    // ---- histogram window: bw = 2^e, width NB*bw in (4, 8] sigma0, centre c* a
-    // multiple of bw near the mean; refined once around the median bin when it
-    // is crowded (outliers inflate sigma0).  Values outside the window land in
-    // the two end bins, whose slices are handled element by element. ---------
-    int e;
-    float cstar, bw, inv_bw;
-    {
-        float span = fmaxf(8.0f * sd0, (vmax - vmin) * 1e-6f);
-        span = fmaxf(span, fabsf(mu0) * 1e-6f + 1e-30f);
-        e = (int)floorf(log2f(span / MS_NB));
-        e = max(min(e, 100), -110);
-        bw = ldexpf(1.0f, e);
-        inv_bw = ldexpf(1.0f, -e);
-        cstar = rintf(mu0 * inv_bw) * bw;
-    }
-    // (S.hcnt was cleared before the barrier above)
-    for (int round = 0; round < 2; round++) {
-#pragma unroll
-        for (int k = 0; k < PPT; k++)
-            if (v[k] == v[k]) atomicAdd(&S.hcnt[bin_of(v[k], cstar, inv_bw)], 1u);
-        __syncthreads();
-        if (warp == 0) {  // exclusive scan of the counts; bins of the 15.87 / 50 / 84.13 percentiles
-            constexpr int PER = (MS_NBT + 31) / 32;
-            const int b0 = lane * PER;
-            int acc = 0;
-            for (int b = b0; b < min(b0 + PER, MS_NBT); b++) acc += (int)S.hcnt[b];
-            int inc = acc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += t;
-            }
-            int run = inc - acc;
-            // each lane resolves the percentiles that fall in its range of bins
-            const int kq[3] = {(int)(0.1587f * n0), n0 / 2, (int)(0.8413f * n0)};
-            int bq[3] = {0, 0, 0};
-            unsigned hit = 0;
-            for (int b = b0; b < min(b0 + PER, MS_NBT); b++) {
-                const int h = (int)S.hcnt[b];
-                S.hstart[b] = (uint32_t)run;
-                S.hfill[b] = (uint32_t)run;  // scatter cursor
-#pragma unroll
-                for (int t = 0; t < 3; t++)
-                    if (kq[t] >= run && kq[t] < run + h) { bq[t] = b; hit |= 1u << t; }
-                run += h;
-            }
-            if (lane == 31) S.hstart[MS_NBT] = (uint32_t)inc;
-            int bqa[3];
-#pragma unroll
-            for (int t = 0; t < 3; t++) {
-                const unsigned who = __ballot_sync(0xffffffffu, (hit >> t) & 1u);
-                bqa[t] = __shfl_sync(0xffffffffu, bq[t], who ? __ffs(who) - 1 : 0);
-            }
+    // ---- check the window: when the median bin is crowded it is narrowed
+    // around the median (window of ~8 robust sigma from the 15.87 / 84.13
+    // percentile bins); when the window missed the bulk of the values (median
+    // in an end bin, or the end bins holding over 1/8 of them) it is re-placed
+    // from the mean and sigma of read 1.  Each change costs one more read (L2).
+    const int kq[3] = {(int)(0.1587f * n0), n0 / 2, (int)(0.8413f * n0)};
+    int bq[3];
+    for (int round = 0; round < 3; round++) {
+        if (warp == 0) {
+            warp0_scan_counts(S, lane, kq, bq);
             if (lane == 0) {
-                int refine = 0;
-                float nc = cstar, nbw = bw, ninv = inv_bw;
+                int redo = 0;
+                float nc = cstar;
                 int ne = e;
-                const int b16 = bqa[0], b50 = bqa[1], b84 = bqa[2];
-                if (round == 0 && b50 >= 1 && b50 <= MS_NB && S.hcnt[b50] > 64) {
+                const int b16 = bq[0], b50 = bq[1], b84 = bq[2];
+                const int ends = (int)(S.hbuf[0] + S.hbuf[MS_NB + 1]);
+                if (round < 2 && ((round == 0 && S.bc_i[BI_SBAD]) || b50 == 0 || b50 == MS_NB + 1 || ends > n0 / 8)) {
+                    float span = fmaxf(8.0f * sd0, (vmax - vmin) * 1e-6f);
+                    span = fmaxf(span, fabsf(mu0) * 1e-6f + 1e-30f);
+                    const int e2 = max(min((int)floorf(log2f(span / MS_NB)), 100), -110);
+                    const float c2 = rintf(mu0 * ldexpf(1.0f, -e2)) * ldexpf(1.0f, e2);
+                    if (e2 != e || c2 != cstar) { redo = 1; ne = e2; nc = c2; }
+                } else if (round < 2 && S.hbuf[b50] > 192) {
                     // window of about +-4 sigma_r: the median bins then hold ~n/100 values
                     const float sr = fmaxf(0.5f * (float)(b84 - b16 + 1) * bw, bw * 0.5f);
-                    int e2 = (int)floorf(log2f(8.0f * sr / MS_NB));
-                    e2 = max(e2, -110);
+                    const int e2 = max((int)floorf(log2f(8.0f * sr / MS_NB)), -110);
                     if (e2 < e) {
-                        refine = 1;
+                        redo = 1;
                         ne = e2;
-                        nbw = ldexpf(1.0f, e2);
-                        ninv = ldexpf(1.0f, -e2);
                         const float centre = cstar + ((float)(b50 - MS_NB / 2 - 1) + 0.5f) * bw;
-                        nc = rintf(centre * ninv) * nbw;
+                        nc = rintf(centre * ldexpf(1.0f, -e2)) * ldexpf(1.0f, e2);
                     }
                 }
-                S.bc_i[7] = refine;
-                S.bc_i[5] = ne;
-                S.bc_f[0] = nc;
-                S.bc_f[1] = nbw;
-                S.bc_f[2] = ninv;
+                S.bc_i[BI_REFINE] = redo;
+                S.bc_i[BI_E] = ne;
+                S.bc_f[4] = nc;
             }
         }
         __syncthreads();
-        const int refine = S.bc_i[7];
-        if (!refine) break;
-        e = S.bc_i[5];
-        cstar = S.bc_f[0];
-        bw = S.bc_f[1];
-        inv_bw = S.bc_f[2];
-        for (int k = threadIdx.x; k < MS_NBT; k += MS_THREADS) S.hcnt[k] = 0;
+        if (!S.bc_i[BI_REFINE]) break;
+        e = S.bc_i[BI_E];
+        cstar = S.bc_f[4];
+        bw = ldexpf(1.0f, e);
+        inv_bw = ldexpf(1.0f, -e);
+        for (int k = threadIdx.x; k < MS_NBT; k += MS_THREADS) S.hbuf[k] = 0;
+        __syncthreads();
+        tot = Sums{0, 0, df{0.f, 0.f}, df{0.f, 0.f}};
+        const float fxs1 = ldexpf(1.0f, MS_SCALE_BITS - e);
+        mesh_for_each(G, [&](float x) {  // re-read (L2)
+            const int b = bin_of(x, cstar, inv_bw);
+            atomicAdd(&S.hbuf[b], 1u);
+            sums_add(tot, x, b, cstar, fxs1);
+        });
         __syncthreads();
     }
-    for (int k = threadIdx.x; k < (MS_NBT + 31) / 32; k += MS_THREADS) S.sorted_bits[k] = 0;
 
-    // ---- scatter into bin order + exact sums of the whole set ----------------
-    // 8 cursor increments are in flight before their stores, not one at a time
-    const float fxs = ldexpf(1.0f, MS_SCALE_BITS - e);           // fixed-point scale
-    const double unit = ldexp(1.0, e - MS_SCALE_BITS);
-    {
-        Sums tot{0, 0, df{0.f, 0.f}, df{0.f, 0.f}};
-        constexpr int CH = PPT < 8 ? PPT : 8;
-#pragma unroll
-        for (int k0 = 0; k0 < PPT; k0 += CH) {
-            int bb[CH];
-            uint32_t pos[CH];
-#pragma unroll
-            for (int j = 0; j < CH; j++) bb[j] = v[k0 + j] == v[k0 + j] ? bin_of(v[k0 + j], cstar, inv_bw) : -1;
-#pragma unroll
-            for (int j = 0; j < CH; j++)
-                if (bb[j] >= 0) pos[j] = atomicAdd(&S.hfill[bb[j]], 1u);
-#pragma unroll
-            for (int j = 0; j < CH; j++)
-                if (bb[j] >= 0) {
-                    sval[pos[j]] = v[k0 + j];
-                    sums_add(tot, v[k0 + j], bb[j], cstar, fxs);
-                }
+    // ---- what to keep on chip: tails beyond ~2 robust sigma and a band
+    // around the median bin, within MS_STORE values ------------------------
+    if (warp == 0) {
+        if (lane == 0) {
+            const int b50 = bq[1];
+            const int srb = max(1, bq[1] - bq[0]);  // robust sigma in bins, from the side stars do not inflate
+            const int ntot = (int)S.hstart[MS_NBT];
+            // tails [0, cl] and [ch, MS_NB+1]: the end bins (outliers) always, when
+            // they fit; a tail of -1 / MS_NBT stores nothing on that side
+            auto tails = [&](int cl, int ch) {
+                return (cl >= 0 ? (int)S.hstart[cl + 1] : 0) + (ch <= MS_NBT - 1 ? ntot - (int)S.hstart[ch] : 0);
+            };
+            auto band = [&](int D) {
+                if (D < 0) return 0;
+                const int a = max(b50 - D, 0), b = min(b50 + D, MS_NBT - 1);
+                return (int)(S.hstart[b + 1] - S.hstart[a]);
+            };
+            int T = 2 * srb, D = MS_BAND;
+            auto cl_of = [&](int t) { return max(b50 - t, 0); };
+            auto ch_of = [&](int t) { return min(b50 + t, MS_NBT - 1); };
+            while (D > 2 && tails(cl_of(T), ch_of(T)) + band(D) > MS_STORE) D--;
+            while (tails(cl_of(T), ch_of(T)) + band(D) > MS_STORE && (cl_of(T) > 0 || ch_of(T) < MS_NBT - 1))
+                T += max(1, srb / 2);
+            int cl = cl_of(T), ch = ch_of(T);
+            while (D >= 0 && tails(cl, ch) + band(D) > MS_STORE) D--;
+            if (tails(cl, ch) > MS_STORE) {  // even the end bins do not fit: keep the smaller one, if any
+                const int lo_n = tails(0, MS_NBT), hi_n = tails(-1, MS_NBT - 1);
+                if (lo_n <= hi_n) { ch = MS_NBT; if (lo_n > MS_STORE) cl = -1; }
+                else { cl = -1; if (hi_n > MS_STORE) ch = MS_NBT; }
+            }
+            // three disjoint, ordered intervals [0, cl] < [ml, mh] < [ch, NBT-1]: a
+            // band touching a tail joins it; tails that meet store everything
+            int ml = D >= 0 ? max(b50 - D, 0) : 1, mh = D >= 0 ? min(b50 + D, MS_NBT - 1) : 0;
+            if (ml <= mh && ml <= cl + 1) { cl = max(cl, mh); ml = 1; mh = 0; }
+            if (ml <= mh && mh >= ch - 1) { ch = min(ch, ml); ml = 1; mh = 0; }
+            if (cl >= ch - 1) { cl = MS_NBT - 1; ch = MS_NBT; ml = 1; mh = 0; }
+            S.bc_i[BI_CL] = cl;
+            S.bc_i[BI_CH] = ch;
+            S.bc_i[BI_ML] = ml;
+            S.bc_i[BI_MH] = mh;
         }
-        const int cz[3] = {0, 0, 0};
-        warp_partial(S, tot, cz, lane, warp);
     }
-    __syncthreads();  // scatter and partials complete
+    for (int k = threadIdx.x; k < (MS_NBT + 31) / 32; k += MS_THREADS) S.sorted_bits[k] = 0;
+    __syncthreads();
+    const Stored St{S.bc_i[BI_CL], S.bc_i[BI_ML], S.bc_i[BI_MH], S.bc_i[BI_CH]};
+    // prefix of the stored counts (closed form over the three intervals) and the scatter cursors
+    for (int b = threadIdx.x; b <= MS_NBT; b += MS_THREADS) {
+        uint32_t v = S.hstart[min(b, St.cl + 1)];
+        if (St.ml <= St.mh && b > St.ml) v += S.hstart[min(b, St.mh + 1)] - S.hstart[St.ml];
+        if (St.ch <= MS_NBT - 1 && b > St.ch) v += S.hstart[b] - S.hstart[St.ch];
+        S.sstart[b] = v;
+        if (b < MS_NBT) S.hbuf[MS_NBT + b] = v;
+    }
+    __syncthreads();
+
+    // ---- last read (L2): scatter the stored bins in bin order ------------------
+    const float fxs = ldexpf(1.0f, MS_SCALE_BITS - e);           // fixed-point scale
+    const df nsig = df_from_d(J.nsigma);
+    {
+        uint32_t* cursor = S.hbuf + MS_NBT;
+        mesh_for_each(G, [&](float x) {
+            const int b = bin_of(x, cstar, inv_bw);
+            if (St.bin(b)) S.store[atomicAdd(&cursor[b], 1u)] = x;
+        });
+        const int cz[3] = {0, 0, 0};
+        warp_partial(S, tot, cz, lane, warp);  // sums of the whole set, from the last histogram read
+    }
+    __syncthreads();  // scatter and partials complete; S.hbuf is free from here on
+    // sort the band bins now, one warp per bin, off the serial path of the clip
+    for (int b = St.ml + warp; b <= St.mh; b += MS_WARPS)
+        if ((int)(S.sstart[b + 1] - S.sstart[b]) <= MS_WARPSORT_MAX) warp_ensure_sorted(S, b, lane);
+    __syncthreads();
 
     // ---- clip passes ----------------------------------------------------------
     // Warp 0 owns the kept set: it reduces the last pass's removals, selects the
-    // median, evaluates Eq. 1-2's statistics and the next bounds (scalar FP64 on
-    // lane 0; the FP64 pipe is narrow) and publishes them.  Every warp then
-    // scans only the bins at the two ends of the kept range for the values the
-    // new bounds remove.  Two barriers per pass.
+    // median, evaluates Eq. 1-2's statistics and the next bounds and publishes
+    // them.  Every warp then finds the values the new bounds remove: in the
+    // stored tails when the bounds fall there, else by reading the mesh again.
+    // Two barriers per pass; two more when a median bin must be fetched.
     KeptSet K;
     K.lo = -INFINITY; K.hi = INFINITY; K.bl = 0; K.bh = MS_NB + 1;
-    K.nbl = (int)S.hcnt[0]; K.nbh = (int)S.hcnt[MS_NB + 1];
+    K.nbl = (int)(S.hstart[1] - S.hstart[0]);
+    K.nbh = (int)(S.hstart[MS_NBT] - S.hstart[MS_NB + 1]);
     K.n = n0;
-    // the running sums and statistics live in shared memory (lane 0 of warp 0
-    // reads and writes them): registers are scarce at two 512-thread CTAs per SM
-    float plo = 0.f, phi = 0.f;            // bounds published for the pending pass (warp 0)
+    float plo = 0.f, phi = 0.f;   // bounds of the pending pass (warp 0)
+    int bm[2] = {0, 0}, rm[2] = {0, 0};  // median bins and ranks of the current set (warp 0)
     if (warp == 0) {
         int cz[3];
-        double o1 = 0.0, o2 = 0.0;
+        df o1, o2;
         long long i1, i2;
         warp0_totals(S, lane, cz, &i1, &i2, &o1, &o2);
-        if (lane == 0) { S.ks_i[0] = i1; S.ks_i[1] = i2; S.ks_o[0] = o1; S.ks_o[1] = o2; }
+        if (lane == 0) {
+            S.ks_i[0] = i1; S.ks_i[1] = i2; S.ks_o[0] = o1; S.ks_o[1] = o2;
+            S.bc_i[BI_GL] = 1; S.bc_i[BI_GH] = 0;   // nothing gathered yet
+        }
+        __syncwarp();
     }
     for (int it = 0;; it++) {
         if (warp == 0) {
+            int state = ST_STOP;
             bool cont = true;
             if (it > 0) {  // removals of pass it-1
                 int c[3];
                 long long i1, i2;
-                double o1 = 0.0, o2 = 0.0;
+                df o1, o2;
                 warp0_totals(S, lane, c, &i1, &i2, &o1, &o2);
                 // no value dropped: the set is stable (c >= n cannot happen: the
                 // median lies inside [med - k sd, med + k sd])
                 if (c[0] == 0 || c[0] >= K.n) {
                     cont = false;
                 } else {
-                    if (lane == 0) { S.ks_i[0] -= i1; S.ks_i[1] -= i2; S.ks_o[0] -= o1; S.ks_o[1] -= o2; }
+                    if (lane == 0) {
+                        S.ks_i[0] -= i1; S.ks_i[1] -= i2;
+                        S.ks_o[0] = df_sub(S.ks_o[0], o1); S.ks_o[1] = df_sub(S.ks_o[1], o2);
+                    }
                     K.bl = bin_of(plo, cstar, inv_bw); K.bh = bin_of(phi, cstar, inv_bw);
                     K.lo = plo; K.hi = phi;
                     K.nbl = c[1]; K.nbh = c[2];
@@ -611,73 +902,127 @@ __global__ void __launch_bounds__(MS_THREADS, 2) k_mesh_stats(MeshJob J) {
                 }
             }
             if (cont) {
+                kept_locate(S, K, (K.n - 1) / 2, lane, &bm[0], &rm[0]);
+                kept_locate(S, K, K.n / 2, lane, &bm[1], &rm[1]);
                 float mid[2];
-                kept_middle(S, sval, K, mid, lane);
-                if (lane == 0) {
-                    double mu, sd;
-                    kept_stats(KeptSums{S.ks_i[0], S.ks_i[1], S.ks_o[0], S.ks_o[1]}, K.n, cstar, unit, &mu, &sd);
-                    S.st[0] = 0.5 * ((double)mid[0] + (double)mid[1]);
-                    S.st[1] = mu;
-                    S.st[2] = sd;
-                }
-                if (it == J.maxiters) {
-                    cont = false;  // statistics of the set left after maxiters passes
+                bool have[2];
+#pragma unroll
+                for (int q = 0; q < 2; q++)
+                    have[q] = warp_value_of(S, St, bm[q], rm[q], K, cstar, inv_bw, lane, &mid[q]);
+                if (have[0] && have[1]) {
+                    state = warp0_finish(S, J, St, K, mid[0], mid[1], it, cstar, e, inv_bw, nsig, lane, &plo, &phi);
                 } else {
+                    // fetch the median bins that are not stored (both, so that a new
+                    // gather never drops one the old gather held): gather them when
+                    // they fit, else select from the mesh directly
+                    const bool u0 = !St.bin(bm[0]), u1 = !St.bin(bm[1]);
+                    const int gl = u0 ? bm[0] : bm[1], gh = u1 ? bm[1] : bm[0];
+                    const int need = (int)(S.hstart[gh + 1] - S.hstart[gl]);
                     if (lane == 0) {
-                        const double med = S.st[0], sd = S.st[2];
-                        const double blo = __dsub_rn(med, __dmul_rn(J.nsigma, sd));
-                        const double bhi = __dadd_rn(med, __dmul_rn(J.nsigma, sd));
-                        plo = fmaxf(K.lo, __double2float_ru(blo));
-                        phi = fminf(K.hi, __double2float_rd(bhi));
+                        S.bc_f[2] = K.lo; S.bc_f[3] = K.hi;
+                        S.bc_i[BI_NEED] = (!have[0]) | ((!have[1]) << 1);
+                        S.bc_i[BI_RB0] = bm[0]; S.bc_i[BI_RR0] = rm[0];
+                        S.bc_i[BI_RB1] = bm[1]; S.bc_i[BI_RR1] = rm[1];
+                        if (need <= MS_GCAP) {
+                            S.bc_i[BI_GL] = gl; S.bc_i[BI_GH] = gh; S.bc_i[BI_GCNT] = 0;
+                        }
                     }
-                    plo = __shfl_sync(0xffffffffu, plo, 0);
-                    phi = __shfl_sync(0xffffffffu, phi, 0);
-                    if (lane == 0) {
-                        S.bc_f[0] = plo; S.bc_f[1] = phi; S.bc_f[2] = K.lo; S.bc_f[3] = K.hi;
-                        S.bc_i[0] = K.bl; S.bc_i[1] = K.bh;
-                    }
+                    state = need <= MS_GCAP ? ST_GATHER : ST_RADIX;
                 }
             }
-            if (lane == 0) S.bc_i[4] = cont;
+            if (lane == 0) S.bc_i[BI_STATE] = state;
         }
         __syncthreads();
-        if (!S.bc_i[4]) break;
+        int state = S.bc_i[BI_STATE];
+        if (state == ST_STOP) break;
+        if (state != ST_SCAN) {  // fetch median bins (block-wide), then finish on warp 0
+            const float klo = S.bc_f[2], khi = S.bc_f[3];
+            if (state == ST_GATHER) {
+                const int gl = S.bc_i[BI_GL], gh = S.bc_i[BI_GH];
+                mesh_for_each(G, [&](float x) {
+                    const int b = bin_of(x, cstar, inv_bw);
+                    if (b >= gl && b <= gh) {
+                        const int p = atomicAdd(&S.bc_i[BI_GCNT], 1);
+                        if (p < MS_GCAP) S.gbuf[p] = x;
+                    }
+                });
+            } else {
+                const int needm = S.bc_i[BI_NEED];
+                for (int q = 0; q < 2; q++) {
+                    if (!((needm >> q) & 1)) continue;
+                    const float v = block_radix_select_global(S, G, klo, khi, S.bc_i[q ? BI_RB1 : BI_RB0], cstar,
+                                                              inv_bw, S.bc_i[q ? BI_RR1 : BI_RR0]);
+                    if (threadIdx.x == 0) S.bc_f[6 + q] = v;
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                float mid[2];
+                const int needm = S.bc_i[BI_NEED];
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    if (state == ST_RADIX && ((needm >> q) & 1)) mid[q] = S.bc_f[6 + q];
+                    else warp_value_of(S, St, bm[q], rm[q], K, cstar, inv_bw, lane, &mid[q]);
+                }
+                const int st2 = warp0_finish(S, J, St, K, mid[0], mid[1], it, cstar, e, inv_bw, nsig, lane, &plo, &phi);
+                if (lane == 0) S.bc_i[BI_STATE] = st2;
+            }
+            __syncthreads();
+            state = S.bc_i[BI_STATE];
+            if (state == ST_STOP) break;
+        }
         const float nlo = S.bc_f[0], nhi = S.bc_f[1], klo = S.bc_f[2], khi = S.bc_f[3];
-        const int kbl = S.bc_i[0], kbh = S.bc_i[1];
+        const int kbl = S.bc_i[BI_KBL], kbh = S.bc_i[BI_KBH];
+        const bool on_chip = S.bc_i[BI_MODE];
         const int nbl_bin = bin_of(nlo, cstar, inv_bw), nbh_bin = bin_of(nhi, cstar, inv_bw);
-        // values removed by this pass lie in bins [bl, nbl_bin] and [nbh_bin, bh]
         Sums rem{0, 0, df{0.f, 0.f}, df{0.f, 0.f}};
         int c[3] = {0, 0, 0};  // removed, kept in new bin bl, kept in new bin bh
-        {
-            const int a0 = S.hstart[kbl], a1 = S.hstart[nbl_bin + 1];
+        if (on_chip) {
+            // values removed by this pass lie in bins [bl, nbl_bin] and [nbh_bin, bh]
+            const int a0 = S.sstart[kbl], a1 = S.sstart[nbl_bin + 1];
             for (int k = a0 + (int)threadIdx.x; k < a1; k += MS_THREADS) {
-                const float x = sval[k];
+                const float x = S.store[k];
                 if (!(x >= klo && x <= khi)) continue;
                 if (x < nlo || x > nhi) { c[0]++; sums_add(rem, x, bin_of(x, cstar, inv_bw), cstar, fxs); }
-                else if (k >= (int)S.hstart[nbl_bin]) c[1]++;
+                else if (k >= (int)S.sstart[nbl_bin]) c[1]++;
             }
-            const int b0 = S.hstart[max(nbh_bin, nbl_bin + 1)], b1 = S.hstart[kbh + 1];
-            for (int k = b0 + (int)threadIdx.x; k < b1; k += MS_THREADS) {
-                const float x = sval[k];
-                if (!(x >= klo && x <= khi)) continue;
-                if (x < nlo || x > nhi) { c[0]++; sums_add(rem, x, bin_of(x, cstar, inv_bw), cstar, fxs); }
-                else if (k < (int)S.hstart[nbh_bin + 1] && nbh_bin != nbl_bin) c[2]++;
+            const int ub = max(nbh_bin, nbl_bin + 1);
+            if (ub <= kbh) {
+                const int b0 = S.sstart[ub], b1 = S.sstart[kbh + 1];
+                for (int k = b0 + (int)threadIdx.x; k < b1; k += MS_THREADS) {
+                    const float x = S.store[k];
+                    if (!(x >= klo && x <= khi)) continue;
+                    if (x < nlo || x > nhi) { c[0]++; sums_add(rem, x, bin_of(x, cstar, inv_bw), cstar, fxs); }
+                    else if (k < (int)S.sstart[nbh_bin + 1] && nbh_bin != nbl_bin) c[2]++;
+                }
             }
+        } else {
+            mesh_for_each(G, [&](float x) {
+                if (!(x >= klo && x <= khi)) return;
+                const int b = bin_of(x, cstar, inv_bw);
+                if (x < nlo || x > nhi) { c[0]++; sums_add(rem, x, b, cstar, fxs); }
+                else if (b == nbl_bin) c[1]++;
+                else if (b == nbh_bin) c[2]++;
+            });
         }
         warp_partial(S, rem, c, lane, warp);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double med = S.st[0], mu = S.st[1], sd = S.st[2];
-        double bk;
+        const df med = S.st[0], mu = S.st[1], sd = S.st[2];
+        df bk;
         switch (J.estimator) {
             case IPP_EST_MEDIAN: bk = med; break;
             case IPP_EST_MEAN: bk = mu; break;
-            case IPP_EST_FACTORS: bk = J.mf * med - J.mnf * mu; break;
-            default: bk = 2.5 * med - 1.5 * mu; break;
+            case IPP_EST_FACTORS: bk = df_sub(df_mul(df_from_d(J.mf), med), df_mul(df_from_d(J.mnf), mu)); break;
+            default: bk = df_sub(df_mul_f(med, 2.5f), df_mul_f(mu, 1.5f)); break;
         }
-        J.raw_bkg[mesh] = (float)bk;
-        J.raw_rms[mesh] = (float)sd;
+        const float b = __fadd_rn(bk.hi, bk.lo), r = __fadd_rn(sd.hi, sd.lo);
+        // values beyond ~1e19 from the window centre overflow the double-float
+        // outlier sums: such a mesh is reported invalid (and filled) rather than wrong
+        const bool ok = isfinite(b) && isfinite(r);
+        J.raw_bkg[mesh] = ok ? b : 0.f;
+        J.raw_rms[mesh] = ok ? r : -1.f;
     }
 }
 
@@ -876,34 +1221,15 @@ __global__ void __launch_bounds__(BG_THREADS) k_bg_subtract(SubJob J) {
 // ------------------------------------------------------------------ host side
 using namespace ipp;
 
-static int mesh_ppt(int area) {
-    if (area <= MS_THREADS * 8) return 8;
-    if (area <= MS_THREADS * 16) return 16;
-    if (area <= MS_THREADS * 32) return 32;
-    return 0;
-}
-
-size_t ipp_mesh_smem_bytes(int ppt) { return sizeof(MeshShared) + (size_t)ppt * MS_THREADS * sizeof(float); }
-
 int ipp_launch_mesh_stats(const MeshJob& J, cudaStream_t s) {
-    int ppt = mesh_ppt(J.mesh_w * J.mesh_h);
-    if (!ppt) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "mesh area %d > %d", J.mesh_w * J.mesh_h, MS_THREADS * 32);
-    size_t sm = ipp_mesh_smem_bytes(ppt);
-    int nm = J.nx * J.ny;
-    switch (ppt) {
-        case 8:
-            cudaFuncSetAttribute(k_mesh_stats<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_mesh_stats<8><<<nm, MS_THREADS, sm, s>>>(J);
-            break;
-        case 16:
-            cudaFuncSetAttribute(k_mesh_stats<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_mesh_stats<16><<<nm, MS_THREADS, sm, s>>>(J);
-            break;
-        default:
-            cudaFuncSetAttribute(k_mesh_stats<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_mesh_stats<32><<<nm, MS_THREADS, sm, s>>>(J);
-            break;
+    if (J.mesh_w * J.mesh_h > 16384)
+        return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "mesh area %d > 16384", J.mesh_w * J.mesh_h);
+    static bool carveout_set = false;  // seven 31 KB CTAs per SM need the largest shared-memory carveout
+    if (!carveout_set) {
+        cudaFuncSetAttribute(k_mesh_stats, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        carveout_set = true;
     }
+    k_mesh_stats<<<J.nx * J.ny, MS_THREADS, 0, s>>>(J);
     return ipp_check_launch("k_mesh_stats");
 }
 

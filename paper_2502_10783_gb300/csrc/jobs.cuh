@@ -117,6 +117,9 @@ int ipp_launch_bg_subtract(const ipp::SubJob& J, cudaStream_t s);
 size_t ipp_ccl_workspace_size(int64_t W, int64_t H);
 int ipp_launch_detect(const ipp::DetectArgs& A, cudaStream_t s);
 int ipp_launch_centroid(const ipp::CenJob& J, cudaStream_t s);
+int ipp_launch_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, const int32_t* n_src_dev,
+                         int32_t max_src, const float* x, const float* y, int S, float* stamps, float* weights,
+                         int32_t* origin, int32_t* flags, cudaStream_t s);
 int ipp_launch_aperture(const ipp::PhotJob& J, cudaStream_t s);
 int ipp_launch_psf_fit(const ipp::FitJob& J, cudaStream_t s);
 int ipp_launch_psf_fwd(const float* params, int64_t N, int S, int model, float beta, float* model_out, cudaStream_t s);

@@ -5,6 +5,8 @@
 // offset so that pixel offsets keep full FP32 precision anywhere in the frame.
 #include <math.h>
 
+#include <algorithm>
+
 #include "jobs.cuh"
 
 namespace ipp {
@@ -382,6 +384,45 @@ __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
     }
 }
 
+// Stamp cut: one thread per stamp pixel, grid-stride over the device-resident
+// count.  Consecutive threads take consecutive columns of a stamp row, so each
+// stamp row is one short contiguous read of the frame.
+__global__ void __launch_bounds__(P_THREADS) k_stamp_cut(const float* __restrict__ sub, int64_t W, int64_t H,
+                                                          int64_t pitch, const int32_t* n_src_dev, int32_t max_src,
+                                                          const float* __restrict__ x, const float* __restrict__ y,
+                                                          int S, float* __restrict__ stamps,
+                                                          float* __restrict__ weights, int32_t* __restrict__ origin,
+                                                          int32_t* __restrict__ flags) {
+    const int64_t n = min(*n_src_dev, max_src);
+    const int SS = S * S, half = S / 2;
+    const int64_t total = n * SS;
+    for (int64_t t = (int64_t)blockIdx.x * P_THREADS + threadIdx.x; t < total; t += (int64_t)gridDim.x * P_THREADS) {
+        const int64_t s = t / SS;
+        const int pix = (int)(t - s * SS);
+        const int r = pix / S, c = pix - r * S;
+        const float xs = x[s], ys = y[s];
+        const float lim = 1073741824.0f + (float)max(W, H);  // 2^30 px beyond the frame
+        const bool pos_ok = isfinite(xs) && isfinite(ys) && fabsf(xs) < lim && fabsf(ys) < lim;
+        int64_t ox = 0, oy = 0;
+        if (pos_ok) {  // floor(v + 1/2) without the rounding of v + 0.5f: v - floor(v) is exact
+            const float fx0 = floorf(xs), fy0 = floorf(ys);
+            ox = (int64_t)fx0 + (xs - fx0 >= 0.5f) - half;
+            oy = (int64_t)fy0 + (ys - fy0 >= 0.5f) - half;
+        }
+        const int64_t fy = oy + r, fx = ox + c;
+        const bool in = pos_ok && fy >= 0 && fy < H && fx >= 0 && fx < W;
+        stamps[t] = in ? __ldg(sub + fy * pitch + fx) : 0.f;
+        if (weights) weights[t] = in ? 1.f : 0.f;
+        if (pix == 0) {
+            if (origin) { origin[2 * s] = (int32_t)ox; origin[2 * s + 1] = (int32_t)oy; }
+            if (flags) {
+                const bool inside = pos_ok && ox >= 0 && oy >= 0 && ox + S <= W && oy + S <= H;
+                flags[s] = inside ? 0 : IPP_FLAG_EDGE;
+            }
+        }
+    }
+}
+
 }  // namespace ipp
 
 using namespace ipp;
@@ -406,4 +447,15 @@ int ipp_launch_aperture(const PhotJob& J, cudaStream_t s) {
     if (J.r_out > (float)ANN_MAXR) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "r_out above %d px", ANN_MAXR);
     k_aperture<<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
     return ipp_check_launch("k_aperture");
+}
+
+int ipp_launch_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, const int32_t* n_src_dev,
+                         int32_t max_src, const float* x, const float* y, int S, float* stamps, float* weights,
+                         int32_t* origin, int32_t* flags, cudaStream_t s) {
+    if (max_src <= 0) return IPP_OK;
+    const int64_t total = (int64_t)max_src * S * S;
+    const int64_t blocks = std::min<int64_t>((total + P_THREADS - 1) / P_THREADS, (int64_t)persistent_blocks(s) * 4);
+    k_stamp_cut<<<(unsigned)blocks, P_THREADS, 0, s>>>(sub, W, H, pitch, n_src_dev, max_src, x, y, S, stamps,
+                                                        weights, origin, flags);
+    return ipp_check_launch("k_stamp_cut");
 }

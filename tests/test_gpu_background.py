@@ -17,10 +17,10 @@ from gpu_util import dev, host, rel_close
 pytestmark = pytest.mark.gpu
 
 
-def _cmp_mesh(gb, gr, ob, orr, rtol=1e-5):
+def _cmp_mesh(gb, gr, ob, orr, rtol=1e-5, atol=1e-6):
     assert gb.shape == ob.shape
-    okb = rel_close(gb, ob, rtol, 1e-6)
-    okr = rel_close(gr, orr, rtol, 1e-6)
+    okb = rel_close(gb, ob, rtol, atol)
+    okr = rel_close(gr, orr, rtol, atol)
     assert okb.all(), f"bkg mismatch at {np.argwhere(~okb)[:5]}: {gb[~okb][:5]} vs {ob[~okb][:5]}"
     assert okr.all(), f"rms mismatch at {np.argwhere(~okr)[:5]}: {gr[~okr][:5]} vs {orr[~okr][:5]}"
 
@@ -142,3 +142,54 @@ def test_uint16_calibrated_input(gpu, orc):
     # reciprocal-multiply vs divide differ in the last bit of each pixel: the
     # mesh statistics of such values agree to ~1e-7 relative
     _cmp_mesh(host(gb), host(gr), ob, orr, rtol=2e-5)
+
+
+def _shaped_frame(kind, H=384, W=512, seed=0):
+    """Meshes whose value distributions exercise every branch of the clip: a
+    Gaussian sky, quantised (integer Poisson) values whose median bin holds
+    thousands of equal values, bimodal mixtures whose median and bounds move
+    into the core during the clip, heavy (Cauchy) tails, and one-sided
+    exponential skew."""
+    rng = np.random.default_rng(seed)
+    if kind == "gauss":
+        return rng.normal(1000, 30, (H, W)).astype(np.float32)
+    if kind == "poisson":
+        return rng.poisson(3.0, (H, W)).astype(np.float32)
+    if kind == "poisson_big":
+        return rng.poisson(40.0, (H, W)).astype(np.float32)
+    if kind == "bimodal":
+        m = rng.random((H, W)) < 0.15
+        return np.where(m, rng.normal(1060, 10, (H, W)), rng.normal(1000, 10, (H, W))).astype(np.float32)
+    if kind == "bimodal_wide":
+        m = rng.random((H, W)) < 0.35
+        return np.where(m, rng.normal(1300, 20, (H, W)), rng.normal(1000, 20, (H, W))).astype(np.float32)
+    if kind == "cauchy":
+        return (1000 + 5 * rng.standard_cauchy((H, W))).astype(np.float32)
+    if kind == "expo":
+        return (500 + rng.exponential(40, (H, W))).astype(np.float32)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind", ["gauss", "poisson", "poisson_big", "bimodal", "bimodal_wide", "cauchy", "expo"])
+@pytest.mark.parametrize("mesh", [128, 64])
+def test_bg_estimate_distribution_shapes(gpu, orc, kind, mesh):
+    img = _shaped_frame(kind, seed=sum(map(ord, kind)))
+    ob, orr, st = orc.bg_estimate(img, mesh=mesh)
+    gb, gr, rb, rr, status = gpu.bg_estimate(dev(img), mesh=mesh, raw=True)
+    v = st["valid"] == 1
+    _cmp_mesh(host(rb)[v], host(rr)[v], st["raw_bkg"][v], st["raw_rms"][v])
+    _cmp_mesh(host(gb), host(gr), ob, orr)
+
+
+@pytest.mark.parametrize("scale", [1e-20, 1e-6, 1e12])
+def test_bg_estimate_extreme_scales(gpu, orc, scale):
+    """Histogram windows far from unit scale: tiny values take the FP64
+    branch of the clip statistics, large ones the double-float branch."""
+    img, _ = synth.tiny_frame(256, 192, 91, n_stars=6)
+    img = (img.astype(np.float64) * scale).astype(np.float32)
+    ob, orr, st = orc.bg_estimate(img, mesh=64)
+    gb, gr, rb, rr, status = gpu.bg_estimate(dev(img), mesh=64, raw=True)
+    v = st["valid"] == 1
+    assert v.all()
+    _cmp_mesh(host(rb)[v], host(rr)[v], st["raw_bkg"][v], st["raw_rms"][v], atol=1e-30)
+    _cmp_mesh(host(gb), host(gr), ob, orr, atol=1e-30)
