@@ -1,18 +1,23 @@
 // detect.cu -- pixel detection and connection into candidates, with the
 // per-candidate pre-analysis of Sec. 2.2.5 (peak, total flux, ...).
 //
-// Tiles of TH x TW pixels, one CTA each.  k_tile_label thresholds a tile (or
-// takes a given mask) into shared-memory bit rows (keeping the tile's values
-// there for the statistics), cuts the rows into runs of
-// detected pixels and unites runs of adjacent rows that touch (8-connectivity)
-// with a union-find whose roots are the earliest run in raster order.
-// Components touching the tile border, or large enough, are kept and get a
-// node with their partial statistics; each run records its node for the final
-// write.  The global phase unites nodes across tile seams, folds the stats into
-// the roots, keeps roots of at least min_area pixels and numbers them by the
-// raster index of their first pixel (survivors bucketed by tile row; a block per
-// tile row ranks its bucket and adds the counts of earlier tile rows).  k_tile_final expands the runs into the label map, writing
-// every pixel once.  Nothing depends on the tile shape but the work split.
+// k_sub_thresh streams the frame in 32 x 128 tiles: Keys-interpolated
+// background and rms, sub = f - B (written once, float4), and the detection
+// mask sub > k rms(x, y) as bit rows (one 32-bit word per 32 pixels).  It is
+// HBM-bound and holds nothing but the node columns of its tile on chip.
+// k_tile_label then works from the bit rows alone (a given mask, in the parity
+// path): one CTA per 32 x 128 tile cuts the rows into runs of detected pixels
+// and unites runs of adjacent rows that touch (8-connectivity) with a
+// union-find whose roots are the earliest run in raster order.  Components
+// touching the tile border, or large enough, are kept and get a node with
+// their partial statistics (values read back from the subtracted frame for the
+// kept runs only); each run records its node for the final write.  The global
+// phase unites nodes across tile seams, folds the stats into the roots, keeps
+// roots of at least min_area pixels and numbers them by the raster index of
+// their first pixel (survivors bucketed by tile row; a block per tile row
+// ranks its bucket and adds the counts of earlier tile rows).  k_tile_final
+// expands the runs into the label map, writing every pixel once.  Nothing
+// depends on the tile shape but the work split.
 #include <algorithm>
 
 #include "jobs.cuh"
@@ -51,34 +56,37 @@ struct CclWs {
     int32_t bcap;        // capacity of one tile row's bucket = ntx * T_CAP
 };
 
-struct TileJob {
-    int mode;
+// Background subtraction + threshold into bit rows (streaming pass).
+struct SubThreshJob {
     int64_t W, H;
-    int ntx, nty;
-    // MODE_FUSED input
+    bool fused;                       // subtract the background from img and write sub
     const void* img; int dtype; int64_t pitch;
     const float* bias_map; float bias; const float* inv_flat;
     const float* mesh_bkg;
-    // sub: input (SUB_THRESH / MASK) or output (FUSED)
-    float* sub; int64_t sub_pitch;
+    float* sub; int64_t sub_pitch;    // output when fused, input otherwise
     const float* mesh_rms;
     int nx, ny, mesh_w, mesh_h;
     float k, thresh_abs;
+    uint32_t* mask;                   // [H][mw] bit rows, bit b of word w = column 32 w + b
+    int64_t mw;
+};
+
+struct TileJob {
+    int64_t W, H;
+    int ntx, nty;
+    const float* sub; int64_t sub_pitch;   // values of the statistics
+    const uint32_t* mask; int64_t mw;      // bit rows (row stride mw words)
     int min_area;
-    const uint32_t* mask_in;  // MODE_MASK: row stride ceil(W/32) words
     CclWs ws;
 };
 
 struct TileShared {
-    float cvb[T_TH][T_NQ];
-    float cvr[T_TH][T_NQ];
-    float val[T_TH][T_TW];           // the tile's background-subtracted values
     uint32_t mask[T_TH][T_WPR];
     int32_t roff[T_TH + 1];
     int16_t rs[T_RCAP], re[T_RCAP];  // run start / end column (inclusive)
     int32_t rpar[T_RCAP];            // union-find over runs
     int32_t rarea[T_RCAP];           // area at the root run; border flag in bit 30
-    int32_t rkid[T_RCAP];            // kept id at the root run, -1 if dropped
+    int16_t rkid[T_RCAP];            // kept id at the root run, -1 if dropped
     int32_t nruns, nkept;
     // statistics of the first T_KCAP kept components
     double k_sum[T_KCAP], k_sx[T_KCAP], k_sy[T_KCAP];
@@ -112,7 +120,7 @@ __device__ __forceinline__ bool mbit(const TileShared& S, int r, int c) {
     return (S.mask[r][c >> 5] >> (c & 31)) & 1u;
 }
 
-__device__ __forceinline__ float tile_load_pix(const TileJob& J, int64_t y, int64_t x) {
+__device__ __forceinline__ float tile_load_pix(const SubThreshJob& J, int64_t y, int64_t x) {
     if (J.dtype == IPP_F32) return __ldg(reinterpret_cast<const float*>(J.img) + y * J.pitch + x);
     float raw = (float)__ldg(reinterpret_cast<const uint16_t*>(J.img) + y * J.pitch + x);
     float b = J.bias_map ? __ldg(J.bias_map + y * J.W + x) : J.bias;
@@ -183,152 +191,271 @@ __device__ void tile_union(TileShared& S) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
+constexpr int ST_TH = 32, ST_TW = 128, ST_THREADS = 256;
+
+__global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh(SubThreshJob J) {
+    __shared__ float cvb[ST_TH][T_NQ], cvr[ST_TH][T_NQ];
+    const int64_t tx0 = (int64_t)blockIdx.x * ST_TW, ty0 = (int64_t)blockIdx.y * ST_TH;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // per row: vertical interpolation of the node columns this tile reads
+    const int qa = (int)floorf(((float)(int)tx0 + 0.5f) / J.mesh_w - 0.5f) - 1;
+    const int qz = (int)floorf(((float)((int)tx0 + ST_TW - 1) + 0.5f) / J.mesh_w - 0.5f) + 2;
+    const int qbase = max(qa, 0);
+    const int nq = min(min(qz, J.nx - 1) - qbase + 1, T_NQ);
+    const float refr = J.mesh_rms[0];
+    const float refb = J.fused ? J.mesh_bkg[0] : 0.f;
+    for (int t = threadIdx.x; t < ST_TH * nq; t += ST_THREADS) {
+        const int r = t / nq, qq = t - r * nq;
+        const int q = min(qbase + qq, J.nx - 1);
+        const float vy = ((float)((int)ty0 + r) + 0.5f) / J.mesh_h - 0.5f;
+        const float pf = floorf(vy);
+        float w[4];
+        keys_weights(vy - pf, w);
+        const int p0 = (int)pf;
+        float ab = 0.f, ar = 0.f;
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            const int p = clampi(p0 - 1 + a, 0, J.ny - 1);
+            ar = fmaf(w[a], J.mesh_rms[p * J.nx + q] - refr, ar);
+            if (J.fused) ab = fmaf(w[a], J.mesh_bkg[p * J.nx + q] - refb, ab);
+        }
+        cvr[r][qq] = ar;
+        cvb[r][qq] = ab;
+    }
+    __syncthreads();
+    const int64_t xc = tx0 + lane * 4;
+    float wx[4][4];
+    int q0c[4];  // first node column of each of the 4 pixels (node index = clamp(q0 - 1 + b))
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const float u = ((float)((int)xc + c) + 0.5f) / J.mesh_w - 0.5f;
+        const float qf = floorf(u);
+        keys_weights(u - qf, wx[c]);
+        q0c[c] = (int)qf;
+    }
+    auto qi = [&](int c, int b) { return min(clampi(q0c[c] - 1 + b, 0, J.nx - 1) - qbase, T_NQ - 1); };
+    const bool vin = (J.pitch % 4 == 0) && (((uintptr_t)J.img & 15) == 0) && J.dtype == IPP_F32;
+    const bool vsub = (J.sub_pitch % 4 == 0) && (((uintptr_t)J.sub & 15) == 0);
+    const bool full4 = xc + 4 <= J.W;
+    // the warp's rows: all loads first (several in flight per thread), then the arithmetic
+    constexpr int RPW = ST_TH / (ST_THREADS / 32);
+    float f[RPW][4];
+#pragma unroll
+    for (int q = 0; q < RPW; q++) {
+        const int64_t y = ty0 + warp + q * (ST_THREADS / 32);
+#pragma unroll
+        for (int c = 0; c < 4; c++) f[q][c] = 0.f;
+        if (y >= J.H || xc >= J.W) continue;
+        if (J.fused) {
+            if (vin && full4) {
+                const float4 t4 = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(J.img) + y * J.pitch + xc));
+                f[q][0] = t4.x; f[q][1] = t4.y; f[q][2] = t4.z; f[q][3] = t4.w;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? tile_load_pix(J, y, xc + c) : 0.f;
+            }
+        } else {
+            if (vsub && full4) {
+                const float4 t4 = __ldg(reinterpret_cast<const float4*>(J.sub + y * J.sub_pitch + xc));
+                f[q][0] = t4.x; f[q][1] = t4.y; f[q][2] = t4.z; f[q][3] = t4.w;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? __ldg(J.sub + y * J.sub_pitch + xc + c) : 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RPW; q++) {
+        const int r = warp + q * (ST_THREADS / 32);
+        const int64_t y = ty0 + r;
+        uint32_t nib = 0;
+        if (y < J.H && xc < J.W) {
+            if (J.fused) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int b = 0; b < 4; b++) acc = fmaf(wx[c][b], cvb[r][qi(c, b)], acc);
+                    f[q][c] = f[q][c] - (refb + acc);
+                }
+                if (vsub && full4) {
+                    *reinterpret_cast<float4*>(J.sub + y * J.sub_pitch + xc) =
+                        make_float4(f[q][0], f[q][1], f[q][2], f[q][3]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; c++)
+                        if (xc + c < J.W) J.sub[y * J.sub_pitch + xc + c] = f[q][c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                float acc = 0.f;
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc = fmaf(wx[c][b], cvr[r][qi(c, b)], acc);
+                const float thr = fmaxf(J.k * (refr + acc), J.thresh_abs);
+                if (xc + c < J.W && f[q][c] > thr) nib |= 1u << c;
+            }
+        }
+        // 8 lanes x 4 bits -> one 32-bit word of the row
+        uint32_t wv = nib << (4 * (lane & 7));
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 2);
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 4);
+        const int64_t wcol = (xc >> 5);
+        if ((lane & 7) == 0 && y < J.H && wcol < J.mw) J.mask[y * J.mw + wcol] = wv;
+    }
+}
+
+// Same pass with the horizontal Keys interpolation in polynomial form: per tile
+// row and node interval q0 the four (row-interpolated) node values give
+// B(t) = c0 + c1 t + c2 t^2 + c3 t^3, t = u - q0 (relative to the reference
+// node value, so a constant sky still subtracts to exactly 0); a pixel costs one
+// shared float4 and three FMAs per map.  For meshes of at least 16 px, where a
+// 128 px tile spans at most 9 intervals.
+constexpr int ST_NINT = 9;
+
+__device__ __forceinline__ float4 keys_poly(float d0, float d1, float d2, float d3) {
+    return make_float4(d1, 0.5f * (d2 - d0), d0 - 2.5f * d1 + 2.0f * d2 - 0.5f * d3,
+                       0.5f * (d3 - d0) + 1.5f * (d1 - d2));
+}
+
+__global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh_poly(SubThreshJob J) {
+    __shared__ float cvb[ST_TH][T_NQ], cvr[ST_TH][T_NQ];
+    __shared__ float4 pb[ST_TH][ST_NINT], pr[ST_TH][ST_NINT];
+    const int64_t tx0 = (int64_t)blockIdx.x * ST_TW, ty0 = (int64_t)blockIdx.y * ST_TH;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int qa = (int)floorf(((float)(int)tx0 + 0.5f) / J.mesh_w - 0.5f) - 1;
+    const int qz = (int)floorf(((float)((int)tx0 + ST_TW - 1) + 0.5f) / J.mesh_w - 0.5f) + 2;
+    const int qbase = max(qa, 0);
+    const int nq = min(min(qz, J.nx - 1) - qbase + 1, T_NQ);
+    const int q0min = qa + 1, nint = min(qz - 2 - q0min + 1, ST_NINT);
+    const float refr = J.mesh_rms[0];
+    const float refb = J.fused ? J.mesh_bkg[0] : 0.f;
+    for (int t = threadIdx.x; t < ST_TH * nq; t += ST_THREADS) {
+        const int r = t / nq, qq = t - r * nq;
+        const int q = min(qbase + qq, J.nx - 1);
+        const float vy = ((float)((int)ty0 + r) + 0.5f) / J.mesh_h - 0.5f;
+        const float pf = floorf(vy);
+        float w[4];
+        keys_weights(vy - pf, w);
+        const int p0 = (int)pf;
+        float ab = 0.f, ar = 0.f;
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            const int p = clampi(p0 - 1 + a, 0, J.ny - 1);
+            ar = fmaf(w[a], J.mesh_rms[p * J.nx + q] - refr, ar);
+            if (J.fused) ab = fmaf(w[a], J.mesh_bkg[p * J.nx + q] - refb, ab);
+        }
+        cvr[r][qq] = ar;
+        cvb[r][qq] = ab;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ST_TH * nint; t += ST_THREADS) {
+        const int r = t / nint, k = t - r * nint;
+        const int q0 = q0min + k;
+        int ix[4];
+#pragma unroll
+        for (int b = 0; b < 4; b++) ix[b] = min(clampi(q0 - 1 + b, 0, J.nx - 1) - qbase, T_NQ - 1);
+        pr[r][k] = keys_poly(cvr[r][ix[0]], cvr[r][ix[1]], cvr[r][ix[2]], cvr[r][ix[3]]);
+        if (J.fused) pb[r][k] = keys_poly(cvb[r][ix[0]], cvb[r][ix[1]], cvb[r][ix[2]], cvb[r][ix[3]]);
+    }
+    __syncthreads();
+    const int64_t xc = tx0 + lane * 4;
+    float tc[4];
+    int kc[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const float u = ((float)((int)xc + c) + 0.5f) / J.mesh_w - 0.5f;
+        const float qf = floorf(u);
+        tc[c] = u - qf;
+        kc[c] = min(max((int)qf - q0min, 0), ST_NINT - 1);
+    }
+    const bool vin = (J.pitch % 4 == 0) && (((uintptr_t)J.img & 15) == 0) && J.dtype == IPP_F32;
+    const bool vsub = (J.sub_pitch % 4 == 0) && (((uintptr_t)J.sub & 15) == 0);
+    const bool full4 = xc + 4 <= J.W;
+    constexpr int RPW = ST_TH / (ST_THREADS / 32);
+    float f[RPW][4];
+#pragma unroll
+    for (int q = 0; q < RPW; q++) {
+        const int64_t y = ty0 + warp + q * (ST_THREADS / 32);
+#pragma unroll
+        for (int c = 0; c < 4; c++) f[q][c] = 0.f;
+        if (y >= J.H || xc >= J.W) continue;
+        if (J.fused) {
+            if (vin && full4) {
+                const float4 t4 = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(J.img) + y * J.pitch + xc));
+                f[q][0] = t4.x; f[q][1] = t4.y; f[q][2] = t4.z; f[q][3] = t4.w;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? tile_load_pix(J, y, xc + c) : 0.f;
+            }
+        } else {
+            if (vsub && full4) {
+                const float4 t4 = __ldg(reinterpret_cast<const float4*>(J.sub + y * J.sub_pitch + xc));
+                f[q][0] = t4.x; f[q][1] = t4.y; f[q][2] = t4.z; f[q][3] = t4.w;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? __ldg(J.sub + y * J.sub_pitch + xc + c) : 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RPW; q++) {
+        const int r = warp + q * (ST_THREADS / 32);
+        const int64_t y = ty0 + r;
+        uint32_t nib = 0;
+        if (y < J.H && xc < J.W) {
+            if (J.fused) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const float4 P = pb[r][kc[c]];
+                    const float t = tc[c];
+                    f[q][c] = f[q][c] - (refb + fmaf(fmaf(fmaf(P.w, t, P.z), t, P.y), t, P.x));
+                }
+                if (vsub && full4) {
+                    *reinterpret_cast<float4*>(J.sub + y * J.sub_pitch + xc) =
+                        make_float4(f[q][0], f[q][1], f[q][2], f[q][3]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; c++)
+                        if (xc + c < J.W) J.sub[y * J.sub_pitch + xc + c] = f[q][c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float4 P = pr[r][kc[c]];
+                const float t = tc[c];
+                const float thr = fmaxf(J.k * (refr + fmaf(fmaf(fmaf(P.w, t, P.z), t, P.y), t, P.x)), J.thresh_abs);
+                if (xc + c < J.W && f[q][c] > thr) nib |= 1u << c;
+            }
+        }
+        uint32_t wv = nib << (4 * (lane & 7));
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 2);
+        wv |= __shfl_xor_sync(0xffffffffu, wv, 4);
+        const int64_t wcol = (xc >> 5);
+        if ((lane & 7) == 0 && y < J.H && wcol < J.mw) J.mask[y * J.mw + wcol] = wv;
+    }
+}
+
+__global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileShared& S = *reinterpret_cast<TileShared*>(smem_raw);
     const int tx = blockIdx.x, ty = blockIdx.y, tile = ty * J.ntx + tx;
     const int64_t tx0 = (int64_t)tx * T_TW, ty0 = (int64_t)ty * T_TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // ---- phase A: values, threshold, bit rows ------------------------------
-    const bool thresh = J.mode != MODE_MASK;
-    const bool fused = J.mode == MODE_FUSED;
-    int qbase = 0;
-    float refb = 0.f, refr = 0.f;
-    if (thresh) {
-        const int qa = (int)floorf(((float)(int)tx0 + 0.5f) / J.mesh_w - 0.5f) - 1;
-        const int qz = (int)floorf(((float)((int)tx0 + T_TW - 1) + 0.5f) / J.mesh_w - 0.5f) + 2;
-        qbase = max(qa, 0);
-        const int nq = min(min(qz, J.nx - 1) - qbase + 1, T_NQ);  // node columns this tile reads
-        refr = J.mesh_rms[0];
-        if (fused) refb = J.mesh_bkg[0];
-        for (int t = threadIdx.x; t < T_TH * nq; t += T_THREADS) {
-            const int r = t / nq, qq = t - r * nq;
-            const int q = min(qbase + qq, J.nx - 1);
-            const float vy = ((float)((int)ty0 + r) + 0.5f) / J.mesh_h - 0.5f;
-            const float pf = floorf(vy);
-            float w[4];
-            keys_weights(vy - pf, w);
-            const int p0 = (int)pf;
-            float ab = 0.f, ar = 0.f;
-#pragma unroll
-            for (int a = 0; a < 4; a++) {
-                const int p = clampi(p0 - 1 + a, 0, J.ny - 1);
-                ar = fmaf(w[a], J.mesh_rms[p * J.nx + q] - refr, ar);
-                if (fused) ab = fmaf(w[a], J.mesh_bkg[p * J.nx + q] - refb, ab);
-            }
-            S.cvr[r][qq] = ar;
-            S.cvb[r][qq] = ab;
+    // ---- phase A: the tile's bit rows (bits beyond W dropped) ---------------
+    if (threadIdx.x < T_TH * T_WPR) {
+        const int r = threadIdx.x / T_WPR, wi = threadIdx.x % T_WPR;
+        const int64_t y = ty0 + r, wcol = (tx0 >> 5) + wi;
+        uint32_t m = 0;
+        if (y < J.H && wcol < J.mw) {
+            m = __ldg(J.mask + y * J.mw + wcol);
+            const int64_t valid = J.W - 32 * wcol;
+            if (valid < 32) m &= valid > 0 ? ((1u << valid) - 1u) : 0u;
         }
-        __syncthreads();
-    }
-    {
-        const int64_t xc = tx0 + lane * 4;
-        float wx[4][4];
-        int qi[4][4];
-        if (thresh) {
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                const float u = ((float)((int)xc + c) + 0.5f) / J.mesh_w - 0.5f;
-                const float qf = floorf(u);
-                keys_weights(u - qf, wx[c]);
-                const int q0 = (int)qf;
-#pragma unroll
-                for (int b = 0; b < 4; b++) qi[c][b] = min(clampi(q0 - 1 + b, 0, J.nx - 1) - qbase, T_NQ - 1);
-            }
-        }
-        const bool vin = (J.pitch % 4 == 0) && (((uintptr_t)J.img & 15) == 0) && J.dtype == IPP_F32;
-        const bool vsub = (J.sub_pitch % 4 == 0) && (((uintptr_t)J.sub & 15) == 0);
-        const bool full4 = xc + 4 <= J.W;
-        // the warp's rows: all loads first (several in flight per thread), then
-        // the arithmetic; values go to shared memory for the stats phase
-        constexpr int RPW = T_TH / (T_THREADS / 32);  // rows per warp
-        float f[RPW][4];
-        uint32_t mbits[RPW];
-#pragma unroll
-        for (int q = 0; q < RPW; q++) {
-            const int r = warp + q * (T_THREADS / 32);
-            const int64_t y = ty0 + r;
-            mbits[q] = 0;
-#pragma unroll
-            for (int c = 0; c < 4; c++) f[q][c] = 0.f;
-            if (y >= J.H || xc >= J.W) continue;
-            if (J.mode == MODE_MASK) {
-                const int64_t mw = (J.W + 31) / 32;
-                const uint32_t word = __ldg(J.mask_in + y * mw + (xc >> 5));
-                mbits[q] = (word >> (xc & 31)) & 0xfu;
-                if (vsub && full4) {
-                    const float4 t4 = __ldg(reinterpret_cast<const float4*>(J.sub + y * J.sub_pitch + xc));
-                    f[q][0] = t4.x; f[q][1] = t4.y; f[q][2] = t4.z; f[q][3] = t4.w;
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? __ldg(J.sub + y * J.sub_pitch + xc + c) : 0.f;
-                }
-            } else if (fused) {
-                if (vin && full4) {
-                    const float4 t4 = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(J.img) + y * J.pitch + xc));
-                    f[q][0] = t4.x; f[q][1] = t4.y; f[q][2] = t4.z; f[q][3] = t4.w;
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? tile_load_pix(J, y, xc + c) : 0.f;
-                }
-            } else {
-                if (vsub && full4) {
-                    const float4 t4 = __ldg(reinterpret_cast<const float4*>(J.sub + y * J.sub_pitch + xc));
-                    f[q][0] = t4.x; f[q][1] = t4.y; f[q][2] = t4.z; f[q][3] = t4.w;
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? __ldg(J.sub + y * J.sub_pitch + xc + c) : 0.f;
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < RPW; q++) {
-            const int r = warp + q * (T_THREADS / 32);
-            const int64_t y = ty0 + r;
-            uint32_t nib = 0;
-            if (y < J.H && xc < J.W) {
-                if (J.mode == MODE_MASK) {
-                    // pixels beyond W were masked by the caller's padding bits: drop them
-#pragma unroll
-                    for (int c = 0; c < 4; c++)
-                        if (xc + c < J.W && ((mbits[q] >> c) & 1u)) nib |= 1u << c;
-                } else {
-                    if (fused) {
-#pragma unroll
-                        for (int c = 0; c < 4; c++) {
-                            float acc = 0.f;
-#pragma unroll
-                            for (int b = 0; b < 4; b++) acc = fmaf(wx[c][b], S.cvb[r][qi[c][b]], acc);
-                            f[q][c] = f[q][c] - (refb + acc);
-                        }
-                        if (vsub && full4) {
-                            *reinterpret_cast<float4*>(J.sub + y * J.sub_pitch + xc) =
-                                make_float4(f[q][0], f[q][1], f[q][2], f[q][3]);
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 4; c++)
-                                if (xc + c < J.W) J.sub[y * J.sub_pitch + xc + c] = f[q][c];
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        float acc = 0.f;
-#pragma unroll
-                        for (int b = 0; b < 4; b++) acc = fmaf(wx[c][b], S.cvr[r][qi[c][b]], acc);
-                        const float thr = fmaxf(J.k * (refr + acc), J.thresh_abs);
-                        if (xc + c < J.W && f[q][c] > thr) nib |= 1u << c;
-                    }
-                }
-            }
-            *reinterpret_cast<float4*>(&S.val[r][lane * 4]) = make_float4(f[q][0], f[q][1], f[q][2], f[q][3]);
-            // 8 lanes x 4 bits -> one 32-bit word
-            uint32_t wv = nib << (4 * (lane & 7));
-            wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
-            wv |= __shfl_xor_sync(0xffffffffu, wv, 2);
-            wv |= __shfl_xor_sync(0xffffffffu, wv, 4);
-            if ((lane & 7) == 0) S.mask[r][lane >> 3] = wv;
-        }
+        S.mask[r][wi] = m;
     }
     __syncthreads();
 
@@ -399,11 +526,18 @@ __global__ void __launch_bounds__(T_THREADS, 3) k_tile_label(TileJob J) {
         const int r = row_of_run(S, i);
         const int st = S.rs[i], en = S.re[i];
         float s0 = 0.f, s1 = 0.f, pk = -INFINITY;
-        for (int c = st; c <= en; c++) {
-            const float f = S.val[r][c];
-            s0 += f;
-            s1 = fmaf(f, (float)c, s1);
-            pk = fmaxf(pk, f);
+        const float* row = J.sub + (ty0 + r) * J.sub_pitch + tx0;
+        for (int c0 = st; c0 <= en; c0 += 8) {  // 8 loads in flight, summed in column order
+            float f[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) f[u] = c0 + u <= en ? __ldg(row + c0 + u) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (c0 + u <= en) {
+                    s0 += f[u];
+                    s1 = fmaf(f[u], (float)(c0 + u), s1);
+                    pk = fmaxf(pk, f[u]);
+                }
         }
         if (kid < T_KCAP) {
             atomicAdd(&S.k_sum[kid], (double)s0);
@@ -715,9 +849,10 @@ static CclLayout ccl_layout(int64_t W, int64_t H) {
         (size_t)(L.nty + 8) * 4,                               // counters + trcnt
         (size_t)L.nodes * 4,                                   // klist
         (size_t)L.nodes * 8, (size_t)L.nodes * 4,              // bucket first / node
+        (size_t)cdiv(W, 32) * (size_t)H * 4,                   // detection bit rows
     };
     size_t o = 0;
-    for (int k = 0; k < 24; k++) { L.off[k] = o; o += align256(sizes[k]); }
+    for (int k = 0; k < 25; k++) { L.off[k] = o; o += align256(sizes[k]); }
     L.total = o;
     return L;
 }
@@ -762,13 +897,29 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
     if (L.nodes >= (int64_t)INT32_MAX) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "frame too large for 32-bit node ids");
     CclWs w = ccl_ws(L, A.ws);
     TileJob J;
-    J.mode = A.mode; J.W = A.W; J.H = A.H; J.ntx = L.ntx; J.nty = L.nty;
-    J.img = A.img; J.dtype = A.dtype; J.pitch = A.pitch;
-    J.bias_map = A.bias_map; J.bias = A.bias; J.inv_flat = A.inv_flat;
-    J.mesh_bkg = A.mesh_bkg; J.sub = A.sub; J.sub_pitch = A.sub_pitch;
-    J.mesh_rms = A.mesh_rms; J.nx = A.nx; J.ny = A.ny; J.mesh_w = A.mesh_w; J.mesh_h = A.mesh_h;
-    J.k = A.k; J.thresh_abs = A.thresh_abs; J.min_area = A.min_area; J.mask_in = A.mask_in;
+    J.W = A.W; J.H = A.H; J.ntx = L.ntx; J.nty = L.nty;
+    J.sub = A.sub; J.sub_pitch = A.sub_pitch;
+    J.mw = cdiv(A.W, 32);
+    J.min_area = A.min_area;
     J.ws = w;
+    if (A.mode == MODE_MASK) {
+        J.mask = A.mask_in;
+    } else {  // subtract (fused) and threshold into the workspace's bit rows
+        SubThreshJob T;
+        T.W = A.W; T.H = A.H; T.fused = A.mode == MODE_FUSED;
+        T.img = A.img; T.dtype = A.dtype; T.pitch = A.pitch;
+        T.bias_map = A.bias_map; T.bias = A.bias; T.inv_flat = A.inv_flat;
+        T.mesh_bkg = A.mesh_bkg; T.sub = A.sub; T.sub_pitch = A.sub_pitch;
+        T.mesh_rms = A.mesh_rms; T.nx = A.nx; T.ny = A.ny; T.mesh_w = A.mesh_w; T.mesh_h = A.mesh_h;
+        T.k = A.k; T.thresh_abs = A.thresh_abs;
+        T.mask = (uint32_t*)((unsigned char*)A.ws + L.off[24]);
+        T.mw = J.mw;
+        dim3 sg((unsigned)cdiv(A.W, ST_TW), (unsigned)cdiv(A.H, ST_TH));
+        if (A.mesh_w >= 16) k_sub_thresh_poly<<<sg, ST_THREADS, 0, s>>>(T);
+        else k_sub_thresh<<<sg, ST_THREADS, 0, s>>>(T);
+        if (int e = ipp_check_launch("k_sub_thresh")) return e;
+        J.mask = T.mask;
+    }
     const size_t sm = sizeof(TileShared);
     cudaFuncSetAttribute(k_tile_label, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 tg(L.ntx, L.nty);

@@ -123,6 +123,114 @@ __global__ void __launch_bounds__(P_THREADS) k_centroid(CenJob J) {
     }
 }
 
+// Group variant: G lanes per source (32/G sources per warp), each lane caching
+// NPL box pixels in registers.  Same arithmetic per pixel as k_centroid; the
+// sums are reduced over the group only.
+template <int G, int NPL>
+__global__ void __launch_bounds__(P_THREADS) k_centroid_grp(CenJob J) {
+    const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int gid = (blockIdx.x * P_THREADS + threadIdx.x) / G;
+    const int ng = (gridDim.x * P_THREADS) / G;
+    const int n = min(*J.n_src_dev, J.max_src);
+    const float rad2 = J.rad * J.rad;
+    const float inv2s2 = 1.0f / (2.0f * J.sw * J.sw);
+    const float Wf = (float)(int)J.W, Hf = (float)(int)J.H;
+    const int R = (int)floorf(J.rad + 0.5f);
+    const int box = 2 * R + 1, nbox = box * box;
+    // offsets (dj, di) of the box pixels whose centre can come within rad of a
+    // centre at most 1/2 px from the anchor, in box order, shared by the block
+    // (registers are what limits the sources in flight)
+    __shared__ float2 offs[G * NPL];
+    __shared__ int n_offs;
+    if (threadIdx.x < 32) {
+        int cnt = 0;
+        for (int base = 0; base < nbox; base += 32) {
+            const int idx = base + lane;
+            const int di = idx / box - R, dj = idx % box - R;
+            const float a = fmaxf(fabsf((float)dj) - 0.5f, 0.f), b = fmaxf(fabsf((float)di) - 0.5f, 0.f);
+            const bool take = idx < nbox && a * a + b * b < rad2 * 1.0001f;
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+            if (take && pos < G * NPL) offs[pos] = make_float2((float)dj, (float)di);
+            cnt += __popc(bal);
+        }
+        if (lane == 0) n_offs = min(cnt, G * NPL);
+    }
+    __syncthreads();
+    const int noff = n_offs;
+    uint32_t inbox = 0;
+#pragma unroll
+    for (int m = 0; m < NPL; m++) inbox |= (uint32_t)(sub + G * m < noff) << m;
+    auto gsum = [&](float v) {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
+        return v;
+    };
+    for (int s = gid; s < n; s += ng) {
+        const float sx0 = J.x0[s], sy0 = J.y0[s];
+        float ax = rintf(sx0), ay = rintf(sy0);
+        float ox = sx0 - ax, oy = sy0 - ay;
+        int fl = IPP_FLAG_WIN_NOT_CONVERGED, it;
+        float cache[NPL];
+        uint32_t valid = 0;
+        float cax = NAN, cay = NAN;  // anchor of the cached pixels
+        for (it = 0; it < J.max_iter; it++) {
+            if (ax != cax || ay != cay) {  // (re)load the box around the anchor
+                const int64_t ia = (int)ay, ja = (int)ax;
+                valid = 0;
+#pragma unroll
+                for (int m = 0; m < NPL; m++) {
+                    const float2 o = offs[min(sub + G * m, G * NPL - 1)];
+                    const int64_t i = ia + (int)o.y, j = ja + (int)o.x;
+                    const bool ok = ((inbox >> m) & 1u) && i >= 0 && i < J.H && j >= 0 && j < J.W;
+                    cache[m] = ok ? __ldg(J.sub + i * J.pitch + j) : 0.f;
+                    valid |= (uint32_t)ok << m;
+                }
+                cax = ax;
+                cay = ay;
+            }
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int m = 0; m < NPL; m++) {
+                const float2 o = offs[min(sub + G * m, G * NPL - 1)];
+                const float dx = o.x - ox, dy = o.y - oy;
+                const float d2 = fmaf(dx, dx, dy * dy);
+                if (((valid >> m) & 1u) && d2 < rad2) {
+                    const float w = __expf(-d2 * inv2s2) * cache[m];
+                    s0 += w;
+                    s1 = fmaf(w, dx, s1);
+                    s2 = fmaf(w, dy, s2);
+                }
+            }
+            s0 = gsum(s0);
+            s1 = gsum(s1);
+            s2 = gsum(s2);
+            if (!(s0 > 0.f)) {  // keep the seed
+                ax = rintf(sx0); ay = rintf(sy0); ox = sx0 - ax; oy = sy0 - ay;
+                it++;
+                break;
+            }
+            const float ddx = 2.0f * s1 / s0, ddy = 2.0f * s2 / s0;
+            ox += ddx;
+            oy += ddy;
+            const float rx = rintf(ox), ry = rintf(oy);  // re-anchor: |offset| <= 1/2
+            ax += rx; ox -= rx;
+            ay += ry; oy -= ry;
+            if (ddx * ddx + ddy * ddy < J.tol2) { fl = 0; it++; break; }
+        }
+        const float xf = ax + ox, yf = ay + oy;
+        if (xf - J.rad < -0.5f || xf + J.rad > Wf - 0.5f || yf - J.rad < -0.5f || yf + J.rad > Hf - 0.5f)
+            fl |= IPP_FLAG_EDGE;
+        if (sub == 0) {
+            J.x[s] = xf;
+            J.y[s] = yf;
+            if (J.niter) J.niter[s] = it;
+            J.flags[s] = fl;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- aperture
 // Area of the disk of radius r centred at (cx, cy) -- coordinates relative to
 // the pixel centre -- intersected with the pixel [-1/2, 1/2]^2.  In disk-centred
@@ -297,69 +405,117 @@ __device__ float warp_median(const float* buf, int na, float* cand, int lane) {
     return (float)(0.5 * ((double)v0 + (double)v1));
 }
 
+// Warp 0: ordered list (row-major box order) of the offsets (di, dj), |di|,
+// |dj| <= R, that satisfy pred; returns the count.  Deterministic order keeps
+// the FP32 sums reproducible.
+template <class P>
+__device__ int build_offsets(int R, int16_t* out, int cap, int lane, P pred) {
+    const int box = 2 * R + 1;
+    int cnt = 0;
+    for (int base = 0; base < box * box; base += 32) {
+        const int idx = base + lane;
+        const int di = idx / box - R, dj = idx % box - R;
+        const bool take = idx < box * box && pred(di, dj);
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+        if (take && pos < cap) out[pos] = (int16_t)((di << 8) | (dj & 0xff));
+        cnt += __popc(bal);
+    }
+    return min(cnt, cap);
+}
+// offsets packed as two signed bytes (|di|, |dj| <= 17)
+__device__ __forceinline__ int off_di(int16_t o) { return o >> 8; }
+__device__ __forceinline__ int off_dj(int16_t o) { return (int)(int8_t)(o & 0xff); }
+
 __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
     __shared__ float ann[P_WARPS][ANN_CAP];
     __shared__ float cand[P_WARPS][32];
+    // pixel lists shared by the block, for any centre within 1/2 px of the anchor:
+    // aperture pixels always inside the disk (weight 1), pixels the disk edge may
+    // cross, and pixels whose centre may lie in the annulus
+    __shared__ int16_t l_ap[ANN_CAP], l_ann[ANN_CAP];  // aperture: inner pixels, then edge pixels
+    __shared__ int n_lists[3];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = (blockIdx.x * P_THREADS + threadIdx.x) >> 5;
     const int nw = (gridDim.x * P_THREADS) >> 5;
     const int n = min(*J.n_src_dev, J.max_src);
     float* buf = ann[wib];
     const float Wf = (float)(int)J.W, Hf = (float)(int)J.H;
-    const int R1 = (int)ceilf(J.r_ap + 1.0f) - 1, box1 = 2 * R1 + 1;  // pixels reaching within r_ap
-    const int R2 = (int)floorf(J.r_out + 0.5f), box2 = 2 * R2 + 1;  // centres within r_out of any offset <= 1/2
+    const int R1 = (int)ceilf(J.r_ap + 1.0f) - 1;  // pixels reaching within r_ap
+    const int R2 = (int)floorf(J.r_out + 0.5f);    // centres within r_out of any offset <= 1/2
     const double rin2d = __dmul_rn((double)J.r_in, (double)J.r_in);
     const double rout2d = __dmul_rn((double)J.r_out, (double)J.r_out);
     const float rin2 = (float)rin2d, rout2 = (float)rout2d;
+    if (wib == 0) {
+        const float r = J.r_ap, r2 = r * r;
+        // nearest / farthest point of the pixel square from a centre within 1/2 px
+        auto near2 = [](int di, int dj) {
+            const float a = fmaxf(fabsf((float)dj) - 1.0f, 0.f), b = fmaxf(fabsf((float)di) - 1.0f, 0.f);
+            return a * a + b * b;
+        };
+        auto far2 = [](int di, int dj) {
+            const float a = fabsf((float)dj) + 1.0f, b = fabsf((float)di) + 1.0f;
+            return a * a + b * b;
+        };
+        const int ni = build_offsets(R1, l_ap, ANN_CAP, lane, [&](int di, int dj) { return far2(di, dj) <= r2; });
+        const int ne = build_offsets(R1, l_ap + ni, ANN_CAP - ni, lane, [&](int di, int dj) {
+            return far2(di, dj) > r2 && near2(di, dj) < r2;
+        });
+        // annulus: the pixel centre's distance ranges over |p| +- sqrt(2)/2
+        const int na = build_offsets(R2, l_ann, ANN_CAP, lane, [&](int di, int dj) {
+            const float a = fmaxf(fabsf((float)dj) - 0.5f, 0.f), b = fmaxf(fabsf((float)di) - 0.5f, 0.f);
+            const float c = fabsf((float)dj) + 0.5f, d = fabsf((float)di) + 0.5f;
+            return a * a + b * b < rout2 * 1.0001f && c * c + d * d >= rin2 * 0.9999f;
+        });
+        if (lane == 0) { n_lists[0] = ni; n_lists[1] = ne; n_lists[2] = na; }
+    }
+    __syncthreads();
+    const int ni = n_lists[0], ne = n_lists[1], nac = n_lists[2];
     for (int s = gw; s < n; s += nw) {
         const float x = J.x[s], y = J.y[s];
         const float ax = rintf(x), ay = rintf(y);
         const float ox = x - ax, oy = y - ay;
         const int64_t ia = (int)ay, ja = (int)ax;
-        // aperture sum with exact overlap weights
+        // aperture sum with exact overlap weights: inner pixels weigh 1, the
+        // edge pixels' overlaps are computed (loads issued before the geometry)
         float sw = 0.f, swf = 0.f;
-        {
-            int di = lane / box1 - R1, dj = lane % box1 - R1;
-            const int sdi = 32 / box1, sdj = 32 % box1;
-            for (int idx = lane; idx < box1 * box1; idx += 32) {
-                const int64_t i = ia + di, j = ja + dj;
-                if (i >= 0 && i < J.H && j >= 0 && j < J.W) {
-                    const float w = circle_pixel_area(ox - (float)dj, oy - (float)di, J.r_ap);
-                    if (w > 0.f) {
-                        sw += w;
-                        swf = fmaf(w, __ldg(J.sub + i * J.pitch + j), swf);
-                    }
-                }
-                di += sdi;
-                dj += sdj;
-                if (dj > R1) { dj -= box1; di++; }
+        for (int t = lane; t < ni + ne; t += 32) {
+            const int16_t o = l_ap[t];
+            const int di = off_di(o), dj = off_dj(o);
+            const int64_t i = ia + di, j = ja + dj;
+            if (i < 0 || i >= J.H || j < 0 || j >= J.W) continue;
+            const float v = __ldg(J.sub + i * J.pitch + j);
+            const float w = t < ni ? 1.0f : circle_pixel_area(ox - (float)dj, oy - (float)di, J.r_ap);
+            if (w > 0.f) {  // pixels outside the aperture never touch the sums
+                sw += w;
+                swf = fmaf(w, v, swf);
             }
         }
         sw = warp_sum(sw);
         swf = warp_sum(swf);
-        // annulus values into the warp's buffer
+        // annulus values into the warp's buffer, NCH loads per lane in flight
         int na = 0;
         {
-            int di = lane / box2 - R2, dj = lane % box2 - R2;
-            const int sdi = 32 / box2, sdj = 32 % box2;
-            for (int base = 0; base < box2 * box2; base += 32) {
-                const int idx = base + lane;
-                bool take = false;
-                float v = 0.f;
-                if (idx < box2 * box2) {
+            constexpr int NCH = 4;
+            for (int base = 0; base < nac; base += 32 * NCH) {
+                float v[NCH];
+                bool take[NCH];
+#pragma unroll
+                for (int c = 0; c < NCH; c++) {
+                    const int t = base + 32 * c + lane;
+                    const int16_t o = t < nac ? l_ann[t] : (int16_t)0;
+                    const int di = off_di(o), dj = off_dj(o);
                     const int64_t i = ia + di, j = ja + dj;
-                    if (i >= 0 && i < J.H && j >= 0 && j < J.W &&
-                        in_annulus((float)dj - ox, (float)di - oy, i, j, x, y, rin2, rout2, rin2d, rout2d)) {
-                        take = true;
-                        v = __ldg(J.sub + i * J.pitch + j);
-                    }
+                    take[c] = t < nac && i >= 0 && i < J.H && j >= 0 && j < J.W &&
+                              in_annulus((float)dj - ox, (float)di - oy, i, j, x, y, rin2, rout2, rin2d, rout2d);
+                    v[c] = take[c] ? __ldg(J.sub + i * J.pitch + j) : 0.f;
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, take);
-                if (take) buf[na + __popc(bal & ((1u << lane) - 1u))] = v;
-                na += __popc(bal);
-                di += sdi;
-                dj += sdj;
-                if (dj > R2) { dj -= box2; di++; }
+#pragma unroll
+                for (int c = 0; c < NCH; c++) {
+                    const unsigned bal = __ballot_sync(0xffffffffu, take[c]);
+                    if (take[c]) buf[na + __popc(bal & ((1u << lane) - 1u))] = v[c];
+                    na += __popc(bal);
+                }
             }
         }
         __syncwarp();
@@ -434,10 +590,26 @@ static int persistent_blocks(cudaStream_t) {
     return sms > 0 ? sms * 4 : 512;
 }
 
+// A persistent grid of exactly the blocks that fit at once (one wave).
+template <class K>
+static int resident_blocks(K kernel, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, P_THREADS, smem) != cudaSuccess || per < 1) per = 1;
+    return (sms > 0 ? sms : 132) * per;
+}
+
 int ipp_launch_centroid(const CenJob& J, cudaStream_t s) {
     const int R = (int)floorf(J.rad + 0.5f);
     const int nbox = (2 * R + 1) * (2 * R + 1);
-    if (nbox <= 32 * 4) k_centroid<4><<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
+    int ncand = 0;  // pixels the group kernel lists (same test as on the device)
+    for (int di = -R; di <= R; di++)
+        for (int dj = -R; dj <= R; dj++) {
+            const float a = fmaxf(fabsf((float)dj) - 0.5f, 0.f), b = fmaxf(fabsf((float)di) - 0.5f, 0.f);
+            ncand += a * a + b * b < J.rad * J.rad * 1.0001f;
+        }
+    if (ncand <= 8 * 16) k_centroid_grp<8, 16><<<resident_blocks(k_centroid_grp<8, 16>, 0), P_THREADS, 0, s>>>(J);
     else if (nbox <= 32 * 8) k_centroid<8><<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
     else k_centroid<0><<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
     return ipp_check_launch("k_centroid");
@@ -445,7 +617,7 @@ int ipp_launch_centroid(const CenJob& J, cudaStream_t s) {
 
 int ipp_launch_aperture(const PhotJob& J, cudaStream_t s) {
     if (J.r_out > (float)ANN_MAXR) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "r_out above %d px", ANN_MAXR);
-    k_aperture<<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
+    k_aperture<<<resident_blocks(k_aperture, 0), P_THREADS, 0, s>>>(J);
     return ipp_check_launch("k_aperture");
 }
 
