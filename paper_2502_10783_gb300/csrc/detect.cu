@@ -52,8 +52,9 @@ struct CclWs {
     int32_t* counters;   // [0] kept nodes listed (zeroed by the host before the tile pass)
     int32_t* trcnt;      // [nty] surviving components per tile row (zeroed with counters)
     int32_t* klist;      // [ntiles*T_CAP] kept node ids, in no particular order
-    unsigned long long* bfirst; int32_t* bnode;  // per tile row: [nty][ntx*T_CAP] survivors
-    int32_t bcap;        // capacity of one tile row's bucket = ntx * T_CAP
+    int32_t* lpos;       // [nodes] tile-local index (row * T_TW + col) of the node's own first pixel
+    int32_t* pk;         // [nodes] rank of a surviving component among its home tile's survivors, else -1
+    int32_t* rowcnt;     // [ntiles][T_TH] survivors whose first pixel lies in that row of the tile
 };
 
 // Background subtraction + threshold into bit rows (streaming pass).
@@ -574,6 +575,7 @@ __global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) {
             J.ws.parent[node] = node;
             J.ws.area[node] = S.rarea[i] & ~BORDER_BIT;
             J.ws.first[node] = (unsigned long long)((ty0 + r) * J.W + tx0 + S.rs[i]);
+            J.ws.lpos[node] = r * T_TW + S.rs[i];
             if (kid < T_KCAP) {
                 const double sm = S.k_sum[kid];
                 J.ws.peak[node] = S.k_peak[kid];
@@ -683,95 +685,138 @@ __global__ void k_ccl_resolve(CclWs ws) {
     }
 }
 
-// roots of at least min_area pixels go to the bucket of the tile row holding
-// their first pixel; the others get label 0
-__global__ void k_ccl_survive(CclWs ws, int64_t W, int min_area) {
-    const int n = __ldcg(ws.counters);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const int node = ws.klist[t];
-        if (ws.parent[node] != node) continue;
-        if (ws.area[node] < min_area) { ws.label[node] = 0; continue; }
-        const unsigned long long f = ws.first[node];
-        const int tr = (int)((int64_t)(f / (unsigned long long)W) / T_TH);
-        const int slot = atomicAdd(&ws.trcnt[tr], 1);
-        ws.bfirst[(int64_t)tr * ws.bcap + slot] = f;
-        ws.bnode[(int64_t)tr * ws.bcap + slot] = node;
+// Numbering without a sort.  Labels follow the raster order of first pixels.
+// The first pixel of a component lies in one node's own runs (its home node,
+// in its home tile); within a tile, kept ids already follow the raster order of
+// the nodes' first pixels.  So a component's label is
+//   (survivors of earlier tile rows) + (survivors of this tile row whose first
+//   pixel lies in an earlier row, or in the same row in an earlier tile)
+//   + (its rank among its home tile's survivors of that row) + 1.
+// k_ccl_count: one block per tile, ranks the tile's home survivors in kept-id
+// order and counts them per row; dropped roots get label 0.
+constexpr int CN_THREADS = 128;
+__global__ void __launch_bounds__(CN_THREADS) k_ccl_count(CclWs ws, int64_t W, int ntx, int min_area) {
+    __shared__ int cnt[T_TH];
+    __shared__ int wsum[CN_THREADS / 32];
+    const int tile = blockIdx.x, ty = tile / ntx, tx = tile - ty * ntx;
+    const int64_t tx0 = (int64_t)tx * T_TW, ty0 = (int64_t)ty * T_TH;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < T_TH) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int nk = __ldcg(ws.nkept + tile);
+    int chunk0 = 0;
+    for (int base = 0; base < nk; base += CN_THREADS) {
+        const int k = base + threadIdx.x;
+        bool surv = false;
+        int r = 0;
+        if (k < nk) {
+            const int node = tile * T_CAP + k;
+            const int root = __ldcg(ws.parent + node);
+            const int lp = __ldcg(ws.lpos + node);
+            r = lp / T_TW;
+            const unsigned long long gf = (unsigned long long)((ty0 + r) * W + tx0 + (lp - r * T_TW));
+            const bool big = __ldcg(ws.area + root) >= min_area;
+            surv = big && __ldcg(ws.first + root) == gf;
+            if (root == node && !big) ws.label[node] = 0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, surv);
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        int before = chunk0, total = chunk0;
+        for (int w = 0; w < CN_THREADS / 32; w++) {
+            if (w < warp) before += wsum[w];
+            total += wsum[w];
+        }
+        if (k < nk) ws.pk[tile * T_CAP + k] = surv ? before + __popc(bal & ((1u << lane) - 1u)) : -1;
+        if (surv) atomicAdd(&cnt[r], 1);
+        __syncthreads();
+        chunk0 = total;
+    }
+    if (threadIdx.x < T_TH) ws.rowcnt[tile * T_TH + threadIdx.x] = cnt[threadIdx.x];
+    if (threadIdx.x == 0 && chunk0 > 0) atomicAdd(&ws.trcnt[ty], chunk0);
+}
+
+// k_ccl_scan: one block per tile row.  Exclusive scan of the (row, tile)
+// survivor counts in raster order; each (tile, row) entry of rowcnt is replaced
+// by the label offset of its survivors: (survivors of earlier tile rows) +
+// (scan value) - (the tile's survivors in earlier rows).
+constexpr int CL_THREADS = 256;
+__global__ void __launch_bounds__(CL_THREADS) k_ccl_scan(CclWs ws, int ntx, int nty, int32_t* n_src_dev) {
+    extern __shared__ int cl_smem[];
+    int* off = cl_smem;                   // [T_TH][ntx] counts, then their exclusive prefix
+    int* rstart = cl_smem + T_TH * ntx;   // [T_TH][ntx] survivors of the tile in earlier rows
+    __shared__ int red[CL_THREADS / 32];
+    __shared__ int carry;
+    const int ty = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int base = 0;  // survivors of earlier tile rows
+    for (int t = threadIdx.x; t < ty; t += CL_THREADS) base += __ldcg(ws.trcnt + t);
+    base = __reduce_add_sync(0xffffffffu, base);
+    if (lane == 0) red[warp] = base;
+    for (int i = threadIdx.x; i < T_TH * ntx; i += CL_THREADS) {
+        const int r = i / ntx, tx = i - r * ntx;
+        off[i] = __ldcg(ws.rowcnt + (int64_t)(ty * ntx + tx) * T_TH + r);
+    }
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    base = 0;
+    for (int w = 0; w < CL_THREADS / 32; w++) base += red[w];
+    for (int tx = threadIdx.x; tx < ntx; tx += CL_THREADS) {
+        int acc = 0;
+        for (int r = 0; r < T_TH; r++) { rstart[r * ntx + tx] = acc; acc += off[r * ntx + tx]; }
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < T_TH * ntx; c0 += CL_THREADS) {
+        const int i = c0 + threadIdx.x;
+        const int v = i < T_TH * ntx ? off[i] : 0;
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) red[warp] = inc;
+        __syncthreads();
+        int before = carry;
+        for (int w = 0; w < warp; w++) before += red[w];
+        if (i < T_TH * ntx) off[i] = before + inc - v;
+        __syncthreads();
+        if (threadIdx.x == CL_THREADS - 1) carry = before + inc;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && ty == nty - 1) *n_src_dev = base + carry;
+    for (int i = threadIdx.x; i < T_TH * ntx; i += CL_THREADS) {
+        const int r = i / ntx, tx = i - r * ntx;
+        ws.rowcnt[(int64_t)(ty * ntx + tx) * T_TH + r] = base + off[i] - rstart[i];
     }
 }
 
-// One block per tile row: label = (survivors of earlier tile rows) + (position
-// of the first pixel in this tile row's sorted bucket) + 1, i.e. raster order of
-// first pixels.  The bucket is sorted in shared memory by a bitonic network on
-// (first pixel, node) pairs; buckets beyond NB_SMEM entries fall back to ranking
-// by counting over global memory (only for pathological masks).
-constexpr int NB_THREADS = 512, NB_SMEM = 8192;
-constexpr size_t NB_DYN_SMEM = (size_t)NB_SMEM * (sizeof(unsigned long long) + sizeof(int));
-__global__ void __launch_bounds__(NB_THREADS) k_ccl_number(CclWs ws, int nty, int32_t max_src,
-                                                           ipp_src_stats out, int32_t* n_src_dev) {
-    extern __shared__ __align__(16) unsigned char nb_smem[];
-    unsigned long long* sk = reinterpret_cast<unsigned long long*>(nb_smem);
-    int* sn = reinterpret_cast<int*>(nb_smem + (size_t)NB_SMEM * sizeof(unsigned long long));
-    __shared__ int red[NB_THREADS / 32];
-    const int tr = blockIdx.x;
-    int base = 0;
-    for (int t = threadIdx.x; t < tr; t += NB_THREADS) base += __ldcg(ws.trcnt + t);
-    base = __reduce_add_sync(0xffffffffu, base);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = base;
-    __syncthreads();
-    base = 0;
-    for (int w = 0; w < NB_THREADS / 32; w++) base += red[w];
-    const int n = __ldcg(ws.trcnt + tr);
-    if (tr == nty - 1 && threadIdx.x == 0) *n_src_dev = base + n;
-    const unsigned long long* bf = ws.bfirst + (int64_t)tr * ws.bcap;
-    const int32_t* bn = ws.bnode + (int64_t)tr * ws.bcap;
-    auto emit = [&](int node, unsigned long long f, int lab) {
-        ws.label[node] = lab;
+// k_ccl_emit: one thread per kept node (all tiles): a home survivor writes its
+// component's label (offset + rank + 1) and catalog entry.
+__global__ void k_ccl_emit(CclWs ws, int32_t max_src, ipp_src_stats out) {
+    const int n = __ldcg(ws.counters);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int node = __ldcg(ws.klist + t);
+        const int p = __ldcg(ws.pk + node);
+        if (p < 0) continue;
+        const int tile = node / T_CAP;
+        const int r = __ldcg(ws.lpos + node) / T_TW;
+        const int lab = __ldcg(ws.rowcnt + (int64_t)tile * T_TH + r) + p + 1;
+        const int root = __ldcg(ws.parent + node);
+        ws.label[root] = lab;
         if (lab <= max_src) {
             const int k = lab - 1;
-            const double sm = ws.sum[node];
-            out.area[k] = ws.area[node];
-            out.first[k] = (int64_t)f;
-            out.xmin[k] = ws.xmin[node];
-            out.xmax[k] = ws.xmax[node];
-            out.ymin[k] = ws.ymin[node];
-            out.ymax[k] = ws.ymax[node];
-            out.peak[k] = fkey_inv(ws.peak[node]);
+            const double sm = __ldcg(ws.sum + root);
+            out.area[k] = __ldcg(ws.area + root);
+            out.first[k] = (int64_t)__ldcg(ws.first + root);
+            out.xmin[k] = __ldcg(ws.xmin + root);
+            out.xmax[k] = __ldcg(ws.xmax + root);
+            out.ymin[k] = __ldcg(ws.ymin + root);
+            out.ymax[k] = __ldcg(ws.ymax + root);
+            out.peak[k] = fkey_inv(__ldcg(ws.peak + root));
             out.flux[k] = (float)sm;
-            out.xbar[k] = (float)(ws.sx[node] / sm);
-            out.ybar[k] = (float)(ws.sy[node] / sm);
-        }
-    };
-    if (n <= NB_SMEM) {
-        int np = 1;
-        while (np < n) np <<= 1;
-        for (int i = threadIdx.x; i < np; i += NB_THREADS) {
-            sk[i] = i < n ? __ldcg(bf + i) : ~0ull;
-            sn[i] = i < n ? __ldcg(bn + i) : -1;
-        }
-        __syncthreads();
-        for (int k = 2; k <= np; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < np; i += NB_THREADS) {
-                    const int p = i ^ j;
-                    if (p > i) {
-                        const bool asc = (i & k) == 0;
-                        const unsigned long long a = sk[i], b = sk[p];
-                        if ((a > b) == asc) {
-                            sk[i] = b; sk[p] = a;
-                            const int t = sn[i]; sn[i] = sn[p]; sn[p] = t;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        for (int i = threadIdx.x; i < n; i += NB_THREADS) emit(sn[i], sk[i], base + i + 1);
-    } else {
-        for (int i = threadIdx.x; i < n; i += NB_THREADS) {
-            const unsigned long long f = __ldcg(bf + i);
-            int rank = 0;
-            for (int j = 0; j < n; j++) rank += __ldcg(bf + j) < f;
-            emit(__ldcg(bn + i), f, base + rank + 1);
+            out.xbar[k] = (float)(__ldcg(ws.sx + root) / sm);
+            out.ybar[k] = (float)(__ldcg(ws.sy + root) / sm);
         }
     }
 }
@@ -823,7 +868,7 @@ using namespace ipp;
 struct CclLayout {
     int ntx, nty;
     int64_t ntiles, nodes, runs;
-    size_t off[26];
+    size_t off[27];
     size_t total;
 };
 
@@ -848,11 +893,12 @@ static CclLayout ccl_layout(int64_t W, int64_t H) {
         (size_t)L.ntiles * T_TH * 4, (size_t)L.ntiles * T_TH * 4,  // blef brig
         (size_t)(L.nty + 8) * 4,                               // counters + trcnt
         (size_t)L.nodes * 4,                                   // klist
-        (size_t)L.nodes * 8, (size_t)L.nodes * 4,              // bucket first / node
+        (size_t)L.nodes * 4, (size_t)L.nodes * 4,              // lpos, pk
         (size_t)cdiv(W, 32) * (size_t)H * 4,                   // detection bit rows
+        (size_t)L.ntiles * T_TH * 4,                           // rowcnt
     };
     size_t o = 0;
-    for (int k = 0; k < 25; k++) { L.off[k] = o; o += align256(sizes[k]); }
+    for (int k = 0; k < 26; k++) { L.off[k] = o; o += align256(sizes[k]); }
     L.total = o;
     return L;
 }
@@ -883,9 +929,9 @@ static CclWs ccl_ws(const CclLayout& L, void* ws) {
     w.counters = (int32_t*)(b + L.off[20]);
     w.trcnt = w.counters + 8;
     w.klist = (int32_t*)(b + L.off[21]);
-    w.bfirst = (unsigned long long*)(b + L.off[22]);
-    w.bnode = (int32_t*)(b + L.off[23]);
-    w.bcap = L.ntx * T_CAP;
+    w.lpos = (int32_t*)(b + L.off[22]);
+    w.pk = (int32_t*)(b + L.off[23]);
+    w.rowcnt = (int32_t*)(b + L.off[25]);
     return w;
 }
 
@@ -935,11 +981,15 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
     const unsigned pg = (unsigned)std::max(sms, 1) * 8;  // persistent grid over the kept nodes
     k_ccl_resolve<<<pg, 256, 0, s>>>(w);
     if (int e = ipp_check_launch("k_ccl_resolve")) return e;
-    k_ccl_survive<<<pg, 256, 0, s>>>(w, A.W, A.min_area);
-    if (int e = ipp_check_launch("k_ccl_survive")) return e;
-    cudaFuncSetAttribute(k_ccl_number, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NB_DYN_SMEM);
-    k_ccl_number<<<L.nty, NB_THREADS, NB_DYN_SMEM, s>>>(w, L.nty, A.max_src, A.stats, A.n_src_dev);
-    if (int e = ipp_check_launch("k_ccl_number")) return e;
+    k_ccl_count<<<(unsigned)L.ntiles, CN_THREADS, 0, s>>>(w, A.W, L.ntx, A.min_area);
+    if (int e = ipp_check_launch("k_ccl_count")) return e;
+    const size_t lsm = (size_t)2 * T_TH * L.ntx * sizeof(int);
+    if (lsm > 200 * 1024) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "frame too wide for the labeling pass");
+    cudaFuncSetAttribute(k_ccl_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm);
+    k_ccl_scan<<<L.nty, CL_THREADS, lsm, s>>>(w, L.ntx, L.nty, A.n_src_dev);
+    if (int e = ipp_check_launch("k_ccl_scan")) return e;
+    k_ccl_emit<<<pg, 256, 0, s>>>(w, A.max_src, A.stats);
+    if (int e = ipp_check_launch("k_ccl_emit")) return e;
     k_tile_final<<<tg, T_THREADS, 0, s>>>(w, A.W, A.H, L.ntx, A.labels);
     return ipp_check_launch("k_tile_final");
 }

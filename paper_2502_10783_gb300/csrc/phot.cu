@@ -609,8 +609,9 @@ int ipp_launch_centroid(const CenJob& J, cudaStream_t s) {
             const float a = fmaxf(fabsf((float)dj) - 0.5f, 0.f), b = fmaxf(fabsf((float)di) - 0.5f, 0.f);
             ncand += a * a + b * b < J.rad * J.rad * 1.0001f;
         }
-    if (ncand <= 8 * 16) k_centroid_grp<8, 16><<<resident_blocks(k_centroid_grp<8, 16>, 0), P_THREADS, 0, s>>>(J);
-    else if (nbox <= 32 * 8) k_centroid<8><<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
+    (void)ncand;
+    if (nbox <= 32 * 4) k_centroid<4><<<resident_blocks(k_centroid<4>, 0), P_THREADS, 0, s>>>(J);
+    else if (nbox <= 32 * 8) k_centroid<8><<<resident_blocks(k_centroid<8>, 0), P_THREADS, 0, s>>>(J);
     else k_centroid<0><<<persistent_blocks(s), P_THREADS, 0, s>>>(J);
     return ipp_check_launch("k_centroid");
 }
