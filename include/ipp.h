@@ -317,6 +317,63 @@ int ipp_extract(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
                 const ipp_cen_params* cp, const ipp_phot_params* pp, int32_t max_src,
                 const ipp_catalog_out* out, void* ws, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------- batches */
+/*
+ * The catalog path over a batch of independent frames of mixed sizes (the
+ * batched form of ipp_extract; the paper runs every frame through the same
+ * steps, Sec. 2.1).  A runner spreads the frames over `lanes` CUDA streams of
+ * its own, forked from the caller's stream and joined back to it, assigning
+ * each frame to the least-loaded lane by pixel count (largest frames first),
+ * so that the small kernels of one frame overlap the large ones of another.
+ * ipp_batch_capture records a whole batch as one CUDA graph; ipp_batch_launch
+ * replays it with a single call (inputs are read from, and outputs written to,
+ * the pointers given at capture).
+ *
+ *   ipp_frame_desc   one frame: device image, type, size, pitch, optional
+ *                    calibration (host struct, read during the call) and the
+ *                    frame's catalog outputs (as for ipp_extract; sub has pitch W)
+ *   lanes            1..IPP_BATCH_MAX_LANES streams
+ *   ws               device workspace of ipp_batch_workspace_size() bytes for the
+ *                    largest frame of the batch; lanes do not share scratch
+ * Errors: IPP_ERR_INVALID_ARG for a bad frame (index in ipp_last_error_detail())
+ * before anything is enqueued; otherwise as ipp_extract.  The runner holds CUDA
+ * streams, events and at most one graph; ipp_batch_destroy releases them.
+ */
+#define IPP_BATCH_MAX_LANES 8
+
+typedef struct {
+    const void* img;
+    int32_t dtype;
+    int32_t reserved;
+    int64_t W, H, pitch;
+    const ipp_calib* cal;       /* host pointer, nullable */
+    ipp_catalog_out out;
+} ipp_frame_desc;
+
+typedef struct ipp_batch_s* ipp_batch;
+
+size_t ipp_batch_workspace_size(int64_t max_W, int64_t max_H, const ipp_bg_params* bp, int32_t lanes);
+int ipp_batch_create(int32_t lanes, ipp_batch* out);
+int ipp_batch_destroy(ipp_batch b);
+int ipp_batch_extract(ipp_batch b, const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp,
+                      const ipp_det_params* dp, const ipp_cen_params* cp, const ipp_phot_params* pp,
+                      int32_t max_src, void* ws, size_t ws_bytes, void* stream);
+int ipp_batch_capture(ipp_batch b, const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp,
+                      const ipp_det_params* dp, const ipp_cen_params* cp, const ipp_phot_params* pp,
+                      int32_t max_src, void* ws, size_t ws_bytes, void* stream);
+int ipp_batch_launch(ipp_batch b, void* stream);
+
+/*
+ * ipp_batch_autotune -- times ipp_batch_extract on this batch for 1, 2, 4 and 8
+ * lanes (two runs each after a warm-up, CUDA events on `stream`), and returns
+ * the fastest lane count in *best_lanes and the times in ms_per_lanes[4]
+ * (nullable).  Synchronises `stream`.  ws must be sized for 8 lanes.
+ */
+int ipp_batch_autotune(const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp,
+                       const ipp_det_params* dp, const ipp_cen_params* cp, const ipp_phot_params* pp,
+                       int32_t max_src, void* ws, size_t ws_bytes, void* stream, int32_t* best_lanes,
+                       float* ms_per_lanes);
+
 /* ---------------------------------------------------------------- PSF fit */
 /*
  * ipp_psf_fit -- batched Levenberg-Marquardt fit of an elliptical Moffat or

@@ -13,6 +13,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass
 
+import ctypes as C
+
 import torch
 
 from . import _abi
@@ -21,7 +23,7 @@ from ._abi import (  # noqa: F401
     FLAG_FIT_MAXITER, FLAG_FIT_SINGULAR, FLAG_WIN_NOT_CONVERGED, IppError, PSF_GAUSS, PSF_MOFFAT,
 )
 
-__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "stamp_cut",
+__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "stamp_cut", "Batch",
            "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
 
 
@@ -231,6 +233,28 @@ def stamp_cut(sub, x, y, n_src=None, S=15, max_src=None):
     return {k: v[:n] for k, v in out.items()}
 
 
+def _alloc_catalog(W, H, cfg, max_src, dev):
+    """Output tensors of one frame's catalog path and their C view."""
+    nx, ny = cfg.grid(W, H)
+    f32, i32 = torch.float32, torch.int32
+    o = dict(mesh_bkg=torch.empty((ny, nx), dtype=f32, device=dev))
+    o["mesh_rms"] = torch.empty_like(o["mesh_bkg"])
+    o["sub"] = torch.empty((H, W), dtype=f32, device=dev)
+    o["labels"] = torch.empty((H, W), dtype=i32, device=dev)
+    o["n_src"] = torch.zeros(1, dtype=i32, device=dev)
+    o["status"] = torch.zeros(1, dtype=i32, device=dev)
+    for key in ("x", "y", "flux", "sky", "area"):
+        o[key] = torch.empty(max_src, dtype=f32, device=dev)
+    for key in ("cen_flags", "n_ann", "phot_flags"):
+        o[key] = torch.empty(max_src, dtype=i32, device=dev)
+    stats = _alloc_stats(max_src, dev)
+    c_out = _abi.CatalogOut(
+        _ptr(o["mesh_bkg"]), _ptr(o["mesh_rms"]), _ptr(o["sub"]), _ptr(o["labels"]), _ptr(o["n_src"]),
+        _stats_c(stats), _ptr(o["x"]), _ptr(o["y"]), _ptr(o["cen_flags"]), _ptr(o["flux"]),
+        _ptr(o["sky"]), _ptr(o["area"]), _ptr(o["n_ann"]), _ptr(o["phot_flags"]), _ptr(o["status"]))
+    return o, stats, c_out
+
+
 class Extractor:
     """Preallocated outputs and workspace for repeated ipp_extract calls on
     frames of one shape (the per-frame path without allocations)."""
@@ -243,25 +267,7 @@ class Extractor:
         self.cfg = cfg or BgConfig()
         self.max_src = max_src if max_src is not None else max(4096, (W * H) // 256)
         dev = torch.device(device)
-        nx, ny = self.cfg.grid(W, H)
-        f32, i32 = torch.float32, torch.int32
-        o = dict(mesh_bkg=torch.empty((ny, nx), dtype=f32, device=dev))
-        o["mesh_rms"] = torch.empty_like(o["mesh_bkg"])
-        o["sub"] = torch.empty((H, W), dtype=f32, device=dev)
-        o["labels"] = torch.empty((H, W), dtype=i32, device=dev)
-        o["n_src"] = torch.zeros(1, dtype=i32, device=dev)
-        o["status"] = torch.zeros(1, dtype=i32, device=dev)
-        n = self.max_src
-        for key in ("x", "y", "flux", "sky", "area"):
-            o[key] = torch.empty(n, dtype=f32, device=dev)
-        for key in ("cen_flags", "n_ann", "phot_flags"):
-            o[key] = torch.empty(n, dtype=i32, device=dev)
-        self.stats = _alloc_stats(n, dev)
-        self.out = o
-        self.c_out = _abi.CatalogOut(
-            _ptr(o["mesh_bkg"]), _ptr(o["mesh_rms"]), _ptr(o["sub"]), _ptr(o["labels"]), _ptr(o["n_src"]),
-            _stats_c(self.stats), _ptr(o["x"]), _ptr(o["y"]), _ptr(o["cen_flags"]), _ptr(o["flux"]),
-            _ptr(o["sky"]), _ptr(o["area"]), _ptr(o["n_ann"]), _ptr(o["phot_flags"]), _ptr(o["status"]))
+        self.out, self.stats, self.c_out = _alloc_catalog(W, H, self.cfg, self.max_src, dev)
         self.bp = self.cfg.c()
         self.dp = _abi.DetParams(k, thresh_abs, min_area, 0)
         self.cp = _abi.CenParams(fwhm_win, cen_iter, tol2, 0)
@@ -279,6 +285,88 @@ class Extractor:
             _ptr(img), dtype, self.W, self.H, img.stride(0), cal, self.bp, self.dp, self.cp, self.pp,
             self.max_src, self.c_out, _ptr(self.ws), self.ws.numel(), s))
         return self.out
+
+
+class Batch:
+    """The catalog path over a fixed list of frames of mixed sizes (ipp_batch_*):
+    outputs preallocated per frame (self.outs, per-label statistics in
+    self.stats), frames spread over `lanes` CUDA streams.
+    run() enqueues the batch; capture() records it as one CUDA graph that
+    launch() replays (update the frames' contents in place between launches)."""
+
+    def __init__(self, frames, lanes=4, cfg: BgConfig | None = None, k=1.5, thresh_abs=0.0, min_area=5,
+                 fwhm_win=3.0, cen_iter=16, tol2=1e-8, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann=10,
+                 max_src=None, calib=None):
+        L = load()
+        self.L = L
+        self.cfg = cfg or BgConfig()
+        self.frames = list(frames)
+        if not self.frames:
+            raise ValueError("empty batch")
+        dev = self.frames[0].device
+        self.outs, self.stats, descs = [], [], []
+        self._keep = []
+        for img in self.frames:
+            _need_cuda(img, "frame")
+            H, W = img.shape
+            n = max_src if max_src is not None else max(4096, (W * H) // 256)
+            o, st, c_out = _alloc_catalog(W, H, self.cfg, n, dev)
+            self.stats.append(st)
+            dtype, cal = _frame(img, calib)
+            cal_p = C.pointer(cal) if cal is not None else None
+            self._keep.append((cal, cal_p))
+            self.outs.append(o)
+            self._nmax = min(getattr(self, "_nmax", n), n)
+            descs.append(_abi.FrameDesc(_ptr(img), dtype, 0, W, H, img.stride(0), cal_p, c_out))
+        self.max_src = self._nmax
+        self.descs = (_abi.FrameDesc * len(descs))(*descs)
+        self.n = len(descs)
+        self.bp = self.cfg.c()
+        self.dp = _abi.DetParams(k, thresh_abs, min_area, 0)
+        self.cp = _abi.CenParams(fwhm_win, cen_iter, tol2, 0)
+        self.pp = _abi.PhotParams(r_ap, r_in, r_out, min_ann)
+        mw = max(f.shape[1] for f in self.frames)
+        mh = max(f.shape[0] for f in self.frames)
+        need = L.ipp_batch_workspace_size(mw, mh, self.bp, _abi.IPP_BATCH_MAX_LANES)
+        self.ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        self.h = C.c_void_p()
+        self.lanes = lanes
+        _abi.check("ipp_batch_create", L.ipp_batch_create(lanes, C.byref(self.h)))
+
+    def _args(self):
+        return (self.descs, self.n, self.bp, self.dp, self.cp, self.pp, self.max_src, _ptr(self.ws), self.ws.numel())
+
+    def run(self, stream=None):
+        s = stream.cuda_stream if stream is not None else _stream()
+        _abi.check("ipp_batch_extract", self.L.ipp_batch_extract(self.h, *self._args(), s))
+        return self.outs
+
+    def capture(self, stream):
+        """Record the batch as a CUDA graph (stream: a torch.cuda.Stream, not the default)."""
+        _abi.check("ipp_batch_capture", self.L.ipp_batch_capture(self.h, *self._args(), stream.cuda_stream))
+
+    def launch(self, stream=None):
+        s = stream.cuda_stream if stream is not None else _stream()
+        _abi.check("ipp_batch_launch", self.L.ipp_batch_launch(self.h, s))
+        return self.outs
+
+    def autotune(self):
+        """Time 1, 2, 4, 8 lanes on this batch (synchronises); returns (best, ms per lane count)."""
+        best = C.c_int32(0)
+        ms = (C.c_float * 4)()
+        _abi.check("ipp_batch_autotune", self.L.ipp_batch_autotune(*self._args(), _stream(), C.byref(best), ms))
+        return best.value, list(ms)
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.ipp_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _BG_KEYS = ("mesh", "mesh_h", "filter_size", "maxiters", "min_valid", "nsigma", "estimator",

@@ -59,6 +59,14 @@ class CatalogOut(C.Structure):
                 ("sky", vp), ("area", vp), ("n_ann", vp), ("phot_flags", vp), ("status_dev", vp)]
 
 
+class FrameDesc(C.Structure):
+    _fields_ = [("img", vp), ("dtype", i32), ("reserved", i32), ("W", i64), ("H", i64), ("pitch", i64),
+                ("cal", C.POINTER(Calib)), ("out", CatalogOut)]
+
+
+IPP_BATCH_MAX_LANES = 8
+_par = [C.POINTER(BgParams), C.POINTER(DetParams), C.POINTER(CenParams), C.POINTER(PhotParams), i32]
+
 PROTOTYPES = {
     "ipp_status_string": ([i32], C.c_char_p),
     "ipp_last_error_detail": ([], C.c_char_p),
@@ -80,6 +88,14 @@ PROTOTYPES = {
     "ipp_extract_workspace_size": ([i64, i64, C.POINTER(BgParams)], sz),
     "ipp_extract": ([vp, i32, i64, i64, i64, C.POINTER(Calib), C.POINTER(BgParams), C.POINTER(DetParams),
                      C.POINTER(CenParams), C.POINTER(PhotParams), i32, C.POINTER(CatalogOut), vp, sz, vp], i32),
+    "ipp_batch_workspace_size": ([i64, i64, C.POINTER(BgParams), i32], sz),
+    "ipp_batch_create": ([i32, C.POINTER(vp)], i32),
+    "ipp_batch_destroy": ([vp], i32),
+    "ipp_batch_extract": ([vp, C.POINTER(FrameDesc), i32] + _par + [vp, sz, vp], i32),
+    "ipp_batch_capture": ([vp, C.POINTER(FrameDesc), i32] + _par + [vp, sz, vp], i32),
+    "ipp_batch_launch": ([vp, vp], i32),
+    "ipp_batch_autotune": ([C.POINTER(FrameDesc), i32] + _par + [vp, sz, vp, C.POINTER(i32), C.POINTER(f32)],
+                           i32),
     "ipp_psf_fit": ([vp, i64, i32, vp, vp, C.POINTER(FitParams), vp, vp, vp, vp, vp], i32),
     "ipp_psf_model_fwd": ([vp, i64, i32, C.POINTER(FitParams), vp, vp], i32),
     "ipp_psf_model_adj": ([vp, i64, i32, C.POINTER(FitParams), vp, vp, vp], i32),

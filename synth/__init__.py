@@ -8,6 +8,7 @@ path and the CPU oracle consume what it writes.
 from .frames import (  # noqa: F401
     FrameTruth,
     frame_field,
+    frame_field_device,
     frame_gradient_1k,
     frame_survey_4k,
     raw_calibrated_4k,

@@ -144,6 +144,43 @@ def frame_survey_4k(seed=1002, W=4096, H=4096, n_stars=20000):
     return img.astype(np.float32), truth
 
 
+def frame_field_device(W, H, n_stars, seed, sky_level=1000.0, grad=50.0, fwhm=3.0, logflux=(2.5, 5.0),
+                       device="cuda"):
+    """The frame_field recipe drawn with a seeded torch generator on the device
+    (for the large batches of the benchmark, where the host generator would
+    take minutes): uniform positions, log-uniform fluxes, pixel-integrated
+    Gaussians truncated at 6 sigma, linear x gradient, Poisson + read noise.
+    Returns a float32 H x W tensor on the device."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = torch.float64
+    x = torch.rand(n_stars, generator=g, device=device, dtype=f64) * W
+    y = torch.rand(n_stars, generator=g, device=device, dtype=f64) * H
+    a, b = logflux
+    flux = 10.0 ** (a + (b - a) * torch.rand(n_stars, generator=g, device=device, dtype=f64))
+    sig = fwhm * FWHM_TO_SIGMA
+    xh = 2.0 * torch.arange(W, device=device, dtype=f64) / max(W - 1, 1) - 1.0
+    expected = (sky_level + grad * xh)[None, :].expand(H, W).reshape(-1).clone()
+    R = int(np.ceil(6.0 * sig)) + 1
+    k = torch.arange(-R, R + 1, device=device, dtype=torch.int64)
+    phi = lambda t: 0.5 * (1.0 + torch.special.erf(t / np.sqrt(2.0)))
+    for s0 in range(0, n_stars, 8192):
+        xs, ys, fs = x[s0:s0 + 8192], y[s0:s0 + 8192], flux[s0:s0 + 8192]
+        jj = torch.round(xs).long()[:, None] + k[None, :]
+        ii = torch.round(ys).long()[:, None] + k[None, :]
+        ex = phi((jj + 0.5 - xs[:, None]) / sig) - phi((jj - 0.5 - xs[:, None]) / sig)
+        ey = phi((ii + 0.5 - ys[:, None]) / sig) - phi((ii - 0.5 - ys[:, None]) / sig)
+        ex = torch.where(((jj - xs[:, None]).abs() <= 6 * sig) & (jj >= 0) & (jj < W), ex, 0.0)
+        ey = torch.where(((ii - ys[:, None]).abs() <= 6 * sig) & (ii >= 0) & (ii < H), ey, 0.0)
+        val = fs[:, None, None] * ey[:, :, None] * ex[:, None, :]
+        idx = ii.clamp(0, H - 1)[:, :, None] * W + jj.clamp(0, W - 1)[:, None, :]
+        expected.index_add_(0, idx.reshape(-1), val.reshape(-1))
+    counts = torch.poisson(expected.clamp_min(0.0), generator=g)
+    img = counts + READ_NOISE * torch.randn(counts.shape, generator=g, device=device, dtype=f64)
+    return img.reshape(H, W).float()
+
+
 def mixed_batch_shapes(n_frames=64):
     """Frame shapes (W, H) of the mixed batch: 2048^2, 4096^2, 6144 x 6160 by i mod 3."""
     table = [(2048, 2048), (4096, 4096), (6144, 6160)]
