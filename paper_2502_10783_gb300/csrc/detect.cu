@@ -28,8 +28,12 @@ constexpr int T_TH = 32, T_TW = 128;
 constexpr int T_WPR = T_TW / 32;                 // mask words per tile row
 constexpr int T_CAP = (T_TH / 2) * (T_TW / 2);   // max 8-connected components in a tile
 constexpr int T_RCAP = T_TH * (T_TW / 2);        // max runs in a tile
-constexpr int T_KCAP = 256;                      // kept components with stats in shared memory
-constexpr int T_THREADS = 256;
+constexpr int T_THREADS = 128;
+// tile kernel capacities: the common pass keeps up to 1024 runs (and the stats
+// of 128 kept components) in shared memory, so ten tiles fit on an SM; tiles
+// with more runs are redone by a second pass with the full capacity
+constexpr int T_RCAP_FAST = 1024, KCAP_FAST = 128;
+constexpr int KCAP_FULL = 256;
 constexpr int T_NQ = 40;
 
 enum TileMode { MODE_SUB_THRESH = 0, MODE_MASK = 1, MODE_FUSED = 2 };
@@ -55,6 +59,7 @@ struct CclWs {
     int32_t* lpos;       // [nodes] tile-local index (row * T_TW + col) of the node's own first pixel
     int32_t* pk;         // [nodes] rank of a surviving component among its home tile's survivors, else -1
     int32_t* rowcnt;     // [ntiles][T_TH] survivors whose first pixel lies in that row of the tile
+    int32_t* ovf;        // [ntiles] tiles left to the full-capacity pass (count in counters[1])
 };
 
 // Background subtraction + threshold into bit rows (streaming pass).
@@ -81,23 +86,26 @@ struct TileJob {
     CclWs ws;
 };
 
+template <int RCAP, int KCAP>
 struct TileShared {
+    static constexpr int kRcap = RCAP, kKcap = KCAP;
     uint32_t mask[T_TH][T_WPR];
     int32_t roff[T_TH + 1];
-    int16_t rs[T_RCAP], re[T_RCAP];  // run start / end column (inclusive)
-    int32_t rpar[T_RCAP];            // union-find over runs
-    int32_t rarea[T_RCAP];           // area at the root run; border flag in bit 30
-    int16_t rkid[T_RCAP];            // kept id at the root run, -1 if dropped
+    int16_t rs[RCAP], re[RCAP];      // run start / end column (inclusive)
+    int32_t rpar[RCAP];              // union-find over runs
+    int32_t rarea[RCAP];             // area at the root run; border flag in bit 30
+    int16_t rkid[RCAP];              // kept id at the root run, -1 if dropped
     int32_t nruns, nkept;
-    // statistics of the first T_KCAP kept components
-    double k_sum[T_KCAP], k_sx[T_KCAP], k_sy[T_KCAP];
-    uint32_t k_peak[T_KCAP];
-    int32_t k_xmin[T_KCAP], k_xmax[T_KCAP], k_ymin[T_KCAP], k_ymax[T_KCAP];
-    int32_t wsum[T_THREADS / 32];  // >= 2 * (T_TH * T_WPR / 32) for the run scan
+    // statistics of the first KCAP kept components
+    double k_sum[KCAP], k_sx[KCAP], k_sy[KCAP];
+    uint32_t k_peak[KCAP];
+    int32_t k_xmin[KCAP], k_xmax[KCAP], k_ymin[KCAP], k_ymax[KCAP];
+    int32_t wsum[2 * (T_TH * T_WPR / 32) > T_THREADS / 32 ? 2 * (T_TH * T_WPR / 32) : T_THREADS / 32];
 };
+using TileFast = TileShared<T_RCAP_FAST, KCAP_FAST>;
+using TileFull = TileShared<T_RCAP, KCAP_FULL>;
 
 constexpr int BORDER_BIT = 1 << 30;
-static_assert(T_THREADS / 32 >= 2 * (T_TH * T_WPR / 32), "run scan uses 2 x (mask words / 32) partial sums");
 static_assert(T_TH * T_WPR <= T_THREADS, "one thread per mask word");
 
 __device__ __forceinline__ int rfind(const int32_t* P, int x) {
@@ -117,7 +125,8 @@ __device__ __forceinline__ void runite(int32_t* P, int a, int b) {
         b = old;
     }
 }
-__device__ __forceinline__ bool mbit(const TileShared& S, int r, int c) {
+template <class SH>
+__device__ __forceinline__ bool mbit(const SH& S, int r, int c) {
     return (S.mask[r][c >> 5] >> (c & 31)) & 1u;
 }
 
@@ -128,7 +137,8 @@ __device__ __forceinline__ float tile_load_pix(const SubThreshJob& J, int64_t y,
     return (raw - b) * __ldg(J.inv_flat + y * J.W + x);
 }
 
-__device__ __forceinline__ int row_of_run(const TileShared& S, int i) {  // largest r with roff[r] <= i
+template <class SH>
+__device__ __forceinline__ int row_of_run(const SH& S, int i) {  // largest r with roff[r] <= i
     int a = 0, b = T_TH - 1;
     while (a < b) { const int m = (a + b + 1) >> 1; if (S.roff[m] <= i) a = m; else b = m - 1; }
     return a;
@@ -138,7 +148,8 @@ __device__ __forceinline__ int row_of_run(const TileShared& S, int i) {  // larg
 // mask word: run starts are set bits whose left neighbour is clear, run ends set
 // bits whose right neighbour is clear (neighbours across word edges included);
 // the k-th start and the k-th end of the tile bound the k-th run.
-__device__ void tile_runs(TileShared& S) {
+template <class SH>
+__device__ void tile_runs(SH& S) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     uint32_t st = 0, en = 0;
     if (t < T_TH * T_WPR) {
@@ -156,11 +167,19 @@ __device__ void tile_runs(TileShared& S) {
         const int a = __shfl_up_sync(0xffffffffu, is, o), b = __shfl_up_sync(0xffffffffu, ie, o);
         if (lane >= o) { is += a; ie += b; }
     }
-    if (lane == 31 && warp < (T_TH * T_WPR) / 32) { S.wsum[warp] = is; S.wsum[4 + warp] = ie; }
+    constexpr int NWW = (T_TH * T_WPR) / 32;  // warps holding mask words
+    if (lane == 31 && warp < NWW) { S.wsum[warp] = is; S.wsum[NWW + warp] = ie; }
     __syncthreads();
+    int total = 0;
+    for (int k = 0; k < NWW; k++) total += S.wsum[k];
+    if (total > SH::kRcap) {  // more runs than this pass holds: the tile is redone by the full pass
+        if (t == 0) S.nruns = -1;
+        __syncthreads();
+        return;
+    }
     if (t < T_TH * T_WPR) {
         int bs = 0, be = 0;
-        for (int k = 0; k < warp; k++) { bs += S.wsum[k]; be += S.wsum[4 + k]; }
+        for (int k = 0; k < warp; k++) { bs += S.wsum[k]; be += S.wsum[NWW + k]; }
         int ps = bs + is - cs, pe = be + ie - ce;
         if (t % T_WPR == 0) S.roff[t / T_WPR] = ps;
         const int base = (t % T_WPR) * 32;
@@ -174,7 +193,8 @@ __device__ void tile_runs(TileShared& S) {
 // Union-find over the runs of the tile: run i of row r joins the runs of row
 // r - 1 that overlap [start - 1, end + 1] (8-connectivity).  Roots end up as the
 // smallest run id of the component (its first run in raster order).
-__device__ void tile_union(TileShared& S) {
+template <class SH>
+__device__ void tile_union(SH& S) {
     const int nr = S.nruns;
     for (int i = threadIdx.x; i < nr; i += T_THREADS) S.rpar[i] = i;
     __syncthreads();
@@ -439,12 +459,15 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh_poly(SubThreshJob 
     }
 }
 
-__global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileShared& S = *reinterpret_cast<TileShared*>(smem_raw);
-    const int tx = blockIdx.x, ty = blockIdx.y, tile = ty * J.ntx + tx;
+// One tile, all threads of the block.  Returns false, having written nothing
+// to global memory, when the tile has more runs than SH holds.
+template <class SH>
+__device__ bool tile_label_body(const TileJob& J, SH& S, int tile) {
+    constexpr int KCAP = SH::kKcap;
+    const int ty = tile / J.ntx, tx = tile - ty * J.ntx;
     const int64_t tx0 = (int64_t)tx * T_TW, ty0 = (int64_t)ty * T_TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();  // shared state of a previous tile of this block is dead
 
     // ---- phase A: the tile's bit rows (bits beyond W dropped) ---------------
     if (threadIdx.x < T_TH * T_WPR) {
@@ -462,6 +485,7 @@ __global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) {
 
     // ---- phase B/C: runs and their union-find --------------------------------
     tile_runs(S);
+    if (S.nruns < 0) return false;
     tile_union(S);
     const int nr = S.nruns;
 
@@ -502,16 +526,16 @@ __global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) {
     }
     __syncthreads();
     const int nk = S.nkept;
-    for (int c = threadIdx.x; c < min(nk, T_KCAP); c += T_THREADS) {
+    for (int c = threadIdx.x; c < min(nk, KCAP); c += T_THREADS) {
         S.k_sum[c] = 0.0; S.k_sx[c] = 0.0; S.k_sy[c] = 0.0;
         S.k_peak[c] = 0u;
         S.k_xmin[c] = T_TW; S.k_xmax[c] = -1; S.k_ymin[c] = T_TH; S.k_ymax[c] = -1;
     }
     // kept components beyond the shared tables accumulate in the global node
-    // arrays directly (only masks with more than T_KCAP kept components per tile)
+    // arrays directly (only masks with more than KCAP kept components per tile)
     for (int i = threadIdx.x; i < nr; i += T_THREADS) {
         const int kid = (S.rpar[i] == i) ? S.rkid[i] : -1;
-        if (kid >= T_KCAP) {
+        if (kid >= KCAP) {
             const int node = tile * T_CAP + kid;
             J.ws.sum[node] = 0.0; J.ws.sx[node] = 0.0; J.ws.sy[node] = 0.0;
             J.ws.peak[node] = 0u;
@@ -540,7 +564,7 @@ __global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) {
                     pk = fmaxf(pk, f[u]);
                 }
         }
-        if (kid < T_KCAP) {
+        if (kid < KCAP) {
             atomicAdd(&S.k_sum[kid], (double)s0);
             atomicAdd(&S.k_sx[kid], (double)s1);
             atomicAdd(&S.k_sy[kid], (double)s0 * (double)r);
@@ -576,7 +600,7 @@ __global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) {
             J.ws.area[node] = S.rarea[i] & ~BORDER_BIT;
             J.ws.first[node] = (unsigned long long)((ty0 + r) * J.W + tx0 + S.rs[i]);
             J.ws.lpos[node] = r * T_TW + S.rs[i];
-            if (kid < T_KCAP) {
+            if (kid < KCAP) {
                 const double sm = S.k_sum[kid];
                 J.ws.peak[node] = S.k_peak[kid];
                 J.ws.xmin[node] = (int)tx0 + S.k_xmin[kid];
@@ -613,6 +637,28 @@ __global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) {
         }
         *dst = v;
     }
+    return true;
+}
+
+// Common pass: one tile per block with the small capacities; tiles that do not
+// fit are listed for the full pass.
+__global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileFast& S = *reinterpret_cast<TileFast*>(smem_raw);
+    const int tile = blockIdx.y * J.ntx + blockIdx.x;
+    if (!tile_label_body(J, S, tile) && threadIdx.x == 0) {
+        const int slot = atomicAdd(&J.ws.counters[1], 1);
+        J.ws.ovf[slot] = tile;
+    }
+}
+
+// Full pass over the listed tiles (any mask fits: T_RCAP is the most runs a
+// tile can have).
+__global__ void __launch_bounds__(T_THREADS) k_tile_label_full(TileJob J) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileFull& S = *reinterpret_cast<TileFull*>(smem_raw);
+    const int n = __ldcg(J.ws.counters + 1);
+    for (int i = blockIdx.x; i < n; i += gridDim.x) tile_label_body(J, S, __ldcg(J.ws.ovf + i));
 }
 
 // ------------------------------------------------------------ global phase
@@ -823,16 +869,17 @@ __global__ void k_ccl_emit(CclWs ws, int32_t max_src, ipp_src_stats out) {
 
 // Second tile pass: expand the tile's runs into the label map (0 for
 // background and dropped components), writing every pixel once, coalesced.
-__global__ void __launch_bounds__(T_THREADS) k_tile_final(CclWs ws, int64_t W, int64_t H, int ntx,
+constexpr int TF_THREADS = 256;
+__global__ void __launch_bounds__(TF_THREADS) k_tile_final(CclWs ws, int64_t W, int64_t H, int ntx,
                                                          int32_t* labels) {
     __shared__ __align__(16) int32_t lab[T_TH][T_TW];
     const int tx = blockIdx.x, ty = blockIdx.y, tile = ty * ntx + tx;
     const int64_t tx0 = (int64_t)tx * T_TW, ty0 = (int64_t)ty * T_TH;
     int4* l4 = reinterpret_cast<int4*>(&lab[0][0]);
-    for (int t = threadIdx.x; t < T_TH * T_TW / 4; t += T_THREADS) l4[t] = make_int4(0, 0, 0, 0);
+    for (int t = threadIdx.x; t < T_TH * T_TW / 4; t += TF_THREADS) l4[t] = make_int4(0, 0, 0, 0);
     __syncthreads();
     const int nr = ws.nruns[tile];
-    for (int i = threadIdx.x; i < nr; i += T_THREADS) {
+    for (int i = threadIdx.x; i < nr; i += TF_THREADS) {
         const int node = __ldcg(ws.run_node + (int64_t)tile * T_RCAP + i);
         if (node < 0) continue;
         const int v = __ldcg(ws.label + __ldcg(ws.parent + node));
@@ -845,7 +892,7 @@ __global__ void __launch_bounds__(T_THREADS) k_tile_final(CclWs ws, int64_t W, i
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t xc = tx0 + lane * 4;
     const bool vec = (W % 4 == 0) && (((uintptr_t)labels & 15) == 0) && (xc + 4 <= W);
-    for (int r = warp; r < T_TH; r += T_THREADS / 32) {
+    for (int r = warp; r < T_TH; r += TF_THREADS / 32) {
         const int64_t y = ty0 + r;
         if (y >= H || xc >= W) continue;
         const int4 o = *reinterpret_cast<const int4*>(&lab[r][lane * 4]);
@@ -868,7 +915,7 @@ using namespace ipp;
 struct CclLayout {
     int ntx, nty;
     int64_t ntiles, nodes, runs;
-    size_t off[27];
+    size_t off[28];
     size_t total;
 };
 
@@ -896,9 +943,10 @@ static CclLayout ccl_layout(int64_t W, int64_t H) {
         (size_t)L.nodes * 4, (size_t)L.nodes * 4,              // lpos, pk
         (size_t)cdiv(W, 32) * (size_t)H * 4,                   // detection bit rows
         (size_t)L.ntiles * T_TH * 4,                           // rowcnt
+        (size_t)L.ntiles * 4,                                  // ovf
     };
     size_t o = 0;
-    for (int k = 0; k < 26; k++) { L.off[k] = o; o += align256(sizes[k]); }
+    for (int k = 0; k < 27; k++) { L.off[k] = o; o += align256(sizes[k]); }
     L.total = o;
     return L;
 }
@@ -932,6 +980,7 @@ static CclWs ccl_ws(const CclLayout& L, void* ws) {
     w.lpos = (int32_t*)(b + L.off[22]);
     w.pk = (int32_t*)(b + L.off[23]);
     w.rowcnt = (int32_t*)(b + L.off[25]);
+    w.ovf = (int32_t*)(b + L.off[26]);
     return w;
 }
 
@@ -966,13 +1015,21 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
         if (int e = ipp_check_launch("k_sub_thresh")) return e;
         J.mask = T.mask;
     }
-    const size_t sm = sizeof(TileShared);
-    cudaFuncSetAttribute(k_tile_label, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_tile_label, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileFast));
+    cudaFuncSetAttribute(k_tile_label_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileFull));
     dim3 tg(L.ntx, L.nty);
-    // the kept-node counter and the per-tile-row counts start at zero
+    // the kept-node counter, the overflow count and the per-tile-row counts start at zero
     if (cudaMemsetAsync(w.counters, 0, (size_t)(L.nty + 8) * 4, s) != cudaSuccess) return ipp_check_launch("memset");
-    k_tile_label<<<tg, T_THREADS, sm, s>>>(J);
+    k_tile_label<<<tg, T_THREADS, sizeof(TileFast), s>>>(J);
     if (int e = ipp_check_launch("k_tile_label")) return e;
+    {
+        int dev0 = 0, nsm = 0;
+        cudaGetDevice(&dev0);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev0);
+        const int64_t fg = std::min<int64_t>(L.ntiles, (int64_t)std::max(nsm, 1) * 4);
+        k_tile_label_full<<<(unsigned)fg, T_THREADS, sizeof(TileFull), s>>>(J);
+        if (int e = ipp_check_launch("k_tile_label_full")) return e;
+    }
     k_ccl_union<<<tg, 128, 0, s>>>(w, L.ntx, L.nty);
     if (int e = ipp_check_launch("k_ccl_union")) return e;
     int dev = 0, sms = 0;
@@ -990,6 +1047,6 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
     if (int e = ipp_check_launch("k_ccl_scan")) return e;
     k_ccl_emit<<<pg, 256, 0, s>>>(w, A.max_src, A.stats);
     if (int e = ipp_check_launch("k_ccl_emit")) return e;
-    k_tile_final<<<tg, T_THREADS, 0, s>>>(w, A.W, A.H, L.ntx, A.labels);
+    k_tile_final<<<tg, TF_THREADS, 0, s>>>(w, A.W, A.H, L.ntx, A.labels);
     return ipp_check_launch("k_tile_final");
 }

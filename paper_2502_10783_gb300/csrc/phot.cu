@@ -313,6 +313,74 @@ __device__ __forceinline__ bool in_annulus(float dx, float dy, int64_t i, int64_
     return e2 >= rin2d && e2 < rout2d;
 }
 
+// Median (Eq. 1) of buf[0..na) by one histogram pass: 30 equal bins over
+// [mean - 2 sd, mean + 2 sd) plus one bin below and one above; the bin index
+// is monotone in the value, so the bins holding the middle order statistics
+// x_k0, x_k1 (k0 = (na-1)/2, k1 = na/2) hold a contiguous range of the sorted
+// values.  When at most 32 values fall in those bins they are ranked directly;
+// otherwise the bisection of warp_median below takes over.
+__device__ float warp_median(const float* buf, int na, float* cand, int lane);
+
+__device__ float warp_median_hist(const float* buf, int na, int* hist, float* cand, int lane) {
+    const int k0 = (na - 1) / 2, k1 = na / 2;
+    float s = 0.f;
+    for (int t = lane; t < na; t += 32) s += buf[t];
+    s = warp_sum(s);
+    const float mean = s / na;
+    float q = 0.f;
+    for (int t = lane; t < na; t += 32) { const float d = buf[t] - mean; q = fmaf(d, d, q); }
+    q = warp_sum(q);
+    const float sd = sqrtf(q / na);
+    const float lo = mean - 2.0f * sd, width = (4.0f * sd) / 30.0f;
+    const float inv = 1.0f / width;
+    if (!(width > 0.f) || !isfinite(inv) || !isfinite(lo)) return warp_median(buf, na, cand, lane);
+    auto bin = [&](float v) {  // 0: below lo, 1..30, 31: at or above lo + 30 width
+        const float u = (v - lo) * inv;
+        return u < 0.f ? 0 : (u >= 30.0f ? 31 : 1 + min((int)u, 29));
+    };
+    hist[lane] = 0;
+    __syncwarp();
+    for (int t = lane; t < na; t += 32) atomicAdd(&hist[bin(buf[t])], 1);
+    __syncwarp();
+    const int c = hist[lane];
+    int cum = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, cum, o);
+        if (lane >= o) cum += t;
+    }
+    const int before = cum - c;
+    const unsigned m0 = __ballot_sync(0xffffffffu, before <= k0 && k0 < cum);
+    const unsigned m1 = __ballot_sync(0xffffffffu, before <= k1 && k1 < cum);
+    const int b0 = __ffs(m0) - 1, b1 = __ffs(m1) - 1;
+    const int base = __shfl_sync(0xffffffffu, before, b0);
+    const int m = __shfl_sync(0xffffffffu, cum, b1) - base;
+    if (m > 32) return warp_median(buf, na, cand, lane);
+    int nc = 0;
+    for (int t0 = 0; t0 < na; t0 += 32) {
+        const int t = t0 + lane;
+        float v = 0.f;
+        bool in = false;
+        if (t < na) { v = buf[t]; const int b = bin(v); in = b >= b0 && b <= b1; }
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (in) cand[nc + __popc(bal & ((1u << lane) - 1u))] = v;
+        nc += __popc(bal);
+    }
+    __syncwarp();
+    const float mine = lane < m ? cand[lane] : INFINITY;
+    int rank = 0;
+    for (int u = 0; u < m; u++) {
+        const float x = cand[u];
+        rank += (x < mine) || (x == mine && u < lane);
+    }
+    const unsigned r0 = __ballot_sync(0xffffffffu, lane < m && rank == k0 - base);
+    const unsigned r1 = __ballot_sync(0xffffffffu, lane < m && rank == k1 - base);
+    const float v0 = __shfl_sync(0xffffffffu, mine, r0 ? __ffs(r0) - 1 : 0);
+    const float v1 = __shfl_sync(0xffffffffu, mine, r1 ? __ffs(r1) - 1 : 0);
+    __syncwarp();
+    return (float)(0.5 * ((double)v0 + (double)v1));
+}
+
 // Median (Eq. 1) of the na values buf[0..na) held by one warp's shared buffer,
 // exact.  Both middle order statistics x_k0, x_k1 (k0 = (na-1)/2, k1 = na/2)
 // minimise sum |x - m|, so they lie within one standard deviation of the mean:
@@ -430,6 +498,7 @@ __device__ __forceinline__ int off_dj(int16_t o) { return (int)(int8_t)(o & 0xff
 __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
     __shared__ float ann[P_WARPS][ANN_CAP];
     __shared__ float cand[P_WARPS][32];
+    __shared__ int hist[P_WARPS][32];
     // pixel lists shared by the block, for any centre within 1/2 px of the anchor:
     // aperture pixels always inside the disk (weight 1), pixels the disk edge may
     // cross, and pixels whose centre may lie in the annulus
@@ -524,7 +593,7 @@ __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
         if (na < J.min_ann) {
             fl |= IPP_FLAG_ANN_FEW;
         } else {
-            skyv = warp_median(buf, na, cand[wib], lane);
+            skyv = warp_median_hist(buf, na, hist[wib], cand[wib], lane);
         }
         __syncwarp();
         const float Rm = fmaxf(J.r_ap, J.r_out);

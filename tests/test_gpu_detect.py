@@ -115,3 +115,17 @@ def test_survey_frame_full_size_labels(gpu, orc):
     om = orc.threshold(osub, orr, 128, 1.5)
     K = _run_mask(gpu, orc, om, osub, 5)
     assert K > 10000
+
+
+def test_mixed_dense_and_sparse_tiles(gpu, orc):
+    """Tiles with more runs than the common pass holds (checkerboard and dense
+    noise) next to ordinary tiles: the dense ones are redone by the
+    full-capacity pass and the seams between the two kinds still merge."""
+    H, W = 200, 700
+    rng = np.random.default_rng(21)
+    mask = (rng.uniform(size=(H, W)) < 0.08).astype(np.uint8)
+    mask[:, :260] = (np.add.outer(np.arange(H), np.arange(260)) % 2).astype(np.uint8)
+    mask[40:140, 400:530] = (rng.uniform(size=(100, 130)) < 0.55).astype(np.uint8)
+    sub = rng.uniform(0.5, 50.0, (H, W)).astype(np.float32)
+    for min_area in (1, 5):
+        _run_mask(gpu, orc, mask, sub, min_area)
