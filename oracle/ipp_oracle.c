@@ -415,7 +415,7 @@ double orc_overlap(double cx, double cy, double r, double x0, double x1,
     pts[np++] = a;
     double ys[2] = {Y0, Y1};
     for (int k = 0; k < 2; k++) {
-        if (fabs(ys[k]) < r) {
+        if (fabs(ys[k]) <= r) {  /* |y| = r: the circle touches the edge line at x = 0 */
             double h = half_chord(ys[k], r);
             if (-h > a && -h < b) pts[np++] = -h;
             if (h > a && h < b) pts[np++] = h;

@@ -183,3 +183,14 @@ def test_aperture_edge_and_few(orc):
     assert ph["flags"][0] & 1
     ph = orc.aperture(img, [10.0], [10.0], r_in=8, r_out=8.5, min_ann=200)
     assert ph["flags"][0] & 4 and ph["sky"][0] == 0.0
+
+
+def test_overlap_sum_is_disk_area_on_edge_lines(orc):
+    """centres on pixel edge lines and centres, where an integer radius makes
+    the circle touch a pixel edge line at a single point: the weights still add
+    up to pi r^2 (the tangent point splits the chord integral)."""
+    for r in (3.0, 5.0, 4.5):
+        for cx, cy in [(0.0, 0.5), (0.5, 0.0), (0.0, 0.0), (0.5, 0.5), (0.25, 0.5), (0.5, 0.75)]:
+            tot = sum(orc.overlap(cx, cy, r, j - 0.5, j + 0.5, i - 0.5, i + 0.5)
+                      for i in range(-8, 9) for j in range(-8, 9))
+            assert tot == pytest.approx(math.pi * r * r, rel=1e-12), (r, cx, cy)
