@@ -258,7 +258,7 @@ __device__ float circle_pixel_area(float cx, float cy, float r) {
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         float yy = fabsf(ys[k]);
-        if (yy < r) {
+        if (yy <= r) {  // |y| = r: the circle touches the edge line at x = 0
             float h = sqrtf((r - yy) * (r + yy));
             if (-h > a && -h < b) pts[np++] = -h;
             if (h > a && h < b) pts[np++] = h;
