@@ -58,6 +58,7 @@ struct PhotJob {
     const float* y;
     float r_ap, r_in, r_out;
     int min_ann;
+    int ann_cap;  // annulus values one warp can gather (set by the launcher)
     float* flux;
     float* sky;
     float* area;

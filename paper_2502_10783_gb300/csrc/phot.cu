@@ -495,10 +495,60 @@ __device__ int build_offsets(int R, int16_t* out, int cap, int lane, P pred) {
 __device__ __forceinline__ int off_di(int16_t o) { return o >> 8; }
 __device__ __forceinline__ int off_dj(int16_t o) { return (int)(int8_t)(o & 0xff); }
 
+// Area of the disk of radius r centred at the origin beyond the corner (u, v),
+// u, v >= 0 (the region X >= u, Y >= v).  With a = sqrt(r^2 - u^2) and
+// b = sqrt(r^2 - v^2) it is the right triangle (u, v), (u, a), (b, v) plus the
+// circular segment between (u, a) and (b, v), whose angle phi has
+// r^2 sin(phi) = a b - u v and r^2 cos(phi) = u b + a v:
+//   K = (a - v)(b - u) / 2 + (r^2 phi - r^2 sin(phi)) / 2.
+// A pixel's overlap is K(near corner) - K(x-far) - K(y-far) + K(far corner)
+// after reflecting it into the first quadrant (splitting it at an axis it
+// straddles), so one table of K over the corner grid of a source serves all its
+// edge pixels.
+__device__ __forceinline__ float corner_area(float u, float v, float r, float r2) {
+    if (fmaf(u, u, v * v) >= r2) return 0.f;
+    const float a = sqrtf((r - u) * (r + u)), b = sqrtf((r - v) * (r + v));
+    const float sn = fmaf(a, b, -u * v), cs = fmaf(u, b, a * v);
+    return 0.5f * ((a - v) * (b - u) + fmaf(r2, atan2f(sn, cs), -sn));
+}
+
+constexpr int AG_RMAX = 7;                    // corner grid for apertures with R1 <= 7 (r_ap < 7)
+constexpr int AG_N = 2 * AG_RMAX + 2;         // grid lines per axis
+constexpr int AG_SIZE = AG_N * AG_N + 2 * AG_N + 1;
+
+// Overlap of edge pixel (di, dj) from a source's corner table: G[r][c] =
+// K(|X_c|, |Y_r|) at the pixel-corner lines X_c = c - R1 - 1/2 - ox,
+// Y_r = r - R1 - 1/2 - oy; A[r] = K(0, |Y_r|), B[c] = K(|X_c|, 0), K00 = K(0, 0).
+__device__ __forceinline__ float grid_pixel_area(const float* tab, int R1, int di, int dj, float ox, float oy) {
+    const int n = 2 * R1 + 2;
+    const float* G = tab;
+    const float* A = tab + n * n;
+    const float* B = A + n;
+    const float K00 = B[n];
+    const int c0 = dj + R1, r0 = di + R1;
+    const float xa = (float)dj - 0.5f - ox, ya = (float)di - 0.5f - oy;
+    const bool xs = xa < 0.f && xa + 1.0f > 0.f, ys = ya < 0.f && ya + 1.0f > 0.f;  // straddles an axis
+    const int cn = xa >= 0.f ? c0 : c0 + 1, cf = xa >= 0.f ? c0 + 1 : c0;
+    const int rn = ya >= 0.f ? r0 : r0 + 1, rf = ya >= 0.f ? r0 + 1 : r0;
+    float area;
+    if (!xs && !ys) {
+        area = (G[rn * n + cn] - G[rn * n + cf]) - (G[rf * n + cn] - G[rf * n + cf]);
+    } else if (xs && !ys) {  // halves [0, |X_c0|] and [0, |X_c1|] in x
+        area = 2.0f * (A[rn] - A[rf]) - (G[rn * n + c0] - G[rf * n + c0]) - (G[rn * n + c0 + 1] - G[rf * n + c0 + 1]);
+    } else if (!xs && ys) {
+        area = 2.0f * (B[cn] - B[cf]) - (G[r0 * n + cn] - G[r0 * n + cf]) - (G[(r0 + 1) * n + cn] - G[(r0 + 1) * n + cf]);
+    } else {
+        area = 4.0f * K00 - 2.0f * (B[c0] + B[c0 + 1]) - 2.0f * (A[r0] + A[r0 + 1]) +
+               (G[r0 * n + c0] + G[r0 * n + c0 + 1] + G[(r0 + 1) * n + c0] + G[(r0 + 1) * n + c0 + 1]);
+    }
+    return fminf(fmaxf(area, 0.f), 1.f);
+}
+
 __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
-    __shared__ float ann[P_WARPS][ANN_CAP];
+    extern __shared__ float ann_dyn[];        // [P_WARPS][J.ann_cap] annulus values
     __shared__ float cand[P_WARPS][32];
     __shared__ int hist[P_WARPS][32];
+    __shared__ float ktab[P_WARPS][AG_SIZE];  // per-source corner table (apertures with R1 <= AG_RMAX)
     // pixel lists shared by the block, for any centre within 1/2 px of the anchor:
     // aperture pixels always inside the disk (weight 1), pixels the disk edge may
     // cross, and pixels whose centre may lie in the annulus
@@ -508,7 +558,7 @@ __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
     const int gw = (blockIdx.x * P_THREADS + threadIdx.x) >> 5;
     const int nw = (gridDim.x * P_THREADS) >> 5;
     const int n = min(*J.n_src_dev, J.max_src);
-    float* buf = ann[wib];
+    float* buf = ann_dyn + (size_t)wib * J.ann_cap;
     const float Wf = (float)(int)J.W, Hf = (float)(int)J.H;
     const int R1 = (int)ceilf(J.r_ap + 1.0f) - 1;  // pixels reaching within r_ap
     const int R2 = (int)floorf(J.r_out + 0.5f);    // centres within r_out of any offset <= 1/2
@@ -531,7 +581,7 @@ __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
             return far2(di, dj) > r2 && near2(di, dj) < r2;
         });
         // annulus: the pixel centre's distance ranges over |p| +- sqrt(2)/2
-        const int na = build_offsets(R2, l_ann, ANN_CAP, lane, [&](int di, int dj) {
+        const int na = build_offsets(R2, l_ann, min(ANN_CAP, J.ann_cap), lane, [&](int di, int dj) {
             const float a = fmaxf(fabsf((float)dj) - 0.5f, 0.f), b = fmaxf(fabsf((float)di) - 0.5f, 0.f);
             const float c = fabsf((float)dj) + 0.5f, d = fabsf((float)di) + 0.5f;
             return a * a + b * b < rout2 * 1.0001f && c * c + d * d >= rin2 * 0.9999f;
@@ -545,21 +595,48 @@ __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
         const float ax = rintf(x), ay = rintf(y);
         const float ox = x - ax, oy = y - ay;
         const int64_t ia = (int)ay, ja = (int)ax;
-        // aperture sum with exact overlap weights: inner pixels weigh 1, the
-        // edge pixels' overlaps are computed (loads issued before the geometry)
+        // aperture sum with exact overlap weights: inner pixels weigh 1; the
+        // edge pixels' overlaps come from a table of corner areas of this source
+        // (one K per grid corner instead of four per pixel), or, for large
+        // apertures, pixel by pixel
         float sw = 0.f, swf = 0.f;
+        const bool tab = R1 <= AG_RMAX;
+        if (tab) {
+            float* kt = ktab[wib];
+            const int n = 2 * R1 + 2;
+            const float r = J.r_ap, r2 = r * r;
+            for (int t = lane; t < n * n + 2 * n + 1; t += 32) {
+                float u, v;
+                if (t < n * n) {
+                    const int rr = t / n, cc = t - rr * n;
+                    u = fabsf((float)(cc - R1) - 0.5f - ox);
+                    v = fabsf((float)(rr - R1) - 0.5f - oy);
+                } else if (t < n * n + n) {
+                    u = 0.f; v = fabsf((float)(t - n * n - R1) - 0.5f - oy);
+                } else if (t < n * n + 2 * n) {
+                    u = fabsf((float)(t - n * n - n - R1) - 0.5f - ox); v = 0.f;
+                } else {
+                    u = 0.f; v = 0.f;
+                }
+                kt[t] = corner_area(u, v, r, r2);
+            }
+            __syncwarp();
+        }
         for (int t = lane; t < ni + ne; t += 32) {
             const int16_t o = l_ap[t];
             const int di = off_di(o), dj = off_dj(o);
             const int64_t i = ia + di, j = ja + dj;
             if (i < 0 || i >= J.H || j < 0 || j >= J.W) continue;
             const float v = __ldg(J.sub + i * J.pitch + j);
-            const float w = t < ni ? 1.0f : circle_pixel_area(ox - (float)dj, oy - (float)di, J.r_ap);
+            const float w = t < ni ? 1.0f
+                            : (tab ? grid_pixel_area(ktab[wib], R1, di, dj, ox, oy)
+                                   : circle_pixel_area(ox - (float)dj, oy - (float)di, J.r_ap));
             if (w > 0.f) {  // pixels outside the aperture never touch the sums
                 sw += w;
                 swf = fmaf(w, v, swf);
             }
         }
+        __syncwarp();  // the table is rebuilt for the next source
         sw = warp_sum(sw);
         swf = warp_sum(swf);
         // annulus values into the warp's buffer, NCH loads per lane in flight
@@ -685,9 +762,24 @@ int ipp_launch_centroid(const CenJob& J, cudaStream_t s) {
     return ipp_check_launch("k_centroid");
 }
 
-int ipp_launch_aperture(const PhotJob& J, cudaStream_t s) {
-    if (J.r_out > (float)ANN_MAXR) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "r_out above %d px", ANN_MAXR);
-    k_aperture<<<resident_blocks(k_aperture, 0), P_THREADS, 0, s>>>(J);
+int ipp_launch_aperture(const PhotJob& J0, cudaStream_t s) {
+    if (J0.r_out > (float)ANN_MAXR) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "r_out above %d px", ANN_MAXR);
+    // annulus buffer per warp: the number of pixels whose centre can lie in the
+    // annulus for a centre within 1/2 px of the anchor (same test as the device list)
+    PhotJob J = J0;
+    const float rin2 = (float)((double)J.r_in * (double)J.r_in), rout2 = (float)((double)J.r_out * (double)J.r_out);
+    const int R2 = (int)floorf(J.r_out + 0.5f);
+    int cap = 0;
+    for (int di = -R2; di <= R2; di++)
+        for (int dj = -R2; dj <= R2; dj++) {
+            const float a = fmaxf(fabsf((float)dj) - 0.5f, 0.f), b = fmaxf(fabsf((float)di) - 0.5f, 0.f);
+            const float c = fabsf((float)dj) + 0.5f, d = fabsf((float)di) + 0.5f;
+            cap += (a * a + b * b < rout2 * 1.0001f && c * c + d * d >= rin2 * 0.9999f);
+        }
+    J.ann_cap = cap + 32;  // slack for host/device rounding differences of the test
+    const size_t dyn = (size_t)P_WARPS * J.ann_cap * sizeof(float);
+    cudaFuncSetAttribute(k_aperture, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    k_aperture<<<resident_blocks(k_aperture, dyn), P_THREADS, dyn, s>>>(J);
     return ipp_check_launch("k_aperture");
 }
 
