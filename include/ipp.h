@@ -382,7 +382,7 @@ int ipp_batch_autotune(const ipp_frame_desc* frames, int32_t n, const ipp_bg_par
  * (0..S-1):  u = cos(t) dx + sin(t) dy, v = -sin(t) dx + cos(t) dy,
  * q = u^2/sx^2 + v^2/sy^2, Moffat F (beta-1)/(pi sx sy) (1+q)^-beta + sky,
  * Gaussian F/(2 pi sx sy) exp(-q/2) + sky.  Model, Jacobian and J'WJ in FP32;
- * the 7x7 damped normal equations solved by Cholesky in FP64.  One trial per
+ * the 7x7 damped normal equations solved in FP64 (LDL' factorisation).  One trial per
  * iteration: accepted when chi^2 drops (lambda /= 10), else lambda *= 10; widths
  * must stay above 0.05.  Converged when an accepted step lowers chi^2 by less
  * than 1e-6 relative (the FP32 chi^2 resolves ~1e-7; an FP64 evaluation would

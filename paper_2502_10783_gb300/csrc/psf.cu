@@ -3,12 +3,12 @@
 // Gaussian, 7 parameters x0, y0, F, sky, sx, sy, theta, point-sampled at the
 // pixel centres of an S x S stamp).
 //
-// A group of G lanes owns one stamp: the stamp stays in registers for the whole
-// fit, each lane accumulates J'WJ (28 terms), J'W r (7) and chi^2 over its
-// pixels in FP32, and the group reduces them with shuffles.  The damped 7 x 7
-// normal equations are solved in FP64 (LDL', no square roots) by every lane of
-// the group on identical data.  Shuffles name only the group's lanes, so the
-// groups of a warp run their fits independently.
+// The fit runs one stamp per lane (k_psf_fit): each lane keeps its LM state,
+// J'WJ (28 terms), J'W r (7) and chi^2 in registers and reads its stamp from a
+// column of the warp's shared-memory tile.  The damped 7 x 7 normal equations
+// are solved in FP64 (LDL', no square roots), one system per lane, so one FP64
+// instruction of the warp serves 32 stamps.  The forward model and its adjoint
+// (k_psf_fwd, k_psf_adj) evaluate the same point-sampled model.
 #include <math.h>
 
 #include <algorithm>
@@ -17,7 +17,6 @@
 
 namespace ipp {
 
-constexpr int F_THREADS = 128;
 constexpr float F_PI = 3.14159265358979f;
 
 struct PsfPix {  // model value and the 7 derivatives at one pixel
@@ -59,233 +58,282 @@ __device__ __forceinline__ void psf_eval(const float p[7], float dx, float dy, i
     o.j[6] = dPdq * 2.0f * u * v * ((sy - sx) * (sy + sx)) * isx2 * isy2;
 }
 
-// Reductions inside a group of G lanes; the mask names only the group, so
-// groups of one warp may diverge (each runs its own fit).
-template <int G>
-__device__ __forceinline__ unsigned gmask() {
-    if constexpr (G == 32) {
-        return 0xffffffffu;
-    } else {
-        return ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
-    }
-}
-template <int G>
-__device__ __forceinline__ float gsum(float v) {
-    const unsigned m = gmask<G>();
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
-    return v;
-}
-template <int G>
-__device__ __forceinline__ int gsum_i(int v) {
-    const unsigned m = gmask<G>();
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
-    return v;
-}
+// Solve (H + lambda D) x = g, D = diag(H) floored at 1e-9 max(diag), in FP64 by
+// an LDL' factorisation (no square roots).  H packed upper-triangular row-major
+// (28 entries).  Row-oriented: row i of L is formed from the earlier rows with
+// W(q) = L(i,q) D(q) held as a temporary, so each product L(i,q) D(q) L(j,q)
+// costs one fused multiply-add.  Returns false if a pivot is not positive.
+__device__ __forceinline__ int tri(int i, int j) { return i * (i - 1) / 2 + j; }  // strictly lower, j < i
 
-// Solve (H + lambda D) x = g, D = diag(H) floored at 1e-9 max(diag), by LDL' in
-// FP64, in place on the packed lower triangle.  H packed upper-triangular
-// row-major (28 entries, the same numbers as the lower triangle).  Returns false
-// if a pivot is not positive (matrix not positive definite).
-__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
-
-__device__ bool solve7(const float Hf[28], const float gf[7], double lam, double x[7]) {
-    double A[28];
+__device__ __forceinline__ bool solve7(const float Hf[28], const float gf[7], double lam, double x[7]) {
+    double L[21], iD[7];
     double dmax = 0.0;
 #pragma unroll
-    for (int a = 0; a < 7; a++) {
-        // upper-row-major index of (a, b), b >= a:  a*7 - a*(a-1)/2 + (b - a)
+    for (int a = 0; a < 7; a++) dmax = fmax(dmax, (double)Hf[a * 7 - a * (a - 1) / 2]);
+    bool ok = true;
 #pragma unroll
-        for (int b = a; b < 7; b++) A[tri(b, a)] = (double)Hf[a * 7 - a * (a - 1) / 2 + (b - a)];
-    }
+    for (int i = 0; i < 7; i++) {
+        double W[7];
 #pragma unroll
-    for (int a = 0; a < 7; a++) dmax = fmax(dmax, A[tri(a, a)]);
+        for (int j = 0; j < i; j++) {
+            // H(j, i) from the upper row-major packing
+            double t = (double)Hf[j * 7 - j * (j - 1) / 2 + (i - j)];
 #pragma unroll
-    for (int a = 0; a < 7; a++) A[tri(a, a)] += lam * fmax(A[tri(a, a)], 1e-9 * dmax);
-    // A[tri(i,j)] becomes L(i,j) * D(j) for j < i and D(i) on the diagonal
-    double iD[7];
-#pragma unroll
-    for (int j = 0; j < 7; j++) {
-#pragma unroll
-        for (int i = j; i < 7; i++) {
-            double t = A[tri(i, j)];
-#pragma unroll
-            for (int q = 0; q < j; q++) t -= A[tri(i, q)] * A[tri(j, q)] * iD[q];
-            A[tri(i, j)] = t;
+            for (int q = 0; q < j; q++) t = fma(-W[q], L[tri(j, q)], t);
+            W[j] = t;
+            L[tri(i, j)] = t * iD[j];
         }
-        if (!(A[tri(j, j)] > 0.0)) return false;
-        iD[j] = 1.0 / A[tri(j, j)];
+        const double h = (double)Hf[i * 7 - i * (i - 1) / 2];
+        double d = fma(lam, fmax(h, 1e-9 * dmax), h);
+#pragma unroll
+        for (int q = 0; q < i; q++) d = fma(-W[q], L[tri(i, q)], d);
+        ok = ok && d > 0.0;
+        iD[i] = 1.0 / d;
     }
+    if (!ok) return false;
     double z[7];
 #pragma unroll
     for (int i = 0; i < 7; i++) {
         double t = (double)gf[i];
 #pragma unroll
-        for (int q = 0; q < i; q++) t -= A[tri(i, q)] * iD[q] * z[q];
+        for (int q = 0; q < i; q++) t = fma(-L[tri(i, q)], z[q], t);
         z[i] = t;
     }
 #pragma unroll
     for (int i = 6; i >= 0; i--) {
         double t = z[i] * iD[i];
 #pragma unroll
-        for (int q = i + 1; q < 7; q++) t -= A[tri(q, i)] * iD[i] * x[q];
+        for (int q = i + 1; q < 7; q++) t = fma(-L[tri(q, i)], x[q], t);
         x[i] = t;
     }
     return true;
 }
 
-template <int G, int NPL>
-__global__ void __launch_bounds__(F_THREADS) k_psf_fit(FitJob J) {
-    const int lg = threadIdx.x % G;
-    const int64_t group = ((int64_t)blockIdx.x * F_THREADS + threadIdx.x) / G;
-    const int64_t ngroups = ((int64_t)gridDim.x * F_THREADS) / G;
+// ---------------------------------------------------------------------------
+// LM fit, one lane per stamp.  A warp (one block) owns a contiguous chunk of
+// stamps and fits 32 of them at a time; every lane runs its own LM state
+// machine and all lanes step through the same round:
+//   (1) lanes without a stamp take the next ones of the chunk, in lane order;
+//       the warp stages each new stamp in shared memory (pitch 33 words, so a
+//       column is written and a row read without bank conflicts) and computes
+//       its default starting point together;
+//   (2) lanes with a fit in progress solve their damped normal equations (FP64);
+//   (3) every lane with a point to try evaluates chi^2, J'WJ and J'Wr there;
+//   (4) each lane accepts, rejects or stops.
+// The Jacobian is evaluated at every trial point, not only after an accepted
+// step: a rejected trial wastes its normal equations, but no lane of the warp
+// waits for another lane's extra evaluation.  Per-lane accumulation over the
+// stamp's pixels is sequential; chi^2 is summed per stamp row first, so its
+// rounding stays near that of a 2 x S-term sum.
+constexpr int FL_PITCH = 33;
+
+template <int MODEL, bool WEIGHTED>
+__device__ __forceinline__ float eval_lane(const float* __restrict__ col, const float* __restrict__ wts, int S,
+                                           float beta, const float pp[7], float Ht[28], float gt[7]) {
+#pragma unroll
+    for (int a = 0; a < 28; a++) Ht[a] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 7; a++) gt[a] = 0.f;
+    float s, c;
+    sincosf(pp[6], &s, &c);
+    float chi = 0.f;
+    for (int i = 0; i < S; i++) {
+        const float dy = (float)i - pp[1];
+        float rowc = 0.f;
+        for (int j = 0; j < S; j++) {
+            const int k = i * S + j;
+            PsfPix e;
+            psf_eval(pp, (float)j - pp[0], dy, MODEL, beta, c, s, true, e);
+            const float wk = WEIGHTED ? __ldg(wts + k) : 1.0f;
+            const float r = col[k * FL_PITCH] - e.m;
+            rowc = fmaf(wk * r, r, rowc);
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < 7; a++) {
+                const float wa = wk * e.j[a];
+                gt[a] = fmaf(wa, r, gt[a]);
+#pragma unroll
+                for (int b = a; b < 7; b++) { Ht[t] = fmaf(wa, e.j[b], Ht[t]); t++; }
+            }
+        }
+        chi += rowc;
+    }
+    return chi;
+}
+
+// Default start of stamp `sr` staged in column r: centre, border-median sky, sum
+// above sky, widths 1.6 / 1.4, theta 0.  All lanes of the warp take part and all
+// return the same values.
+__device__ __forceinline__ void init_coop(const float* __restrict__ sm, int r, int S, float p[7]) {
+    const int lane = threadIdx.x & 31;
+    const int NP = S * S, nb = 4 * S - 4;
+    const int k0 = (nb - 1) / 2, k1 = nb / 2;
+    uint32_t lo = 0u, hi = 0xffffffffu;
+    while (lo < hi) {  // smallest key with more than k0 border values at or below it
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        int c = 0;
+        for (int k = lane; k < NP; k += 32) {
+            const int i = k / S, j = k - i * S;
+            const bool border = i == 0 || j == 0 || i == S - 1 || j == S - 1;
+            c += border && fkey(sm[k * FL_PITCH + r]) <= mid;
+        }
+        c = warp_sum_i(c);
+        if (c > k0) hi = mid; else lo = mid + 1;
+    }
+    const uint32_t ka = lo;
+    int cle = 0;
+    uint32_t nxt = 0xffffffffu;
+    for (int k = lane; k < NP; k += 32) {
+        const int i = k / S, j = k - i * S;
+        if (i == 0 || j == 0 || i == S - 1 || j == S - 1) {
+            const uint32_t kk = fkey(sm[k * FL_PITCH + r]);
+            cle += kk <= ka;
+            if (kk > ka && kk < nxt) nxt = kk;
+        }
+    }
+    cle = warp_sum_i(cle);
+    nxt = __reduce_min_sync(0xffffffffu, nxt);
+    const uint32_t kb = cle > k1 ? ka : nxt;
+    const float sky0 = (float)(0.5 * ((double)fkey_inv(ka) + (double)fkey_inv(kb)));
+    float fs = 0.f;
+    for (int k = lane; k < NP; k += 32) fs += sm[k * FL_PITCH + r] - sky0;
+    fs = warp_sum(fs);
+    p[0] = 0.5f * (S - 1); p[1] = 0.5f * (S - 1); p[2] = fs; p[3] = sky0;
+    p[4] = 1.6f; p[5] = 1.4f; p[6] = 0.f;
+}
+
+template <int MODEL, bool WEIGHTED>
+__global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
+    extern __shared__ float fl_sm[];  // [S*S][FL_PITCH]: pixel k of the stamp in column `lane`
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x;
     const int S = J.S, NP = S * S;
-    const unsigned gm = gmask<G>();
-    for (int64_t st = group; st < J.N; st += ngroups) {
-        const float* stamp = J.stamps + st * NP;
-        const float* wts = J.weights ? J.weights + st * NP : nullptr;
-        float d[NPL];
+    const int64_t c0 = (int64_t)blockIdx.x * chunk;
+    const int64_t c1 = c0 + chunk < J.N ? c0 + chunk : J.N;
+    int64_t next = c0;
+    int64_t st = -1;
+    float p[7], H[28], g[7], chi2 = 0.f;
+    double lam = 0.0;
+    int it = 0, nsing = 0;
+    bool fresh = false;
 #pragma unroll
-        for (int m = 0; m < NPL; m++) {
-            int k = lg + G * m;
-            d[m] = k < NP ? __ldg(stamp + k) : 0.f;
-        }
-        float p[7];
-        if (J.init) {
-#pragma unroll
-            for (int a = 0; a < 7; a++) p[a] = __ldg(J.init + st * 7 + a);
-        } else {
-            // start: centre, border median sky, sum above sky, widths 1.6 / 1.4
-            const int nb = 4 * S - 4;
-            uint32_t lo = 0u, hi = 0xffffffffu;
-            const int k0 = (nb - 1) / 2, k1 = nb / 2;
-            while (lo < hi) {
-                uint32_t mid = lo + ((hi - lo) >> 1);
-                int c = 0;
-#pragma unroll
-                for (int m = 0; m < NPL; m++) {
-                    int k = lg + G * m, i = k / S, j = k - i * S;
-                    bool border = k < NP && (i == 0 || j == 0 || i == S - 1 || j == S - 1);
-                    c += border && fkey(d[m]) <= mid;
-                }
-                c = gsum_i<G>(c);
-                if (c > k0) hi = mid; else lo = mid + 1;
+    for (int a = 0; a < 7; a++) p[a] = 0.f;
+    while (true) {
+        // (1) refill the idle lanes from the chunk
+        const unsigned idle = __ballot_sync(FULL, st < 0);
+        if (idle && next < c1) {
+            const int rank = __popc(idle & ((1u << lane) - 1u));
+            if (st < 0 && next + rank < c1) {
+                st = next + rank;
+                fresh = true;
+                it = 0; nsing = 0;
+                lam = (double)J.lambda0;
             }
-            const uint32_t ka = lo;
-            int cle = 0;
-            uint32_t nxt = 0xffffffffu;
+            next += __popc(idle) < c1 - next ? __popc(idle) : c1 - next;
+            unsigned nm = __ballot_sync(FULL, fresh);
+            while (nm) {
+                const int r = __ffs(nm) - 1;
+                nm &= nm - 1u;
+                const int64_t sr = __shfl_sync(FULL, st, r);
+                const float* src = J.stamps + sr * NP;
+                for (int k = lane; k < NP; k += 32) fl_sm[k * FL_PITCH + r] = __ldg(src + k);
+                __syncwarp();
+                if (J.init) {
+                    if (lane == r) {
 #pragma unroll
-            for (int m = 0; m < NPL; m++) {
-                int k = lg + G * m, i = k / S, j = k - i * S;
-                bool border = k < NP && (i == 0 || j == 0 || i == S - 1 || j == S - 1);
-                if (border) {
-                    uint32_t kk = fkey(d[m]);
-                    cle += kk <= ka;
-                    if (kk > ka && kk < nxt) nxt = kk;
-                }
-            }
-            cle = gsum_i<G>(cle);
+                        for (int a = 0; a < 7; a++) p[a] = __ldg(J.init + sr * 7 + a);
+                    }
+                } else {
+                    float q[7];
+                    init_coop(fl_sm, r, S, q);
+                    if (lane == r) {
 #pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) nxt = min(nxt, __shfl_xor_sync(gm, nxt, o));
-            const uint32_t kb = cle > k1 ? ka : nxt;
-            const float sky0 = (float)(0.5 * ((double)fkey_inv(ka) + (double)fkey_inv(kb)));
-            float fs = 0.f;
-#pragma unroll
-            for (int m = 0; m < NPL; m++)
-                if (lg + G * m < NP) fs += d[m] - sky0;
-            fs = gsum<G>(fs);
-            p[0] = 0.5f * (S - 1); p[1] = 0.5f * (S - 1); p[2] = fs; p[3] = sky0;
-            p[4] = 1.6f; p[5] = 1.4f; p[6] = 0.f;
-        }
-        // chi^2 and, when `full`, J'WJ (packed upper triangle) and J'W r at pp
-        float H[28], g[7];
-        auto evaluate = [&](const float pp[7], bool full) -> float {
-            const float c = cosf(pp[6]), s = sinf(pp[6]);
-            float chi = 0.f;
-            if (full) {
-#pragma unroll
-                for (int a = 0; a < 28; a++) H[a] = 0.f;
-#pragma unroll
-                for (int a = 0; a < 7; a++) g[a] = 0.f;
-            }
-#pragma unroll
-            for (int m = 0; m < NPL; m++) {
-                int k = lg + G * m;
-                if (k < NP) {
-                    int i = k / S, j = k - i * S;
-                    PsfPix e;
-                    psf_eval(pp, (float)j - pp[0], (float)i - pp[1], J.model, J.beta, c, s, full, e);
-                    float wk = wts ? __ldg(wts + k) : 1.0f;
-                    float r = d[m] - e.m;
-                    chi = fmaf(wk * r, r, chi);
-                    if (full) {
-                        int t = 0;
-#pragma unroll
-                        for (int a = 0; a < 7; a++) {
-                            float wa = wk * e.j[a];
-                            g[a] = fmaf(wa, r, g[a]);
-#pragma unroll
-                            for (int b = a; b < 7; b++) { H[t] = fmaf(wa, e.j[b], H[t]); t++; }
-                        }
+                        for (int a = 0; a < 7; a++) p[a] = q[a];
                     }
                 }
             }
-            chi = gsum<G>(chi);
-            if (full) {
+        }
+        if (!__any_sync(FULL, st >= 0)) break;
+
+        // (2) the trial point of this round
+        float pt[7];
+        bool try_pt = false;
+        int fl = -1;  // >= 0: the fit ends this round with these flags
+        if (st >= 0) {
+            if (fresh) {
 #pragma unroll
-                for (int a = 0; a < 28; a++) H[a] = gsum<G>(H[a]);
-#pragma unroll
-                for (int a = 0; a < 7; a++) g[a] = gsum<G>(g[a]);
-            }
-            return chi;
-        };
-        float chi2 = evaluate(p, true);
-        double lam = (double)J.lambda0;
-        int fl = IPP_FLAG_FIT_MAXITER, it, nsing = 0;
-        for (it = 0; it < J.max_iter; it++) {
-            double delta[7];
-            if (!solve7(H, g, lam, delta)) {
-                lam *= 10.0;
-                nsing++;
-                if (lam > 1e10) { it++; break; }
-                continue;
-            }
-            float pt[7];
-#pragma unroll
-            for (int a = 0; a < 7; a++) pt[a] = (float)((double)p[a] + delta[a]);
-            if (!(pt[4] > 0.05f) || !(pt[5] > 0.05f)) {
-                lam *= 10.0;
-                if (lam > 1e10) { fl = 0; it++; break; }
-                continue;
-            }
-            float c2t = evaluate(pt, false);
-            if (c2t < chi2) {
-                float rel = (chi2 - c2t) / chi2;
-#pragma unroll
-                for (int a = 0; a < 7; a++) p[a] = pt[a];
-                chi2 = c2t;
-                lam *= 0.1;
-                // FP32 chi^2 resolves ~1e-7: the relative-decrease test of the
-                // FP64 rule (1e-8) is taken at 1e-6 here
-                if (rel < 1e-6f) { fl = 0; it++; break; }
-                evaluate(p, true);
+                for (int a = 0; a < 7; a++) pt[a] = p[a];
+                try_pt = true;
             } else {
-                lam *= 10.0;
-                if (lam > 1e10) { fl = 0; it++; break; }
+                double delta[7];
+                if (!solve7(H, g, lam, delta)) {
+                    lam *= 10.0;
+                    nsing++;
+                    it++;
+                    if (lam > 1e10) fl = IPP_FLAG_FIT_MAXITER;
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 7; a++) pt[a] = (float)((double)p[a] + delta[a]);
+                    if (!(pt[4] > 0.05f) || !(pt[5] > 0.05f)) {
+                        lam *= 10.0;
+                        it++;
+                        if (lam > 1e10) fl = 0;
+                    } else {
+                        try_pt = true;
+                    }
+                }
             }
         }
-        if (nsing > 0 && fl) fl |= IPP_FLAG_FIT_SINGULAR;
-        if (!(p[4] > 0.05f) || !(p[5] > 0.05f)) fl |= IPP_FLAG_FIT_BAD_SIGMA;
-        if (p[4] < p[5]) { float t = p[4]; p[4] = p[5]; p[5] = t; p[6] += 0.5f * F_PI; }
-        p[6] = p[6] - F_PI * floorf((p[6] + 0.5f * F_PI) / F_PI);
-        if (lg == 0) {
+        // (3) chi^2 and normal equations at the trial point
+        float Ht[28], gt[7], c2t = 0.f;
+        if (try_pt) {
+            const float* wts = WEIGHTED ? J.weights + st * NP : nullptr;
+            c2t = eval_lane<MODEL, WEIGHTED>(fl_sm + lane, wts, S, J.beta, pt, Ht, gt);
+        }
+        // (4) accept, reject or stop
+        if (try_pt) {
+            bool take = fresh;
+            if (!fresh) {
+                it++;
+                if (c2t < chi2) {
+                    take = true;
+                    // FP32 chi^2 resolves ~1e-7: the relative-decrease test of the
+                    // FP64 rule (1e-8) is taken at 1e-6 here
+                    if ((chi2 - c2t) / chi2 < 1e-6f) fl = 0;
+                    lam *= 0.1;
+                } else {
+                    lam *= 10.0;
+                    if (lam > 1e10) fl = 0;
+                }
+            }
+            if (take) {
 #pragma unroll
-            for (int a = 0; a < 7; a++) J.params[st * 7 + a] = p[a];
+                for (int a = 0; a < 7; a++) p[a] = pt[a];
+#pragma unroll
+                for (int a = 0; a < 28; a++) H[a] = Ht[a];
+#pragma unroll
+                for (int a = 0; a < 7; a++) g[a] = gt[a];
+                chi2 = c2t;
+            }
+            fresh = false;
+        }
+        if (st >= 0 && fl < 0 && it >= J.max_iter) fl = IPP_FLAG_FIT_MAXITER;
+        if (fl >= 0) {
+            if (nsing > 0 && fl) fl |= IPP_FLAG_FIT_SINGULAR;
+            if (!(p[4] > 0.05f) || !(p[5] > 0.05f)) fl |= IPP_FLAG_FIT_BAD_SIGMA;
+            float q[7];
+#pragma unroll
+            for (int a = 0; a < 7; a++) q[a] = p[a];
+            if (q[4] < q[5]) { const float t = q[4]; q[4] = q[5]; q[5] = t; q[6] += 0.5f * F_PI; }
+            q[6] = q[6] - F_PI * floorf((q[6] + 0.5f * F_PI) / F_PI);
+#pragma unroll
+            for (int a = 0; a < 7; a++) J.params[st * 7 + a] = q[a];
             J.chi2[st] = chi2;
             if (J.iters) J.iters[st] = it;
             if (J.flags) J.flags[st] = fl;
+            st = -1;
         }
+        __syncwarp();
     }
 }
 
@@ -347,23 +395,27 @@ static int sm_count() {
     return sms > 0 ? sms : 132;
 }
 
-int ipp_launch_psf_fit(const FitJob& J, cudaStream_t s) {
-    const int NP = J.S * J.S;
-    int blocks;
-    if (NP <= 8 * 32) {
-        constexpr int G = 8;
-        int64_t groups = J.N;
-        blocks = (int)std::min<int64_t>((groups * G + F_THREADS - 1) / F_THREADS, (int64_t)sm_count() * 16);
-        k_psf_fit<G, 32><<<blocks, F_THREADS, 0, s>>>(J);
-    } else if (NP <= 32 * 32) {
-        constexpr int G = 32;
-        int64_t groups = J.N;
-        blocks = (int)std::min<int64_t>((groups * G + F_THREADS - 1) / F_THREADS, (int64_t)sm_count() * 16);
-        k_psf_fit<G, 32><<<blocks, F_THREADS, 0, s>>>(J);
-    } else {
-        return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "stamp size %d above 32", J.S);
-    }
+template <int MODEL, bool WEIGHTED>
+static int launch_fit(const FitJob& J, cudaStream_t s) {
+    auto k = k_psf_fit<MODEL, WEIGHTED>;
+    const size_t smem = (size_t)J.S * J.S * FL_PITCH * sizeof(float);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 32, smem) != cudaSuccess || per < 1) per = 1;
+    // one resident warp per block and a contiguous chunk of stamps per warp:
+    // as few chunks as fill the GPU, so that each lane fits several stamps
+    const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per, (J.N + 31) / 32);
+    const int64_t chunk = (J.N + blocks - 1) / blocks;
+    k<<<(unsigned)blocks, 32, smem, s>>>(J, chunk);
     return ipp_check_launch("k_psf_fit");
+}
+
+int ipp_launch_psf_fit(const FitJob& J, cudaStream_t s) {
+    if (J.S * J.S * FL_PITCH * sizeof(float) > 227 * 1024)
+        return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "stamp size %d above 32", J.S);
+    if (J.model == IPP_PSF_GAUSS) return J.weights ? launch_fit<IPP_PSF_GAUSS, true>(J, s) : launch_fit<IPP_PSF_GAUSS, false>(J, s);
+    return J.weights ? launch_fit<IPP_PSF_MOFFAT, true>(J, s) : launch_fit<IPP_PSF_MOFFAT, false>(J, s);
 }
 
 int ipp_launch_psf_fwd(const float* params, int64_t N, int S, int model, float beta, float* out, cudaStream_t s) {
