@@ -127,6 +127,15 @@ __device__ __forceinline__ bool solve7(const float Hf[28], const float gf[7], do
 // rounding stays near that of a 2 x S-term sum.
 constexpr int FL_PITCH = 33;
 
+// chi^2, J'WJ and J'Wr of one stamp at pp.  The model of psf_eval with the
+// per-trial constants (reciprocal widths, normalisation, trig) taken out of the
+// pixel loop and its derivatives regrouped around T = 2 dP/dq, a = u/sx^2 and
+// b = v/sy^2:
+//   dm/dx0 = T (b s - a c),  dm/dy0 = -T (a s + b c),  dm/dF = P/F,  dm/dsky = 1,
+//   dm/dsx = -(P + T a u)/sx,  dm/dsy = -(P + T b v)/sy,
+//   dm/dtheta = T u v (sy^2 - sx^2)/(sx^2 sy^2).
+// Moffat (1+q)^-beta is exp2(-beta log2(1+q)) with the fast base-2 logarithm
+// (absolute error ~2^-22 on the exponent, a few ulp in P).
 template <int MODEL, bool WEIGHTED>
 __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const float* __restrict__ wts, int S,
                                            float beta, const float pp[7], float Ht[28], float gt[7]) {
@@ -134,26 +143,55 @@ __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const 
     for (int a = 0; a < 28; a++) Ht[a] = 0.f;
 #pragma unroll
     for (int a = 0; a < 7; a++) gt[a] = 0.f;
-    float s, c;
-    sincosf(pp[6], &s, &c);
+    float sn, cs;
+    sincosf(pp[6], &sn, &cs);
+    const float x0 = pp[0], F = pp[2], sky = pp[3];
+    const float isx = 1.0f / pp[4], isy = 1.0f / pp[5];
+    const float isx2 = isx * isx, isy2 = isy * isy;
+    const float kth = (pp[5] - pp[4]) * (pp[5] + pp[4]) * isx2 * isy2;
+    const float A0 = (MODEL == IPP_PSF_GAUSS ? 0.5f / F_PI : (beta - 1.0f) / F_PI) * isx * isy;
+    const float tq = MODEL == IPP_PSF_GAUSS ? -1.0f : -2.0f * beta;  // T = tq P / (1+q) (Moffat), -P (Gauss)
     float chi = 0.f;
     for (int i = 0; i < S; i++) {
         const float dy = (float)i - pp[1];
+        const float sdy = sn * dy, cdy = cs * dy;
+        const float* row = col + i * S * FL_PITCH;
         float rowc = 0.f;
-        for (int j = 0; j < S; j++) {
-            const int k = i * S + j;
-            PsfPix e;
-            psf_eval(pp, (float)j - pp[0], dy, MODEL, beta, c, s, true, e);
-            const float wk = WEIGHTED ? __ldg(wts + k) : 1.0f;
-            const float r = col[k * FL_PITCH] - e.m;
+        float jf = 0.f;
+        for (int j = 0; j < S; j++, jf += 1.0f) {
+            const float dx = jf - x0;
+            const float u = fmaf(cs, dx, sdy), v = fmaf(-sn, dx, cdy);
+            const float a = u * isx2, b = v * isy2;
+            const float q = fmaf(u, a, v * b);
+            float A1, P, T;
+            if (MODEL == IPP_PSF_GAUSS) {
+                A1 = A0 * exp2f(-0.72134752f * q);  // exp(-q/2)
+                P = F * A1;
+                T = -P;
+            } else {
+                const float base = 1.0f + q;
+                A1 = A0 * exp2f(-beta * __log2f(base));
+                P = F * A1;
+                T = __fdividef(tq * P, base);
+            }
+            const float wk = WEIGHTED ? __ldg(wts + i * S + j) : 1.0f;
+            const float r = row[j * FL_PITCH] - (P + sky);
             rowc = fmaf(wk * r, r, rowc);
+            float e[7];
+            e[0] = T * fmaf(b, sn, -a * cs);
+            e[1] = -T * fmaf(a, sn, b * cs);
+            e[2] = A1;
+            e[3] = 1.0f;
+            e[4] = -isx * fmaf(T * a, u, P);
+            e[5] = -isy * fmaf(T * b, v, P);
+            e[6] = T * u * v * kth;
             int t = 0;
 #pragma unroll
-            for (int a = 0; a < 7; a++) {
-                const float wa = wk * e.j[a];
-                gt[a] = fmaf(wa, r, gt[a]);
+            for (int c = 0; c < 7; c++) {
+                const float wa = wk * e[c];
+                gt[c] = fmaf(wa, r, gt[c]);
 #pragma unroll
-                for (int b = a; b < 7; b++) { Ht[t] = fmaf(wa, e.j[b], Ht[t]); t++; }
+                for (int d = c; d < 7; d++) { Ht[t] = fmaf(wa, e[d], Ht[t]); t++; }
             }
         }
         chi += rowc;
