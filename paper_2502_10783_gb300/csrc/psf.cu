@@ -3,11 +3,12 @@
 // Gaussian, 7 parameters x0, y0, F, sky, sx, sy, theta, point-sampled at the
 // pixel centres of an S x S stamp).
 //
-// The fit runs one stamp per lane (k_psf_fit): each lane keeps its LM state,
-// J'WJ (28 terms), J'W r (7) and chi^2 in registers and reads its stamp from a
-// column of the warp's shared-memory tile.  The damped 7 x 7 normal equations
-// are solved in FP64 (LDL', no square roots), one system per lane, so one FP64
-// instruction of the warp serves 32 stamps.  The forward model and its adjoint
+// The fit (k_psf_fit) gives each stamp two lanes of a warp: both keep the
+// stamp's LM state, J'WJ (28 terms), J'W r (7) and chi^2 in registers, each
+// evaluates half of the stamp's rows from a column of the warp's shared-memory
+// tile, and one shuffle adds the halves.  The damped 7 x 7 normal equations are
+// solved in FP64 (LDL', no square roots), one system per lane, so one FP64
+// instruction of the warp serves 16 stamps.  The forward model and its adjoint
 // (k_psf_fwd, k_psf_adj) evaluate the same point-sampled model.
 #include <math.h>
 
@@ -110,22 +111,29 @@ __device__ __forceinline__ bool solve7(const float Hf[28], const float gf[7], do
 }
 
 // ---------------------------------------------------------------------------
-// LM fit, one lane per stamp.  A warp (one block) owns a contiguous chunk of
-// stamps and fits 32 of them at a time; every lane runs its own LM state
-// machine and all lanes step through the same round:
-//   (1) lanes without a stamp take the next ones of the chunk, in lane order;
-//       the warp stages each new stamp in shared memory (pitch 33 words, so a
-//       column is written and a row read without bank conflicts) and computes
-//       its default starting point together;
-//   (2) lanes with a fit in progress solve their damped normal equations (FP64);
-//   (3) every lane with a point to try evaluates chi^2, J'WJ and J'Wr there;
-//   (4) each lane accepts, rejects or stops.
+// LM fit, G lanes per stamp.  A warp (one block) owns a contiguous chunk of
+// stamps and fits 32/G of them at a time, one per slot; the G lanes of a slot
+// hold identical copies of its LM state and all slots step through the same
+// round:
+//   (1) idle slots take the next stamps of the chunk, in slot order; the warp
+//       stages each new stamp in shared memory (pixel k of slot s at
+//       k (32/G + 1) + s, so a column is written and a row read without bank
+//       conflicts) and computes its default starting point together;
+//   (2) slots with a fit in progress solve their damped normal equations (FP64);
+//   (3) every slot with a point to try evaluates chi^2, J'WJ and J'Wr there,
+//       each lane of the slot over every G-th stamp row, and the slot's lanes
+//       add their sums with shuffles;
+//   (4) each slot accepts, rejects or stops.
 // The Jacobian is evaluated at every trial point, not only after an accepted
-// step: a rejected trial wastes its normal equations, but no lane of the warp
-// waits for another lane's extra evaluation.  Per-lane accumulation over the
-// stamp's pixels is sequential; chi^2 is summed per stamp row first, so its
-// rounding stays near that of a 2 x S-term sum.
-constexpr int FL_PITCH = 33;
+// step: a rejected trial wastes its normal equations, but no slot of the warp
+// waits for another slot's extra evaluation.  Per-lane accumulation over the
+// pixels is sequential; chi^2 is summed per stamp row first, so its rounding
+// stays near that of a 2 x S-term sum.
+//
+// G = 2: the shared-memory tile of 16 stamps (15 KB at S = 15) lets 12 warps
+// share an SM, against 7 warps of 32 stamps at G = 1; the price is that each
+// solve is done by both lanes of a slot, which the FP64 pipe can afford.
+constexpr int FL_G = 2;
 
 // chi^2, J'WJ and J'Wr of one stamp at pp.  The model of psf_eval with the
 // per-trial constants (reciprocal widths, normalisation, trig) taken out of the
@@ -136,9 +144,10 @@ constexpr int FL_PITCH = 33;
 //   dm/dtheta = T u v (sy^2 - sx^2)/(sx^2 sy^2).
 // Moffat (1+q)^-beta is exp2(-beta log2(1+q)) with the fast base-2 logarithm
 // (absolute error ~2^-22 on the exponent, a few ulp in P).
-template <int MODEL, bool WEIGHTED>
+template <int MODEL, bool WEIGHTED, int G, int PITCH>
 __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const float* __restrict__ wts, int S,
                                            float beta, const float pp[7], float Ht[28], float gt[7]) {
+    const int h = (threadIdx.x & 31) % G;
 #pragma unroll
     for (int a = 0; a < 28; a++) Ht[a] = 0.f;
 #pragma unroll
@@ -152,12 +161,13 @@ __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const 
     const float A0 = (MODEL == IPP_PSF_GAUSS ? 0.5f / F_PI : (beta - 1.0f) / F_PI) * isx * isy;
     const float tq = MODEL == IPP_PSF_GAUSS ? -1.0f : -2.0f * beta;  // T = tq P / (1+q) (Moffat), -P (Gauss)
     float chi = 0.f;
-    for (int i = 0; i < S; i++) {
+    for (int i = h; i < S; i += G) {
         const float dy = (float)i - pp[1];
         const float sdy = sn * dy, cdy = cs * dy;
-        const float* row = col + i * S * FL_PITCH;
+        const float* row = col + i * S * PITCH;
         float rowc = 0.f;
         float jf = 0.f;
+#pragma unroll 5
         for (int j = 0; j < S; j++, jf += 1.0f) {
             const float dx = jf - x0;
             const float u = fmaf(cs, dx, sdy), v = fmaf(-sn, dx, cdy);
@@ -175,7 +185,7 @@ __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const 
                 T = __fdividef(tq * P, base);
             }
             const float wk = WEIGHTED ? __ldg(wts + i * S + j) : 1.0f;
-            const float r = row[j * FL_PITCH] - (P + sky);
+            const float r = row[j * PITCH] - (P + sky);
             rowc = fmaf(wk * r, r, rowc);
             float e[7];
             e[0] = T * fmaf(b, sn, -a * cs);
@@ -196,12 +206,21 @@ __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const 
         }
         chi += rowc;
     }
+    if (G == 2) {  // both lanes of the slot are here (their states are identical)
+        const unsigned pm = 3u << ((threadIdx.x & 31) & ~1);
+#pragma unroll
+        for (int a = 0; a < 28; a++) Ht[a] += __shfl_xor_sync(pm, Ht[a], 1);
+#pragma unroll
+        for (int a = 0; a < 7; a++) gt[a] += __shfl_xor_sync(pm, gt[a], 1);
+        chi += __shfl_xor_sync(pm, chi, 1);
+    }
     return chi;
 }
 
 // Default start of stamp `sr` staged in column r: centre, border-median sky, sum
 // above sky, widths 1.6 / 1.4, theta 0.  All lanes of the warp take part and all
 // return the same values.
+template <int PITCH>
 __device__ __forceinline__ void init_coop(const float* __restrict__ sm, int r, int S, float p[7]) {
     const int lane = threadIdx.x & 31;
     const int NP = S * S, nb = 4 * S - 4;
@@ -213,7 +232,7 @@ __device__ __forceinline__ void init_coop(const float* __restrict__ sm, int r, i
         for (int k = lane; k < NP; k += 32) {
             const int i = k / S, j = k - i * S;
             const bool border = i == 0 || j == 0 || i == S - 1 || j == S - 1;
-            c += border && fkey(sm[k * FL_PITCH + r]) <= mid;
+            c += border && fkey(sm[k * PITCH + r]) <= mid;
         }
         c = warp_sum_i(c);
         if (c > k0) hi = mid; else lo = mid + 1;
@@ -224,7 +243,7 @@ __device__ __forceinline__ void init_coop(const float* __restrict__ sm, int r, i
     for (int k = lane; k < NP; k += 32) {
         const int i = k / S, j = k - i * S;
         if (i == 0 || j == 0 || i == S - 1 || j == S - 1) {
-            const uint32_t kk = fkey(sm[k * FL_PITCH + r]);
+            const uint32_t kk = fkey(sm[k * PITCH + r]);
             cle += kk <= ka;
             if (kk > ka && kk < nxt) nxt = kk;
         }
@@ -234,17 +253,20 @@ __device__ __forceinline__ void init_coop(const float* __restrict__ sm, int r, i
     const uint32_t kb = cle > k1 ? ka : nxt;
     const float sky0 = (float)(0.5 * ((double)fkey_inv(ka) + (double)fkey_inv(kb)));
     float fs = 0.f;
-    for (int k = lane; k < NP; k += 32) fs += sm[k * FL_PITCH + r] - sky0;
+    for (int k = lane; k < NP; k += 32) fs += sm[k * PITCH + r] - sky0;
     fs = warp_sum(fs);
     p[0] = 0.5f * (S - 1); p[1] = 0.5f * (S - 1); p[2] = fs; p[3] = sky0;
     p[4] = 1.6f; p[5] = 1.4f; p[6] = 0.f;
 }
 
-template <int MODEL, bool WEIGHTED>
-__global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
-    extern __shared__ float fl_sm[];  // [S*S][FL_PITCH]: pixel k of the stamp in column `lane`
+template <int MODEL, bool WEIGHTED, int G>
+__global__ void __launch_bounds__(32, 12) k_psf_fit(FitJob J, int64_t chunk) {  // 12 warps/SM: <= 168 registers
+    constexpr int SLOTS = 32 / G, PITCH = SLOTS + 1;
+    extern __shared__ float fl_sm[];  // [S*S][PITCH]: pixel k of the stamp of slot s in column s
     const unsigned FULL = 0xffffffffu;
+    const unsigned HEADS = G == 1 ? FULL : 0x55555555u;  // the first lane of each slot
     const int lane = threadIdx.x;
+    const int slot = lane / G;
     const int S = J.S, NP = S * S;
     const int64_t c0 = (int64_t)blockIdx.x * chunk;
     const int64_t c1 = c0 + chunk < J.N ? c0 + chunk : J.N;
@@ -257,10 +279,9 @@ __global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
 #pragma unroll
     for (int a = 0; a < 7; a++) p[a] = 0.f;
     while (true) {
-        // (1) refill the idle lanes from the chunk
-        const unsigned idle = __ballot_sync(FULL, st < 0);
+        const unsigned idle = __ballot_sync(FULL, st < 0) & HEADS;
         if (idle && next < c1) {
-            const int rank = __popc(idle & ((1u << lane) - 1u));
+            const int rank = __popc(idle & ((1u << (slot * G)) - 1u));
             if (st < 0 && next + rank < c1) {
                 st = next + rank;
                 fresh = true;
@@ -268,23 +289,23 @@ __global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
                 lam = (double)J.lambda0;
             }
             next += __popc(idle) < c1 - next ? __popc(idle) : c1 - next;
-            unsigned nm = __ballot_sync(FULL, fresh);
+            unsigned nm = __ballot_sync(FULL, fresh) & HEADS;
             while (nm) {
-                const int r = __ffs(nm) - 1;
+                const int rl = __ffs(nm) - 1, r = rl / G;
                 nm &= nm - 1u;
-                const int64_t sr = __shfl_sync(FULL, st, r);
+                const int64_t sr = __shfl_sync(FULL, st, rl);
                 const float* src = J.stamps + sr * NP;
-                for (int k = lane; k < NP; k += 32) fl_sm[k * FL_PITCH + r] = __ldg(src + k);
+                for (int k = lane; k < NP; k += 32) fl_sm[k * PITCH + r] = __ldg(src + k);
                 __syncwarp();
                 if (J.init) {
-                    if (lane == r) {
+                    if (slot == r) {
 #pragma unroll
                         for (int a = 0; a < 7; a++) p[a] = __ldg(J.init + sr * 7 + a);
                     }
                 } else {
                     float q[7];
-                    init_coop(fl_sm, r, S, q);
-                    if (lane == r) {
+                    init_coop<PITCH>(fl_sm, r, S, q);
+                    if (slot == r) {
 #pragma unroll
                         for (int a = 0; a < 7; a++) p[a] = q[a];
                     }
@@ -293,10 +314,9 @@ __global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
         }
         if (!__any_sync(FULL, st >= 0)) break;
 
-        // (2) the trial point of this round
         float pt[7];
         bool try_pt = false;
-        int fl = -1;  // >= 0: the fit ends this round with these flags
+        int fl = -1;
         if (st >= 0) {
             if (fresh) {
 #pragma unroll
@@ -322,21 +342,18 @@ __global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
                 }
             }
         }
-        // (3) chi^2 and normal equations at the trial point
         float Ht[28], gt[7], c2t = 0.f;
+        // both lanes of a slot take the same branch: their states are identical
         if (try_pt) {
             const float* wts = WEIGHTED ? J.weights + st * NP : nullptr;
-            c2t = eval_lane<MODEL, WEIGHTED>(fl_sm + lane, wts, S, J.beta, pt, Ht, gt);
+            c2t = eval_lane<MODEL, WEIGHTED, G, PITCH>(fl_sm + slot, wts, S, J.beta, pt, Ht, gt);
         }
-        // (4) accept, reject or stop
         if (try_pt) {
             bool take = fresh;
             if (!fresh) {
                 it++;
                 if (c2t < chi2) {
                     take = true;
-                    // FP32 chi^2 resolves ~1e-7: the relative-decrease test of the
-                    // FP64 rule (1e-8) is taken at 1e-6 here
                     if ((chi2 - c2t) / chi2 < 1e-6f) fl = 0;
                     lam *= 0.1;
                 } else {
@@ -364,11 +381,13 @@ __global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
             for (int a = 0; a < 7; a++) q[a] = p[a];
             if (q[4] < q[5]) { const float t = q[4]; q[4] = q[5]; q[5] = t; q[6] += 0.5f * F_PI; }
             q[6] = q[6] - F_PI * floorf((q[6] + 0.5f * F_PI) / F_PI);
+            if (lane % G == 0) {
 #pragma unroll
-            for (int a = 0; a < 7; a++) J.params[st * 7 + a] = q[a];
-            J.chi2[st] = chi2;
-            if (J.iters) J.iters[st] = it;
-            if (J.flags) J.flags[st] = fl;
+                for (int a = 0; a < 7; a++) J.params[st * 7 + a] = q[a];
+                J.chi2[st] = chi2;
+                if (J.iters) J.iters[st] = it;
+                if (J.flags) J.flags[st] = fl;
+            }
             st = -1;
         }
         __syncwarp();
@@ -435,22 +454,23 @@ static int sm_count() {
 
 template <int MODEL, bool WEIGHTED>
 static int launch_fit(const FitJob& J, cudaStream_t s) {
-    auto k = k_psf_fit<MODEL, WEIGHTED>;
-    const size_t smem = (size_t)J.S * J.S * FL_PITCH * sizeof(float);
+    constexpr int G = FL_G;
+    auto k = k_psf_fit<MODEL, WEIGHTED, G>;
+    const size_t smem = (size_t)J.S * J.S * (32 / G + 1) * sizeof(float);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int per = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 32, smem) != cudaSuccess || per < 1) per = 1;
     // one resident warp per block and a contiguous chunk of stamps per warp:
-    // as few chunks as fill the GPU, so that each lane fits several stamps
-    const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per, (J.N + 31) / 32);
+    // as few chunks as fill the GPU, so that each slot fits several stamps
+    const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per, (J.N + 32 / G - 1) / (32 / G));
     const int64_t chunk = (J.N + blocks - 1) / blocks;
     k<<<(unsigned)blocks, 32, smem, s>>>(J, chunk);
     return ipp_check_launch("k_psf_fit");
 }
 
 int ipp_launch_psf_fit(const FitJob& J, cudaStream_t s) {
-    if (J.S * J.S * FL_PITCH * sizeof(float) > 227 * 1024)
+    if (J.S * J.S * (32 / FL_G + 1) * sizeof(float) > 227 * 1024)
         return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "stamp size %d above 32", J.S);
     if (J.model == IPP_PSF_GAUSS) return J.weights ? launch_fit<IPP_PSF_GAUSS, true>(J, s) : launch_fit<IPP_PSF_GAUSS, false>(J, s);
     return J.weights ? launch_fit<IPP_PSF_MOFFAT, true>(J, s) : launch_fit<IPP_PSF_MOFFAT, false>(J, s);
