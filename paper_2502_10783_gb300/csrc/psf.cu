@@ -3,12 +3,11 @@
 // Gaussian, 7 parameters x0, y0, F, sky, sx, sy, theta, point-sampled at the
 // pixel centres of an S x S stamp).
 //
-// The fit (k_psf_fit) gives each stamp two lanes of a warp: both keep the
-// stamp's LM state, J'WJ (28 terms), J'W r (7) and chi^2 in registers, each
-// evaluates half of the stamp's rows from a column of the warp's shared-memory
-// tile, and one shuffle adds the halves.  The damped 7 x 7 normal equations are
-// solved in FP64 (LDL', no square roots), one system per lane, so one FP64
-// instruction of the warp serves 16 stamps.  The forward model and its adjoint
+// The fit (k_psf_fit) runs one stamp per lane: each lane keeps its LM state,
+// J'WJ (28 terms), J'W r (7) and chi^2 in registers and evaluates its stamp from
+// a column of the warp's shared-memory tile.  The damped 7 x 7 normal equations
+// are solved in FP64 (LDL', no square roots), one system per lane, so one FP64
+// instruction of the warp serves 32 stamps.  The forward model and its adjoint
 // (k_psf_fwd, k_psf_adj) evaluate the same point-sampled model.
 #include <math.h>
 
@@ -59,18 +58,68 @@ __device__ __forceinline__ void psf_eval(const float p[7], float dx, float dy, i
     o.j[6] = dPdq * 2.0f * u * v * ((sy - sx) * (sy + sx)) * isx2 * isy2;
 }
 
+// The FP64 pipe of this part is narrow (1/64 of the FP32 rate), so the solve
+// spends it on the arithmetic of the factorisation alone: the widening of the
+// FP32 normal equations, the pivot tests and the reciprocal seeds are integer
+// operations on the IEEE-754 bit patterns.
+
+// Exact float -> double (sign, exponent rebiased by 1023 - 127, mantissa
+// shifted up by 52 - 23 bits); zeros, infinities and NaNs map to their double
+// counterparts, subnormals take the conversion instruction.
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu, sg = u & 0x80000000u;
+    if (e == 0u && m != 0u) return (double)f;
+    const uint32_t e64 = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
+    return __hiloint2double((int)(sg | (e64 << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// double -> float rounded to nearest (ties away from zero) for |v| in the
+// normal single range, 0 below it and infinity above it.
+__device__ __forceinline__ float narrow(double v) {
+    const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    const uint32_t sg = hi & 0x80000000u;
+    if (e <= 0) return __uint_as_float(sg);
+    if (e >= 255) return __uint_as_float(sg | 0x7f800000u);
+    // exponent and the top 23 mantissa bits, plus the first discarded bit
+    // (a carry out of the mantissa moves into the exponent, as it should)
+    const uint32_t body = ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return __uint_as_float(sg | (body + ((lo >> 28) & 1u)));
+}
+
+// 1/d for a pivot d by Newton's iteration x <- x + x (1 - d x) from a
+// single-precision seed; each step doubles the correct bits (about 22 -> 44 ->
+// beyond double precision).  Pivots outside 2^-100 .. 2^100 divide.
+__device__ __forceinline__ double recip_pivot(double d) {
+    const int e = (__double2hiint(d) >> 20) & 0x7ff;
+    if (e > 923 && e < 1123) {
+        double x = widen(__fdividef(1.0f, narrow(d)));
+        x = fma(x, fma(-d, x, 1.0), x);
+        return fma(x, fma(-d, x, 1.0), x);
+    }
+    return 1.0 / d;
+}
+
+// d > 0, finite and normal: sign clear, exponent field in 1 .. 2046
+__device__ __forceinline__ bool pivot_ok(double d) {
+    const uint32_t hi = (uint32_t)__double2hiint(d);
+    return hi - 0x00100000u < 0x7fe00000u;
+}
+
+__device__ __forceinline__ int tri(int i, int j) { return i * (i - 1) / 2 + j; }  // strictly lower, j < i
+
 // Solve (H + lambda D) x = g, D = diag(H) floored at 1e-9 max(diag), in FP64 by
 // an LDL' factorisation (no square roots).  H packed upper-triangular row-major
 // (28 entries).  Row-oriented: row i of L is formed from the earlier rows with
 // W(q) = L(i,q) D(q) held as a temporary, so each product L(i,q) D(q) L(j,q)
 // costs one fused multiply-add.  Returns false if a pivot is not positive.
-__device__ __forceinline__ int tri(int i, int j) { return i * (i - 1) / 2 + j; }  // strictly lower, j < i
-
 __device__ __forceinline__ bool solve7(const float Hf[28], const float gf[7], double lam, double x[7]) {
     double L[21], iD[7];
-    double dmax = 0.0;
+    float dmaxf = 0.f;
 #pragma unroll
-    for (int a = 0; a < 7; a++) dmax = fmax(dmax, (double)Hf[a * 7 - a * (a - 1) / 2]);
+    for (int a = 0; a < 7; a++) dmaxf = fmaxf(dmaxf, Hf[a * 7 - a * (a - 1) / 2]);
+    const double floor_d = 1e-9 * widen(dmaxf);
     bool ok = true;
 #pragma unroll
     for (int i = 0; i < 7; i++) {
@@ -78,24 +127,24 @@ __device__ __forceinline__ bool solve7(const float Hf[28], const float gf[7], do
 #pragma unroll
         for (int j = 0; j < i; j++) {
             // H(j, i) from the upper row-major packing
-            double t = (double)Hf[j * 7 - j * (j - 1) / 2 + (i - j)];
+            double t = widen(Hf[j * 7 - j * (j - 1) / 2 + (i - j)]);
 #pragma unroll
             for (int q = 0; q < j; q++) t = fma(-W[q], L[tri(j, q)], t);
             W[j] = t;
             L[tri(i, j)] = t * iD[j];
         }
-        const double h = (double)Hf[i * 7 - i * (i - 1) / 2];
-        double d = fma(lam, fmax(h, 1e-9 * dmax), h);
+        const double h = widen(Hf[i * 7 - i * (i - 1) / 2]);
+        double d = fma(lam, fmax(h, floor_d), h);
 #pragma unroll
         for (int q = 0; q < i; q++) d = fma(-W[q], L[tri(i, q)], d);
-        ok = ok && d > 0.0;
-        iD[i] = 1.0 / d;
+        ok = ok && pivot_ok(d);
+        iD[i] = recip_pivot(d);
     }
     if (!ok) return false;
     double z[7];
 #pragma unroll
     for (int i = 0; i < 7; i++) {
-        double t = (double)gf[i];
+        double t = widen(gf[i]);
 #pragma unroll
         for (int q = 0; q < i; q++) t = fma(-L[tri(i, q)], z[q], t);
         z[i] = t;
@@ -130,10 +179,11 @@ __device__ __forceinline__ bool solve7(const float Hf[28], const float gf[7], do
 // pixels is sequential; chi^2 is summed per stamp row first, so its rounding
 // stays near that of a 2 x S-term sum.
 //
-// G = 2: the shared-memory tile of 16 stamps (15 KB at S = 15) lets 12 warps
-// share an SM, against 7 warps of 32 stamps at G = 1; the price is that each
-// solve is done by both lanes of a slot, which the FP64 pipe can afford.
-constexpr int FL_G = 2;
+// G = 1: one FP64 instruction serves 32 solves.  G = 2 halves the shared-memory
+// tile (12 warps an SM instead of 7) but repeats every solve on both lanes of a
+// slot, and the FP64 pipe of this part (1/64 of the FP32 rate) makes that the
+// slower choice.
+constexpr int FL_G = 1;
 
 // chi^2, J'WJ and J'Wr of one stamp at pp.  The model of psf_eval with the
 // per-trial constants (reciprocal widths, normalisation, trig) taken out of the
@@ -217,35 +267,48 @@ __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const 
     return chi;
 }
 
+// Pixel index of border pixel b (0 <= b < 4S-4) of an S x S stamp: the top
+// row, the bottom row, then rows 1..S-2 alternating left and right edge.
+__device__ __forceinline__ int border_k(int b, int S) {
+    if (b < S) return b;
+    if (b < 2 * S) return (S - 1) * S + (b - S);
+    const int c = b - 2 * S;
+    return (1 + (c >> 1)) * S + ((c & 1) ? S - 1 : 0);
+}
+
 // Default start of stamp `sr` staged in column r: centre, border-median sky, sum
 // above sky, widths 1.6 / 1.4, theta 0.  All lanes of the warp take part and all
-// return the same values.
+// return the same values.  The border keys (at most 4 a lane for S <= 32) stay
+// in registers during the bisection for the two middle order statistics.
 template <int PITCH>
 __device__ __forceinline__ void init_coop(const float* __restrict__ sm, int r, int S, float p[7]) {
     const int lane = threadIdx.x & 31;
     const int NP = S * S, nb = 4 * S - 4;
     const int k0 = (nb - 1) / 2, k1 = nb / 2;
+    uint32_t key[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        const int b = lane + 32 * t;
+        key[t] = b < nb ? fkey(sm[border_k(b, S) * PITCH + r]) : 0xffffffffu;
+    }
+    const int nmine = (nb - lane + 31) >> 5;  // border values this lane holds
     uint32_t lo = 0u, hi = 0xffffffffu;
     while (lo < hi) {  // smallest key with more than k0 border values at or below it
         const uint32_t mid = lo + ((hi - lo) >> 1);
         int c = 0;
-        for (int k = lane; k < NP; k += 32) {
-            const int i = k / S, j = k - i * S;
-            const bool border = i == 0 || j == 0 || i == S - 1 || j == S - 1;
-            c += border && fkey(sm[k * PITCH + r]) <= mid;
-        }
+#pragma unroll
+        for (int t = 0; t < 4; t++) c += t < nmine && key[t] <= mid;
         c = warp_sum_i(c);
         if (c > k0) hi = mid; else lo = mid + 1;
     }
     const uint32_t ka = lo;
     int cle = 0;
     uint32_t nxt = 0xffffffffu;
-    for (int k = lane; k < NP; k += 32) {
-        const int i = k / S, j = k - i * S;
-        if (i == 0 || j == 0 || i == S - 1 || j == S - 1) {
-            const uint32_t kk = fkey(sm[k * PITCH + r]);
-            cle += kk <= ka;
-            if (kk > ka && kk < nxt) nxt = kk;
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        if (t < nmine) {
+            cle += key[t] <= ka;
+            if (key[t] > ka && key[t] < nxt) nxt = key[t];
         }
     }
     cle = warp_sum_i(cle);
@@ -260,7 +323,7 @@ __device__ __forceinline__ void init_coop(const float* __restrict__ sm, int r, i
 }
 
 template <int MODEL, bool WEIGHTED, int G>
-__global__ void __launch_bounds__(32, 12) k_psf_fit(FitJob J, int64_t chunk) {  // 12 warps/SM: <= 168 registers
+__global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
     constexpr int SLOTS = 32 / G, PITCH = SLOTS + 1;
     extern __shared__ float fl_sm[];  // [S*S][PITCH]: pixel k of the stamp of slot s in column s
     const unsigned FULL = 0xffffffffu;
@@ -331,7 +394,7 @@ __global__ void __launch_bounds__(32, 12) k_psf_fit(FitJob J, int64_t chunk) {  
                     if (lam > 1e10) fl = IPP_FLAG_FIT_MAXITER;
                 } else {
 #pragma unroll
-                    for (int a = 0; a < 7; a++) pt[a] = (float)((double)p[a] + delta[a]);
+                    for (int a = 0; a < 7; a++) pt[a] = narrow(widen(p[a]) + delta[a]);
                     if (!(pt[4] > 0.05f) || !(pt[5] > 0.05f)) {
                         lam *= 10.0;
                         it++;
