@@ -179,11 +179,12 @@ __device__ __forceinline__ bool solve7(const float Hf[28], const float gf[7], do
 // pixels is sequential; chi^2 is summed per stamp row first, so its rounding
 // stays near that of a 2 x S-term sum.
 //
-// G = 1: one FP64 instruction serves 32 solves.  G = 2 halves the shared-memory
-// tile (12 warps an SM instead of 7) but repeats every solve on both lanes of a
-// slot, and the FP64 pipe of this part (1/64 of the FP32 rate) makes that the
-// slower choice.
-constexpr int FL_G = 1;
+// G = 1 for large batches: one FP64 instruction serves 32 solves, and G = 2
+// (12 warps an SM instead of 7) measured slower on 200,000 stamps because it
+// repeats every solve on both lanes of a slot, the FP64 pipe of this part
+// running at 1/64 of the FP32 rate.  Batches too small to give every lane a
+// stamp take G = 2 or 4 (fit_lanes_per_stamp), where the shorter rounds win.
+constexpr int FL_MAX_WARPS = 8;
 
 // chi^2, J'WJ and J'Wr of one stamp at pp.  The model of psf_eval with the
 // per-trial constants (reciprocal widths, normalisation, trig) taken out of the
@@ -256,13 +257,16 @@ __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const 
         }
         chi += rowc;
     }
-    if (G == 2) {  // both lanes of the slot are here (their states are identical)
-        const unsigned pm = 3u << ((threadIdx.x & 31) & ~1);
+    if (G > 1) {  // all lanes of the slot are here (their states are identical)
+        const unsigned pm = ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
 #pragma unroll
-        for (int a = 0; a < 28; a++) Ht[a] += __shfl_xor_sync(pm, Ht[a], 1);
+        for (int o = 1; o < G; o <<= 1) {
 #pragma unroll
-        for (int a = 0; a < 7; a++) gt[a] += __shfl_xor_sync(pm, gt[a], 1);
-        chi += __shfl_xor_sync(pm, chi, 1);
+            for (int a = 0; a < 28; a++) Ht[a] += __shfl_xor_sync(pm, Ht[a], o);
+#pragma unroll
+            for (int a = 0; a < 7; a++) gt[a] += __shfl_xor_sync(pm, gt[a], o);
+            chi += __shfl_xor_sync(pm, chi, o);
+        }
     }
     return chi;
 }
@@ -323,17 +327,21 @@ __device__ __forceinline__ void init_coop(const float* __restrict__ sm, int r, i
 }
 
 template <int MODEL, bool WEIGHTED, int G>
-__global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
+__global__ void __launch_bounds__(32 * FL_MAX_WARPS) k_psf_fit(FitJob J, int64_t chunk) {
     constexpr int SLOTS = 32 / G, PITCH = SLOTS + 1;
-    extern __shared__ float fl_sm[];  // [S*S][PITCH]: pixel k of the stamp of slot s in column s
+    extern __shared__ float fl_sm_all[];  // per warp [S*S][PITCH]: pixel k of slot s's stamp in column s
+    __shared__ unsigned long long blk_next;  // next stamp of the block's chunk
     const unsigned FULL = 0xffffffffu;
-    const unsigned HEADS = G == 1 ? FULL : 0x55555555u;  // the first lane of each slot
-    const int lane = threadIdx.x;
+    const unsigned HEADS = G == 1 ? FULL : (G == 2 ? 0x55555555u : 0x11111111u);  // first lane of each slot
+    const int lane = threadIdx.x & 31;
     const int slot = lane / G;
     const int S = J.S, NP = S * S;
+    float* fl_sm = fl_sm_all + (threadIdx.x >> 5) * NP * PITCH;
     const int64_t c0 = (int64_t)blockIdx.x * chunk;
     const int64_t c1 = c0 + chunk < J.N ? c0 + chunk : J.N;
-    int64_t next = c0;
+    if (threadIdx.x == 0) blk_next = (unsigned long long)c0;
+    __syncthreads();
+    bool drained = false;  // the block's chunk has been handed out
     int64_t st = -1;
     float p[7], H[28], g[7], chi2 = 0.f;
     double lam = 0.0;
@@ -343,7 +351,13 @@ __global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
     for (int a = 0; a < 7; a++) p[a] = 0.f;
     while (true) {
         const unsigned idle = __ballot_sync(FULL, st < 0) & HEADS;
-        if (idle && next < c1) {
+        if (idle && !drained) {
+            // the warp takes as many stamps as it has idle slots from the
+            // block's chunk; the shared cursor may run past c1
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&blk_next, (unsigned long long)__popc(idle));
+            const int64_t next = (int64_t)__shfl_sync(FULL, base, 0);
+            drained = next + __popc(idle) >= c1;
             const int rank = __popc(idle & ((1u << (slot * G)) - 1u));
             if (st < 0 && next + rank < c1) {
                 st = next + rank;
@@ -351,7 +365,6 @@ __global__ void __launch_bounds__(32) k_psf_fit(FitJob J, int64_t chunk) {
                 it = 0; nsing = 0;
                 lam = (double)J.lambda0;
             }
-            next += __popc(idle) < c1 - next ? __popc(idle) : c1 - next;
             unsigned nm = __ballot_sync(FULL, fresh) & HEADS;
             while (nm) {
                 const int rl = __ffs(nm) - 1, r = rl / G;
@@ -515,28 +528,59 @@ static int sm_count() {
     return sms > 0 ? sms : 132;
 }
 
-template <int MODEL, bool WEIGHTED>
+static size_t fit_warp_bytes(int S, int G) { return (size_t)S * S * (32 / G + 1) * sizeof(float); }
+static int fit_max_warps(int S, int G) {
+    return (int)std::min<size_t>(FL_MAX_WARPS, (size_t)(227 * 1024) / fit_warp_bytes(S, G));
+}
+
+template <int MODEL, bool WEIGHTED, int G>
 static int launch_fit(const FitJob& J, cudaStream_t s) {
-    constexpr int G = FL_G;
     auto k = k_psf_fit<MODEL, WEIGHTED, G>;
-    const size_t smem = (size_t)J.S * J.S * (32 / G + 1) * sizeof(float);
+    const size_t per_warp = fit_warp_bytes(J.S, G);
+    // warps of one block share a chunk of stamps: the block's chunk drains with
+    // every slot busy until its last few stamps, so the larger the block, the
+    // smaller the idle tail.  One block per SM, as many warps as its shared
+    // memory holds.
+    const int wmax = fit_max_warps(J.S, G);
+    const int64_t warps = std::min<int64_t>((int64_t)sm_count() * wmax, (J.N + 32 / G - 1) / (32 / G));
+    const int64_t blocks = std::min<int64_t>(sm_count(), warps);
+    const int wpb = (int)((warps + blocks - 1) / blocks);
+    const size_t smem = per_warp * wpb;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 32, smem) != cudaSuccess || per < 1) per = 1;
-    // one resident warp per block and a contiguous chunk of stamps per warp:
-    // as few chunks as fill the GPU, so that each slot fits several stamps
-    const int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per, (J.N + 32 / G - 1) / (32 / G));
     const int64_t chunk = (J.N + blocks - 1) / blocks;
-    k<<<(unsigned)blocks, 32, smem, s>>>(J, chunk);
+    k<<<(unsigned)blocks, 32 * wpb, smem, s>>>(J, chunk);
     return ipp_check_launch("k_psf_fit");
 }
 
+// Lanes per stamp: 1 when the stamps fill every lane the GPU can hold (one FP64
+// instruction then serves 32 solves); for smaller batches 2 or 4 lanes share a
+// stamp, so that the batch still spreads over the lanes and each round is
+// shorter.  G is taken while N G stays within 1.25 x the lanes resident at G
+// (measured on 152 SMs, 15 x 15 stamps: G = 4 up to ~12,000 stamps, G = 2 up
+// to ~24,000, G = 1 beyond).
+static int fit_lanes_per_stamp(const FitJob& J) {
+    const int64_t sms = sm_count();
+    for (int G = 4; G > 1; G >>= 1)
+        if (J.N * G * 4 <= sms * fit_max_warps(J.S, G) * 32 * 5) return G;
+    return 1;
+}
+
+template <int MODEL, bool WEIGHTED>
+static int launch_fit_g(const FitJob& J, cudaStream_t s) {
+    switch (fit_lanes_per_stamp(J)) {
+        case 4: return launch_fit<MODEL, WEIGHTED, 4>(J, s);
+        case 2: return launch_fit<MODEL, WEIGHTED, 2>(J, s);
+        default: return launch_fit<MODEL, WEIGHTED, 1>(J, s);
+    }
+}
+
 int ipp_launch_psf_fit(const FitJob& J, cudaStream_t s) {
-    if (J.S * J.S * (32 / FL_G + 1) * sizeof(float) > 227 * 1024)
+    if (fit_warp_bytes(J.S, 1) > 227 * 1024)
         return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "stamp size %d above 32", J.S);
-    if (J.model == IPP_PSF_GAUSS) return J.weights ? launch_fit<IPP_PSF_GAUSS, true>(J, s) : launch_fit<IPP_PSF_GAUSS, false>(J, s);
-    return J.weights ? launch_fit<IPP_PSF_MOFFAT, true>(J, s) : launch_fit<IPP_PSF_MOFFAT, false>(J, s);
+    if (J.model == IPP_PSF_GAUSS)
+        return J.weights ? launch_fit_g<IPP_PSF_GAUSS, true>(J, s) : launch_fit_g<IPP_PSF_GAUSS, false>(J, s);
+    return J.weights ? launch_fit_g<IPP_PSF_MOFFAT, true>(J, s) : launch_fit_g<IPP_PSF_MOFFAT, false>(J, s);
 }
 
 int ipp_launch_psf_fwd(const float* params, int64_t N, int S, int model, float beta, float* out, cudaStream_t s) {

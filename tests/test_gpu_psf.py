@@ -69,14 +69,21 @@ def test_adjoint_vs_finite_differences(gpu):
         assert np.all(np.abs(fd - ga[:, k]) <= 2e-2 * sc), k
 
 
-def test_fit_parity(gpu, orc):
+@pytest.mark.parametrize("n_batch", [400, 18000, 40000])
+def test_fit_parity(gpu, orc, n_batch):
     """Faint stamps (F of a few hundred ADU on a 1000 ADU sky) crawl for hundreds
     of LM trials on both sides, so at max_iter = 50 about half stop with
     FIT_MAXITER; the parity gate is on stamps that both sides converge, and
-    well-measured stars must converge."""
+    well-measured stars must converge.  The 400 compared stamps lead batches of
+    400, 18,000 and 40,000 stamps, which the fit runs with 4, 2 and 1 lanes per
+    stamp on a 152-SM GPU."""
     stamps, truth = synth.moffat_stamps(400, seed=4000)
     o = orc.psf_fit(stamps)
-    g = {k: host(v) for k, v in gpu.psf_fit(dev(stamps)).items()}
+    batch = stamps
+    if n_batch > 400:
+        pad, _ = synth.moffat_stamps(n_batch - 400, seed=4001, oversample=2)
+        batch = np.concatenate([stamps, pad])
+    g = {k: host(v)[:400] for k, v in gpu.psf_fit(dev(batch)).items()}
     conv = (o["flags"] == 0) & (g["flags"] == 0)
     assert conv.mean() > 0.3
     strong = truth[:, 2] > 5e3
