@@ -31,6 +31,7 @@ FLAG_ANN_FEW = 4
 FLAG_FIT_MAXITER = 8
 FLAG_FIT_SINGULAR = 16
 FLAG_FIT_BAD_SIGMA = 32
+FLAG_KRON_BAD = 64
 
 EST_SIGMA, EST_MEDIAN, EST_MEAN, EST_FACTORS = 0, 1, 2, 3
 PSF_MOFFAT, PSF_GAUSS = 0, 1
@@ -83,6 +84,7 @@ def lib():
             L.orc_overlap.restype = d
             L.orc_aperture.argtypes = [vp, i64, i64, i64, vp, vp, d, d, d, i32, vp, vp, vp, vp, vp]
             L.orc_stamp_cut.argtypes = [vp, i64, i64, i64, vp, vp, i32, vp, vp, vp, vp]
+            L.orc_auto_phot.argtypes = [vp, vp, i64, i64, i64] + [vp] * 6 + [d, d, d] + [vp] * 7
             L.orc_psf_model.argtypes = [vp, i32, i32, d, vp, vp]
             L.orc_psf_fit.argtypes = [vp, i64, i32, vp, vp, i32, d, i32, d, vp, vp, vp, vp]
             L.orc_psf_init.argtypes = [vp, i32, vp]
@@ -231,6 +233,26 @@ def aperture(sub, x, y, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann=10):
     lib().orc_aperture(_p(sub), W, H, n, _p(x), _p(y), float(r_ap), float(r_in), float(r_out),
                        int(min_ann), _p(out["flux"]), _p(out["sky"]), _p(out["area"]),
                        _p(out["n_ann"]), _p(out["flags"]))
+    return out
+
+
+def auto_phot(sub, labels, stats, k_kron=2.5, r_min=3.5, r_kmax=6.0):
+    """Auto (Kron) photometry of the labelled sources; `stats` holds xmin, xmax,
+    ymin, ymax (int) and xbar, ybar (cast to float32, the precision the
+    library's statistics carry)."""
+    sub = _f32(sub)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    H, W = sub.shape
+    n = len(stats["xbar"])
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    xb, yb = _f32(stats["xbar"]), _f32(stats["ybar"])
+    bb = [i32(stats[k]) for k in ("xmin", "xmax", "ymin", "ymax")]
+    out = dict(flux=np.zeros(n), area=np.zeros(n), kron=np.zeros(n), x2=np.zeros(n),
+               y2=np.zeros(n), xy=np.zeros(n), flags=np.zeros(n, np.int32))
+    lib().orc_auto_phot(_p(sub), _p(labels), W, H, n, *[_p(b) for b in bb], _p(xb), _p(yb),
+                        float(k_kron), float(r_min), float(r_kmax), _p(out["flux"]),
+                        _p(out["area"]), _p(out["kron"]), _p(out["x2"]), _p(out["y2"]),
+                        _p(out["xy"]), _p(out["flags"]))
     return out
 
 

@@ -498,6 +498,110 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
     return ORC_OK;
 }
 
+/* ------------------------------------------------------ auto photometry */
+/*
+ * Auto photometry (Sec. 2.2.5 lists it beside aperture and isophotal photometry;
+ * the method is paper-silent: the reading follows Kron's first-moment radius
+ * and SExtractor's automatic elliptical aperture).  Per source k (label k+1):
+ *  1. shape -- second moments of sub over the isophotal footprint about the
+ *     given barycentre:  x2 = sum f dx^2 / sum f, y2 = sum f dy^2 / sum f,
+ *     xy = sum f dx dy / sum f, dx = x - xbar, dy = y - ybar.  A footprint
+ *     thinner than a pixel (x2 y2 - xy^2 < 1/144) gets 1/12, the variance of a
+ *     uniform pixel, added to x2 and y2.  A footprint whose sum f is not
+ *     positive takes x2 = y2 = 1/12, xy = 0 and is flagged KRON_BAD.
+ *  2. elliptical radius of a pixel centre:
+ *     r^2 = (y2 dx^2 - 2 xy dx dy + x2 dy^2) / (x2 y2 - xy^2),
+ *     the Mahalanobis distance under the moment covariance (r = 1 on its
+ *     1-sigma ellipse).
+ *  3. Kron radius r1 = sum r f / sum f over every in-frame pixel with
+ *     r <= r_kmax (not only the footprint; neighbours are not masked).  If
+ *     either sum is not positive, r1 = 0 and KRON_BAD.
+ *  4. aperture R = max(k_kron r1, r_min); flux = sum f over in-frame pixels
+ *     with r <= R, area = their number; EDGE when a pixel centre with r <= R
+ *     lies off the frame.
+ * Integer points examined: the box xbar -/+ (R sqrt(x2) + 1), likewise in y,
+ * which holds the whole ellipse r <= R.
+ */
+static void ellipse_box(double c, double half, int64_t* lo, int64_t* hi) {
+    *lo = (int64_t)floor(c - half) - 1;
+    *hi = (int64_t)ceil(c + half) + 1;
+}
+
+int orc_auto_phot(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t n,
+                  const int32_t* xmin, const int32_t* xmax, const int32_t* ymin,
+                  const int32_t* ymax, const float* xbar, const float* ybar,
+                  double k_kron, double r_min, double r_kmax, double* flux, double* area,
+                  double* kron, double* x2o, double* y2o, double* xyo, int32_t* flags) {
+    if (!sub || !labels || W <= 0 || H <= 0 || n < 0 || !(k_kron > 0) || !(r_min >= 0) ||
+        !(r_kmax > 0))
+        return ORC_INVALID_ARG;
+    for (int64_t k = 0; k < n; k++) {
+        const double xb = (double)xbar[k], yb = (double)ybar[k];
+        int32_t fl = 0;
+        /* 1. moments over the footprint */
+        double s0 = 0.0, sxx = 0.0, syy = 0.0, sxy = 0.0;
+        for (int64_t i = ymin[k]; i <= ymax[k]; i++)
+            for (int64_t j = xmin[k]; j <= xmax[k]; j++) {
+                if (labels[i * W + j] != (int32_t)(k + 1)) continue;
+                const double f = (double)sub[i * W + j], dx = (double)j - xb, dy = (double)i - yb;
+                s0 += f;
+                sxx += f * dx * dx;
+                syy += f * dy * dy;
+                sxy += f * dx * dy;
+            }
+        double x2, y2, xy;
+        if (s0 > 0.0) {
+            x2 = sxx / s0; y2 = syy / s0; xy = sxy / s0;
+            if (x2 * y2 - xy * xy < 1.0 / 144.0) { x2 += 1.0 / 12.0; y2 += 1.0 / 12.0; }
+        } else {
+            x2 = 1.0 / 12.0; y2 = 1.0 / 12.0; xy = 0.0;
+            fl |= ORC_FLAG_KRON_BAD;
+        }
+        const double det = x2 * y2 - xy * xy;
+        /* 3. Kron radius */
+        double r1 = 0.0;
+        if (!(fl & ORC_FLAG_KRON_BAD)) {
+            int64_t x0, x1, y0, y1;
+            ellipse_box(xb, r_kmax * sqrt(x2), &x0, &x1);
+            ellipse_box(yb, r_kmax * sqrt(y2), &y0, &y1);
+            double sr = 0.0, sf = 0.0;
+            for (int64_t i = y0; i <= y1; i++)
+                for (int64_t j = x0; j <= x1; j++) {
+                    if (i < 0 || i >= H || j < 0 || j >= W) continue;
+                    const double dx = (double)j - xb, dy = (double)i - yb;
+                    const double r2 = (y2 * dx * dx - 2.0 * xy * dx * dy + x2 * dy * dy) / det;
+                    if (r2 > r_kmax * r_kmax) continue;
+                    const double f = (double)sub[i * W + j];
+                    sr += sqrt(r2) * f;
+                    sf += f;
+                }
+            if (sf > 0.0 && sr > 0.0) r1 = sr / sf;
+            else fl |= ORC_FLAG_KRON_BAD;
+        }
+        /* 4. the automatic aperture */
+        const double R = fmax(k_kron * r1, r_min);
+        int64_t x0, x1, y0, y1;
+        ellipse_box(xb, R * sqrt(x2), &x0, &x1);
+        ellipse_box(yb, R * sqrt(y2), &y0, &y1);
+        double fs = 0.0, na = 0.0;
+        for (int64_t i = y0; i <= y1; i++)
+            for (int64_t j = x0; j <= x1; j++) {
+                const double dx = (double)j - xb, dy = (double)i - yb;
+                const double r2 = (y2 * dx * dx - 2.0 * xy * dx * dy + x2 * dy * dy) / det;
+                if (r2 > R * R) continue;
+                if (i < 0 || i >= H || j < 0 || j >= W) { fl |= ORC_FLAG_EDGE; continue; }
+                fs += (double)sub[i * W + j];
+                na += 1.0;
+            }
+        flux[k] = fs; area[k] = na; kron[k] = r1;
+        if (x2o) x2o[k] = x2;
+        if (y2o) y2o[k] = y2;
+        if (xyo) xyo[k] = xy;
+        flags[k] = fl;
+    }
+    return ORC_OK;
+}
+
 /* ----------------------------------------------------------- stamps ---- */
 /* The stamp of a source is the S x S block of the subtracted frame centred on
  * the pixel nearest to its position, ties rounded up: centre column

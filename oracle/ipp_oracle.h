@@ -28,6 +28,7 @@
 #define ORC_FLAG_FIT_MAXITER 8
 #define ORC_FLAG_FIT_SINGULAR 16
 #define ORC_FLAG_FIT_BAD_SIGMA 32
+#define ORC_FLAG_KRON_BAD 64
 
 /* background estimators, Sec. 2.2.2 Eqs. 1-4 */
 #define ORC_EST_SIGMA 0   /* Eq. 3: 2.5 median - 1.5 mean (default) */
@@ -89,6 +90,15 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
                  const float* x, const float* y, double r_ap, double r_in,
                  double r_out, int32_t min_ann, double* flux, double* sky,
                  double* area, int32_t* n_ann, int32_t* flags);
+
+/* Auto (Kron) photometry (Sec. 2.2.5; method paper-silent): moments over the
+ * footprint labels == k+1, Kron radius within elliptical radius r_kmax,
+ * flux within max(k_kron r1, r_min); see the definition for the steps. */
+int orc_auto_phot(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t n,
+                  const int32_t* xmin, const int32_t* xmax, const int32_t* ymin,
+                  const int32_t* ymax, const float* xbar, const float* ybar,
+                  double k_kron, double r_min, double r_kmax, double* flux, double* area,
+                  double* kron, double* x2, double* y2, double* xy, int32_t* flags);
 
 /* Stamp cut (paper-silent; input of the PSF fit): S x S stamp whose centre pixel
  * is (floor(x + 1/2), floor(y + 1/2)); out-of-frame pixels 0 with weight 0. */
