@@ -518,9 +518,10 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
  *     either sum is not positive, r1 = 0 and KRON_BAD.
  *  4. aperture R = max(k_kron r1, r_min); flux = sum f over in-frame pixels
  *     with r <= R, area = their number; EDGE when a pixel centre with r <= R
- *     lies off the frame.
+ *     lies in the one-pixel border around the frame (rows -1 and H, columns
+ *     -1 and W).
  * Integer points examined: the box xbar -/+ (R sqrt(x2) + 1), likewise in y,
- * which holds the whole ellipse r <= R.
+ * which holds the whole ellipse r <= R, cut to the frame and its border.
  */
 static void ellipse_box(double c, double half, int64_t* lo, int64_t* hi) {
     *lo = (int64_t)floor(c - half) - 1;
@@ -583,6 +584,10 @@ int orc_auto_phot(const float* sub, const int32_t* labels, int64_t W, int64_t H,
         int64_t x0, x1, y0, y1;
         ellipse_box(xb, R * sqrt(x2), &x0, &x1);
         ellipse_box(yb, R * sqrt(y2), &y0, &y1);
+        if (x0 < -1) x0 = -1;
+        if (x1 > W) x1 = W;
+        if (y0 < -1) y0 = -1;
+        if (y1 > H) y1 = H;
         double fs = 0.0, na = 0.0;
         for (int64_t i = y0; i <= y1; i++)
             for (int64_t j = x0; j <= x1; j++) {
