@@ -409,6 +409,9 @@ def main():
     stages["centroid"] = timeit(lambda k: ipp.centroid(subbuf, st["xbar"], st["ybar"], n_src=nsrc, max_src=65536))
     cx, cy, _, _ = ipp.centroid(subbuf, st["xbar"], st["ybar"], n_src=nsrc, max_src=65536)
     stages["aperture_phot"] = timeit(lambda k: ipp.aperture_phot(subbuf, cx, cy, n_src=nsrc, max_src=65536))
+    # auto (Kron) photometry of the same catalog: a widening of the path, timed
+    # beside it, not part of the step
+    stages["auto_phot"] = timeit(lambda k: ipp.auto_phot(subbuf, lab, nsrc, st, max_src=65536))
 
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)

@@ -15,6 +15,7 @@
  *   ipp_centroid      windowed centroid of each candidate     (positions, Sec. 2.2.5)
  *   ipp_aperture_phot circular aperture photometry with a local sky annulus
  *                                                             (Sec. 2.2.5)
+ *   ipp_auto_phot     auto (Kron) photometry in an elliptical aperture (Sec. 2.2.5)
  *   ipp_stamp_cut     S x S stamps at the measured positions (input of the fit)
  *   ipp_psf_fit       batched Levenberg-Marquardt PSF fit of stamps
  *   ipp_extract       all catalog steps of one frame, fused where the data allow
@@ -66,6 +67,7 @@ extern "C" {
 #define IPP_FLAG_FIT_MAXITER 8       /* PSF fit stopped at max_iter */
 #define IPP_FLAG_FIT_SINGULAR 16     /* PSF fit normal matrix not positive definite */
 #define IPP_FLAG_FIT_BAD_SIGMA 32    /* PSF fit width at or below 0.05 px */
+#define IPP_FLAG_KRON_BAD 64         /* auto photometry: no usable Kron radius (minimum aperture used) */
 
 /* background estimators (Sec. 2.2.2) */
 #define IPP_EST_SIGMA 0   /* Eq. 3: 2.5 median - 1.5 mean (default) */
@@ -112,6 +114,14 @@ typedef struct {
     float r_in, r_out;  /* sky annulus: pixel centres with r_in <= d < r_out [8, 12]; r_out <= 32 */
     int32_t min_ann;    /* fewest annulus pixels for a sky value [10] */
 } ipp_phot_params;
+
+/* Auto (Kron) photometry parameters (paper-silent reading). */
+typedef struct {
+    float k_kron;       /* aperture = k_kron x Kron radius, in moment units [2.5] */
+    float r_min;        /* smallest aperture, moment units [3.5] */
+    float r_kmax;       /* Kron radius measured out to this moment radius [6] */
+    int32_t reserved;
+} ipp_auto_params;
 
 /* PSF fit parameters (paper-silent reading). */
 typedef struct {
@@ -270,6 +280,36 @@ int ipp_aperture_phot(const float* sub, int64_t W, int64_t H, int64_t pitch,
                       const int32_t* n_src_dev, int32_t max_src, const float* x, const float* y,
                       const ipp_phot_params* p, float* flux, float* sky, float* area,
                       int32_t* n_ann, int32_t* flags, void* stream);
+
+/*
+ * ipp_auto_phot -- auto (Kron) photometry; Sec. 2.2.5 lists auto photometry
+ * beside aperture and isophotal photometry without defining it (reading after
+ * Kron's first-moment radius and SExtractor's automatic aperture):
+ *   1. second moments of sub over the source's isophotal footprint (pixels with
+ *      labels == k+1 inside its bounding box) about (xbar, ybar):
+ *      x2 = sum f dx^2 / sum f, y2, xy likewise; 1/12 is added to x2 and y2
+ *      when x2 y2 - xy^2 < 1/144; a footprint with sum f <= 0 takes
+ *      x2 = y2 = 1/12, xy = 0 and KRON_BAD;
+ *   2. elliptical radius r^2 = (y2 dx^2 - 2 xy dx dy + x2 dy^2) / (x2 y2 - xy^2);
+ *      Kron radius r1 = sum r f / sum f over in-frame pixels with r <= r_kmax
+ *      (neighbours not masked); sums not positive give r1 = 0 and KRON_BAD;
+ *   3. flux = sum f over in-frame pixel centres with r <= max(k_kron r1, r_min),
+ *      area = their number; EDGE when such a pixel centre lies in the one-pixel
+ *      border around the frame.
+ * Frames must hold fewer than 2^31 pixels (32-bit box coordinates).
+ * Processes min(*n_src_dev, max_src) sources; the isophotal flux is
+ * stats->flux of ipp_detect_label.
+ *   labels     device int32 label map of ipp_detect_label (pitch W)
+ *   stats      host struct of device arrays (xmin, xmax, ymin, ymax, xbar, ybar read)
+ *   flux       device float[max_src] (required); area, kron (r1) nullable;
+ *   shape      nullable device float[3*max_src]: x2, y2, xy per source;
+ *   flags      nullable device int32[max_src]: EDGE, KRON_BAD
+ * Errors: INVALID_ARG for NULL inputs, k_kron <= 0, r_min < 0 or r_kmax <= 0.
+ */
+int ipp_auto_phot(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t pitch,
+                  const int32_t* n_src_dev, int32_t max_src, const ipp_src_stats* stats,
+                  const ipp_auto_params* p, float* flux, float* area, float* kron, float* shape,
+                  int32_t* flags, void* stream);
 
 /*
  * ipp_stamp_cut -- S x S stamps of the subtracted frame around each source, the

@@ -23,7 +23,7 @@ from ._abi import (  # noqa: F401
     FLAG_FIT_MAXITER, FLAG_FIT_SINGULAR, FLAG_WIN_NOT_CONVERGED, IppError, PSF_GAUSS, PSF_MOFFAT,
 )
 
-__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "stamp_cut", "Batch",
+__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "stamp_cut", "Batch",
            "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
 
 
@@ -141,7 +141,7 @@ def _alloc_stats(max_src, dev):
 
 
 def _stats_c(st):
-    return _abi.SrcStats(*[_ptr(st[k]) for k in _STAT_TYPES])
+    return _abi.SrcStats(*[_ptr(st.get(k)) for k in _STAT_TYPES])
 
 
 def detect_label(sub, mesh_rms=None, cfg: BgConfig | None = None, k=1.5, thresh_abs=0.0, min_area=5,
@@ -209,6 +209,28 @@ def aperture_phot(sub, x, y, n_src=None, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann
         _ptr(sub), W, H, sub.stride(0), _ptr(n_src), n, _ptr(x.contiguous()), _ptr(y.contiguous()),
         _abi.PhotParams(r_ap, r_in, r_out, min_ann), _ptr(out["flux"]), _ptr(out["sky"]), _ptr(out["area"]),
         _ptr(out["n_ann"]), _ptr(out["flags"]), _stream()))
+    return {k: v[:n] for k, v in out.items()}
+
+
+def auto_phot(sub, labels, n_src, stats, k_kron=2.5, r_min=3.5, r_kmax=6.0, max_src=None):
+    """Auto (Kron) photometry of the labelled sources (ipp_auto_phot): flux,
+    area, Kron radius, moments (x2, y2, xy) and flags per source.  `labels`,
+    `n_src` and `stats` as returned by detect_label."""
+    L = load()
+    _need_cuda(sub, "sub", torch.float32)
+    _need_cuda(labels, "labels", torch.int32)
+    H, W = sub.shape
+    n = stats["xbar"].numel() if max_src is None else max_src
+    dev = sub.device
+    out = dict(flux=torch.empty(max(n, 1), dtype=torch.float32, device=dev))
+    out["area"] = torch.empty_like(out["flux"])
+    out["kron"] = torch.empty_like(out["flux"])
+    out["shape"] = torch.empty((max(n, 1), 3), dtype=torch.float32, device=dev)
+    out["flags"] = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    _abi.check("ipp_auto_phot", L.ipp_auto_phot(
+        _ptr(sub), _ptr(labels.contiguous()), W, H, sub.stride(0), _ptr(n_src), n, _stats_c(stats),
+        _abi.AutoParams(k_kron, r_min, r_kmax, 0), _ptr(out["flux"]), _ptr(out["area"]), _ptr(out["kron"]),
+        _ptr(out["shape"]), _ptr(out["flags"]), _stream()))
     return {k: v[:n] for k, v in out.items()}
 
 

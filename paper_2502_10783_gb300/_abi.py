@@ -40,6 +40,10 @@ class PhotParams(C.Structure):
     _fields_ = [("r_ap", f32), ("r_in", f32), ("r_out", f32), ("min_ann", i32)]
 
 
+class AutoParams(C.Structure):
+    _fields_ = [("k_kron", f32), ("r_min", f32), ("r_kmax", f32), ("reserved", i32)]
+
+
 class FitParams(C.Structure):
     _fields_ = [("model", i32), ("beta", f32), ("max_iter", i32), ("lambda0", f32)]
 
@@ -84,6 +88,8 @@ PROTOTYPES = {
     "ipp_centroid": ([vp, i64, i64, i64, vp, i32, vp, vp, C.POINTER(CenParams), vp, vp, vp, vp, vp], i32),
     "ipp_aperture_phot": ([vp, i64, i64, i64, vp, i32, vp, vp, C.POINTER(PhotParams), vp, vp, vp, vp, vp, vp],
                           i32),
+    "ipp_auto_phot": ([vp, vp, i64, i64, i64, vp, i32, C.POINTER(SrcStats), C.POINTER(AutoParams), vp, vp, vp,
+                       vp, vp, vp], i32),
     "ipp_stamp_cut": ([vp, i64, i64, i64, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp], i32),
     "ipp_extract_workspace_size": ([i64, i64, C.POINTER(BgParams)], sz),
     "ipp_extract": ([vp, i32, i64, i64, i64, C.POINTER(Calib), C.POINTER(BgParams), C.POINTER(DetParams),

@@ -225,6 +225,28 @@ extern "C" int ipp_aperture_phot(const float* sub, int64_t W, int64_t H, int64_t
     return ipp_launch_aperture(J, (cudaStream_t)stream);
 }
 
+extern "C" int ipp_auto_phot(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t pitch,
+                             const int32_t* n_src_dev, int32_t max_src, const ipp_src_stats* stats,
+                             const ipp_auto_params* p, float* flux, float* area, float* kron, float* shape,
+                             int32_t* flags, void* stream) {
+    if (int e = check_frame(sub, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(p && p->k_kron > 0.f && p->r_min >= 0.f && p->r_kmax > 0.f, "bad auto photometry params");
+    REQUIRE(labels && n_src_dev && stats && flux, "NULL pointer");
+    REQUIRE(stats->xmin && stats->xmax && stats->ymin && stats->ymax && stats->xbar && stats->ybar,
+            "stats arrays NULL");
+    REQUIRE(max_src >= 0, "max_src < 0");
+    REQUIRE((W + 2) * (H + 2) < (int64_t(1) << 31) && pitch * H < (int64_t(1) << 31),
+            "auto photometry needs a frame below 2^31 pixels");
+    AutoJob J;
+    J.sub = sub; J.labels = labels; J.W = W; J.H = H; J.pitch = pitch;
+    J.n_src_dev = n_src_dev; J.max_src = max_src;
+    J.xmin = stats->xmin; J.xmax = stats->xmax; J.ymin = stats->ymin; J.ymax = stats->ymax;
+    J.xbar = stats->xbar; J.ybar = stats->ybar;
+    J.k_kron = p->k_kron; J.r_min = p->r_min; J.r_kmax = p->r_kmax;
+    J.flux = flux; J.area = area; J.kron = kron; J.shape = shape; J.flags = flags;
+    return ipp_launch_auto_phot(J, (cudaStream_t)stream);
+}
+
 extern "C" int ipp_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, const int32_t* n_src_dev,
                              int32_t max_src, const float* x, const float* y, int32_t S, float* stamps,
                              float* weights, int32_t* origin, int32_t* flags, void* stream) {

@@ -66,6 +66,22 @@ struct PhotJob {
     int32_t* flags;
 };
 
+struct AutoJob {
+    const float* sub;
+    const int32_t* labels;  // pitch W
+    int64_t W, H, pitch;
+    const int32_t* n_src_dev;
+    int32_t max_src;
+    const int32_t *xmin, *xmax, *ymin, *ymax;
+    const float *xbar, *ybar;
+    float k_kron, r_min, r_kmax;
+    float* flux;
+    float* area;
+    float* kron;
+    float* shape;  // nullable: x2, y2, xy per source
+    int32_t* flags;
+};
+
 // detection: mode 0 = threshold a given sub frame, 1 = given bit mask,
 // 2 = fused with interpolation + subtraction of the raw frame
 struct DetectArgs {
@@ -122,6 +138,7 @@ int ipp_launch_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, 
                          int32_t max_src, const float* x, const float* y, int S, float* stamps, float* weights,
                          int32_t* origin, int32_t* flags, cudaStream_t s);
 int ipp_launch_aperture(const ipp::PhotJob& J, cudaStream_t s);
+int ipp_launch_auto_phot(const ipp::AutoJob& J, cudaStream_t s);
 int ipp_launch_psf_fit(const ipp::FitJob& J, cudaStream_t s);
 int ipp_launch_psf_fwd(const float* params, int64_t N, int S, int model, float beta, float* model_out, cudaStream_t s);
 int ipp_launch_psf_adj(const float* params, int64_t N, int S, int model, float beta, const float* grad_model,

@@ -713,6 +713,194 @@ __global__ void __launch_bounds__(P_THREADS) k_stamp_cut(const float* __restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// Auto (Kron) photometry (Sec. 2.2.5 lists it; method paper-silent), three
+// passes over small boxes of the subtracted frame (read through the caches
+// right after the frame is written):
+//   1. second moments of sub over the isophotal footprint (labels == k+1 in the
+//      source's bounding box) about its barycentre; 1/12 is added to x2 and y2
+//      when x2 y2 - xy^2 < 1/144 (a footprint thinner than a pixel);
+//   2. Kron radius r1 = sum r f / sum f over in-frame pixels with elliptical
+//      (Mahalanobis) radius r <= r_kmax,
+//      r^2 = (y2 dx^2 - 2 xy dx dy + x2 dy^2) / (x2 y2 - xy^2);
+//   3. flux and pixel count within r <= max(k_kron r1, r_min); EDGE when a
+//      pixel centre inside that ellipse lies in the one-pixel border around
+//      the frame.
+// A warp takes a source whose footprint box has at most AUTO_BIG_BOX pixels
+// (k_auto_phot); larger sources, whose Kron and aperture boxes run to tens of
+// thousands of pixels, take a whole block (k_auto_phot_big), so that no single
+// warp carries the tail of the launch.  Each thread sums its pixels in FP32 and
+// the group adds them in a fixed order, leaving identical totals in every
+// thread, so all threads take the same decisions afterwards.
+constexpr int AUTO_BIG_BOX = 128;
+
+// Integer points examined for an ellipse of half-widths `half` about c: one
+// beyond each rounded end (the oracle's box), clipped to [lo_clip, hi_clip].
+__device__ __forceinline__ void auto_box(float c, float half, int lo_clip, int hi_clip, int& lo, int& hi) {
+    lo = max((int)fmaxf(floorf(c - half) - 1.0f, (float)lo_clip), lo_clip);
+    hi = min((int)fminf(ceilf(c + half) + 1.0f, (float)hi_clip), hi_clip);
+}
+
+// Sum over the NT threads of a group (a warp, or a block of NT threads with
+// `red` holding NT/32 floats of shared memory); every thread gets the total.
+template <int NT>
+__device__ __forceinline__ float auto_sum(float v, float* red) {
+    v = warp_sum(v);
+    if constexpr (NT == 32) {
+        return v;
+    } else {
+        __syncthreads();  // earlier readers of red are done
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < NT / 32; w++) t += red[w];
+        return t;
+    }
+}
+template <int NT>
+__device__ __forceinline__ bool auto_any(bool v) {
+    if constexpr (NT == 32) return __any_sync(0xffffffffu, v);
+    else return __syncthreads_or(v) != 0;
+}
+
+// The w x h box at (x0, y0), visited by the NT threads of a group (rank me) in
+// raster order, four pixels a thread in flight: the values (and, for the
+// footprint pass, the labels) of a step are loaded before any is used.  The
+// box lies within the frame plus a one-pixel border, so 32-bit coordinates
+// hold it (frames below 2^31 pixels).  (A column per thread, which keeps the
+// column terms in registers, measured slower: narrow boxes leave most of a
+// warp idle.)  fn(i, j, f, in_frame, in_footprint).
+template <int NT, bool LAB, class Fn>
+__device__ __forceinline__ void auto_visit(const AutoJob& J, int x0, int y0, int w, int h, int me, int32_t lab,
+                                           Fn&& fn) {
+    if (w <= 0 || h <= 0) return;
+    const int n = w * h;
+    const int dq = NT / w, dc = NT - dq * w;  // index + NT: dq rows and dc columns on
+    const int W = (int)J.W, H = (int)J.H, pitch = (int)J.pitch;
+    int r = me / w, c = me - r * w;
+    for (int t0 = me; t0 < n; t0 += 4 * NT) {
+        int ii[4], jj[4];
+        bool ok[4], inf[4], inl[4];
+        float f[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            ok[u] = t0 + u * NT < n;
+            ii[u] = y0 + r;
+            jj[u] = x0 + c;
+            c += dc;
+            r += dq;
+            if (c >= w) { c -= w; r++; }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            inf[u] = ok[u] && (unsigned)ii[u] < (unsigned)H && (unsigned)jj[u] < (unsigned)W;
+            f[u] = inf[u] ? __ldg(J.sub + ((int64_t)ii[u] * pitch + jj[u])) : 0.f;
+            inl[u] = LAB && inf[u] && __ldg(J.labels + ((int64_t)ii[u] * W + jj[u])) == lab;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (ok[u]) fn(ii[u], jj[u], f[u], inf[u], inl[u]);
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void auto_source(const AutoJob& J, int64_t k, int me, float* red) {
+    const float xb = __ldg(J.xbar + k), yb = __ldg(J.ybar + k);
+    const int bx0 = __ldg(J.xmin + k), by0 = __ldg(J.ymin + k);
+    const int bw = __ldg(J.xmax + k) - bx0 + 1, bh = __ldg(J.ymax + k) - by0 + 1;
+    const int W = (int)J.W, H = (int)J.H;
+    const int32_t lab = (int32_t)(k + 1);
+    int fl = 0;
+    // 1. footprint moments
+    float s0 = 0.f, sxx = 0.f, syy = 0.f, sxy = 0.f;
+    auto_visit<NT, true>(J, bx0, by0, bw, bh, me, lab, [&](int i, int j, float f, bool, bool inl) {
+        if (!inl) return;
+        const float dx = (float)j - xb, dy = (float)i - yb;
+        s0 += f;
+        sxx = fmaf(f * dx, dx, sxx);
+        syy = fmaf(f * dy, dy, syy);
+        sxy = fmaf(f * dx, dy, sxy);
+    });
+    s0 = auto_sum<NT>(s0, red); sxx = auto_sum<NT>(sxx, red);
+    syy = auto_sum<NT>(syy, red); sxy = auto_sum<NT>(sxy, red);
+    float x2, y2, xy;
+    if (s0 > 0.f) {
+        x2 = sxx / s0; y2 = syy / s0; xy = sxy / s0;
+        if (x2 * y2 - xy * xy < 1.0f / 144.0f) { x2 += 1.0f / 12.0f; y2 += 1.0f / 12.0f; }
+    } else {
+        x2 = 1.0f / 12.0f; y2 = 1.0f / 12.0f; xy = 0.f;
+        fl |= IPP_FLAG_KRON_BAD;
+    }
+    const float det = x2 * y2 - xy * xy;
+    const float ca = y2 / det, cb = -2.0f * xy / det, cc = x2 / det;
+    // 2. Kron radius (in-frame pixels only)
+    float r1 = 0.f;
+    if (!(fl & IPP_FLAG_KRON_BAD)) {
+        int x0, x1, y0, y1;
+        auto_box(xb, J.r_kmax * sqrtf(x2), 0, W - 1, x0, x1);
+        auto_box(yb, J.r_kmax * sqrtf(y2), 0, H - 1, y0, y1);
+        const float rk2 = J.r_kmax * J.r_kmax;
+        float sr = 0.f, sf = 0.f;
+        auto_visit<NT, false>(J, x0, y0, x1 - x0 + 1, y1 - y0 + 1, me, lab,
+                              [&](int i, int j, float f, bool, bool) {
+            const float dx = (float)j - xb, dy = (float)i - yb;
+            const float q = fmaf(ca * dx, dx, fmaf(cb * dx, dy, cc * dy * dy));
+            if (q > rk2) return;
+            sr = fmaf(sqrtf(q), f, sr);
+            sf += f;
+        });
+        sr = auto_sum<NT>(sr, red); sf = auto_sum<NT>(sf, red);
+        if (sf > 0.f && sr > 0.f) r1 = sr / sf;
+        else fl |= IPP_FLAG_KRON_BAD;
+    }
+    // 3. the automatic aperture (the frame and its one-pixel border)
+    const float R = fmaxf(J.k_kron * r1, J.r_min), R2 = R * R;
+    int x0, x1, y0, y1;
+    auto_box(xb, R * sqrtf(x2), -1, W, x0, x1);
+    auto_box(yb, R * sqrtf(y2), -1, H, y0, y1);
+    float fs = 0.f, na = 0.f;
+    bool edge = false;
+    auto_visit<NT, false>(J, x0, y0, x1 - x0 + 1, y1 - y0 + 1, me, lab,
+                          [&](int i, int j, float f, bool inf, bool) {
+        const float dx = (float)j - xb, dy = (float)i - yb;
+        const float q = fmaf(ca * dx, dx, fmaf(cb * dx, dy, cc * dy * dy));
+        if (q > R2) return;
+        if (!inf) { edge = true; return; }
+        fs += f;
+        na += 1.0f;
+    });
+    fs = auto_sum<NT>(fs, red); na = auto_sum<NT>(na, red);
+    if (auto_any<NT>(edge)) fl |= IPP_FLAG_EDGE;
+    if (me == 0) {
+        J.flux[k] = fs;
+        if (J.area) J.area[k] = na;
+        if (J.kron) J.kron[k] = r1;
+        if (J.shape) { J.shape[3 * k] = x2; J.shape[3 * k + 1] = y2; J.shape[3 * k + 2] = xy; }
+        if (J.flags) J.flags[k] = fl;
+    }
+}
+
+__device__ __forceinline__ bool auto_is_big(const AutoJob& J, int64_t k) {
+    const int64_t bw = (int64_t)__ldg(J.xmax + k) - __ldg(J.xmin + k) + 1;
+    const int64_t bh = (int64_t)__ldg(J.ymax + k) - __ldg(J.ymin + k) + 1;
+    return bw * bh > AUTO_BIG_BOX;
+}
+
+__global__ void __launch_bounds__(P_THREADS) k_auto_phot(AutoJob J) {
+    const int64_t nsrc = min((int64_t)__ldg(J.n_src_dev), (int64_t)J.max_src);
+    const int64_t nwarps = ((int64_t)gridDim.x * P_THREADS) >> 5;
+    for (int64_t k = (((int64_t)blockIdx.x * P_THREADS) + threadIdx.x) >> 5; k < nsrc; k += nwarps)
+        if (!auto_is_big(J, k)) auto_source<32>(J, k, threadIdx.x & 31, nullptr);
+}
+
+__global__ void __launch_bounds__(P_THREADS) k_auto_phot_big(AutoJob J) {
+    __shared__ float red[P_WARPS];
+    const int64_t nsrc = min((int64_t)__ldg(J.n_src_dev), (int64_t)J.max_src);
+    for (int64_t k = blockIdx.x; k < nsrc; k += gridDim.x)
+        if (auto_is_big(J, k)) auto_source<P_THREADS>(J, k, threadIdx.x, red);
+}
+
 }  // namespace ipp
 
 using namespace ipp;
@@ -737,13 +925,6 @@ static int resident_blocks(K kernel, size_t smem) {
 int ipp_launch_centroid(const CenJob& J, cudaStream_t s) {
     const int R = (int)floorf(J.rad + 0.5f);
     const int nbox = (2 * R + 1) * (2 * R + 1);
-    int ncand = 0;  // pixels the group kernel lists (same test as on the device)
-    for (int di = -R; di <= R; di++)
-        for (int dj = -R; dj <= R; dj++) {
-            const float a = fmaxf(fabsf((float)dj) - 0.5f, 0.f), b = fmaxf(fabsf((float)di) - 0.5f, 0.f);
-            ncand += a * a + b * b < J.rad * J.rad * 1.0001f;
-        }
-    (void)ncand;
     if (2 * R + 1 <= CR_BOX) k_centroid_rows<<<resident_blocks(k_centroid_rows, 0), P_THREADS, 0, s>>>(J);
     else if (nbox <= 32 * 4) k_centroid<4><<<resident_blocks(k_centroid<4>, 0), P_THREADS, 0, s>>>(J);
     else if (nbox <= 32 * 8) k_centroid<8><<<resident_blocks(k_centroid<8>, 0), P_THREADS, 0, s>>>(J);
@@ -770,6 +951,14 @@ int ipp_launch_aperture(const PhotJob& J0, cudaStream_t s) {
     cudaFuncSetAttribute(k_aperture, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     k_aperture<<<resident_blocks(k_aperture, dyn), P_THREADS, dyn, s>>>(J);
     return ipp_check_launch("k_aperture");
+}
+
+int ipp_launch_auto_phot(const AutoJob& J, cudaStream_t s) {
+    if (J.max_src <= 0) return IPP_OK;
+    k_auto_phot<<<resident_blocks(k_auto_phot, 0), P_THREADS, 0, s>>>(J);
+    if (int e = ipp_check_launch("k_auto_phot")) return e;
+    k_auto_phot_big<<<resident_blocks(k_auto_phot_big, 0), P_THREADS, 0, s>>>(J);
+    return ipp_check_launch("k_auto_phot_big");
 }
 
 int ipp_launch_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, const int32_t* n_src_dev,
