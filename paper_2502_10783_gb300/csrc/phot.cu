@@ -726,10 +726,10 @@ __global__ void __launch_bounds__(P_THREADS) k_stamp_cut(const float* __restrict
 //   3. flux and pixel count within r <= max(k_kron r1, r_min); EDGE when a
 //      pixel centre inside that ellipse lies in the one-pixel border around
 //      the frame.
-// A warp takes a source whose footprint box has at most AUTO_BIG_BOX pixels
-// (k_auto_phot); larger sources, whose Kron and aperture boxes run to tens of
-// thousands of pixels, take a whole block (k_auto_phot_big), so that no single
-// warp carries the tail of the launch.  Each thread sums its pixels in FP32 and
+// A warp takes a source whose footprint box has at most AUTO_BIG_BOX pixels;
+// larger sources, whose Kron and aperture boxes run to tens of thousands of
+// pixels, take a whole block, so that no single warp carries the tail of the
+// launch.  Each thread sums its pixels in FP32 and
 // the group adds them in a fixed order, leaving identical totals in every
 // thread, so all threads take the same decisions afterwards.
 constexpr int AUTO_BIG_BOX = 128;
@@ -887,18 +887,17 @@ __device__ __forceinline__ bool auto_is_big(const AutoJob& J, int64_t k) {
     return bw * bh > AUTO_BIG_BOX;
 }
 
+// One launch: each block first takes the large sources of its grid-stride
+// share as a block, then its warps take the small sources of theirs, so the
+// blocks that meet no large source start on the small ones at once.
 __global__ void __launch_bounds__(P_THREADS) k_auto_phot(AutoJob J) {
-    const int64_t nsrc = min((int64_t)__ldg(J.n_src_dev), (int64_t)J.max_src);
-    const int64_t nwarps = ((int64_t)gridDim.x * P_THREADS) >> 5;
-    for (int64_t k = (((int64_t)blockIdx.x * P_THREADS) + threadIdx.x) >> 5; k < nsrc; k += nwarps)
-        if (!auto_is_big(J, k)) auto_source<32>(J, k, threadIdx.x & 31, nullptr);
-}
-
-__global__ void __launch_bounds__(P_THREADS) k_auto_phot_big(AutoJob J) {
     __shared__ float red[P_WARPS];
     const int64_t nsrc = min((int64_t)__ldg(J.n_src_dev), (int64_t)J.max_src);
     for (int64_t k = blockIdx.x; k < nsrc; k += gridDim.x)
         if (auto_is_big(J, k)) auto_source<P_THREADS>(J, k, threadIdx.x, red);
+    const int64_t nwarps = ((int64_t)gridDim.x * P_THREADS) >> 5;
+    for (int64_t k = (((int64_t)blockIdx.x * P_THREADS) + threadIdx.x) >> 5; k < nsrc; k += nwarps)
+        if (!auto_is_big(J, k)) auto_source<32>(J, k, threadIdx.x & 31, nullptr);
 }
 
 }  // namespace ipp
@@ -956,9 +955,7 @@ int ipp_launch_aperture(const PhotJob& J0, cudaStream_t s) {
 int ipp_launch_auto_phot(const AutoJob& J, cudaStream_t s) {
     if (J.max_src <= 0) return IPP_OK;
     k_auto_phot<<<resident_blocks(k_auto_phot, 0), P_THREADS, 0, s>>>(J);
-    if (int e = ipp_check_launch("k_auto_phot")) return e;
-    k_auto_phot_big<<<resident_blocks(k_auto_phot_big, 0), P_THREADS, 0, s>>>(J);
-    return ipp_check_launch("k_auto_phot_big");
+    return ipp_check_launch("k_auto_phot");
 }
 
 int ipp_launch_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, const int32_t* n_src_dev,
