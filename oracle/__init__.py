@@ -85,6 +85,8 @@ def lib():
             L.orc_aperture.argtypes = [vp, i64, i64, i64, vp, vp, d, d, d, i32, vp, vp, vp, vp, vp]
             L.orc_stamp_cut.argtypes = [vp, i64, i64, i64, vp, vp, i32, vp, vp, vp, vp]
             L.orc_auto_phot.argtypes = [vp, vp, i64, i64, i64] + [vp] * 6 + [d, d, d] + [vp] * 7
+            L.orc_deblend.argtypes = [vp, vp, i64, i64, i64, i32, d, vp]
+            L.orc_deblend.restype = i64
             L.orc_psf_model.argtypes = [vp, i32, i32, d, vp, vp]
             L.orc_psf_fit.argtypes = [vp, i64, i32, vp, vp, i32, d, i32, d, vp, vp, vp, vp]
             L.orc_psf_init.argtypes = [vp, i32, vp]
@@ -234,6 +236,17 @@ def aperture(sub, x, y, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann=10):
                        int(min_ann), _p(out["flux"]), _p(out["sky"]), _p(out["area"]),
                        _p(out["n_ann"]), _p(out["flags"]))
     return out
+
+
+def deblend(sub, labels, K, nthresh=32, mincont=0.005):
+    """Deblended label map (objects numbered in raster order) and its count."""
+    sub = _f32(sub)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    H, W = sub.shape
+    out = np.zeros((H, W), np.int32)
+    n = lib().orc_deblend(_p(sub), _p(labels), W, H, int(K), int(nthresh), float(mincont), _p(out))
+    assert n >= 0
+    return out, int(n)
 
 
 def auto_phot(sub, labels, stats, k_kron=2.5, r_min=3.5, r_kmax=6.0):

@@ -498,6 +498,259 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
     return ORC_OK;
 }
 
+/* ------------------------------------------------------------ deblending */
+/*
+ * Deblending (Sec. 2.2.4, source detection: multi-level thresholds between each
+ * candidate's threshold and its peak, a tree of the sub-components found at
+ * each level, traversed bottom-up and pruned on intensity).  Reading:
+ *  levels -- per candidate C (pixels labelled c): T = min sub over C,
+ *    P = max sub over C, L_i = T (P/T)^(i/N) for i = 1 .. N-1 (N = nthresh),
+ *    in FP64.  A candidate with T <= 0 or P <= T stays whole.
+ *  tree -- the nodes of level i are the 8-connected components of
+ *    {p in C : sub(p) > L_i}; level 0 is C itself.  The parent of a level-i
+ *    node is the level-(i-1) node holding its pixels (level sets are nested).
+ *    flux(node) = sum of sub over its pixels.
+ *  objects, from the top level down -- a node without children is one object.
+ *    Otherwise let S be its children whose flux is at least mincont x flux(C):
+ *    |S| >= 2 gives the objects of every member of S; |S| = 1 gives the
+ *    objects of that child when it has two or more, else the node itself;
+ *    |S| = 0 gives the node itself.  C splits when its root yields two or
+ *    more objects.
+ *  pixels -- the pixels of an object's node are its core.  Every other pixel
+ *    of C goes to the object whose elliptical Gaussian is largest there:
+ *    F exp(-r^2/2) / sqrt(x2 y2 - xy^2), with F, barycentre and second moments
+ *    (x2, y2, xy) of the core (weights sub; 1/12 added to x2 and y2 when
+ *    x2 y2 - xy^2 < 1/144) and r the Mahalanobis distance; ties go to the
+ *    object whose core starts first in raster order.
+ *  numbering -- all objects of the frame, 1..K' in raster order of their
+ *    first pixel.
+ * Returns K'.
+ */
+static int cmp_i64(const void* a, const void* b) {
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
+int64_t orc_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t K,
+                    int32_t nthresh, double mincont, int32_t* out) {
+    if (!sub || !labels || !out || W <= 0 || H <= 0 || K < 0 || nthresh < 2) return -1;
+    const int64_t npx = W * H;
+    /* pixel lists of the candidates, raster order (CSR) */
+    int64_t* start = (int64_t*)calloc((size_t)K + 2, sizeof(int64_t));
+    for (int64_t q = 0; q < npx; q++)
+        if (labels[q] > 0 && labels[q] <= K) start[labels[q] + 1]++;
+    for (int64_t c = 0; c <= K; c++) start[c + 1] += start[c];
+    int64_t* pix = (int64_t*)malloc(sizeof(int64_t) * (size_t)(start[K + 1] > 0 ? start[K + 1] : 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(K + 1));
+    for (int64_t c = 0; c <= K; c++) fill[c] = start[c];
+    for (int64_t q = 0; q < npx; q++) {
+        out[q] = 0;
+        if (labels[q] > 0 && labels[q] <= K) pix[fill[labels[q]]++] = q;
+    }
+    /* object id of every pixel (provisional numbering), and each object's first pixel */
+    int64_t* obj_of = (int64_t*)malloc(sizeof(int64_t) * (size_t)(npx > 0 ? npx : 1));
+    int64_t cap_obj = K + 16, nobj = 0;
+    int64_t* obj_first = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap_obj);
+    for (int64_t c = 1; c <= K; c++) {
+        const int64_t n = start[c + 1] - start[c];
+        const int64_t* P = pix + start[c];
+        if (n == 0) continue;
+        double T = INFINITY, Pk = -INFINITY, Fc = 0.0;
+        int64_t i0 = INT64_MAX, i1 = -1, j0 = INT64_MAX, j1 = -1;
+        for (int64_t t = 0; t < n; t++) {
+            const double f = (double)sub[P[t]];
+            if (f < T) T = f;
+            if (f > Pk) Pk = f;
+            Fc += f;
+            const int64_t i = P[t] / W, j = P[t] % W;
+            if (i < i0) i0 = i;
+            if (i > i1) i1 = i;
+            if (j < j0) j0 = j;
+            if (j > j1) j1 = j;
+        }
+        /* local index map of the candidate's box */
+        const int64_t bw = j1 - j0 + 1, bh = i1 - i0 + 1;
+        int64_t* map = (int64_t*)malloc(sizeof(int64_t) * (size_t)(bw * bh));
+        for (int64_t t = 0; t < bw * bh; t++) map[t] = -1;
+        for (int64_t t = 0; t < n; t++) map[(P[t] / W - i0) * bw + (P[t] % W - j0)] = t;
+        /* node of each pixel at each level (-1: below the level); level 0 = node 0 */
+        const int N = nthresh;
+        int64_t* node = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n * N));
+        int64_t* nnodes = (int64_t*)calloc((size_t)N, sizeof(int64_t));
+        for (int64_t t = 0; t < n; t++) node[t] = 0;
+        nnodes[0] = 1;
+        const int split_ok = T > 0.0 && Pk > T;
+        int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+        for (int lv = 1; lv < N; lv++) {
+            int64_t* nd = node + (int64_t)lv * n;
+            for (int64_t t = 0; t < n; t++) nd[t] = -1;
+            if (!split_ok) continue;
+            const double L = T * pow(Pk / T, (double)lv / (double)N);
+            int64_t m = 0;
+            for (int64_t s0 = 0; s0 < n; s0++) {
+                if (nd[s0] >= 0 || !((double)sub[P[s0]] > L)) continue;
+                int64_t head = 0, tail = 0;
+                queue[tail++] = s0;
+                nd[s0] = m;
+                while (head < tail) {
+                    const int64_t u = queue[head++];
+                    const int64_t ui = P[u] / W - i0, uj = P[u] % W - j0;
+                    for (int64_t di = -1; di <= 1; di++)
+                        for (int64_t dj = -1; dj <= 1; dj++) {
+                            const int64_t vi = ui + di, vj = uj + dj;
+                            if (vi < 0 || vi >= bh || vj < 0 || vj >= bw) continue;
+                            const int64_t v = map[vi * bw + vj];
+                            if (v < 0 || nd[v] >= 0 || !((double)sub[P[v]] > L)) continue;
+                            nd[v] = m;
+                            queue[tail++] = v;
+                        }
+                }
+                m++;
+            }
+            nnodes[lv] = m;
+        }
+        /* node offsets, fluxes, parents, first pixel (in the candidate's raster list) */
+        int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N + 1));
+        off[0] = 0;
+        for (int lv = 0; lv < N; lv++) off[lv + 1] = off[lv] + nnodes[lv];
+        const int64_t tot = off[N];
+        double* flux = (double*)calloc((size_t)tot, sizeof(double));
+        int64_t* parent = (int64_t*)malloc(sizeof(int64_t) * (size_t)tot);
+        int64_t* nfirst = (int64_t*)malloc(sizeof(int64_t) * (size_t)tot);
+        for (int64_t g = 0; g < tot; g++) { parent[g] = -1; nfirst[g] = INT64_MAX; }
+        for (int lv = 0; lv < N; lv++)
+            for (int64_t t = 0; t < n; t++) {
+                const int64_t a = node[(int64_t)lv * n + t];
+                if (a < 0) continue;
+                const int64_t g = off[lv] + a;
+                flux[g] += (double)sub[P[t]];
+                if (t < nfirst[g]) nfirst[g] = t;
+                if (lv > 0) parent[g] = off[lv - 1] + node[(int64_t)(lv - 1) * n + t];
+            }
+        /* objects bottom-up: each node's list of object nodes (CSR built per node) */
+        int64_t** objs = (int64_t**)calloc((size_t)tot, sizeof(int64_t*));
+        int64_t* nob = (int64_t*)calloc((size_t)tot, sizeof(int64_t));
+        for (int lv = N - 1; lv >= 0; lv--)
+            for (int64_t a = 0; a < nnodes[lv]; a++) {
+                const int64_t g = off[lv] + a;
+                int64_t nsig = 0, sig = -1, total = 0;
+                if (lv + 1 < N)
+                    for (int64_t b = 0; b < nnodes[lv + 1]; b++) {
+                        const int64_t h = off[lv + 1] + b;
+                        if (parent[h] != g) continue;
+                        if (flux[h] >= mincont * Fc) { nsig++; sig = h; total += nob[h]; }
+                    }
+                int64_t cnt = 0;
+                if (nsig >= 2) cnt = total;
+                else if (nsig == 1 && nob[sig] >= 2) cnt = nob[sig];
+                else cnt = 1;
+                objs[g] = (int64_t*)malloc(sizeof(int64_t) * (size_t)cnt);
+                nob[g] = cnt;
+                if (nsig >= 2) {
+                    int64_t w = 0;
+                    for (int64_t b = 0; b < nnodes[lv + 1]; b++) {
+                        const int64_t h = off[lv + 1] + b;
+                        if (parent[h] != g || !(flux[h] >= mincont * Fc)) continue;
+                        for (int64_t e = 0; e < nob[h]; e++) objs[g][w++] = objs[h][e];
+                    }
+                } else if (nsig == 1 && nob[sig] >= 2) {
+                    for (int64_t e = 0; e < nob[sig]; e++) objs[g][e] = objs[sig][e];
+                } else {
+                    objs[g][0] = g;
+                }
+            }
+        const int64_t no = nob[0];
+        /* order the objects by the first pixel of their cores */
+        int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * no));
+        for (int64_t e = 0; e < no; e++) { ord[2 * e] = nfirst[objs[0][e]]; ord[2 * e + 1] = objs[0][e]; }
+        qsort(ord, (size_t)no, 2 * sizeof(int64_t), cmp_i64);
+        /* level and node index of each object's core */
+        int* olv = (int*)malloc(sizeof(int) * (size_t)no);
+        int64_t* onode = (int64_t*)malloc(sizeof(int64_t) * (size_t)no);
+        for (int64_t e = 0; e < no; e++) {
+            const int64_t g = ord[2 * e + 1];
+            int lv = 0;
+            while (lv + 1 <= N && off[lv + 1] <= g) lv++;
+            olv[e] = lv;
+            onode[e] = g - off[lv];
+        }
+        int64_t* assign = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+        for (int64_t t = 0; t < n; t++) assign[t] = -1;
+        if (no == 1) {
+            for (int64_t t = 0; t < n; t++) assign[t] = 0;
+        } else {
+            double* F = (double*)calloc((size_t)no, sizeof(double));
+            double* mx = (double*)calloc((size_t)no, sizeof(double));
+            double* my = (double*)calloc((size_t)no, sizeof(double));
+            double* ca = (double*)calloc((size_t)no, sizeof(double));
+            double* cb = (double*)calloc((size_t)no, sizeof(double));
+            double* cc = (double*)calloc((size_t)no, sizeof(double));
+            double* nrm = (double*)calloc((size_t)no, sizeof(double));
+            for (int64_t e = 0; e < no; e++) {
+                double s0 = 0, sx = 0, sy = 0;
+                for (int64_t t = 0; t < n; t++) {
+                    if (node[(int64_t)olv[e] * n + t] != onode[e]) continue;
+                    assign[t] = e;
+                    const double f = (double)sub[P[t]];
+                    s0 += f; sx += f * (double)(P[t] % W); sy += f * (double)(P[t] / W);
+                }
+                F[e] = s0; mx[e] = sx / s0; my[e] = sy / s0;
+                double sxx = 0, syy = 0, sxy = 0;
+                for (int64_t t = 0; t < n; t++) {
+                    if (node[(int64_t)olv[e] * n + t] != onode[e]) continue;
+                    const double f = (double)sub[P[t]];
+                    const double dx = (double)(P[t] % W) - mx[e], dy = (double)(P[t] / W) - my[e];
+                    sxx += f * dx * dx; syy += f * dy * dy; sxy += f * dx * dy;
+                }
+                double x2 = sxx / s0, y2 = syy / s0, xy = sxy / s0;
+                if (x2 * y2 - xy * xy < 1.0 / 144.0) { x2 += 1.0 / 12.0; y2 += 1.0 / 12.0; }
+                const double det = x2 * y2 - xy * xy;
+                ca[e] = y2 / det; cb[e] = -2.0 * xy / det; cc[e] = x2 / det;
+                nrm[e] = F[e] / sqrt(det);
+            }
+            for (int64_t t = 0; t < n; t++) {
+                if (assign[t] >= 0) continue;
+                const double x = (double)(P[t] % W), y = (double)(P[t] / W);
+                int64_t best = 0;
+                double bv = -1.0;
+                for (int64_t e = 0; e < no; e++) {
+                    const double dx = x - mx[e], dy = y - my[e];
+                    const double r2 = ca[e] * dx * dx + cb[e] * dx * dy + cc[e] * dy * dy;
+                    const double v = nrm[e] * exp(-0.5 * r2);
+                    if (v > bv) { bv = v; best = e; }
+                }
+                assign[t] = best;
+            }
+            free(F); free(mx); free(my); free(ca); free(cb); free(cc); free(nrm);
+        }
+        /* provisional object ids; the first pixel of each object */
+        if (nobj + no > cap_obj) {
+            while (nobj + no > cap_obj) cap_obj *= 2;
+            obj_first = (int64_t*)realloc(obj_first, sizeof(int64_t) * (size_t)cap_obj);
+        }
+        for (int64_t e = 0; e < no; e++) obj_first[nobj + e] = INT64_MAX;
+        for (int64_t t = 0; t < n; t++) {
+            const int64_t id = nobj + assign[t];
+            obj_of[P[t]] = id;
+            if (P[t] < obj_first[id]) obj_first[id] = P[t];
+        }
+        nobj += no;
+        for (int64_t g = 0; g < tot; g++) free(objs[g]);
+        free(objs); free(nob); free(ord); free(olv); free(onode); free(assign);
+        free(flux); free(parent); free(nfirst); free(off); free(node); free(nnodes); free(queue); free(map);
+    }
+    /* canonical numbering: raster order of the objects' first pixels */
+    int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * (nobj > 0 ? nobj : 1)));
+    for (int64_t e = 0; e < nobj; e++) { ord[2 * e] = obj_first[e]; ord[2 * e + 1] = e; }
+    qsort(ord, (size_t)nobj, 2 * sizeof(int64_t), cmp_i64);
+    int64_t* rank = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nobj > 0 ? nobj : 1));
+    for (int64_t e = 0; e < nobj; e++) rank[ord[2 * e + 1]] = e + 1;
+    for (int64_t c = 1; c <= K; c++)
+        for (int64_t t = start[c]; t < start[c + 1]; t++) out[pix[t]] = (int32_t)rank[obj_of[pix[t]]];
+    free(ord); free(rank); free(obj_first); free(obj_of); free(fill); free(pix); free(start);
+    return nobj;
+}
+
 /* ------------------------------------------------------ auto photometry */
 /*
  * Auto photometry (Sec. 2.2.5 lists it beside aperture and isophotal photometry;

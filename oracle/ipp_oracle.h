@@ -91,6 +91,12 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
                  double r_out, int32_t min_ann, double* flux, double* sky,
                  double* area, int32_t* n_ann, int32_t* flags);
 
+/* Deblending (Sec. 2.2.4): multi-level thresholds, sub-component tree, pruning
+ * on intensity (mincont), remaining pixels to the likeliest object; the map of
+ * all objects numbered in raster order of their first pixel.  Returns K'. */
+int64_t orc_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t K,
+                    int32_t nthresh, double mincont, int32_t* out);
+
 /* Auto (Kron) photometry (Sec. 2.2.5; method paper-silent): moments over the
  * footprint labels == k+1, Kron radius within elliptical radius r_kmax,
  * flux within max(k_kron r1, r_min); see the definition for the steps. */
