@@ -522,8 +522,9 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
  *    (x2, y2, xy) of the core (weights sub; 1/12 added to x2 and y2 when
  *    x2 y2 - xy^2 < 1/144) and r the Mahalanobis distance; ties go to the
  *    object whose core starts first in raster order.
- *  numbering -- all objects of the frame, 1..K' in raster order of their
- *    first pixel.
+ *  numbering -- the objects of candidate 1 first, then those of candidate 2,
+ *    and so on; within a candidate, raster order of each object's first pixel.
+ *    Numbers run 1..K'.
  * Returns K'.
  */
 static int cmp_i64(const void* a, const void* b) {
@@ -551,6 +552,7 @@ int64_t orc_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t 
     int64_t* obj_of = (int64_t*)malloc(sizeof(int64_t) * (size_t)(npx > 0 ? npx : 1));
     int64_t cap_obj = K + 16, nobj = 0;
     int64_t* obj_first = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap_obj);
+    int64_t* obj_cand = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap_obj);
     for (int64_t c = 1; c <= K; c++) {
         const int64_t n = start[c + 1] - start[c];
         const int64_t* P = pix + start[c];
@@ -727,8 +729,9 @@ int64_t orc_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t 
         if (nobj + no > cap_obj) {
             while (nobj + no > cap_obj) cap_obj *= 2;
             obj_first = (int64_t*)realloc(obj_first, sizeof(int64_t) * (size_t)cap_obj);
+            obj_cand = (int64_t*)realloc(obj_cand, sizeof(int64_t) * (size_t)cap_obj);
         }
-        for (int64_t e = 0; e < no; e++) obj_first[nobj + e] = INT64_MAX;
+        for (int64_t e = 0; e < no; e++) { obj_first[nobj + e] = INT64_MAX; obj_cand[nobj + e] = c; }
         for (int64_t t = 0; t < n; t++) {
             const int64_t id = nobj + assign[t];
             obj_of[P[t]] = id;
@@ -739,15 +742,21 @@ int64_t orc_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t 
         free(objs); free(nob); free(ord); free(olv); free(onode); free(assign);
         free(flux); free(parent); free(nfirst); free(off); free(node); free(nnodes); free(queue); free(map);
     }
-    /* canonical numbering: raster order of the objects' first pixels */
-    int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * (nobj > 0 ? nobj : 1)));
-    for (int64_t e = 0; e < nobj; e++) { ord[2 * e] = obj_first[e]; ord[2 * e + 1] = e; }
-    qsort(ord, (size_t)nobj, 2 * sizeof(int64_t), cmp_i64);
+    /* numbering: candidate by candidate (provisional ids are consecutive per
+     * candidate), within one by the raster order of the objects' first pixels */
     int64_t* rank = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nobj > 0 ? nobj : 1));
-    for (int64_t e = 0; e < nobj; e++) rank[ord[2 * e + 1]] = e + 1;
+    int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * (nobj > 0 ? nobj : 1)));
+    for (int64_t e0 = 0; e0 < nobj;) {
+        int64_t e1 = e0 + 1;
+        while (e1 < nobj && obj_cand[e1] == obj_cand[e0]) e1++;
+        for (int64_t e = e0; e < e1; e++) { ord[2 * (e - e0)] = obj_first[e]; ord[2 * (e - e0) + 1] = e; }
+        qsort(ord, (size_t)(e1 - e0), 2 * sizeof(int64_t), cmp_i64);
+        for (int64_t e = e0; e < e1; e++) rank[ord[2 * (e - e0) + 1]] = e0 + (e - e0) + 1;
+        e0 = e1;
+    }
     for (int64_t c = 1; c <= K; c++)
         for (int64_t t = start[c]; t < start[c + 1]; t++) out[pix[t]] = (int32_t)rank[obj_of[pix[t]]];
-    free(ord); free(rank); free(obj_first); free(obj_of); free(fill); free(pix); free(start);
+    free(ord); free(rank); free(obj_first); free(obj_cand); free(obj_of); free(fill); free(pix); free(start);
     return nobj;
 }
 

@@ -92,8 +92,9 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
                  double* area, int32_t* n_ann, int32_t* flags);
 
 /* Deblending (Sec. 2.2.4): multi-level thresholds, sub-component tree, pruning
- * on intensity (mincont), remaining pixels to the likeliest object; the map of
- * all objects numbered in raster order of their first pixel.  Returns K'. */
+ * on intensity (mincont), remaining pixels to the likeliest object; objects
+ * numbered candidate by candidate, within one in raster order of their first
+ * pixel.  Returns K'. */
 int64_t orc_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t K,
                     int32_t nthresh, double mincont, int32_t* out);
 

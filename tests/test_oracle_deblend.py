@@ -40,9 +40,10 @@ def _check_partition(labels, out, K2):
     # each object lies inside one candidate
     for o in range(1, K2 + 1):
         assert len(np.unique(labels[out == o])) == 1
-    # numbering: raster order of first pixels
-    firsts = [np.flatnonzero(out.ravel() == o)[0] for o in range(1, K2 + 1)]
-    assert firsts == sorted(firsts)
+    # numbering: candidate by candidate, within one by raster order of first pixels
+    keys = [(labels.ravel()[np.flatnonzero(out.ravel() == o)[0]], np.flatnonzero(out.ravel() == o)[0])
+            for o in range(1, K2 + 1)]
+    assert keys == sorted(keys)
 
 
 def test_single_star_stays_whole(orc):
