@@ -15,6 +15,7 @@
  *   ipp_centroid      windowed centroid of each candidate     (positions, Sec. 2.2.5)
  *   ipp_aperture_phot circular aperture photometry with a local sky annulus
  *                                                             (Sec. 2.2.5)
+ *   ipp_deblend       multi-threshold deblending of the candidates (Sec. 2.2.4)
  *   ipp_auto_phot     auto (Kron) photometry in an elliptical aperture (Sec. 2.2.5)
  *   ipp_stamp_cut     S x S stamps at the measured positions (input of the fit)
  *   ipp_psf_fit       batched Levenberg-Marquardt PSF fit of stamps
@@ -114,6 +115,12 @@ typedef struct {
     float r_in, r_out;  /* sky annulus: pixel centres with r_in <= d < r_out [8, 12]; r_out <= 32 */
     int32_t min_ann;    /* fewest annulus pixels for a sky value [10] */
 } ipp_phot_params;
+
+/* Deblending parameters (Sec. 2.2.4; values are readings). */
+typedef struct {
+    int32_t nthresh;    /* number of levels N between a candidate's lowest and highest pixel [32] */
+    float mincont;      /* a branch splits off when it holds this fraction of the candidate's flux [0.005] */
+} ipp_deblend_params;
 
 /* Auto (Kron) photometry parameters (paper-silent reading). */
 typedef struct {
@@ -280,6 +287,40 @@ int ipp_aperture_phot(const float* sub, int64_t W, int64_t H, int64_t pitch,
                       const int32_t* n_src_dev, int32_t max_src, const float* x, const float* y,
                       const ipp_phot_params* p, float* flux, float* sky, float* area,
                       int32_t* n_ann, int32_t* flags, void* stream);
+
+/*
+ * ipp_deblend -- deblending of the candidates of ipp_detect_label (Sec. 2.2.4:
+ * multi-level thresholds between each candidate's threshold and its peak, a
+ * tree of the sub-components found at each level, traversed bottom-up and
+ * pruned on intensity).  Reading:
+ *   levels  L_i = T (P/T)^(i/N), i = 1..N-1 (FP64), T and P the candidate's
+ *           lowest and highest pixel; T <= 0 or P <= T keeps it whole;
+ *   tree    nodes of level i are the 8-connected components of the candidate's
+ *           pixels above L_i; level 0 is the candidate;
+ *   objects from the top level down: a node with two or more children holding
+ *           at least mincont of the candidate's flux passes on their objects,
+ *           with one such child it passes on that child's objects when there
+ *           are two or more, otherwise it is one object whose core is its pixels;
+ *   pixels  outside every core go to the object whose elliptical Gaussian (core
+ *           flux, barycentre and second moments; 1/12 added to x2 and y2 when
+ *           x2 y2 - xy^2 < 1/144) is largest there, ties to the earlier core;
+ *   numbers objects of candidate 1 first, then of candidate 2, ...; within a
+ *           candidate by the raster order of the object's first pixel.
+ * Processes min(*n_src_dev, max_src) candidates.
+ *   labels      device int32 label map of ipp_detect_label (pitch W)
+ *   stats       host struct of device arrays (xmin, xmax, ymin, ymax, area read)
+ *   out_labels  device int32[W*H] (pitch W): the deblended map, 0 = background
+ *   n_out_dev   device int32[1]: the number of objects
+ *   ws          device workspace of ipp_deblend_workspace_size(W, H, max_src)
+ *               bytes (112 B per frame pixel), 256-byte aligned
+ * Errors: INVALID_ARG for NULL inputs, nthresh outside 2..256, mincont outside
+ * 0..1, a small workspace or a frame of 2^31 pixels or more.
+ */
+size_t ipp_deblend_workspace_size(int64_t W, int64_t H, int32_t max_src);
+int ipp_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t pitch,
+                const int32_t* n_src_dev, int32_t max_src, const ipp_src_stats* stats,
+                const ipp_deblend_params* p, int32_t* out_labels, int32_t* n_out_dev, void* ws,
+                size_t ws_bytes, void* stream);
 
 /*
  * ipp_auto_phot -- auto (Kron) photometry; Sec. 2.2.5 lists auto photometry

@@ -23,7 +23,7 @@ from ._abi import (  # noqa: F401
     FLAG_FIT_MAXITER, FLAG_FIT_SINGULAR, FLAG_WIN_NOT_CONVERGED, IppError, PSF_GAUSS, PSF_MOFFAT,
 )
 
-__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "stamp_cut", "Batch",
+__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "deblend", "stamp_cut", "Batch",
            "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
 
 
@@ -210,6 +210,26 @@ def aperture_phot(sub, x, y, n_src=None, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann
         _abi.PhotParams(r_ap, r_in, r_out, min_ann), _ptr(out["flux"]), _ptr(out["sky"]), _ptr(out["area"]),
         _ptr(out["n_ann"]), _ptr(out["flags"]), _stream()))
     return {k: v[:n] for k, v in out.items()}
+
+
+def deblend(sub, labels, n_src, stats, nthresh=32, mincont=0.005, max_src=None, ws=None):
+    """Deblended label map and device object count (ipp_deblend).  `labels`,
+    `n_src` and `stats` as returned by detect_label."""
+    L = load()
+    _need_cuda(sub, "sub", torch.float32)
+    _need_cuda(labels, "labels", torch.int32)
+    H, W = sub.shape
+    n = stats["xbar"].numel() if max_src is None else max_src
+    dev = sub.device
+    need = L.ipp_deblend_workspace_size(W, H, n)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    out = torch.empty((H, W), dtype=torch.int32, device=dev)
+    n_out = torch.empty(1, dtype=torch.int32, device=dev)
+    _abi.check("ipp_deblend", L.ipp_deblend(
+        _ptr(sub), _ptr(labels.contiguous()), W, H, sub.stride(0), _ptr(n_src), n, _stats_c(stats),
+        _abi.DeblendParams(nthresh, mincont), _ptr(out), _ptr(n_out), _ptr(ws), ws.numel(), _stream()))
+    return out, n_out
 
 
 def auto_phot(sub, labels, n_src, stats, k_kron=2.5, r_min=3.5, r_kmax=6.0, max_src=None):

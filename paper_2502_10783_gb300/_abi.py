@@ -40,6 +40,10 @@ class PhotParams(C.Structure):
     _fields_ = [("r_ap", f32), ("r_in", f32), ("r_out", f32), ("min_ann", i32)]
 
 
+class DeblendParams(C.Structure):
+    _fields_ = [("nthresh", i32), ("mincont", f32)]
+
+
 class AutoParams(C.Structure):
     _fields_ = [("k_kron", f32), ("r_min", f32), ("r_kmax", f32), ("reserved", i32)]
 
@@ -88,6 +92,9 @@ PROTOTYPES = {
     "ipp_centroid": ([vp, i64, i64, i64, vp, i32, vp, vp, C.POINTER(CenParams), vp, vp, vp, vp, vp], i32),
     "ipp_aperture_phot": ([vp, i64, i64, i64, vp, i32, vp, vp, C.POINTER(PhotParams), vp, vp, vp, vp, vp, vp],
                           i32),
+    "ipp_deblend_workspace_size": ([i64, i64, i32], sz),
+    "ipp_deblend": ([vp, vp, i64, i64, i64, vp, i32, C.POINTER(SrcStats), C.POINTER(DeblendParams), vp, vp, vp, sz,
+                     vp], i32),
     "ipp_auto_phot": ([vp, vp, i64, i64, i64, vp, i32, C.POINTER(SrcStats), C.POINTER(AutoParams), vp, vp, vp,
                        vp, vp, vp], i32),
     "ipp_stamp_cut": ([vp, i64, i64, i64, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp], i32),

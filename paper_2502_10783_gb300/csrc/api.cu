@@ -247,6 +247,34 @@ extern "C" int ipp_auto_phot(const float* sub, const int32_t* labels, int64_t W,
     return ipp_launch_auto_phot(J, (cudaStream_t)stream);
 }
 
+extern "C" size_t ipp_deblend_workspace_size(int64_t W, int64_t H, int32_t max_src) {
+    if (W <= 0 || H <= 0) return 0;
+    return ipp_deblend_ws_carve(W, H, max_src, nullptr, nullptr);
+}
+
+extern "C" int ipp_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t pitch,
+                           const int32_t* n_src_dev, int32_t max_src, const ipp_src_stats* stats,
+                           const ipp_deblend_params* p, int32_t* out_labels, int32_t* n_out_dev, void* ws,
+                           size_t ws_bytes, void* stream) {
+    if (int e = check_frame(sub, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(p && p->nthresh >= 2 && p->nthresh <= 256 && p->mincont >= 0.f && p->mincont <= 1.f,
+            "bad deblending params");
+    REQUIRE(labels && n_src_dev && stats && out_labels && n_out_dev && ws, "NULL pointer");
+    REQUIRE(stats->xmin && stats->xmax && stats->ymin && stats->ymax && stats->area, "stats arrays NULL");
+    REQUIRE(max_src >= 0, "max_src < 0");
+    REQUIRE(W * H < (int64_t(1) << 31), "deblending needs a frame below 2^31 pixels");
+    REQUIRE(((uintptr_t)ws & 255) == 0, "workspace not 256-byte aligned");
+    REQUIRE(ws_bytes >= ipp_deblend_ws_carve(W, H, max_src, nullptr, nullptr), "workspace too small");
+    DeblendJob J;
+    J.sub = sub; J.pitch = pitch; J.labels = labels; J.W = W; J.H = H;
+    J.n_src_dev = n_src_dev; J.max_src = max_src;
+    J.xmin = stats->xmin; J.xmax = stats->xmax; J.ymin = stats->ymin; J.ymax = stats->ymax; J.area = stats->area;
+    J.nthresh = p->nthresh; J.mincont = (double)p->mincont;
+    J.out = out_labels; J.n_out_dev = n_out_dev;
+    ipp_deblend_ws_carve(W, H, max_src, ws, &J.ws);
+    return ipp_launch_deblend(J, (cudaStream_t)stream);
+}
+
 extern "C" int ipp_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, const int32_t* n_src_dev,
                              int32_t max_src, const float* x, const float* y, int32_t S, float* stamps,
                              float* weights, int32_t* origin, int32_t* flags, void* stream) {

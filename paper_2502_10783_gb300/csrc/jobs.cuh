@@ -82,6 +82,31 @@ struct AutoJob {
     int32_t* flags;
 };
 
+// Deblending workspace: per-candidate arrays of max_src entries and per-slot
+// arrays of W*H entries (a candidate's pixels take slots [base, base + n)).
+struct DeblendWs {
+    int32_t *base, *nobj, *npx, *offs, *counters;
+    int32_t* map;
+    int32_t *pidx, *par, *nidA, *nidB, *core, *asg, *rootA, *rootB, *nobA, *nobB, *nsig, *tot, *sgc, *dec;
+    float* f;
+    double *fluxA, *fluxB, *o2, *o3, *o4, *o5;
+};
+
+struct DeblendJob {
+    const float* sub;
+    int64_t pitch;
+    const int32_t* labels;  // pitch W
+    int64_t W, H;
+    const int32_t* n_src_dev;
+    int32_t max_src;
+    const int32_t *xmin, *xmax, *ymin, *ymax, *area;
+    int32_t nthresh;
+    double mincont;
+    int32_t* out;        // [W*H] pitch W
+    int32_t* n_out_dev;  // [1]
+    DeblendWs ws;
+};
+
 // detection: mode 0 = threshold a given sub frame, 1 = given bit mask,
 // 2 = fused with interpolation + subtraction of the raw frame
 struct DetectArgs {
@@ -139,6 +164,8 @@ int ipp_launch_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, 
                          int32_t* origin, int32_t* flags, cudaStream_t s);
 int ipp_launch_aperture(const ipp::PhotJob& J, cudaStream_t s);
 int ipp_launch_auto_phot(const ipp::AutoJob& J, cudaStream_t s);
+int ipp_launch_deblend(const ipp::DeblendJob& J, cudaStream_t s);
+size_t ipp_deblend_ws_carve(int64_t W, int64_t H, int32_t max_src, void* ws, ipp::DeblendWs* out);
 int ipp_launch_psf_fit(const ipp::FitJob& J, cudaStream_t s);
 int ipp_launch_psf_fwd(const float* params, int64_t N, int S, int model, float beta, float* model_out, cudaStream_t s);
 int ipp_launch_psf_adj(const float* params, int64_t N, int S, int model, float beta, const float* grad_model,
