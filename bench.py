@@ -412,6 +412,11 @@ def main():
     # auto (Kron) photometry of the same catalog: a widening of the path, timed
     # beside it, not part of the step
     stages["auto_phot"] = timeit(lambda k: ipp.auto_phot(subbuf, lab, nsrc, st, max_src=65536))
+    # deblending of the same candidates (also a widening, timed beside the step)
+    dbws = torch.empty(ipp.load().ipp_deblend_workspace_size(W, H, 65536), dtype=torch.uint8, device=dev)
+    stages["deblend"] = timeit(lambda k: ipp.deblend(subbuf, lab, nsrc, st, max_src=65536, ws=dbws))
+    _, n_deb = ipp.deblend(subbuf, lab, nsrc, st, max_src=65536, ws=dbws)
+    deblended_objects = int(n_deb.item())
 
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
@@ -480,7 +485,7 @@ def main():
                                    "mesh 128, 3x3 filter, k=1.5, min_area 5, r=5, annulus 8-12",
                        "parallelism": f"replicas x{ws} (independent frames), {L} streams per GPU",
                        "l2": "inputs larger than L2: 3 rotating 64 MiB frames"},
-            "sources_per_s": src_per_s, "sources_per_frame": K,
+            "sources_per_s": src_per_s, "sources_per_frame": K, "deblended_objects_per_frame": deblended_objects,
             "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": W * H * 4,
                     "pipelining": f"each step H2D + catalog + D2H on one of {L} lane streams",
                     "d2h_bytes_per_step": 4 + 3 * 4 * nmax},
