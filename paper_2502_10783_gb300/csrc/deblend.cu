@@ -37,10 +37,15 @@ namespace ipp {
 constexpr int DB_T = 128;
 constexpr int DB_W = DB_T / 32;
 
+constexpr int DB_MAXLV = 256;  // nthresh limit of the C ABI
+
 struct DbShared {
     double red_d[DB_W];
     int red_i[DB_W];
     int scan_w[DB_W];
+    // level thresholds as floats: for a float v, (double)v > L exactly when
+    // v > L rounded toward -infinity to float (no float lies in between)
+    float lev[DB_MAXLV];
 };
 
 __device__ __forceinline__ double db_warp_sum(double v) {
@@ -195,7 +200,7 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     if (__ldg(J.labels + (int64_t)ni * W + nj) != lab) continue;
                     const int u = J.ws.map[(int64_t)ni * W + nj];
                     if ((unsigned)u >= (unsigned)n || P[u] != ni * W + nj) continue;  // not gathered
-                    if ((double)F[u] > v) top = false;
+                    if (F[u] > F[t]) top = false;
                 }
             nmax += top;
         }
@@ -205,6 +210,8 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
         int no = 1;
         bool whole = !(T > 0.0 && Pk > T) || nmax <= 1 || n < 2;
         if (!whole) {
+            for (int lv = threadIdx.x; lv < J.nthresh; lv += DB_T)
+                S.lev[lv] = lv > 0 ? __double2float_rd(T * pow(Pk / T, (double)lv / (double)J.nthresh)) : -INFINITY;
             for (int t = threadIdx.x; t < n; t += DB_T) core[t] = -1;
             int* nidC = J.ws.nidA + b0;
             int* nidN = J.ws.nidB + b0;
@@ -221,17 +228,18 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
             int mN = 0, prev = -1;
             for (int t = threadIdx.x; t < n; t += DB_T) nidN[t] = -1;
             for (int lv = J.nthresh - 1; lv >= 0; lv--) {
-                const double L = lv > 0 ? T * pow(Pk / T, (double)lv / (double)J.nthresh) : NEG;
+                __syncthreads();  // S.lev written
+                const float L = S.lev[lv];
                 int cnt = 0;
-                for (int t = threadIdx.x; t < n; t += DB_T) cnt += (double)F[t] > L;
+                for (int t = threadIdx.x; t < n; t += DB_T) cnt += F[t] > L;
                 cnt = db_sum_i(cnt, S);
                 if (cnt == prev) continue;  // same pixel set as the level above: same tree
                 prev = cnt;
                 // union-find over the pixels above L (backward neighbours suffice)
-                for (int t = threadIdx.x; t < n; t += DB_T) par[t] = (double)F[t] > L ? t : -1;
+                for (int t = threadIdx.x; t < n; t += DB_T) par[t] = F[t] > L ? t : -1;
                 __syncthreads();
                 for (int t = threadIdx.x; t < n; t += DB_T) {
-                    if (!((double)F[t] > L)) continue;
+                    if (!(F[t] > L)) continue;
                     const int q = P[t], qi = q / W, qj = q - qi * W;
                     const int nbr[4][2] = {{0, -1}, {-1, -1}, {-1, 0}, {-1, 1}};
 #pragma unroll
@@ -241,7 +249,7 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                         if (__ldg(J.labels + (int64_t)ni * W + nj) != lab) continue;
                         const int u = J.ws.map[(int64_t)ni * W + nj];
                         if ((unsigned)u >= (unsigned)n || P[u] != ni * W + nj) continue;  // not gathered
-                        if ((double)F[u] > L) db_union(par, t, u);
+                        if (F[u] > L) db_union(par, t, u);
                     }
                 }
                 __syncthreads();
