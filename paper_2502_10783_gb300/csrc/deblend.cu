@@ -39,7 +39,7 @@ constexpr int DB_W = DB_T / 32;
 
 constexpr int DB_MAXLV = 256;  // nthresh limit of the C ABI
 
-struct DbShared {
+struct DbShared {  // block helpers below work for blocks of 1 .. DB_W warps
     double red_d[DB_W];
     int red_i[DB_W];
     int scan_w[DB_W];
@@ -62,7 +62,7 @@ __device__ __forceinline__ double db_sum(double v, DbShared& S) {
     __syncthreads();
     double t = 0.0;
 #pragma unroll
-    for (int w = 0; w < DB_W; w++) t += S.red_d[w];
+    for (int w = 0; w < DB_W; w++) t += w < (int)(blockDim.x >> 5) ? S.red_d[w] : 0.0;
     return t;
 }
 __device__ __forceinline__ double db_min(double v, DbShared& S) {
@@ -73,7 +73,7 @@ __device__ __forceinline__ double db_min(double v, DbShared& S) {
     __syncthreads();
     double t = S.red_d[0];
 #pragma unroll
-    for (int w = 1; w < DB_W; w++) t = fmin(t, S.red_d[w]);
+    for (int w = 1; w < DB_W; w++) t = w < (int)(blockDim.x >> 5) ? fmin(t, S.red_d[w]) : t;
     return t;
 }
 __device__ __forceinline__ double db_max(double v, DbShared& S) {
@@ -84,7 +84,7 @@ __device__ __forceinline__ double db_max(double v, DbShared& S) {
     __syncthreads();
     double t = S.red_d[0];
 #pragma unroll
-    for (int w = 1; w < DB_W; w++) t = fmax(t, S.red_d[w]);
+    for (int w = 1; w < DB_W; w++) t = w < (int)(blockDim.x >> 5) ? fmax(t, S.red_d[w]) : t;
     return t;
 }
 __device__ __forceinline__ int db_sum_i(int v, DbShared& S) {
@@ -94,7 +94,7 @@ __device__ __forceinline__ int db_sum_i(int v, DbShared& S) {
     __syncthreads();
     int t = 0;
 #pragma unroll
-    for (int w = 0; w < DB_W; w++) t += S.red_i[w];
+    for (int w = 0; w < DB_W; w++) t += w < (int)(blockDim.x >> 5) ? S.red_i[w] : 0;
     return t;
 }
 
@@ -109,8 +109,9 @@ __device__ __forceinline__ int db_scan(bool flag, int& total, DbShared& S) {
     int off = 0, tot = 0;
 #pragma unroll
     for (int k = 0; k < DB_W; k++) {
-        off += k < w ? S.scan_w[k] : 0;
-        tot += S.scan_w[k];
+        const int v = k < (int)(blockDim.x >> 5) ? S.scan_w[k] : 0;
+        off += k < w ? v : 0;
+        tot += v;
     }
     total = tot;
     return off + pre;
@@ -141,19 +142,268 @@ __device__ __forceinline__ void db_union(int* par, int a, int b) {
 
 enum { DB_PASS_ALL = 0, DB_PASS_ONE = 1, DB_OBJECT = 2 };
 
+// ---------------------------------------------------------------------------
+// Candidates of at most 32 pixels (most of a frame's): one warp each, one
+// pixel a lane, no block barrier.  A level's components are closures of the
+// lanes' 8-neighbour bit masks within the ballot of the pixels above the level;
+// a component's root is its lowest slot, as in the union-find of larger ones.
+constexpr int DB_SMALL = 32;
+
+struct DbWarp {
+    int P[32], qi[32], qj[32];
+    float F[32];
+    unsigned adj[32];
+    float lev[DB_MAXLV];
+    int rootN[32], nobN[32], rootC[32], nobC[32], nsig[32], tot[32], sgc[32], dec[32];
+    double fluxN[32], fluxC[32];
+    double o[6][32];
+    int ofirst[32], orank[32];
+};
+
+__device__ __noinline__ void db_small(const DeblendJob& J, int64_t c, DbWarp& Wp) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int W = (int)J.W;
+    const int lab = (int)(c + 1);
+    const int b0 = J.ws.base[c];
+    const int x0 = __ldg(J.xmin + c), y0 = __ldg(J.ymin + c);
+    const int bw = __ldg(J.xmax + c) - x0 + 1, bh = __ldg(J.ymax + c) - y0 + 1;
+    const int64_t nb = (int64_t)bw * bh;
+    const int64_t room = (int64_t)W * J.H - b0;
+    const int cap = b0 < 0 ? 0 : (int)min((int64_t)min(max(__ldg(J.area + c), 0), DB_SMALL), max(room, (int64_t)0));
+    // gather in raster order
+    int n = 0;
+    for (int64_t t0 = 0; t0 < nb && n < cap; t0 += 32) {
+        const int64_t t = t0 + lane;
+        bool in = false;
+        int i = 0, j = 0;
+        if (t < nb) {
+            i = y0 + (int)(t / bw);
+            j = x0 + (int)(t - (t / bw) * bw);
+            in = __ldg(J.labels + (int64_t)i * W + j) == lab;
+        }
+        const unsigned bal = __ballot_sync(FULL, in);
+        const int pos = __popc(bal & ((1u << lane) - 1u));
+        if (in && n + pos < cap) {
+            Wp.P[n + pos] = i * W + j; Wp.qi[n + pos] = i; Wp.qj[n + pos] = j;
+            Wp.F[n + pos] = __ldg(J.sub + (int64_t)i * J.pitch + j);
+        }
+        n += __popc(bal);
+    }
+    n = min(n, cap);
+    __syncwarp();
+    const bool have = lane < n;
+    const int q = have ? Wp.P[lane] : 0, qi = have ? Wp.qi[lane] : 0, qj = have ? Wp.qj[lane] : 0;
+    const float f = have ? Wp.F[lane] : 0.f;
+    unsigned adj = 0u;
+    for (int u = 0; u < n; u++)
+        if (u != lane && abs(Wp.qi[u] - qi) <= 1 && abs(Wp.qj[u] - qj) <= 1) adj |= 1u << u;
+    Wp.adj[lane] = have ? adj : 0u;
+    // lowest / highest pixel, flux, local maxima
+    float lo = have ? f : INFINITY, hi = have ? f : -INFINITY;
+    double fc = have ? (double)f : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(FULL, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(FULL, hi, o));
+        fc += __shfl_xor_sync(FULL, fc, o);
+    }
+    __syncwarp();
+    bool top = have;
+    for (unsigned r = adj; r; r &= r - 1u) top = top && !(Wp.F[__ffs(r) - 1] > f);
+    const int nmax = __popc(__ballot_sync(FULL, top));
+    const double T = (double)lo, Pk = (double)hi, cut = J.mincont * fc;
+    int no = n > 0 ? 1 : 0, asg = 0;
+    if (T > 0.0 && Pk > T && nmax > 1 && n >= 2) {
+        for (int lv = lane; lv < J.nthresh; lv += 32)
+            Wp.lev[lv] = lv > 0 ? __double2float_rd(T * pow(Pk / T, (double)lv / (double)J.nthresh)) : -INFINITY;
+        __syncwarp();
+        int core = -1, nidN = -1, mN = 0;
+        unsigned prevA = 0u;
+        bool firstlv = true;
+        for (int lv = J.nthresh - 1; lv >= 0; lv--) {
+            const bool above = have && f > Wp.lev[lv];
+            const unsigned A = __ballot_sync(FULL, above);
+            if (!firstlv && A == prevA) continue;  // same pixel set as the level above
+            firstlv = false;
+            prevA = A;
+            unsigned m = above ? 1u << lane : 0u;
+            while (m) {  // closure of the lane's component within A
+                unsigned m2 = m;
+                for (unsigned r = m; r; r &= r - 1u) m2 |= Wp.adj[__ffs(r) - 1];
+                m2 &= A;
+                if (m2 == m) break;
+                m = m2;
+            }
+            const int root = above ? __ffs(m) - 1 : -1;
+            const unsigned R = __ballot_sync(FULL, above && root == lane);
+            const int nid = above ? __popc(R & ((1u << root) - 1u)) : -1;
+            const int mC = __popc(R);
+            if (lane < mC) { Wp.fluxC[lane] = 0.0; Wp.nsig[lane] = 0; Wp.tot[lane] = 0; Wp.sgc[lane] = -1; }
+            if (above && root == lane) Wp.rootC[nid] = lane;
+            __syncwarp();
+            if (above) atomicAdd(&Wp.fluxC[nid], (double)f);
+            {
+                const int src = lane < mN ? Wp.rootN[lane] : 0;
+                const int g = __shfl_sync(FULL, nid, src);
+                if (lane < mN && Wp.fluxN[lane] >= cut) {
+                    atomicAdd(&Wp.nsig[g], 1);
+                    atomicAdd(&Wp.tot[g], Wp.nobN[lane]);
+                    Wp.sgc[g] = lane;
+                }
+            }
+            __syncwarp();
+            if (lane < mC) {
+                const int k = Wp.nsig[lane];
+                const int d = k >= 2 ? DB_PASS_ALL : (k == 1 && Wp.nobN[Wp.sgc[lane]] >= 2 ? DB_PASS_ONE : DB_OBJECT);
+                Wp.dec[lane] = d;
+                Wp.nobC[lane] = d == DB_PASS_ALL ? Wp.tot[lane] : (d == DB_PASS_ONE ? Wp.nobN[Wp.sgc[lane]] : 1);
+            }
+            __syncwarp();
+            if (above) {
+                if (Wp.dec[nid] == DB_OBJECT) core = Wp.rootC[nid];
+                else if (nidN >= 0 && !(Wp.fluxN[nidN] >= cut)) core = -1;
+            }
+            __syncwarp();
+            if (lane < mC) { Wp.rootN[lane] = Wp.rootC[lane]; Wp.fluxN[lane] = Wp.fluxC[lane]; Wp.nobN[lane] = Wp.nobC[lane]; }
+            nidN = nid;
+            mN = mC;
+            __syncwarp();
+        }
+        no = Wp.nobN[0];
+        if (no >= 2) {
+            const unsigned CORES = __reduce_or_sync(FULL, core >= 0 ? 1u << core : 0u);
+            no = __popc(CORES);
+            const int ec = core >= 0 ? __popc(CORES & ((1u << core) - 1u)) : -1;
+            if (lane < no) {
+                for (int k = 0; k < 6; k++) Wp.o[k][lane] = 0.0;
+                Wp.ofirst[lane] = INT32_MAX;
+            }
+            __syncwarp();
+            const double x = (double)qj, y = (double)qi;
+            if (ec >= 0) {
+                atomicAdd(&Wp.o[0][ec], (double)f);
+                atomicAdd(&Wp.o[1][ec], (double)f * x);
+                atomicAdd(&Wp.o[2][ec], (double)f * y);
+            }
+            __syncwarp();
+            if (lane < no) { Wp.o[1][lane] /= Wp.o[0][lane]; Wp.o[2][lane] /= Wp.o[0][lane]; }
+            __syncwarp();
+            if (ec >= 0) {
+                const double dx = x - Wp.o[1][ec], dy = y - Wp.o[2][ec];
+                atomicAdd(&Wp.o[3][ec], (double)f * dx * dx);
+                atomicAdd(&Wp.o[4][ec], (double)f * dy * dy);
+                atomicAdd(&Wp.o[5][ec], (double)f * dx * dy);
+            }
+            __syncwarp();
+            if (lane < no) {
+                const double F0 = Wp.o[0][lane];
+                double x2 = Wp.o[3][lane] / F0, y2 = Wp.o[4][lane] / F0, xy = Wp.o[5][lane] / F0;
+                if (x2 * y2 - xy * xy < 1.0 / 144.0) { x2 += 1.0 / 12.0; y2 += 1.0 / 12.0; }
+                const double det = x2 * y2 - xy * xy;
+                Wp.o[3][lane] = y2 / det;
+                Wp.o[4][lane] = x2 / det;
+                Wp.o[5][lane] = -2.0 * xy / det;
+                Wp.o[0][lane] = F0 / sqrt(det);
+            }
+            __syncwarp();
+            int best = ec;
+            if (have && ec < 0) {
+                double bv = -1.0;
+                best = 0;
+                for (int e = 0; e < no; e++) {
+                    const double dx = x - Wp.o[1][e], dy = y - Wp.o[2][e];
+                    const double r2 = Wp.o[3][e] * dx * dx + Wp.o[5][e] * dx * dy + Wp.o[4][e] * dy * dy;
+                    const double v = Wp.o[0][e] * exp(-0.5 * r2);
+                    if (v > bv) { bv = v; best = e; }
+                }
+            }
+            if (have) atomicMin(&Wp.ofirst[best], lane);
+            __syncwarp();
+            if (lane < no) {
+                int r = 0;
+                for (int e2 = 0; e2 < no; e2++) r += Wp.ofirst[e2] < Wp.ofirst[lane];
+                Wp.orank[lane] = r;
+            }
+            __syncwarp();
+            asg = have ? Wp.orank[best] : 0;
+        } else {
+            no = 1;
+        }
+    }
+    if (have) { J.ws.pidx[b0 + lane] = q; J.ws.asg[b0 + lane] = asg; }
+    if (lane == 0) { J.ws.nobj[c] = no; J.ws.npx[c] = n; }
+    __syncwarp();
+}
+
+
+// The block path keeps a candidate of at most DB_SMEM_PX pixels in shared
+// memory (the same buffer the warps used for the small candidates), larger
+// ones in their workspace slots.
+constexpr int DB_SMEM_PX = 512;
+
+struct DbArrays {
+    int* nb4;  // shared-memory path: slots of the 4 backward neighbours (-1: none)
+    int *P, *par, *core, *asg, *nidA, *nidB, *rootA, *rootB, *nobA, *nobB, *nsig, *tot, *sgc, *dec;
+    float* F;
+    double *fluxA, *fluxB, *o2, *o3, *o4, *o5;
+};
+
+__device__ __forceinline__ DbArrays db_arrays(const DeblendJob& J, int b0, bool sm, char* buf) {
+    DbArrays a;
+    if (sm) {
+        double* d = (double*)buf;
+        a.fluxA = d; a.fluxB = d + DB_SMEM_PX; a.o2 = d + 2 * DB_SMEM_PX; a.o3 = d + 3 * DB_SMEM_PX;
+        a.o4 = d + 4 * DB_SMEM_PX; a.o5 = d + 5 * DB_SMEM_PX;
+        int* q = (int*)(d + 6 * DB_SMEM_PX);
+        int** ints[] = {&a.P, &a.par, &a.core, &a.asg, &a.nidA, &a.nidB, &a.rootA, &a.rootB, &a.nobA, &a.nobB,
+                        &a.nsig, &a.tot, &a.sgc, &a.dec};
+        for (int k = 0; k < 14; k++) *ints[k] = q + k * DB_SMEM_PX;
+        a.F = (float*)(q + 14 * DB_SMEM_PX);
+        a.nb4 = q + 15 * DB_SMEM_PX;
+    } else {
+        a.nb4 = nullptr;
+        a.P = J.ws.pidx + b0; a.par = J.ws.par + b0; a.core = J.ws.core + b0; a.asg = J.ws.asg + b0;
+        a.nidA = J.ws.nidA + b0; a.nidB = J.ws.nidB + b0; a.rootA = J.ws.rootA + b0; a.rootB = J.ws.rootB + b0;
+        a.nobA = J.ws.nobA + b0; a.nobB = J.ws.nobB + b0; a.nsig = J.ws.nsig + b0; a.tot = J.ws.tot + b0;
+        a.sgc = J.ws.sgc + b0; a.dec = J.ws.dec + b0; a.F = J.ws.f + b0;
+        a.fluxA = J.ws.fluxA + b0; a.fluxB = J.ws.fluxB + b0; a.o2 = J.ws.o2 + b0; a.o3 = J.ws.o3 + b0;
+        a.o4 = J.ws.o4 + b0; a.o5 = J.ws.o5 + b0;
+    }
+    return a;
+}
+constexpr size_t DB_SMEM_BYTES = (size_t)DB_SMEM_PX * (6 * 8 + 19 * 4);
+constexpr size_t DB_DYN_BYTES = DB_SMEM_BYTES;
+
+// Candidates of at most DB_SMALL pixels: a warp each.
+__global__ void __launch_bounds__(DB_T) k_deblend_small(DeblendJob J) {
+    __shared__ DbWarp WS[DB_W];
+    const int64_t nsrc = min((int64_t)__ldg(J.n_src_dev), (int64_t)J.max_src);
+    const int64_t nw = (int64_t)gridDim.x * DB_W;
+    for (int64_t c = (int64_t)blockIdx.x * DB_W + (threadIdx.x >> 5); c < nsrc; c += nw)
+        if (__ldg(J.area + c) <= DB_SMALL) db_small(J, c, WS[threadIdx.x >> 5]);
+}
+
 __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
+    const int NT = blockDim.x;
     __shared__ DbShared S;
+    extern __shared__ __align__(16) char buf[];  // DB_DYN_BYTES
     const int64_t nsrc = min((int64_t)__ldg(J.n_src_dev), (int64_t)J.max_src);
     const int W = (int)J.W, H = (int)J.H;
     const double NEG = -INFINITY;
+    // candidates above DB_SMALL pixels: a block each
     for (int64_t c = blockIdx.x; c < nsrc; c += gridDim.x) {
+        const int area_c = __ldg(J.area + c);
+        if (area_c <= DB_SMALL) continue;
         const int lab = (int)(c + 1);
         const int b0 = J.ws.base[c];
-        int* P = J.ws.pidx + b0;
-        float* F = J.ws.f + b0;
-        int* par = J.ws.par + b0;
-        int* core = J.ws.core + b0;
-        int* asg = J.ws.asg + b0;
+        const bool sm = area_c <= DB_SMEM_PX;
+        const DbArrays A = db_arrays(J, b0, sm, buf);
+        int* P = A.P;
+        float* F = A.F;
+        int* par = A.par;
+        int* core = A.core;
+        int* asg = A.asg;
         // ---- gather the candidate's pixels in raster order ------------------
         const int x0 = __ldg(J.xmin + c), y0 = __ldg(J.ymin + c);
         const int bw = __ldg(J.xmax + c) - x0 + 1, bh = __ldg(J.ymax + c) - y0 + 1;
@@ -162,7 +412,7 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
         const int64_t room = (int64_t)W * H - b0;
         const int cap = b0 < 0 ? 0 : (int)min((int64_t)max(__ldg(J.area + c), 0), max(room, (int64_t)0));
         int n = 0;
-        for (int64_t t0 = 0; t0 < nb; t0 += DB_T) {
+        for (int64_t t0 = 0; t0 < nb; t0 += NT) {
             const int64_t t = t0 + threadIdx.x;
             bool in = false;
             int i = 0, j = 0;
@@ -186,7 +436,7 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
         // ---- levels, flux, local maxima -------------------------------------
         double lo = INFINITY, hi = NEG, fc = 0.0;
         int nmax = 0;
-        for (int t = threadIdx.x; t < n; t += DB_T) {
+        for (int t = threadIdx.x; t < n; t += NT) {
             const double v = (double)F[t];
             lo = fmin(lo, v);
             hi = fmax(hi, v);
@@ -210,36 +460,61 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
         int no = 1;
         bool whole = !(T > 0.0 && Pk > T) || nmax <= 1 || n < 2;
         if (!whole) {
-            for (int lv = threadIdx.x; lv < J.nthresh; lv += DB_T)
+            if (A.nb4) {  // backward neighbours of each pixel, looked up once
+                for (int t = threadIdx.x; t < n; t += NT) {
+                    const int q = P[t], qi = q / W, qj = q - qi * W;
+                    const int nbr[4][2] = {{0, -1}, {-1, -1}, {-1, 0}, {-1, 1}};
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const int ni = qi + nbr[k][0], nj = qj + nbr[k][1];
+                        int u = -1;
+                        if ((unsigned)ni < (unsigned)H && (unsigned)nj < (unsigned)W &&
+                            __ldg(J.labels + (int64_t)ni * W + nj) == lab) {
+                            u = J.ws.map[(int64_t)ni * W + nj];
+                            if ((unsigned)u >= (unsigned)n || P[u] != ni * W + nj) u = -1;  // not gathered
+                        }
+                        A.nb4[4 * t + k] = u;
+                    }
+                }
+            }
+            for (int lv = threadIdx.x; lv < J.nthresh; lv += NT)
                 S.lev[lv] = lv > 0 ? __double2float_rd(T * pow(Pk / T, (double)lv / (double)J.nthresh)) : -INFINITY;
-            for (int t = threadIdx.x; t < n; t += DB_T) core[t] = -1;
-            int* nidC = J.ws.nidA + b0;
-            int* nidN = J.ws.nidB + b0;
-            int* rootC = J.ws.rootA + b0;
-            int* rootN = J.ws.rootB + b0;
-            int* nobC = J.ws.nobA + b0;
-            int* nobN = J.ws.nobB + b0;
-            double* fluxC = J.ws.fluxA + b0;
-            double* fluxN = J.ws.fluxB + b0;
-            int* nsig = J.ws.nsig + b0;
-            int* tot = J.ws.tot + b0;
-            int* sgc = J.ws.sgc + b0;
-            int* dec = J.ws.dec + b0;
+            for (int t = threadIdx.x; t < n; t += NT) core[t] = -1;
+            int* nidC = A.nidA;
+            int* nidN = A.nidB;
+            int* rootC = A.rootA;
+            int* rootN = A.rootB;
+            int* nobC = A.nobA;
+            int* nobN = A.nobB;
+            double* fluxC = A.fluxA;
+            double* fluxN = A.fluxB;
+            int* nsig = A.nsig;
+            int* tot = A.tot;
+            int* sgc = A.sgc;
+            int* dec = A.dec;
             int mN = 0, prev = -1;
-            for (int t = threadIdx.x; t < n; t += DB_T) nidN[t] = -1;
+            for (int t = threadIdx.x; t < n; t += NT) nidN[t] = -1;
             for (int lv = J.nthresh - 1; lv >= 0; lv--) {
                 __syncthreads();  // S.lev written
                 const float L = S.lev[lv];
                 int cnt = 0;
-                for (int t = threadIdx.x; t < n; t += DB_T) cnt += F[t] > L;
+                for (int t = threadIdx.x; t < n; t += NT) cnt += F[t] > L;
                 cnt = db_sum_i(cnt, S);
                 if (cnt == prev) continue;  // same pixel set as the level above: same tree
                 prev = cnt;
                 // union-find over the pixels above L (backward neighbours suffice)
-                for (int t = threadIdx.x; t < n; t += DB_T) par[t] = F[t] > L ? t : -1;
+                for (int t = threadIdx.x; t < n; t += NT) par[t] = F[t] > L ? t : -1;
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += DB_T) {
+                for (int t = threadIdx.x; t < n; t += NT) {
                     if (!(F[t] > L)) continue;
+                    if (A.nb4) {
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            const int u = A.nb4[4 * t + k];
+                            if (u >= 0 && F[u] > L) db_union(par, t, u);
+                        }
+                        continue;
+                    }
                     const int q = P[t], qi = q / W, qj = q - qi * W;
                     const int nbr[4][2] = {{0, -1}, {-1, -1}, {-1, 0}, {-1, 1}};
 #pragma unroll
@@ -253,12 +528,12 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     }
                 }
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += DB_T)
+                for (int t = threadIdx.x; t < n; t += NT)
                     if (par[t] >= 0) par[t] = db_find(par, t);
                 __syncthreads();
                 // node ids: roots in slot order
                 int m = 0;
-                for (int t0 = 0; t0 < n; t0 += DB_T) {
+                for (int t0 = 0; t0 < n; t0 += NT) {
                     const int t = t0 + threadIdx.x;
                     const bool root = t < n && par[t] == t;
                     int cntr;
@@ -267,17 +542,17 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     m += cntr;
                 }
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += DB_T) {
+                for (int t = threadIdx.x; t < n; t += NT) {
                     const int p = par[t];
                     if (p < 0) nidC[t] = -1;
                     else if (p != t) nidC[t] = nidC[p];
                 }
-                for (int g = threadIdx.x; g < m; g += DB_T) { fluxC[g] = 0.0; nsig[g] = 0; tot[g] = 0; sgc[g] = -1; }
+                for (int g = threadIdx.x; g < m; g += NT) { fluxC[g] = 0.0; nsig[g] = 0; tot[g] = 0; sgc[g] = -1; }
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += DB_T)
+                for (int t = threadIdx.x; t < n; t += NT)
                     if (nidC[t] >= 0) atomicAdd(fluxC + nidC[t], (double)F[t]);
                 // children: the nodes of the level processed before this one
-                for (int h = threadIdx.x; h < mN; h += DB_T) {
+                for (int h = threadIdx.x; h < mN; h += NT) {
                     if (!(fluxN[h] >= cut)) continue;
                     const int g = nidC[rootN[h]];
                     atomicAdd(nsig + g, 1);
@@ -285,14 +560,14 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     sgc[g] = h;
                 }
                 __syncthreads();
-                for (int g = threadIdx.x; g < m; g += DB_T) {
+                for (int g = threadIdx.x; g < m; g += NT) {
                     const int k = nsig[g];
                     const int d = k >= 2 ? DB_PASS_ALL : (k == 1 && nobN[sgc[g]] >= 2 ? DB_PASS_ONE : DB_OBJECT);
                     dec[g] = d;
                     nobC[g] = d == DB_PASS_ALL ? tot[g] : (d == DB_PASS_ONE ? nobN[sgc[g]] : 1);
                 }
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += DB_T) {
+                for (int t = threadIdx.x; t < n; t += NT) {
                     const int g = nidC[t];
                     if (g < 0) continue;
                     if (dec[g] == DB_OBJECT) {
@@ -315,23 +590,23 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
             whole = no <= 1;
             if (!whole) {
                 // objects: distinct core owners, numbered in slot order of their root
-                int* oid = J.ws.nsig + b0;   // per slot: object of the root at this slot
-                int* ofirst = J.ws.tot + b0; // per object: first slot of its pixels
-                int* otmp = J.ws.sgc + b0;   // per slot: provisional object
-                int* orank = J.ws.dec + b0;  // per object: rank by first pixel
-                double* o0 = J.ws.fluxA + b0;
-                double* o1 = J.ws.fluxB + b0;
-                double* o2 = J.ws.o2 + b0;
-                double* o3 = J.ws.o3 + b0;
-                double* o4 = J.ws.o4 + b0;
-                double* o5 = J.ws.o5 + b0;
-                for (int t = threadIdx.x; t < n; t += DB_T) oid[t] = 0;
+                int* oid = A.nsig;    // per slot: object of the root at this slot
+                int* ofirst = A.tot;  // per object: first slot of its pixels
+                int* otmp = A.sgc;    // per slot: provisional object
+                int* orank = A.dec;   // per object: rank by first pixel
+                double* o0 = A.fluxA;
+                double* o1 = A.fluxB;
+                double* o2 = A.o2;
+                double* o3 = A.o3;
+                double* o4 = A.o4;
+                double* o5 = A.o5;
+                for (int t = threadIdx.x; t < n; t += NT) oid[t] = 0;
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += DB_T)
+                for (int t = threadIdx.x; t < n; t += NT)
                     if (core[t] >= 0) oid[core[t]] = 1;
                 __syncthreads();
                 int ne = 0;
-                for (int t0 = 0; t0 < n; t0 += DB_T) {
+                for (int t0 = 0; t0 < n; t0 += NT) {
                     const int t = t0 + threadIdx.x;
                     const bool isr = t < n && oid[t] == 1;
                     int cntr;
@@ -341,13 +616,13 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     ne += cntr;
                 }
                 no = ne;
-                for (int e = threadIdx.x; e < no; e += DB_T) {
+                for (int e = threadIdx.x; e < no; e += NT) {
                     o0[e] = 0.0; o1[e] = 0.0; o2[e] = 0.0; o3[e] = 0.0; o4[e] = 0.0; o5[e] = 0.0;
                     ofirst[e] = INT32_MAX;
                 }
                 __syncthreads();
                 // core flux and barycentre
-                for (int t = threadIdx.x; t < n; t += DB_T) {
+                for (int t = threadIdx.x; t < n; t += NT) {
                     if (core[t] < 0) continue;
                     const int e = oid[core[t]] - 2;
                     const double v = (double)F[t];
@@ -357,9 +632,9 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     atomicAdd(o2 + e, v * (double)(q / W));
                 }
                 __syncthreads();
-                for (int e = threadIdx.x; e < no; e += DB_T) { o1[e] /= o0[e]; o2[e] /= o0[e]; }
+                for (int e = threadIdx.x; e < no; e += NT) { o1[e] /= o0[e]; o2[e] /= o0[e]; }
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += DB_T) {
+                for (int t = threadIdx.x; t < n; t += NT) {
                     if (core[t] < 0) continue;
                     const int e = oid[core[t]] - 2;
                     const double v = (double)F[t];
@@ -372,7 +647,7 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                 __syncthreads();
                 // the elliptical Gaussian of each core: o0 <- F / sqrt(det),
                 // o3, o4, o5 <- r^2 coefficients of dx^2, dy^2, dx dy
-                for (int e = threadIdx.x; e < no; e += DB_T) {
+                for (int e = threadIdx.x; e < no; e += NT) {
                     double x2 = o3[e] / o0[e], y2 = o4[e] / o0[e], xy = o5[e] / o0[e];
                     if (x2 * y2 - xy * xy < 1.0 / 144.0) { x2 += 1.0 / 12.0; y2 += 1.0 / 12.0; }
                     const double det = x2 * y2 - xy * xy;
@@ -382,7 +657,7 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     o0[e] = o0[e] / sqrt(det);
                 }
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += DB_T) {
+                for (int t = threadIdx.x; t < n; t += NT) {
                     int best;
                     if (core[t] >= 0) {
                         best = oid[core[t]] - 2;
@@ -402,18 +677,22 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     atomicMin(ofirst + best, t);
                 }
                 __syncthreads();
-                for (int e = threadIdx.x; e < no; e += DB_T) {
+                for (int e = threadIdx.x; e < no; e += NT) {
                     int r = 0;
                     for (int e2 = 0; e2 < no; e2++) r += ofirst[e2] < ofirst[e];
                     orank[e] = r;
                 }
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += DB_T) asg[t] = orank[otmp[t]];
+                for (int t = threadIdx.x; t < n; t += NT) asg[t] = orank[otmp[t]];
             }
         }
         if (whole) {
             no = n > 0 ? 1 : 0;  // an empty candidate yields no object
-            for (int t = threadIdx.x; t < n; t += DB_T) asg[t] = 0;
+            for (int t = threadIdx.x; t < n; t += NT) asg[t] = 0;
+        }
+        if (sm) {  // the write pass reads pixel indices and objects from the slots
+            __syncthreads();
+            for (int t = threadIdx.x; t < n; t += NT) { J.ws.pidx[b0 + t] = P[t]; J.ws.asg[b0 + t] = asg[t]; }
         }
         if (threadIdx.x == 0) { J.ws.nobj[c] = no; J.ws.npx[c] = n; }
         __syncthreads();
@@ -482,9 +761,15 @@ int ipp_launch_deblend(const DeblendJob& J, cudaStream_t s) {
     }
     k_deblend_scan<<<1, 1024, 0, s>>>(J.n_src_dev, J.max_src, J.area, J.ws.base, J.ws.counters);
     if (int e = ipp_check_launch("k_deblend_scan")) return e;
+    int ps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_deblend_small, DB_T, 0) != cudaSuccess || ps < 1) ps = 1;
+    k_deblend_small<<<db_sms() * ps, DB_T, 0, s>>>(J);
+    if (int e = ipp_check_launch("k_deblend_small")) return e;
+    cudaFuncSetAttribute(k_deblend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DB_DYN_BYTES);
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_deblend, DB_T, 0) != cudaSuccess || per < 1) per = 1;
-    k_deblend<<<db_sms() * per, DB_T, 0, s>>>(J);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_deblend, DB_T, DB_DYN_BYTES) != cudaSuccess || per < 1)
+        per = 1;
+    k_deblend<<<db_sms() * per, DB_T, DB_DYN_BYTES, s>>>(J);
     if (int e = ipp_check_launch("k_deblend")) return e;
     k_deblend_scan<<<1, 1024, 0, s>>>(J.n_src_dev, J.max_src, J.ws.nobj, J.ws.offs, J.n_out_dev);
     if (int e = ipp_check_launch("k_deblend_scan")) return e;
