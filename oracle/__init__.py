@@ -77,6 +77,7 @@ def lib():
             L.orc_interp_map.argtypes = [vp, i64, i64, i32, i32, i64, i64, vp]
             L.orc_bg_subtract.argtypes = [vp, i64, i64, i64, vp, i64, i64, i32, i32, vp, vp]
             L.orc_threshold.argtypes = [vp, i64, i64, vp, i64, i64, i32, i32, d, d, vp]
+            L.orc_threshold_filtered.argtypes = [vp, i64, i64, vp, i64, i64, i32, i32, d, d, vp]
             L.orc_label.argtypes = [vp, vp, i64, i64, i32, vp, i64] + [vp] * 10
             L.orc_label.restype = i64
             L.orc_centroid.argtypes = [vp, i64, i64, i64, vp, vp, d, i32, d, vp, vp, vp, vp]
@@ -176,13 +177,13 @@ def bg_subtract(img, mesh_bkg, mesh_w, mesh_h=None):
     return sub, bmap
 
 
-def threshold(sub, mesh_rms, mesh_w, k=1.5, thresh_abs=0.0, mesh_h=None):
+def threshold(sub, mesh_rms, mesh_w, k=1.5, thresh_abs=0.0, mesh_h=None, filtered=False):
     sub, mesh_rms = _f32(sub), _f32(mesh_rms)
     H, W = sub.shape
     ny, nx = mesh_rms.shape
     m = np.zeros((H, W), np.uint8)
-    rc = lib().orc_threshold(_p(sub), W, H, _p(mesh_rms), nx, ny, mesh_w, mesh_h or mesh_w,
-                             float(k), float(thresh_abs), _p(m))
+    fn = lib().orc_threshold_filtered if filtered else lib().orc_threshold
+    rc = fn(_p(sub), W, H, _p(mesh_rms), nx, ny, mesh_w, mesh_h or mesh_w, float(k), float(thresh_abs), _p(m))
     assert rc == 0
     return m
 

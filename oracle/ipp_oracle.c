@@ -269,6 +269,36 @@ int orc_threshold(const float* sub, int64_t W, int64_t H, const float* mesh_rms,
     return ORC_OK;
 }
 
+/*
+ * Detection on a smoothed frame (the detection filter of SExtractor-style
+ * pipelines; paper-silent, reading): the subtracted frame is convolved with the
+ * 3 x 3 pyramid [1 2 1; 2 4 2; 1 2 1] / 16, the weights renormalised over the
+ * taps inside the frame (a constant frame stays constant at the edges), and the
+ * convolved value is compared with the same threshold k rms(x, y) (floored at
+ * thresh_abs) as unsmoothed detection.  The statistics of the candidates still
+ * come from the unsmoothed frame.
+ */
+int orc_threshold_filtered(const float* sub, int64_t W, int64_t H, const float* mesh_rms,
+                           int64_t nx, int64_t ny, int32_t mesh_w, int32_t mesh_h,
+                           double k, double thresh_abs, uint8_t* mask) {
+    static const double kw[3][3] = {{1, 2, 1}, {2, 4, 2}, {1, 2, 1}};
+    for (int64_t i = 0; i < H; i++)
+        for (int64_t j = 0; j < W; j++) {
+            double num = 0.0, den = 0.0;
+            for (int di = -1; di <= 1; di++)
+                for (int dj = -1; dj <= 1; dj++) {
+                    const int64_t a = i + di, b = j + dj;
+                    if (a < 0 || a >= H || b < 0 || b >= W) continue;
+                    num += kw[di + 1][dj + 1] * (double)sub[a * W + b];
+                    den += kw[di + 1][dj + 1];
+                }
+            double thr = k * interp_at(mesh_rms, nx, ny, mesh_w, mesh_h, i, j);
+            if (thresh_abs > thr) thr = thresh_abs;
+            mask[i * W + j] = num / den > thr;
+        }
+    return ORC_OK;
+}
+
 /* ---------------------------------------------------------- c6 / c7 ---- */
 /*
  * Sec. 2.2.5: detected pixels are connected into candidates (8-connectivity);

@@ -72,6 +72,11 @@ int orc_threshold(const float* sub, int64_t W, int64_t H, const float* mesh_rms,
                   int64_t nx, int64_t ny, int32_t mesh_w, int32_t mesh_h,
                   double k, double thresh_abs, uint8_t* mask);
 
+/* Detection on the frame smoothed by the normalised 3 x 3 pyramid (reading). */
+int orc_threshold_filtered(const float* sub, int64_t W, int64_t H, const float* mesh_rms,
+                           int64_t nx, int64_t ny, int32_t mesh_w, int32_t mesh_h,
+                           double k, double thresh_abs, uint8_t* mask);
+
 int64_t orc_label(const uint8_t* mask, const float* sub, int64_t W, int64_t H,
                   int32_t min_area, int32_t* labels, int64_t max_src,
                   int32_t* area, int64_t* first, int32_t* xmin, int32_t* xmax,
