@@ -98,7 +98,10 @@ typedef struct {
     float k;            /* threshold in units of the interpolated mesh rms [1.5] */
     float thresh_abs;   /* absolute floor of the threshold, ADU [0] */
     int32_t min_area;   /* smallest kept candidate, px [5] */
-    int32_t reserved;   /* must be 0 */
+    int32_t filter;     /* 0: threshold sub itself [0]; 1: threshold sub smoothed by the
+                           3 x 3 pyramid [1 2 1; 2 4 2; 1 2 1] / 16, weights renormalised over
+                           the taps inside the frame (detection filter; statistics still
+                           from the unsmoothed sub) */
 } ipp_det_params;
 
 /* Windowed-centroid parameters (paper-silent reading). */

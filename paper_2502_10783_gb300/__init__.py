@@ -145,11 +145,12 @@ def _stats_c(st):
 
 
 def detect_label(sub, mesh_rms=None, cfg: BgConfig | None = None, k=1.5, thresh_abs=0.0, min_area=5,
-                 mask_in=None, max_src=None, ws=None, **kw):
+                 mask_in=None, max_src=None, ws=None, filter=0, **kw):
     """Labels, device source count and per-source stats (ipp_detect_label).
 
     mask_in: optional packed bit mask (uint32 words, ceil(W/32) per row) that
-    replaces the threshold."""
+    replaces the threshold.  filter=1 thresholds the frame smoothed by the
+    3 x 3 pyramid detection filter."""
     L = load()
     cfg = _bgcfg(cfg, kw)
     _need_cuda(sub, "sub", torch.float32)
@@ -169,7 +170,7 @@ def detect_label(sub, mesh_rms=None, cfg: BgConfig | None = None, k=1.5, thresh_
         mi = mask_in.contiguous()
     rms = None if mesh_rms is None else mesh_rms.contiguous()
     _abi.check("ipp_detect_label", L.ipp_detect_label(
-        _ptr(sub), W, H, sub.stride(0), _ptr(rms), cfg.c(), _abi.DetParams(k, thresh_abs, min_area, 0),
+        _ptr(sub), W, H, sub.stride(0), _ptr(rms), cfg.c(), _abi.DetParams(k, thresh_abs, min_area, filter),
         _ptr(mi), _ptr(labels), _ptr(n_src), max_src, _stats_c(st), _ptr(ws), ws.numel(), _stream()))
     return labels, n_src, st
 
@@ -303,7 +304,7 @@ class Extractor:
 
     def __init__(self, W, H, cfg: BgConfig | None = None, k=1.5, thresh_abs=0.0, min_area=5, fwhm_win=3.0,
                  cen_iter=16, tol2=1e-8, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann=10, max_src=None,
-                 device="cuda"):
+                 device="cuda", filter=0):
         L = load()
         self.L, self.W, self.H = L, W, H
         self.cfg = cfg or BgConfig()
@@ -311,7 +312,7 @@ class Extractor:
         dev = torch.device(device)
         self.out, self.stats, self.c_out = _alloc_catalog(W, H, self.cfg, self.max_src, dev)
         self.bp = self.cfg.c()
-        self.dp = _abi.DetParams(k, thresh_abs, min_area, 0)
+        self.dp = _abi.DetParams(k, thresh_abs, min_area, filter)
         self.cp = _abi.CenParams(fwhm_win, cen_iter, tol2, 0)
         self.pp = _abi.PhotParams(r_ap, r_in, r_out, min_ann)
         need = L.ipp_extract_workspace_size(W, H, self.bp)

@@ -29,7 +29,7 @@ class BgParams(C.Structure):
 
 
 class DetParams(C.Structure):
-    _fields_ = [("k", f32), ("thresh_abs", f32), ("min_area", i32), ("reserved", i32)]
+    _fields_ = [("k", f32), ("thresh_abs", f32), ("min_area", i32), ("filter", i32)]
 
 
 class CenParams(C.Structure):

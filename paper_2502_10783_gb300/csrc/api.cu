@@ -164,6 +164,7 @@ extern "C" int ipp_detect_label(const float* sub, int64_t W, int64_t H, int64_t 
     if (int e = check_frame(sub, IPP_F32, W, H, pitch, nullptr)) return e;
     REQUIRE(dp, "det params NULL");
     REQUIRE(dp->min_area >= 1, "min_area must be >= 1");
+    REQUIRE(dp->filter == 0 || dp->filter == 1, "detection filter must be 0 or 1");
     if (!mask_in) {
         if (int e = check_bg(bp)) return e;
         REQUIRE(mesh_rms, "mesh_rms NULL (needed without mask_in)");
@@ -185,6 +186,7 @@ extern "C" int ipp_detect_label(const float* sub, int64_t W, int64_t H, int64_t 
         A.mesh_w = bp->mesh_w; A.mesh_h = bp->mesh_h;
     }
     A.k = dp->k; A.thresh_abs = dp->thresh_abs; A.min_area = dp->min_area; A.mask_in = mask_in;
+    A.filter = dp->filter;
     A.labels = labels; A.n_src_dev = n_src_dev; A.max_src = max_src; A.stats = *stats; A.ws = ws;
     return ipp_launch_detect(A, (cudaStream_t)stream);
 }
@@ -303,6 +305,7 @@ extern "C" int ipp_extract(const void* img, int dtype, int64_t W, int64_t H, int
     REQUIRE(out->x && out->y && out->cen_flags && out->flux, "NULL per-source output");
     if (int e = check_stats(&out->stats)) return e;
     REQUIRE(dp->min_area >= 1 && dp->k >= 0.f, "bad detection params");
+    REQUIRE(dp->filter == 0 || dp->filter == 1, "detection filter must be 0 or 1");
     REQUIRE(cp->fwhm_win > 0.f && cp->fwhm_win <= 16.f && cp->max_iter >= 1, "bad centroid params");
     REQUIRE(pp->r_ap > 0.f && pp->r_ap <= 16.f && pp->r_out > pp->r_in && pp->r_in >= 0.f, "bad aperture params");
     REQUIRE(pp->r_out <= 16.f, "r_out above 16 px not supported");
@@ -325,6 +328,7 @@ extern "C" int ipp_extract(const void* img, int dtype, int64_t W, int64_t H, int
     grid_of(W, H, bp, &A.nx, &A.ny);
     A.mesh_w = bp->mesh_w; A.mesh_h = bp->mesh_h;
     A.k = dp->k; A.thresh_abs = dp->thresh_abs; A.min_area = dp->min_area; A.mask_in = nullptr;
+    A.filter = dp->filter;
     A.labels = out->labels; A.n_src_dev = out->n_src_dev; A.max_src = max_src; A.stats = out->stats;
     A.ws = w + bgws;
     if (int e = ipp_launch_detect(A, s)) return e;

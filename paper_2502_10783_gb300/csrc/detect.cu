@@ -73,6 +73,7 @@ struct SubThreshJob {
     const float* mesh_rms;
     int nx, ny, mesh_w, mesh_h;
     float k, thresh_abs;
+    bool filter;                      // threshold the 3 x 3 pyramid-smoothed sub (not fused)
     uint32_t* mask;                   // [H][mw] bit rows, bit b of word w = column 32 w + b
     int64_t mw;
 };
@@ -275,6 +276,31 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh(SubThreshJob J) {
 #pragma unroll
                 for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? tile_load_pix(J, y, xc + c) : 0.f;
             }
+        } else if (J.filter) {
+            // detection filter: [1 2 1; 2 4 2; 1 2 1] over the taps inside the frame,
+            // divided by the sum of their weights
+            float row[3][6];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const int64_t yy = y - 1 + a;
+#pragma unroll
+                for (int b = 0; b < 6; b++) {
+                    const int64_t xx = xc - 1 + b;
+                    row[a][b] = (yy >= 0 && yy < J.H && xx >= 0 && xx < J.W) ? __ldg(J.sub + yy * J.sub_pitch + xx) : 0.f;
+                }
+            }
+            const float wy0 = y > 0 ? 1.f : 0.f, wy2 = y + 1 < J.H ? 1.f : 0.f;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const int64_t x = xc + c;
+                const float wx0 = x > 0 ? 1.f : 0.f, wx2 = x + 1 < J.W ? 1.f : 0.f;
+                float num = 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    num += (a == 1 ? 2.f : 1.f) * (row[a][c] + 2.f * row[a][c + 1] + row[a][c + 2]);
+                const float den = (wy0 + 2.f + wy2) * (wx0 + 2.f + wx2);
+                f[q][c] = num / den;
+            }
         } else {
             if (vsub && full4) {
                 const float4 t4 = __ldg(reinterpret_cast<const float4*>(J.sub + y * J.sub_pitch + xc));
@@ -409,6 +435,31 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh_poly(SubThreshJob 
             } else {
 #pragma unroll
                 for (int c = 0; c < 4; c++) f[q][c] = (xc + c < J.W) ? tile_load_pix(J, y, xc + c) : 0.f;
+            }
+        } else if (J.filter) {
+            // detection filter: [1 2 1; 2 4 2; 1 2 1] over the taps inside the frame,
+            // divided by the sum of their weights
+            float row[3][6];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const int64_t yy = y - 1 + a;
+#pragma unroll
+                for (int b = 0; b < 6; b++) {
+                    const int64_t xx = xc - 1 + b;
+                    row[a][b] = (yy >= 0 && yy < J.H && xx >= 0 && xx < J.W) ? __ldg(J.sub + yy * J.sub_pitch + xx) : 0.f;
+                }
+            }
+            const float wy0 = y > 0 ? 1.f : 0.f, wy2 = y + 1 < J.H ? 1.f : 0.f;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const int64_t x = xc + c;
+                const float wx0 = x > 0 ? 1.f : 0.f, wx2 = x + 1 < J.W ? 1.f : 0.f;
+                float num = 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    num += (a == 1 ? 2.f : 1.f) * (row[a][c] + 2.f * row[a][c + 1] + row[a][c + 2]);
+                const float den = (wy0 + 2.f + wy2) * (wx0 + 2.f + wx2);
+                f[q][c] = num / den;
             }
         } else {
             if (vsub && full4) {
@@ -1006,13 +1057,20 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
         T.bias_map = A.bias_map; T.bias = A.bias; T.inv_flat = A.inv_flat;
         T.mesh_bkg = A.mesh_bkg; T.sub = A.sub; T.sub_pitch = A.sub_pitch;
         T.mesh_rms = A.mesh_rms; T.nx = A.nx; T.ny = A.ny; T.mesh_w = A.mesh_w; T.mesh_h = A.mesh_h;
-        T.k = A.k; T.thresh_abs = A.thresh_abs;
+        T.k = A.k; T.thresh_abs = A.thresh_abs; T.filter = false;
         T.mask = (uint32_t*)((unsigned char*)A.ws + L.off[24]);
         T.mw = J.mw;
         dim3 sg((unsigned)cdiv(A.W, ST_TW), (unsigned)cdiv(A.H, ST_TH));
         if (A.mesh_w >= 16) k_sub_thresh_poly<<<sg, ST_THREADS, 0, s>>>(T);
         else k_sub_thresh<<<sg, ST_THREADS, 0, s>>>(T);
         if (int e = ipp_check_launch("k_sub_thresh")) return e;
+        if (A.filter) {  // detection filter: threshold again, on the smoothed sub just written
+            SubThreshJob Tf = T;
+            Tf.fused = false;
+            Tf.filter = true;
+            k_sub_thresh<<<sg, ST_THREADS, 0, s>>>(Tf);
+            if (int e = ipp_check_launch("k_sub_thresh (filtered)")) return e;
+        }
         J.mask = T.mask;
     }
     cudaFuncSetAttribute(k_tile_label, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileFast));

@@ -125,6 +125,7 @@ struct DetectArgs {
     int nx, ny, mesh_w, mesh_h;
     float k, thresh_abs;
     int min_area;
+    int filter;  // 1: threshold the 3 x 3 pyramid-smoothed sub
     const uint32_t* mask_in;
     int32_t* labels;
     int32_t* n_src_dev;
