@@ -405,6 +405,9 @@ def main():
     stages["bg_subtract"] = timeit(lambda k: ipp.bg_subtract(frames[k % 3], mb, cfg=cfg, out=subbuf))
     dws = torch.empty(ipp.load().ipp_detect_label_workspace_size(W, H), dtype=torch.uint8, device=dev)
     stages["detect_label"] = timeit(lambda k: ipp.detect_label(subbuf, mr, cfg=cfg, max_src=65536, ws=dws))
+    # detection on the pyramid-smoothed frame (the detection filter; a widening)
+    stages["detect_label_filtered"] = timeit(
+        lambda k: ipp.detect_label(subbuf, mr, cfg=cfg, max_src=65536, ws=dws, filter=1))
     lab, nsrc, st = ipp.detect_label(subbuf, mr, cfg=cfg, max_src=65536, ws=dws)
     stages["centroid"] = timeit(lambda k: ipp.centroid(subbuf, st["xbar"], st["ybar"], n_src=nsrc, max_src=65536))
     cx, cy, _, _ = ipp.centroid(subbuf, st["xbar"], st["ybar"], n_src=nsrc, max_src=65536)
