@@ -54,6 +54,31 @@ __device__ __forceinline__ double db_warp_sum(double v) {
     return v;
 }
 
+// Keyed sums of a warp: every lane with key >= 0 adds v into slot `key`; the
+// lanes sharing a key are summed with shuffles first, so each distinct key of
+// the warp costs one update (an atomic when several warps share the slots,
+// a plain store of the complete sum when `alone`).  All 32 lanes must call.
+template <int NV>
+__device__ __forceinline__ void db_keyed_add(double* const (&acc)[NV], int key, const double (&v)[NV], bool alone) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    unsigned pending = __ballot_sync(FULL, key >= 0);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int k = __shfl_sync(FULL, key, leader);
+        const bool mine = key == k;
+#pragma unroll
+        for (int a = 0; a < NV; a++) {
+            const double sv = db_warp_sum(mine ? v[a] : 0.0);
+            if (lane == leader) {
+                if (alone) acc[a][k] = sv;
+                else atomicAdd(acc[a] + k, sv);
+            }
+        }
+        pending &= ~__ballot_sync(FULL, mine);
+    }
+}
+
 // Block reductions (every thread gets the result).
 __device__ __forceinline__ double db_sum(double v, DbShared& S) {
     v = db_warp_sum(v);
@@ -239,10 +264,14 @@ __device__ __noinline__ void db_small(const DeblendJob& J, int64_t c, DbWarp& Wp
             const unsigned R = __ballot_sync(FULL, above && root == lane);
             const int nid = above ? __popc(R & ((1u << root) - 1u)) : -1;
             const int mC = __popc(R);
-            if (lane < mC) { Wp.fluxC[lane] = 0.0; Wp.nsig[lane] = 0; Wp.tot[lane] = 0; Wp.sgc[lane] = -1; }
+            if (lane < mC) { Wp.nsig[lane] = 0; Wp.tot[lane] = 0; Wp.sgc[lane] = -1; }
             if (above && root == lane) Wp.rootC[nid] = lane;
             __syncwarp();
-            if (above) atomicAdd(&Wp.fluxC[nid], (double)f);
+            {
+                double* const acc[1] = {Wp.fluxC};
+                const double v[1] = {(double)f};
+                db_keyed_add<1>(acc, above ? nid : -1, v, true);
+            }
             {
                 const int src = lane < mN ? Wp.rootN[lane] : 0;
                 const int g = __shfl_sync(FULL, nid, src);
@@ -275,25 +304,22 @@ __device__ __noinline__ void db_small(const DeblendJob& J, int64_t c, DbWarp& Wp
             const unsigned CORES = __reduce_or_sync(FULL, core >= 0 ? 1u << core : 0u);
             no = __popc(CORES);
             const int ec = core >= 0 ? __popc(CORES & ((1u << core) - 1u)) : -1;
-            if (lane < no) {
-                for (int k = 0; k < 6; k++) Wp.o[k][lane] = 0.0;
-                Wp.ofirst[lane] = INT32_MAX;
-            }
+            if (lane < no) Wp.ofirst[lane] = INT32_MAX;
             __syncwarp();
             const double x = (double)qj, y = (double)qi;
-            if (ec >= 0) {
-                atomicAdd(&Wp.o[0][ec], (double)f);
-                atomicAdd(&Wp.o[1][ec], (double)f * x);
-                atomicAdd(&Wp.o[2][ec], (double)f * y);
+            {
+                double* const acc[3] = {Wp.o[0], Wp.o[1], Wp.o[2]};
+                const double v[3] = {(double)f, (double)f * x, (double)f * y};
+                db_keyed_add<3>(acc, ec, v, true);
             }
             __syncwarp();
             if (lane < no) { Wp.o[1][lane] /= Wp.o[0][lane]; Wp.o[2][lane] /= Wp.o[0][lane]; }
             __syncwarp();
-            if (ec >= 0) {
-                const double dx = x - Wp.o[1][ec], dy = y - Wp.o[2][ec];
-                atomicAdd(&Wp.o[3][ec], (double)f * dx * dx);
-                atomicAdd(&Wp.o[4][ec], (double)f * dy * dy);
-                atomicAdd(&Wp.o[5][ec], (double)f * dx * dy);
+            {
+                const double dx = ec >= 0 ? x - Wp.o[1][ec] : 0.0, dy = ec >= 0 ? y - Wp.o[2][ec] : 0.0;
+                double* const acc[3] = {Wp.o[3], Wp.o[4], Wp.o[5]};
+                const double v[3] = {(double)f * dx * dx, (double)f * dy * dy, (double)f * dx * dy};
+                db_keyed_add<3>(acc, ec, v, true);
             }
             __syncwarp();
             if (lane < no) {
@@ -549,8 +575,12 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                 }
                 for (int g = threadIdx.x; g < m; g += NT) { fluxC[g] = 0.0; nsig[g] = 0; tot[g] = 0; sgc[g] = -1; }
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += NT)
-                    if (nidC[t] >= 0) atomicAdd(fluxC + nidC[t], (double)F[t]);
+                for (int t0 = 0; t0 < n; t0 += NT) {  // whole warps: keyed sums
+                    const int t = t0 + threadIdx.x;
+                    double* const acc[1] = {fluxC};
+                    const double v[1] = {t < n ? (double)F[t] : 0.0};
+                    db_keyed_add<1>(acc, t < n ? nidC[t] : -1, v, false);
+                }
                 // children: the nodes of the level processed before this one
                 for (int h = threadIdx.x; h < mN; h += NT) {
                     if (!(fluxN[h] >= cut)) continue;
@@ -622,27 +652,27 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                 }
                 __syncthreads();
                 // core flux and barycentre
-                for (int t = threadIdx.x; t < n; t += NT) {
-                    if (core[t] < 0) continue;
-                    const int e = oid[core[t]] - 2;
-                    const double v = (double)F[t];
-                    const int q = P[t];
-                    atomicAdd(o0 + e, v);
-                    atomicAdd(o1 + e, v * (double)(q % W));
-                    atomicAdd(o2 + e, v * (double)(q / W));
+                for (int t0 = 0; t0 < n; t0 += NT) {
+                    const int t = t0 + threadIdx.x;
+                    const int e = t < n && core[t] >= 0 ? oid[core[t]] - 2 : -1;
+                    const double v = e >= 0 ? (double)F[t] : 0.0;
+                    const int q = e >= 0 ? P[t] : 0;
+                    double* const acc[3] = {o0, o1, o2};
+                    const double vv[3] = {v, v * (double)(q % W), v * (double)(q / W)};
+                    db_keyed_add<3>(acc, e, vv, false);
                 }
                 __syncthreads();
                 for (int e = threadIdx.x; e < no; e += NT) { o1[e] /= o0[e]; o2[e] /= o0[e]; }
                 __syncthreads();
-                for (int t = threadIdx.x; t < n; t += NT) {
-                    if (core[t] < 0) continue;
-                    const int e = oid[core[t]] - 2;
-                    const double v = (double)F[t];
-                    const int q = P[t];
-                    const double dx = (double)(q % W) - o1[e], dy = (double)(q / W) - o2[e];
-                    atomicAdd(o3 + e, v * dx * dx);
-                    atomicAdd(o4 + e, v * dy * dy);
-                    atomicAdd(o5 + e, v * dx * dy);
+                for (int t0 = 0; t0 < n; t0 += NT) {
+                    const int t = t0 + threadIdx.x;
+                    const int e = t < n && core[t] >= 0 ? oid[core[t]] - 2 : -1;
+                    const double v = e >= 0 ? (double)F[t] : 0.0;
+                    const int q = e >= 0 ? P[t] : 0;
+                    const double dx = e >= 0 ? (double)(q % W) - o1[e] : 0.0, dy = e >= 0 ? (double)(q / W) - o2[e] : 0.0;
+                    double* const acc[3] = {o3, o4, o5};
+                    const double vv[3] = {v * dx * dx, v * dy * dy, v * dx * dy};
+                    db_keyed_add<3>(acc, e, vv, false);
                 }
                 __syncthreads();
                 // the elliptical Gaussian of each core: o0 <- F / sqrt(det),
