@@ -366,7 +366,7 @@ __device__ __noinline__ void db_small(const DeblendJob& J, int64_t c, DbWarp& Wp
 // The block path keeps a candidate of at most DB_SMEM_PX pixels in shared
 // memory (the same buffer the warps used for the small candidates), larger
 // ones in their workspace slots.
-constexpr int DB_SMEM_PX = 512;
+constexpr int DB_SMEM_PX = 384;  // even: the double views of int pairs stay 8-byte aligned
 
 struct DbArrays {
     int* nb4;  // shared-memory path: slots of the 4 backward neighbours (-1: none)
@@ -379,14 +379,19 @@ __device__ __forceinline__ DbArrays db_arrays(const DeblendJob& J, int b0, bool 
     DbArrays a;
     if (sm) {
         double* d = (double*)buf;
-        a.fluxA = d; a.fluxB = d + DB_SMEM_PX; a.o2 = d + 2 * DB_SMEM_PX; a.o3 = d + 3 * DB_SMEM_PX;
-        a.o4 = d + 4 * DB_SMEM_PX; a.o5 = d + 5 * DB_SMEM_PX;
-        int* q = (int*)(d + 6 * DB_SMEM_PX);
+        a.fluxA = d; a.fluxB = d + DB_SMEM_PX;
+        int* q = (int*)(d + 2 * DB_SMEM_PX);
         int** ints[] = {&a.P, &a.par, &a.core, &a.asg, &a.nidA, &a.nidB, &a.rootA, &a.rootB, &a.nobA, &a.nobB,
                         &a.nsig, &a.tot, &a.sgc, &a.dec};
         for (int k = 0; k < 14; k++) *ints[k] = q + k * DB_SMEM_PX;
         a.F = (float*)(q + 14 * DB_SMEM_PX);
         a.nb4 = q + 15 * DB_SMEM_PX;
+        // object moments reuse arrays the tree no longer needs once it is built:
+        // the neighbour slots and the node ids / roots of the two levels
+        a.o2 = (double*)(q + 15 * DB_SMEM_PX);
+        a.o3 = (double*)(q + 17 * DB_SMEM_PX);
+        a.o4 = (double*)(q + 4 * DB_SMEM_PX);
+        a.o5 = (double*)(q + 6 * DB_SMEM_PX);
     } else {
         a.nb4 = nullptr;
         a.P = J.ws.pidx + b0; a.par = J.ws.par + b0; a.core = J.ws.core + b0; a.asg = J.ws.asg + b0;
@@ -398,7 +403,7 @@ __device__ __forceinline__ DbArrays db_arrays(const DeblendJob& J, int b0, bool 
     }
     return a;
 }
-constexpr size_t DB_SMEM_BYTES = (size_t)DB_SMEM_PX * (6 * 8 + 19 * 4);
+constexpr size_t DB_SMEM_BYTES = (size_t)DB_SMEM_PX * (2 * 8 + 19 * 4);
 constexpr size_t DB_DYN_BYTES = DB_SMEM_BYTES;
 
 // Candidates of at most DB_SMALL pixels: a warp each.
