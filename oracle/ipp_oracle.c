@@ -535,7 +535,8 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
  * each level, traversed bottom-up and pruned on intensity).  Reading:
  *  levels -- per candidate C (pixels labelled c): T = min sub over C,
  *    P = max sub over C, L_i = T (P/T)^(i/N) for i = 1 .. N-1 (N = nthresh),
- *    in FP64.  A candidate with T <= 0 or P <= T stays whole.
+ *    in FP64 (by square roots and products when N is a power of two, see
+ *    level_of).  A candidate with T <= 0 or P <= T stays whole.
  *  tree -- the nodes of level i are the 8-connected components of
  *    {p in C : sub(p) > L_i}; level 0 is C itself.  The parent of a level-i
  *    node is the level-(i-1) node holding its pixels (level sets are nested).
@@ -560,6 +561,21 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
 static int cmp_i64(const void* a, const void* b) {
     int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
     return (x > y) - (x < y);
+}
+
+/* Level lv of N between T and P: T (P/T)^(lv/N).  For N a power of two the
+ * N-th root of P/T is taken by log2(N) square roots and the level is T r^lv
+ * formed by lv successive products (basic IEEE operations only, so any
+ * implementation following the same steps gets the same double); else pow. */
+static double level_of(double T, double P, int lv, int N) {
+    if ((N & (N - 1)) == 0) {
+        double r = P / T;
+        for (int m = N; m > 1; m >>= 1) r = sqrt(r);
+        double L = T;
+        for (int k = 0; k < lv; k++) L = L * r;
+        return L;
+    }
+    return T * pow(P / T, (double)lv / (double)N);
 }
 
 int64_t orc_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t K,
@@ -617,7 +633,7 @@ int64_t orc_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t 
             int64_t* nd = node + (int64_t)lv * n;
             for (int64_t t = 0; t < n; t++) nd[t] = -1;
             if (!split_ok) continue;
-            const double L = T * pow(Pk / T, (double)lv / (double)N);
+            const double L = level_of(T, Pk, lv, N);
             int64_t m = 0;
             for (int64_t s0 = 0; s0 < n; s0++) {
                 if (nd[s0] >= 0 || !((double)sub[P[s0]] > L)) continue;
