@@ -3,7 +3,9 @@
 // sub-components found at each level, traversed bottom-up and pruned on
 // intensity).  Reading of the steps:
 //   levels  L_i = T (P/T)^(i/N), i = 1..N-1, T / P = lowest / highest pixel of
-//           the candidate, in FP64; T <= 0 or P <= T keeps the candidate whole;
+//           the candidate, in FP64 (for N a power of two by square roots and
+//           products, bit-identical to the oracle); T <= 0 or P <= T keeps the
+//           candidate whole;
 //   tree    the nodes of level i are the 8-connected components of the
 //           candidate's pixels above L_i; level 0 is the whole candidate;
 //   objects from the top level down, a node with two or more children holding
@@ -167,6 +169,29 @@ __device__ __forceinline__ void db_union(int* par, int a, int b) {
 
 enum { DB_PASS_ALL = 0, DB_PASS_ONE = 1, DB_OBJECT = 2 };
 
+// Level lv of N between T and P, rounded toward -infinity to float (for a float
+// v, (double)v > L exactly when v > that float).  For N a power of two the
+// ratio's N-th root is taken by log2(N) correctly rounded square roots and
+// L_lv = L_{lv-1} r from L_0 = T, in that order -- IEEE basic operations only,
+// so the oracle's identical sequence gives bit-identical levels; other N use pow.
+__device__ __forceinline__ void db_levels(double T, double Pk, int N, float* lev, int rank, int nt) {
+    if ((N & (N - 1)) == 0) {
+        if (rank == 0) {
+            double r = Pk / T;
+            for (int m = N; m > 1; m >>= 1) r = sqrt(r);
+            double L = T;
+            lev[0] = -INFINITY;
+            for (int lv = 1; lv < N; lv++) {
+                L = L * r;
+                lev[lv] = __double2float_rd(L);
+            }
+        }
+    } else {
+        for (int lv = rank; lv < N; lv += nt)
+            lev[lv] = lv > 0 ? __double2float_rd(T * pow(Pk / T, (double)lv / (double)N)) : -INFINITY;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Candidates of at most 32 pixels (most of a frame's): one warp each, one
 // pixel a lane, no block barrier.  A level's components are closures of the
@@ -240,8 +265,7 @@ __device__ __noinline__ void db_small(const DeblendJob& J, int64_t c, DbWarp& Wp
     const double T = (double)lo, Pk = (double)hi, cut = J.mincont * fc;
     int no = n > 0 ? 1 : 0, asg = 0;
     if (T > 0.0 && Pk > T && nmax > 1 && n >= 2) {
-        for (int lv = lane; lv < J.nthresh; lv += 32)
-            Wp.lev[lv] = lv > 0 ? __double2float_rd(T * pow(Pk / T, (double)lv / (double)J.nthresh)) : -INFINITY;
+        db_levels(T, Pk, J.nthresh, Wp.lev, lane, 32);
         __syncwarp();
         int core = -1, nidN = -1, mN = 0;
         unsigned prevA = 0u;
@@ -404,16 +428,8 @@ __device__ __forceinline__ DbArrays db_arrays(const DeblendJob& J, int b0, bool 
     return a;
 }
 constexpr size_t DB_SMEM_BYTES = (size_t)DB_SMEM_PX * (2 * 8 + 19 * 4);
-constexpr size_t DB_DYN_BYTES = DB_SMEM_BYTES;
+constexpr size_t DB_DYN_BYTES = DB_SMEM_BYTES > sizeof(DbWarp) * DB_W ? DB_SMEM_BYTES : sizeof(DbWarp) * DB_W;
 
-// Candidates of at most DB_SMALL pixels: a warp each.
-__global__ void __launch_bounds__(DB_T) k_deblend_small(DeblendJob J) {
-    __shared__ DbWarp WS[DB_W];
-    const int64_t nsrc = min((int64_t)__ldg(J.n_src_dev), (int64_t)J.max_src);
-    const int64_t nw = (int64_t)gridDim.x * DB_W;
-    for (int64_t c = (int64_t)blockIdx.x * DB_W + (threadIdx.x >> 5); c < nsrc; c += nw)
-        if (__ldg(J.area + c) <= DB_SMALL) db_small(J, c, WS[threadIdx.x >> 5]);
-}
 
 __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
     const int NT = blockDim.x;
@@ -508,8 +524,7 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     }
                 }
             }
-            for (int lv = threadIdx.x; lv < J.nthresh; lv += NT)
-                S.lev[lv] = lv > 0 ? __double2float_rd(T * pow(Pk / T, (double)lv / (double)J.nthresh)) : -INFINITY;
+            db_levels(T, Pk, J.nthresh, S.lev, threadIdx.x, NT);
             for (int t = threadIdx.x; t < n; t += NT) core[t] = -1;
             int* nidC = A.nidA;
             int* nidN = A.nidB;
@@ -732,6 +747,12 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
         if (threadIdx.x == 0) { J.ws.nobj[c] = no; J.ws.npx[c] = n; }
         __syncthreads();
     }
+    // then the candidates of at most DB_SMALL pixels, a warp each (blocks that
+    // met no large candidate start on them at once)
+    DbWarp* WS = reinterpret_cast<DbWarp*>(buf);
+    const int64_t nw = (int64_t)gridDim.x * (NT >> 5);
+    for (int64_t c = (int64_t)blockIdx.x * (NT >> 5) + (threadIdx.x >> 5); c < nsrc; c += nw)
+        if (__ldg(J.area + c) <= DB_SMALL) db_small(J, c, WS[threadIdx.x >> 5]);
 }
 
 // Exclusive scan of per-candidate counts in one block; total to *total.
@@ -796,10 +817,6 @@ int ipp_launch_deblend(const DeblendJob& J, cudaStream_t s) {
     }
     k_deblend_scan<<<1, 1024, 0, s>>>(J.n_src_dev, J.max_src, J.area, J.ws.base, J.ws.counters);
     if (int e = ipp_check_launch("k_deblend_scan")) return e;
-    int ps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_deblend_small, DB_T, 0) != cudaSuccess || ps < 1) ps = 1;
-    k_deblend_small<<<db_sms() * ps, DB_T, 0, s>>>(J);
-    if (int e = ipp_check_launch("k_deblend_small")) return e;
     cudaFuncSetAttribute(k_deblend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DB_DYN_BYTES);
     int per = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_deblend, DB_T, DB_DYN_BYTES) != cudaSuccess || per < 1)
