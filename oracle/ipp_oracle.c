@@ -551,7 +551,9 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
  *    of C goes to the object whose elliptical Gaussian is largest there:
  *    F exp(-r^2/2) / sqrt(x2 y2 - xy^2), with F, barycentre and second moments
  *    (x2, y2, xy) of the core (weights sub; 1/12 added to x2 and y2 when
- *    x2 y2 - xy^2 < 1/144) and r the Mahalanobis distance; ties go to the
+ *    x2 y2 - xy^2 < 1/144) and r the Mahalanobis distance, compared as
+ *    log F - log(x2 y2 - xy^2)/2 - r^2/2 (far from every core the Gaussians
+ *    themselves underflow to 0 and could not be told apart); ties go to the
  *    object whose core starts first in raster order.
  *  numbering -- the objects of candidate 1 first, then those of candidate 2,
  *    and so on; within a candidate, raster order of each object's first pixel.
@@ -754,17 +756,17 @@ int64_t orc_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t 
                 if (x2 * y2 - xy * xy < 1.0 / 144.0) { x2 += 1.0 / 12.0; y2 += 1.0 / 12.0; }
                 const double det = x2 * y2 - xy * xy;
                 ca[e] = y2 / det; cb[e] = -2.0 * xy / det; cc[e] = x2 / det;
-                nrm[e] = F[e] / sqrt(det);
+                nrm[e] = log(F[e]) - 0.5 * log(det);  /* log of F / sqrt(det) */
             }
             for (int64_t t = 0; t < n; t++) {
                 if (assign[t] >= 0) continue;
                 const double x = (double)(P[t] % W), y = (double)(P[t] / W);
                 int64_t best = 0;
-                double bv = -1.0;
-                for (int64_t e = 0; e < no; e++) {
+                double bv = -INFINITY;
+                for (int64_t e = 0; e < no; e++) {  /* largest log-likelihood */
                     const double dx = x - mx[e], dy = y - my[e];
                     const double r2 = ca[e] * dx * dx + cb[e] * dx * dy + cc[e] * dy * dy;
-                    const double v = nrm[e] * exp(-0.5 * r2);
+                    const double v = nrm[e] - 0.5 * r2;
                     if (v > bv) { bv = v; best = e; }
                 }
                 assign[t] = best;
