@@ -14,7 +14,8 @@
 //           or more, and any other node is one object (its pixels its core);
 //   pixels  a pixel outside every core goes to the object whose elliptical
 //           Gaussian (core flux, barycentre and second moments) is largest
-//           there, ties to the object whose core starts first;
+//           there, compared as log-likelihoods, ties to the object whose core
+//           starts first;
 //   numbers candidate by candidate, within one by the raster order of each
 //           object's first pixel.
 //
@@ -77,6 +78,34 @@ __device__ __forceinline__ void db_keyed_add(double* const (&acc)[NV], int key, 
                 else atomicAdd(acc[a] + k, sv);
             }
         }
+        pending &= ~__ballot_sync(FULL, mine);
+    }
+}
+
+// Keyed sums of one warp in double-float (an unevaluated pair of floats, sums
+// by Knuth's TwoSum): the node fluxes of a small candidate on the FP32 pipe.
+// Every lane with key >= 0 adds v into slot `key`; the leader of each distinct
+// key stores hi + lo as a double.  All 32 lanes must call.
+__device__ __forceinline__ void db_keyed_store_df(double* acc, int key, float v) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    unsigned pending = __ballot_sync(FULL, key >= 0);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int k = __shfl_sync(FULL, key, leader);
+        const bool mine = key == k;
+        float hi = mine ? v : 0.f, lo = 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(FULL, hi, o), l2 = __shfl_xor_sync(FULL, lo, o);
+            const float sum = __fadd_rn(hi, h2);
+            const float bb = __fsub_rn(sum, hi);
+            const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(h2, bb));
+            const float low = __fadd_rn(__fadd_rn(lo, l2), err);
+            hi = __fadd_rn(sum, low);
+            lo = __fsub_rn(low, __fsub_rn(hi, sum));
+        }
+        if (lane == leader) acc[k] = (double)hi + (double)lo;
         pending &= ~__ballot_sync(FULL, mine);
     }
 }
@@ -291,11 +320,7 @@ __device__ __noinline__ void db_small(const DeblendJob& J, int64_t c, DbWarp& Wp
             if (lane < mC) { Wp.nsig[lane] = 0; Wp.tot[lane] = 0; Wp.sgc[lane] = -1; }
             if (above && root == lane) Wp.rootC[nid] = lane;
             __syncwarp();
-            {
-                double* const acc[1] = {Wp.fluxC};
-                const double v[1] = {(double)f};
-                db_keyed_add<1>(acc, above ? nid : -1, v, true);
-            }
+            db_keyed_store_df(Wp.fluxC, above ? nid : -1, f);
             {
                 const int src = lane < mN ? Wp.rootN[lane] : 0;
                 const int g = __shfl_sync(FULL, nid, src);
@@ -354,17 +379,17 @@ __device__ __noinline__ void db_small(const DeblendJob& J, int64_t c, DbWarp& Wp
                 Wp.o[3][lane] = y2 / det;
                 Wp.o[4][lane] = x2 / det;
                 Wp.o[5][lane] = -2.0 * xy / det;
-                Wp.o[0][lane] = F0 / sqrt(det);
+                Wp.o[0][lane] = log(F0) - 0.5 * log(det);  // log of F / sqrt(det)
             }
             __syncwarp();
             int best = ec;
             if (have && ec < 0) {
-                double bv = -1.0;
+                double bv = -INFINITY;
                 best = 0;
-                for (int e = 0; e < no; e++) {
+                for (int e = 0; e < no; e++) {  // largest log-likelihood
                     const double dx = x - Wp.o[1][e], dy = y - Wp.o[2][e];
                     const double r2 = Wp.o[3][e] * dx * dx + Wp.o[5][e] * dx * dy + Wp.o[4][e] * dy * dy;
-                    const double v = Wp.o[0][e] * exp(-0.5 * r2);
+                    const double v = Wp.o[0][e] - 0.5 * r2;
                     if (v > bv) { bv = v; best = e; }
                 }
             }
@@ -704,7 +729,7 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     o3[e] = y2 / det;
                     o4[e] = x2 / det;
                     o5[e] = -2.0 * xy / det;
-                    o0[e] = o0[e] / sqrt(det);
+                    o0[e] = log(o0[e]) - 0.5 * log(det);  // log of F / sqrt(det)
                 }
                 __syncthreads();
                 for (int t = threadIdx.x; t < n; t += NT) {
@@ -714,12 +739,12 @@ __global__ void __launch_bounds__(DB_T) k_deblend(DeblendJob J) {
                     } else {
                         const int q = P[t];
                         const double x = (double)(q % W), y = (double)(q / W);
-                        double bv = -1.0;
+                        double bv = -INFINITY;
                         best = 0;
-                        for (int e = 0; e < no; e++) {
+                        for (int e = 0; e < no; e++) {  // largest log-likelihood
                             const double dx = x - o1[e], dy = y - o2[e];
                             const double r2 = o3[e] * dx * dx + o5[e] * dx * dy + o4[e] * dy * dy;
-                            const double v = o0[e] * exp(-0.5 * r2);
+                            const double v = o0[e] - 0.5 * r2;
                             if (v > bv) { bv = v; best = e; }
                         }
                     }
