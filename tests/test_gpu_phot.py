@@ -110,3 +110,29 @@ def test_device_count_limits_work(gpu, orc):
     out = gpu.aperture_phot(dev(sub), x, y, n_src=n)
     fl = host(out["n_ann"])
     assert np.all(fl[:3] > 0)
+
+
+def test_centroid_aperture_survey_frame_full_size(gpu, orc):
+    """the 4096^2 survey frame of the benchmark through ipp_extract (the launch
+    configuration the benchmark times); a seeded sample of 600 sources
+    recomputed by the oracle from the GPU's own subtracted frame, seeds and
+    positions."""
+    img, _ = synth.frame_survey_4k()
+    out = gpu.extract(dev(img), mesh=128)
+    n = int(host(out["n_src"])[0])
+    assert n > 10000
+    sub = host(out["sub"])
+    pick = np.sort(np.random.default_rng(5).choice(n, 600, replace=False))
+    x0 = host(out["stats"]["xbar"])[pick].astype(np.float32)
+    y0 = host(out["stats"]["ybar"])[pick].astype(np.float32)
+    ox, oy, _, ofl = orc.centroid(sub, x0, y0)
+    gx, gy = host(out["x"])[pick], host(out["y"])[pick]
+    conv = (ofl & 2) == 0
+    assert conv.mean() > 0.5
+    tol = 3e-4 + 2 * float_ulp(ox)
+    assert np.all(np.abs(gx - ox)[conv] <= tol[conv]) and np.all(np.abs(gy - oy)[conv] <= tol[conv])
+    ph = orc.aperture(sub, gx.astype(np.float32), gy.astype(np.float32))
+    gf = host(out["flux"])[pick]
+    rms = float(np.median(host(out["mesh_rms"])))
+    scale = np.abs(ph["flux"]) + ph["area"] * (np.abs(ph["sky"]) + rms)
+    assert np.all(np.abs(gf - ph["flux"]) <= 1e-5 * scale)

@@ -140,3 +140,21 @@ def test_fit_gaussian_and_weights(gpu, orc):
     ok = (o["flags"] == 0) & (g["flags"] == 0)
     assert ok.mean() > 0.8
     assert np.all(np.abs(g["chi2"][ok] - o["chi2"][ok]) <= 1e-4 * o["chi2"][ok])
+
+
+def test_fit_full_size_sampled(gpu, orc):
+    """the benchmark's 200,000 stamps in one call (one lane per stamp); a seeded
+    sample of 300 refitted by the oracle.  Converged-on-both fits reach the same
+    chi^2 optimum."""
+    stamps, truth = synth.moffat_stamps(200000, seed=4000, oversample=3)
+    g = {k: host(v) for k, v in gpu.psf_fit(dev(stamps)).items()}
+    pick = np.sort(np.random.default_rng(9).choice(len(stamps), 300, replace=False))
+    o = orc.psf_fit(stamps[pick])
+    conv = (o["flags"] == 0) & (g["flags"][pick] == 0)
+    assert conv.mean() > 0.3
+    rel = np.abs(g["chi2"][pick] - o["chi2"]) / o["chi2"]
+    assert np.median(rel[conv]) < 1e-5
+    bright = conv & (truth[pick, 2] > 5e3)
+    assert bright.sum() > 10 and np.all(rel[bright] < 1e-4)
+    gp, op = g["params"][pick][bright], o["params"][bright]
+    assert np.all(np.abs(gp[:, :2] - op[:, :2]) <= 1e-4 + 4e-6 * np.abs(op[:, :2]))
