@@ -87,6 +87,8 @@ def lib():
             L.orc_stamp_cut.argtypes = [vp, i64, i64, i64, vp, vp, i32, vp, vp, vp, vp]
             L.orc_auto_phot.argtypes = [vp, vp, i64, i64, i64] + [vp] * 6 + [d, d, d] + [vp] * 7
             L.orc_deblend.argtypes = [vp, vp, i64, i64, i64, i32, d, vp]
+            L.orc_gray_transform.argtypes = [vp, i64, i64, i32, d, d, d, vp]
+            L.orc_hist_equalize.argtypes = [vp, i64, i64, i32, vp]
             L.orc_deblend.restype = i64
             L.orc_psf_model.argtypes = [vp, i32, i32, d, vp, vp]
             L.orc_psf_fit.argtypes = [vp, i64, i32, vp, vp, i32, d, i32, d, vp, vp, vp, vp]
@@ -236,6 +238,25 @@ def aperture(sub, x, y, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann=10):
     lib().orc_aperture(_p(sub), W, H, n, _p(x), _p(y), float(r_ap), float(r_in), float(r_out),
                        int(min_ann), _p(out["flux"]), _p(out["sky"]), _p(out["area"]),
                        _p(out["n_ann"]), _p(out["flags"]))
+    return out
+
+
+GRAY_LINEAR, GRAY_LOG, GRAY_POWER, GRAY_EXP = 0, 1, 2, 3
+
+
+def gray_transform(img, kind, lo, hi, a=1000.0):
+    img = _f32(img)
+    H, W = img.shape
+    out = np.zeros((H, W))
+    assert lib().orc_gray_transform(_p(img), W, H, int(kind), float(lo), float(hi), float(a), _p(out)) == 0
+    return out
+
+
+def hist_equalize(img, nbins=4096):
+    img = _f32(img)
+    H, W = img.shape
+    out = np.zeros((H, W))
+    assert lib().orc_hist_equalize(_p(img), W, H, int(nbins), _p(out)) == 0
     return out
 
 

@@ -528,6 +528,90 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
     return ORC_OK;
 }
 
+/* ----------------------------------------------------- gray-scale maps */
+/*
+ * Gray-scale transforms (Sec. 2.2.6: pixel values mapped to new gray values by
+ * mathematical functions; the functions are readings after the usual display
+ * scales).  xn = clip((x - lo) / (hi - lo), 0, 1); non-finite x gives 0.
+ *   ORC_GRAY_LINEAR  y = xn
+ *   ORC_GRAY_LOG     y = log10(a xn + 1) / log10(a + 1)
+ *   ORC_GRAY_POWER   y = xn ^ a            (a > 0)
+ *   ORC_GRAY_EXP     y = (a ^ xn - 1) / (a - 1)   (a > 0, a != 1)
+ */
+int orc_gray_transform(const float* img, int64_t W, int64_t H, int32_t kind, double lo, double hi,
+                       double a, double* out) {
+    if (!(hi > lo)) return ORC_INVALID_ARG;
+    for (int64_t k = 0; k < W * H; k++) {
+        const double x = (double)img[k];
+        if (!isfinite(x)) { out[k] = 0.0; continue; }
+        double xn = (x - lo) / (hi - lo);
+        xn = xn < 0.0 ? 0.0 : (xn > 1.0 ? 1.0 : xn);
+        double y;
+        switch (kind) {
+            case 1: y = log10(a * xn + 1.0) / log10(a + 1.0); break;
+            case 2: y = pow(xn, a); break;
+            case 3: y = (pow(a, xn) - 1.0) / (a - 1.0); break;
+            default: y = xn;
+        }
+        out[k] = y;
+    }
+    return ORC_OK;
+}
+
+/*
+ * Histogram equalisation (Sec. 2.2.6: a histogram of the gray values, its
+ * cumulative distribution, and an interpolation that maps each value onto a
+ * uniform distribution).  Over the finite pixels: mn, mx = min, max; nbins bins
+ * of width (mx - mn) / nbins; the bin of x is floor((x - mn) s), s = nbins /
+ * (mx - mn), clamped to the last bin -- taken in single precision, exactly as
+ * written here, because it decides an integer; cdf_i = (count of bins <= i) / N;
+ * y = the linear interpolation of cdf between the bin centres at
+ * t = (x - mn) s - 1/2 (float), held at cdf_0 below the first centre and cdf_last
+ * above the last.  mx == mn gives 0; non-finite pixels give 0.
+ */
+int orc_hist_equalize(const float* img, int64_t W, int64_t H, int32_t nbins, double* out) {
+    if (nbins < 2) return ORC_INVALID_ARG;
+    const int64_t n = W * H;
+    float mn = INFINITY, mx = -INFINITY;
+    int64_t nf = 0;
+    for (int64_t k = 0; k < n; k++) {
+        const float x = img[k];
+        if (!isfinite(x)) continue;
+        if (x < mn) mn = x;
+        if (x > mx) mx = x;
+        nf++;
+    }
+    if (nf == 0 || !(mx > mn)) {
+        for (int64_t k = 0; k < n; k++) out[k] = 0.0;
+        return ORC_OK;
+    }
+    const float sc = (float)nbins / (mx - mn);
+    int64_t* cnt = (int64_t*)calloc((size_t)nbins, sizeof(int64_t));
+    for (int64_t k = 0; k < n; k++) {
+        const float x = img[k];
+        if (!isfinite(x)) continue;
+        int b = (int)floorf((x - mn) * sc);
+        if (b > nbins - 1) b = nbins - 1;
+        if (b < 0) b = 0;
+        cnt[b]++;
+    }
+    double* cdf = (double*)malloc(sizeof(double) * (size_t)nbins);
+    int64_t run = 0;
+    for (int b = 0; b < nbins; b++) { run += cnt[b]; cdf[b] = (double)run / (double)nf; }
+    for (int64_t k = 0; k < n; k++) {
+        const float x = img[k];
+        if (!isfinite(x)) { out[k] = 0.0; continue; }
+        const float t = (x - mn) * sc - 0.5f;
+        if (!(t > 0.0f)) { out[k] = cdf[0]; continue; }
+        const int b = (int)floorf(t);
+        if (b >= nbins - 1) { out[k] = cdf[nbins - 1]; continue; }
+        const double fr = (double)(t - (float)b);
+        out[k] = cdf[b] + fr * (cdf[b + 1] - cdf[b]);
+    }
+    free(cnt); free(cdf);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------ deblending */
 /*
  * Deblending (Sec. 2.2.4, source detection: multi-level thresholds between each

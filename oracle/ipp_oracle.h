@@ -96,6 +96,12 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
                  double r_out, int32_t min_ann, double* flux, double* sky,
                  double* area, int32_t* n_ann, int32_t* flags);
 
+/* Gray-scale maps (Sec. 2.2.6): kind 0 linear, 1 log, 2 power, 3 exp of the
+ * value clipped to [lo, hi]; histogram equalisation over nbins bins. */
+int orc_gray_transform(const float* img, int64_t W, int64_t H, int32_t kind, double lo, double hi,
+                       double a, double* out);
+int orc_hist_equalize(const float* img, int64_t W, int64_t H, int32_t nbins, double* out);
+
 /* Deblending (Sec. 2.2.4): multi-level thresholds, sub-component tree, pruning
  * on intensity (mincont), remaining pixels to the likeliest object; objects
  * numbered candidate by candidate, within one in raster order of their first
