@@ -420,6 +420,16 @@ def main():
     stages["deblend"] = timeit(lambda k: ipp.deblend(subbuf, lab, nsrc, st, max_src=65536, ws=dbws))
     _, n_deb = ipp.deblend(subbuf, lab, nsrc, st, max_src=65536, ws=dbws)
     deblended_objects = int(n_deb.item())
+    # gray-scale maps of the subtracted frame (a widening, timed beside the step):
+    # four distinct input/output pairs rotate, 512 MiB in all, so that each call
+    # reads its input from HBM, not L2
+    gin = [subbuf.clone() for _ in range(4)]
+    gout = [torch.empty_like(subbuf) for _ in range(4)]
+    gws = torch.empty(ipp.load().ipp_hist_equalize_workspace_size(4096), dtype=torch.uint8, device=dev)
+    stages["gray_log"] = timeit(
+        lambda k: ipp.gray_transform(gin[k % 4], ipp.GRAY_LOG, 0.0, 2000.0, a=1000.0, out=gout[k % 4]))
+    stages["hist_equalize"] = timeit(lambda k: ipp.hist_equalize(gin[k % 4], nbins=4096, out=gout[k % 4], ws=gws))
+    del gin, gout
 
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
@@ -435,6 +445,14 @@ def main():
     whole = {"algorithmic_bytes_per_step": 16 * W * H, "achieved_gbs": 16 * W * H / (step_ms / 1e3) / 1e9}
     whole["frac_of_measured_hbm"] = whole["achieved_gbs"] / hbm
     whole["frac_of_nominal_hbm"] = whole["achieved_gbs"] / 7900.0
+    # gray maps: the log map reads and writes each pixel once (8 B/px); equalisation
+    # reads the frame three times (min/max, histogram, apply) and writes it once
+    # (16 B/px; 12 B/px would be the floor of any two-pass form)
+    gray = {}
+    for key, bpp, kern in (("gray_log", 8, "k_gray"), ("hist_equalize", 16, "k_minmax + k_hist + k_cdf + k_equalize")):
+        gb = bpp * W * H / (stages[key] / 1e3) / 1e9
+        gray[key] = {"kernels": kern, "bytes_per_px": bpp, "ms": stages[key], "achieved_gbs": gb,
+                     "frac_of_measured_hbm": gb / hbm}
 
     # ---- PSF fit leg: 200k Moffat stamps ---------------------------------------
     psf = None
@@ -493,7 +511,7 @@ def main():
                     "pipelining": f"each step H2D + catalog + D2H on one of {L} lane streams",
                     "d2h_bytes_per_step": 4 + 3 * 4 * nmax},
             "gpu_launches": KERNELS_PER_FRAME * args.steps,
-            "roofline": roof, "step_roofline": whole, "stages_ms": stages,
+            "roofline": roof, "step_roofline": whole, "stages_ms": stages, "gray_maps": gray,
             "clocks": clk.summary(), "psf_fit": psf, "batched": batch, "raw_u16_stream": raw,
             "cpu_baseline": cpu,
         }

@@ -77,6 +77,12 @@ extern "C" {
 #define IPP_EST_FACTORS 3 /* Eq. 4, read as median_factor * median - mean_factor * mean */
 
 /* PSF models */
+/* Gray-scale functions of ipp_gray_transform (Sec. 2.2.6). */
+#define IPP_GRAY_LINEAR 0
+#define IPP_GRAY_LOG 1
+#define IPP_GRAY_POWER 2
+#define IPP_GRAY_EXP 3
+
 #define IPP_PSF_MOFFAT 0
 #define IPP_PSF_GAUSS 1
 
@@ -354,6 +360,47 @@ int ipp_auto_phot(const float* sub, const int32_t* labels, int64_t W, int64_t H,
                   const int32_t* n_src_dev, int32_t max_src, const ipp_src_stats* stats,
                   const ipp_auto_params* p, float* flux, float* area, float* kron, float* shape,
                   int32_t* flags, void* stream);
+
+/*
+ * ipp_gray_transform -- value-to-gray map of Sec. 2.2.6 (the display functions
+ * it lists: linear, logarithmic, power, exponential).  With
+ * xn = clip((x - lo) / (hi - lo), 0, 1) per pixel:
+ *   IPP_GRAY_LINEAR  xn
+ *   IPP_GRAY_LOG     log10(a xn + 1) / log10(a + 1)      (a > 0)
+ *   IPP_GRAY_POWER   xn^a                                (a > 0)
+ *   IPP_GRAY_EXP     (a^xn - 1) / (a - 1)                (a > 0, a != 1)
+ * Non-finite pixels map to 0.  Arithmetic is FP32 (xn from (x - lo) times the
+ * rounded 1 / (hi - lo)); the result is within a few 1e-7 of the FP64 value.
+ *   img     device float, rows of `pitch` elements
+ *   out     device float, rows of `out_pitch` (>= W); must not alias img
+ *   lo, hi  finite, lo < hi
+ * Errors: INVALID_ARG for NULL pointers, bad sizes or pitches, an unknown kind,
+ * lo >= hi or an `a` outside the ranges above, or out == img.
+ */
+int ipp_gray_transform(const float* img, int64_t W, int64_t H, int64_t pitch, int32_t kind, float lo, float hi,
+                       float a, float* out, int64_t out_pitch, void* stream);
+
+/*
+ * ipp_hist_equalize -- histogram equalisation of Sec. 2.2.6.  Over the finite
+ * pixels, min and max give nbins bins of width (max - min) / nbins; pixel x falls
+ * in bin floor((x - min) s), s = nbins / (max - min) (FP32, clamped to
+ * [0, nbins - 1]); C(b) is the fraction of finite pixels in bins 0..b.  The gray
+ * value is C interpolated linearly between bin centres at t = (x - min) s - 1/2:
+ * C(0) for t <= 0, C(nbins - 1) for t >= nbins - 1.  Non-finite pixels, and every
+ * pixel of a frame with no finite value or max == min, map to 0.
+ *   nbins   2 <= nbins <= 16384
+ *   out     device float, rows of `out_pitch` (>= W); must not alias img
+ *   ws      device workspace of ipp_hist_equalize_workspace_size(nbins) bytes,
+ *           256-byte aligned; after the call it holds (from byte 256) the counts
+ *           uint32[nbins] and, at the next 256-byte boundary, C as float[nbins]
+ * Four launches (min/max, histogram, cumulative sum, apply) and three memsets on
+ * `stream`; no host synchronisation.
+ * Errors: INVALID_ARG for NULL pointers, bad sizes or pitches, nbins out of range,
+ * a misaligned or short workspace, or out == img.
+ */
+size_t ipp_hist_equalize_workspace_size(int32_t nbins);
+int ipp_hist_equalize(const float* img, int64_t W, int64_t H, int64_t pitch, int32_t nbins, float* out,
+                      int64_t out_pitch, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * ipp_stamp_cut -- S x S stamps of the subtracted frame around each source, the

@@ -20,10 +20,12 @@ import torch
 from . import _abi
 from ._abi import (  # noqa: F401
     EST_FACTORS, EST_MEAN, EST_MEDIAN, EST_SIGMA, FLAG_ANN_FEW, FLAG_EDGE, FLAG_FIT_BAD_SIGMA,
-    FLAG_FIT_MAXITER, FLAG_FIT_SINGULAR, FLAG_WIN_NOT_CONVERGED, IppError, PSF_GAUSS, PSF_MOFFAT,
+    FLAG_FIT_MAXITER, FLAG_FIT_SINGULAR, FLAG_WIN_NOT_CONVERGED, GRAY_EXP, GRAY_LINEAR, GRAY_LOG, GRAY_POWER,
+    IppError, PSF_GAUSS, PSF_MOFFAT,
 )
 
 __all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "deblend", "stamp_cut", "Batch",
+           "gray_transform", "hist_equalize",
            "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
 
 
@@ -253,6 +255,47 @@ def auto_phot(sub, labels, n_src, stats, k_kron=2.5, r_min=3.5, r_kmax=6.0, max_
         _abi.AutoParams(k_kron, r_min, r_kmax, 0), _ptr(out["flux"]), _ptr(out["area"]), _ptr(out["kron"]),
         _ptr(out["shape"]), _ptr(out["flags"]), _stream()))
     return {k: v[:n] for k, v in out.items()}
+
+
+def _frame2d(img, name):
+    _need_cuda(img, name, torch.float32)
+    if img.dim() != 2 or img.stride(1) != 1:
+        raise TypeError(f"{name} must be a 2-D tensor with unit column stride")
+
+
+def gray_transform(img, kind, lo, hi, a=1000.0, out=None):
+    """Value-to-gray map of the frame (ipp_gray_transform): GRAY_LINEAR, GRAY_LOG,
+    GRAY_POWER or GRAY_EXP of clip((x - lo) / (hi - lo), 0, 1)."""
+    L = load()
+    _frame2d(img, "img")
+    H, W = img.shape
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    _frame2d(out, "out")
+    _abi.check("ipp_gray_transform", L.ipp_gray_transform(
+        _ptr(img), W, H, img.stride(0), int(kind), float(lo), float(hi), float(a), _ptr(out), out.stride(0),
+        _stream()))
+    return out
+
+
+def hist_equalize(img, nbins=4096, out=None, ws=None):
+    """Histogram-equalised gray map of the frame (ipp_hist_equalize); returns the
+    map and the workspace, which holds the bin counts and the cumulative
+    distribution after the call."""
+    L = load()
+    _frame2d(img, "img")
+    H, W = img.shape
+    need = L.ipp_hist_equalize_workspace_size(int(nbins))
+    if need == 0:
+        raise ValueError(f"nbins must be 2..16384, got {nbins}")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    _frame2d(out, "out")
+    _abi.check("ipp_hist_equalize", L.ipp_hist_equalize(
+        _ptr(img), W, H, img.stride(0), int(nbins), _ptr(out), out.stride(0), _ptr(ws), ws.numel(), _stream()))
+    return out, ws
 
 
 def stamp_cut(sub, x, y, n_src=None, S=15, max_src=None):

@@ -18,6 +18,7 @@ FLAG_EDGE, FLAG_WIN_NOT_CONVERGED, FLAG_ANN_FEW = 1, 2, 4
 FLAG_FIT_MAXITER, FLAG_FIT_SINGULAR, FLAG_FIT_BAD_SIGMA = 8, 16, 32
 EST_SIGMA, EST_MEDIAN, EST_MEAN, EST_FACTORS = 0, 1, 2, 3
 PSF_MOFFAT, PSF_GAUSS = 0, 1
+GRAY_LINEAR, GRAY_LOG, GRAY_POWER, GRAY_EXP = 0, 1, 2, 3
 
 vp, i32, i64, f32, f64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_size_t
 
@@ -97,6 +98,9 @@ PROTOTYPES = {
                      vp], i32),
     "ipp_auto_phot": ([vp, vp, i64, i64, i64, vp, i32, C.POINTER(SrcStats), C.POINTER(AutoParams), vp, vp, vp,
                        vp, vp, vp], i32),
+    "ipp_gray_transform": ([vp, i64, i64, i64, i32, f32, f32, f32, vp, i64, vp], i32),
+    "ipp_hist_equalize_workspace_size": ([i32], sz),
+    "ipp_hist_equalize": ([vp, i64, i64, i64, i32, vp, i64, vp, sz, vp], i32),
     "ipp_stamp_cut": ([vp, i64, i64, i64, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp], i32),
     "ipp_extract_workspace_size": ([i64, i64, C.POINTER(BgParams)], sz),
     "ipp_extract": ([vp, i32, i64, i64, i64, C.POINTER(Calib), C.POINTER(BgParams), C.POINTER(DetParams),

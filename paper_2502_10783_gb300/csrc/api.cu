@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libipp: argument validation, workspace layout and the
 // launch sequences of each call.  All calls are asynchronous on `stream`.
 #include <stdarg.h>
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -275,6 +276,35 @@ extern "C" int ipp_deblend(const float* sub, const int32_t* labels, int64_t W, i
     J.out = out_labels; J.n_out_dev = n_out_dev;
     ipp_deblend_ws_carve(W, H, max_src, ws, &J.ws);
     return ipp_launch_deblend(J, (cudaStream_t)stream);
+}
+
+// ---- gray-scale maps ------------------------------------------------------------------
+extern "C" int ipp_gray_transform(const float* img, int64_t W, int64_t H, int64_t pitch, int32_t kind, float lo,
+                                  float hi, float a, float* out, int64_t out_pitch, void* stream) {
+    if (int e = check_frame(img, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(out && out_pitch >= W, "out NULL or out_pitch < W");
+    REQUIRE((const void*)out != (const void*)img, "out must not alias img");
+    REQUIRE(kind >= IPP_GRAY_LINEAR && kind <= IPP_GRAY_EXP, "unknown gray function %d", kind);
+    REQUIRE(std::isfinite(lo) && std::isfinite(hi) && lo < hi, "need finite lo < hi");
+    if (kind != IPP_GRAY_LINEAR) REQUIRE(a > 0.f && std::isfinite(a), "need finite a > 0");
+    if (kind == IPP_GRAY_EXP) REQUIRE(a != 1.f, "exponential map needs a != 1");
+    return ipp_launch_gray(img, W, H, pitch, kind, lo, hi, a, out, out_pitch, (cudaStream_t)stream);
+}
+
+extern "C" size_t ipp_hist_equalize_workspace_size(int32_t nbins) {
+    if (nbins < 2 || nbins > 16384) return 0;
+    return ipp_equalize_ws_bytes(nbins);
+}
+
+extern "C" int ipp_hist_equalize(const float* img, int64_t W, int64_t H, int64_t pitch, int32_t nbins, float* out,
+                                 int64_t out_pitch, void* ws, size_t ws_bytes, void* stream) {
+    if (int e = check_frame(img, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(nbins >= 2 && nbins <= 16384, "nbins must be 2..16384 (got %d)", nbins);
+    REQUIRE(out && out_pitch >= W, "out NULL or out_pitch < W");
+    REQUIRE((const void*)out != (const void*)img, "out must not alias img");
+    REQUIRE(ws && ((uintptr_t)ws & 255) == 0, "workspace NULL or not 256-byte aligned");
+    REQUIRE(ws_bytes >= ipp_equalize_ws_bytes(nbins), "workspace too small");
+    return ipp_launch_equalize(img, W, H, pitch, nbins, out, out_pitch, ws, (cudaStream_t)stream);
 }
 
 extern "C" int ipp_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, const int32_t* n_src_dev,

@@ -168,6 +168,11 @@ int ipp_launch_auto_phot(const ipp::AutoJob& J, cudaStream_t s);
 int ipp_launch_deblend(const ipp::DeblendJob& J, cudaStream_t s);
 size_t ipp_deblend_ws_carve(int64_t W, int64_t H, int32_t max_src, void* ws, ipp::DeblendWs* out);
 int ipp_launch_psf_fit(const ipp::FitJob& J, cudaStream_t s);
+int ipp_launch_gray(const float* img, int64_t W, int64_t H, int64_t pitch, int kind, float lo, float hi, float a,
+                    float* out, int64_t opitch, cudaStream_t s);
+size_t ipp_equalize_ws_bytes(int nbins);
+int ipp_launch_equalize(const float* img, int64_t W, int64_t H, int64_t pitch, int nbins, float* out,
+                        int64_t opitch, void* ws, cudaStream_t s);
 int ipp_launch_psf_fwd(const float* params, int64_t N, int S, int model, float beta, float* model_out, cudaStream_t s);
 int ipp_launch_psf_adj(const float* params, int64_t N, int S, int model, float beta, const float* grad_model,
                        float* grad_params, cudaStream_t s);
