@@ -393,7 +393,8 @@ int ipp_gray_transform(const float* img, int64_t W, int64_t H, int64_t pitch, in
  *   ws      device workspace of ipp_hist_equalize_workspace_size(nbins) bytes,
  *           256-byte aligned; after the call it holds (from byte 256) the counts
  *           uint32[nbins] and, at the next 256-byte boundary, C as float[nbins]
- * Four launches (min/max, histogram, cumulative sum, apply) and three memsets on
+ *           (followed by the pairs (C(b), C(b + 1) - C(b)) the apply pass reads)
+ * Four launches (min/max, histogram, cumulative sum, apply) and one memset on
  * `stream`; no host synchronisation.
  * Errors: INVALID_ARG for NULL pointers, bad sizes or pitches, nbins out of range,
  * a misaligned or short workspace, or out == img.

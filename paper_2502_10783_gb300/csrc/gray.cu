@@ -9,11 +9,14 @@
 //   gray value is the cumulative distribution interpolated between bin centres at
 //   t = (x - min) s - 1/2, clamped to the first and last bin.
 // Every pass streams the frame in groups of four pixels (one 128-bit load where
-// the row pitch and base allow); the histogram is privatised per block in
-// shared memory and merged with one atomic per non-empty bin.
+// the row pitch and base allow), two groups in flight per thread; a frame whose
+// rows are contiguous is streamed as one flat row (no row arithmetic).  The
+// histogram is privatised per block in shared memory and merged with one atomic
+// per non-empty bin.
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "jobs.cuh"
 
@@ -21,28 +24,46 @@ namespace ipp {
 
 constexpr int GR_T = 256;
 
-__device__ __forceinline__ float gray_map(float x, int kind, float lo, float inv, float a, float ka) {
+// Internal forms of the four functions.  The fast forms use the hardware
+// base-2 logarithm and exponential (absolute error near 2^-22 in log2, relative
+// near 2^-22 in exp2); they are taken where that error, carried to the gray
+// value, stays below a few 1e-7: log for a >= 1 (the error is divided by
+// log2(1 + a) >= 1), exp for base >= 2, power always (the exponent error a 2^-22
+// is relative in xn^a).  log1p / expm1 keep full relative accuracy for a < 1
+// (log) or a base below 2 (exp), where 1 + a xn or a^xn - 1 would cancel.
+enum GrForm { GR_LINEAR = 0, GR_LOG_FAST, GR_POWER_FAST, GR_EXP_FAST, GR_LOG1P, GR_EXPM1 };
+
+template <int FORM>
+__device__ __forceinline__ float gray_map(float x, float lo, float inv, float a, float ka) {
     if (!isfinite(x)) return 0.f;
     float xn = __fmul_rn(__fsub_rn(x, lo), inv);
     xn = fminf(fmaxf(xn, 0.f), 1.f);
-    switch (kind) {
-        // log1p / expm1 keep full relative accuracy for a near 0 (log) or 1 (exp)
-        case IPP_GRAY_LOG: return log1pf(a * xn) * ka;     // ka = 1 / ln(a + 1)
-        case IPP_GRAY_POWER: return xn > 0.f ? powf(xn, a) : 0.f;
-        case IPP_GRAY_EXP: return expm1f(xn * a) * ka;     // a = ln(base), ka = 1 / (base - 1)
-        default: return xn;
-    }
+    if (FORM == GR_LOG_FAST) return __log2f(fmaf(a, xn, 1.f)) * ka;            // ka = 1 / log2(1 + a)
+    if (FORM == GR_POWER_FAST) return xn > 0.f ? exp2f(a * __log2f(xn)) : 0.f;
+    if (FORM == GR_EXP_FAST) return (exp2f(xn * a) - 1.f) * ka;                 // a = log2(base)
+    if (FORM == GR_LOG1P) return log1pf(a * xn) * ka;                           // ka = 1 / ln(1 + a)
+    if (FORM == GR_EXPM1) return expm1f(xn * a) * ka;                           // a = ln(base)
+    return xn;                                                                   // ka = 1 / (base - 1)
 }
 
-// Group q of four pixels of a W x H frame: row y, first column x0, and the
-// values (0 beyond the row's end).  I is the index type (32-bit when the
-// number of groups allows).
-template <class I>
-__device__ __forceinline__ void load4(const float* __restrict__ img, I q, I qpr, int64_t W, int64_t pitch, bool vec,
-                                      int64_t& y, int64_t& x0, float v[4]) {
-    const I yy = q / qpr;
-    y = (int64_t)yy;
-    x0 = (int64_t)(q - yy * qpr) * 4;
+// Index modes of the streaming loops: 0 a flat row with 32-bit group indices,
+// 1 rows with 32-bit group indices, 2 rows with 64-bit group indices.
+template <int MODE>
+using GrIdx = typename std::conditional<MODE == 2, uint64_t, uint32_t>::type;
+
+// Group q of four pixels: row y, first column x0, and the values (0 beyond the
+// row's end).
+template <int MODE>
+__device__ __forceinline__ void load4(const float* __restrict__ img, GrIdx<MODE> q, GrIdx<MODE> qpr, int64_t W,
+                                      int64_t pitch, bool vec, int64_t& y, int64_t& x0, float v[4]) {
+    if (MODE == 0) {
+        y = 0;
+        x0 = (int64_t)q * 4;
+    } else {
+        const GrIdx<MODE> yy = q / qpr;
+        y = (int64_t)yy;
+        x0 = (int64_t)(q - yy * qpr) * 4;
+    }
     const float* row = img + y * pitch;
     if (vec && x0 + 4 <= W) {
         const float4 t = __ldg(reinterpret_cast<const float4*>(row + x0));
@@ -65,44 +86,56 @@ __device__ __forceinline__ void store4(float* __restrict__ out, int64_t y, int64
     }
 }
 
-__device__ __forceinline__ bool vec_ok(const void* p, int64_t pitch) {
-    return (pitch % 4 == 0) && (((uintptr_t)p & 15) == 0);
-}
-
-template <class I>
-__global__ void __launch_bounds__(GR_T) k_gray(const float* __restrict__ img, int64_t W, int64_t H, int64_t pitch,
-                                               int kind, float lo, float inv, float a, float ka,
-                                               float* __restrict__ out, int64_t opitch) {
-    const I qpr = (I)((W + 3) >> 2), nq = qpr * (I)H;
-    const bool vin = vec_ok(img, pitch), vout = vec_ok(out, opitch);
-    for (I q = (I)blockIdx.x * GR_T + threadIdx.x; q < nq; q += (I)gridDim.x * GR_T) {
-        int64_t y, x0;
-        float v[4];
-        load4<I>(img, q, qpr, W, pitch, vin, y, x0, v);
-#pragma unroll
-        for (int c = 0; c < 4; c++) v[c] = gray_map(v[c], kind, lo, inv, a, ka);
-        store4(out, y, x0, W, opitch, vout, v);
+// Grid-stride visit of all groups, the loads of two groups issued before either
+// is processed: fn(v, y, x0) per group.
+template <int MODE, class Fn>
+__device__ __forceinline__ void stream_groups(const float* __restrict__ img, int64_t W, int64_t H, int64_t pitch,
+                                              bool vin, Fn&& fn) {
+    using I = GrIdx<MODE>;
+    const I qpr = (I)((W + 3) >> 2), nq = qpr * (I)H, stride = (I)gridDim.x * GR_T;
+    for (I q = (I)blockIdx.x * GR_T + threadIdx.x; q < nq; q += 2 * stride) {
+        const I q2 = q + stride;
+        const bool two = q2 < nq;
+        int64_t y0, x0, y1 = 0, x1 = 0;
+        float a[4], b[4] = {0.f, 0.f, 0.f, 0.f};
+        load4<MODE>(img, q, qpr, W, pitch, vin, y0, x0, a);
+        if (two) load4<MODE>(img, q2, qpr, W, pitch, vin, y1, x1, b);
+        fn(a, y0, x0);
+        if (two) fn(b, y1, x1);
     }
 }
 
+template <int MODE, int FORM>
+__global__ void __launch_bounds__(GR_T, 8) k_gray(const float* __restrict__ img, int64_t W, int64_t H, int64_t pitch,
+                                               bool vin, float lo, float inv, float a, float ka,
+                                               float* __restrict__ out, int64_t opitch, bool vout) {
+    stream_groups<MODE>(img, W, H, pitch, vin, [&](float v[4], int64_t y, int64_t x0) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) v[c] = gray_map<FORM>(v[c], lo, inv, a, ka);
+        store4(out, y, x0, W, opitch, vout, v);
+    });
+}
+
+// Workspace: a 256-byte header (the three reduction words on separate 64-byte
+// lines, all zero-initialised by one memset together with the counts), the
+// counts and the cumulative distribution.
 struct GrayWs {
-    uint32_t* kmin;   // fkey of the smallest finite value
-    uint32_t* kmax;   // fkey of the largest
+    uint32_t* kminc;  // complement of the fkey of the smallest finite value (max of complements)
+    uint32_t* kmax;   // fkey of the largest finite value
     unsigned long long* nfin;
     uint32_t* cnt;    // [nbins]
     float* cdf;       // [nbins]
+    float2* seg;      // [nbins]: (C(b), C(b + 1) - C(b)), one gather per interpolation
 };
 
-template <class I>
-__global__ void __launch_bounds__(GR_T) k_minmax(const float* __restrict__ img, int64_t W, int64_t H, int64_t pitch,
-                                                 GrayWs w) {
-    const I qpr = (I)((W + 3) >> 2), nq = qpr * (I)H;
-    const bool vin = vec_ok(img, pitch);
+__device__ __forceinline__ float gr_min(const GrayWs& w) { return fkey_inv(~*w.kminc); }
+__device__ __forceinline__ float gr_max(const GrayWs& w) { return fkey_inv(*w.kmax); }
+
+template <int MODE>
+__global__ void __launch_bounds__(GR_T, 8) k_minmax(const float* __restrict__ img, int64_t W, int64_t H, int64_t pitch,
+                                                 bool vin, GrayWs w) {
     uint32_t kmn = 0xffffffffu, kmx = 0u, nf = 0;
-    for (I q = (I)blockIdx.x * GR_T + threadIdx.x; q < nq; q += (I)gridDim.x * GR_T) {
-        int64_t y, x0;
-        float v[4];
-        load4<I>(img, q, qpr, W, pitch, vin, y, x0, v);
+    stream_groups<MODE>(img, W, H, pitch, vin, [&](float v[4], int64_t, int64_t x0) {
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             if (x0 + c >= W || !isfinite(v[c])) continue;
@@ -111,32 +144,44 @@ __global__ void __launch_bounds__(GR_T) k_minmax(const float* __restrict__ img, 
             kmx = max(kmx, k);
             nf++;
         }
-    }
+    });
+    // warp, then block reduction: one set of atomics per block
+    __shared__ uint32_t r_mn[GR_T / 32], r_mx[GR_T / 32], r_nf[GR_T / 32];
     kmn = __reduce_min_sync(0xffffffffu, kmn);
     kmx = __reduce_max_sync(0xffffffffu, kmx);
-    nf = __reduce_add_sync(0xffffffffu, nf);   // a warp's share of the frame: far below 2^32 pixels
-    if ((threadIdx.x & 31) == 0 && nf) {
-        atomicMin(w.kmin, kmn);
-        atomicMax(w.kmax, kmx);
-        atomicAdd(w.nfin, (unsigned long long)nf);
+    nf = __reduce_add_sync(0xffffffffu, nf);   // a block's share of the frame: far below 2^32 pixels
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    if (lane == 0) {
+        r_mn[wi] = kmn;
+        r_mx[wi] = kmx;
+        r_nf[wi] = nf;
+    }
+    __syncthreads();
+    if (wi == 0) {
+        kmn = lane < GR_T / 32 ? r_mn[lane] : 0xffffffffu;
+        kmx = lane < GR_T / 32 ? r_mx[lane] : 0u;
+        nf = lane < GR_T / 32 ? r_nf[lane] : 0u;
+        kmn = __reduce_min_sync(0xffffffffu, kmn);
+        kmx = __reduce_max_sync(0xffffffffu, kmx);
+        nf = __reduce_add_sync(0xffffffffu, nf);
+        if (lane == 0 && nf) {
+            atomicMax(w.kminc, ~kmn);
+            atomicMax(w.kmax, kmx);
+            atomicAdd(w.nfin, (unsigned long long)nf);
+        }
     }
 }
 
-template <class I>
-__global__ void __launch_bounds__(GR_T) k_hist(const float* __restrict__ img, int64_t W, int64_t H, int64_t pitch,
-                                               int nbins, GrayWs w) {
+template <int MODE>
+__global__ void __launch_bounds__(GR_T, 8) k_hist(const float* __restrict__ img, int64_t W, int64_t H, int64_t pitch,
+                                               bool vin, int nbins, GrayWs w) {
     extern __shared__ uint32_t hsm[];
     for (int b = threadIdx.x; b < nbins; b += GR_T) hsm[b] = 0u;
     __syncthreads();
-    const float mn = fkey_inv(*w.kmin), mx = fkey_inv(*w.kmax);
+    const float mn = gr_min(w), mx = gr_max(w);
     if (*w.nfin > 0 && mx > mn) {
         const float sc = __fdiv_rn((float)nbins, __fsub_rn(mx, mn));
-        const I qpr = (I)((W + 3) >> 2), nq = qpr * (I)H;
-        const bool vin = vec_ok(img, pitch);
-        for (I q = (I)blockIdx.x * GR_T + threadIdx.x; q < nq; q += (I)gridDim.x * GR_T) {
-            int64_t y, x0;
-            float v[4];
-            load4<I>(img, q, qpr, W, pitch, vin, y, x0, v);
+        stream_groups<MODE>(img, W, H, pitch, vin, [&](float v[4], int64_t, int64_t x0) {
 #pragma unroll
             for (int c = 0; c < 4; c++) {
                 if (x0 + c >= W || !isfinite(v[c])) continue;
@@ -144,62 +189,61 @@ __global__ void __launch_bounds__(GR_T) k_hist(const float* __restrict__ img, in
                 b = min(max(b, 0), nbins - 1);
                 atomicAdd(&hsm[b], 1u);
             }
-        }
+        });
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += GR_T)
         if (hsm[b]) atomicAdd(&w.cnt[b], hsm[b]);
 }
 
-// Cumulative distribution of the counts: one block of 1024 threads, each owning
-// a contiguous run of bins; warp and block exclusive scans of the run totals.
-__global__ void __launch_bounds__(1024) k_cdf(int nbins, GrayWs w) {
-    __shared__ unsigned long long wsum[32];
-    const int per = (nbins + 1023) / 1024;
-    const int s0 = min(nbins, (int)threadIdx.x * per), s1 = min(nbins, s0 + per);
-    unsigned long long acc = 0;
-    for (int b = s0; b < s1; b++) acc += w.cnt[b];
+// Cumulative distribution of the counts, spread over nbins / 256 blocks (the
+// FP64 division per bin is the costly step): block k adds up the counts before
+// its slice, scans its 256 bins and divides one bin per thread.
+__global__ void __launch_bounds__(GR_T) k_cdf(int nbins, GrayWs w) {
+    __shared__ unsigned long long part[GR_T / 32];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    unsigned long long x = acc;
+    const int s0 = blockIdx.x * GR_T, b = s0 + threadIdx.x;
+    unsigned long long before = 0;
+    for (int j = threadIdx.x; j < s0; j += GR_T) before += w.cnt[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+    if (lane == 0) part[wi] = before;
+    __syncthreads();
+    before = 0;
+#pragma unroll
+    for (int k = 0; k < GR_T / 32; k++) before += part[k];
+    __syncthreads();
+    const unsigned long long c = b < nbins ? w.cnt[b] : 0ull;
+    unsigned long long x = c;   // inclusive scan within the warp
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long t = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += t;
     }
-    if (lane == 31) wsum[wi] = x;
+    if (lane == 31) part[wi] = x;
     __syncthreads();
-    if (wi == 0) {
-        unsigned long long z = wsum[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long t = __shfl_up_sync(0xffffffffu, z, o);
-            if (lane >= o) z += t;
-        }
-        wsum[lane] = z;
-    }
-    __syncthreads();
-    unsigned long long run = (x - acc) + (wi > 0 ? wsum[wi - 1] : 0ull);
+    for (int k = 0; k < wi; k++) x += part[k];
     const unsigned long long nf = *w.nfin;
-    for (int b = s0; b < s1; b++) {
-        run += w.cnt[b];
-        w.cdf[b] = (float)((double)run / (double)(nf ? nf : 1ull));
+    const double dn = (double)(nf ? nf : 1ull);
+    if (b < nbins) {
+        const unsigned long long run = before + x;
+        const float c0 = (float)((double)run / dn);
+        // C(b + 1) from the same integer sum the next bin's thread divides
+        const float c1 = b + 1 < nbins ? (float)((double)(run + w.cnt[b + 1]) / dn) : c0;
+        w.cdf[b] = c0;
+        w.seg[b] = make_float2(c0, c1 - c0);
     }
 }
 
-template <class I>
-__global__ void __launch_bounds__(GR_T) k_equalize(const float* __restrict__ img, int64_t W, int64_t H,
-                                                   int64_t pitch, int nbins, GrayWs w, float* __restrict__ out,
-                                                   int64_t opitch) {
-    const float mn = fkey_inv(*w.kmin), mx = fkey_inv(*w.kmax);
+template <int MODE>
+__global__ void __launch_bounds__(GR_T, 8) k_equalize(const float* __restrict__ img, int64_t W, int64_t H,
+                                                   int64_t pitch, bool vin, int nbins, GrayWs w,
+                                                   float* __restrict__ out, int64_t opitch, bool vout) {
+    const float mn = gr_min(w), mx = gr_max(w);
     const bool flat = !(*w.nfin > 0 && mx > mn);
     const float sc = flat ? 0.f : __fdiv_rn((float)nbins, __fsub_rn(mx, mn));
     const float cfirst = __ldg(w.cdf), clast = __ldg(w.cdf + nbins - 1);
-    const I qpr = (I)((W + 3) >> 2), nq = qpr * (I)H;
-    const bool vin = vec_ok(img, pitch), vout = vec_ok(out, opitch);
-    for (I q = (I)blockIdx.x * GR_T + threadIdx.x; q < nq; q += (I)gridDim.x * GR_T) {
-        int64_t y, x0;
-        float v[4];
-        load4<I>(img, q, qpr, W, pitch, vin, y, x0, v);
+    stream_groups<MODE>(img, W, H, pitch, vin, [&](float v[4], int64_t y, int64_t x0) {
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             const float x = v[c];
@@ -213,54 +257,117 @@ __global__ void __launch_bounds__(GR_T) k_equalize(const float* __restrict__ img
                     if (b >= nbins - 1) {
                         g = clast;
                     } else {
-                        const float c0 = __ldg(w.cdf + b), c1 = __ldg(w.cdf + b + 1);
-                        g = fmaf(t - (float)b, c1 - c0, c0);
+                        const float2 cd = __ldg(w.seg + b);
+                        g = fmaf(t - (float)b, cd.y, cd.x);
                     }
                 }
             }
             v[c] = g;
         }
         store4(out, y, x0, W, opitch, vout, v);
-    }
+    });
 }
 
 }  // namespace ipp
 
 using namespace ipp;
 
-static unsigned gr_grid(int64_t W, int64_t H, int per_sm) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t nq = ((W + 3) >> 2) * H;
-    const int64_t need = (nq + GR_T - 1) / GR_T, cap = (int64_t)(sms > 0 ? sms : 152) * per_sm;
-    return (unsigned)std::max<int64_t>(1, std::min(need, cap));
+namespace {
+
+// A frame as the streaming loops see it: contiguous rows (in and, where there
+// is one, out) collapse to one flat row.
+struct GrView {
+    int64_t W, H, pitch, opitch;
+    bool vin, vout;
+    int mode;
+    unsigned grid(int per_sm) const {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t nq = ((W + 3) >> 2) * H;
+        const int64_t need = (nq + GR_T - 1) / GR_T, cap = (int64_t)(sms > 0 ? sms : 152) * per_sm;
+        return (unsigned)std::max<int64_t>(1, std::min(need, cap));
+    }
+};
+
+GrView gr_view(const float* img, int64_t W, int64_t H, int64_t pitch, const float* out, int64_t opitch) {
+    GrView v{W, H, pitch, opitch, false, false, 1};
+    if (pitch == W && (!out || opitch == W)) {
+        v.W = W * H;
+        v.H = 1;
+        v.pitch = v.opitch = v.W;
+    }
+    v.vin = ((uintptr_t)img & 15) == 0 && (v.H == 1 || v.pitch % 4 == 0);
+    v.vout = out && ((uintptr_t)out & 15) == 0 && (v.H == 1 || v.opitch % 4 == 0);
+    // 32-bit group indices while q plus twice the grid's stride stays below 2^32
+    const bool small = ((v.W + 3) >> 2) * v.H < (int64_t(1) << 31);
+    v.mode = !small ? 2 : (v.H == 1 ? 0 : 1);
+    return v;
 }
 
-static bool gr_small(int64_t W, int64_t H) {
-    // 32-bit group indices: q plus the grid's stride stays below 2^32
-    return ((W + 3) >> 2) * H < (int64_t(1) << 31);
+template <int MODE, int FORM>
+int launch_gray_f(const float* img, const GrView& v, float lo, float inv, float a, float ka, float* out,
+                  cudaStream_t s) {
+    k_gray<MODE, FORM><<<v.grid(8), GR_T, 0, s>>>(img, v.W, v.H, v.pitch, v.vin, lo, inv, a, ka, out, v.opitch,
+                                                   v.vout);
+    return ipp_check_launch("k_gray");
 }
+
+template <int MODE>
+int launch_gray_m(const float* img, const GrView& v, int form, float lo, float inv, float a, float ka, float* out,
+                  cudaStream_t s) {
+    switch (form) {
+        case GR_LOG_FAST: return launch_gray_f<MODE, GR_LOG_FAST>(img, v, lo, inv, a, ka, out, s);
+        case GR_POWER_FAST: return launch_gray_f<MODE, GR_POWER_FAST>(img, v, lo, inv, a, ka, out, s);
+        case GR_EXP_FAST: return launch_gray_f<MODE, GR_EXP_FAST>(img, v, lo, inv, a, ka, out, s);
+        case GR_LOG1P: return launch_gray_f<MODE, GR_LOG1P>(img, v, lo, inv, a, ka, out, s);
+        case GR_EXPM1: return launch_gray_f<MODE, GR_EXPM1>(img, v, lo, inv, a, ka, out, s);
+        default: return launch_gray_f<MODE, GR_LINEAR>(img, v, lo, inv, a, ka, out, s);
+    }
+}
+
+template <int MODE>
+int launch_equalize_m(const float* img, const GrView& v, int nbins, GrayWs w, float* out, cudaStream_t s) {
+    const size_t hs = (size_t)nbins * 4;
+    // 8 resident blocks per SM while their histograms fit beside each other
+    const int per_sm = hs <= 24 * 1024 ? 8 : (hs <= 48 * 1024 ? 4 : 3);
+    k_minmax<MODE><<<v.grid(8), GR_T, 0, s>>>(img, v.W, v.H, v.pitch, v.vin, w);
+    if (int e = ipp_check_launch("k_minmax")) return e;
+    cudaFuncSetAttribute(k_hist<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs);
+    k_hist<MODE><<<v.grid(per_sm), GR_T, hs, s>>>(img, v.W, v.H, v.pitch, v.vin, nbins, w);
+    if (int e = ipp_check_launch("k_hist")) return e;
+    k_cdf<<<(unsigned)((nbins + GR_T - 1) / GR_T), GR_T, 0, s>>>(nbins, w);
+    if (int e = ipp_check_launch("k_cdf")) return e;
+    k_equalize<MODE><<<v.grid(8), GR_T, 0, s>>>(img, v.W, v.H, v.pitch, v.vin, nbins, w, out, v.opitch, v.vout);
+    return ipp_check_launch("k_equalize");
+}
+
+}  // namespace
 
 int ipp_launch_gray(const float* img, int64_t W, int64_t H, int64_t pitch, int kind, float lo, float hi, float a,
                     float* out, int64_t opitch, cudaStream_t s) {
     const float inv = (float)(1.0 / ((double)hi - (double)lo));
     float ap = a, ka = 1.f;
-    if (kind == IPP_GRAY_LOG) ka = (float)(1.0 / log1p((double)a));
-    if (kind == IPP_GRAY_EXP) {
-        ap = (float)log((double)a);
+    int form = GR_LINEAR;
+    if (kind == IPP_GRAY_LOG) {
+        form = a >= 1.f ? GR_LOG_FAST : GR_LOG1P;
+        ka = (float)(form == GR_LOG_FAST ? 1.0 / log2(1.0 + (double)a) : 1.0 / log1p((double)a));
+    } else if (kind == IPP_GRAY_POWER) {
+        form = GR_POWER_FAST;
+    } else if (kind == IPP_GRAY_EXP) {
+        form = a >= 2.f ? GR_EXP_FAST : GR_EXPM1;
+        ap = (float)(form == GR_EXP_FAST ? log2((double)a) : log((double)a));
         ka = (float)(1.0 / ((double)a - 1.0));
     }
-    const unsigned g = gr_grid(W, H, 8);
-    if (gr_small(W, H))
-        k_gray<uint32_t><<<g, GR_T, 0, s>>>(img, W, H, pitch, kind, lo, inv, ap, ka, out, opitch);
-    else
-        k_gray<uint64_t><<<g, GR_T, 0, s>>>(img, W, H, pitch, kind, lo, inv, ap, ka, out, opitch);
-    return ipp_check_launch("k_gray");
+    const GrView v = gr_view(img, W, H, pitch, out, opitch);
+    if (v.mode == 0) return launch_gray_m<0>(img, v, form, lo, inv, ap, ka, out, s);
+    if (v.mode == 1) return launch_gray_m<1>(img, v, form, lo, inv, ap, ka, out, s);
+    return launch_gray_m<2>(img, v, form, lo, inv, ap, ka, out, s);
 }
 
 size_t ipp_equalize_ws_bytes(int nbins) {
-    return 256 + (((size_t)nbins * 4 + 255) & ~(size_t)255) * 2;
+    const size_t nb = ((size_t)nbins * 4 + 255) & ~(size_t)255;
+    return 256 + nb * 4;   // header, counts, C, (C, dC) pairs
 }
 
 int ipp_launch_equalize(const float* img, int64_t W, int64_t H, int64_t pitch, int nbins, float* out,
@@ -268,32 +375,16 @@ int ipp_launch_equalize(const float* img, int64_t W, int64_t H, int64_t pitch, i
     GrayWs w;
     char* b = (char*)ws;
     const size_t nb = ((size_t)nbins * 4 + 255) & ~(size_t)255;
-    w.kmin = (uint32_t*)b;
-    w.kmax = (uint32_t*)(b + 4);
-    w.nfin = (unsigned long long*)(b + 8);
+    w.kminc = (uint32_t*)b;
+    w.kmax = (uint32_t*)(b + 64);
+    w.nfin = (unsigned long long*)(b + 128);
     w.cnt = (uint32_t*)(b + 256);
     w.cdf = (float*)(b + 256 + nb);
-    if (cudaMemsetAsync(b, 0xff, 4, s) != cudaSuccess || cudaMemsetAsync(b + 4, 0, 12, s) != cudaSuccess ||
-        cudaMemsetAsync(w.cnt, 0, (size_t)nbins * 4, s) != cudaSuccess)
+    w.seg = (float2*)(b + 256 + 2 * nb);
+    if (cudaMemsetAsync(b, 0, 256 + (size_t)nbins * 4, s) != cudaSuccess)
         return ipp_check_launch("equalize workspace memset");
-    const bool sm = gr_small(W, H);
-    const unsigned g = gr_grid(W, H, 8), gh = gr_grid(W, H, 4);
-    const size_t hs = (size_t)nbins * 4;
-    if (sm) {
-        k_minmax<uint32_t><<<g, GR_T, 0, s>>>(img, W, H, pitch, w);
-        cudaFuncSetAttribute(k_hist<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs);
-        k_hist<uint32_t><<<gh, GR_T, hs, s>>>(img, W, H, pitch, nbins, w);
-    } else {
-        k_minmax<uint64_t><<<g, GR_T, 0, s>>>(img, W, H, pitch, w);
-        cudaFuncSetAttribute(k_hist<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs);
-        k_hist<uint64_t><<<gh, GR_T, hs, s>>>(img, W, H, pitch, nbins, w);
-    }
-    if (int e = ipp_check_launch("k_minmax/k_hist")) return e;
-    k_cdf<<<1, 1024, 0, s>>>(nbins, w);
-    if (int e = ipp_check_launch("k_cdf")) return e;
-    if (sm)
-        k_equalize<uint32_t><<<g, GR_T, 0, s>>>(img, W, H, pitch, nbins, w, out, opitch);
-    else
-        k_equalize<uint64_t><<<g, GR_T, 0, s>>>(img, W, H, pitch, nbins, w, out, opitch);
-    return ipp_check_launch("k_equalize");
+    const GrView v = gr_view(img, W, H, pitch, out, opitch);
+    if (v.mode == 0) return launch_equalize_m<0>(img, v, nbins, w, out, s);
+    if (v.mode == 1) return launch_equalize_m<1>(img, v, nbins, w, out, s);
+    return launch_equalize_m<2>(img, v, nbins, w, out, s);
 }
