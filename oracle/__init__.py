@@ -49,6 +49,26 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class Wcs(C.Structure):
+    _fields_ = [("crpix", C.c_double * 2), ("crval", C.c_double * 2), ("cd", C.c_double * 4),
+                ("a_order", C.c_int32), ("b_order", C.c_int32),
+                ("a", C.c_double * 36), ("b", C.c_double * 36)]
+
+
+def _wcs(w):
+    """dict(crpix, crval, cd (2x2), a, b (6x6 arrays, a[p][q] of u^p v^q), a_order,
+    b_order) -> the oracle's struct"""
+    s = Wcs()
+    s.crpix[:] = [float(v) for v in w["crpix"]]
+    s.crval[:] = [float(v) for v in w["crval"]]
+    s.cd[:] = [float(v) for v in np.asarray(w["cd"], np.float64).ravel()]
+    for key in ("a", "b"):
+        c = np.zeros((6, 6)) if w.get(key) is None else np.asarray(w[key], np.float64)
+        getattr(s, key)[:] = [float(v) for v in c.ravel()]
+        setattr(s, key + "_order", int(w.get(key + "_order", 0)))
+    return s
+
+
 class BgParams(C.Structure):
     _fields_ = [("mesh_w", C.c_int32), ("mesh_h", C.c_int32),
                 ("filter_w", C.c_int32), ("filter_h", C.c_int32),
@@ -89,6 +109,11 @@ def lib():
             L.orc_deblend.argtypes = [vp, vp, i64, i64, i64, i32, d, vp]
             L.orc_gray_transform.argtypes = [vp, i64, i64, i32, d, d, d, vp]
             L.orc_hist_equalize.argtypes = [vp, i64, i64, i32, vp]
+            L.orc_wcs_pix2world.argtypes = [C.POINTER(Wcs), vp, vp, i64, vp, vp]
+            L.orc_wcs_world2pix.argtypes = [C.POINTER(Wcs), vp, vp, i64, vp, vp]
+            L.orc_wcs_map.argtypes = [C.POINTER(Wcs), C.POINTER(Wcs), i64, i64, i32, vp, vp]
+            L.orc_affine_fit.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+            L.orc_reproject_affine.argtypes = [vp, i64, i64, vp, i64, i64, d, vp]
             L.orc_deblend.restype = i64
             L.orc_psf_model.argtypes = [vp, i32, i32, d, vp, vp]
             L.orc_psf_fit.argtypes = [vp, i64, i32, vp, vp, i32, d, i32, d, vp, vp, vp, vp]
@@ -349,3 +374,53 @@ def catalog(img, mesh=64, filter_size=3, k=1.5, min_area=5, fwhm_win=3.0,
     ph = aperture(sub, x.astype(np.float32), y.astype(np.float32), r_ap, r_in, r_out)
     return dict(bkg=bkg, rms=rms, mesh_stats=st, sub=sub, mask=m, labels=labels, K=K,
                 stats=stats, x=x, y=y, cen_iter=it, cen_flags=cfl, **ph)
+
+
+def wcs_pix2world(w, x, y):
+    """0-based pixel positions -> (RA, Dec) in degrees (Eqs. 1-3)."""
+    x = np.ascontiguousarray(x, np.float64).ravel()
+    y = np.ascontiguousarray(y, np.float64).ravel()
+    ra, de = np.zeros_like(x), np.zeros_like(x)
+    s = _wcs(w)
+    assert lib().orc_wcs_pix2world(C.byref(s), _p(x), _p(y), x.size, _p(ra), _p(de)) == 0
+    return ra, de
+
+
+def wcs_world2pix(w, ra, dec):
+    """(RA, Dec) in degrees -> 0-based pixel positions (inverse chain)."""
+    ra = np.ascontiguousarray(ra, np.float64).ravel()
+    de = np.ascontiguousarray(dec, np.float64).ravel()
+    x, y = np.zeros_like(ra), np.zeros_like(ra)
+    s = _wcs(w)
+    assert lib().orc_wcs_world2pix(C.byref(s), _p(ra), _p(de), ra.size, _p(x), _p(y)) == 0
+    return x, y
+
+
+def wcs_map(src, tgt, W, H, step=1):
+    """target-frame positions of the source node grid (multiples of step)."""
+    nx, ny = (W - 1) // step + 1, (H - 1) // step + 1
+    xo, yo = np.zeros((ny, nx)), np.zeros((ny, nx))
+    a, b = _wcs(src), _wcs(tgt)
+    assert lib().orc_wcs_map(C.byref(a), C.byref(b), W, H, int(step), _p(xo), _p(yo)) == 0
+    return xo, yo
+
+
+def affine_fit(x, y, xt, yt):
+    """partial affine least squares (x, y) -> (xt, yt): (M, Minv), 2x3 each."""
+    x, y, xt, yt = (np.ascontiguousarray(v, np.float64).ravel() for v in (x, y, xt, yt))
+    M, Mi = np.zeros(6), np.zeros(6)
+    e = lib().orc_affine_fit(_p(x), _p(y), _p(xt), _p(yt), x.size, _p(M), _p(Mi))
+    if e:
+        raise ValueError("affine fit needs two distinct finite points")
+    return M.reshape(2, 3), Mi.reshape(2, 3)
+
+
+def reproject_affine(src, Minv, Wo, Ho, fill=0.0):
+    """bilinear reprojection of src onto a Wo x Ho frame through Minv (output
+    pixel -> source position)."""
+    src = _f32(src)
+    H, W = src.shape
+    Mi = np.ascontiguousarray(Minv, np.float64).ravel()
+    out = np.zeros((Ho, Wo))
+    assert lib().orc_reproject_affine(_p(src), W, H, _p(Mi), Wo, Ho, float(fill), _p(out)) == 0
+    return out

@@ -1239,3 +1239,191 @@ int orc_psf_fit(const float* stamps, int64_t N, int32_t S, const float* weights,
     free(m); free(J);
     return ORC_OK;
 }
+
+/* ---------------------------------------------------------------------------
+ * Image alignment (Sec. 2.2.3): pixel -> sky -> pixel coordinate mapping
+ * (Eqs. 1-3 and their inverses), the partial affine (similarity) estimate, and
+ * bilinear reprojection.  Readings:
+ *   pixel (column j, row i), 0-based, is FITS pixel (j + 1, i + 1);
+ *   Eq. 1 is the SIP distortion applied to the offsets from the reference pixel,
+ *     u = x - CRPIX1, v = y - CRPIX2:  xi = u + sum A_pq u^p v^q,
+ *     eta = v + sum B_pq u^p v^q  (p + q <= order, every given term);
+ *   Eq. 2 maps (xi, eta) through CD (degrees per pixel) to the standard
+ *     coordinates (in radians below);
+ *   Eq. 3 is the gnomonic (TAN) deprojection about (CRVAL1, CRVAL2);
+ *   the inverse chain inverts Eq. 3 (the gnomonic projection about the target's
+ *   CRVAL; points at or beyond 90 degrees from it have no image: NaN), Eq. 2
+ *   (CD^-1) and Eq. 1 (Newton's method from (xi, eta), at most 50 steps, until
+ *   the step is below 1e-12 px; not converged: NaN).
+ * ------------------------------------------------------------------------- */
+static const double ORC_D2R = M_PI / 180.0;
+
+static void sip_eval(const double* c, int order, double u, double v, double* val, double* du, double* dv) {
+    /* sum c[p*6+q] u^p v^q over p + q <= order, and its partial derivatives */
+    double s = 0.0, su = 0.0, sv = 0.0;
+    for (int p = 0; p <= order; p++) {
+        for (int q = 0; q <= order - p; q++) {
+            const double k = c[p * 6 + q];
+            if (k == 0.0) continue;
+            s += k * pow(u, p) * pow(v, q);
+            if (p > 0) su += k * p * pow(u, p - 1) * pow(v, q);
+            if (q > 0) sv += k * q * pow(u, p) * pow(v, q - 1);
+        }
+    }
+    *val = s;
+    if (du) *du = su;
+    if (dv) *dv = sv;
+}
+
+int orc_wcs_pix2world(const orc_wcs* w, const double* x, const double* y, int64_t n, double* ra, double* dec) {
+    const double a0 = w->crval[0] * ORC_D2R, d0 = w->crval[1] * ORC_D2R;
+    for (int64_t k = 0; k < n; k++) {
+        const double u = x[k] + 1.0 - w->crpix[0], v = y[k] + 1.0 - w->crpix[1];
+        double f, g;
+        sip_eval(w->a, w->a_order, u, v, &f, NULL, NULL);
+        sip_eval(w->b, w->b_order, u, v, &g, NULL, NULL);
+        const double xi = u + f, eta = v + g;                                   /* Eq. 1 */
+        const double p = (w->cd[0] * xi + w->cd[1] * eta) * ORC_D2R;           /* Eq. 2 */
+        const double q = (w->cd[2] * xi + w->cd[3] * eta) * ORC_D2R;
+        const double den = cos(d0) - q * sin(d0);                               /* Eq. 3 */
+        double al = a0 + atan2(p, den);
+        al = fmod(al, 2.0 * M_PI);
+        if (al < 0.0) al += 2.0 * M_PI;
+        ra[k] = al / ORC_D2R;
+        dec[k] = atan2(q * cos(d0) + sin(d0), sqrt(p * p + den * den)) / ORC_D2R;
+    }
+    return ORC_OK;
+}
+
+int orc_wcs_world2pix(const orc_wcs* w, const double* ra, const double* dec, int64_t n, double* x, double* y) {
+    const double a0 = w->crval[0] * ORC_D2R, d0 = w->crval[1] * ORC_D2R;
+    const double det = w->cd[0] * w->cd[3] - w->cd[1] * w->cd[2];
+    if (det == 0.0) return ORC_INVALID_ARG;
+    for (int64_t k = 0; k < n; k++) {
+        const double al = ra[k] * ORC_D2R, de = dec[k] * ORC_D2R;
+        /* inverse of Eq. 3: gnomonic projection about (a0, d0) */
+        const double cc = sin(d0) * sin(de) + cos(d0) * cos(de) * cos(al - a0);
+        if (!(cc > 0.0)) { x[k] = NAN; y[k] = NAN; continue; }
+        const double p = cos(de) * sin(al - a0) / cc / ORC_D2R;
+        const double q = (cos(d0) * sin(de) - sin(d0) * cos(de) * cos(al - a0)) / cc / ORC_D2R;
+        /* inverse of Eq. 2 */
+        const double xi = (w->cd[3] * p - w->cd[1] * q) / det;
+        const double eta = (-w->cd[2] * p + w->cd[0] * q) / det;
+        /* inverse of Eq. 1: Newton on (u + f(u, v) - xi, v + g(u, v) - eta) */
+        double u = xi, v = eta;
+        int ok = 0;
+        for (int it = 0; it < 50; it++) {
+            double f, fu, fv, g, gu, gv;
+            sip_eval(w->a, w->a_order, u, v, &f, &fu, &fv);
+            sip_eval(w->b, w->b_order, u, v, &g, &gu, &gv);
+            const double r1 = u + f - xi, r2 = v + g - eta;
+            const double j11 = 1.0 + fu, j12 = fv, j21 = gu, j22 = 1.0 + gv;
+            const double dj = j11 * j22 - j12 * j21;
+            if (dj == 0.0) break;
+            const double su = (j22 * r1 - j12 * r2) / dj, sv = (-j21 * r1 + j11 * r2) / dj;
+            u -= su;
+            v -= sv;
+            if (fabs(su) < 1e-12 && fabs(sv) < 1e-12) { ok = 1; break; }
+        }
+        if (!ok) { x[k] = NAN; y[k] = NAN; continue; }
+        x[k] = u + w->crpix[0] - 1.0;
+        y[k] = v + w->crpix[1] - 1.0;
+    }
+    return ORC_OK;
+}
+
+/* Source pixel -> target pixel on the node grid (j step, i step), j step <= W - 1,
+ * i step <= H - 1 (the paper maps every pixel: step 1).  Row-major nodes. */
+int orc_wcs_map(const orc_wcs* src, const orc_wcs* tgt, int64_t W, int64_t H, int32_t step, double* xo,
+                double* yo) {
+    if (step < 1 || W < 1 || H < 1) return ORC_INVALID_ARG;
+    const int64_t nx = (W - 1) / step + 1, ny = (H - 1) / step + 1;
+    for (int64_t i = 0; i < ny; i++) {
+        for (int64_t j = 0; j < nx; j++) {
+            const double x = (double)(j * step), y = (double)(i * step);
+            double ra, de;
+            orc_wcs_pix2world(src, &x, &y, 1, &ra, &de);
+            int e = orc_wcs_world2pix(tgt, &ra, &de, 1, &xo[i * nx + j], &yo[i * nx + j]);
+            if (e) return e;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Partial affine (similarity: rotation, one scale, translation) least-squares
+ * estimate from point pairs (x, y) -> (xt, yt), the model of the OpenCV routine
+ * the paper names (read without its outlier rejection: correspondences from a
+ * WCS mapping have no outliers).  Closed form about the centroids:
+ *   a = s cos t = sum(dx dxt + dy dyt) / sum(dx^2 + dy^2),
+ *   b = s sin t = sum(dx dyt - dy dxt) / sum(dx^2 + dy^2),
+ *   M = [a -b tx; b a ty], (tx, ty) = centroid_t - [a -b; b a] centroid.
+ * Pairs with a non-finite member are skipped.  Minv is the inverse map.
+ * Returns INVALID_ARG with fewer than two distinct points. */
+int orc_affine_fit(const double* x, const double* y, const double* xt, const double* yt, int64_t n, double* M,
+                   double* Minv) {
+    double sx = 0, sy = 0, stx = 0, sty = 0;
+    int64_t m = 0;
+    for (int64_t k = 0; k < n; k++) {
+        if (!isfinite(x[k]) || !isfinite(y[k]) || !isfinite(xt[k]) || !isfinite(yt[k])) continue;
+        sx += x[k]; sy += y[k]; stx += xt[k]; sty += yt[k];
+        m++;
+    }
+    if (m < 2) return ORC_INVALID_ARG;
+    const double cx = sx / m, cy = sy / m, ctx = stx / m, cty = sty / m;
+    double saa = 0, sa = 0, sb = 0;
+    for (int64_t k = 0; k < n; k++) {
+        if (!isfinite(x[k]) || !isfinite(y[k]) || !isfinite(xt[k]) || !isfinite(yt[k])) continue;
+        const double dx = x[k] - cx, dy = y[k] - cy, ex = xt[k] - ctx, ey = yt[k] - cty;
+        saa += dx * dx + dy * dy;
+        sa += dx * ex + dy * ey;
+        sb += dx * ey - dy * ex;
+    }
+    if (!(saa > 0.0)) return ORC_INVALID_ARG;
+    const double a = sa / saa, b = sb / saa;
+    M[0] = a; M[1] = -b; M[2] = ctx - (a * cx - b * cy);
+    M[3] = b; M[4] = a;  M[5] = cty - (b * cx + a * cy);
+    const double s2 = a * a + b * b;
+    if (!(s2 > 0.0)) return ORC_INVALID_ARG;
+    /* inverse of [a -b; b a] is [a b; -b a] / s2 */
+    Minv[0] = a / s2;  Minv[1] = b / s2;  Minv[2] = -(Minv[0] * M[2] + Minv[1] * M[5]);
+    Minv[3] = -b / s2; Minv[4] = a / s2;  Minv[5] = -(Minv[3] * M[2] + Minv[4] * M[5]);
+    return ORC_OK;
+}
+
+/* Reprojection (Sec. 2.2.3): output pixel (j, i) of a Wo x Ho frame takes the
+ * source value at (x, y) = Minv (j, i, 1), by bilinear interpolation between the
+ * four surrounding pixel centres.  Defined on 0 <= x <= W - 1, 0 <= y <= H - 1
+ * (at x = W - 1 the right-hand pair has weight 0 and is not read); elsewhere, or
+ * when a weighted neighbour is not finite, the output is `fill`. */
+int orc_reproject_affine(const float* src, int64_t W, int64_t H, const double* Minv, int64_t Wo, int64_t Ho,
+                         double fill, double* out) {
+    for (int64_t i = 0; i < Ho; i++) {
+        for (int64_t j = 0; j < Wo; j++) {
+            const double x = Minv[0] * j + Minv[1] * i + Minv[2];
+            const double y = Minv[3] * j + Minv[4] * i + Minv[5];
+            double r = fill;
+            if (x >= 0.0 && x <= (double)(W - 1) && y >= 0.0 && y <= (double)(H - 1)) {
+                int64_t x0 = (int64_t)floor(x), y0 = (int64_t)floor(y);
+                if (x0 > W - 2) x0 = W - 2 < 0 ? 0 : W - 2;
+                if (y0 > H - 2) y0 = H - 2 < 0 ? 0 : H - 2;
+                const double t = x - x0, s = y - y0;
+                double acc = 0.0;
+                int bad = 0;
+                for (int dy = 0; dy <= 1; dy++) {
+                    for (int dx = 0; dx <= 1; dx++) {
+                        const double wgt = (dx ? t : 1.0 - t) * (dy ? s : 1.0 - s);
+                        if (wgt == 0.0) continue;
+                        const int64_t xx = x0 + dx, yy = y0 + dy;
+                        if (xx >= W || yy >= H) { bad = 1; continue; }
+                        const double v = (double)src[yy * W + xx];
+                        if (!isfinite(v)) bad = 1;
+                        acc += wgt * v;
+                    }
+                }
+                r = bad ? fill : acc;
+            }
+            out[i * Wo + j] = r;
+        }
+    }
+    return ORC_OK;
+}

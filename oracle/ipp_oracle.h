@@ -102,6 +102,24 @@ int orc_gray_transform(const float* img, int64_t W, int64_t H, int32_t kind, dou
                        double a, double* out);
 int orc_hist_equalize(const float* img, int64_t W, int64_t H, int32_t nbins, double* out);
 
+/* Image alignment (Sec. 2.2.3, Eqs. 1-3).  SIP coefficient a[p*6+q] multiplies
+ * u^p v^q, p + q <= order <= 5; crpix 1-based; crval and cd in degrees. */
+typedef struct {
+    double crpix[2];
+    double crval[2];
+    double cd[4];       /* CD1_1, CD1_2, CD2_1, CD2_2 */
+    int32_t a_order, b_order;
+    double a[36], b[36];
+} orc_wcs;
+int orc_wcs_pix2world(const orc_wcs* w, const double* x, const double* y, int64_t n, double* ra, double* dec);
+int orc_wcs_world2pix(const orc_wcs* w, const double* ra, const double* dec, int64_t n, double* x, double* y);
+int orc_wcs_map(const orc_wcs* src, const orc_wcs* tgt, int64_t W, int64_t H, int32_t step, double* xo,
+                double* yo);
+int orc_affine_fit(const double* x, const double* y, const double* xt, const double* yt, int64_t n, double* M,
+                   double* Minv);
+int orc_reproject_affine(const float* src, int64_t W, int64_t H, const double* Minv, int64_t Wo, int64_t Ho,
+                         double fill, double* out);
+
 /* Deblending (Sec. 2.2.4): multi-level thresholds, sub-component tree, pruning
  * on intensity (mincont), remaining pixels to the likeliest object; objects
  * numbered candidate by candidate, within one in raster order of their first
