@@ -56,6 +56,7 @@ extern "C" {
 #define IPP_ERR_NO_VALID_MESH 4 /* device status: no mesh had enough usable pixels */
 #define IPP_ERR_TIMEOUT 5       /* device status: a bounded device-side wait ran out */
 #define IPP_ERR_NOT_SUPPORTED 6 /* valid request outside what this build implements */
+#define IPP_ERR_DEGENERATE 7    /* device status: too few usable points (ipp_affine_fit) */
 
 /* image element types */
 #define IPP_F32 0
@@ -77,6 +78,18 @@ extern "C" {
 #define IPP_EST_FACTORS 3 /* Eq. 4, read as median_factor * median - mean_factor * mean */
 
 /* PSF models */
+/* World coordinate system of a frame (Sec. 2.2.3, Eqs. 1-3): SIP distortion,
+ * CD matrix and gnomonic (TAN) projection. */
+typedef struct {
+    double crpix[2];     /* reference pixel, FITS 1-based (0-based pixel j is FITS j + 1) */
+    double crval[2];     /* RA, Dec of the reference pixel, degrees */
+    double cd[4];        /* CD1_1, CD1_2, CD2_1, CD2_2, degrees per pixel */
+    int32_t a_order;     /* SIP orders 0..5 (0: no distortion) */
+    int32_t b_order;
+    double a[36];        /* a[p*6 + q]: coefficient of u^p v^q in xi, p + q <= a_order */
+    double b[36];        /* likewise in eta */
+} ipp_wcs;
+
 /* Gray-scale functions of ipp_gray_transform (Sec. 2.2.6). */
 #define IPP_GRAY_LINEAR 0
 #define IPP_GRAY_LOG 1
@@ -402,6 +415,70 @@ int ipp_gray_transform(const float* img, int64_t W, int64_t H, int64_t pitch, in
 size_t ipp_hist_equalize_workspace_size(int32_t nbins);
 int ipp_hist_equalize(const float* img, int64_t W, int64_t H, int64_t pitch, int32_t nbins, float* out,
                       int64_t out_pitch, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ipp_wcs_map -- coordinate mapping of Sec. 2.2.3: source pixel -> sky -> target
+ * pixel, through Eq. 1 (SIP, on the offsets u = x - CRPIX1, v = y - CRPIX2 of
+ * the FITS pixel position), Eq. 2 (CD) and Eq. 3 (gnomonic deprojection about
+ * the source's CRVAL), then the inverse chain of the target: gnomonic projection
+ * about its CRVAL, CD^-1, and the inverse of its SIP polynomial by Newton's
+ * method (at most 50 steps, until the step is below 1e-12 px).  FP64.
+ * Node (j, i) of the grid is source pixel (j step, i step), 0 <= j < nx =
+ * (W - 1) / step + 1, 0 <= i < ny = (H - 1) / step + 1; step 1 maps every pixel
+ * (the paper's thread per pixel; FP64-bound, about 300 FP64 operations a node).
+ *   x_out, y_out  device double[ny * nx], row-major: the 0-based target pixel
+ *                 position of each node; NaN where the sky point is 90 degrees or
+ *                 more from the target's tangent point or Newton does not converge
+ * Errors: INVALID_ARG for NULL pointers, W, H or step < 1, a SIP order outside
+ * 0..5, non-finite WCS values or a singular target CD.
+ */
+int ipp_wcs_map(const ipp_wcs* src, const ipp_wcs* tgt, int64_t W, int64_t H, int32_t step, double* x_out,
+                double* y_out, void* stream);
+
+/*
+ * ipp_affine_fit -- the partial affine estimate of Sec. 2.2.3 (rotation, one
+ * scale and a translation, the model of OpenCV's estimateAffinePartial2D that
+ * the paper uses), as the least-squares similarity of point pairs
+ * (x, y) -> (xt, yt) in closed form about the centroids: a = s cos t and
+ * b = s sin t are the centred cross sums over the centred source norm.  No
+ * outlier rejection (pairs from a WCS mapping have no outliers); pairs with a
+ * non-finite member are skipped.  FP64, deterministic (fixed reduction order).
+ *   x, y      device double[n], or both NULL: then pair k's source point is the
+ *             grid node ((k % grid_nx) grid_step, (k / grid_nx) grid_step) of
+ *             ipp_wcs_map
+ *   xt, yt    device double[n]
+ *   M_out     device double[12]: M = [a -b tx; b a ty] (source -> target), then
+ *             its inverse (target -> source), each 2 x 3 row-major
+ *   status_dev nullable device int32: IPP_OK, or IPP_ERR_DEGENERATE (fewer than
+ *             two distinct usable pairs; M_out is then NaN)
+ *   ws        device workspace of ipp_affine_fit_workspace_size() bytes,
+ *             8-byte aligned
+ * Errors: INVALID_ARG for NULL pointers, n < 0, or grid_nx / grid_step < 1 when
+ * x, y are NULL.
+ */
+size_t ipp_affine_fit_workspace_size(void);
+int ipp_affine_fit(const double* x, const double* y, const double* xt, const double* yt, int64_t n,
+                   int64_t grid_nx, int32_t grid_step, double* M_out, int32_t* status_dev, void* ws,
+                   size_t ws_bytes, void* stream);
+
+/*
+ * ipp_reproject_affine -- image reprojection of Sec. 2.2.3: output pixel (j, i)
+ * of a Wo x Ho frame is the source value at (x, y) = Minv (j, i, 1) by bilinear
+ * interpolation between the four surrounding pixel centres.  Defined for
+ * 0 <= x <= W - 1 and 0 <= y <= H - 1 (on the last column or row the pair
+ * beyond has weight 0 and is not read); elsewhere, or when a neighbour with
+ * non-zero weight is not finite, the output is `fill`.  The position is formed
+ * in double-float arithmetic once per 128 output pixels and offset in FP32
+ * (error near 1e-5 px); the interpolation is FP32.  Wo, Ho < 2^24.
+ *   src       device float, rows of `pitch` elements
+ *   Minv_dev  device double[6] (2 x 3 row-major), e.g. M_out + 6 of ipp_affine_fit,
+ *             read by the kernel: no host synchronisation between fit and warp
+ *   out       device float, rows of `out_pitch` (>= Wo); must not alias src
+ * Errors: INVALID_ARG for NULL pointers, bad sizes or pitches, Wo or Ho >= 2^24,
+ * or out == src.
+ */
+int ipp_reproject_affine(const float* src, int64_t W, int64_t H, int64_t pitch, const double* Minv_dev, int64_t Wo,
+                         int64_t Ho, float fill, float* out, int64_t out_pitch, void* stream);
 
 /*
  * ipp_stamp_cut -- S x S stamps of the subtracted frame around each source, the

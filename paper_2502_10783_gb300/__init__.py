@@ -11,10 +11,10 @@ raises when a call returns an error status.  There is no CPU fallback.
 """
 from __future__ import annotations
 
+import ctypes as C
 from dataclasses import dataclass
 
-import ctypes as C
-
+import numpy as np
 import torch
 
 from . import _abi
@@ -25,7 +25,7 @@ from ._abi import (  # noqa: F401
 )
 
 __all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "deblend", "stamp_cut", "Batch",
-           "gray_transform", "hist_equalize",
+           "gray_transform", "hist_equalize", "wcs_map", "affine_fit", "reproject_affine", "align",
            "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
 
 
@@ -296,6 +296,86 @@ def hist_equalize(img, nbins=4096, out=None, ws=None):
     _abi.check("ipp_hist_equalize", L.ipp_hist_equalize(
         _ptr(img), W, H, img.stride(0), int(nbins), _ptr(out), out.stride(0), _ptr(ws), ws.numel(), _stream()))
     return out, ws
+
+
+def _wcs(w):
+    """dict(crpix, crval, cd (2 x 2), a, b (6 x 6, a[p][q] of u^p v^q), a_order,
+    b_order) -> the ABI struct"""
+    s = _abi.Wcs()
+    s.crpix[:] = [float(v) for v in w["crpix"]]
+    s.crval[:] = [float(v) for v in w["crval"]]
+    s.cd[:] = [float(v) for v in np.asarray(w["cd"], np.float64).ravel()]
+    for key in ("a", "b"):
+        c = np.zeros((6, 6)) if w.get(key) is None else np.asarray(w[key], np.float64)
+        getattr(s, key)[:] = [float(v) for v in c.ravel()]
+        setattr(s, key + "_order", int(w.get(key + "_order", 0)))
+    return s
+
+
+def wcs_map(src_wcs, tgt_wcs, W, H, step=1, device="cuda"):
+    """Target-frame pixel positions (x, y) of the source node grid (multiples of
+    `step`) through both frames' WCS (ipp_wcs_map); float64 (ny, nx) each."""
+    L = load()
+    nx, ny = (W - 1) // step + 1, (H - 1) // step + 1
+    xo = torch.empty((ny, nx), dtype=torch.float64, device=device)
+    yo = torch.empty_like(xo)
+    a, b = _wcs(src_wcs), _wcs(tgt_wcs)
+    _abi.check("ipp_wcs_map", L.ipp_wcs_map(C.byref(a), C.byref(b), W, H, int(step), _ptr(xo), _ptr(yo),
+                                            _stream()))
+    return xo, yo
+
+
+def affine_fit(xt, yt, x=None, y=None, grid_step=None, ws=None):
+    """Partial affine (similarity) least squares of (x, y) -> (xt, yt)
+    (ipp_affine_fit).  Without x, y the source points are the node grid of
+    wcs_map: xt, yt of shape (ny, nx) and `grid_step`.  Returns the device
+    float64 [12] (M, then its inverse, 2 x 3 each) and the device status."""
+    L = load()
+    _need_cuda(xt, "xt", torch.float64)
+    _need_cuda(yt, "yt", torch.float64)
+    dev = xt.device
+    n = xt.numel()
+    gnx = xt.shape[-1] if x is None else 1
+    need = L.ipp_affine_fit_workspace_size()
+    if ws is None or ws.numel() * ws.element_size() < need:
+        ws = torch.empty((need + 7) // 8, dtype=torch.float64, device=dev)
+    M = torch.empty(12, dtype=torch.float64, device=dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    xc = None if x is None else x.contiguous()
+    yc = None if y is None else y.contiguous()
+    _abi.check("ipp_affine_fit", L.ipp_affine_fit(
+        _ptr(xc), _ptr(yc), _ptr(xt.contiguous()), _ptr(yt.contiguous()), n, gnx, int(grid_step or 1), _ptr(M),
+        _ptr(st), _ptr(ws), ws.numel() * ws.element_size(), _stream()))
+    return M, st
+
+
+def reproject_affine(src, Minv, Wo, Ho, fill=0.0, out=None):
+    """Bilinear reprojection of `src` onto a Wo x Ho frame: output pixel (j, i)
+    samples src at Minv (j, i, 1) (ipp_reproject_affine).  Minv: device float64
+    [6] (e.g. affine_fit(...)[0][6:])."""
+    L = load()
+    _frame2d(src, "src")
+    _need_cuda(Minv, "Minv", torch.float64)
+    H, W = src.shape
+    if out is None:
+        out = torch.empty((Ho, Wo), dtype=torch.float32, device=src.device)
+    _frame2d(out, "out")
+    Mi = Minv.contiguous()
+    _abi.check("ipp_reproject_affine", L.ipp_reproject_affine(
+        _ptr(src), W, H, src.stride(0), _ptr(Mi), Wo, Ho, float(fill), _ptr(out), out.stride(0), _stream()))
+    return out
+
+
+def align(src, src_wcs, tgt_wcs, Wo, Ho, step=32, fill=0.0, out=None):
+    """The alignment function of Sec. 2.2.3 on the GPU: map the source node grid
+    into the target frame (wcs_map), estimate the partial affine transform
+    (affine_fit) and reproject the source onto the Wo x Ho target grid
+    (reproject_affine).  Three device calls, no host synchronisation; returns
+    (image, M [12], status)."""
+    H, W = src.shape
+    xo, yo = wcs_map(src_wcs, tgt_wcs, W, H, step=step, device=src.device)
+    M, st = affine_fit(xo, yo, grid_step=step)
+    return reproject_affine(src, M[6:], Wo, Ho, fill=fill, out=out), M, st
 
 
 def stamp_cut(sub, x, y, n_src=None, S=15, max_src=None):

@@ -12,7 +12,7 @@ import threading
 from . import _build
 
 IPP_OK, IPP_ERR_INVALID_ARG, IPP_ERR_CUDA, IPP_ERR_CAPACITY = 0, 1, 2, 3
-IPP_ERR_NO_VALID_MESH, IPP_ERR_TIMEOUT, IPP_ERR_NOT_SUPPORTED = 4, 5, 6
+IPP_ERR_NO_VALID_MESH, IPP_ERR_TIMEOUT, IPP_ERR_NOT_SUPPORTED, IPP_ERR_DEGENERATE = 4, 5, 6, 7
 IPP_F32, IPP_U16 = 0, 1
 FLAG_EDGE, FLAG_WIN_NOT_CONVERGED, FLAG_ANN_FEW = 1, 2, 4
 FLAG_FIT_MAXITER, FLAG_FIT_SINGULAR, FLAG_FIT_BAD_SIGMA = 8, 16, 32
@@ -39,6 +39,11 @@ class CenParams(C.Structure):
 
 class PhotParams(C.Structure):
     _fields_ = [("r_ap", f32), ("r_in", f32), ("r_out", f32), ("min_ann", i32)]
+
+
+class Wcs(C.Structure):
+    _fields_ = [("crpix", f64 * 2), ("crval", f64 * 2), ("cd", f64 * 4), ("a_order", i32), ("b_order", i32),
+                ("a", f64 * 36), ("b", f64 * 36)]
 
 
 class DeblendParams(C.Structure):
@@ -98,6 +103,10 @@ PROTOTYPES = {
                      vp], i32),
     "ipp_auto_phot": ([vp, vp, i64, i64, i64, vp, i32, C.POINTER(SrcStats), C.POINTER(AutoParams), vp, vp, vp,
                        vp, vp, vp], i32),
+    "ipp_wcs_map": ([C.POINTER(Wcs), C.POINTER(Wcs), i64, i64, i32, vp, vp, vp], i32),
+    "ipp_affine_fit_workspace_size": ([], sz),
+    "ipp_affine_fit": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, sz, vp], i32),
+    "ipp_reproject_affine": ([vp, i64, i64, i64, vp, i64, i64, f32, vp, i64, vp], i32),
     "ipp_gray_transform": ([vp, i64, i64, i64, i32, f32, f32, f32, vp, i64, vp], i32),
     "ipp_hist_equalize_workspace_size": ([i32], sz),
     "ipp_hist_equalize": ([vp, i64, i64, i64, i32, vp, i64, vp, sz, vp], i32),

@@ -35,6 +35,7 @@ extern "C" const char* ipp_status_string(int status) {
         case IPP_ERR_NO_VALID_MESH: return "no valid mesh";
         case IPP_ERR_TIMEOUT: return "device wait timed out";
         case IPP_ERR_NOT_SUPPORTED: return "not supported";
+        case IPP_ERR_DEGENERATE: return "too few usable points";
         default: return "unknown status";
     }
 }
@@ -276,6 +277,50 @@ extern "C" int ipp_deblend(const float* sub, const int32_t* labels, int64_t W, i
     J.out = out_labels; J.n_out_dev = n_out_dev;
     ipp_deblend_ws_carve(W, H, max_src, ws, &J.ws);
     return ipp_launch_deblend(J, (cudaStream_t)stream);
+}
+
+// ---- image alignment -------------------------------------------------------------------
+static int check_wcs(const ipp_wcs* w, bool need_inverse) {
+    REQUIRE(w, "wcs NULL");
+    REQUIRE(w->a_order >= 0 && w->a_order <= 5 && w->b_order >= 0 && w->b_order <= 5, "SIP order must be 0..5");
+    for (int k = 0; k < 2; k++) REQUIRE(std::isfinite(w->crpix[k]) && std::isfinite(w->crval[k]), "non-finite WCS");
+    for (int k = 0; k < 4; k++) REQUIRE(std::isfinite(w->cd[k]), "non-finite CD");
+    for (int k = 0; k < 36; k++) REQUIRE(std::isfinite(w->a[k]) && std::isfinite(w->b[k]), "non-finite SIP term");
+    if (need_inverse) REQUIRE(w->cd[0] * w->cd[3] - w->cd[1] * w->cd[2] != 0.0, "singular target CD");
+    return IPP_OK;
+}
+
+extern "C" int ipp_wcs_map(const ipp_wcs* src, const ipp_wcs* tgt, int64_t W, int64_t H, int32_t step,
+                           double* x_out, double* y_out, void* stream) {
+    if (int e = check_wcs(src, false)) return e;
+    if (int e = check_wcs(tgt, true)) return e;
+    REQUIRE(W >= 1 && H >= 1 && step >= 1, "W, H and step must be >= 1");
+    REQUIRE(x_out && y_out, "NULL output");
+    return ipp_launch_wcs_map(*src, *tgt, (W - 1) / step + 1, (H - 1) / step + 1, step, x_out, y_out,
+                              (cudaStream_t)stream);
+}
+
+extern "C" size_t ipp_affine_fit_workspace_size(void) { return ipp_affine_ws_bytes(); }
+
+extern "C" int ipp_affine_fit(const double* x, const double* y, const double* xt, const double* yt, int64_t n,
+                              int64_t grid_nx, int32_t grid_step, double* M_out, int32_t* status_dev, void* ws,
+                              size_t ws_bytes, void* stream) {
+    REQUIRE(xt && yt && M_out && ws, "NULL pointer");
+    REQUIRE((x == nullptr) == (y == nullptr), "x and y must both be given or both be NULL");
+    REQUIRE(n >= 0, "n < 0");
+    if (!x) REQUIRE(grid_nx >= 1 && grid_step >= 1, "grid_nx and grid_step must be >= 1");
+    REQUIRE(((uintptr_t)ws & 7) == 0 && ws_bytes >= ipp_affine_ws_bytes(), "workspace misaligned or too small");
+    return ipp_launch_affine_fit(x, y, xt, yt, n, grid_nx, grid_step, M_out, status_dev, ws, (cudaStream_t)stream);
+}
+
+extern "C" int ipp_reproject_affine(const float* src, int64_t W, int64_t H, int64_t pitch, const double* Minv_dev,
+                                    int64_t Wo, int64_t Ho, float fill, float* out, int64_t out_pitch,
+                                    void* stream) {
+    if (int e = check_frame(src, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(Minv_dev && out, "NULL pointer");
+    REQUIRE(Wo >= 1 && Ho >= 1 && Wo < (1ll << 24) && Ho < (1ll << 24) && out_pitch >= Wo, "bad output size");
+    REQUIRE((const void*)out != (const void*)src, "out must not alias src");
+    return ipp_launch_reproject(src, W, H, pitch, Minv_dev, Wo, Ho, fill, out, out_pitch, (cudaStream_t)stream);
 }
 
 // ---- gray-scale maps ------------------------------------------------------------------

@@ -171,6 +171,13 @@ int ipp_launch_psf_fit(const ipp::FitJob& J, cudaStream_t s);
 int ipp_launch_gray(const float* img, int64_t W, int64_t H, int64_t pitch, int kind, float lo, float hi, float a,
                     float* out, int64_t opitch, cudaStream_t s);
 size_t ipp_equalize_ws_bytes(int nbins);
+int ipp_launch_wcs_map(const ipp_wcs& src, const ipp_wcs& tgt, int64_t nx, int64_t ny, int step, double* xo,
+                       double* yo, cudaStream_t s);
+size_t ipp_affine_ws_bytes();
+int ipp_launch_affine_fit(const double* x, const double* y, const double* xt, const double* yt, int64_t n,
+                          int64_t grid_nx, int step, double* M, int32_t* status, void* ws, cudaStream_t s);
+int ipp_launch_reproject(const float* src, int64_t W, int64_t H, int64_t pitch, const double* Minv, int64_t Wo,
+                         int64_t Ho, float fill, float* out, int64_t opitch, cudaStream_t s);
 int ipp_launch_equalize(const float* img, int64_t W, int64_t H, int64_t pitch, int nbins, float* out,
                         int64_t opitch, void* ws, cudaStream_t s);
 int ipp_launch_psf_fwd(const float* params, int64_t N, int S, int model, float beta, float* model_out, cudaStream_t s);

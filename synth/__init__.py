@@ -15,4 +15,5 @@ from .frames import (  # noqa: F401
     moffat_stamps,
     tiny_frame,
     mixed_batch_shapes,
+    wcs_pair,
 )

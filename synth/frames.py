@@ -247,3 +247,31 @@ def moffat_stamps(n, seed=4000, S=15, beta=2.5, oversample=5):
 def tiny_frame(W, H, seed, n_stars=4, sky=100.0, fwhm=2.5, flux=(3.0, 4.0)):
     """Small field for parity tests that must span several tiles with a ragged tail."""
     return frame_field(W, H, n_stars, seed, sky_level=sky, grad=10.0, fwhm=fwhm, logflux=flux)
+
+
+def wcs_pair(W=4096, H=4096, seed=7000, scale_arcsec=1.5, order=3):
+    """Headers of two overlapping exposures of one field, as a survey camera
+    with a few pixels of optical distortion at the corners would carry them:
+    a source and a target WCS (dicts: crpix, crval, cd, a, b, a_order,
+    b_order).  The target is pointed 0.02-0.05 degrees away, rotated by up to
+    half a degree, with its own distortion.  Header values only; no mapping."""
+    rng = np.random.default_rng(seed)
+    s = scale_arcsec / 3600.0
+
+    def one(ra, dec, rot, k):
+        c, sn = np.cos(rot), np.sin(rot)
+        a, b = np.zeros((6, 6)), np.zeros((6, 6))
+        half = max(W, H) / 2.0
+        for p in range(6):
+            for q in range(6 - p):
+                if 2 <= p + q <= order:
+                    a[p, q] = rng.normal(0.0, 1.0) * 2.0 * half ** (-p - q)
+                    b[p, q] = rng.normal(0.0, 1.0) * 2.0 * half ** (-p - q)
+        return dict(crpix=[W / 2.0 + 0.5 + k, H / 2.0 + 0.5 - k], crval=[ra, dec],
+                    cd=[[-s * c, s * sn], [s * sn, s * c]], a=a, b=b, a_order=order, b_order=order)
+
+    ra0, dec0 = rng.uniform(0.0, 360.0), rng.uniform(-60.0, 60.0)
+    src = one(ra0, dec0, rng.uniform(-0.01, 0.01), 0.0)
+    tgt = one(ra0 + rng.uniform(0.02, 0.05) / np.cos(np.radians(dec0)), dec0 + rng.uniform(-0.05, -0.02),
+              rng.uniform(0.2, 0.5) * np.pi / 180.0, 3.25)
+    return src, tgt
