@@ -294,6 +294,28 @@ __device__ __forceinline__ void df_floor(df a, int& ip, float& frac) {
     frac = f;
 }
 
+// one output pixel at source position (ix + tx, iy + ty): 0 <= x <= W - 1 and
+// 0 <= y <= H - 1, the pair beyond the last column / row not read, `fill` when
+// outside or when a neighbour of non-zero weight is not finite
+__device__ __forceinline__ float rp_careful(const float* __restrict__ src, int64_t pitch, int Wi, int Hi, int ix,
+                                           int iy, float tx, float ty, float fill) {
+    const bool in = ix >= 0 && iy >= 0 && (ix < Wi - 1 || (ix == Wi - 1 && tx == 0.f)) &&
+                    (iy < Hi - 1 || (iy == Hi - 1 && ty == 0.f));
+    if (!in) return fill;
+    // the left / top pair of the last column / row is the one below the edge
+    const int x0 = min(ix, max(Wi - 2, 0)), y0 = min(iy, max(Hi - 2, 0));
+    const float t = tx + (float)(ix - x0), s = ty + (float)(iy - y0);
+    const float w00 = (1.f - t) * (1.f - s), w10 = t * (1.f - s), w01 = (1.f - t) * s, w11 = t * s;
+    const float* row = src + (int64_t)y0 * pitch + x0;
+    float acc = 0.f;
+    bool bad = false;
+    if (w00 != 0.f) { const float q = __ldg(row); bad |= !isfinite(q); acc = fmaf(w00, q, acc); }
+    if (w10 != 0.f) { const float q = __ldg(row + 1); bad |= !isfinite(q); acc = fmaf(w10, q, acc); }
+    if (w01 != 0.f) { const float q = __ldg(row + pitch); bad |= !isfinite(q); acc = fmaf(w01, q, acc); }
+    if (w11 != 0.f) { const float q = __ldg(row + pitch + 1); bad |= !isfinite(q); acc = fmaf(w11, q, acc); }
+    return bad ? fill : acc;
+}
+
 __global__ void __launch_bounds__(AL_T) k_reproject(const float* __restrict__ src, int64_t W, int64_t H,
                                                     int64_t pitch, const double* __restrict__ Minv, int64_t Wo,
                                                     int64_t Ho, float fill, float* __restrict__ out,
@@ -324,10 +346,11 @@ __global__ void __launch_bounds__(AL_T) k_reproject(const float* __restrict__ sr
     const int64_t segs = (Wo + RP_SEG - 1) / RP_SEG, tasks = segs * Ho;
     const int64_t warps = (int64_t)gridDim.x * (AL_T / 32);
     const float lim = 1073741824.f;   // 2^30: positions beyond are outside any frame
+    const int Wi = (int)W, Hi = (int)H;
     for (int64_t t = (int64_t)blockIdx.x * (AL_T / 32) + (threadIdx.x >> 5); t < tasks; t += warps) {
         const int64_t i = t / segs, j0 = (t - i * segs) * RP_SEG;
         // first source position of the segment, Minv (j0, i, 1), in double-float
-        const float fj = (float)j0, fi = (float)i;   // exact: Wo, Ho < 2^24
+        const float fj = (float)(int)j0, fi = (float)(int)i;   // exact: Wo, Ho < 2^24
         const df X0 = df_add(df_add(df_mul_exact(m0, fj), df_mul_exact(m1, fi)), m2);
         const df Y0 = df_add(df_add(df_mul_exact(m3, fj), df_mul_exact(m4, fi)), m5);
         const bool base_ok = sane && fabsf(X0.hi) < lim && fabsf(Y0.hi) < lim;
@@ -337,36 +360,40 @@ __global__ void __launch_bounds__(AL_T) k_reproject(const float* __restrict__ sr
             df_floor(X0, ibx, fbx);
             df_floor(Y0, iby, fby);
         }
-        const int Wi = (int)W, Hi = (int)H;
+        // the positions are monotone along the segment: when both ends have all four
+        // neighbours inside the frame, so has every pixel between (no per-pixel
+        // bounds tests, four unconditional loads)
+        const int kmax = (int)min((int64_t)RP_SEG, Wo - j0) - 1;
+        bool interior = false;
+        if (base_ok) {
+            const float xb = fmaf(f0, (float)kmax, fbx), yb = fmaf(f3, (float)kmax, fby);
+            const int ixa = ibx + (int)floorf(fbx), ixb = ibx + (int)floorf(xb);
+            const int iya = iby + (int)floorf(fby), iyb = iby + (int)floorf(yb);
+            interior = min(ixa, ixb) >= 0 && max(ixa, ixb) <= Wi - 2 && min(iya, iyb) >= 0 && max(iya, iyb) <= Hi - 2;
+        }
         float v[4];
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             const int k = lane * 4 + c;
-            const float fx = fmaf(f0, (float)k, fbx), fy = fmaf(f3, (float)k, fby);
-            const float flx = floorf(fx), fly = floorf(fy);
-            const int ix = ibx + (int)flx, iy = iby + (int)fly;
-            const float tx = fx - flx, ty = fy - fly;
             float r = fill;
-            // 0 <= x <= W - 1 and 0 <= y <= H - 1
-            const bool in = base_ok && ix >= 0 && iy >= 0 && (ix < Wi - 1 || (ix == Wi - 1 && tx == 0.f)) &&
-                            (iy < Hi - 1 || (iy == Hi - 1 && ty == 0.f));
-            if (in && j0 + k < Wo) {
-                // the left / top pair of the last column / row is the one below the edge
-                const int x0 = min(ix, max(Wi - 2, 0)), y0 = min(iy, max(Hi - 2, 0));
-                const float t = tx + (float)(ix - x0), s = ty + (float)(iy - y0);
-                const float w00 = (1.f - t) * (1.f - s), w10 = t * (1.f - s), w01 = (1.f - t) * s, w11 = t * s;
-                const float* row = src + (int64_t)y0 * pitch + x0;
-                float acc = 0.f;
-                bool bad = false;
-                if (w00 != 0.f) { const float q = __ldg(row); bad |= !isfinite(q); acc = fmaf(w00, q, acc); }
-                if (w10 != 0.f) { const float q = __ldg(row + 1); bad |= !isfinite(q); acc = fmaf(w10, q, acc); }
-                if (w01 != 0.f) { const float q = __ldg(row + pitch); bad |= !isfinite(q); acc = fmaf(w01, q, acc); }
-                if (w11 != 0.f) {
-                    const float q = __ldg(row + pitch + 1);
-                    bad |= !isfinite(q);
-                    acc = fmaf(w11, q, acc);
+            if (base_ok && k <= kmax) {
+                const float fx = fmaf(f0, (float)k, fbx), fy = fmaf(f3, (float)k, fby);
+                const float flx = floorf(fx), fly = floorf(fy);
+                const int ix = ibx + (int)flx, iy = iby + (int)fly;
+                const float tx = fx - flx, ty = fy - fly;
+                if (interior) {
+                    const float* row = src + (int64_t)iy * pitch + ix;
+                    const float q00 = __ldg(row), q10 = __ldg(row + 1);
+                    const float q01 = __ldg(row + pitch), q11 = __ldg(row + pitch + 1);
+                    const float w00 = (1.f - tx) * (1.f - ty), w10 = tx * (1.f - ty), w01 = (1.f - tx) * ty,
+                                w11 = tx * ty;
+                    // the same sum, in the same order, as the careful form: a term of
+                    // zero weight adds 0 exactly when its value is finite
+                    const float acc = fmaf(w11, q11, fmaf(w01, q01, fmaf(w10, q10, w00 * q00)));
+                    r = isfinite(acc) ? acc : rp_careful(src, pitch, Wi, Hi, ix, iy, tx, ty, fill);
+                } else {
+                    r = rp_careful(src, pitch, Wi, Hi, ix, iy, tx, ty, fill);
                 }
-                r = bad ? fill : acc;
             }
             v[c] = r;
         }
