@@ -114,6 +114,7 @@ def lib():
             L.orc_wcs_map.argtypes = [C.POINTER(Wcs), C.POINTER(Wcs), i64, i64, i32, vp, vp]
             L.orc_affine_fit.argtypes = [vp, vp, vp, vp, i64, vp, vp]
             L.orc_reproject_affine.argtypes = [vp, i64, i64, vp, i64, i64, d, vp]
+            L.orc_zscale.argtypes = [vp, i64, i64, i32, d, d, i32, vp, vp]
             L.orc_deblend.restype = i64
             L.orc_psf_model.argtypes = [vp, i32, i32, d, vp, vp]
             L.orc_psf_fit.argtypes = [vp, i64, i32, vp, vp, i32, d, i32, d, vp, vp, vp, vp]
@@ -424,3 +425,15 @@ def reproject_affine(src, Minv, Wo, Ho, fill=0.0):
     out = np.zeros((Ho, Wo))
     assert lib().orc_reproject_affine(_p(src), W, H, _p(Mi), Wo, Ho, float(fill), _p(out)) == 0
     return out
+
+
+def zscale(img, n_samples=1000, contrast=0.25, krej=2.5, max_iter=5):
+    """ZScale limits (z1, z2) and (samples, good samples)."""
+    img = _f32(img)
+    H, W = img.shape
+    z, cnt = np.zeros(2), np.zeros(2, np.int32)
+    e = lib().orc_zscale(_p(img), W, H, int(n_samples), float(contrast), float(krej), int(max_iter), _p(z),
+                         _p(cnt))
+    if e:
+        raise ValueError("zscale: no finite sample or bad parameters")
+    return float(z[0]), float(z[1]), (int(cnt[0]), int(cnt[1]))

@@ -1427,3 +1427,99 @@ int orc_reproject_affine(const float* src, int64_t W, int64_t H, const double* M
     }
     return ORC_OK;
 }
+
+/* ---------------------------------------------------------------------------
+ * ZScale display limits (Sec. 2.2.6 names SAOimage's zscale; reading after the
+ * published IRAF algorithm):
+ *   samples: up to n_samples pixels at flat (row-major) indices k * stride,
+ *     stride = max(1, W H / n_samples), non-finite ones dropped; sorted;
+ *   npix samples s_0 <= ... ; zmin = s_0, zmax = s_{npix-1}; c = (npix - 1) / 2
+ *     (integer); median = s_c (npix odd) or (s_c + s_{c+1}) / 2;
+ *   minpix = max(5, (int)(0.5 npix)); rejections grow by h = max(1, (int)(0.01
+ *     npix)) / 2 samples on each side;
+ *   iteration (at most max_iter): stop when ngood >= the previous ngood or
+ *     ngood < minpix; least-squares line of s_k against x_k = k - c over the
+ *     good samples; flat_k = s_k - (slope x_k + intercept) for every sample;
+ *     sigma = population standard deviation of flat over the good samples;
+ *     a sample is rejected when |flat| > krej sigma; a sample is good when no
+ *     rejected sample lies within h of it; ngood = the number of good samples;
+ *   limits: with ngood >= minpix, z1 = max(zmin, median - (c - 1) slope /
+ *     contrast), z2 = min(zmax, median + (npix - c) slope / contrast); otherwise
+ *     (zmin, zmax).  No finite sample: INVALID_ARG.
+ * ------------------------------------------------------------------------- */
+static int cmp_f(const void* a, const void* b) {
+    const float x = *(const float*)a, y = *(const float*)b;
+    return (x > y) - (x < y);
+}
+
+int orc_zscale(const float* img, int64_t W, int64_t H, int32_t n_samples, double contrast, double krej,
+               int32_t max_iter, double* z, int32_t* counts) {
+    if (W < 1 || H < 1 || n_samples < 1 || !(contrast > 0.0) || !(krej > 0.0) || max_iter < 0) return ORC_INVALID_ARG;
+    const int64_t N = W * H;
+    int64_t stride = N / n_samples;
+    if (stride < 1) stride = 1;
+    float* s = (float*)malloc(sizeof(float) * (size_t)n_samples);
+    int64_t npix = 0;
+    for (int64_t k = 0; k < n_samples && k * stride < N; k++) {
+        const float v = img[k * stride];
+        if (isfinite(v)) s[npix++] = v;
+    }
+    if (npix == 0) { free(s); return ORC_INVALID_ARG; }
+    qsort(s, (size_t)npix, sizeof(float), cmp_f);
+    const double zmin = s[0], zmax = s[npix - 1];
+    const int64_t c = (npix - 1) / 2;
+    const double median = (npix & 1) ? (double)s[c] : 0.5 * ((double)s[c] + (double)s[c + 1]);
+    int64_t minpix = (int64_t)(0.5 * (double)npix);
+    if (minpix < 5) minpix = 5;
+    int64_t ngrow = (int64_t)(0.01 * (double)npix);
+    if (ngrow < 1) ngrow = 1;
+    const int64_t h = ngrow / 2;
+    unsigned char* good = (unsigned char*)malloc((size_t)npix);
+    unsigned char* bad = (unsigned char*)malloc((size_t)npix);
+    double* flat = (double*)malloc(sizeof(double) * (size_t)npix);
+    for (int64_t k = 0; k < npix; k++) good[k] = 1;
+    int64_t ngood = npix, last = npix + 1;
+    double slope = 0.0;
+    for (int it = 0; it < max_iter; it++) {
+        if (ngood >= last || ngood < minpix) break;
+        /* least-squares line over the good samples */
+        double n = 0, sx = 0, sy = 0, sxx = 0, sxy = 0;
+        for (int64_t k = 0; k < npix; k++) {
+            if (!good[k]) continue;
+            const double x = (double)(k - c), y = s[k];
+            n += 1.0; sx += x; sy += y; sxx += x * x; sxy += x * y;
+        }
+        const double den = n * sxx - sx * sx;
+        slope = den != 0.0 ? (n * sxy - sx * sy) / den : 0.0;
+        const double icpt = (sy - slope * sx) / n;
+        for (int64_t k = 0; k < npix; k++) flat[k] = (double)s[k] - (slope * (double)(k - c) + icpt);
+        double m = 0.0;
+        for (int64_t k = 0; k < npix; k++) if (good[k]) m += flat[k];
+        m /= n;
+        double v = 0.0;
+        for (int64_t k = 0; k < npix; k++) if (good[k]) v += (flat[k] - m) * (flat[k] - m);
+        const double thr = krej * sqrt(v / n);
+        for (int64_t k = 0; k < npix; k++) bad[k] = (flat[k] < -thr) || (flat[k] > thr);
+        last = ngood;
+        ngood = 0;
+        for (int64_t k = 0; k < npix; k++) {
+            int ok = 1;
+            for (int64_t j = k - h; j <= k + h; j++)
+                if (j >= 0 && j < npix && bad[j]) { ok = 0; break; }
+            good[k] = (unsigned char)ok;
+            ngood += ok;
+        }
+    }
+    if (ngood >= minpix) {
+        const double sl = slope / contrast;
+        const double a = median - (double)(c - 1) * sl, b = median + (double)(npix - c) * sl;
+        z[0] = a > zmin ? a : zmin;
+        z[1] = b < zmax ? b : zmax;
+    } else {
+        z[0] = zmin;
+        z[1] = zmax;
+    }
+    if (counts) { counts[0] = (int32_t)npix; counts[1] = (int32_t)ngood; }
+    free(s); free(good); free(bad); free(flat);
+    return ORC_OK;
+}

@@ -120,6 +120,11 @@ int orc_affine_fit(const double* x, const double* y, const double* xt, const dou
 int orc_reproject_affine(const float* src, int64_t W, int64_t H, const double* Minv, int64_t Wo, int64_t Ho,
                          double fill, double* out);
 
+/* ZScale display limits (Sec. 2.2.6; reading after the published IRAF
+ * algorithm): z[0], z[1] = z1, z2; counts = (samples, good samples). */
+int orc_zscale(const float* img, int64_t W, int64_t H, int32_t n_samples, double contrast, double krej,
+               int32_t max_iter, double* z, int32_t* counts);
+
 /* Deblending (Sec. 2.2.4): multi-level thresholds, sub-component tree, pruning
  * on intensity (mincont), remaining pixels to the likeliest object; objects
  * numbered candidate by candidate, within one in raster order of their first
