@@ -429,6 +429,8 @@ def main():
     stages["gray_log"] = timeit(
         lambda k: ipp.gray_transform(gin[k % 4], ipp.GRAY_LOG, 0.0, 2000.0, a=1000.0, out=gout[k % 4]))
     stages["hist_equalize"] = timeit(lambda k: ipp.hist_equalize(gin[k % 4], nbins=4096, out=gout[k % 4], ws=gws))
+    # zscale display limits of the same frames (1000 samples, one block)
+    stages["zscale"] = timeit(lambda k: ipp.zscale(gin[k % 4]))
     # image alignment of the subtracted frame onto a second exposure's pixel grid
     # (a widening): WCS mapping of a 32 px node grid, partial affine fit, bilinear
     # reprojection; same four rotating input/output pairs

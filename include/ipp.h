@@ -90,6 +90,14 @@ typedef struct {
     double b[36];        /* likewise in eta */
 } ipp_wcs;
 
+/* ZScale parameters (Sec. 2.2.6; defaults of the published IRAF algorithm). */
+typedef struct {
+    int32_t n_samples;  /* pixels sampled at a flat stride, 1..4096 [1000] */
+    float contrast;     /* slope divisor, > 0 [0.25] */
+    float krej;         /* rejection threshold in sigma of the residuals, > 0 [2.5] */
+    int32_t max_iter;   /* fit-and-reject passes, 0..100 [5] */
+} ipp_zscale_params;
+
 /* Gray-scale functions of ipp_gray_transform (Sec. 2.2.6). */
 #define IPP_GRAY_LINEAR 0
 #define IPP_GRAY_LOG 1
@@ -479,6 +487,28 @@ int ipp_affine_fit(const double* x, const double* y, const double* xt, const dou
  */
 int ipp_reproject_affine(const float* src, int64_t W, int64_t H, int64_t pitch, const double* Minv_dev, int64_t Wo,
                          int64_t Ho, float fill, float* out, int64_t out_pitch, void* stream);
+
+/*
+ * ipp_zscale -- display limits of Sec. 2.2.6 (SAOimage's zscale; reading after
+ * the published IRAF algorithm).  Samples: up to n_samples pixels at flat
+ * (row-major) indices k stride, stride = max(1, W H / n_samples), non-finite
+ * ones dropped, sorted: s_0 <= ... <= s_{npix-1}; c = (npix - 1) / 2; median =
+ * s_c (npix odd) or (s_c + s_{c+1}) / 2.  Up to max_iter passes, stopping when
+ * the good count stops falling or drops below minpix = max(5, npix / 2): the
+ * least-squares line of s_k against k - c over the good samples; residuals of
+ * every sample; rejection where |residual| > krej x their population standard
+ * deviation over the good samples; a sample is good when no rejected sample
+ * lies within h = max(1, npix / 100) / 2 of it.  Limits: with at least minpix
+ * good samples z1 = max(s_0, median - (c - 1) slope / contrast), z2 =
+ * min(s_{npix-1}, median + (npix - c) slope / contrast), else (s_0, s_{npix-1}).
+ * FP64 fit; one block of 1024 threads (the samples sorted in shared memory).
+ *   z_out       device double[2]: z1, z2 (NaN when no sample is finite)
+ *   counts_out  nullable device int32[2]: samples used, good samples at the end
+ * Errors: INVALID_ARG for NULL pointers, bad sizes or pitches, or parameters
+ * outside the ranges above.
+ */
+int ipp_zscale(const float* img, int64_t W, int64_t H, int64_t pitch, const ipp_zscale_params* p, double* z_out,
+               int32_t* counts_out, void* stream);
 
 /*
  * ipp_stamp_cut -- S x S stamps of the subtracted frame around each source, the

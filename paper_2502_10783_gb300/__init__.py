@@ -25,7 +25,7 @@ from ._abi import (  # noqa: F401
 )
 
 __all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "deblend", "stamp_cut", "Batch",
-           "gray_transform", "hist_equalize", "wcs_map", "affine_fit", "reproject_affine", "align",
+           "gray_transform", "hist_equalize", "zscale", "wcs_map", "affine_fit", "reproject_affine", "align",
            "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
 
 
@@ -276,6 +276,20 @@ def gray_transform(img, kind, lo, hi, a=1000.0, out=None):
         _ptr(img), W, H, img.stride(0), int(kind), float(lo), float(hi), float(a), _ptr(out), out.stride(0),
         _stream()))
     return out
+
+
+def zscale(img, n_samples=1000, contrast=0.25, krej=2.5, max_iter=5):
+    """ZScale display limits of the frame (ipp_zscale): device float64 [2]
+    (z1, z2) and device int32 [2] (samples used, good samples)."""
+    L = load()
+    _frame2d(img, "img")
+    H, W = img.shape
+    z = torch.empty(2, dtype=torch.float64, device=img.device)
+    cnt = torch.empty(2, dtype=torch.int32, device=img.device)
+    _abi.check("ipp_zscale", L.ipp_zscale(
+        _ptr(img), W, H, img.stride(0), C.byref(_abi.ZscaleParams(n_samples, contrast, krej, max_iter)), _ptr(z),
+        _ptr(cnt), _stream()))
+    return z, cnt
 
 
 def hist_equalize(img, nbins=4096, out=None, ws=None):

@@ -46,6 +46,10 @@ class Wcs(C.Structure):
                 ("a", f64 * 36), ("b", f64 * 36)]
 
 
+class ZscaleParams(C.Structure):
+    _fields_ = [("n_samples", i32), ("contrast", f32), ("krej", f32), ("max_iter", i32)]
+
+
 class DeblendParams(C.Structure):
     _fields_ = [("nthresh", i32), ("mincont", f32)]
 
@@ -107,6 +111,7 @@ PROTOTYPES = {
     "ipp_affine_fit_workspace_size": ([], sz),
     "ipp_affine_fit": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, sz, vp], i32),
     "ipp_reproject_affine": ([vp, i64, i64, i64, vp, i64, i64, f32, vp, i64, vp], i32),
+    "ipp_zscale": ([vp, i64, i64, i64, C.POINTER(ZscaleParams), vp, vp, vp], i32),
     "ipp_gray_transform": ([vp, i64, i64, i64, i32, f32, f32, f32, vp, i64, vp], i32),
     "ipp_hist_equalize_workspace_size": ([i32], sz),
     "ipp_hist_equalize": ([vp, i64, i64, i64, i32, vp, i64, vp, sz, vp], i32),

@@ -336,6 +336,18 @@ extern "C" int ipp_gray_transform(const float* img, int64_t W, int64_t H, int64_
     return ipp_launch_gray(img, W, H, pitch, kind, lo, hi, a, out, out_pitch, (cudaStream_t)stream);
 }
 
+extern "C" int ipp_zscale(const float* img, int64_t W, int64_t H, int64_t pitch, const ipp_zscale_params* p,
+                          double* z_out, int32_t* counts_out, void* stream) {
+    if (int e = check_frame(img, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(p && p->n_samples >= 1 && p->n_samples <= 4096, "n_samples must be 1..4096");
+    REQUIRE(p->contrast > 0.f && std::isfinite(p->contrast) && p->krej > 0.f && std::isfinite(p->krej),
+            "contrast and krej must be finite and > 0");
+    REQUIRE(p->max_iter >= 0 && p->max_iter <= 100, "max_iter must be 0..100");
+    REQUIRE(z_out, "z_out NULL");
+    return ipp_launch_zscale(img, W, H, pitch, p->n_samples, (double)p->contrast, (double)p->krej, p->max_iter,
+                             z_out, counts_out, (cudaStream_t)stream);
+}
+
 extern "C" size_t ipp_hist_equalize_workspace_size(int32_t nbins) {
     if (nbins < 2 || nbins > 16384) return 0;
     return ipp_equalize_ws_bytes(nbins);

@@ -388,3 +388,203 @@ int ipp_launch_equalize(const float* img, int64_t W, int64_t H, int64_t pitch, i
     if (v.mode == 1) return launch_equalize_m<1>(img, v, nbins, w, out, s);
     return launch_equalize_m<2>(img, v, nbins, w, out, s);
 }
+
+// ---- zscale display limits -----------------------------------------------------------
+// Reading after the published IRAF algorithm (Sec. 2.2.6 names SAOimage's zscale):
+// up to n_samples pixels at a flat stride, non-finite ones dropped, sorted; an
+// iterated least-squares line of the sorted samples against their index with
+// krej-sigma rejection grown by h samples on each side; the limits from the line's
+// slope over the contrast, about the median, clipped to the sample range.  One
+// block: the samples are sorted in shared memory (bitonic network), each thread
+// keeps the residuals of its four samples in registers, and every sum is a block
+// reduction in a fixed order, so the result does not depend on scheduling.
+namespace ipp {
+
+constexpr int ZS_T = 1024, ZS_MAX = 4096, ZS_PER = ZS_MAX / ZS_T;
+
+// sum of NV doubles over the block, the same value in every thread
+template <int NV>
+__device__ __forceinline__ void zs_sum(double v[NV], double (*red)[ZS_T / 32]) {
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+        if (lane == 0) red[c][wi] = v[c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+        double s = 0.0;
+        for (int k = 0; k < ZS_T / 32; k++) s += red[c][k];
+        v[c] = s;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(ZS_T) k_zscale(const float* __restrict__ img, int64_t W, int64_t H, int64_t pitch,
+                                                 int ns, double contrast, double krej, int max_iter,
+                                                 double* __restrict__ z, int32_t* __restrict__ counts) {
+    __shared__ float s[ZS_MAX];
+    __shared__ unsigned char good[ZS_MAX], bad[ZS_MAX];
+    __shared__ int pre[ZS_MAX + 1];
+    __shared__ int tsum[ZS_T];
+    __shared__ double red[5][ZS_T / 32];
+    __shared__ int npix_sh;
+    const int tid = threadIdx.x;
+    const int64_t N = W * H;
+    const int64_t stride = max((int64_t)1, N / ns);
+    // samples; absent or non-finite ones become +inf and sort to the end
+    for (int k = tid; k < ZS_MAX; k += ZS_T) {
+        float v = INFINITY;
+        if (k < ns && (int64_t)k * stride < N) {
+            const int64_t idx = (int64_t)k * stride, r = idx / W;
+            const float q = __ldg(img + r * pitch + (idx - r * W));
+            if (isfinite(q)) v = q;
+        }
+        s[k] = v;
+    }
+    if (tid == 0) npix_sh = 0;
+    __syncthreads();
+    // bitonic sort, ascending
+    for (int size = 2; size <= ZS_MAX; size <<= 1) {
+        for (int st = size >> 1; st > 0; st >>= 1) {
+            for (int t = tid; t < ZS_MAX / 2; t += ZS_T) {
+                const int lo = 2 * t - (t & (st - 1)), hi = lo + st;
+                const bool asc = (lo & size) == 0;
+                const float a = s[lo], b = s[hi];
+                if ((a > b) == asc) {
+                    s[lo] = b;
+                    s[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int k = tid; k < ZS_MAX; k += ZS_T)
+        if (s[k] < INFINITY && (k + 1 == ZS_MAX || !(s[k + 1] < INFINITY))) npix_sh = k + 1;
+    __syncthreads();
+    const int npix = npix_sh;
+    if (npix == 0) {
+        if (tid == 0) {
+            z[0] = z[1] = NAN;
+            if (counts) counts[0] = counts[1] = 0;
+        }
+        return;
+    }
+    const double zmin = s[0], zmax = s[npix - 1];
+    const int c = (npix - 1) / 2;
+    const double median = (npix & 1) ? (double)s[c] : 0.5 * ((double)s[c] + (double)s[c + 1]);
+    const int minpix = max(5, (int)(0.5 * (double)npix));
+    const int h = max(1, (int)(0.01 * (double)npix)) / 2;
+    for (int k = tid; k < ZS_MAX; k += ZS_T) good[k] = k < npix;
+    __syncthreads();
+    int ngood = npix, last = npix + 1;
+    double slope = 0.0;
+    for (int it = 0; it < max_iter; it++) {
+        if (ngood >= last || ngood < minpix) break;
+        // least-squares line over the good samples, x = k - c
+        double v5[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < ZS_PER; j++) {
+            const int k = tid + j * ZS_T;
+            if (k < npix && good[k]) {
+                const double x = (double)(k - c), y = (double)s[k];
+                v5[0] += 1.0;
+                v5[1] += x;
+                v5[2] += y;
+                v5[3] = __dadd_rn(v5[3], __dmul_rn(x, x));
+                v5[4] = __dadd_rn(v5[4], __dmul_rn(x, y));
+            }
+        }
+        zs_sum<5>(v5, red);
+        const double n = v5[0];
+        const double den = __dsub_rn(__dmul_rn(n, v5[3]), __dmul_rn(v5[1], v5[1]));
+        slope = den != 0.0 ? __dsub_rn(__dmul_rn(n, v5[4]), __dmul_rn(v5[1], v5[2])) / den : 0.0;
+        const double icpt = __dsub_rn(v5[2], __dmul_rn(slope, v5[1])) / n;
+        double fl[ZS_PER];
+        double m1[1] = {0.0};
+#pragma unroll
+        for (int j = 0; j < ZS_PER; j++) {
+            const int k = tid + j * ZS_T;
+            fl[j] = __dsub_rn((double)s[k], __dadd_rn(__dmul_rn(slope, (double)(k - c)), icpt));
+            if (k < npix && good[k]) m1[0] += fl[j];
+        }
+        zs_sum<1>(m1, red);
+        const double m = m1[0] / n;
+        double v1[1] = {0.0};
+#pragma unroll
+        for (int j = 0; j < ZS_PER; j++) {
+            const int k = tid + j * ZS_T;
+            if (k < npix && good[k]) {
+                const double d = __dsub_rn(fl[j], m);
+                v1[0] = __dadd_rn(v1[0], __dmul_rn(d, d));
+            }
+        }
+        zs_sum<1>(v1, red);
+        const double thr = krej * sqrt(v1[0] / n);
+#pragma unroll
+        for (int j = 0; j < ZS_PER; j++) {
+            const int k = tid + j * ZS_T;
+            bad[k] = k < npix && (fl[j] < -thr || fl[j] > thr);
+        }
+        __syncthreads();
+        // prefix counts of rejected samples: thread t owns samples 4t .. 4t + 3
+        int loc = 0;
+#pragma unroll
+        for (int j = 0; j < ZS_PER; j++) loc += bad[tid * ZS_PER + j];
+        tsum[tid] = loc;
+        __syncthreads();
+        for (int o = 1; o < ZS_T; o <<= 1) {   // inclusive scan of the thread totals
+            const int add = tid >= o ? tsum[tid - o] : 0;
+            __syncthreads();
+            tsum[tid] += add;
+            __syncthreads();
+        }
+        int run = tsum[tid] - loc;
+        if (tid == 0) pre[0] = 0;
+#pragma unroll
+        for (int j = 0; j < ZS_PER; j++) {
+            run += bad[tid * ZS_PER + j];
+            pre[tid * ZS_PER + j + 1] = run;
+        }
+        __syncthreads();
+        // good: no rejected sample within h
+        int g = 0;
+#pragma unroll
+        for (int j = 0; j < ZS_PER; j++) {
+            const int k = tid + j * ZS_T;
+            const bool ok = k < npix && pre[min(k + h + 1, npix)] - pre[max(k - h, 0)] == 0;
+            good[k] = ok;
+            g += ok;
+        }
+        double gs[1] = {(double)g};
+        zs_sum<1>(gs, red);
+        last = ngood;
+        ngood = (int)gs[0];
+    }
+    if (tid == 0) {
+        if (ngood >= minpix) {
+            const double sl = slope / contrast;
+            const double a = __dsub_rn(median, __dmul_rn((double)(c - 1), sl));
+            const double b = __dadd_rn(median, __dmul_rn((double)(npix - c), sl));
+            z[0] = a > zmin ? a : zmin;
+            z[1] = b < zmax ? b : zmax;
+        } else {
+            z[0] = zmin;
+            z[1] = zmax;
+        }
+        if (counts) {
+            counts[0] = npix;
+            counts[1] = ngood;
+        }
+    }
+}
+
+}  // namespace ipp
+
+int ipp_launch_zscale(const float* img, int64_t W, int64_t H, int64_t pitch, int ns, double contrast, double krej,
+                      int max_iter, double* z, int32_t* counts, cudaStream_t s) {
+    ipp::k_zscale<<<1, ipp::ZS_T, 0, s>>>(img, W, H, pitch, ns, contrast, krej, max_iter, z, counts);
+    return ipp_check_launch("k_zscale");
+}
