@@ -15,7 +15,7 @@
  *   ipp_centroid      windowed centroid of each candidate     (positions, Sec. 2.2.5)
  *   ipp_aperture_phot circular aperture photometry with a local sky annulus
  *                                                             (Sec. 2.2.5)
- *   ipp_deblend       multi-threshold deblending of the candidates (Sec. 2.2.4)
+ *   ipp_deblend       multi-threshold deblending of the candidates (Sec. 2.2.5)
  *   ipp_auto_phot     auto (Kron) photometry in an elliptical aperture (Sec. 2.2.5)
  *   ipp_stamp_cut     S x S stamps at the measured positions (input of the fit)
  *   ipp_psf_fit       batched Levenberg-Marquardt PSF fit of stamps
@@ -78,7 +78,7 @@ extern "C" {
 #define IPP_EST_FACTORS 3 /* Eq. 4, read as median_factor * median - mean_factor * mean */
 
 /* PSF models */
-/* World coordinate system of a frame (Sec. 2.2.3, Eqs. 1-3): SIP distortion,
+/* World coordinate system of a frame (Sec. 2.2.3, Eqs. 5-7): SIP distortion,
  * CD matrix and gnomonic (TAN) projection. */
 typedef struct {
     double crpix[2];     /* reference pixel, FITS 1-based (0-based pixel j is FITS j + 1) */
@@ -146,7 +146,7 @@ typedef struct {
     int32_t min_ann;    /* fewest annulus pixels for a sky value [10] */
 } ipp_phot_params;
 
-/* Deblending parameters (Sec. 2.2.4; values are readings). */
+/* Deblending parameters (Sec. 2.2.5; values are readings). */
 typedef struct {
     int32_t nthresh;    /* number of levels N between a candidate's lowest and highest pixel [32] */
     float mincont;      /* a branch splits off when it holds this fraction of the candidate's flux [0.005] */
@@ -319,7 +319,7 @@ int ipp_aperture_phot(const float* sub, int64_t W, int64_t H, int64_t pitch,
                       int32_t* n_ann, int32_t* flags, void* stream);
 
 /*
- * ipp_deblend -- deblending of the candidates of ipp_detect_label (Sec. 2.2.4:
+ * ipp_deblend -- deblending of the candidates of ipp_detect_label (Sec. 2.2.5:
  * multi-level thresholds between each candidate's threshold and its peak, a
  * tree of the sub-components found at each level, traversed bottom-up and
  * pruned on intensity).  Reading:
@@ -426,8 +426,8 @@ int ipp_hist_equalize(const float* img, int64_t W, int64_t H, int64_t pitch, int
 
 /*
  * ipp_wcs_map -- coordinate mapping of Sec. 2.2.3: source pixel -> sky -> target
- * pixel, through Eq. 1 (SIP, on the offsets u = x - CRPIX1, v = y - CRPIX2 of
- * the FITS pixel position), Eq. 2 (CD) and Eq. 3 (gnomonic deprojection about
+ * pixel, through Eq. 5 (SIP, on the offsets u = x - CRPIX1, v = y - CRPIX2 of
+ * the FITS pixel position), Eq. 6 (CD) and Eq. 7 (gnomonic deprojection about
  * the source's CRVAL), then the inverse chain of the target: gnomonic projection
  * about its CRVAL, CD^-1, and the inverse of its SIP polynomial by Newton's
  * method (at most 50 steps, until the step is below 1e-12 px).  FP64.

@@ -378,7 +378,7 @@ def catalog(img, mesh=64, filter_size=3, k=1.5, min_area=5, fwhm_win=3.0,
 
 
 def wcs_pix2world(w, x, y):
-    """0-based pixel positions -> (RA, Dec) in degrees (Eqs. 1-3)."""
+    """0-based pixel positions -> (RA, Dec) in degrees (Eqs. 5-7)."""
     x = np.ascontiguousarray(x, np.float64).ravel()
     y = np.ascontiguousarray(y, np.float64).ravel()
     ra, de = np.zeros_like(x), np.zeros_like(x)

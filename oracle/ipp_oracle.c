@@ -614,7 +614,7 @@ int orc_hist_equalize(const float* img, int64_t W, int64_t H, int32_t nbins, dou
 
 /* ------------------------------------------------------------ deblending */
 /*
- * Deblending (Sec. 2.2.4, source detection: multi-level thresholds between each
+ * Deblending (Sec. 2.2.5, source detection: multi-level thresholds between each
  * candidate's threshold and its peak, a tree of the sub-components found at
  * each level, traversed bottom-up and pruned on intensity).  Reading:
  *  levels -- per candidate C (pixels labelled c): T = min sub over C,
@@ -1242,18 +1242,18 @@ int orc_psf_fit(const float* stamps, int64_t N, int32_t S, const float* weights,
 
 /* ---------------------------------------------------------------------------
  * Image alignment (Sec. 2.2.3): pixel -> sky -> pixel coordinate mapping
- * (Eqs. 1-3 and their inverses), the partial affine (similarity) estimate, and
+ * (Eqs. 5-7 and their inverses), the partial affine (similarity) estimate, and
  * bilinear reprojection.  Readings:
  *   pixel (column j, row i), 0-based, is FITS pixel (j + 1, i + 1);
- *   Eq. 1 is the SIP distortion applied to the offsets from the reference pixel,
+ *   Eq. 5 is the SIP distortion applied to the offsets from the reference pixel,
  *     u = x - CRPIX1, v = y - CRPIX2:  xi = u + sum A_pq u^p v^q,
  *     eta = v + sum B_pq u^p v^q  (p + q <= order, every given term);
- *   Eq. 2 maps (xi, eta) through CD (degrees per pixel) to the standard
+ *   Eq. 6 maps (xi, eta) through CD (degrees per pixel) to the standard
  *     coordinates (in radians below);
- *   Eq. 3 is the gnomonic (TAN) deprojection about (CRVAL1, CRVAL2);
- *   the inverse chain inverts Eq. 3 (the gnomonic projection about the target's
- *   CRVAL; points at or beyond 90 degrees from it have no image: NaN), Eq. 2
- *   (CD^-1) and Eq. 1 (Newton's method from (xi, eta), at most 50 steps, until
+ *   Eq. 7 is the gnomonic (TAN) deprojection about (CRVAL1, CRVAL2);
+ *   the inverse chain inverts Eq. 7 (the gnomonic projection about the target's
+ *   CRVAL; points at or beyond 90 degrees from it have no image: NaN), Eq. 6
+ *   (CD^-1) and Eq. 5 (Newton's method from (xi, eta), at most 50 steps, until
  *   the step is below 1e-12 px; not converged: NaN).
  * ------------------------------------------------------------------------- */
 static const double ORC_D2R = M_PI / 180.0;
@@ -1282,10 +1282,10 @@ int orc_wcs_pix2world(const orc_wcs* w, const double* x, const double* y, int64_
         double f, g;
         sip_eval(w->a, w->a_order, u, v, &f, NULL, NULL);
         sip_eval(w->b, w->b_order, u, v, &g, NULL, NULL);
-        const double xi = u + f, eta = v + g;                                   /* Eq. 1 */
-        const double p = (w->cd[0] * xi + w->cd[1] * eta) * ORC_D2R;           /* Eq. 2 */
+        const double xi = u + f, eta = v + g;                                   /* Eq. 5 */
+        const double p = (w->cd[0] * xi + w->cd[1] * eta) * ORC_D2R;           /* Eq. 6 */
         const double q = (w->cd[2] * xi + w->cd[3] * eta) * ORC_D2R;
-        const double den = cos(d0) - q * sin(d0);                               /* Eq. 3 */
+        const double den = cos(d0) - q * sin(d0);                               /* Eq. 7 */
         double al = a0 + atan2(p, den);
         al = fmod(al, 2.0 * M_PI);
         if (al < 0.0) al += 2.0 * M_PI;
@@ -1301,15 +1301,15 @@ int orc_wcs_world2pix(const orc_wcs* w, const double* ra, const double* dec, int
     if (det == 0.0) return ORC_INVALID_ARG;
     for (int64_t k = 0; k < n; k++) {
         const double al = ra[k] * ORC_D2R, de = dec[k] * ORC_D2R;
-        /* inverse of Eq. 3: gnomonic projection about (a0, d0) */
+        /* inverse of Eq. 7: gnomonic projection about (a0, d0) */
         const double cc = sin(d0) * sin(de) + cos(d0) * cos(de) * cos(al - a0);
         if (!(cc > 0.0)) { x[k] = NAN; y[k] = NAN; continue; }
         const double p = cos(de) * sin(al - a0) / cc / ORC_D2R;
         const double q = (cos(d0) * sin(de) - sin(d0) * cos(de) * cos(al - a0)) / cc / ORC_D2R;
-        /* inverse of Eq. 2 */
+        /* inverse of Eq. 6 */
         const double xi = (w->cd[3] * p - w->cd[1] * q) / det;
         const double eta = (-w->cd[2] * p + w->cd[0] * q) / det;
-        /* inverse of Eq. 1: Newton on (u + f(u, v) - xi, v + g(u, v) - eta) */
+        /* inverse of Eq. 5: Newton on (u + f(u, v) - xi, v + g(u, v) - eta) */
         double u = xi, v = eta;
         int ok = 0;
         for (int it = 0; it < 50; it++) {
@@ -1521,5 +1521,239 @@ int orc_zscale(const float* img, int64_t W, int64_t H, int32_t n_samples, double
     }
     if (counts) { counts[0] = (int32_t)npix; counts[1] = (int32_t)ngood; }
     free(s); free(good); free(bad); free(flat);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Image subtraction (Sec. 2.2.4, HOTPANTS-style: Eqs. 8-10).  Readings:
+ *   basis (Eq. 9): for each Gaussian k (width sig_k, degree deg_k) and every
+ *     i + j <= deg_k (i outer, j inner), K_n(u, v) = exp(-(u^2 + v^2) /
+ *     (2 sig_k^2)) u^i v^j on -hw <= u, v <= hw, stored row-major by v then u;
+ *   convolution: (R (x) K)(x, y) = sum_{u,v} K(u, v) R(x - u, y - v);
+ *   spatial terms: xs = 2x / (W - 1) - 1, ys = 2y / (H - 1) - 1 (0 for a single
+ *     column or row); terms xs^p ys^q, p outer, q inner, p + q <= order;
+ *   Eq. 8: a_n(x, y) = sum_s c_{n,s} P_s(x, y); Eq. 10 read as the model
+ *     I + B = R (x) K with B(x, y) = sum_b d_b P_b(x, y) (background order);
+ *   stamps: the frame is cut into nsx x nsy regions; in each, the brightest
+ *     template pixel whose fit footprint (2 fh + 1)^2 and convolution support
+ *     (2 (fh + hw) + 1)^2 lie inside the frame and are finite in R and I is a
+ *     candidate when it exceeds the region's median by nsig robust sigmas
+ *     (1.4826 MAD over the region's finite pixels);
+ *   fit: unweighted least squares over every footprint pixel of every
+ *     candidate, the kernel's spatial terms taken at the candidate's centre
+ *     (constant over a footprint) and the background's at each pixel; normal
+ *     equations in FP64, Cholesky;
+ *   apply: the kernel is evaluated at the centre of each tile x tile block of
+ *     the output (the paper's stamp-per-block convolution) and convolved with R
+ *     for the block's pixels; D = I + B - R (x) K where the whole kernel support
+ *     lies inside the frame, NaN elsewhere.
+ * ------------------------------------------------------------------------- */
+static int sub_nbasis(const int32_t* deg, int32_t nk) {
+    int nb = 0;
+    for (int k = 0; k < nk; k++) nb += (deg[k] + 1) * (deg[k] + 2) / 2;
+    return nb;
+}
+
+int orc_sub_basis(int32_t hw, const double* sig, const int32_t* deg, int32_t nk, double* out) {
+    if (hw < 0 || nk < 1) return -1;
+    const int S = 2 * hw + 1;
+    int n = 0;
+    for (int k = 0; k < nk; k++) {
+        if (!(sig[k] > 0.0) || deg[k] < 0) return -1;
+        for (int i = 0; i <= deg[k]; i++) {
+            for (int j = 0; j <= deg[k] - i; j++) {
+                for (int v = -hw; v <= hw; v++) {
+                    for (int u = -hw; u <= hw; u++) {
+                        const double g = exp(-(double)(u * u + v * v) / (2.0 * sig[k] * sig[k]));
+                        out[(int64_t)n * S * S + (v + hw) * S + (u + hw)] = g * pow((double)u, i) * pow((double)v, j);
+                    }
+                }
+                n++;
+            }
+        }
+    }
+    return n;
+}
+
+static int sub_nterms(int order) { return (order + 1) * (order + 2) / 2; }
+
+static void sub_terms(double x, double y, int64_t W, int64_t H, int order, double* t) {
+    const double xs = W > 1 ? 2.0 * x / (double)(W - 1) - 1.0 : 0.0;
+    const double ys = H > 1 ? 2.0 * y / (double)(H - 1) - 1.0 : 0.0;
+    int n = 0;
+    for (int p = 0; p <= order; p++)
+        for (int q = 0; q <= order - p; q++) t[n++] = pow(xs, p) * pow(ys, q);
+}
+
+static int cmp_d(const void* a, const void* b) {
+    const double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+static double median_d(double* v, int64_t n) {
+    qsort(v, (size_t)n, sizeof(double), cmp_d);
+    return (n & 1) ? v[n / 2] : 0.5 * (v[n / 2 - 1] + v[n / 2]);
+}
+
+int orc_sub_stamps(const float* I, const float* R, int64_t W, int64_t H, int32_t nsx, int32_t nsy, int32_t hw,
+                   int32_t fh, double nsig, int32_t* cx, int32_t* cy) {
+    if (nsx < 1 || nsy < 1 || hw < 0 || fh < 0) return -1;
+    const int64_t m = (int64_t)fh + hw;
+    int nc = 0;
+    double* buf = (double*)malloc(sizeof(double) * (size_t)(W * H / ((int64_t)nsx * nsy) + W + H + 16));
+    for (int sy = 0; sy < nsy; sy++) {
+        for (int sx = 0; sx < nsx; sx++) {
+            const int64_t x0 = sx * W / nsx, x1 = (sx + 1) * W / nsx, y0 = sy * H / nsy, y1 = (sy + 1) * H / nsy;
+            int64_t n = 0;
+            for (int64_t y = y0; y < y1; y++)
+                for (int64_t x = x0; x < x1; x++)
+                    if (isfinite(R[y * W + x])) buf[n++] = R[y * W + x];
+            if (n == 0) continue;
+            const double med = median_d(buf, n);
+            for (int64_t k = 0; k < n; k++) buf[k] = fabs(buf[k] - med);
+            const double sgm = 1.4826 * median_d(buf, n);
+            /* brightest eligible pixel, first in row-major order among equals */
+            double best = -INFINITY;
+            int64_t bx = -1, by = -1;
+            for (int64_t y = y0; y < y1; y++) {
+                for (int64_t x = x0; x < x1; x++) {
+                    if (x < m || y < m || x > W - 1 - m || y > H - 1 - m) continue;
+                    const double v = R[y * W + x];
+                    if (!(v > best)) continue;
+                    int ok = 1;
+                    for (int64_t yy = y - m; yy <= y + m && ok; yy++)
+                        for (int64_t xx = x - m; xx <= x + m; xx++)
+                            if (!isfinite(R[yy * W + xx])) { ok = 0; break; }
+                    for (int64_t yy = y - fh; yy <= y + fh && ok; yy++)
+                        for (int64_t xx = x - fh; xx <= x + fh; xx++)
+                            if (!isfinite(I[yy * W + xx])) { ok = 0; break; }
+                    if (!ok) continue;
+                    best = v; bx = x; by = y;
+                }
+            }
+            if (bx >= 0 && best > med + nsig * sgm) {
+                cx[nc] = (int32_t)bx;
+                cy[nc] = (int32_t)by;
+                nc++;
+            }
+        }
+    }
+    free(buf);
+    return nc;
+}
+
+/* Cholesky solve of the SPD system A x = b (n x n, row-major, overwritten) */
+static int chol_solve(double* A, double* b, int n) {
+    for (int j = 0; j < n; j++) {
+        double d = A[j * n + j];
+        for (int k = 0; k < j; k++) d -= A[j * n + k] * A[j * n + k];
+        if (!(d > 0.0)) return -1;
+        d = sqrt(d);
+        A[j * n + j] = d;
+        for (int i = j + 1; i < n; i++) {
+            double s = A[i * n + j];
+            for (int k = 0; k < j; k++) s -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = s / d;
+        }
+    }
+    for (int i = 0; i < n; i++) {            /* L y = b */
+        double s = b[i];
+        for (int k = 0; k < i; k++) s -= A[i * n + k] * b[k];
+        b[i] = s / A[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; i--) {       /* L' x = y */
+        double s = b[i];
+        for (int k = i + 1; k < n; k++) s -= A[k * n + i] * b[k];
+        b[i] = s / A[i * n + i];
+    }
+    return 0;
+}
+
+/* coef: [nb * ns] kernel coefficients c_{n,s} (n outer), then [nbg] background d_b */
+int orc_sub_fit(const float* I, const float* R, int64_t W, int64_t H, const int32_t* cx, const int32_t* cy,
+                int32_t nc, int32_t hw, int32_t fh, const double* sig, const int32_t* deg, int32_t nk, int32_t sord,
+                int32_t bord, double* coef) {
+    if (nc < 1 || sord < 0 || bord < -1) return ORC_INVALID_ARG;
+    const int S = 2 * hw + 1, nb = sub_nbasis(deg, nk), ns = sub_nterms(sord), ng = bord >= 0 ? sub_nterms(bord) : 0;
+    const int np = nb * ns + ng;
+    double* K = (double*)malloc(sizeof(double) * (size_t)nb * S * S);
+    if (orc_sub_basis(hw, sig, deg, nk, K) != nb) { free(K); return ORC_INVALID_ARG; }
+    double* AtA = (double*)calloc((size_t)np * np, sizeof(double));
+    double* Atb = (double*)calloc((size_t)np, sizeof(double));
+    double* row = (double*)malloc(sizeof(double) * (size_t)np);
+    double* C = (double*)malloc(sizeof(double) * (size_t)nb);
+    double Ps[64], Pb[64];
+    for (int c = 0; c < nc; c++) {
+        sub_terms((double)cx[c], (double)cy[c], W, H, sord, Ps);
+        for (int dv = -fh; dv <= fh; dv++) {
+            for (int du = -fh; du <= fh; du++) {
+                const int64_t x = cx[c] + du, y = cy[c] + dv;
+                for (int n = 0; n < nb; n++) {            /* (R (x) K_n)(x, y) */
+                    double s = 0.0;
+                    for (int v = -hw; v <= hw; v++)
+                        for (int u = -hw; u <= hw; u++)
+                            s += K[(int64_t)n * S * S + (v + hw) * S + (u + hw)] * (double)R[(y - v) * W + (x - u)];
+                    C[n] = s;
+                }
+                for (int n = 0; n < nb; n++)
+                    for (int t = 0; t < ns; t++) row[n * ns + t] = C[n] * Ps[t];
+                if (ng) {
+                    sub_terms((double)x, (double)y, W, H, bord, Pb);
+                    for (int t = 0; t < ng; t++) row[nb * ns + t] = -Pb[t];
+                }
+                const double target = I[y * W + x];
+                for (int a = 0; a < np; a++) {
+                    Atb[a] += row[a] * target;
+                    for (int b = 0; b <= a; b++) AtA[a * np + b] += row[a] * row[b];
+                }
+            }
+        }
+    }
+    for (int a = 0; a < np; a++)
+        for (int b = a + 1; b < np; b++) AtA[a * np + b] = AtA[b * np + a];
+    const int e = chol_solve(AtA, Atb, np);
+    if (!e) memcpy(coef, Atb, sizeof(double) * (size_t)np);
+    free(K); free(AtA); free(Atb); free(row); free(C);
+    return e ? ORC_INVALID_ARG : ORC_OK;
+}
+
+int orc_sub_apply(const float* I, const float* R, int64_t W, int64_t H, int32_t hw, const double* sig,
+                  const int32_t* deg, int32_t nk, int32_t sord, int32_t bord, const double* coef, int32_t tile,
+                  double* D) {
+    if (tile < 1) return ORC_INVALID_ARG;
+    const int S = 2 * hw + 1, nb = sub_nbasis(deg, nk), ns = sub_nterms(sord), ng = bord >= 0 ? sub_nterms(bord) : 0;
+    double* K = (double*)malloc(sizeof(double) * (size_t)nb * S * S);
+    if (orc_sub_basis(hw, sig, deg, nk, K) != nb) { free(K); return ORC_INVALID_ARG; }
+    double* Kt = (double*)malloc(sizeof(double) * (size_t)S * S);
+    double Ps[64], Pb[64];
+    const int64_t ntx = (W + tile - 1) / tile, nty = (H + tile - 1) / tile;
+    for (int64_t ty = 0; ty < nty; ty++) {
+        for (int64_t tx = 0; tx < ntx; tx++) {
+            /* Eq. 8 at the tile centre */
+            sub_terms((double)(tx * tile) + 0.5 * (tile - 1), (double)(ty * tile) + 0.5 * (tile - 1), W, H, sord, Ps);
+            for (int k = 0; k < S * S; k++) Kt[k] = 0.0;
+            for (int n = 0; n < nb; n++) {
+                double a = 0.0;
+                for (int t = 0; t < ns; t++) a += coef[n * ns + t] * Ps[t];
+                for (int k = 0; k < S * S; k++) Kt[k] += a * K[(int64_t)n * S * S + k];
+            }
+            for (int64_t y = ty * tile; y < (ty + 1) * tile && y < H; y++) {
+                for (int64_t x = tx * tile; x < (tx + 1) * tile && x < W; x++) {
+                    if (x < hw || y < hw || x > W - 1 - hw || y > H - 1 - hw) { D[y * W + x] = NAN; continue; }
+                    double s = 0.0;
+                    for (int v = -hw; v <= hw; v++)
+                        for (int u = -hw; u <= hw; u++)
+                            s += Kt[(v + hw) * S + (u + hw)] * (double)R[(y - v) * W + (x - u)];
+                    double b = 0.0;
+                    if (ng) {
+                        sub_terms((double)x, (double)y, W, H, bord, Pb);
+                        for (int t = 0; t < ng; t++) b += coef[nb * ns + t] * Pb[t];
+                    }
+                    D[y * W + x] = (double)I[y * W + x] + b - s;
+                }
+            }
+        }
+    }
+    free(K); free(Kt);
     return ORC_OK;
 }

@@ -102,7 +102,7 @@ int orc_gray_transform(const float* img, int64_t W, int64_t H, int32_t kind, dou
                        double a, double* out);
 int orc_hist_equalize(const float* img, int64_t W, int64_t H, int32_t nbins, double* out);
 
-/* Image alignment (Sec. 2.2.3, Eqs. 1-3).  SIP coefficient a[p*6+q] multiplies
+/* Image alignment (Sec. 2.2.3, Eqs. 5-7).  SIP coefficient a[p*6+q] multiplies
  * u^p v^q, p + q <= order <= 5; crpix 1-based; crval and cd in degrees. */
 typedef struct {
     double crpix[2];
@@ -125,7 +125,7 @@ int orc_reproject_affine(const float* src, int64_t W, int64_t H, const double* M
 int orc_zscale(const float* img, int64_t W, int64_t H, int32_t n_samples, double contrast, double krej,
                int32_t max_iter, double* z, int32_t* counts);
 
-/* Deblending (Sec. 2.2.4): multi-level thresholds, sub-component tree, pruning
+/* Deblending (Sec. 2.2.5): multi-level thresholds, sub-component tree, pruning
  * on intensity (mincont), remaining pixels to the likeliest object; objects
  * numbered candidate by candidate, within one in raster order of their first
  * pixel.  Returns K'. */

@@ -1,14 +1,14 @@
 // align.cu -- image alignment of Sec. 2.2.3: coordinate mapping of a source
-// frame into a target frame through both frames' WCS (Eqs. 1-3 and the inverse
+// frame into a target frame through both frames' WCS (Eqs. 5-7 and the inverse
 // chain), the partial affine (similarity) estimate, and bilinear reprojection.
 //
-// Mapping, per node in FP64: SIP offsets (Eq. 1), CD (Eq. 2), then the gnomonic
+// Mapping, per node in FP64: SIP offsets (Eq. 5), CD (Eq. 6), then the gnomonic
 // deprojection about the source tangent point followed by the projection about
 // the target's.  The two are composed as one rotation: the point (p, q) of the
 // source tangent plane is the direction p e + q n + c of the source's east,
 // north and centre unit vectors, and its target standard coordinates are
 // (R0 . w, R1 . w) / (R2 . w) with R the target basis expressed in the source
-// basis -- the same mathematics as Eq. 3 and its inverse without a
+// basis -- the same mathematics as Eq. 7 and its inverse without a
 // trigonometric call per node.  Then CD^-1 and Newton's method on the target's
 // SIP polynomial (at most 50 steps, stop below 1e-12 px; otherwise NaN).
 //
@@ -91,14 +91,14 @@ __global__ void __launch_bounds__(AL_T) k_wcs_map(WcsDev src, WcsDev tgt, int64_
     const int64_t n = nx * ny;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = k / nx, j = k - i * nx;
-        // Eq. 1 on the source (FITS pixel = 0-based + 1)
+        // Eq. 5 on the source (FITS pixel = 0-based + 1)
         const double u = (double)(j * step) + 1.0 - src.crpix[0], v = (double)(i * step) + 1.0 - src.crpix[1];
         const double xi = u + sip_val(src.a, src.a_order, u, v);
         const double eta = v + sip_val(src.b, src.b_order, u, v);
-        // Eq. 2, radians
+        // Eq. 6, radians
         const double p = (src.cd[0] * xi + src.cd[1] * eta) * AL_D2R;
         const double q = (src.cd[2] * xi + src.cd[3] * eta) * AL_D2R;
-        // Eq. 3 and the target's gnomonic projection, composed
+        // Eq. 7 and the target's gnomonic projection, composed
         const double X = R[0] * p + R[1] * q + R[2];
         const double Y = R[3] * p + R[4] * q + R[5];
         const double Z = R[6] * p + R[7] * q + R[8];

@@ -1,4 +1,4 @@
-// deblend.cu -- deblending of the detected candidates (Sec. 2.2.4: multi-level
+// deblend.cu -- deblending of the detected candidates (Sec. 2.2.5: multi-level
 // thresholds between a candidate's threshold and its peak, a tree of the
 // sub-components found at each level, traversed bottom-up and pruned on
 // intensity).  Reading of the steps:

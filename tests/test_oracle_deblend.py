@@ -1,4 +1,4 @@
-"""Pins of the oracle's deblending (Sec. 2.2.4: multi-level thresholds between a
+"""Pins of the oracle's deblending (Sec. 2.2.5: multi-level thresholds between a
 candidate's threshold and its peak, a tree of sub-components, pruning on
 intensity; the stated reading for the levels, the pruning rule and the
 assignment of the remaining pixels) against scenes whose answer is fixed by
