@@ -67,7 +67,7 @@ def _reproject_check(orc, img, Mi, Wo, Ho, g, fill):
     return int(inside.sum())
 
 
-pytest.mark.parametrize("W,H,step", [(4096, 4096, 64), (517, 389, 1), (1001, 77, 7)])
+@pytest.mark.parametrize("W,H,step", [(4096, 4096, 64), (517, 389, 1), (1001, 77, 7)])
 def test_wcs_map_parity(gpu, orc, W, H, step):
     src, tgt = synth.wcs_pair(W, H, seed=7000 + step)
     gx, gy = gpu.wcs_map(src, tgt, W, H, step=step)
@@ -122,7 +122,7 @@ def test_affine_fit_parity(gpu, orc):
     assert int(host(st)[0]) == gpu._abi.IPP_ERR_DEGENERATE
 
 
-pytest.mark.parametrize("case", ["rotation", "ragged_views", "nan_fill"])
+@pytest.mark.parametrize("case", ["rotation", "ragged_views", "nan_fill"])
 def test_reproject_parity(gpu, orc, case):
     img, _ = synth.tiny_frame(517, 389, 91, n_stars=50, sky=300.0, flux=(3.0, 4.5))
     th, s = 0.6 * math.pi / 180.0, 1.0003
@@ -166,7 +166,7 @@ def test_reproject_exact_cases(gpu):
         gpu.reproject_affine(d, ident, 75, 61, out=d)
 
 
-pytest.mark.parametrize("which", ["survey_4k"])
+@pytest.mark.parametrize("which", ["survey_4k"])
 def test_align_chain_full_size(gpu, orc, which):
     """map (step 32) -> fit -> reproject on the 4096^2 survey frame, against the
     oracle's chain on the same inputs; every output pixel compared"""

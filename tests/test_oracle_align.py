@@ -45,7 +45,7 @@ def test_reference_pixel_maps_to_crval(orc):
     assert ra[0] == pytest.approx(210.5, abs=1e-12) and de[0] == pytest.approx(-45.25, abs=1e-12)
 
 
-pytest.mark.parametrize("crval", [(0.0, 0.0), (150.0, 30.0), (300.0, -72.5), (45.0, 89.9)])
+@pytest.mark.parametrize("crval", [(0.0, 0.0), (150.0, 30.0), (300.0, -72.5), (45.0, 89.9)])
 def test_gnomonic_distance_is_atan_of_radius(orc, crval):
     """TAN projection: a point at standard-coordinate radius r (radians) lies at
     angular distance atan(r) from the tangent point, in the direction atan2(p, q)
@@ -74,7 +74,7 @@ def test_lines_through_reference_pixel_are_great_circles(orc):
     u = _unit(ra, de)
     n = np.cross(u[0], u[-1])
     n /= np.linalg.norm(n)
-    assert np.max(np.abs(u  n)) < 1e-13
+    assert np.max(np.abs(u @ n)) < 1e-13
 
 
 def test_sip_term_is_a_shift_of_the_input_pixel(orc):
@@ -92,7 +92,7 @@ def test_sip_term_is_a_shift_of_the_input_pixel(orc):
     assert np.max(_sep(r1, d1, r0, d0)) < 1e-14
 
 
-pytest.mark.parametrize("order", [0, 3, 5])
+@pytest.mark.parametrize("order", [0, 3, 5])
 def test_inverse_chain_undoes_the_forward_chain(orc, order):
     rng = np.random.default_rng(order)
     a, b = np.zeros((6, 6)), np.zeros((6, 6))
@@ -136,7 +136,7 @@ def test_affine_fit_recovers_a_similarity_and_matches_lstsq(orc):
     M, Mi = orc.affine_fit(x, y, xt, yt)
     ref = np.array([[s * math.cos(th), -s * math.sin(th), tx], [s * math.sin(th), s * math.cos(th), ty]])
     assert np.max(np.abs(M - ref)) < 1e-10
-    comp = np.vstack([Mi, [0, 0, 1]])  np.vstack([M, [0, 0, 1]])
+    comp = np.vstack([Mi, [0, 0, 1]]) @ np.vstack([M, [0, 0, 1]])
     assert np.max(np.abs(comp - np.eye(3))) < 1e-12
     # with noise: the linear least squares in (a, b, tx, ty) by numpy
     xn, yn = xt + rng.normal(0, 0.3, 500), yt + rng.normal(0, 0.3, 500)
