@@ -115,6 +115,10 @@ def lib():
             L.orc_affine_fit.argtypes = [vp, vp, vp, vp, i64, vp, vp]
             L.orc_reproject_affine.argtypes = [vp, i64, i64, vp, i64, i64, d, vp]
             L.orc_zscale.argtypes = [vp, i64, i64, i32, d, d, i32, vp, vp]
+            L.orc_sub_basis.argtypes = [i32, vp, vp, i32, vp]
+            L.orc_sub_stamps.argtypes = [vp, vp, i64, i64, i32, i32, i32, i32, d, vp, vp]
+            L.orc_sub_fit.argtypes = [vp, vp, i64, i64, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, vp]
+            L.orc_sub_apply.argtypes = [vp, vp, i64, i64, i32, vp, vp, i32, i32, i32, vp, i32, vp]
             L.orc_deblend.restype = i64
             L.orc_psf_model.argtypes = [vp, i32, i32, d, vp, vp]
             L.orc_psf_fit.argtypes = [vp, i64, i32, vp, vp, i32, d, i32, d, vp, vp, vp, vp]
@@ -437,3 +441,66 @@ def zscale(img, n_samples=1000, contrast=0.25, krej=2.5, max_iter=5):
     if e:
         raise ValueError("zscale: no finite sample or bad parameters")
     return float(z[0]), float(z[1]), (int(cnt[0]), int(cnt[1]))
+
+
+# ---- image subtraction (Sec. 2.2.4) ------------------------------------------------
+SUB_SIG = (0.7, 1.5, 3.0)   # Gaussian widths of the basis (a reading: HOTPANTS' usual set)
+SUB_DEG = (6, 4, 2)         # their polynomial degrees
+
+
+def _basis_args(sig, deg):
+    sg = np.ascontiguousarray(sig, np.float64)
+    dg = np.ascontiguousarray(deg, np.int32)
+    return sg, dg
+
+
+def sub_basis(hw=10, sig=SUB_SIG, deg=SUB_DEG):
+    """the basis kernels K_n (Eq. 9): (nb, 2 hw + 1, 2 hw + 1), rows v, columns u"""
+    sg, dg = _basis_args(sig, deg)
+    nb = int(sum((k + 1) * (k + 2) // 2 for k in deg))
+    S = 2 * hw + 1
+    out = np.zeros((nb, S, S))
+    assert lib().orc_sub_basis(hw, _p(sg), _p(dg), len(sg), _p(out)) == nb
+    return out
+
+
+def sub_stamps(img, tmpl, nsx=10, nsy=10, hw=10, fh=10, nsig=5.0):
+    """candidate stamp centres (x, y): one per region at most"""
+    img, tmpl = _f32(img), _f32(tmpl)
+    H, W = img.shape
+    cx = np.zeros(nsx * nsy, np.int32)
+    cy = np.zeros(nsx * nsy, np.int32)
+    n = lib().orc_sub_stamps(_p(img), _p(tmpl), W, H, nsx, nsy, hw, fh, float(nsig), _p(cx), _p(cy))
+    assert n >= 0
+    return cx[:n].copy(), cy[:n].copy()
+
+
+def sub_fit(img, tmpl, cx, cy, hw=10, fh=10, sig=SUB_SIG, deg=SUB_DEG, sord=2, bord=1):
+    """kernel coefficients c[n, s] (n basis, s spatial term) and background d[b]"""
+    img, tmpl = _f32(img), _f32(tmpl)
+    H, W = img.shape
+    sg, dg = _basis_args(sig, deg)
+    cx = np.ascontiguousarray(cx, np.int32)
+    cy = np.ascontiguousarray(cy, np.int32)
+    nb = int(sum((k + 1) * (k + 2) // 2 for k in deg))
+    ns = (sord + 1) * (sord + 2) // 2
+    ng = (bord + 1) * (bord + 2) // 2 if bord >= 0 else 0
+    coef = np.zeros(nb * ns + ng)
+    e = lib().orc_sub_fit(_p(img), _p(tmpl), W, H, _p(cx), _p(cy), len(cx), hw, fh, _p(sg), _p(dg), len(sg), sord,
+                          bord, _p(coef))
+    if e:
+        raise ValueError("subtraction fit: no candidate or a singular normal matrix")
+    return coef
+
+
+def sub_apply(img, tmpl, coef, hw=10, sig=SUB_SIG, deg=SUB_DEG, sord=2, bord=1, tile=21):
+    """difference image D = I + B - R (x) K (Eq. 10), NaN where the kernel
+    support leaves the frame"""
+    img, tmpl = _f32(img), _f32(tmpl)
+    H, W = img.shape
+    sg, dg = _basis_args(sig, deg)
+    c = np.ascontiguousarray(coef, np.float64)
+    D = np.zeros((H, W))
+    assert lib().orc_sub_apply(_p(img), _p(tmpl), W, H, hw, _p(sg), _p(dg), len(sg), sord, bord, _p(c), int(tile),
+                               _p(D)) == 0
+    return D

@@ -125,6 +125,17 @@ int orc_reproject_affine(const float* src, int64_t W, int64_t H, const double* M
 int orc_zscale(const float* img, int64_t W, int64_t H, int32_t n_samples, double contrast, double krej,
                int32_t max_iter, double* z, int32_t* counts);
 
+/* Image subtraction (Sec. 2.2.4, Eqs. 8-10): basis, stamps, fit, apply. */
+int orc_sub_basis(int32_t hw, const double* sig, const int32_t* deg, int32_t nk, double* out);
+int orc_sub_stamps(const float* I, const float* R, int64_t W, int64_t H, int32_t nsx, int32_t nsy, int32_t hw,
+                   int32_t fh, double nsig, int32_t* cx, int32_t* cy);
+int orc_sub_fit(const float* I, const float* R, int64_t W, int64_t H, const int32_t* cx, const int32_t* cy,
+                int32_t nc, int32_t hw, int32_t fh, const double* sig, const int32_t* deg, int32_t nk, int32_t sord,
+                int32_t bord, double* coef);
+int orc_sub_apply(const float* I, const float* R, int64_t W, int64_t H, int32_t hw, const double* sig,
+                  const int32_t* deg, int32_t nk, int32_t sord, int32_t bord, const double* coef, int32_t tile,
+                  double* D);
+
 /* Deblending (Sec. 2.2.5): multi-level thresholds, sub-component tree, pruning
  * on intensity (mincont), remaining pixels to the likeliest object; objects
  * numbered candidate by candidate, within one in raster order of their first
