@@ -431,6 +431,15 @@ def main():
     stages["hist_equalize"] = timeit(lambda k: ipp.hist_equalize(gin[k % 4], nbins=4096, out=gout[k % 4], ws=gws))
     # zscale display limits of the same frames (1000 samples, one block)
     stages["zscale"] = timeit(lambda k: ipp.zscale(gin[k % 4]))
+    # convolution and difference of image subtraction (49 basis kernels of 21 x 21,
+    # spatial order 2, background order 1): the frame against a copy of itself
+    # as the template, fixed coefficients (the fit is not part of this call)
+    sub_coef = np.zeros(49 * 6 + 3, np.float32)
+    sub_coef[0] = 1.0 / (2.0 * np.pi * 0.7 ** 2)
+    sub_coef = torch.from_numpy(sub_coef).to(dev)      # resident: no copy inside the timed calls
+    sub_ws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+    stages["sub_apply"] = timeit(
+        lambda k: ipp.sub_apply(gin[k % 4], gin[(k + 1) % 4], sub_coef, out=gout[k % 4], ws=sub_ws))
     # image alignment of the subtracted frame onto a second exposure's pixel grid
     # (a widening): WCS mapping of a 32 px node grid, partial affine fit, bilinear
     # reprojection; same four rotating input/output pairs
@@ -464,6 +473,12 @@ def main():
         gb = bpp * W * H / (stages[key] / 1e3) / 1e9
         gray[key] = {"kernels": kern, "bytes_per_px": bpp, "ms": stages[key], "achieved_gbs": gb,
                      "frac_of_measured_hbm": gb / hbm}
+    # image subtraction: 441 taps a pixel (2 flops each) plus the tile kernels
+    # (49 x 441 multiply-adds a tile); FP32 ALU-bound
+    sub_flops = 2.0 * 441 * W * H + 2.0 * 49 * 441 * ((W + 20) // 21) * ((H + 20) // 21)
+    subtraction = {"ms": stages["sub_apply"], "achieved_tflops": sub_flops / (stages["sub_apply"] / 1e3) / 1e12,
+                   "flops_per_call": sub_flops, "kernels": "k_sub_basis + k_sub_apply (one block per 21 x 21 tile)",
+                   "workload": "survey_4k subtracted frame against a copy, 21 x 21 kernel, 49 basis functions"}
     gb = 8 * W * H / (stages["reproject"] / 1e3) / 1e9
     align = {"ms": stages["align"], "reproject_ms": stages["reproject"], "reproject_bytes_per_px": 8,
              "reproject_achieved_gbs": gb, "reproject_frac_of_measured_hbm": gb / hbm,
@@ -528,7 +543,7 @@ def main():
                     "pipelining": f"each step H2D + catalog + D2H on one of {L} lane streams",
                     "d2h_bytes_per_step": 4 + 3 * 4 * nmax},
             "gpu_launches": KERNELS_PER_FRAME * args.steps,
-            "roofline": roof, "step_roofline": whole, "stages_ms": stages, "gray_maps": gray, "alignment": align,
+            "roofline": roof, "step_roofline": whole, "stages_ms": stages, "gray_maps": gray, "alignment": align, "subtraction": subtraction,
             "clocks": clk.summary(), "psf_fit": psf, "batched": batch, "raw_u16_stream": raw,
             "cpu_baseline": cpu,
         }

@@ -511,6 +511,34 @@ int ipp_zscale(const float* img, int64_t W, int64_t H, int64_t pitch, const ipp_
                int32_t* counts_out, void* stream);
 
 /*
+ * ipp_sub_apply -- the convolution and difference of image subtraction
+ * (Sec. 2.2.4, HOTPANTS-style; Eqs. 8-10), the paper's dominant cost.  Given the
+ * fitted coefficients, the kernel of each (2 hw + 1)^2 output tile is
+ *   K(u, v) = sum_n a_n(xc, yc) K_n(u, v),  a_n = sum_s c[n * ns + s] P_s (Eq. 8),
+ *   K_n(u, v) = exp(-(u^2 + v^2) / (2 sig_k^2)) u^i v^j  (Eq. 9; Gaussian k outer,
+ *   then i, then j, i + j <= deg_k; u and v the offsets in x and y),
+ * at the tile's centre (xc, yc); P_s are xs^p ys^q (p outer, p + q <= sord) of
+ * xs = 2x / (W - 1) - 1, ys = 2y / (H - 1) - 1.  The difference (the residual of
+ * Eq. 10, read as I + B = R (x) K) is
+ *   D(x, y) = I(x, y) + B(x, y) - sum_{u,v} K(u, v) R(x - u, y - v),
+ *   B = sum_b c[nb * ns + b] P_b(x, y) (order bord; none when bord = -1),
+ * NaN where the kernel's support leaves the frame.  FP32 arithmetic.
+ *   I, R      device float, W x H, rows of `pitch` elements (the same for both)
+ *   coef      device float[nb * ns + nb_bg]: kernel coefficients, then background
+ *   sig, deg  host arrays of nk (1..8) Gaussian widths (> 0) and degrees (0..8);
+ *             nb = sum (deg_k + 1)(deg_k + 2) / 2 <= 64
+ *   hw        kernel half width: 4, 6, 8, 10 or 12 (NOT_SUPPORTED otherwise)
+ *   D         device float, rows of `out_pitch` (>= W); must not alias I or R
+ *   ws        device workspace of ipp_sub_apply_workspace_size() bytes (the basis)
+ * Errors: INVALID_ARG for NULL pointers, bad sizes, orders (sord 0..4, bord
+ * -1..4) or basis descriptions; NOT_SUPPORTED for another hw.
+ */
+size_t ipp_sub_apply_workspace_size(int32_t hw, int32_t nk, const int32_t* deg);
+int ipp_sub_apply(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int32_t hw, int32_t nk,
+                  const float* sig, const int32_t* deg, const float* coef, int32_t sord, int32_t bord, float* D,
+                  int64_t out_pitch, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * ipp_stamp_cut -- S x S stamps of the subtracted frame around each source, the
  * input of the PSF fit (the paper fits no PSF; this cut is part of that
  * paper-silent reading of Sec. 2.2.5's photometry).  For source s < min(*n_src_dev,

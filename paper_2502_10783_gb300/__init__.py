@@ -25,7 +25,7 @@ from ._abi import (  # noqa: F401
 )
 
 __all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "deblend", "stamp_cut", "Batch",
-           "gray_transform", "hist_equalize", "zscale", "wcs_map", "affine_fit", "reproject_affine", "align",
+           "gray_transform", "hist_equalize", "zscale", "sub_apply", "wcs_map", "affine_fit", "reproject_affine", "align",
            "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
 
 
@@ -274,6 +274,39 @@ def gray_transform(img, kind, lo, hi, a=1000.0, out=None):
     _frame2d(out, "out")
     _abi.check("ipp_gray_transform", L.ipp_gray_transform(
         _ptr(img), W, H, img.stride(0), int(kind), float(lo), float(hi), float(a), _ptr(out), out.stride(0),
+        _stream()))
+    return out
+
+
+def sub_apply(img, tmpl, coef, hw=10, sig=(0.7, 1.5, 3.0), deg=(6, 4, 2), sord=2, bord=1, out=None, ws=None):
+    """Difference image D = I + B - R (x) K of image subtraction (ipp_sub_apply):
+    the kernel of each (2 hw + 1)^2 tile from the coefficients `coef` (kernel
+    terms c[n, s], then background terms), evaluated at the tile's centre."""
+    L = load()
+    _frame2d(img, "img")
+    _frame2d(tmpl, "tmpl")
+    if tmpl.shape != img.shape or tmpl.stride(0) != img.stride(0):
+        raise TypeError("img and tmpl must have the same shape and row pitch")
+    H, W = img.shape
+    sg = np.ascontiguousarray(sig, np.float32)
+    dg = np.ascontiguousarray(deg, np.int32)
+    need = L.ipp_sub_apply_workspace_size(int(hw), len(dg), dg.ctypes.data_as(C.c_void_p))
+    if need == 0:
+        raise ValueError("bad basis description")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    nb = sum((int(d) + 1) * (int(d) + 2) // 2 for d in dg)
+    nterm = nb * (sord + 1) * (sord + 2) // 2 + ((bord + 1) * (bord + 2) // 2 if bord >= 0 else 0)
+    c = torch.as_tensor(np.asarray(coef, np.float32) if not isinstance(coef, torch.Tensor) else coef,
+                        dtype=torch.float32, device=img.device).contiguous()
+    if c.numel() < nterm:
+        raise ValueError(f"coef holds {c.numel()} values, the basis and orders need {nterm}")
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    _frame2d(out, "out")
+    _abi.check("ipp_sub_apply", L.ipp_sub_apply(
+        _ptr(img), _ptr(tmpl), W, H, img.stride(0), int(hw), len(dg), sg.ctypes.data_as(C.c_void_p),
+        dg.ctypes.data_as(C.c_void_p), _ptr(c), int(sord), int(bord), _ptr(out), out.stride(0), _ptr(ws), ws.numel(),
         _stream()))
     return out
 

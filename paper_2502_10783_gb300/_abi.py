@@ -112,6 +112,8 @@ PROTOTYPES = {
     "ipp_affine_fit": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, sz, vp], i32),
     "ipp_reproject_affine": ([vp, i64, i64, i64, vp, i64, i64, f32, vp, i64, vp], i32),
     "ipp_zscale": ([vp, i64, i64, i64, C.POINTER(ZscaleParams), vp, vp, vp], i32),
+    "ipp_sub_apply_workspace_size": ([i32, i32, vp], sz),
+    "ipp_sub_apply": ([vp, vp, i64, i64, i64, i32, i32, vp, vp, vp, i32, i32, vp, i64, vp, sz, vp], i32),
     "ipp_gray_transform": ([vp, i64, i64, i64, i32, f32, f32, f32, vp, i64, vp], i32),
     "ipp_hist_equalize_workspace_size": ([i32], sz),
     "ipp_hist_equalize": ([vp, i64, i64, i64, i32, vp, i64, vp, sz, vp], i32),

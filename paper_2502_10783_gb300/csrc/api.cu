@@ -279,6 +279,43 @@ extern "C" int ipp_deblend(const float* sub, const int32_t* labels, int64_t W, i
     return ipp_launch_deblend(J, (cudaStream_t)stream);
 }
 
+// ---- image subtraction -----------------------------------------------------------------
+static int sub_nb(int32_t nk, const int32_t* deg) {
+    int nb = 0;
+    for (int k = 0; k < nk; k++) nb += (deg[k] + 1) * (deg[k] + 2) / 2;
+    return nb;
+}
+
+extern "C" size_t ipp_sub_apply_workspace_size(int32_t hw, int32_t nk, const int32_t* deg) {
+    if (hw < 1 || nk < 1 || nk > 8 || !deg) return 0;
+    for (int k = 0; k < nk; k++)
+        if (deg[k] < 0 || deg[k] > 8) return 0;
+    return ipp_sub_ws_bytes(sub_nb(nk, deg), hw);
+}
+
+extern "C" int ipp_sub_apply(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int32_t hw,
+                             int32_t nk, const float* sig, const int32_t* deg, const float* coef, int32_t sord,
+                             int32_t bord, float* D, int64_t out_pitch, void* ws, size_t ws_bytes, void* stream) {
+    if (int e = check_frame(I, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(R && coef && D && ws && sig && deg, "NULL pointer");
+    REQUIRE(out_pitch >= W, "out_pitch < W");
+    REQUIRE((const void*)D != (const void*)I && (const void*)D != (const void*)R, "D must not alias I or R");
+    REQUIRE(nk >= 1 && nk <= 8, "nk must be 1..8");
+    for (int k = 0; k < nk; k++)
+        REQUIRE(deg[k] >= 0 && deg[k] <= 8 && sig[k] > 0.f && std::isfinite(sig[k]), "bad basis description");
+    const int nb = sub_nb(nk, deg);
+    REQUIRE(nb <= 64, "more than 64 basis functions");
+    REQUIRE(sord >= 0 && sord <= 4 && bord >= -1 && bord <= 4, "spatial order 0..4, background order -1..4");
+    REQUIRE(((W + 2 * hw) / (2 * hw + 1)) * ((H + 2 * hw) / (2 * hw + 1)) < (int64_t(1) << 31),
+            "frame too large (tiles)");
+    if (hw != 4 && hw != 6 && hw != 8 && hw != 10 && hw != 12)
+        return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "kernel half width %d (built: 4, 6, 8, 10, 12)", hw);
+    REQUIRE(ws_bytes >= ipp_sub_ws_bytes(nb, hw) && ((uintptr_t)ws & 15) == 0, "workspace too small or misaligned");
+    const int ns = (sord + 1) * (sord + 2) / 2;
+    return ipp_launch_sub_apply(I, R, W, H, pitch, hw, nk, sig, deg, nb, coef, sord, coef + (size_t)nb * ns, bord,
+                                D, out_pitch, ws, (cudaStream_t)stream);
+}
+
 // ---- image alignment -------------------------------------------------------------------
 static int check_wcs(const ipp_wcs* w, bool need_inverse) {
     REQUIRE(w, "wcs NULL");

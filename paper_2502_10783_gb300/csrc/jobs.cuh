@@ -171,6 +171,10 @@ int ipp_launch_psf_fit(const ipp::FitJob& J, cudaStream_t s);
 int ipp_launch_gray(const float* img, int64_t W, int64_t H, int64_t pitch, int kind, float lo, float hi, float a,
                     float* out, int64_t opitch, cudaStream_t s);
 size_t ipp_equalize_ws_bytes(int nbins);
+size_t ipp_sub_ws_bytes(int nb, int hw);
+int ipp_launch_sub_apply(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int hw, int nk,
+                         const float* sig, const int* deg, int nb, const float* cs, int sord, const float* cb,
+                         int bord, float* D, int64_t opitch, void* ws, cudaStream_t s);
 int ipp_launch_zscale(const float* img, int64_t W, int64_t H, int64_t pitch, int ns, double contrast, double krej,
                       int max_iter, double* z, int32_t* counts, cudaStream_t s);
 int ipp_launch_wcs_map(const ipp_wcs& src, const ipp_wcs& tgt, int64_t nx, int64_t ny, int step, double* xo,
