@@ -95,6 +95,7 @@ def lib():
             L.orc_keys_weight.argtypes = [d]
             L.orc_keys_weight.restype = d
             L.orc_interp_map.argtypes = [vp, i64, i64, i32, i32, i64, i64, vp]
+            L.orc_spline_map.argtypes = [vp, i64, i64, i32, i32, i64, i64, vp]
             L.orc_bg_subtract.argtypes = [vp, i64, i64, i64, vp, i64, i64, i32, i32, vp, vp]
             L.orc_threshold.argtypes = [vp, i64, i64, vp, i64, i64, i32, i32, d, d, vp]
             L.orc_threshold_filtered.argtypes = [vp, i64, i64, vp, i64, i64, i32, i32, d, d, vp]
@@ -183,6 +184,15 @@ def bg_estimate(img, mask=None, **kw):
     fs = kw.get("filter_size", 3)
     b, r = fill_filter(st["raw_bkg"], st["raw_rms"], st["valid"], fs)
     return b.astype(np.float32), r.astype(np.float32), st
+
+
+def spline_map(mesh, mesh_w, W, H, mesh_h=None):
+    """natural-spline background map of the node grid (W x H, FP64)"""
+    mesh = _f32(mesh)
+    ny, nx = mesh.shape
+    out = np.zeros((H, W))
+    assert lib().orc_spline_map(_p(mesh), nx, ny, mesh_w, mesh_h or mesh_w, W, H, _p(out)) == 0
+    return out
 
 
 def keys_weight(s):

@@ -1757,3 +1757,72 @@ int orc_sub_apply(const float* I, const float* R, int64_t W, int64_t H, int32_t 
     free(K); free(Kt);
     return ORC_OK;
 }
+
+/* ---------------------------------------------------------------------------
+ * Natural-spline background map (Sec. 2.2.2 scales the filtered mesh back to
+ * full resolution by spline interpolation; the Keys cubic above is the default
+ * reading, this is the natural cubic spline variant).  Tensor product of 1-D
+ * natural cubic splines through the mesh nodes (node (p, q) at pixel
+ * ((q + 1/2) mesh_w - 1/2, (p + 1/2) mesh_h - 1/2), unit spacing in node
+ * coordinates): second derivatives zero at the end nodes, interior ones from
+ * M_{k-1} + 4 M_k + M_{k+1} = 6 (y_{k+1} - 2 y_k + y_{k-1}) (Thomas algorithm);
+ * beyond the end nodes the spline continues as the line with the end slope (the
+ * natural spline's C2 extension).  First along x through each node row, then
+ * along y through those values for each pixel column.
+ * ------------------------------------------------------------------------- */
+static void nspline_m(const double* y, int64_t n, double* M, double* c) {
+    /* M[0] = M[n-1] = 0; c: scratch of n doubles */
+    for (int64_t k = 0; k < n; k++) M[k] = 0.0;
+    if (n < 3) return;
+    /* forward sweep on rows k = 1 .. n-2: M_{k-1} + 4 M_k + M_{k+1} = r_k */
+    double prev_c = 0.0, prev_d = 0.0;
+    for (int64_t k = 1; k <= n - 2; k++) {
+        const double r = 6.0 * (y[k + 1] - 2.0 * y[k] + y[k - 1]);
+        const double den = 4.0 - (k > 1 ? prev_c : 0.0);
+        const double ck = 1.0 / den;
+        const double dk = (r - (k > 1 ? prev_d : 0.0)) / den;
+        c[k] = ck;
+        M[k] = dk;
+        prev_c = ck;
+        prev_d = dk;
+    }
+    for (int64_t k = n - 3; k >= 1; k--) M[k] -= c[k] * M[k + 1];
+}
+
+static double nspline_eval(const double* y, const double* M, int64_t n, double u) {
+    if (n == 1) return y[0];
+    if (u < 0.0) {
+        const double d0 = (y[1] - y[0]) - (2.0 * M[0] + M[1]) / 6.0;
+        return y[0] + u * d0;
+    }
+    if (u > (double)(n - 1)) {
+        const double d1 = (y[n - 1] - y[n - 2]) + (M[n - 2] + 2.0 * M[n - 1]) / 6.0;
+        return y[n - 1] + (u - (double)(n - 1)) * d1;
+    }
+    int64_t k = (int64_t)floor(u);
+    if (k > n - 2) k = n - 2;
+    const double b = u - (double)k, a = 1.0 - b;
+    return a * y[k] + b * y[k + 1] + ((a * a * a - a) * M[k] + (b * b * b - b) * M[k + 1]) / 6.0;
+}
+
+int orc_spline_map(const float* mesh, int64_t nx, int64_t ny, int32_t mesh_w, int32_t mesh_h, int64_t W, int64_t H,
+                   double* out) {
+    if (!mesh || !out || nx < 1 || ny < 1 || mesh_w < 1 || mesh_h < 1) return ORC_INVALID_ARG;
+    double* rows = (double*)malloc(sizeof(double) * (size_t)(ny * W));   /* row p at each pixel column */
+    const int64_t nm = nx > ny ? nx : ny;
+    double* y = (double*)malloc(sizeof(double) * (size_t)nm);
+    double* M = (double*)malloc(sizeof(double) * (size_t)nm);
+    double* c = (double*)malloc(sizeof(double) * (size_t)nm);
+    for (int64_t p = 0; p < ny; p++) {
+        for (int64_t q = 0; q < nx; q++) y[q] = mesh[p * nx + q];
+        nspline_m(y, nx, M, c);
+        for (int64_t j = 0; j < W; j++) rows[p * W + j] = nspline_eval(y, M, nx, ((double)j + 0.5) / mesh_w - 0.5);
+    }
+    for (int64_t j = 0; j < W; j++) {
+        for (int64_t p = 0; p < ny; p++) y[p] = rows[p * W + j];
+        nspline_m(y, ny, M, c);
+        for (int64_t i = 0; i < H; i++) out[i * W + j] = nspline_eval(y, M, ny, ((double)i + 0.5) / mesh_h - 0.5);
+    }
+    free(rows); free(y); free(M); free(c);
+    return ORC_OK;
+}
