@@ -116,6 +116,8 @@ def lib():
             L.orc_affine_fit.argtypes = [vp, vp, vp, vp, i64, vp, vp]
             L.orc_reproject_affine.argtypes = [vp, i64, i64, vp, i64, i64, d, vp]
             L.orc_zscale.argtypes = [vp, i64, i64, i32, d, d, i32, vp, vp]
+            L.orc_clean.argtypes = [vp, vp, i64, i64, i64, vp, d, vp]
+            L.orc_clean.restype = i64
             L.orc_sub_basis.argtypes = [i32, vp, vp, i32, vp]
             L.orc_sub_stamps.argtypes = [vp, vp, i64, i64, i32, i32, i32, i32, d, vp, vp]
             L.orc_sub_fit.argtypes = [vp, vp, i64, i64, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, vp]
@@ -514,3 +516,15 @@ def sub_apply(img, tmpl, coef, hw=10, sig=SUB_SIG, deg=SUB_DEG, sord=2, bord=1, 
     assert lib().orc_sub_apply(_p(img), _p(tmpl), W, H, hw, _p(sg), _p(dg), len(sg), sord, bord, _p(c), int(tile),
                                _p(D)) == 0
     return D
+
+
+def clean(sub, labels, nobj, thr, beta=1.0):
+    """cleaned label map and object count (SExtractor-style cleaning)"""
+    sub = _f32(sub)
+    labels = np.ascontiguousarray(labels, np.int32)
+    H, W = sub.shape
+    thr = np.ascontiguousarray(np.broadcast_to(np.asarray(thr, np.float32), (H, W)))
+    out = np.zeros((H, W), np.int32)
+    k = lib().orc_clean(_p(sub), _p(labels), W, H, int(nobj), _p(thr), float(beta), _p(out))
+    assert k >= 0
+    return out, int(k)

@@ -1826,3 +1826,102 @@ int orc_spline_map(const float* mesh, int64_t nx, int64_t ny, int32_t mesh_w, in
     free(rows); free(y); free(M); free(c);
     return ORC_OK;
 }
+
+/* ---------------------------------------------------------------------------
+ * Cleaning of the deblended objects (Sec. 2.2.5: each object is tested
+ * against its neighbours and merged when it does not stand out from them).
+ * Reading after SExtractor's cleaning:
+ *   per object, from its pixels (sub values f): the peak (largest f, first in
+ *     raster order), the barycentre and second moments weighted by max(f, 0)
+ *     (1/12 added to x2 and y2 when x2 y2 - xy^2 < 1/144; a footprint with no
+ *     positive pixel takes its unweighted centre, x2 = y2 = 1/12, xy = 0);
+ *   model of object j: an elliptical Moffat profile peak_j (1 + r^2 / a^2)^-beta,
+ *     r^2 = (y2 dx^2 - 2 xy dx dy + x2 dy^2) / (x2 y2 - xy^2) about its
+ *     barycentre, a = sqrt(2 ln 2) / sqrt(2^(1/beta) - 1) so that its FWHM is the
+ *     FWHM of the Gaussian with the object's moments;
+ *   object i is spurious when its peak value minus the models of every brighter
+ *     object (larger peak; equal peaks: smaller label) at i's peak pixel is
+ *     below the detection threshold there; it is merged into the brighter
+ *     object whose model is largest there (ties: smaller label), following
+ *     merges to an object that is kept;
+ *   kept objects are renumbered 1.. in the order of their labels.
+ * ------------------------------------------------------------------------- */
+int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t nobj, const float* thr,
+                  double beta, int32_t* out) {
+    if (!(beta > 0.0) || nobj < 0) return -1;
+    const int64_t n = nobj;
+    double *sw = calloc(n + 1, sizeof(double)), *sx = calloc(n + 1, sizeof(double)), *sy = calloc(n + 1, sizeof(double));
+    double *sxx = calloc(n + 1, sizeof(double)), *syy = calloc(n + 1, sizeof(double)), *sxy = calloc(n + 1, sizeof(double));
+    double *ux = calloc(n + 1, sizeof(double)), *uy = calloc(n + 1, sizeof(double)), *cnt = calloc(n + 1, sizeof(double));
+    double* pk = malloc(sizeof(double) * (n + 1));
+    int64_t* pidx = malloc(sizeof(int64_t) * (n + 1));
+    for (int64_t k = 0; k <= n; k++) { pk[k] = -INFINITY; pidx[k] = -1; }
+    for (int64_t i = 0; i < H; i++) {
+        for (int64_t j = 0; j < W; j++) {
+            const int32_t l = labels[i * W + j];
+            if (l <= 0 || l > n) continue;
+            const double f = sub[i * W + j];
+            if (f > pk[l]) { pk[l] = f; pidx[l] = i * W + j; }
+            cnt[l] += 1.0; ux[l] += j; uy[l] += i;
+            if (f > 0.0) { sw[l] += f; sx[l] += f * j; sy[l] += f * i; }
+        }
+    }
+    double *cx = malloc(sizeof(double) * (n + 1)), *cy = malloc(sizeof(double) * (n + 1));
+    double *x2 = malloc(sizeof(double) * (n + 1)), *y2 = malloc(sizeof(double) * (n + 1)), *xy = malloc(sizeof(double) * (n + 1));
+    for (int64_t l = 1; l <= n; l++) {
+        if (sw[l] > 0.0) { cx[l] = sx[l] / sw[l]; cy[l] = sy[l] / sw[l]; }
+        else if (cnt[l] > 0.0) { cx[l] = ux[l] / cnt[l]; cy[l] = uy[l] / cnt[l]; }
+        else { cx[l] = cy[l] = 0.0; }
+    }
+    for (int64_t i = 0; i < H; i++) {
+        for (int64_t j = 0; j < W; j++) {
+            const int32_t l = labels[i * W + j];
+            if (l <= 0 || l > n) continue;
+            const double f = sub[i * W + j];
+            if (!(f > 0.0)) continue;
+            const double dx = j - cx[l], dy = i - cy[l];
+            sxx[l] += f * dx * dx; syy[l] += f * dy * dy; sxy[l] += f * dx * dy;
+        }
+    }
+    for (int64_t l = 1; l <= n; l++) {
+        if (sw[l] > 0.0) {
+            x2[l] = sxx[l] / sw[l]; y2[l] = syy[l] / sw[l]; xy[l] = sxy[l] / sw[l];
+            if (x2[l] * y2[l] - xy[l] * xy[l] < 1.0 / 144.0) { x2[l] += 1.0 / 12.0; y2[l] += 1.0 / 12.0; }
+        } else {
+            x2[l] = y2[l] = 1.0 / 12.0; xy[l] = 0.0;
+        }
+    }
+    const double a2 = 2.0 * log(2.0) / (pow(2.0, 1.0 / beta) - 1.0);
+    int64_t* into = malloc(sizeof(int64_t) * (n + 1));
+    for (int64_t i = 1; i <= n; i++) {
+        into[i] = i;
+        if (pidx[i] < 0) continue;
+        const double px = (double)(pidx[i] % W), py = (double)(pidx[i] / W);
+        double sum = 0.0, best = -1.0;
+        int64_t bj = -1;
+        for (int64_t j = 1; j <= n; j++) {
+            if (j == i || pidx[j] < 0) continue;
+            if (!(pk[j] > pk[i] || (pk[j] == pk[i] && j < i))) continue;
+            const double dx = px - cx[j], dy = py - cy[j];
+            const double det = x2[j] * y2[j] - xy[j] * xy[j];
+            const double r2 = (y2[j] * dx * dx - 2.0 * xy[j] * dx * dy + x2[j] * dy * dy) / det;
+            const double m = pk[j] * pow(1.0 + r2 / a2, -beta);
+            sum += m;
+            if (m > best) { best = m; bj = j; }
+        }
+        if (bj > 0 && pk[i] - sum < (double)thr[pidx[i]]) into[i] = bj;
+    }
+    /* follow merges to a kept object (targets are strictly brighter: no cycle) */
+    int64_t* root = malloc(sizeof(int64_t) * (n + 1));
+    for (int64_t i = 1; i <= n; i++) { int64_t r = i; while (into[r] != r) r = into[r]; root[i] = r; }
+    int64_t* num = calloc(n + 1, sizeof(int64_t));
+    int64_t k = 0;
+    for (int64_t i = 1; i <= n; i++) if (root[i] == i) num[i] = ++k;
+    for (int64_t p = 0; p < W * H; p++) {
+        const int32_t l = labels[p];
+        out[p] = (l <= 0 || l > n) ? 0 : (int32_t)num[root[l]];
+    }
+    free(sw); free(sx); free(sy); free(sxx); free(syy); free(sxy); free(ux); free(uy); free(cnt);
+    free(pk); free(pidx); free(cx); free(cy); free(x2); free(y2); free(xy); free(into); free(root); free(num);
+    return k;
+}

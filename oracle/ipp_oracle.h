@@ -129,6 +129,11 @@ int orc_reproject_affine(const float* src, int64_t W, int64_t H, const double* M
 int orc_zscale(const float* img, int64_t W, int64_t H, int32_t n_samples, double contrast, double krej,
                int32_t max_iter, double* z, int32_t* counts);
 
+/* Cleaning of deblended objects (Sec. 2.2.5; SExtractor-style reading):
+ * returns the number of kept objects, out = cleaned label map. */
+int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t nobj, const float* thr,
+                  double beta, int32_t* out);
+
 /* Image subtraction (Sec. 2.2.4, Eqs. 8-10): basis, stamps, fit, apply. */
 int orc_sub_basis(int32_t hw, const double* sig, const int32_t* deg, int32_t nk, double* out);
 int orc_sub_stamps(const float* I, const float* R, int64_t W, int64_t H, int32_t nsx, int32_t nsy, int32_t hw,
