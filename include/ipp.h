@@ -21,6 +21,15 @@
  *   ipp_psf_fit       batched Levenberg-Marquardt PSF fit of stamps
  *   ipp_extract       all catalog steps of one frame, fused where the data allow
  *
+ * and, beside that path:
+ *
+ *   ipp_wcs_map, ipp_affine_fit, ipp_reproject_affine
+ *                     image alignment through both frames' WCS   (Sec. 2.2.3, Eqs. 5-7)
+ *   ipp_sub_apply     convolution and difference of image subtraction
+ *                                                             (Sec. 2.2.4, Eqs. 8-10)
+ *   ipp_gray_transform, ipp_hist_equalize, ipp_zscale
+ *                     gray-scale maps and display limits       (Sec. 2.2.6)
+ *
  * Conventions for every call
  *   - Pixel (row i, col j) has its centre at (x = j, y = i).  Frames are row-major
  *     with `pitch` elements between rows (pitch >= W).
