@@ -121,6 +121,7 @@ def lib():
             L.orc_sub_basis.argtypes = [i32, vp, vp, i32, vp]
             L.orc_sub_stamps.argtypes = [vp, vp, i64, i64, i32, i32, i32, i32, d, vp, vp]
             L.orc_sub_fit.argtypes = [vp, vp, i64, i64, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, vp]
+            L.orc_sub_normal.argtypes = [vp, vp, i64, i64, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, vp, vp]
             L.orc_sub_apply.argtypes = [vp, vp, i64, i64, i32, vp, vp, i32, i32, i32, vp, i32, vp]
             L.orc_deblend.restype = i64
             L.orc_psf_model.argtypes = [vp, i32, i32, d, vp, vp]
@@ -503,6 +504,23 @@ def sub_fit(img, tmpl, cx, cy, hw=10, fh=10, sig=SUB_SIG, deg=SUB_DEG, sord=2, b
     if e:
         raise ValueError("subtraction fit: no candidate or a singular normal matrix")
     return coef
+
+
+def sub_normal(img, tmpl, cx, cy, hw=10, fh=10, sig=SUB_SIG, deg=SUB_DEG, sord=2, bord=1):
+    """normal equations (AtA, Atb) of the fit, unknowns ordered as sub_fit's"""
+    img, tmpl = _f32(img), _f32(tmpl)
+    H, W = img.shape
+    sg, dg = _basis_args(sig, deg)
+    cx = np.ascontiguousarray(cx, np.int32)
+    cy = np.ascontiguousarray(cy, np.int32)
+    nb = int(sum((k + 1) * (k + 2) // 2 for k in deg))
+    npar = nb * (sord + 1) * (sord + 2) // 2 + ((bord + 1) * (bord + 2) // 2 if bord >= 0 else 0)
+    AtA, Atb = np.zeros((npar, npar)), np.zeros(npar)
+    e = lib().orc_sub_normal(_p(img), _p(tmpl), W, H, _p(cx), _p(cy), len(cx), hw, fh, _p(sg), _p(dg), len(sg),
+                             sord, bord, _p(AtA), _p(Atb))
+    if e:
+        raise ValueError("subtraction normal equations: bad arguments")
+    return AtA, Atb
 
 
 def sub_apply(img, tmpl, coef, hw=10, sig=SUB_SIG, deg=SUB_DEG, sord=2, bord=1, tile=21):

@@ -1669,17 +1669,20 @@ static int chol_solve(double* A, double* b, int n) {
     return 0;
 }
 
-/* coef: [nb * ns] kernel coefficients c_{n,s} (n outer), then [nbg] background d_b */
-int orc_sub_fit(const float* I, const float* R, int64_t W, int64_t H, const int32_t* cx, const int32_t* cy,
-                int32_t nc, int32_t hw, int32_t fh, const double* sig, const int32_t* deg, int32_t nk, int32_t sord,
-                int32_t bord, double* coef) {
+/* Normal equations of the fit: AtA (np x np, full, row-major) and Atb (np), the
+ * unknowns ordered as the coefficients below; the design row of footprint pixel
+ * p of candidate c is [C_n(p) P_s(c) for n, s] then [-P_b(p) for b], its target
+ * I(p), C_n = R (x) K_n. */
+int orc_sub_normal(const float* I, const float* R, int64_t W, int64_t H, const int32_t* cx, const int32_t* cy,
+                   int32_t nc, int32_t hw, int32_t fh, const double* sig, const int32_t* deg, int32_t nk,
+                   int32_t sord, int32_t bord, double* AtA, double* Atb) {
     if (nc < 1 || sord < 0 || bord < -1) return ORC_INVALID_ARG;
     const int S = 2 * hw + 1, nb = sub_nbasis(deg, nk), ns = sub_nterms(sord), ng = bord >= 0 ? sub_nterms(bord) : 0;
     const int np = nb * ns + ng;
     double* K = (double*)malloc(sizeof(double) * (size_t)nb * S * S);
     if (orc_sub_basis(hw, sig, deg, nk, K) != nb) { free(K); return ORC_INVALID_ARG; }
-    double* AtA = (double*)calloc((size_t)np * np, sizeof(double));
-    double* Atb = (double*)calloc((size_t)np, sizeof(double));
+    for (int64_t k = 0; k < (int64_t)np * np; k++) AtA[k] = 0.0;
+    for (int k = 0; k < np; k++) Atb[k] = 0.0;
     double* row = (double*)malloc(sizeof(double) * (size_t)np);
     double* C = (double*)malloc(sizeof(double) * (size_t)nb);
     double Ps[64], Pb[64];
@@ -1704,17 +1707,32 @@ int orc_sub_fit(const float* I, const float* R, int64_t W, int64_t H, const int3
                 const double target = I[y * W + x];
                 for (int a = 0; a < np; a++) {
                     Atb[a] += row[a] * target;
-                    for (int b = 0; b <= a; b++) AtA[a * np + b] += row[a] * row[b];
+                    for (int b = 0; b <= a; b++) AtA[(int64_t)a * np + b] += row[a] * row[b];
                 }
             }
         }
     }
     for (int a = 0; a < np; a++)
-        for (int b = a + 1; b < np; b++) AtA[a * np + b] = AtA[b * np + a];
-    const int e = chol_solve(AtA, Atb, np);
+        for (int b = a + 1; b < np; b++) AtA[(int64_t)a * np + b] = AtA[(int64_t)b * np + a];
+    free(K); free(row); free(C);
+    return ORC_OK;
+}
+
+/* coef: [nb * ns] kernel coefficients c_{n,s} (n outer), then [nbg] background d_b:
+ * the solution of the normal equations above by Cholesky */
+int orc_sub_fit(const float* I, const float* R, int64_t W, int64_t H, const int32_t* cx, const int32_t* cy,
+                int32_t nc, int32_t hw, int32_t fh, const double* sig, const int32_t* deg, int32_t nk, int32_t sord,
+                int32_t bord, double* coef) {
+    if (nc < 1 || sord < 0 || bord < -1) return ORC_INVALID_ARG;
+    const int nb = sub_nbasis(deg, nk), ns = sub_nterms(sord), ng = bord >= 0 ? sub_nterms(bord) : 0;
+    const int np = nb * ns + ng;
+    double* AtA = (double*)malloc(sizeof(double) * (size_t)np * np);
+    double* Atb = (double*)malloc(sizeof(double) * (size_t)np);
+    int e = orc_sub_normal(I, R, W, H, cx, cy, nc, hw, fh, sig, deg, nk, sord, bord, AtA, Atb);
+    if (!e) e = chol_solve(AtA, Atb, np) ? ORC_INVALID_ARG : ORC_OK;
     if (!e) memcpy(coef, Atb, sizeof(double) * (size_t)np);
-    free(K); free(AtA); free(Atb); free(row); free(C);
-    return e ? ORC_INVALID_ARG : ORC_OK;
+    free(AtA); free(Atb);
+    return e;
 }
 
 int orc_sub_apply(const float* I, const float* R, int64_t W, int64_t H, int32_t hw, const double* sig,

@@ -138,6 +138,9 @@ int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H,
 int orc_sub_basis(int32_t hw, const double* sig, const int32_t* deg, int32_t nk, double* out);
 int orc_sub_stamps(const float* I, const float* R, int64_t W, int64_t H, int32_t nsx, int32_t nsy, int32_t hw,
                    int32_t fh, double nsig, int32_t* cx, int32_t* cy);
+int orc_sub_normal(const float* I, const float* R, int64_t W, int64_t H, const int32_t* cx, const int32_t* cy,
+                   int32_t nc, int32_t hw, int32_t fh, const double* sig, const int32_t* deg, int32_t nk,
+                   int32_t sord, int32_t bord, double* AtA, double* Atb);
 int orc_sub_fit(const float* I, const float* R, int64_t W, int64_t H, const int32_t* cx, const int32_t* cy,
                 int32_t nc, int32_t hw, int32_t fh, const double* sig, const int32_t* deg, int32_t nk, int32_t sord,
                 int32_t bord, double* coef);

@@ -159,3 +159,40 @@ def test_stamp_selection(orc):
     assert not any(x >= 120 and y >= 120 for x, y in found)
     assert (65, 64) not in found
     assert len(found & expect) == 14 and len(found) <= 15
+
+
+def test_normal_equations_match_an_explicit_design_matrix(orc):
+    """the normal equations equal A'A and A'b of the design matrix built here from
+    scipy convolutions of the template with each basis kernel, the spatial terms
+    at the candidates' centres and the background terms at each pixel"""
+    rng = np.random.default_rng(12)
+    H, W, hw, fh = 70, 90, 4, 3
+    R = (100 + rng.normal(0, 10, (H, W))).astype(np.float32)
+    I = (100 + rng.normal(0, 10, (H, W))).astype(np.float32)
+    sig, deg, sord, bord = (1.0, 2.0), (2, 1), 1, 1
+    cx, cy = np.array([20, 55, 70], np.int32), np.array([15, 40, 50], np.int32)
+    AtA, Atb = orc.sub_normal(I, R, cx, cy, hw=hw, fh=fh, sig=sig, deg=deg, sord=sord, bord=bord)
+    B = orc.sub_basis(hw, sig, deg)
+    conv = [convolve2d(R.astype(np.float64), B[n], mode="same") for n in range(B.shape[0])]
+
+    def terms(x, y, order):
+        xs, ys = 2.0 * x / (W - 1) - 1.0, 2.0 * y / (H - 1) - 1.0
+        return [xs ** p * ys ** q for p in range(order + 1) for q in range(order + 1 - p)]
+
+    rows, b = [], []
+    for c in range(3):
+        Ps = terms(cx[c], cy[c], sord)
+        for dv in range(-fh, fh + 1):
+            for du in range(-fh, fh + 1):
+                x, y = cx[c] + du, cy[c] + dv
+                r = [conv[n][y, x] * p for n in range(B.shape[0]) for p in Ps]
+                r += [-t for t in terms(x, y, bord)]
+                rows.append(r)
+                b.append(float(I[y, x]))
+    A, b = np.array(rows), np.array(b)
+    assert AtA.shape == (A.shape[1], A.shape[1])
+    assert np.allclose(AtA, A.T @ A, rtol=1e-11, atol=1e-6)
+    assert np.allclose(Atb, A.T @ b, rtol=1e-11, atol=1e-6)
+    # and the fit solves them
+    coef = orc.sub_fit(I, R, cx, cy, hw=hw, fh=fh, sig=sig, deg=deg, sord=sord, bord=bord)
+    assert np.allclose(coef, np.linalg.lstsq(A, b, rcond=None)[0], rtol=1e-6, atol=1e-8)
