@@ -118,6 +118,7 @@ def lib():
             L.orc_zscale.argtypes = [vp, i64, i64, i32, d, d, i32, vp, vp]
             L.orc_clean.argtypes = [vp, vp, i64, i64, i64, vp, d, vp]
             L.orc_clean.restype = i64
+            L.orc_clean_stats.argtypes = [vp, vp, i64, i64, i64] + [vp] * 7
             L.orc_sub_basis.argtypes = [i32, vp, vp, i32, vp]
             L.orc_sub_stamps.argtypes = [vp, vp, i64, i64, i32, i32, i32, i32, d, vp, vp]
             L.orc_sub_fit.argtypes = [vp, vp, i64, i64, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, vp]
@@ -546,3 +547,18 @@ def clean(sub, labels, nobj, thr, beta=1.0):
     k = lib().orc_clean(_p(sub), _p(labels), W, H, int(nobj), _p(thr), float(beta), _p(out))
     assert k >= 0
     return out, int(k)
+
+
+def clean_stats(sub, labels, nobj):
+    """per-object peak, peak index, barycentre and moments of the cleaning test
+    (arrays indexed by label, entry 0 unused)"""
+    sub = _f32(sub)
+    labels = np.ascontiguousarray(labels, np.int32)
+    H, W = sub.shape
+    n = int(nobj) + 1
+    out = {k: np.zeros(n) for k in ("peak", "cx", "cy", "x2", "y2", "xy")}
+    pidx = np.zeros(n, np.int64)
+    assert lib().orc_clean_stats(_p(sub), _p(labels), W, H, int(nobj), _p(out["peak"]), _p(pidx), _p(out["cx"]),
+                                 _p(out["cy"]), _p(out["x2"]), _p(out["y2"]), _p(out["xy"])) == 0
+    out["peak_index"] = pidx
+    return out

@@ -1864,15 +1864,16 @@ int orc_spline_map(const float* mesh, int64_t nx, int64_t ny, int32_t mesh_w, in
  *     merges to an object that is kept;
  *   kept objects are renumbered 1.. in the order of their labels.
  * ------------------------------------------------------------------------- */
-int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t nobj, const float* thr,
-                  double beta, int32_t* out) {
-    if (!(beta > 0.0) || nobj < 0) return -1;
+/* Per-object statistics of the cleaning test (arrays of nobj + 1, index = label):
+ * peak value and its raster index (-1 for an empty label), barycentre and second
+ * moments as stated above. */
+int orc_clean_stats(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t nobj, double* pk,
+                    int64_t* pidx, double* cx, double* cy, double* x2, double* y2, double* xy) {
+    if (nobj < 0) return ORC_INVALID_ARG;
     const int64_t n = nobj;
     double *sw = calloc(n + 1, sizeof(double)), *sx = calloc(n + 1, sizeof(double)), *sy = calloc(n + 1, sizeof(double));
     double *sxx = calloc(n + 1, sizeof(double)), *syy = calloc(n + 1, sizeof(double)), *sxy = calloc(n + 1, sizeof(double));
     double *ux = calloc(n + 1, sizeof(double)), *uy = calloc(n + 1, sizeof(double)), *cnt = calloc(n + 1, sizeof(double));
-    double* pk = malloc(sizeof(double) * (n + 1));
-    int64_t* pidx = malloc(sizeof(int64_t) * (n + 1));
     for (int64_t k = 0; k <= n; k++) { pk[k] = -INFINITY; pidx[k] = -1; }
     for (int64_t i = 0; i < H; i++) {
         for (int64_t j = 0; j < W; j++) {
@@ -1884,11 +1885,9 @@ int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H,
             if (f > 0.0) { sw[l] += f; sx[l] += f * j; sy[l] += f * i; }
         }
     }
-    double *cx = malloc(sizeof(double) * (n + 1)), *cy = malloc(sizeof(double) * (n + 1));
-    double *x2 = malloc(sizeof(double) * (n + 1)), *y2 = malloc(sizeof(double) * (n + 1)), *xy = malloc(sizeof(double) * (n + 1));
-    for (int64_t l = 1; l <= n; l++) {
-        if (sw[l] > 0.0) { cx[l] = sx[l] / sw[l]; cy[l] = sy[l] / sw[l]; }
-        else if (cnt[l] > 0.0) { cx[l] = ux[l] / cnt[l]; cy[l] = uy[l] / cnt[l]; }
+    for (int64_t l = 0; l <= n; l++) {
+        if (l > 0 && sw[l] > 0.0) { cx[l] = sx[l] / sw[l]; cy[l] = sy[l] / sw[l]; }
+        else if (l > 0 && cnt[l] > 0.0) { cx[l] = ux[l] / cnt[l]; cy[l] = uy[l] / cnt[l]; }
         else { cx[l] = cy[l] = 0.0; }
     }
     for (int64_t i = 0; i < H; i++) {
@@ -1901,14 +1900,27 @@ int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H,
             sxx[l] += f * dx * dx; syy[l] += f * dy * dy; sxy[l] += f * dx * dy;
         }
     }
-    for (int64_t l = 1; l <= n; l++) {
-        if (sw[l] > 0.0) {
+    for (int64_t l = 0; l <= n; l++) {
+        if (l > 0 && sw[l] > 0.0) {
             x2[l] = sxx[l] / sw[l]; y2[l] = syy[l] / sw[l]; xy[l] = sxy[l] / sw[l];
             if (x2[l] * y2[l] - xy[l] * xy[l] < 1.0 / 144.0) { x2[l] += 1.0 / 12.0; y2[l] += 1.0 / 12.0; }
         } else {
             x2[l] = y2[l] = 1.0 / 12.0; xy[l] = 0.0;
         }
     }
+    free(sw); free(sx); free(sy); free(sxx); free(syy); free(sxy); free(ux); free(uy); free(cnt);
+    return ORC_OK;
+}
+
+int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t nobj, const float* thr,
+                  double beta, int32_t* out) {
+    if (!(beta > 0.0) || nobj < 0) return -1;
+    const int64_t n = nobj;
+    double* pk = malloc(sizeof(double) * (n + 1));
+    int64_t* pidx = malloc(sizeof(int64_t) * (n + 1));
+    double *cx = malloc(sizeof(double) * (n + 1)), *cy = malloc(sizeof(double) * (n + 1));
+    double *x2 = malloc(sizeof(double) * (n + 1)), *y2 = malloc(sizeof(double) * (n + 1)), *xy = malloc(sizeof(double) * (n + 1));
+    orc_clean_stats(sub, labels, W, H, n, pk, pidx, cx, cy, x2, y2, xy);
     const double a2 = 2.0 * log(2.0) / (pow(2.0, 1.0 / beta) - 1.0);
     int64_t* into = malloc(sizeof(int64_t) * (n + 1));
     for (int64_t i = 1; i <= n; i++) {
@@ -1939,7 +1951,6 @@ int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H,
         const int32_t l = labels[p];
         out[p] = (l <= 0 || l > n) ? 0 : (int32_t)num[root[l]];
     }
-    free(sw); free(sx); free(sy); free(sxx); free(syy); free(sxy); free(ux); free(uy); free(cnt);
     free(pk); free(pidx); free(cx); free(cy); free(x2); free(y2); free(xy); free(into); free(root); free(num);
     return k;
 }

@@ -133,6 +133,8 @@ int orc_zscale(const float* img, int64_t W, int64_t H, int32_t n_samples, double
  * returns the number of kept objects, out = cleaned label map. */
 int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t nobj, const float* thr,
                   double beta, int32_t* out);
+int orc_clean_stats(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t nobj, double* pk,
+                    int64_t* pidx, double* cx, double* cy, double* x2, double* y2, double* xy);
 
 /* Image subtraction (Sec. 2.2.4, Eqs. 8-10): basis, stamps, fit, apply. */
 int orc_sub_basis(int32_t hw, const double* sig, const int32_t* deg, int32_t nk, double* out);

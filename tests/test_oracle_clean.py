@@ -97,3 +97,32 @@ def test_numbering_invariance(orc):
     # the same partition of the pixels
     pairs = np.unique(np.stack([out[lab > 0], out2[lab > 0]], 1), axis=0)
     assert len(pairs) == k and len(np.unique(pairs[:, 0])) == k and len(np.unique(pairs[:, 1])) == k
+
+
+def test_object_statistics_brute_force(orc):
+    """peak, barycentre and moments per object against a direct numpy evaluation"""
+    rng = np.random.default_rng(9)
+    sub = rng.normal(0, 5, (40, 50)).astype(np.float32)
+    lab = np.zeros((40, 50), np.int32)
+    lab[5:12, 5:15] = 1
+    lab[20:30, 30:33] = 2
+    lab[35, 40] = 3                       # one pixel
+    sub[35, 40] = -2.0                    # with no positive value
+    sub[5:12, 5:15] += 40.0
+    st = orc.clean_stats(sub, lab, 3)
+    for l in (1, 2, 3):
+        i, j = np.nonzero(lab == l)
+        f = sub[i, j].astype(np.float64)
+        k = np.argmax(f)                   # first maximum in raster order
+        assert st["peak"][l] == f[k] and st["peak_index"][l] == i[k] * 50 + j[k]
+        w = np.maximum(f, 0.0)
+        if w.sum() > 0:
+            cx, cy = (w * j).sum() / w.sum(), (w * i).sum() / w.sum()
+            x2, y2 = (w * (j - cx) ** 2).sum() / w.sum(), (w * (i - cy) ** 2).sum() / w.sum()
+            xy = (w * (j - cx) * (i - cy)).sum() / w.sum()
+            if x2 * y2 - xy * xy < 1 / 144:
+                x2, y2 = x2 + 1 / 12, y2 + 1 / 12
+        else:
+            cx, cy, x2, y2, xy = j.mean(), i.mean(), 1 / 12, 1 / 12, 0.0
+        got = [st[k2][l] for k2 in ("cx", "cy", "x2", "y2", "xy")]
+        assert np.allclose(got, [cx, cy, x2, y2, xy], rtol=1e-12, atol=1e-12)
