@@ -96,6 +96,7 @@ def lib():
             L.orc_keys_weight.restype = d
             L.orc_interp_map.argtypes = [vp, i64, i64, i32, i32, i64, i64, vp]
             L.orc_spline_map.argtypes = [vp, i64, i64, i32, i32, i64, i64, vp]
+            L.orc_spline_nodes.argtypes = [vp, i64, i64, vp, vp, vp]
             L.orc_bg_subtract.argtypes = [vp, i64, i64, i64, vp, i64, i64, i32, i32, vp, vp]
             L.orc_threshold.argtypes = [vp, i64, i64, vp, i64, i64, i32, i32, d, d, vp]
             L.orc_threshold_filtered.argtypes = [vp, i64, i64, vp, i64, i64, i32, i32, d, d, vp]
@@ -197,6 +198,15 @@ def spline_map(mesh, mesh_w, W, H, mesh_h=None):
     out = np.zeros((H, W))
     assert lib().orc_spline_map(_p(mesh), nx, ny, mesh_w, mesh_h or mesh_w, W, H, _p(out)) == 0
     return out
+
+
+def spline_nodes(mesh):
+    """second derivatives of the natural tensor spline at the nodes: Mx, My, Mxy"""
+    mesh = _f32(mesh)
+    ny, nx = mesh.shape
+    Mx, My, Mxy = np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx))
+    assert lib().orc_spline_nodes(_p(mesh), nx, ny, _p(Mx), _p(My), _p(Mxy)) == 0
+    return Mx, My, Mxy
 
 
 def keys_weight(s):

@@ -1954,3 +1954,30 @@ int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H,
     free(pk); free(pidx); free(cx); free(cy); free(x2); free(y2); free(xy); free(into); free(root); free(num);
     return k;
 }
+
+/* Node quantities of the same tensor-product spline: second derivatives along x
+ * of each node row (Mx), along y of each node column (My), and along y of the Mx
+ * columns (Mxy), each [ny][nx].  With the node values they fix the spline
+ * between any 2 x 2 nodes. */
+int orc_spline_nodes(const float* mesh, int64_t nx, int64_t ny, double* Mx, double* My, double* Mxy) {
+    if (!mesh || nx < 1 || ny < 1) return ORC_INVALID_ARG;
+    const int64_t nm = nx > ny ? nx : ny;
+    double* y = (double*)malloc(sizeof(double) * (size_t)nm);
+    double* M = (double*)malloc(sizeof(double) * (size_t)nm);
+    double* c = (double*)malloc(sizeof(double) * (size_t)nm);
+    for (int64_t p = 0; p < ny; p++) {
+        for (int64_t q = 0; q < nx; q++) y[q] = mesh[p * nx + q];
+        nspline_m(y, nx, M, c);
+        for (int64_t q = 0; q < nx; q++) Mx[p * nx + q] = M[q];
+    }
+    for (int64_t q = 0; q < nx; q++) {
+        for (int64_t p = 0; p < ny; p++) y[p] = mesh[p * nx + q];
+        nspline_m(y, ny, M, c);
+        for (int64_t p = 0; p < ny; p++) My[p * nx + q] = M[p];
+        for (int64_t p = 0; p < ny; p++) y[p] = Mx[p * nx + q];
+        nspline_m(y, ny, M, c);
+        for (int64_t p = 0; p < ny; p++) Mxy[p * nx + q] = M[p];
+    }
+    free(y); free(M); free(c);
+    return ORC_OK;
+}

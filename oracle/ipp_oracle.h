@@ -67,6 +67,7 @@ int orc_interp_map(const float* mesh, int64_t nx, int64_t ny, int32_t mesh_w,
  * spline through the mesh nodes, linear beyond the end nodes) */
 int orc_spline_map(const float* mesh, int64_t nx, int64_t ny, int32_t mesh_w, int32_t mesh_h, int64_t W, int64_t H,
                    double* out);
+int orc_spline_nodes(const float* mesh, int64_t nx, int64_t ny, double* Mx, double* My, double* Mxy);
 
 int orc_bg_subtract(const float* img, int64_t W, int64_t H, int64_t pitch,
                     const float* mesh_bkg, int64_t nx, int64_t ny,

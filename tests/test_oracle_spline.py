@@ -54,3 +54,45 @@ def test_small_grids(orc):
     got = orc.spline_map(two, 4, 8, 3)
     u = _node_coords(8, 4)
     assert np.max(np.abs(got - (1.0 + 2.0 * u)[None, :])) < 1e-12
+
+
+def test_node_second_derivatives_match_scipy(orc):
+    """Mx, My and the cross term Mxy are the natural splines' second derivatives
+    at the knots (scipy), and with the node values they give the map: the
+    tensor form evaluated here from the 2 x 2 bracketing nodes equals the
+    oracle's map inside the hull"""
+    rng = np.random.default_rng(4)
+    ny, nx, m = 6, 8, 16
+    mesh = rng.normal(50.0, 3.0, (ny, nx)).astype(np.float32)
+    Y = mesh.astype(np.float64)
+    Mx, My, Mxy = orc.spline_nodes(mesh)
+    kx, ky = np.arange(nx), np.arange(ny)
+    assert np.allclose(Mx, CubicSpline(kx, Y, axis=1, bc_type="natural")(kx, 2), atol=1e-10)
+    assert np.allclose(My, CubicSpline(ky, Y, axis=0, bc_type="natural")(ky, 2), atol=1e-10)
+    assert np.allclose(Mxy, CubicSpline(ky, Mx, axis=0, bc_type="natural")(ky, 2), atol=1e-10)
+    got = orc.spline_map(mesh, m, nx * m, ny * m)
+    u, v = _node_coords(nx * m, m), _node_coords(ny * m, m)
+
+    def w(t):      # weights of value, value, second derivative, second derivative on [k, k + 1]
+        b = t - np.floor(t)
+        a = 1 - b
+        return a, b, (a ** 3 - a) / 6, (b ** 3 - b) / 6
+
+    for ii in range(0, ny * m, 7):
+        for jj in range(0, nx * m, 5):
+            if not (0 <= u[jj] <= nx - 1 and 0 <= v[ii] <= ny - 1):
+                continue
+            q, p = min(int(u[jj]), nx - 2), min(int(v[ii]), ny - 2)
+            ax, bx, cx, dx = w(u[jj] - q)
+            ay, by, cy, dy = w(v[ii] - p)
+            if u[jj] - q >= 1:
+                ax, bx, cx, dx = 0.0, 1.0, 0.0, 0.0
+            if v[ii] - p >= 1:
+                ay, by, cy, dy = 0.0, 1.0, 0.0, 0.0
+
+            def along_x(F, G, r):   # x-spline of row r from values F and x-derivatives G
+                return ax * F[r, q] + bx * F[r, q + 1] + cx * G[r, q] + dx * G[r, q + 1]
+
+            val = (ay * along_x(Y, Mx, p) + by * along_x(Y, Mx, p + 1)
+                   + cy * along_x(My, Mxy, p) + dy * along_x(My, Mxy, p + 1))
+            assert abs(val - got[ii, jj]) < 1e-10
