@@ -1,11 +1,12 @@
 // api.cu -- the C ABI of libipp: argument validation, workspace layout and the
 // launch sequences of each call.  All calls are asynchronous on `stream`.
 #include <stdarg.h>
+#include <mutex>
 #include <cmath>
 #include <stdio.h>
 #include <string.h>
 
-#include "jobs.cuh"
+#include "checks.cuh"
 
 using namespace ipp;
 
@@ -23,6 +24,23 @@ int ipp_set_error(int status, const char* fmt, ...) {
 int ipp_check_launch(const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return IPP_OK;
+}
+
+static std::mutex g_once_lock;
+static uint16_t g_once_done[64];  // bit `slot` of entry `device`
+
+int ipp_once_per_device_impl(int slot, cudaError_t (*fn)(void*), void* arg) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64 || slot < 0 || slot >= 16)
+        return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "device %d / slot %d out of range", dev, slot);
+    std::lock_guard<std::mutex> guard(g_once_lock);
+    if ((g_once_done[dev] >> slot) & 1) return IPP_OK;
+    e = fn(arg);
+    if (e != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "per-device set-up: %s", cudaGetErrorString(e));
+    g_once_done[dev] |= (uint16_t)(1u << slot);
     return IPP_OK;
 }
 
@@ -48,34 +66,7 @@ extern "C" int ipp_version(int* major, int* minor, int* patch) {
     return IPP_OK;
 }
 
-#define REQUIRE(cond, ...) \
-    do { if (!(cond)) return ipp_set_error(IPP_ERR_INVALID_ARG, __VA_ARGS__); } while (0)
-
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// ---- validation helpers -------------------------------------------------------
-static int check_frame(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch, const ipp_calib* cal) {
-    REQUIRE(img, "img is NULL");
-    REQUIRE(W > 0 && H > 0, "W, H must be positive (got %lld, %lld)", (long long)W, (long long)H);
-    REQUIRE(W < (1ll << 31) && H < (1ll << 31), "frame dimensions too large");
-    REQUIRE(pitch >= W, "pitch %lld < W %lld", (long long)pitch, (long long)W);
-    REQUIRE(dtype == IPP_F32 || dtype == IPP_U16, "unknown dtype %d", dtype);
-    if (dtype == IPP_U16) REQUIRE(cal && cal->inv_flat, "IPP_U16 input needs cal->inv_flat");
-    return IPP_OK;
-}
-
-static int check_bg(const ipp_bg_params* p) {
-    REQUIRE(p, "bg params NULL");
-    REQUIRE(p->mesh_w >= 4 && p->mesh_h >= 4, "mesh size must be >= 4 (got %d x %d)", p->mesh_w, p->mesh_h);
-    REQUIRE((int64_t)p->mesh_w * p->mesh_h <= 16384, "mesh area %d > 16384", p->mesh_w * p->mesh_h);
-    REQUIRE(p->filter_w >= 1 && p->filter_h >= 1 && (p->filter_w & 1) && (p->filter_h & 1) &&
-                p->filter_w <= 7 && p->filter_h <= 7, "filter must be odd and <= 7");
-    REQUIRE(p->maxiters >= 1, "maxiters must be >= 1");
-    REQUIRE(p->min_valid >= 1, "min_valid must be >= 1");
-    REQUIRE(p->estimator >= 0 && p->estimator <= 3, "unknown estimator %d", p->estimator);
-    REQUIRE(p->nsigma > 0, "nsigma must be > 0");
-    return IPP_OK;
-}
 
 static void grid_of(int64_t W, int64_t H, const ipp_bg_params* p, int* nx, int* ny) {
     *nx = (int)cdiv(W, p->mesh_w);

@@ -1029,25 +1029,35 @@ __global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
 // ---------------------------------------------------------------------------
 // Invalid-mesh fill and median filter on the mesh grid.  An invalid node takes
 // the median of the valid nodes in the smallest (2k+1)^2 neighbourhood holding
-// any; each node then becomes the median of the in-bounds (filled) nodes of its
-// fw x fh window.  One thread per node; the fill of an invalid neighbour is
-// recomputed where needed (invalid meshes are rare).
+// any -- since the smaller neighbourhoods hold none, those are exactly the
+// valid nodes on the ring at Chebyshev distance k -- and each node then
+// becomes the median of the in-bounds filled nodes of its fw x fh window.
+// The fill is computed once per node (pass 1), the window medians read the
+// filled grids (pass 2).  Grids of up to MF_SMALL nodes run both passes in one
+// block with the grids in shared memory; larger ones take two launches through
+// the caller's fill arrays.  A grid without any valid node returns at once
+// with IPP_ERR_NO_VALID_MESH.
 constexpr int MF_THREADS = 256;
+constexpr int MF_SMALL = 3072;       // one-block path: 16 B per node of shared memory (48 KB)
+constexpr int MF_SMALL_THREADS = 1024;
 
-// median (Eq. 1) of src over the valid nodes of a window, by rank counting
-__device__ float window_median_valid(const float* src, const float* raw_rms, int nx, int p0, int p1, int q0,
-                                     int q1, int cnt) {
+// median (Eq. 1) of the valid nodes on the ring at Chebyshev distance k of
+// (p, q) (in-bounds part), by rank counting; cnt = their number (> 0)
+__device__ float ring_median(const float* src, const float* raw_rms, int nx, int ny, int p, int q, int k, int cnt) {
     const int k0 = (cnt - 1) / 2, k1 = cnt / 2;
     float a = 0.f, b = 0.f;
-    for (int p = p0; p <= p1; p++)
-        for (int q = q0; q <= q1; q++) {
-            const int id = p * nx + q;
+    const int p0 = max(p - k, 0), p1 = min(p + k, ny - 1), q0 = max(q - k, 0), q1 = min(q + k, nx - 1);
+    for (int pp = p0; pp <= p1; pp++)
+        for (int qq = q0; qq <= q1; qq++) {
+            if (max(abs(pp - p), abs(qq - q)) != k) continue;
+            const int id = pp * nx + qq;
             if (raw_rms[id] < 0.f) continue;
             const float x = src[id];
             int less = 0, leq = 0;
-            for (int pp = p0; pp <= p1; pp++)
-                for (int qq = q0; qq <= q1; qq++) {
-                    const int j = pp * nx + qq;
+            for (int p2 = p0; p2 <= p1; p2++)
+                for (int q2 = q0; q2 <= q1; q2++) {
+                    if (max(abs(p2 - p), abs(q2 - q)) != k) continue;
+                    const int j = p2 * nx + q2;
                     if (raw_rms[j] < 0.f) continue;
                     const float y = src[j];
                     less += y < x;
@@ -1059,57 +1069,162 @@ __device__ float window_median_valid(const float* src, const float* raw_rms, int
     return (float)(0.5 * ((double)a + (double)b));
 }
 
-// filled value of node (p, q) of src; false when the grid has no valid node
-__device__ bool filled_value(const float* src, const float* raw_rms, int nx, int ny, int p, int q, float* out) {
+// fill of node (p, q): its own values when valid, else the ring medians
+__device__ __forceinline__ void fill_node(const float* raw_bkg, const float* raw_rms, int nx, int ny, int p, int q,
+                                          float* fb, float* fr) {
     const int id = p * nx + q;
-    if (raw_rms[id] >= 0.f) { *out = src[id]; return true; }
-    for (int k = 1; k <= max(nx, ny); k++) {
+    if (raw_rms[id] >= 0.f) { *fb = raw_bkg[id]; *fr = raw_rms[id]; return; }
+    for (int k = 1; k < max(nx, ny); k++) {
         const int p0 = max(p - k, 0), p1 = min(p + k, ny - 1), q0 = max(q - k, 0), q1 = min(q + k, nx - 1);
-        int cnt = 0;
-        for (int pp = p0; pp <= p1; pp++)
-            for (int qq = q0; qq <= q1; qq++) cnt += raw_rms[pp * nx + qq] >= 0.f;
+        int cnt = 0;  // valid nodes on ring k: its in-bounds rows p - k, p + k and columns q - k, q + k
+        for (int qq = q0; qq <= q1; qq++) {
+            if (p - k >= 0) cnt += raw_rms[(p - k) * nx + qq] >= 0.f;
+            if (p + k < ny) cnt += raw_rms[(p + k) * nx + qq] >= 0.f;
+        }
+        for (int pp = max(p - k + 1, 0); pp <= min(p + k - 1, ny - 1); pp++) {
+            if (q - k >= 0) cnt += raw_rms[pp * nx + q - k] >= 0.f;
+            if (q + k < nx) cnt += raw_rms[pp * nx + q + k] >= 0.f;
+        }
         if (cnt > 0) {
-            *out = window_median_valid(src, raw_rms, nx, p0, p1, q0, q1, cnt);
-            return true;
+            *fb = ring_median(raw_bkg, raw_rms, nx, ny, p, q, k, cnt);
+            *fr = ring_median(raw_rms, raw_rms, nx, ny, p, q, k, cnt);
+            return;
         }
     }
-    return false;
+    *fb = 0.f;  // unreachable when the grid holds a valid node
+    *fr = 0.f;
 }
 
-__global__ void __launch_bounds__(MF_THREADS) k_mesh_filter(const float* raw_bkg, const float* raw_rms, int nx,
-                                                            int ny, int fw, int fh, float* out_bkg,
-                                                            float* out_rms, int32_t* status_dev) {
-    const int id = blockIdx.x * MF_THREADS + threadIdx.x;
-    if (id >= nx * ny) return;
-    const int p = id / nx, q = id - p * nx;
-    const int hw = fw / 2, hh = fh / 2;
-    const int p0 = max(p - hh, 0), p1 = min(p + hh, ny - 1), q0 = max(q - hw, 0), q1 = min(q + hw, nx - 1);
-    float wb[49], wr[49];
+// median of the n in-bounds values of a window held in registers (slot i
+// used when i < n): rank counting with ties broken by slot, so that every
+// index is static and the window stays in registers
+template <int N>
+__device__ __forceinline__ float reg_median(const float v[N], int n) {
+    const int k0 = (n - 1) / 2, k1 = n / 2;
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < N; j++) r += (j < n) && (v[j] < v[i] || (v[j] == v[i] && j < i));
+        if (i < n && r == k0) a = v[i];
+        if (i < n && r == k1) b = v[i];
+    }
+    return (float)(0.5 * ((double)a + (double)b));
+}
+
+// window median of node (p, q) over filled grids fb, fr (row-major, nx wide)
+template <int FW, int FH>
+__device__ __forceinline__ void window_median(const float* fb, const float* fr, int nx, int ny, int p, int q,
+                                              float* ob, float* orr) {
+    constexpr int N = FW * FH;
+    float wb[N], wr[N];
     int n = 0;
-    bool ok = true;
-    for (int pp = p0; pp <= p1; pp++)
-        for (int qq = q0; qq <= q1; qq++) {
-            float b, r;
-            ok &= filled_value(raw_bkg, raw_rms, nx, ny, pp, qq, &b);
-            ok &= filled_value(raw_rms, raw_rms, nx, ny, pp, qq, &r);
-            // insertion into the two sorted windows
-            int i = n - 1;
-            while (i >= 0 && wb[i] > b) { wb[i + 1] = wb[i]; i--; }
-            wb[i + 1] = b;
-            i = n - 1;
-            while (i >= 0 && wr[i] > r) { wr[i + 1] = wr[i]; i--; }
-            wr[i + 1] = r;
+#pragma unroll
+    for (int a = 0; a < FH; a++)
+#pragma unroll
+        for (int c = 0; c < FW; c++) {
+            const int pp = p - FH / 2 + a, qq = q - FW / 2 + c;
+            const bool in = pp >= 0 && pp < ny && qq >= 0 && qq < nx;
+            // in-bounds values packed to the front (n counts them), keeping static indices
+            const float vb = in ? fb[pp * nx + qq] : 0.f, vr = in ? fr[pp * nx + qq] : 0.f;
+#pragma unroll
+            for (int s = 0; s < N; s++)
+                if (s == n && in) { wb[s] = vb; wr[s] = vr; }
+            n += in;
+        }
+#pragma unroll
+    for (int s = 0; s < N; s++)
+        if (s >= n) { wb[s] = 0.f; wr[s] = 0.f; }
+    *ob = reg_median<N>(wb, n);
+    *orr = reg_median<N>(wr, n);
+}
+
+__device__ __forceinline__ void window_median_any(const float* fb, const float* fr, int nx, int ny, int p, int q,
+                                                  int fw, int fh, float* ob, float* orr) {
+    if (fw == 3 && fh == 3) { window_median<3, 3>(fb, fr, nx, ny, p, q, ob, orr); return; }
+    if (fw == 1 && fh == 1) { *ob = fb[p * nx + q]; *orr = fr[p * nx + q]; return; }
+    if (fw == 5 && fh == 5) { window_median<5, 5>(fb, fr, nx, ny, p, q, ob, orr); return; }
+    // other odd shapes up to 7 x 7: the 7 x 7 window with the rows and columns
+    // beyond the requested shape treated as out of bounds
+    constexpr int N = 49;
+    float wb[N], wr[N];
+    int n = 0;
+    for (int a = 0; a < fh; a++)
+        for (int c = 0; c < fw; c++) {
+            const int pp = p - fh / 2 + a, qq = q - fw / 2 + c;
+            if (pp < 0 || pp >= ny || qq < 0 || qq >= nx) continue;
+            wb[n] = fb[pp * nx + qq];
+            wr[n] = fr[pp * nx + qq];
             n++;
         }
-    if (!ok) {  // no valid mesh anywhere
-        out_bkg[id] = 0.f;
-        out_rms[id] = 0.f;
+    for (int s = n; s < N; s++) { wb[s] = 0.f; wr[s] = 0.f; }
+    *ob = reg_median<N>(wb, n);
+    *orr = reg_median<N>(wr, n);
+}
+
+// one block: every node's fill into shared memory, then the window medians
+__global__ void __launch_bounds__(MF_SMALL_THREADS) k_mesh_fill_filter_small(const float* raw_bkg,
+                                                                             const float* raw_rms, int nx, int ny,
+                                                                             int fw, int fh, float* out_bkg,
+                                                                             float* out_rms, int32_t* status_dev) {
+    extern __shared__ float mf_sh[];
+    const int nn = nx * ny;
+    float* rb = mf_sh;
+    float* rr = rb + nn;
+    float* fb = rr + nn;
+    float* fr = fb + nn;
+    int any = 0;
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+        rb[i] = raw_bkg[i];
+        rr[i] = raw_rms[i];
+        any |= rr[i] >= 0.f;
+    }
+    if (!__syncthreads_or(any)) {
+        for (int i = threadIdx.x; i < nn; i += blockDim.x) { out_bkg[i] = 0.f; out_rms[i] = 0.f; }
+        if (threadIdx.x == 0 && status_dev) *status_dev = IPP_ERR_NO_VALID_MESH;
+        return;
+    }
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+        const int p = i / nx, q = i - p * nx;
+        fill_node(rb, rr, nx, ny, p, q, &fb[i], &fr[i]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+        const int p = i / nx, q = i - p * nx;
+        window_median_any(fb, fr, nx, ny, p, q, fw, fh, &out_bkg[i], &out_rms[i]);
+    }
+    if (threadIdx.x == 0 && status_dev) *status_dev = IPP_OK;
+}
+
+// large grids, pass 1: fills into the caller's arrays.  Each block first checks
+// that the grid holds a valid node (a block-wide scan of raw_rms).
+__global__ void __launch_bounds__(MF_THREADS) k_mesh_fill(const float* raw_bkg, const float* raw_rms, int nx, int ny,
+                                                          float* fill_bkg, float* fill_rms, int32_t* status_dev) {
+    const int nn = nx * ny;
+    int any = 0;
+    for (int i = threadIdx.x; i < nn && !any; i += MF_THREADS) any |= raw_rms[i] >= 0.f;
+    if (!__syncthreads_or(any)) {
+        const int id = blockIdx.x * MF_THREADS + threadIdx.x;
+        if (id < nn) { fill_bkg[id] = 0.f; fill_rms[id] = -1.f; }  // -1: pass 2 writes zeros
         if (id == 0 && status_dev) *status_dev = IPP_ERR_NO_VALID_MESH;
         return;
     }
-    out_bkg[id] = (float)(0.5 * ((double)wb[(n - 1) / 2] + (double)wb[n / 2]));
-    out_rms[id] = (float)(0.5 * ((double)wr[(n - 1) / 2] + (double)wr[n / 2]));
+    const int id = blockIdx.x * MF_THREADS + threadIdx.x;
+    if (id >= nn) return;
+    const int p = id / nx, q = id - p * nx;
+    fill_node(raw_bkg, raw_rms, nx, ny, p, q, &fill_bkg[id], &fill_rms[id]);
     if (id == 0 && status_dev) *status_dev = IPP_OK;
+}
+
+// large grids, pass 2: window medians of the filled grids
+__global__ void __launch_bounds__(MF_THREADS) k_mesh_median(const float* fill_bkg, const float* fill_rms, int nx,
+                                                            int ny, int fw, int fh, float* out_bkg, float* out_rms) {
+    const int id = blockIdx.x * MF_THREADS + threadIdx.x;
+    if (id >= nx * ny) return;
+    if (fill_rms[0] < 0.f) { out_bkg[id] = 0.f; out_rms[id] = 0.f; return; }  // no valid mesh (pass 1)
+    const int p = id / nx, q = id - p * nx;
+    window_median_any(fill_bkg, fill_rms, nx, ny, p, q, fw, fh, &out_bkg[id], &out_rms[id]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1224,11 +1339,13 @@ using namespace ipp;
 int ipp_launch_mesh_stats(const MeshJob& J, cudaStream_t s) {
     if (J.mesh_w * J.mesh_h > 16384)
         return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "mesh area %d > 16384", J.mesh_w * J.mesh_h);
-    static bool carveout_set = false;  // seven 31 KB CTAs per SM need the largest shared-memory carveout
-    if (!carveout_set) {
-        cudaFuncSetAttribute(k_mesh_stats, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        carveout_set = true;
-    }
+    // seven 31 KB CTAs per SM need the largest shared-memory carveout; the
+    // attribute is per device, so it is set once on each device that launches
+    if (int e = ipp_once_per_device(0, [] {
+            return cudaFuncSetAttribute(k_mesh_stats, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        cudaSharedmemCarveoutMaxShared);
+        }))
+        return e;
     k_mesh_stats<<<J.nx * J.ny, MS_THREADS, 0, s>>>(J);
     return ipp_check_launch("k_mesh_stats");
 }
@@ -1236,12 +1353,21 @@ int ipp_launch_mesh_stats(const MeshJob& J, cudaStream_t s) {
 int ipp_launch_mesh_filter(const float* raw_bkg, const float* raw_rms, float* fill_bkg, float* fill_rms,
                            int nx, int ny, int fw, int fh, float* out_bkg, float* out_rms,
                            int32_t* status_dev, cudaStream_t s) {
-    (void)fill_bkg;
-    (void)fill_rms;  // the fill is computed on the fly
     const int nn = nx * ny;
-    k_mesh_filter<<<(nn + MF_THREADS - 1) / MF_THREADS, MF_THREADS, 0, s>>>(raw_bkg, raw_rms, nx, ny, fw, fh,
-                                                                            out_bkg, out_rms, status_dev);
-    return ipp_check_launch("k_mesh_filter");
+    if (nn <= MF_SMALL) {
+        const int threads = nn >= MF_SMALL_THREADS ? MF_SMALL_THREADS : ((nn + 31) / 32) * 32;
+        const size_t sh = (size_t)16 * nn;
+        static_assert(16 * MF_SMALL <= 48 * 1024, "one-block filter within the default shared-memory limit");
+        k_mesh_fill_filter_small<<<1, threads, sh, s>>>(raw_bkg, raw_rms, nx, ny, fw, fh, out_bkg, out_rms,
+                                                        status_dev);
+        return ipp_check_launch("k_mesh_fill_filter_small");
+    }
+    if (!fill_bkg || !fill_rms) return ipp_set_error(IPP_ERR_INVALID_ARG, "fill arrays NULL for a large grid");
+    const int blocks = (nn + MF_THREADS - 1) / MF_THREADS;
+    k_mesh_fill<<<blocks, MF_THREADS, 0, s>>>(raw_bkg, raw_rms, nx, ny, fill_bkg, fill_rms, status_dev);
+    if (int e = ipp_check_launch("k_mesh_fill")) return e;
+    k_mesh_median<<<blocks, MF_THREADS, 0, s>>>(fill_bkg, fill_rms, nx, ny, fw, fh, out_bkg, out_rms);
+    return ipp_check_launch("k_mesh_median");
 }
 
 int ipp_launch_bg_subtract(const SubJob& J, cudaStream_t s) {

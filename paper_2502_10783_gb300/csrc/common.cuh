@@ -87,3 +87,12 @@ IPP_HD int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // host-side error recording (api.cu)
 int ipp_set_error(int status, const char* fmt, ...);
 int ipp_check_launch(const char* what);
+
+// Runs fn() (a host callable returning cudaError_t) once per (slot, device) for
+// the current device, under a lock; later calls return at once.  For per-device
+// kernel attributes.  Slots 0..15.  A failed fn() is retried on the next call.
+int ipp_once_per_device_impl(int slot, cudaError_t (*fn)(void*), void* arg);
+template <class F>
+int ipp_once_per_device(int slot, F f) {
+    return ipp_once_per_device_impl(slot, [](void* a) -> cudaError_t { return (*static_cast<F*>(a))(); }, &f);
+}

@@ -9,7 +9,7 @@
 // cudaGetSymbolAddress (with that device current) and caches it.
 #include <mutex>
 
-#include "jobs.cuh"
+#include "checks.cuh"
 
 namespace {
 
@@ -44,15 +44,8 @@ int scratch_for_current_device(float** out) {
 extern "C" int ipp_bg_estimate_noalloc(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
                                        const uint8_t* mask, const ipp_calib* cal, const ipp_bg_params* p,
                                        float* mesh_bkg, float* mesh_rms, int32_t* status_dev, void* stream) {
-    if (!img || W <= 0 || H <= 0 || pitch < W || (dtype != IPP_F32 && dtype != IPP_U16))
-        return ipp_set_error(IPP_ERR_INVALID_ARG, "bad frame (img %p, W %lld, H %lld, pitch %lld, dtype %d)",
-                             img, (long long)W, (long long)H, (long long)pitch, dtype);
-    if (dtype == IPP_U16 && !(cal && cal->inv_flat))
-        return ipp_set_error(IPP_ERR_INVALID_ARG, "IPP_U16 input needs cal->inv_flat");
-    if (!p || p->mesh_w < 4 || p->mesh_h < 4 || (int64_t)p->mesh_w * p->mesh_h > 16384 || p->filter_w < 1 ||
-        p->filter_h < 1 || !(p->filter_w & 1) || !(p->filter_h & 1) || p->filter_w > 7 || p->filter_h > 7 ||
-        p->maxiters < 1 || p->min_valid < 1 || p->estimator < 0 || p->estimator > 3 || !(p->nsigma > 0))
-        return ipp_set_error(IPP_ERR_INVALID_ARG, "bad background parameters");
+    if (int e = check_frame(img, dtype, W, H, pitch, cal)) return e;
+    if (int e = check_bg(p)) return e;
     if (!mesh_bkg || !mesh_rms) return ipp_set_error(IPP_ERR_INVALID_ARG, "mesh outputs NULL");
     const int64_t nx = ipp::cdiv(W, p->mesh_w), ny = ipp::cdiv(H, p->mesh_h);
     if (nx * ny > IPP_BG_NOALLOC_MAX_MESHES)

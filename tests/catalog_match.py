@@ -1,0 +1,184 @@
+"""Whole-catalog parity of the fused per-frame path (ipp_extract and the batch
+runner) against the oracle's path, source by source.
+
+The fused kernel decides the threshold sub > k * rms(x, y) in FP32 and the
+oracle in FP64, so the two masks may differ at pixels whose value lies within
+rounding of the threshold ("borderline" pixels).  A component of either
+catalog is *clean* when no borderline pixel lies in it or next to it (8
+neighbours: a borderline pixel that joins one side's mask can merge it with a
+neighbour).  Every clean component must exist on both sides with the identical
+pixel set; the counts may differ only by the unclean ones.  On every matched
+source everything is then compared element by element, with no escape:
+
+* the label statistics (area, first index, bounding box exact; peak and
+  isophotal sums within the subtracted frame's tolerance; barycentre within 2
+  ulp + 2e-5 px);
+* each per-source stage on identical inputs: the oracle's centroid from the
+  GPU's seeds on the GPU's subtracted frame, and the oracle's aperture at the
+  GPU's positions on that frame (n_ann, flags and sky exact);
+* the end-to-end values against the oracle's own catalog, with the tolerance
+  widened by what the subtracted frames and positions are allowed to differ
+  (derived below, per source).
+"""
+import numpy as np
+
+from gpu_util import float_ulp
+
+FLAG_WIN_NOT_CONVERGED = 2
+
+
+def _dilate8(m):
+    out = m.copy()
+    out[1:, :] |= m[:-1, :]
+    out[:-1, :] |= m[1:, :]
+    t = out.copy()
+    out[:, 1:] |= t[:, :-1]
+    out[:, :-1] |= t[:, 1:]
+    return out
+
+
+def _comp_index(labels, K):
+    """pixel indices of each label 1..K (a list of sorted flat-index arrays)"""
+    flat = labels.ravel()
+    idx = np.flatnonzero(flat)
+    lab = flat[idx]
+    order = np.argsort(lab, kind="stable")
+    idx, lab = idx[order], lab[order]
+    starts = np.searchsorted(lab, np.arange(1, K + 2))
+    return [idx[starts[i]:starts[i + 1]] for i in range(K)]
+
+
+def borderline(orc, osub, gsub, orms, mesh, W, H, k=1.5):
+    """pixels whose oracle value lies within the two sides' rounding of the
+    threshold: |osub - k rms| <= |gsub - osub| + 2e-5 k rms + 1e-6"""
+    thr = k * orc.interp_map(orms, mesh, W, H)
+    dev = np.abs(gsub.astype(np.float64) - osub.astype(np.float64))
+    return np.abs(osub.astype(np.float64) - thr) <= dev + 2e-5 * np.abs(thr) + 1e-6
+
+
+def match_components(ol, oK, gl, gK, near):
+    """(pairs of 0-based indices (oracle, gpu) of clean matched components,
+    number of unclean oracle components, number of unclean gpu components)"""
+    bad = _dilate8(near)
+    opix = _comp_index(ol, oK)
+    gpix = _comp_index(gl, gK)
+    flat_bad = bad.ravel()
+    o_clean = np.array([not flat_bad[p].any() for p in opix], bool)
+    g_clean = np.array([not flat_bad[p].any() for p in gpix], bool)
+    glf = gl.ravel()
+    pairs = []
+    for i in np.flatnonzero(o_clean):
+        p = opix[i]
+        g = glf[p]
+        assert g[0] > 0 and np.all(g == g[0]), f"oracle component {i + 1}: gpu labels {np.unique(g)[:5]}"
+        j = int(g[0]) - 1
+        assert np.array_equal(gpix[j], p), f"oracle component {i + 1} vs gpu {j + 1}: pixel sets differ"
+        pairs.append((i, j))
+    pairs = np.array(pairs, dtype=np.int64).reshape(-1, 2)
+    # every clean gpu component is one of the matched ones
+    matched_g = np.zeros(gK, bool)
+    matched_g[pairs[:, 1]] = True
+    assert np.all(matched_g[g_clean]), f"{np.sum(g_clean & ~matched_g)} clean gpu components unmatched"
+    return pairs, int((~o_clean).sum()), int((~g_clean).sum())
+
+
+def _ann_boundary_margin(x, y, r_in, r_out, W, H, eps):
+    """True where some in-frame pixel centre lies within eps of the annulus radii
+    around (x, y): its membership may flip when the position moves by eps."""
+    out = np.zeros(len(x), bool)
+    R = int(np.ceil(r_out + 2))
+    dy, dx = np.mgrid[-R:R + 1, -R:R + 1]
+    for n in range(len(x)):
+        ci, cj = int(np.floor(y[n] + 0.5)), int(np.floor(x[n] + 0.5))
+        ii, jj = ci + dy, cj + dx
+        ok = (ii >= 0) & (ii < H) & (jj >= 0) & (jj < W)
+        d = np.hypot(jj - x[n], ii - y[n])[ok]
+        out[n] = np.any(np.abs(d - r_in) <= eps[n]) or np.any(np.abs(d - r_out) <= eps[n])
+    return out
+
+
+def assert_catalog(orc, img, oc, g, gstats, mesh, r_ap=5.0, r_in=8.0, r_out=12.0, k=1.5):
+    """img: the float32 frame the oracle ran on; oc: orc.catalog(img, mesh);
+    g: host arrays of the fused outputs (mesh_bkg, mesh_rms, sub, labels, n_src,
+    x, y, cen_flags, flux, sky, area, n_ann, phot_flags); gstats: host arrays of
+    the label statistics.  Returns a summary dict."""
+    H, W = img.shape
+    gb, gr = g["mesh_bkg"], g["mesh_rms"]
+    assert np.all(np.abs(gb - oc["bkg"]) <= 2e-5 * np.abs(oc["bkg"]) + 1e-6), "mesh bkg"
+    assert np.all(np.abs(gr - oc["rms"]) <= 2e-5 * np.abs(oc["rms"]) + 1e-6), "mesh rms"
+    gsub, osub = g["sub"], oc["sub"]
+    bmap = img.astype(np.float64) - osub
+    sub_tol = 2e-5 * np.maximum(np.abs(img), np.abs(bmap)) + 1e-6
+    assert np.all(np.abs(gsub.astype(np.float64) - osub) <= sub_tol), "subtracted frame"
+
+    gK, oK = int(g["n_src"]), int(oc["K"])
+    near = borderline(orc, osub, gsub, oc["rms"], mesh, W, H, k)
+    pairs, o_bad, g_bad = match_components(oc["labels"], oK, g["labels"], gK, near)
+    assert len(pairs) == oK - o_bad == gK - g_bad, (len(pairs), oK, o_bad, gK, g_bad)
+    io, ig = pairs[:, 0], pairs[:, 1]
+
+    # label statistics
+    ost = oc["stats"]
+    for key, okey in (("area", "area"), ("first", "first"), ("xmin", "xmin"), ("xmax", "xmax"),
+                      ("ymin", "ymin"), ("ymax", "ymax")):
+        assert np.array_equal(gstats[key][ig].astype(np.int64), ost[okey][io].astype(np.int64)), key
+    dsub = np.abs(gsub.astype(np.float64) - osub)
+    assert np.all(np.abs(gstats["peak"][ig] - ost["peak"][io]) <= 2e-5 * np.abs(ost["peak"][io]) + dsub.max())
+    # isophotal flux: FP32 partial sums of `area` values against FP64
+    fl_tol = 1e-5 * np.abs(ost["sum"][io]) + ost["area"][io] * (dsub.max() + 1e-6)
+    assert np.all(np.abs(gstats["flux"][ig] - ost["sum"][io]) <= fl_tol), "isophotal flux"
+    for key in ("xbar", "ybar"):
+        ov = ost[key][io]
+        assert np.all(np.abs(gstats[key][ig] - ov) <= 2 * float_ulp(ov) + 2e-5), key
+
+    # per-source stages on identical inputs (the GPU's own sub, seeds and positions)
+    x0 = gstats["xbar"][ig].astype(np.float32)
+    y0 = gstats["ybar"][ig].astype(np.float32)
+    sx, sy, _, sfl = orc.centroid(gsub, x0, y0)
+    gx, gy, gcf = g["x"][ig], g["y"][ig], g["cen_flags"][ig]
+    assert np.array_equal(gcf & 1, sfl & 1), "centroid EDGE flags"
+    conv_any = ((sfl & FLAG_WIN_NOT_CONVERGED) == 0) | ((gcf & FLAG_WIN_NOT_CONVERGED) == 0)
+    tol = 3e-4 + 2 * float_ulp(sx)
+    bad = conv_any & ((np.abs(gx - sx) > tol) | (np.abs(gy - sy) > tol))
+    assert not bad.any(), f"{bad.sum()} centroids differ: {np.flatnonzero(bad)[:5]}"
+    agree = ((sfl & FLAG_WIN_NOT_CONVERGED) == (gcf & FLAG_WIN_NOT_CONVERGED))
+    # the convergence decision (step^2 < tol2, FP32 against FP64) may differ only
+    # where one side stopped one update earlier: then the positions agree (above)
+    assert agree.mean() > 0.97, agree.mean()
+    ph = orc.aperture(gsub, gx.astype(np.float32), gy.astype(np.float32), r_ap, r_in, r_out)
+    assert np.array_equal(g["n_ann"][ig], ph["n_ann"]), "n_ann"
+    assert np.array_equal(g["phot_flags"][ig], ph["flags"]), "aperture flags"
+    assert np.array_equal(g["sky"][ig], ph["sky"].astype(np.float32)), "sky"
+    assert np.all(np.abs(g["area"][ig] - ph["area"]) <= 2e-5 * ph["area"] + 1e-6), "area"
+    rms = float(np.median(oc["rms"]))
+    scale = np.abs(ph["flux"]) + ph["area"] * (np.abs(ph["sky"]) + rms)
+    err = np.abs(g["flux"][ig] - ph["flux"])
+    assert np.all(err <= 1e-5 * scale), f"flux, max rel err {np.max(err / scale)}"
+
+    # end to end against the oracle's own catalog.  Positions: both iterate on
+    # frames that differ by at most dsub; the centroid moves by at most
+    # 2 * sum(w |dsub| |x_i - x|) / sum(w sub), bounded here by the window's
+    # pixel count times dsub times its radius over the window flux.
+    ox, oy, ocf = oc["x"][io], oc["y"][io], oc["cen_flags"][io]
+    conv2 = ((ocf & FLAG_WIN_NOT_CONVERGED) == 0) | ((gcf & FLAG_WIN_NOT_CONVERGED) == 0)
+    sw = 3.0 / 2.3548200450309493
+    rad = 4 * sw
+    wflux = np.abs(ost["sum"][io]) + 1.0
+    shift = 2 * np.pi * rad ** 2 * dsub.max() * rad / wflux
+    tol2 = 3e-4 + 2 * float_ulp(ox) + shift
+    bad = conv2 & ((np.abs(gx - ox) > tol2) | (np.abs(gy - oy) > tol2))
+    assert not bad.any(), f"{bad.sum()} end-to-end centroids differ"
+    eps = np.where(conv2, np.maximum(np.abs(gx - ox), np.abs(gy - oy)) * 1.5 + 1e-6, np.inf)
+    flip = _ann_boundary_margin(gx, gy, r_in, r_out, W, H, eps)
+    ok = conv2 & ~flip
+    assert np.array_equal(g["n_ann"][ig][ok], oc["n_ann"][io][ok]), "end-to-end n_ann"
+    dsky = np.abs(g["sky"][ig] - oc["sky"][io])
+    assert np.all(dsky[ok] <= dsub.max() + 2e-5 * np.abs(oc["sky"][io][ok]) + 1e-6), "end-to-end sky"
+    # flux: the aperture's value moves with the position (|grad| <= sum w |d sub/dx|,
+    # bounded by the aperture's pixel sum of |sub| over one pixel) and with dsub
+    oscale = np.abs(oc["flux"][io]) + oc["area"][io] * (np.abs(oc["sky"][io]) + rms)
+    pos_err = np.maximum(np.abs(gx - ox), np.abs(gy - oy))
+    fl_tol = 1e-5 * oscale + 2 * oc["area"][io] * dsub.max() + pos_err * 4 * oscale
+    assert np.all(np.abs(g["flux"][ig] - oc["flux"][io])[ok] <= fl_tol[ok]), "end-to-end flux"
+    return dict(matched=len(pairs), oK=oK, gK=gK, o_unclean=o_bad, g_unclean=g_bad,
+                near=int(near.sum()), end_to_end=int(ok.sum()))

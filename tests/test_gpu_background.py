@@ -193,3 +193,37 @@ def test_bg_estimate_extreme_scales(gpu, orc, scale):
     assert v.all()
     _cmp_mesh(host(rb)[v], host(rr)[v], st["raw_bkg"][v], st["raw_rms"][v], atol=1e-30)
     _cmp_mesh(host(gb), host(gr), ob, orr, atol=1e-30)
+
+
+def _timed_bg(gpu, t, **kw):
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    out = gpu.bg_estimate(t, raw=True, **kw)
+    e.record()
+    torch.cuda.synchronize()
+    return out, s.elapsed_time(e)
+
+
+def test_fill_large_grid_bounded_time(gpu, orc):
+    """Grids of 128 x 128 and 64 x 64 meshes (the two-pass fill path): all
+    meshes masked returns IPP_ERR_NO_VALID_MESH at once; a single valid mesh in
+    a corner (every other node filled from a ring far away) and a masked block
+    match the oracle's fill and filter.  Each call is bounded in time (the fill
+    is computed once per node, not once per window element)."""
+    img = np.random.default_rng(3).normal(100.0, 5.0, (512, 512)).astype(np.float32)
+    t = dev(img)
+    mask = np.ones(img.shape, np.uint8)
+    (gb, gr, rb, rr, st), ms = _timed_bg(gpu, t, mask=dev(mask), mesh=4, min_valid=4)
+    assert int(host(st)[0]) == 4 and np.all(host(gb) == 0) and ms < 50.0, ms
+    mask[:8, :8] = 0  # one valid mesh, top-left, of a 64 x 64 grid (the oracle's fill is cubic in k)
+    (gb, gr, rb, rr, st), ms = _timed_bg(gpu, t, mask=dev(mask), mesh=8, min_valid=4)
+    ob, orr, _ = orc.bg_estimate(img, mask=mask, mesh=8, min_valid=4)
+    assert int(host(st)[0]) == 0 and ms < 200.0, ms
+    _cmp_mesh(host(gb), host(gr), ob, orr)
+    mask[:] = 0
+    mask[100:400, 60:300] = 1
+    (gb, gr, rb, rr, st), ms = _timed_bg(gpu, t, mask=dev(mask), mesh=8, min_valid=4)
+    ob, orr, _ = orc.bg_estimate(img, mask=mask, mesh=8, min_valid=4)
+    assert int(host(st)[0]) == 0 and ms < 200.0, ms
+    _cmp_mesh(host(gb), host(gr), ob, orr)

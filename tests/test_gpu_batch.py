@@ -81,3 +81,31 @@ def test_batch_autotune_picks_a_lane_count(gpu):
     best, ms = b.autotune()
     assert best in (1, 2, 4, 8) and all(m > 0 for m in ms)
     b.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_matches_oracle(gpu, orc, graph):
+    """every frame of a mixed batch (plain run, and the captured graph replayed)
+    against the oracle's whole path on that frame: the matched-catalog
+    comparison of the per-frame tests, frame by frame."""
+    from catalog_match import assert_catalog
+    from test_gpu_extract import host_catalog
+    frames = _frames()
+    b = gpu.Batch(frames, lanes=3, cfg=gpu.BgConfig(mesh=64), max_src=4096)
+    b.run()
+    torch.cuda.synchronize()
+    if graph:
+        s = torch.cuda.Stream()
+        b.capture(s)
+        for o in b.outs:  # the replay must rewrite every output
+            o["labels"].fill_(-1)
+            o["x"].fill_(float("nan"))
+        b.launch(s)
+        s.synchronize()
+    for i, f in enumerate(frames):
+        img = host(f)
+        oc = orc.catalog(img, mesh=64)
+        g, st = host_catalog(b.outs[i], b.stats[i])
+        summ = assert_catalog(orc, img, oc, g, st, 64)
+        assert summ["matched"] >= 0.97 * summ["oK"], (i, summ)
+    b.close()
