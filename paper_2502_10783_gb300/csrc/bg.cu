@@ -34,6 +34,7 @@ constexpr int MS_GCAP = 512;         // gathered values of unstored median bins
 constexpr int MS_BAND = 8;           // median band half-width in bins (at most)
 constexpr int MS_CHUNK = 8;          // loads in flight per thread
 constexpr int MS_WARPSORT_MAX = 256;
+constexpr int MS_WARP_SCAN = 192;   // removal ranges up to this length are scanned by warp 0 alone
 
 // slots of MeshShared::bc_i
 enum { BI_STATE = 0, BI_MODE, BI_KBL, BI_KBH, BI_GL, BI_GH, BI_GCNT, BI_NEED, BI_RB0, BI_RR0, BI_RB1, BI_RR1,
@@ -103,7 +104,7 @@ __device__ __forceinline__ bool mesh_value_at(const MeshGeom& G, int r, int c, f
 // any is used: addresses are clamped into the mesh and slots beyond it are
 // skipped afterwards.  Every call forms the values with the same arithmetic, so
 // re-reads see identical values.
-template <class F>
+template <int T = MS_THREADS, class F>
 __device__ __forceinline__ void mesh_for_each(const MeshGeom& G, F&& f) {
     if (G.vec) {
         constexpr int VCH = 4;
@@ -111,9 +112,9 @@ __device__ __forceinline__ void mesh_for_each(const MeshGeom& G, F&& f) {
         const float4* base = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(G.img) + G.y0 * G.pitch +
                                                              G.x0);
         const int64_t p4 = G.pitch >> 2;
-        const int dr = MS_THREADS / qpr, dc = MS_THREADS - dr * qpr;
+        const int dr = T / qpr, dc = T - dr * qpr;
         int r = threadIdx.x / qpr, c = threadIdx.x - r * qpr;
-        for (int e0 = threadIdx.x; e0 < nq; e0 += VCH * MS_THREADS) {
+        for (int e0 = threadIdx.x; e0 < nq; e0 += VCH * T) {
             float4 q[VCH];
 #pragma unroll
             for (int j = 0; j < VCH; j++) {
@@ -124,7 +125,7 @@ __device__ __forceinline__ void mesh_for_each(const MeshGeom& G, F&& f) {
             }
 #pragma unroll
             for (int j = 0; j < VCH; j++) {
-                if (e0 + j * MS_THREADS >= nq) continue;
+                if (e0 + j * T >= nq) continue;
                 if (isfinite(q[j].x)) f(q[j].x);
                 if (isfinite(q[j].y)) f(q[j].y);
                 if (isfinite(q[j].z)) f(q[j].z);
@@ -133,14 +134,14 @@ __device__ __forceinline__ void mesh_for_each(const MeshGeom& G, F&& f) {
         }
         return;
     }
-    const int dr = MS_THREADS / G.mw, dc = MS_THREADS - dr * G.mw;
+    const int dr = T / G.mw, dc = T - dr * G.mw;
     int r = threadIdx.x / G.mw, c = threadIdx.x - r * G.mw;
-    for (int e0 = threadIdx.x; e0 < G.slots; e0 += MS_CHUNK * MS_THREADS) {
+    for (int e0 = threadIdx.x; e0 < G.slots; e0 += MS_CHUNK * T) {
         float v[MS_CHUNK];
         bool ok[MS_CHUNK];
 #pragma unroll
         for (int j = 0; j < MS_CHUNK; j++) {
-            const bool in = e0 + j * MS_THREADS < G.slots && r < G.he && c < G.we;
+            const bool in = e0 + j * T < G.slots && r < G.he && c < G.we;
             ok[j] = mesh_value_at(G, min(r, G.he - 1), min(c, G.we - 1), &v[j]) && in;
             r += dr;
             c += dc;
@@ -172,6 +173,28 @@ __device__ __forceinline__ void sums_add(Sums& a, float v, int b, float cstar, f
         q = df_add_f(q, __fmul_rn(2.0f * d.hi, d.lo));
         a.o1 = df_add(a.o1, d);
         a.o2 = df_add(a.o2, q);
+    }
+}
+
+// Read-1 accumulation of one value: its bin's count, and the sums of sums_add
+// with the in-window part in per-thread registers (a1: at most 128 values of
+// |d| <= 2^23 per thread, so int32 holds it).  The same bins and fixed-point
+// values as bin_of and sums_add.
+__device__ __forceinline__ void hist_acc(uint32_t* hist, float x, float cstar, float inv_bw, int& a1, long long& a2,
+                                         Sums& o) {
+    const float t = (x - cstar) * inv_bw;
+    const int f = min(max(__float2int_rd(t), -MS_NB / 2 - 1), MS_NB / 2);
+    atomicAdd(&hist[f + MS_NB / 2 + 1], 1u);
+    if (f >= -MS_NB / 2 && f < MS_NB / 2) {
+        const int d = __float2int_rn(t * (float)(1 << MS_SCALE_BITS));
+        a1 += d;
+        a2 += (long long)d * d;
+    } else {
+        const df dd = two_sum(x, -cstar);
+        df q = sq_exact(dd.hi);
+        q = df_add_f(q, __fmul_rn(2.0f * dd.hi, dd.lo));
+        o.o1 = df_add(o.o1, dd);
+        o.o2 = df_add(o.o2, q);
     }
 }
 
@@ -506,11 +529,12 @@ __device__ __forceinline__ void kept_stats(long long i1, long long i2, df o1, df
 
 // Warp 0 only: exclusive prefix of the histogram counts into S.hstart, and the
 // bins holding the order statistics kq[0..2] (broadcast to every lane).
-__device__ __forceinline__ void warp0_scan_counts(MeshShared& S, int lane, const int kq[3], int bq[3]) {
+__device__ __forceinline__ void warp_scan_counts(const uint32_t* counts, uint32_t* hstart, int lane, const int kq[3],
+                                                 int bq[3]) {
     constexpr int PER = (MS_NBT + 31) / 32;
     const int b0 = lane * PER, b1 = min(b0 + PER, MS_NBT);
     int acc = 0;
-    for (int b = b0; b < b1; b++) acc += (int)S.hbuf[b];
+    for (int b = b0; b < b1; b++) acc += (int)counts[b];
     int inc = acc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -521,20 +545,24 @@ __device__ __forceinline__ void warp0_scan_counts(MeshShared& S, int lane, const
     int loc[3] = {0, 0, 0};
     unsigned hit = 0;
     for (int b = b0; b < b1; b++) {
-        const int h = (int)S.hbuf[b];
-        S.hstart[b] = (uint32_t)run;
+        const int h = (int)counts[b];
+        hstart[b] = (uint32_t)run;
 #pragma unroll
         for (int t = 0; t < 3; t++)
             if (kq[t] >= run && kq[t] < run + h) { loc[t] = b; hit |= 1u << t; }
         run += h;
     }
-    if (lane == 31) S.hstart[MS_NBT] = (uint32_t)inc;
+    if (lane == 31) hstart[MS_NBT] = (uint32_t)inc;
 #pragma unroll
     for (int t = 0; t < 3; t++) {
         const unsigned who = __ballot_sync(0xffffffffu, (hit >> t) & 1u);
         bq[t] = __shfl_sync(0xffffffffu, loc[t], who ? __ffs(who) - 1 : 0);
     }
     __syncwarp();
+}
+
+__device__ __forceinline__ void warp0_scan_counts(MeshShared& S, int lane, const int kq[3], int bq[3]) {
+    warp_scan_counts(S.hbuf, S.hstart, lane, kq, bq);
 }
 
 // Warp 0 only: value of rank r (among kept values) in bin b, when it is on chip:
@@ -659,17 +687,17 @@ __global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
     // centre, count, min, max ----------------------------------------------------
     Sums tot{0, 0, df{0.f, 0.f}, df{0.f, 0.f}};
     {
-        const float fxs0 = ldexpf(1.0f, MS_SCALE_BITS - e);
-        int n_loc = 0;
+        int n_loc = 0, a1 = 0;
+        long long a2 = 0;
         float vmin = INFINITY, vmax = -INFINITY;
         mesh_for_each(G, [&](float x) {
-            const int b = bin_of(x, cstar, inv_bw);
-            atomicAdd(&S.hbuf[b], 1u);
-            sums_add(tot, x, b, cstar, fxs0);
+            hist_acc(S.hbuf, x, cstar, inv_bw, a1, a2, tot);
             n_loc++;
             vmin = fminf(vmin, x);
             vmax = fmaxf(vmax, x);
         });
+        tot.i1 = a1;
+        tot.i2 = a2;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
@@ -771,12 +799,11 @@ __global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
         for (int k = threadIdx.x; k < MS_NBT; k += MS_THREADS) S.hbuf[k] = 0;
         __syncthreads();
         tot = Sums{0, 0, df{0.f, 0.f}, df{0.f, 0.f}};
-        const float fxs1 = ldexpf(1.0f, MS_SCALE_BITS - e);
-        mesh_for_each(G, [&](float x) {  // re-read (L2)
-            const int b = bin_of(x, cstar, inv_bw);
-            atomicAdd(&S.hbuf[b], 1u);
-            sums_add(tot, x, b, cstar, fxs1);
-        });
+        int a1 = 0;
+        long long a2 = 0;
+        mesh_for_each(G, [&](float x) { hist_acc(S.hbuf, x, cstar, inv_bw, a1, a2, tot); });  // re-read (L2)
+        tot.i1 = a1;
+        tot.i2 = a2;
         __syncthreads();
     }
 
@@ -848,17 +875,16 @@ __global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
         warp_partial(S, tot, cz, lane, warp);  // sums of the whole set, from the last histogram read
     }
     __syncthreads();  // scatter and partials complete; S.hbuf is free from here on
-    // sort the band bins now, one warp per bin, off the serial path of the clip
-    for (int b = St.ml + warp; b <= St.mh; b += MS_WARPS)
-        if ((int)(S.sstart[b + 1] - S.sstart[b]) <= MS_WARPSORT_MAX) warp_ensure_sorted(S, b, lane);
-    __syncthreads();
+    // (the band's bins are sorted when a pass first needs one: typically one or
+    // two of them hold a median over all passes)
 
     // ---- clip passes ----------------------------------------------------------
-    // Warp 0 owns the kept set: it reduces the last pass's removals, selects the
-    // median, evaluates Eq. 1-2's statistics and the next bounds and publishes
-    // them.  Every warp then finds the values the new bounds remove: in the
-    // stored tails when the bounds fall there, else by reading the mesh again.
-    // Two barriers per pass; two more when a median bin must be fetched.
+    // Warp 0 owns the kept set: it selects the median, evaluates Eq. 1-2's
+    // statistics and the next bounds, and -- when the values a pass removes are
+    // on chip and few -- finds and subtracts them itself and goes on to the
+    // next pass without the block.  The block joins (two barriers) only for a
+    // long removal range (the first passes over bright stars), a removal that
+    // must read the mesh again, or a median bin that must be fetched.
     KeptSet K;
     K.lo = -INFINITY; K.hi = INFINITY; K.bl = 0; K.bh = MS_NB + 1;
     K.nbl = (int)(S.hstart[1] - S.hstart[0]);
@@ -866,6 +892,11 @@ __global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
     K.n = n0;
     float plo = 0.f, phi = 0.f;   // bounds of the pending pass (warp 0)
     int bm[2] = {0, 0}, rm[2] = {0, 0};  // median bins and ranks of the current set (warp 0)
+    int it = 0;                   // passes whose bounds are set (warp 0)
+    int pend = 0;                 // removals to apply: 1 in the block partials, 2 in wrem / wc (warp 0)
+    int fetched = ST_STOP;        // a median fetch just served by the block (warp 0)
+    Sums wrem{0, 0, df{0.f, 0.f}, df{0.f, 0.f}};
+    int wc[3] = {0, 0, 0};
     if (warp == 0) {
         int cz[3];
         df o1, o2;
@@ -877,20 +908,27 @@ __global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
         }
         __syncwarp();
     }
-    for (int it = 0;; it++) {
+    // Every round of this loop either ends it, completes a pass, or serves a
+    // fetch that the next round's pass consumes: at most 3 (maxiters + 1)
+    // rounds.  The cap only guards that bound.
+    for (int round = 0; round < 3 * (J.maxiters + 2); round++) {
         if (warp == 0) {
             int state = ST_STOP;
-            bool cont = true;
-            if (it > 0) {  // removals of pass it-1
-                int c[3];
-                long long i1, i2;
-                df o1, o2;
-                warp0_totals(S, lane, c, &i1, &i2, &o1, &o2);
-                // no value dropped: the set is stable (c >= n cannot happen: the
-                // median lies inside [med - k sd, med + k sd])
-                if (c[0] == 0 || c[0] >= K.n) {
-                    cont = false;
-                } else {
+            for (int guard = 0; guard <= J.maxiters + 1; guard++) {
+                if (pend) {  // removals of the last pass
+                    int c[3];
+                    long long i1, i2;
+                    df o1, o2;
+                    if (pend == 1) {
+                        warp0_totals(S, lane, c, &i1, &i2, &o1, &o2);
+                    } else {
+                        c[0] = wc[0]; c[1] = wc[1]; c[2] = wc[2];
+                        i1 = wrem.i1; i2 = wrem.i2; o1 = wrem.o1; o2 = wrem.o2;
+                    }
+                    pend = 0;
+                    // no value dropped: the set is stable (c >= n cannot happen: the
+                    // median lies inside [med - k sd, med + k sd])
+                    if (c[0] == 0 || c[0] >= K.n) { state = ST_STOP; break; }
                     if (lane == 0) {
                         S.ks_i[0] -= i1; S.ks_i[1] -= i2;
                         S.ks_o[0] = df_sub(S.ks_o[0], o1); S.ks_o[1] = df_sub(S.ks_o[1], o2);
@@ -900,42 +938,88 @@ __global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
                     K.nbl = c[1]; K.nbh = c[2];
                     K.n -= c[0];
                 }
-            }
-            if (cont) {
-                kept_locate(S, K, (K.n - 1) / 2, lane, &bm[0], &rm[0]);
-                kept_locate(S, K, K.n / 2, lane, &bm[1], &rm[1]);
                 float mid[2];
-                bool have[2];
+                if (fetched != ST_STOP) {  // the median bins the block just fetched
+                    const int needm = S.bc_i[BI_NEED];
 #pragma unroll
-                for (int q = 0; q < 2; q++)
-                    have[q] = warp_value_of(S, St, bm[q], rm[q], K, cstar, inv_bw, lane, &mid[q]);
-                if (have[0] && have[1]) {
-                    state = warp0_finish(S, J, St, K, mid[0], mid[1], it, cstar, e, inv_bw, nsig, lane, &plo, &phi);
-                } else {
-                    // fetch the median bins that are not stored (both, so that a new
-                    // gather never drops one the old gather held): gather them when
-                    // they fit, else select from the mesh directly
-                    const bool u0 = !St.bin(bm[0]), u1 = !St.bin(bm[1]);
-                    const int gl = u0 ? bm[0] : bm[1], gh = u1 ? bm[1] : bm[0];
-                    const int need = (int)(S.hstart[gh + 1] - S.hstart[gl]);
-                    if (lane == 0) {
-                        S.bc_f[2] = K.lo; S.bc_f[3] = K.hi;
-                        S.bc_i[BI_NEED] = (!have[0]) | ((!have[1]) << 1);
-                        S.bc_i[BI_RB0] = bm[0]; S.bc_i[BI_RR0] = rm[0];
-                        S.bc_i[BI_RB1] = bm[1]; S.bc_i[BI_RR1] = rm[1];
-                        if (need <= MS_GCAP) {
-                            S.bc_i[BI_GL] = gl; S.bc_i[BI_GH] = gh; S.bc_i[BI_GCNT] = 0;
-                        }
+                    for (int q = 0; q < 2; q++) {
+                        if (fetched == ST_RADIX && ((needm >> q) & 1)) mid[q] = S.bc_f[6 + q];
+                        else warp_value_of(S, St, bm[q], rm[q], K, cstar, inv_bw, lane, &mid[q]);
                     }
-                    state = need <= MS_GCAP ? ST_GATHER : ST_RADIX;
+                    fetched = ST_STOP;
+                } else {
+                    kept_locate(S, K, (K.n - 1) / 2, lane, &bm[0], &rm[0]);
+                    kept_locate(S, K, K.n / 2, lane, &bm[1], &rm[1]);
+                    bool have[2];
+#pragma unroll
+                    for (int q = 0; q < 2; q++)
+                        have[q] = warp_value_of(S, St, bm[q], rm[q], K, cstar, inv_bw, lane, &mid[q]);
+                    if (!(have[0] && have[1])) {
+                        // fetch the median bins that are not stored (both, so that a new
+                        // gather never drops one the old gather held): gather them when
+                        // they fit, else select from the mesh directly
+                        const bool u0 = !St.bin(bm[0]), u1 = !St.bin(bm[1]);
+                        const int gl = u0 ? bm[0] : bm[1], gh = u1 ? bm[1] : bm[0];
+                        const int need = (int)(S.hstart[gh + 1] - S.hstart[gl]);
+                        if (lane == 0) {
+                            S.bc_f[2] = K.lo; S.bc_f[3] = K.hi;
+                            S.bc_i[BI_NEED] = (!have[0]) | ((!have[1]) << 1);
+                            S.bc_i[BI_RB0] = bm[0]; S.bc_i[BI_RR0] = rm[0];
+                            S.bc_i[BI_RB1] = bm[1]; S.bc_i[BI_RR1] = rm[1];
+                            if (need <= MS_GCAP) {
+                                S.bc_i[BI_GL] = gl; S.bc_i[BI_GH] = gh; S.bc_i[BI_GCNT] = 0;
+                            }
+                        }
+                        state = need <= MS_GCAP ? ST_GATHER : ST_RADIX;
+                        fetched = state;
+                        break;
+                    }
                 }
+                state = warp0_finish(S, J, St, K, mid[0], mid[1], it, cstar, e, inv_bw, nsig, lane, &plo, &phi);
+                __syncwarp();   // lane 0's statistics and bounds in shared memory are visible to the warp
+                if (state == ST_STOP) break;
+                it++;
+                // removals on chip (the same decision warp0_finish published, taken from
+                // registers every lane holds): scanned here when the range is short
+                const int nbl_bin = bin_of(plo, cstar, inv_bw), nbh_bin = bin_of(phi, cstar, inv_bw);
+                if (St.range(K.bl, nbl_bin) && St.range(max(nbh_bin, nbl_bin + 1), K.bh)) {
+                    const int a0 = S.sstart[K.bl], a1 = S.sstart[nbl_bin + 1];
+                    const int ub = max(nbh_bin, nbl_bin + 1);
+                    const int b0 = ub <= K.bh ? (int)S.sstart[ub] : 0, b1 = ub <= K.bh ? (int)S.sstart[K.bh + 1] : 0;
+                    if ((a1 - a0) + (b1 - b0) <= MS_WARP_SCAN) {
+                        Sums rem{0, 0, df{0.f, 0.f}, df{0.f, 0.f}};
+                        int c[3] = {0, 0, 0};
+                        for (int k = a0 + lane; k < a1; k += kWarp) {
+                            const float x = S.store[k];
+                            if (!(x >= K.lo && x <= K.hi)) continue;
+                            if (x < plo || x > phi) { c[0]++; sums_add(rem, x, bin_of(x, cstar, inv_bw), cstar, fxs); }
+                            else if (k >= (int)S.sstart[nbl_bin]) c[1]++;
+                        }
+                        for (int k = b0 + lane; k < b1; k += kWarp) {
+                            const float x = S.store[k];
+                            if (!(x >= K.lo && x <= K.hi)) continue;
+                            if (x < plo || x > phi) { c[0]++; sums_add(rem, x, bin_of(x, cstar, inv_bw), cstar, fxs); }
+                            else if (k < (int)S.sstart[nbh_bin + 1] && nbh_bin != nbl_bin) c[2]++;
+                        }
+                        wc[0] = warp_sum_i(c[0]); wc[1] = warp_sum_i(c[1]); wc[2] = warp_sum_i(c[2]);
+                        const bool anyo = __any_sync(0xffffffffu, rem.o1.hi != 0.f || rem.o2.hi != 0.f);
+                        wrem.i1 = warp_sum_ll(rem.i1);
+                        wrem.i2 = warp_sum_ll(rem.i2);
+                        wrem.o1 = anyo ? warp_sum_df(rem.o1) : df{0.f, 0.f};
+                        wrem.o2 = anyo ? warp_sum_df(rem.o2) : df{0.f, 0.f};
+                        pend = 2;
+                        continue;
+                    }
+                }
+                pend = 1;  // the block scans this pass's removals
+                break;
             }
             if (lane == 0) S.bc_i[BI_STATE] = state;
         }
         __syncthreads();
-        int state = S.bc_i[BI_STATE];
+        const int state = S.bc_i[BI_STATE];
         if (state == ST_STOP) break;
-        if (state != ST_SCAN) {  // fetch median bins (block-wide), then finish on warp 0
+        if (state != ST_SCAN) {  // fetch median bins (block-wide); warp 0 then goes on from the fetched values
             const float klo = S.bc_f[2], khi = S.bc_f[3];
             if (state == ST_GATHER) {
                 const int gl = S.bc_i[BI_GL], gh = S.bc_i[BI_GH];
@@ -956,20 +1040,7 @@ __global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
                 }
             }
             __syncthreads();
-            if (warp == 0) {
-                float mid[2];
-                const int needm = S.bc_i[BI_NEED];
-#pragma unroll
-                for (int q = 0; q < 2; q++) {
-                    if (state == ST_RADIX && ((needm >> q) & 1)) mid[q] = S.bc_f[6 + q];
-                    else warp_value_of(S, St, bm[q], rm[q], K, cstar, inv_bw, lane, &mid[q]);
-                }
-                const int st2 = warp0_finish(S, J, St, K, mid[0], mid[1], it, cstar, e, inv_bw, nsig, lane, &plo, &phi);
-                if (lane == 0) S.bc_i[BI_STATE] = st2;
-            }
-            __syncthreads();
-            state = S.bc_i[BI_STATE];
-            if (state == ST_STOP) break;
+            continue;
         }
         const float nlo = S.bc_f[0], nhi = S.bc_f[1], klo = S.bc_f[2], khi = S.bc_f[3];
         const int kbl = S.bc_i[BI_KBL], kbh = S.bc_i[BI_KBH];

