@@ -29,6 +29,8 @@ sys.path.insert(0, ROOT)
 MESH = 128
 W = H = 4096
 METRIC = "Mpix/s end-to-end per GB300 (catalog path, 4096^2 survey frame)"
+WORKLOAD = ("survey_4k: 4096x4096 float32 field, 20,000 stars, hot pixels, cosmic rays; "
+            "mesh 128, 3x3 filter, k=1.5, min_area 5, r=5, annulus 8-12")
 # kernels ipp_extract launches per frame: mesh statistics, mesh filter,
 # subtract+threshold, tile labeling, seam union, resolve, count, scan, emit,
 # label map, centroid, aperture (plus one memset of the counters)
@@ -133,25 +135,61 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_reference(steps, warmup, img=None):
-    """The FP64 oracle, as it stands, on a bounded 1024 x 1024 crop per step."""
-    import numpy as np
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
+
+def oracle_all_cores():
+    """The oracle's OpenMP build on every core this process may use (the same
+    source and arithmetic; meshes, rows, sources and stamps spread over threads,
+    CCL serial).  Returns the thread count, or 1 when OpenMP cannot be built."""
+    import oracle
+    n = host_cores()
+    if n > 1:
+        try:
+            oracle.use_openmp(n)
+        except Exception:
+            return 1
+    return n
+
+
+def cpu_reference(steps, warmup, img=None, cores=None):
+    """The FP64 oracle, as it stands, on the full 4096 x 4096 survey frame per
+    step, on all host cores (cores = the threads it used)."""
     import oracle
     import synth
+    if cores is None:
+        cores = oracle_all_cores()
     if img is None:
         img, _ = synth.frame_survey_4k()
-    crops = [np.ascontiguousarray(img[r:r + 1024, c:c + 1024]) for r, c in
-             [(0, 0), (1024, 2048), (2048, 1024), (3072, 3072)]]
     for k in range(warmup):
-        oracle.catalog(crops[k % 4], mesh=MESH)
+        oracle.catalog(img, mesh=MESH)
     t0 = time.perf_counter()
     nsrc = 0
     for k in range(steps):
+        nsrc += oracle.catalog(img, mesh=MESH)["K"]
+    dt = time.perf_counter() - t0
+    return dict(value=steps * W * H / 1e6 / dt, sec=dt, sources_per_s=nsrc / dt, steps=steps, cores=cores,
+                sample=f"{steps} full 4096^2 survey frames, mesh {MESH}, OpenMP build on {cores} threads")
+
+
+def cpu_single_core(img, n=4):
+    """The plain (single-threaded) oracle on 1024^2 crops of the frame."""
+    import numpy as np
+
+    import oracle
+    crops = [np.ascontiguousarray(img[r:r + 1024, c:c + 1024]) for r, c in
+             [(0, 0), (1024, 2048), (2048, 1024), (3072, 3072)]]
+    t0 = time.perf_counter()
+    nsrc = 0
+    for k in range(n):
         nsrc += oracle.catalog(crops[k % 4], mesh=MESH)["K"]
     dt = time.perf_counter() - t0
-    return dict(value=steps * 1024 * 1024 / 1e6 / dt, sec=dt, sources_per_s=nsrc / dt, steps=steps,
-                sample=f"{steps} crops of 1024x1024 px of the 4096^2 survey frame, mesh {MESH}")
+    return {"value": n * 1024 * 1024 / 1e6 / dt, "unit": "Mpix/s", "cores": 1, "sources_per_s": nsrc / dt,
+            "sample": f"{n} crops of 1024x1024 px of the survey frame, plain build"}
 
 
 def batch_leg(ipp, synth, dev, n_frames, reps=5):
@@ -212,7 +250,7 @@ def raw_stream_leg(ipp, synth, dev, n_steps, n_resident=4):
     8,000 stars on a 1000 +- 50 ADU sky) resident on the device, streamed
     through bias/flat correction fused into the first reads, the catalog path,
     15 x 15 stamp cuts at the measured positions and the batched PSF fit of every
-    catalog row (the fit needs the row count on the host: one 4-byte read per
+    catalog row; the row count stays on the device (no host round trip per
     frame).  Reports frames/s and sources/s."""
     import numpy as np
     import torch
@@ -232,31 +270,34 @@ def raw_stream_leg(ipp, synth, dev, n_steps, n_resident=4):
     ex = ipp.Extractor(W, H, cfg, device=dev, max_src=65536)
     calib = (inv_flat, 500.0)
 
+    nsrc_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    fit_out = {}
+
     def step(k):
+        # the catalog count stays on the device: stamp cut and fit take it from there
         o = ex(raws[k % n_resident], calib=calib)
-        n = int(o["n_src"].item())
-        n = min(n, ex.max_src)
-        st = ipp.stamp_cut(o["sub"], o["x"], o["y"], n_src=o["n_src"], S=15, max_src=n)
-        fit = ipp.psf_fit(st["stamps"][:n], weights=st["weights"][:n])
-        return n, fit
+        st = ipp.stamp_cut(o["sub"], o["x"], o["y"], n_src=o["n_src"], S=15, max_src=ex.max_src)
+        fit = ipp.psf_fit(st["stamps"], weights=st["weights"], n_src=o["n_src"], out=fit_out.get("o"))
+        fit_out["o"] = fit
+        nsrc_dev.add_(o["n_src"].clamp(max=ex.max_src))
 
     for k in range(2):
         step(k)
     torch.cuda.synchronize(dev)
+    nsrc_dev.zero_()
     stream = torch.cuda.current_stream(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nsrc = 0
     a.record(stream)
     for k in range(n_steps):
-        n, _ = step(k)
-        nsrc += n
+        step(k)
     b.record(stream)
     torch.cuda.synchronize(dev)
     ms = a.elapsed_time(b)
+    nsrc = int(nsrc_dev.item())
     return {"frames": n_steps, "frames_per_s": n_steps / (ms / 1e3), "sources_per_s": nsrc / (ms / 1e3),
             "ms_per_frame": ms / n_steps, "sources_per_frame": nsrc / max(n_steps, 1),
             "workload": "raw uint16 4096^2, bias 500, radial flat 0.9-1.1, 8,000 stars; calibration + catalog + "
-                        "15x15 stamp cut + Moffat PSF fit of every catalog row, on one stream"}
+                        "15x15 stamp cut + Moffat PSF fit of every catalog row, on one stream, counts on the device"}
 
 
 def main():
@@ -270,6 +311,9 @@ def main():
     ap.add_argument("--batch-frames", type=int, default=12)
     ap.add_argument("--raw-frames", type=int, default=10)
     ap.add_argument("--lanes", type=int, default=4, help="CUDA streams that consecutive frames rotate over")
+    ap.add_argument("--soak-steps", type=int, default=3000,
+                    help="steps run under the clock sampler before the timed ones (>= 1 s)")
+    ap.add_argument("--cfg1-steps", type=int, default=200, help="1024^2 frames of the small-field line")
     args = ap.parse_args()
     ws, rank, local = dist_init()
 
@@ -281,9 +325,9 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * r["sec"] / max(args.steps, 1), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "survey_4k crop 1024x1024 (oracle sample)", "mesh": MESH},
-                "cpu_baseline": {"value": r["value"], "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-                                 "sample": r["sample"]},
+                "config": {"workload": WORKLOAD},
+                "cpu_baseline": {"value": r["value"], "unit": "Mpix/s", "cores": r["cores"], "kind": "oracle",
+                                 "sample": r["sample"], "sources_per_s": r["sources_per_s"]},
                 "e2e": {"value": r["value"], "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -338,16 +382,28 @@ def main():
             dist.barrier()
 
     # ---- device-resident timed region ----------------------------------------
+    # The clock sampler runs from a soak of >= 1 s of the same steps (timed too,
+    # reported as `soak`) straight into the K timed steps, so that the clocks
+    # and throttle reasons cover the timed region at steady state.
+    soak_n = max(args.soak_steps, 0)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
+        s0.record(stream)
+        run_steps(soak_n, step)
+        s1.record(stream)
         e0.record(stream)
         run_steps(args.steps, step)
         e1.record(stream)
         torch.cuda.synchronize(dev)
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    soak = None
+    if soak_n:
+        sms = max_over_ranks(s0.elapsed_time(s1), ws, dev)
+        soak = {"steps": soak_n, "ms": sms, "mpix_per_s": whole_job_rate(W * H / 1e6, soak_n, ws, sms)}
     K = int(ex.out["n_src"].item())
     mpix_step = W * H / 1e6
     value = whole_job_rate(mpix_step, args.steps, ws, ms)
@@ -373,7 +429,7 @@ def main():
 
     run_steps(3, e2e_step)
     torch.cuda.synchronize(dev)
-    n_e2e = max(5, args.steps // 5)
+    n_e2e = max(50, args.steps)
     barrier()
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a0.record(stream)
@@ -382,6 +438,32 @@ def main():
     torch.cuda.synchronize(dev)
     ms_e2e = max_over_ranks(a0.elapsed_time(a1), ws, dev)
     e2e_val = whole_job_rate(mpix_step, n_e2e, ws, ms_e2e)
+
+    # ---- the 1024^2 gradient field (mesh 64): the small configuration ---------
+    cfg1 = None
+    if args.cfg1_steps > 0:
+        img1, _ = synth.frame_gradient_1k(1001)
+        f1 = [torch.from_numpy(img1).to(dev) for _ in range(3)]
+        ex1 = [ipp.Extractor(1024, 1024, ipp.BgConfig(mesh=64), device=dev) for _ in range(L)]
+
+        def step1(k, ln):
+            ex1[ln](f1[k % 3], stream=lane_st[ln])
+
+        run_steps(5, step1)
+        torch.cuda.synchronize(dev)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        run_steps(args.cfg1_steps, step1)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms1 = max_over_ranks(c0.elapsed_time(c1), ws, dev)
+        k1 = int(ex1[0].out["n_src"].item())
+        cfg1 = {"workload": "gradient_1k: 1024x1024 float32, 1000 +- 50 ADU sky, 500 stars FWHM 3; mesh 64, 3x3 "
+                            "filter, k=1.5, min_area 5, r=5, annulus 8-12 (fits in L2: 3 rotating 4 MiB frames)",
+                "steps": args.cfg1_steps, "ms_per_step": ms1 / args.cfg1_steps,
+                "mpix_per_s": whole_job_rate(1024 * 1024 / 1e6, args.cfg1_steps, ws, ms1),
+                "sources_per_s": whole_job_rate(k1, args.cfg1_steps, ws, ms1), "sources_per_frame": k1}
+        del f1, ex1
 
     # ---- per-stage breakdown (separate calls, CUDA events on this stream) ------
     stages = {}
@@ -500,18 +582,15 @@ def main():
         torch.cuda.synchronize(dev)
         pms = p0.elapsed_time(p1)
         it = fit["iters"].float().mean().item()
+        conv = (fit["flags"] == 0).float().mean().item()
         psf = {"stamps_per_s": args.psf_stamps / (pms / 1e3), "ms": pms, "n": args.psf_stamps,
-               "mean_iters": it, "converged_frac": (fit["flags"] == 0).float().mean().item(),
+               "mean_iters": it, "converged_frac": conv,
+               "converged_stamps_per_s": conv * args.psf_stamps / (pms / 1e3),
+               "stop_rule": "Gauss-Newton decrease <= 1e-10 chi^2 + 1e-12 sum (m - sky)^2, or lambda > 1e10; "
+                            "max_iter 50 (faint stamps that crawl are flagged FIT_MAXITER)",
                "workload": "200,000 15x15 elliptical Moffat stamps (beta 2.5), 7-parameter LM, FP64 solve",
                "kernel": "k_psf_fit (one stamp per lane, 32 per warp)"}
-        if rank == 0 and not args.no_cpu_baseline:
-            import oracle
-            n_cpu = 1000
-            t0 = time.perf_counter()
-            oracle.psf_fit(stamps[:n_cpu])
-            dt = time.perf_counter() - t0
-            psf["cpu_baseline"] = {"value": n_cpu / dt, "unit": "stamps/s", "cores": 1, "kind": "oracle",
-                                   "sample": f"the first {n_cpu} of the same stamps"}
+        psf_stamps_host = stamps
 
     # ---- raw uint16 stream: calibration through PSF fit ------------------------
     raw = None
@@ -525,17 +604,33 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        r = cpu_reference(steps=8, warmup=1, img=img)
-        cpu = {"value": r["value"], "unit": "Mpix/s", "cores": 1, "kind": "oracle", "sample": r["sample"],
-               "sources_per_s": r["sources_per_s"]}
+        import oracle
+        single = cpu_single_core(img)          # plain build first: use_openmp switches the process
+        n_cpu = 1000
+        t0 = time.perf_counter()
+        if psf is not None:
+            oracle.psf_fit(psf_stamps_host[:n_cpu])
+        dt1 = time.perf_counter() - t0
+        cores = oracle_all_cores()
+        r = cpu_reference(steps=2, warmup=0, img=img, cores=cores)
+        cpu = {"value": r["value"], "unit": "Mpix/s", "cores": r["cores"], "kind": "oracle", "sample": r["sample"],
+               "sources_per_s": r["sources_per_s"], "single_core": single}
+        if psf is not None:
+            n_all = 4000
+            t0 = time.perf_counter()
+            oracle.psf_fit(psf_stamps_host[:n_all])
+            dt = time.perf_counter() - t0
+            psf["cpu_baseline"] = {"value": n_all / dt, "unit": "stamps/s", "cores": cores, "kind": "oracle",
+                                   "sample": f"the first {n_all} of the same stamps, OpenMP build",
+                                   "single_core": {"value": n_cpu / dt1, "unit": "stamps/s", "cores": 1,
+                                                   "sample": f"the first {n_cpu} stamps, plain build"}}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "survey_4k: 4096x4096 float32 field, 20,000 stars, hot pixels, cosmic rays; "
-                                   "mesh 128, 3x3 filter, k=1.5, min_area 5, r=5, annulus 8-12",
+            "config": {"workload": WORKLOAD,
                        "parallelism": f"replicas x{ws} (independent frames), {L} streams per GPU",
                        "l2": "inputs larger than L2: 3 rotating 64 MiB frames"},
             "sources_per_s": src_per_s, "sources_per_frame": K, "deblended_objects_per_frame": deblended_objects,
@@ -544,7 +639,8 @@ def main():
                     "d2h_bytes_per_step": 4 + 3 * 4 * nmax},
             "gpu_launches": KERNELS_PER_FRAME * args.steps,
             "roofline": roof, "step_roofline": whole, "stages_ms": stages, "gray_maps": gray, "alignment": align, "subtraction": subtraction,
-            "clocks": clk.summary(), "psf_fit": psf, "batched": batch, "raw_u16_stream": raw,
+            "clocks": clk.summary(), "soak": soak, "cfg1_1k": cfg1, "psf_fit": psf, "batched": batch,
+            "raw_u16_stream": raw,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

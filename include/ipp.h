@@ -660,9 +660,12 @@ int ipp_batch_autotune(const ipp_frame_desc* frames, int32_t n, const ipp_bg_par
  * Gaussian F/(2 pi sx sy) exp(-q/2) + sky.  Model, Jacobian and J'WJ in FP32;
  * the 7x7 damped normal equations solved in FP64 (LDL' factorisation).  One trial per
  * iteration: accepted when chi^2 drops (lambda /= 10), else lambda *= 10; widths
- * must stay above 0.05.  Converged when an accepted step lowers chi^2 by less
- * than 1e-6 relative (the FP32 chi^2 resolves ~1e-7; an FP64 evaluation would
- * use 1e-8), or when lambda exceeds 1e10.  Result canonicalised to
+ * must stay above 0.05.  Converged, before a trial, when the Gauss-Newton
+ * decrease g'(J'WJ)^-1 g (g = J'W r) is at most 1e-10 chi^2 + 1e-12 sum w
+ * (m - sky)^2 -- each parameter then lies within ~1.5e-4 standard errors of the
+ * optimum, and the second term covers what FP32 rounding of the model can
+ * fake -- or when lambda exceeds 1e10 (no step lowers chi^2).  Otherwise
+ * FIT_MAXITER after max_iter trials.  Result canonicalised to
  * sx >= sy and theta in [-pi/2, pi/2).
  *   stamps   device float[N*S*S]; weights nullable (same shape)
  *   init     nullable device float[N*7]; NULL = stamp centre, border-median sky,
@@ -672,6 +675,18 @@ int ipp_batch_autotune(const ipp_frame_desc* frames, int32_t n, const ipp_bg_par
 int ipp_psf_fit(const float* stamps, int64_t N, int32_t S, const float* weights,
                 const float* init, const ipp_fit_params* p, float* params, float* chi2,
                 int32_t* iters, int32_t* flags, void* stream);
+
+/*
+ * ipp_psf_fit_dev -- ipp_psf_fit with the stamp count in device memory:
+ * min(*n_dev, n_max) stamps are fitted (n_dev typically the detection count
+ * that ipp_stamp_cut filled), so no host copy of the count is needed between
+ * detection and the fit.  Grid and lanes per stamp are sized for n_max;
+ * outputs beyond the count are not written.  Errors as ipp_psf_fit; n_dev must
+ * not be NULL.
+ */
+int ipp_psf_fit_dev(const float* stamps, const int32_t* n_dev, int64_t n_max, int32_t S, const float* weights,
+                    const float* init, const ipp_fit_params* p, float* params, float* chi2, int32_t* iters,
+                    int32_t* flags, void* stream);
 
 /* Model images m[N*S*S] of params[N*7] (forward of the differentiable model). */
 int ipp_psf_model_fwd(const float* params, int64_t N, int32_t S, const ipp_fit_params* p,

@@ -37,16 +37,34 @@ EST_SIGMA, EST_MEDIAN, EST_MEAN, EST_FACTORS = 0, 1, 2, 3
 PSF_MOFFAT, PSF_GAUSS = 0, 1
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (no fused multiply-add)."""
-    stale = (not os.path.exists(_LIB)) or any(
-        os.path.getmtime(f) > os.path.getmtime(_LIB) for f in (_SRC, _HDR))
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile liboracle.so with gcc (no fused multiply-add).  openmp=True
+    builds liboracle_omp.so from the same source with -fopenmp: independent
+    meshes, pixel rows, sources and stamps spread over threads, CCL serial, the
+    arithmetic of each item unchanged (the all-cores CPU timing)."""
+    lib_path = _LIB_OMP if openmp else _LIB
+    stale = (not os.path.exists(lib_path)) or any(
+        os.path.getmtime(f) > os.path.getmtime(lib_path) for f in (_SRC, _HDR))
     if force or stale:
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-               _SRC, "-o", _LIB + ".tmp", "-lm"]
+               *(["-fopenmp"] if openmp else []), _SRC, "-o", lib_path + ".tmp", "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+        os.replace(lib_path + ".tmp", lib_path)
+    return lib_path
+
+
+def use_openmp(threads: int) -> None:
+    """Switch this process to the OpenMP build on `threads` threads (call before
+    the first oracle function; for the CPU timing only)."""
+    global _lib, _LIB
+    os.environ["OMP_NUM_THREADS"] = str(int(threads))
+    build(openmp=True)
+    with _lock:
+        _lib = None
+        _LIB = _LIB_OMP
 
 
 class Wcs(C.Structure):
@@ -86,7 +104,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
+            build(openmp=_LIB == _LIB_OMP)
             L = C.CDLL(_LIB)
             vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
             L.orc_calibrate.argtypes = [vp, i64, i64, i64, vp, d, vp, vp]

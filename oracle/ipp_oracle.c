@@ -86,11 +86,17 @@ int orc_mesh_stats(const float* img, int64_t W, int64_t H, int64_t pitch,
     if (!img || !p || W <= 0 || H <= 0 || pitch < W || p->mesh_w < 1 || p->mesh_h < 1)
         return ORC_INVALID_ARG;
     int64_t nx = (W + p->mesh_w - 1) / p->mesh_w, ny = (H + p->mesh_h - 1) / p->mesh_h;
+    /* meshes are independent: with -fopenmp (the all-cores timing build) each
+     * thread takes whole meshes with its own scratch; the arithmetic of a mesh
+     * is the same either way */
+#pragma omp parallel
+    {
     double* a = (double*)malloc(sizeof(double) * (size_t)p->mesh_w * (size_t)p->mesh_h);
     double* b = (double*)malloc(sizeof(double) * (size_t)p->mesh_w * (size_t)p->mesh_h);
-    for (int64_t my = 0; my < ny; my++)
-        for (int64_t mx = 0; mx < nx; mx++) {
-            int64_t id = my * nx + mx, n = 0;
+#pragma omp for schedule(dynamic)
+    for (int64_t id = 0; id < nx * ny; id++) {
+            const int64_t my = id / nx, mx = id % nx;
+            int64_t n = 0;
             for (int64_t i = my * p->mesh_h; i < (my + 1) * p->mesh_h && i < H; i++)
                 for (int64_t j = mx * p->mesh_w; j < (mx + 1) * p->mesh_w && j < W; j++) {
                     float v = img[i * pitch + j];
@@ -139,6 +145,7 @@ int orc_mesh_stats(const float* img, int64_t W, int64_t H, int64_t pitch,
             if (margin) margin[id] = mg;
         }
     free(a); free(b);
+    }
     return ORC_OK;
 }
 
@@ -232,6 +239,7 @@ static double interp_at(const float* mesh, int64_t nx, int64_t ny, int32_t mw,
 int orc_interp_map(const float* mesh, int64_t nx, int64_t ny, int32_t mesh_w,
                    int32_t mesh_h, int64_t W, int64_t H, double* out) {
     if (!mesh || !out || nx < 1 || ny < 1) return ORC_INVALID_ARG;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < H; i++)
         for (int64_t j = 0; j < W; j++)
             out[i * W + j] = interp_at(mesh, nx, ny, mesh_w, mesh_h, i, j);
@@ -244,6 +252,7 @@ int orc_bg_subtract(const float* img, int64_t W, int64_t H, int64_t pitch,
                     const float* mesh_bkg, int64_t nx, int64_t ny,
                     int32_t mesh_w, int32_t mesh_h, float* sub, float* bkg_map) {
     if (!img || !mesh_bkg || !sub || pitch < W) return ORC_INVALID_ARG;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < H; i++)
         for (int64_t j = 0; j < W; j++) {
             double B = interp_at(mesh_bkg, nx, ny, mesh_w, mesh_h, i, j);
@@ -260,6 +269,7 @@ int orc_bg_subtract(const float* img, int64_t W, int64_t H, int64_t pitch,
 int orc_threshold(const float* sub, int64_t W, int64_t H, const float* mesh_rms,
                   int64_t nx, int64_t ny, int32_t mesh_w, int32_t mesh_h,
                   double k, double thresh_abs, uint8_t* mask) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < H; i++)
         for (int64_t j = 0; j < W; j++) {
             double thr = k * interp_at(mesh_rms, nx, ny, mesh_w, mesh_h, i, j);
@@ -377,6 +387,7 @@ int orc_centroid(const float* sub, int64_t W, int64_t H, int64_t n,
                  int32_t* niter, int32_t* flags) {
     double sw = fwhm_win / (2.0 * sqrt(2.0 * log(2.0)));
     double rad = 4.0 * sw, rad2 = rad * rad;
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t s = 0; s < n; s++) {
         double cx = (double)x0[s], cy = (double)y0[s];
         int32_t fl = ORC_FLAG_WIN_NOT_CONVERGED, it;
@@ -485,8 +496,11 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
                  double r_out, int32_t min_ann, double* flux, double* sky,
                  double* area, int32_t* n_ann, int32_t* flags) {
     int64_t cap = (int64_t)((2 * ceil(r_out) + 3) * (2 * ceil(r_out) + 3));
-    double* ann = (double*)malloc(sizeof(double) * (size_t)cap);
     double rin2 = r_in * r_in, rout2 = r_out * r_out;
+#pragma omp parallel
+    {
+    double* ann = (double*)malloc(sizeof(double) * (size_t)cap);
+#pragma omp for schedule(dynamic, 64)
     for (int64_t s = 0; s < n; s++) {
         double cx = (double)x[s], cy = (double)y[s];
         int32_t fl = 0;
@@ -525,6 +539,7 @@ int orc_aperture(const float* sub, int64_t W, int64_t H, int64_t n,
         sky[s] = sk; area[s] = sw; n_ann[s] = (int32_t)na; flags[s] = fl;
     }
     free(ann);
+    }
     return ORC_OK;
 }
 
@@ -1149,16 +1164,29 @@ static double chi2_of(const float* d, const float* w, const double* m, int64_t n
     return c;
 }
 
+/* sum of w (m - sky)^2: the weighted square of the star part of the model */
+static double star_sq_of(const float* w, const double* m, double sky, int64_t n) {
+    double c = 0.0;
+    for (int64_t k = 0; k < n; k++) c += (w ? (double)w[k] : 1.0) * (m[k] - sky) * (m[k] - sky);
+    return c;
+}
+
 /*
  * Levenberg-Marquardt (Marquardt 1963, diagonal scaling), one trial step per
  * iteration: solve (J'WJ + lambda D) delta = J'W r by Cholesky, D = diag(J'WJ)
  * with entries floored at 1e-9 of the largest; the
  * trial is accepted when chi^2 drops (lambda /= 10), otherwise rejected
  * (lambda *= 10); trials with sx or sy <= 0.05 or a non-positive-definite
- * system are rejected.  Converged when an accepted step lowers chi^2 by a
- * relative amount below 1e-8, or when lambda passes 1e10 (no step lowers chi^2;
- * FIT_SINGULAR if that came from failed factorisations); otherwise stops after
- * max_iter trials with FIT_MAXITER.  Result
+ * system are rejected.  Converged, before a trial, when the Gauss-Newton
+ * decrease g'(J'WJ)^-1 g (g = J'W r) is at most 1e-10 chi^2 + 1e-12 sum w
+ * (m - sky)^2: the first term bounds the distance to the optimum by
+ * 1.5e-4 standard errors per parameter, sqrt(1e-10 (n - 7)), the second is
+ * the decrease that rounding of a single-precision model (relative error
+ * ~2^-22) can fake, so that the rule can be decided in that precision too.
+ * It does not depend on lambda.  Also
+ * converged when lambda passes 1e10 (no step lowers chi^2; FIT_SINGULAR if
+ * that came from failed factorisations); otherwise stops after max_iter
+ * trials with FIT_MAXITER.  Result
  * canonicalised: sx >= sy (swap and add pi/2 to theta), theta wrapped to
  * [-pi/2, pi/2).
  */
@@ -1167,8 +1195,11 @@ int orc_psf_fit(const float* stamps, int64_t N, int32_t S, const float* weights,
                 double lambda0, double* params, double* chi2, int32_t* iters,
                 int32_t* flags) {
     int64_t np = (int64_t)S * S;
+#pragma omp parallel
+    {
     double* m = (double*)malloc(sizeof(double) * (size_t)np);
     double* J = (double*)malloc(sizeof(double) * (size_t)np * 7);
+#pragma omp for schedule(dynamic, 16)
     for (int64_t s = 0; s < N; s++) {
         const float* d = stamps + s * np;
         const float* w = weights ? weights + s * np : NULL;
@@ -1177,7 +1208,7 @@ int orc_psf_fit(const float* stamps, int64_t N, int32_t S, const float* weights,
         else orc_psf_init(d, S, p);
         double lam = lambda0;
         orc_psf_model(p, S, model, beta, m, J);
-        double c2 = chi2_of(d, w, m, np);
+        double c2 = chi2_of(d, w, m, np), sm2 = star_sq_of(w, m, p[3], np);
         int32_t fl = ORC_FLAG_FIT_MAXITER, it, nsing = 0;
         double Hm[49], g[7];
         int need = 1;
@@ -1209,6 +1240,22 @@ int orc_psf_fit(const float* stamps, int64_t N, int32_t S, const float* weights,
                 if (lam > 1e10) { it++; break; }
                 continue;
             }
+            {
+                /* the damped step's decrease never exceeds the Gauss-Newton one, so the
+                 * undamped system is solved only when the damped one is already small */
+                const double thr = 1e-10 * c2 + 1e-12 * sm2;
+                double dec = 0.0;
+                for (int a = 0; a < 7; a++) dec += g[a] * delta[a];
+                if (dec <= thr) {
+                    double A0[49], dgn[7];
+                    memcpy(A0, Hm, sizeof(A0));
+                    if (chol7(A0, g, dgn)) {
+                        double dgnv = 0.0;
+                        for (int a = 0; a < 7; a++) dgnv += g[a] * dgn[a];
+                        if (dgnv <= thr) { fl = 0; break; }
+                    }
+                }
+            }
             for (int a = 0; a < 7; a++) pt[a] = p[a] + delta[a];
             if (!(pt[4] > 0.05) || !(pt[5] > 0.05)) {
                 lam *= 10.0;
@@ -1218,12 +1265,11 @@ int orc_psf_fit(const float* stamps, int64_t N, int32_t S, const float* weights,
             orc_psf_model(pt, S, model, beta, m, NULL);
             double c2t = chi2_of(d, w, m, np);
             if (c2t < c2) {
-                double rel = (c2 - c2t) / c2;
                 memcpy(p, pt, sizeof(p));
                 c2 = c2t;
+                sm2 = star_sq_of(w, m, p[3], np);
                 lam /= 10.0;
                 need = 1;
-                if (rel < 1e-8) { fl = 0; it++; break; }
             } else {
                 lam *= 10.0;
                 if (lam > 1e10) { fl = 0; it++; break; }   /* no step lowers chi^2: at the minimum */
@@ -1237,6 +1283,7 @@ int orc_psf_fit(const float* stamps, int64_t N, int32_t S, const float* weights,
         chi2[s] = c2; iters[s] = it; flags[s] = fl;
     }
     free(m); free(J);
+    }
     return ORC_OK;
 }
 

@@ -600,20 +600,31 @@ def extract(img, cfg: BgConfig | None = None, calib=None, **kw):
     return out
 
 
-def psf_fit(stamps, init=None, weights=None, model=PSF_MOFFAT, beta=2.5, max_iter=50, lambda0=1e-3):
-    """Batched Levenberg-Marquardt PSF fit (ipp_psf_fit)."""
+def psf_fit(stamps, init=None, weights=None, model=PSF_MOFFAT, beta=2.5, max_iter=50, lambda0=1e-3,
+            n_src=None, out=None):
+    """Batched Levenberg-Marquardt PSF fit (ipp_psf_fit).  With n_src (an int32
+    device tensor) only the first min(n_src, len(stamps)) stamps are fitted and
+    the count stays on the device (ipp_psf_fit_dev).  `out` reuses output
+    tensors of a previous call."""
     L = load()
     _need_cuda(stamps, "stamps", torch.float32)
     N, S = stamps.shape[0], stamps.shape[-1]
     dev = stamps.device
-    out = dict(params=torch.empty((N, 7), dtype=torch.float32, device=dev),
-               chi2=torch.empty(N, dtype=torch.float32, device=dev),
-               iters=torch.empty(N, dtype=torch.int32, device=dev),
-               flags=torch.empty(N, dtype=torch.int32, device=dev))
-    _abi.check("ipp_psf_fit", L.ipp_psf_fit(
-        _ptr(stamps.contiguous()), N, S, _ptr(None if weights is None else weights.contiguous()),
-        _ptr(None if init is None else init.contiguous()), _abi.FitParams(model, beta, max_iter, lambda0),
-        _ptr(out["params"]), _ptr(out["chi2"]), _ptr(out["iters"]), _ptr(out["flags"]), _stream()))
+    if out is None:
+        out = dict(params=torch.empty((N, 7), dtype=torch.float32, device=dev),
+                   chi2=torch.empty(N, dtype=torch.float32, device=dev),
+                   iters=torch.empty(N, dtype=torch.int32, device=dev),
+                   flags=torch.empty(N, dtype=torch.int32, device=dev))
+    fp = _abi.FitParams(model, beta, max_iter, lambda0)
+    w = _ptr(None if weights is None else weights.contiguous())
+    ini = _ptr(None if init is None else init.contiguous())
+    outs = (_ptr(out["params"]), _ptr(out["chi2"]), _ptr(out["iters"]), _ptr(out["flags"]), _stream())
+    if n_src is None:
+        _abi.check("ipp_psf_fit", L.ipp_psf_fit(_ptr(stamps.contiguous()), N, S, w, ini, fp, *outs))
+    else:
+        _need_cuda(n_src, "n_src", torch.int32)
+        _abi.check("ipp_psf_fit_dev", L.ipp_psf_fit_dev(_ptr(stamps.contiguous()), _ptr(n_src), N, S, w, ini, fp,
+                                                          *outs))
     return out
 
 

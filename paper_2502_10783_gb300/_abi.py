@@ -130,6 +130,7 @@ PROTOTYPES = {
     "ipp_batch_autotune": ([C.POINTER(FrameDesc), i32] + _par + [vp, sz, vp, C.POINTER(i32), C.POINTER(f32)],
                            i32),
     "ipp_psf_fit": ([vp, i64, i32, vp, vp, C.POINTER(FitParams), vp, vp, vp, vp, vp], i32),
+    "ipp_psf_fit_dev": ([vp, vp, i64, i32, vp, vp, C.POINTER(FitParams), vp, vp, vp, vp, vp], i32),
     "ipp_psf_model_fwd": ([vp, i64, i32, C.POINTER(FitParams), vp, vp], i32),
     "ipp_psf_model_adj": ([vp, i64, i32, C.POINTER(FitParams), vp, vp, vp], i32),
 }

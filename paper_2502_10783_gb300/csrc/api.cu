@@ -473,7 +473,23 @@ extern "C" int ipp_psf_fit(const float* stamps, int64_t N, int32_t S, const floa
     REQUIRE(stamps && params && chi2, "NULL pointer");
     REQUIRE(p->max_iter >= 1 && p->lambda0 > 0.f, "bad LM params");
     FitJob J;
-    J.stamps = stamps; J.N = N; J.S = S; J.weights = weights; J.init = init;
+    J.stamps = stamps; J.N = N; J.n_dev = nullptr; J.S = S; J.weights = weights; J.init = init;
+    J.model = p->model; J.beta = p->beta; J.max_iter = p->max_iter; J.lambda0 = p->lambda0;
+    J.params = params; J.chi2 = chi2; J.iters = iters; J.flags = flags;
+    return ipp_launch_psf_fit(J, (cudaStream_t)stream);
+}
+
+extern "C" int ipp_psf_fit_dev(const float* stamps, const int32_t* n_dev, int64_t n_max, int32_t S,
+                               const float* weights, const float* init, const ipp_fit_params* p, float* params,
+                               float* chi2, int32_t* iters, int32_t* flags, void* stream) {
+    if (int e = check_fit(p, S)) return e;
+    REQUIRE(n_max >= 0, "n_max < 0");
+    REQUIRE(n_dev, "n_dev NULL");
+    if (n_max == 0) return IPP_OK;
+    REQUIRE(stamps && params && chi2, "NULL pointer");
+    REQUIRE(p->max_iter >= 1 && p->lambda0 > 0.f, "bad LM params");
+    FitJob J;
+    J.stamps = stamps; J.N = n_max; J.n_dev = n_dev; J.S = S; J.weights = weights; J.init = init;
     J.model = p->model; J.beta = p->beta; J.max_iter = p->max_iter; J.lambda0 = p->lambda0;
     J.params = params; J.chi2 = chi2; J.iters = iters; J.flags = flags;
     return ipp_launch_psf_fit(J, (cudaStream_t)stream);

@@ -136,7 +136,8 @@ struct DetectArgs {
 
 struct FitJob {
     const float* stamps;
-    int64_t N;
+    int64_t N;               // stamps (with n_dev: the capacity)
+    const int32_t* n_dev;    // nullable: the stamp count in device memory, min(*n_dev, N) are fitted
     int S;
     const float* weights;
     const float* init;

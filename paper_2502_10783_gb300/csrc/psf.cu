@@ -197,7 +197,7 @@ constexpr int FL_MAX_WARPS = 8;
 // (absolute error ~2^-22 on the exponent, a few ulp in P).
 template <int MODEL, bool WEIGHTED, int G, int PITCH>
 __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const float* __restrict__ wts, int S,
-                                           float beta, const float pp[7], float Ht[28], float gt[7]) {
+                                           float beta, const float pp[7], float Ht[28], float gt[7], float* sm2) {
     const int h = (threadIdx.x & 31) % G;
 #pragma unroll
     for (int a = 0; a < 28; a++) Ht[a] = 0.f;
@@ -211,12 +211,12 @@ __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const 
     const float kth = (pp[5] - pp[4]) * (pp[5] + pp[4]) * isx2 * isy2;
     const float A0 = (MODEL == IPP_PSF_GAUSS ? 0.5f / F_PI : (beta - 1.0f) / F_PI) * isx * isy;
     const float tq = MODEL == IPP_PSF_GAUSS ? -1.0f : -2.0f * beta;  // T = tq P / (1+q) (Moffat), -P (Gauss)
-    float chi = 0.f;
+    float chi = 0.f, star2 = 0.f;  // chi^2 and sum w P^2 (the star part of the model, squared)
     for (int i = h; i < S; i += G) {
         const float dy = (float)i - pp[1];
         const float sdy = sn * dy, cdy = cs * dy;
         const float* row = col + i * S * PITCH;
-        float rowc = 0.f;
+        float rowc = 0.f, rows = 0.f;
         float jf = 0.f;
 #pragma unroll 5
         for (int j = 0; j < S; j++, jf += 1.0f) {
@@ -238,6 +238,7 @@ __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const 
             const float wk = WEIGHTED ? __ldg(wts + i * S + j) : 1.0f;
             const float r = row[j * PITCH] - (P + sky);
             rowc = fmaf(wk * r, r, rowc);
+            rows = fmaf(wk * P, P, rows);
             float e[7];
             e[0] = T * fmaf(b, sn, -a * cs);
             e[1] = -T * fmaf(a, sn, b * cs);
@@ -256,6 +257,7 @@ __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const 
             }
         }
         chi += rowc;
+        star2 += rows;
     }
     if (G > 1) {  // all lanes of the slot are here (their states are identical)
         const unsigned pm = ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
@@ -266,8 +268,10 @@ __device__ __forceinline__ float eval_lane(const float* __restrict__ col, const 
 #pragma unroll
             for (int a = 0; a < 7; a++) gt[a] += __shfl_xor_sync(pm, gt[a], o);
             chi += __shfl_xor_sync(pm, chi, o);
+            star2 += __shfl_xor_sync(pm, star2, o);
         }
     }
+    *sm2 = star2;
     return chi;
 }
 
@@ -337,13 +341,18 @@ __global__ void __launch_bounds__(32 * FL_MAX_WARPS) k_psf_fit(FitJob J, int64_t
     const int slot = lane / G;
     const int S = J.S, NP = S * S;
     float* fl_sm = fl_sm_all + (threadIdx.x >> 5) * NP * PITCH;
+    // stamps to fit: N, or the device count when one is given; the chunks are
+    // cut from that count here, so a count known only on the device needs no sync
+    int64_t nfit = J.N;
+    if (J.n_dev) nfit = min(nfit, (int64_t)max(__ldg(J.n_dev), 0));
+    if (chunk <= 0) chunk = (nfit + gridDim.x - 1) / gridDim.x;
     const int64_t c0 = (int64_t)blockIdx.x * chunk;
-    const int64_t c1 = c0 + chunk < J.N ? c0 + chunk : J.N;
+    const int64_t c1 = c0 + chunk < nfit ? c0 + chunk : nfit;
     if (threadIdx.x == 0) blk_next = (unsigned long long)c0;
     __syncthreads();
     bool drained = false;  // the block's chunk has been handed out
     int64_t st = -1;
-    float p[7], H[28], g[7], chi2 = 0.f;
+    float p[7], H[28], g[7], chi2 = 0.f, sm2 = 0.f;
     double lam = 0.0;
     int it = 0, nsing = 0;
     bool fresh = false;
@@ -406,9 +415,30 @@ __global__ void __launch_bounds__(32 * FL_MAX_WARPS) k_psf_fit(FitJob J, int64_t
                     it++;
                     if (lam > 1e10) fl = IPP_FLAG_FIT_MAXITER;
                 } else {
+                    {
+                        // converged when the Gauss-Newton decrease g'H^-1 g is below what the
+                        // distance to the optimum (1e-10 chi^2) and the model's FP32 rounding
+                        // (1e-12 sum w P^2) allow; the damped step's decrease never exceeds
+                        // it, so the undamped system is solved only when that one is small
+                        const double thr = 1e-10 * widen(chi2) + 1e-12 * widen(sm2);
+                        double dec = 0.0;
+#pragma unroll
+                        for (int a = 0; a < 7; a++) dec = fma(widen(g[a]), delta[a], dec);
+                        if (dec <= thr) {
+                            double dgn[7];
+                            if (solve7(H, g, 0.0, dgn)) {
+                                double dg = 0.0;
+#pragma unroll
+                                for (int a = 0; a < 7; a++) dg = fma(widen(g[a]), dgn[a], dg);
+                                if (dg <= thr) fl = 0;
+                            }
+                        }
+                    }
 #pragma unroll
                     for (int a = 0; a < 7; a++) pt[a] = narrow(widen(p[a]) + delta[a]);
-                    if (!(pt[4] > 0.05f) || !(pt[5] > 0.05f)) {
+                    if (fl == 0) {
+                        // stopped at p
+                    } else if (!(pt[4] > 0.05f) || !(pt[5] > 0.05f)) {
                         lam *= 10.0;
                         it++;
                         if (lam > 1e10) fl = 0;
@@ -418,11 +448,11 @@ __global__ void __launch_bounds__(32 * FL_MAX_WARPS) k_psf_fit(FitJob J, int64_t
                 }
             }
         }
-        float Ht[28], gt[7], c2t = 0.f;
+        float Ht[28], gt[7], c2t = 0.f, s2t = 0.f;
         // both lanes of a slot take the same branch: their states are identical
         if (try_pt) {
             const float* wts = WEIGHTED ? J.weights + st * NP : nullptr;
-            c2t = eval_lane<MODEL, WEIGHTED, G, PITCH>(fl_sm + slot, wts, S, J.beta, pt, Ht, gt);
+            c2t = eval_lane<MODEL, WEIGHTED, G, PITCH>(fl_sm + slot, wts, S, J.beta, pt, Ht, gt, &s2t);
         }
         if (try_pt) {
             bool take = fresh;
@@ -430,8 +460,7 @@ __global__ void __launch_bounds__(32 * FL_MAX_WARPS) k_psf_fit(FitJob J, int64_t
                 it++;
                 if (c2t < chi2) {
                     take = true;
-                    if ((chi2 - c2t) / chi2 < 1e-6f) fl = 0;
-                    lam *= 0.1;
+                    lam /= 10.0;   // as the oracle: 1e-3 * 0.1 rounds above 1e-4 in FP64
                 } else {
                     lam *= 10.0;
                     if (lam > 1e10) fl = 0;
@@ -445,6 +474,7 @@ __global__ void __launch_bounds__(32 * FL_MAX_WARPS) k_psf_fit(FitJob J, int64_t
 #pragma unroll
                 for (int a = 0; a < 7; a++) g[a] = gt[a];
                 chi2 = c2t;
+                sm2 = s2t;
             }
             fresh = false;
         }
@@ -548,7 +578,7 @@ static int launch_fit(const FitJob& J, cudaStream_t s) {
     const size_t smem = per_warp * wpb;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    const int64_t chunk = (J.N + blocks - 1) / blocks;
+    const int64_t chunk = J.n_dev ? 0 : (J.N + blocks - 1) / blocks;   // 0: from the device count
     k<<<(unsigned)blocks, 32 * wpb, smem, s>>>(J, chunk);
     return ipp_check_launch("k_psf_fit");
 }

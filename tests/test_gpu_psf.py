@@ -3,13 +3,17 @@
   * forward model vs the oracle's FP64 model: 2e-5 relative to the peak;
   * adjoint (hand-written Jacobian-transpose kernel) vs the oracle's analytic
     Jacobian and vs central finite differences (h = 1e-3) of the GPU forward;
-  * fit: chi^2 within 1e-4 relative and positions within 1e-4 px on
-    well-measured stamps.  The FP32 fit stops once an accepted step lowers chi^2
-    by less than 1e-6 relative (the FP64 oracle at 1e-8); along the shallow
-    flux-width direction of the Moffat that leaves offsets up to ~1e-3 relative
-    in (F, sky, sx, sy), so those are gated at 1e-3 with a median below 1e-5,
-    and theta at 0.05 of its standard error.
-    Faint stamps can take other accept/reject paths and are compared by chi^2."""
+  * fit: both sides run the same Marquardt iteration and the same stop rule
+    (converged when the Gauss-Newton decrease g'(J'WJ)^-1 g falls below
+    1e-10 chi^2 + 1e-12 sum w (m - sky)^2).  Every fit converged on both
+    sides reaches the same chi^2 (1e-5 relative); on well-measured stamps the
+    optimum is the same point to 1e-4 (px, relative, rad), or to the distance
+    the stop rule allows where that is larger.  On faint stamps
+    (a few hundred ADU on a 1000 ADU sky) the chi^2 surface is flat or has
+    several minima, and accept/reject decisions at the FP32 resolution of
+    chi^2 (~1e-7 relative) can send the two sides along different paths to
+    minima of equal chi^2; many such fits also reach max_iter, on one side or
+    both."""
 import math
 
 import numpy as np
@@ -69,14 +73,61 @@ def test_adjoint_vs_finite_differences(gpu):
         assert np.all(np.abs(fd - ga[:, k]) <= 2e-2 * sc), k
 
 
+def _std_errors(orc, params, chi2, S=15, model=0, beta=2.5):
+    """standard errors of the 7 parameters from the oracle's covariance
+    chi^2 / (n - 7) (J'J)^-1 at its optimum, and the stop rule's bound rho on
+    the distance of a converged fit from the optimum in those units: the
+    Gauss-Newton decrease there is (p - p*)' J'J (p - p*), so stopping below
+    thr = 1e-10 chi^2 + 1e-12 sum (m - sky)^2 puts every parameter within
+    sqrt(thr (n - 7) / chi^2) standard errors"""
+    out = np.empty((len(params), 7))
+    rho = np.empty(len(params))
+    for n, (p, c2) in enumerate(zip(params, chi2)):
+        m, Jm = orc.psf_model(p, S, model, beta)
+        out[n] = np.sqrt(np.maximum(np.diag(np.linalg.pinv(Jm.T @ Jm)), 0.0) * c2 / (S * S - 7))
+        thr = 1e-10 * c2 + 1e-12 * np.sum((m - p[3]) ** 2)
+        rho[n] = np.sqrt(thr * (S * S - 7) / c2)
+    return out, rho
+
+
+def _assert_same_optimum(orc, g, o, sel, strong, chi2_all=True):
+    """Every stamp converged on both sides reaches the same chi^2 (1e-5
+    relative).  On the well-measured ones (`strong`: every parameter but theta
+    determined to better than 2% by the oracle's covariance) the optimum is
+    the same point: within 1e-4 px (x, y), 1e-4 relative (F, sky, sx, sy) and
+    1e-3 rad (theta, elliptical stamps), or, where that is larger, 3 rho
+    standard errors -- rho the stop rule's bound on each side's distance from
+    the optimum (1.5e-4 for faint stamps; the FP32-rounding term of the rule
+    makes it larger for bright ones)."""
+    csel = sel if chi2_all else sel & strong
+    rc = np.abs(g["chi2"][csel] - o["chi2"][csel]) / o["chi2"][csel]
+    assert np.all(rc <= 1e-5), rc.max()
+    se, rho = _std_errors(orc, o["params"], o["chi2"])
+    well = sel & strong & np.all(se[:, 2:6] <= 0.02 * np.abs(o["params"][:, 2:6]), axis=1)
+    gp, op, se, rho = g["params"][well], o["params"][well], se[well], rho[well]
+    d = np.abs(gp - op)
+    d[:, 6] = np.abs((gp[:, 6] - op[:, 6] + math.pi / 2) % math.pi - math.pi / 2)
+    tol = np.empty_like(d)
+    tol[:, :2] = 1e-4
+    tol[:, 2:6] = 1e-4 * np.abs(op[:, 2:6])
+    tol[:, 6] = 1e-3   # theta is outside the 1e-4 set: compared on elliptical stamps, with the model images
+    tol = np.maximum(tol, 3 * rho[:, None] * se)
+    ell = np.abs(op[:, 4] - op[:, 5]) / op[:, 4] > 0.05
+    d[~ell, 6] = 0.0   # theta is not identifiable on round stamps
+    bad = d > tol
+    assert not bad.any(), (np.flatnonzero(well)[bad.any(1)][:5], (d / tol).max(axis=0))
+    # the model images of the two fits (FP64, from each side's parameters): the
+    # same star to 1e-4 of its peak, whatever theta does on round stamps
+    for a, b in zip(gp.astype(np.float64), op):
+        ma, mb = orc.psf_model(a, 15, 0, 2.5, jac=False), orc.psf_model(b, 15, 0, 2.5, jac=False)
+        assert np.max(np.abs(ma - mb)) <= 1e-4 * np.max(mb - b[3]), np.max(np.abs(ma - mb)) / np.max(mb - b[3])
+    return int(well.sum())
+
+
 @pytest.mark.parametrize("n_batch", [400, 18000, 40000])
 def test_fit_parity(gpu, orc, n_batch):
-    """Faint stamps (F of a few hundred ADU on a 1000 ADU sky) crawl for hundreds
-    of LM trials on both sides, so at max_iter = 50 about half stop with
-    FIT_MAXITER; the parity gate is on stamps that both sides converge, and
-    well-measured stars must converge.  The 400 compared stamps lead batches of
-    400, 18,000 and 40,000 stamps, which the fit runs with 4, 2 and 1 lanes per
-    stamp on a 152-SM GPU."""
+    """The 400 compared stamps lead batches of 400, 18,000 and 40,000 stamps,
+    which the fit runs with 4, 2 and 1 lanes per stamp on a 152-SM GPU."""
     stamps, truth = synth.moffat_stamps(400, seed=4000)
     o = orc.psf_fit(stamps)
     batch = stamps
@@ -84,34 +135,25 @@ def test_fit_parity(gpu, orc, n_batch):
         pad, _ = synth.moffat_stamps(n_batch - 400, seed=4001, oversample=2)
         batch = np.concatenate([stamps, pad])
     g = {k: host(v)[:400] for k, v in gpu.psf_fit(dev(batch)).items()}
-    conv = (o["flags"] == 0) & (g["flags"] == 0)
-    assert conv.mean() > 0.3
+    oc, gc = o["flags"] == 0, g["flags"] == 0
+    # the decisions differ only on faint stamps that reach max_iter on one side
+    # (measured: 93% agreement on these 400, 89% on the 200,000-stamp sample)
+    assert np.mean(oc == gc) > 0.85, np.mean(oc == gc)
     strong = truth[:, 2] > 5e3
-    assert np.mean(g["flags"][strong] == 0) > 0.95 and np.mean(o["flags"][strong] == 0) > 0.95
-    # chi^2 of converged fits: the same optimum
-    rel = np.abs(g["chi2"] - o["chi2"]) / o["chi2"]
-    assert np.median(rel[conv]) < 1e-5
-    bright = conv & (truth[:, 2] > 5e3) & (o["params"][:, 4] > 0.3) & (o["params"][:, 5] > 0.3)
-    assert bright.sum() > 20
-    assert np.all(rel[bright] < 1e-4)
-    gp, op = g["params"][bright], o["params"][bright]
-    assert np.all(np.abs(gp[:, :2] - op[:, :2]) <= 1e-4 + 4e-6 * np.abs(op[:, :2]))
-    relp = np.abs(gp[:, 2:6] - op[:, 2:6]) / (np.abs(op[:, 2:6]) + 1e-3)
-    assert np.all(relp <= 1e-3), relp.max(axis=0)
-    assert np.all(np.median(relp, axis=0) < 1e-5), np.median(relp, axis=0)
-    # theta: stopping at a relative chi^2 decrease of 1e-6 leaves the fit within
-    # Delta chi^2 ~ 1e-6 chi^2 of the optimum, about 0.015 standard errors of any
-    # parameter.  Theta of a mildly elliptical star has a standard error of a few
-    # 1e-2 rad, so it is gated at 0.05 of its standard error (1e-3 rad at least),
-    # the error taken from the oracle's covariance chi^2/(n-7) (J'J)^-1.
-    ell = np.abs(op[:, 4] - op[:, 5]) / op[:, 4] > 0.05
-    dth = (gp[:, 6] - op[:, 6] + math.pi / 2) % math.pi - math.pi / 2
-    sig_t = np.empty(len(op))
-    for n, k in enumerate(np.flatnonzero(bright)):
-        _, Jm = orc.psf_model(o["params"][k], 15, 0, 2.5)
-        cov = np.linalg.inv(Jm.T @ Jm) * o["chi2"][k] / (15 * 15 - 7)
-        sig_t[n] = math.sqrt(cov[6, 6])
-    assert np.all(np.abs(dth[ell]) <= np.maximum(1e-3, 0.05 * sig_t[ell])), (dth[ell], sig_t[ell])
+    assert np.all(gc[strong]) and np.all(oc[strong])
+    assert _assert_same_optimum(orc, g, o, oc & gc, strong) >= 20
+
+
+def test_fit_parity_high_max_iter(gpu, orc):
+    """max_iter = 400: most faint stamps converge too (on both sides), and every
+    stamp converged on both sides is at the same optimum."""
+    stamps, truth = synth.moffat_stamps(200, seed=4010)
+    o = orc.psf_fit(stamps, max_iter=400)
+    g = {k: host(v) for k, v in gpu.psf_fit(dev(stamps), max_iter=400).items()}
+    oc, gc = o["flags"] == 0, g["flags"] == 0
+    assert np.mean(oc & gc) > 0.6, np.mean(oc & gc)
+    # after hundreds of trials faint stamps may settle in different minima
+    _assert_same_optimum(orc, g, o, oc & gc, truth[:, 2] > 5e3, chi2_all=False)
 
 
 def test_fit_noise_free_recovery_and_init(gpu, orc):
@@ -144,17 +186,34 @@ def test_fit_gaussian_and_weights(gpu, orc):
 
 def test_fit_full_size_sampled(gpu, orc):
     """the benchmark's 200,000 stamps in one call (one lane per stamp); a seeded
-    sample of 300 refitted by the oracle.  Converged-on-both fits reach the same
-    chi^2 optimum."""
+    sample of 300 refitted by the oracle: every stamp converged on both sides
+    at the same optimum."""
     stamps, truth = synth.moffat_stamps(200000, seed=4000, oversample=3)
     g = {k: host(v) for k, v in gpu.psf_fit(dev(stamps)).items()}
     pick = np.sort(np.random.default_rng(9).choice(len(stamps), 300, replace=False))
     o = orc.psf_fit(stamps[pick])
-    conv = (o["flags"] == 0) & (g["flags"][pick] == 0)
-    assert conv.mean() > 0.3
-    rel = np.abs(g["chi2"][pick] - o["chi2"]) / o["chi2"]
-    assert np.median(rel[conv]) < 1e-5
-    bright = conv & (truth[pick, 2] > 5e3)
-    assert bright.sum() > 10 and np.all(rel[bright] < 1e-4)
-    gp, op = g["params"][pick][bright], o["params"][bright]
-    assert np.all(np.abs(gp[:, :2] - op[:, :2]) <= 1e-4 + 4e-6 * np.abs(op[:, :2]))
+    gs = {k: v[pick] for k, v in g.items()}
+    oc, gc = o["flags"] == 0, gs["flags"] == 0
+    assert np.mean(oc == gc) > 0.85, np.mean(oc == gc)
+    strong = truth[pick, 2] > 5e3
+    assert np.all(gc[strong]) and np.all(oc[strong])
+    assert _assert_same_optimum(orc, gs, o, oc & gc, strong) >= 10
+
+
+def test_fit_device_count(gpu):
+    """ipp_psf_fit_dev: a device count of 200 out of 300 stamps fits exactly the
+    first 200 (each stamp's fit is independent of the others) and leaves the
+    remaining outputs untouched."""
+    stamps, _ = synth.moffat_stamps(300, seed=4020)
+    t = dev(stamps)
+    ref = {k: host(v) for k, v in gpu.psf_fit(t[:200]).items()}
+    out = dict(params=torch.full((300, 7), float("nan"), device="cuda"),
+               chi2=torch.full((300,), float("nan"), device="cuda"),
+               iters=torch.full((300,), -7, dtype=torch.int32, device="cuda"),
+               flags=torch.full((300,), -7, dtype=torch.int32, device="cuda"))
+    n = torch.tensor([200], dtype=torch.int32, device="cuda")
+    g = {k: host(v) for k, v in gpu.psf_fit(t, n_src=n, out=out).items()}
+    # same lanes per stamp is not guaranteed (sized for 300), the arithmetic per stamp is
+    assert np.array_equal(g["flags"][:200], ref["flags"])
+    assert np.array_equal(g["params"][:200], ref["params"]) and np.array_equal(g["chi2"][:200], ref["chi2"])
+    assert np.all(np.isnan(g["params"][200:])) and np.all(g["flags"][200:] == -7)
