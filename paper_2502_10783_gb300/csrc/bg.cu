@@ -463,40 +463,6 @@ struct Stored {
 // error ~1e-14): the FP64 pipe of this GPU is narrow and its latency sits on
 // the serial path of every clip pass.  Windows so fine or so coarse that the
 // scaled sums would leave the FP32 range (|e| > 40) take the FP64 branch.
-__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
-__device__ __forceinline__ df df_scale(df a, float p2) { return df{a.hi * p2, a.lo * p2}; }  // p2 a power of two
-__device__ __forceinline__ df df_mul_f(df a, float b) {
-    const float p = __fmul_rn(a.hi, b);
-    float e = __fmaf_rn(a.hi, b, -p);
-    e = __fmaf_rn(a.lo, b, e);
-    return two_sum(p, e);
-}
-__device__ __forceinline__ df df_mul(df a, df b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    return two_sum(p, e);
-}
-__device__ __forceinline__ df df_div(df a, df b) {  // one correction step after the FP32 quotient
-    const float q1 = __fdiv_rn(a.hi, b.hi);
-    const df r = df_sub(a, df_mul_f(b, q1));
-    return two_sum(q1, __fdiv_rn(r.hi, b.hi));
-}
-__device__ __forceinline__ df df_sqrt(df a) {  // one Newton step after the FP32 root
-    if (!(a.hi > 0.f)) return df{0.f, 0.f};
-    const float r = __fsqrt_rn(a.hi);
-    const df d = df_sub(a, sq_exact(r));
-    return two_sum(r, __fdiv_rn(d.hi, 2.0f * r));
-}
-// exact split of an int64 into three pieces of at most 21 bits
-__device__ __forceinline__ df df_from_i64(long long i) {
-    const float c2 = (float)(int)(i >> 42);
-    const float c1 = (float)(int)((i >> 21) & 0x1fffff);
-    const float c0 = (float)(int)(i & 0x1fffff);
-    return df_add_f(two_sum(c2 * 4398046511104.0f, c1 * 2097152.0f), c0);
-}
 __device__ __forceinline__ df df_from_d(double d) {
     const float h = __double2float_rn(d);
     return df{h, __double2float_rn(d - (double)h)};
@@ -1103,14 +1069,11 @@ __global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
 // any -- since the smaller neighbourhoods hold none, those are exactly the
 // valid nodes on the ring at Chebyshev distance k -- and each node then
 // becomes the median of the in-bounds filled nodes of its fw x fh window.
-// The fill is computed once per node (pass 1), the window medians read the
-// filled grids (pass 2).  Grids of up to MF_SMALL nodes run both passes in one
-// block with the grids in shared memory; larger ones take two launches through
-// the caller's fill arrays.  A grid without any valid node returns at once
-// with IPP_ERR_NO_VALID_MESH.
-constexpr int MF_THREADS = 256;
-constexpr int MF_SMALL = 3072;       // one-block path: 16 B per node of shared memory (48 KB)
-constexpr int MF_SMALL_THREADS = 1024;
+// The fill is computed once per node into the caller's fill arrays (pass 1),
+// the window medians read the filled grids (pass 2), each pass a thread per
+// node over many blocks.  A grid without any valid node returns at once with
+// IPP_ERR_NO_VALID_MESH.
+constexpr int MF_THREADS = 64;     // small blocks: a 32 x 32 grid still spreads over 16 SMs
 
 // median (Eq. 1) of the valid nodes on the ring at Chebyshev distance k of
 // (p, q) (in-bounds part), by rank counting; cnt = their number (> 0)
@@ -1234,41 +1197,7 @@ __device__ __forceinline__ void window_median_any(const float* fb, const float* 
     *orr = reg_median<N>(wr, n);
 }
 
-// one block: every node's fill into shared memory, then the window medians
-__global__ void __launch_bounds__(MF_SMALL_THREADS) k_mesh_fill_filter_small(const float* raw_bkg,
-                                                                             const float* raw_rms, int nx, int ny,
-                                                                             int fw, int fh, float* out_bkg,
-                                                                             float* out_rms, int32_t* status_dev) {
-    extern __shared__ float mf_sh[];
-    const int nn = nx * ny;
-    float* rb = mf_sh;
-    float* rr = rb + nn;
-    float* fb = rr + nn;
-    float* fr = fb + nn;
-    int any = 0;
-    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-        rb[i] = raw_bkg[i];
-        rr[i] = raw_rms[i];
-        any |= rr[i] >= 0.f;
-    }
-    if (!__syncthreads_or(any)) {
-        for (int i = threadIdx.x; i < nn; i += blockDim.x) { out_bkg[i] = 0.f; out_rms[i] = 0.f; }
-        if (threadIdx.x == 0 && status_dev) *status_dev = IPP_ERR_NO_VALID_MESH;
-        return;
-    }
-    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-        const int p = i / nx, q = i - p * nx;
-        fill_node(rb, rr, nx, ny, p, q, &fb[i], &fr[i]);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-        const int p = i / nx, q = i - p * nx;
-        window_median_any(fb, fr, nx, ny, p, q, fw, fh, &out_bkg[i], &out_rms[i]);
-    }
-    if (threadIdx.x == 0 && status_dev) *status_dev = IPP_OK;
-}
-
-// large grids, pass 1: fills into the caller's arrays.  Each block first checks
+// pass 1: fills into the caller's arrays.  Each block first checks
 // that the grid holds a valid node (a block-wide scan of raw_rms).
 __global__ void __launch_bounds__(MF_THREADS) k_mesh_fill(const float* raw_bkg, const float* raw_rms, int nx, int ny,
                                                           float* fill_bkg, float* fill_rms, int32_t* status_dev) {
@@ -1288,7 +1217,7 @@ __global__ void __launch_bounds__(MF_THREADS) k_mesh_fill(const float* raw_bkg, 
     if (id == 0 && status_dev) *status_dev = IPP_OK;
 }
 
-// large grids, pass 2: window medians of the filled grids
+// pass 2: window medians of the filled grids
 __global__ void __launch_bounds__(MF_THREADS) k_mesh_median(const float* fill_bkg, const float* fill_rms, int nx,
                                                             int ny, int fw, int fh, float* out_bkg, float* out_rms) {
     const int id = blockIdx.x * MF_THREADS + threadIdx.x;
@@ -1425,15 +1354,7 @@ int ipp_launch_mesh_filter(const float* raw_bkg, const float* raw_rms, float* fi
                            int nx, int ny, int fw, int fh, float* out_bkg, float* out_rms,
                            int32_t* status_dev, cudaStream_t s) {
     const int nn = nx * ny;
-    if (nn <= MF_SMALL) {
-        const int threads = nn >= MF_SMALL_THREADS ? MF_SMALL_THREADS : ((nn + 31) / 32) * 32;
-        const size_t sh = (size_t)16 * nn;
-        static_assert(16 * MF_SMALL <= 48 * 1024, "one-block filter within the default shared-memory limit");
-        k_mesh_fill_filter_small<<<1, threads, sh, s>>>(raw_bkg, raw_rms, nx, ny, fw, fh, out_bkg, out_rms,
-                                                        status_dev);
-        return ipp_check_launch("k_mesh_fill_filter_small");
-    }
-    if (!fill_bkg || !fill_rms) return ipp_set_error(IPP_ERR_INVALID_ARG, "fill arrays NULL for a large grid");
+    if (!fill_bkg || !fill_rms) return ipp_set_error(IPP_ERR_INVALID_ARG, "fill arrays NULL");
     const int blocks = (nn + MF_THREADS - 1) / MF_THREADS;
     k_mesh_fill<<<blocks, MF_THREADS, 0, s>>>(raw_bkg, raw_rms, nx, ny, fill_bkg, fill_rms, status_dev);
     if (int e = ipp_check_launch("k_mesh_fill")) return e;

@@ -69,6 +69,42 @@ IPP_D df warp_sum_df(df v) {
     return v;
 }
 
+// double-float arithmetic on the FP32 pipe (~48-bit significands)
+IPP_D df df_neg(df a) { return df{-a.hi, -a.lo}; }
+IPP_D df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+IPP_D df df_scale(df a, float p2) { return df{a.hi * p2, a.lo * p2}; }  // p2 a power of two
+IPP_D df df_mul_f(df a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return two_sum(p, e);
+}
+IPP_D df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return two_sum(p, e);
+}
+IPP_D df df_div(df a, df b) {  // one correction step after the FP32 quotient
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const df r = df_sub(a, df_mul_f(b, q1));
+    return two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+IPP_D df df_sqrt(df a) {  // one Newton step after the FP32 root
+    if (!(a.hi > 0.f)) return df{0.f, 0.f};
+    const float r = __fsqrt_rn(a.hi);
+    const df d = df_sub(a, sq_exact(r));
+    return two_sum(r, __fdiv_rn(d.hi, 2.0f * r));
+}
+// exact split of an int64 into three pieces of at most 21 bits
+IPP_D df df_from_i64(long long i) {
+    const float c2 = (float)(int)(i >> 42);
+    const float c1 = (float)(int)((i >> 21) & 0x1fffff);
+    const float c0 = (float)(int)(i & 0x1fffff);
+    return df_add_f(two_sum(c2 * 4398046511104.0f, c1 * 2097152.0f), c0);
+}
+
 // Keys (1981) cubic-convolution weights, a = -1/2, for fractional offset s in
 // [0, 1): nodes at distances 1 + s, s, 1 - s, 2 - s.
 IPP_D void keys_weights(float s, float w[4]) {

@@ -49,11 +49,14 @@ struct CclWs {
     unsigned long long* first;
     uint32_t* peak;      // order-preserving key
     int32_t* xmin; int32_t* xmax; int32_t* ymin; int32_t* ymax;
-    double* sum; double* sx; double* sy;
+    // component sums sum f, sum f x, sum f y, each as two integers (see FxSum):
+    // integer adds are exact, so the totals do not depend on the order in which
+    // runs, tiles and nodes are merged
+    long long* sum; long long* sx; long long* sy;     // [nodes][2]
     int32_t* label;
     int32_t* btop; int32_t* bbot;    // [ntiles*T_TW]
     int32_t* blef; int32_t* brig;    // [ntiles*T_TH]
-    int32_t* counters;   // [0] kept nodes listed (zeroed by the host before the tile pass)
+    int32_t* counters;   // [0] kept nodes listed, [1] overflow tiles (zeroed by the host before the tile pass)
     int32_t* trcnt;      // [nty] surviving components per tile row (zeroed with counters)
     int32_t* klist;      // [ntiles*T_CAP] kept node ids, in no particular order
     int32_t* lpos;       // [nodes] tile-local index (row * T_TW + col) of the node's own first pixel
@@ -98,7 +101,7 @@ struct TileShared {
     int16_t rkid[RCAP];              // kept id at the root run, -1 if dropped
     int32_t nruns, nkept;
     // statistics of the first KCAP kept components
-    double k_sum[KCAP], k_sx[KCAP], k_sy[KCAP];
+    long long k_sum[KCAP][2], k_sx[KCAP][2], k_sy[KCAP][2];
     uint32_t k_peak[KCAP];
     int32_t k_xmin[KCAP], k_xmax[KCAP], k_ymin[KCAP], k_ymax[KCAP];
     int32_t wsum[2 * (T_TH * T_WPR / 32) > T_THREADS / 32 ? 2 * (T_TH * T_WPR / 32) : T_THREADS / 32];
@@ -107,6 +110,23 @@ using TileFast = TileShared<T_RCAP_FAST, KCAP_FAST>;
 using TileFull = TileShared<T_RCAP, KCAP_FULL>;
 
 constexpr int BORDER_BIT = 1 << 30;
+
+// A float as two integers, v = c 2^-8 + f 2^-40 exactly for |v| >= 2^-17 (its
+// bits below 2^-40 are dropped otherwise): c = rint(v 2^8), and f the residual
+// v - c 2^-8 (|.| <= 2^-9, formed exactly in FP32) in units of 2^-40.  Sums of
+// such pairs are exact and order-independent; the c sums stay in range while
+// the totals stay below ~3.6e16 (values, or values times pixel coordinates).
+__device__ __forceinline__ void fx_split(float v, long long out[2]) {
+    const long long c = __float2ll_rn(v * 256.0f);
+    const float rsd = fabsf(v) < 65536.0f ? v - (float)c * (1.0f / 256.0f) : 0.0f;
+    out[0] = c;
+    out[1] = __float2ll_rn(rsd * 1099511627776.0f);
+}
+// the pair's value in double-float
+__device__ __forceinline__ df fx_value(const long long* p) {
+    const df a = df_from_i64(__ldcg(p)), b = df_from_i64(__ldcg(p + 1));
+    return df_add(df_scale(a, 1.0f / 256.0f), df_scale(b, 1.0f / 1099511627776.0f));
+}
 static_assert(T_TH * T_WPR <= T_THREADS, "one thread per mask word");
 
 __device__ __forceinline__ int rfind(const int32_t* P, int x) {
@@ -578,7 +598,7 @@ __device__ bool tile_label_body(const TileJob& J, SH& S, int tile) {
     __syncthreads();
     const int nk = S.nkept;
     for (int c = threadIdx.x; c < min(nk, KCAP); c += T_THREADS) {
-        S.k_sum[c] = 0.0; S.k_sx[c] = 0.0; S.k_sy[c] = 0.0;
+        S.k_sum[c][0] = S.k_sum[c][1] = 0; S.k_sx[c][0] = S.k_sx[c][1] = 0; S.k_sy[c][0] = S.k_sy[c][1] = 0;
         S.k_peak[c] = 0u;
         S.k_xmin[c] = T_TW; S.k_xmax[c] = -1; S.k_ymin[c] = T_TH; S.k_ymax[c] = -1;
     }
@@ -588,7 +608,7 @@ __device__ bool tile_label_body(const TileJob& J, SH& S, int tile) {
         const int kid = (S.rpar[i] == i) ? S.rkid[i] : -1;
         if (kid >= KCAP) {
             const int node = tile * T_CAP + kid;
-            J.ws.sum[node] = 0.0; J.ws.sx[node] = 0.0; J.ws.sy[node] = 0.0;
+            for (int h = 0; h < 2; h++) J.ws.sum[2 * node + h] = J.ws.sx[2 * node + h] = J.ws.sy[2 * node + h] = 0;
             J.ws.peak[node] = 0u;
             J.ws.xmin[node] = INT32_MAX; J.ws.xmax[node] = -1; J.ws.ymin[node] = INT32_MAX; J.ws.ymax[node] = -1;
         }
@@ -615,10 +635,16 @@ __device__ bool tile_label_body(const TileJob& J, SH& S, int tile) {
                     pk = fmaxf(pk, f[u]);
                 }
         }
+        // the run's FP32 partial sums as exact integer pairs
+        long long f0[2], f1[2];
+        fx_split(s0, f0);
+        fx_split(s1, f1);
         if (kid < KCAP) {
-            atomicAdd(&S.k_sum[kid], (double)s0);
-            atomicAdd(&S.k_sx[kid], (double)s1);
-            atomicAdd(&S.k_sy[kid], (double)s0 * (double)r);
+            for (int h = 0; h < 2; h++) {
+                atomicAdd(reinterpret_cast<unsigned long long*>(&S.k_sum[kid][h]), (unsigned long long)f0[h]);
+                atomicAdd(reinterpret_cast<unsigned long long*>(&S.k_sx[kid][h]), (unsigned long long)f1[h]);
+                atomicAdd(reinterpret_cast<unsigned long long*>(&S.k_sy[kid][h]), (unsigned long long)(f0[h] * r));
+            }
             atomicMax(&S.k_peak[kid], fkey(pk));
             atomicMin(&S.k_xmin[kid], st);
             atomicMax(&S.k_xmax[kid], en);
@@ -626,9 +652,13 @@ __device__ bool tile_label_body(const TileJob& J, SH& S, int tile) {
             atomicMax(&S.k_ymax[kid], r);
         } else {
             const int node = tile * T_CAP + kid;
-            atomicAdd(&J.ws.sum[node], (double)s0);
-            atomicAdd(&J.ws.sx[node], (double)s1 + (double)(int)tx0 * (double)s0);
-            atomicAdd(&J.ws.sy[node], (double)s0 * (double)((int)ty0 + r));
+            for (int h = 0; h < 2; h++) {
+                atomicAdd(reinterpret_cast<unsigned long long*>(&J.ws.sum[2 * node + h]), (unsigned long long)f0[h]);
+                atomicAdd(reinterpret_cast<unsigned long long*>(&J.ws.sx[2 * node + h]),
+                          (unsigned long long)(f1[h] + tx0 * f0[h]));
+                atomicAdd(reinterpret_cast<unsigned long long*>(&J.ws.sy[2 * node + h]),
+                          (unsigned long long)(f0[h] * (ty0 + r)));
+            }
             atomicMax(&J.ws.peak[node], fkey(pk));
             atomicMin(&J.ws.xmin[node], (int)tx0 + st);
             atomicMax(&J.ws.xmax[node], (int)tx0 + en);
@@ -652,15 +682,18 @@ __device__ bool tile_label_body(const TileJob& J, SH& S, int tile) {
             J.ws.first[node] = (unsigned long long)((ty0 + r) * J.W + tx0 + S.rs[i]);
             J.ws.lpos[node] = r * T_TW + S.rs[i];
             if (kid < KCAP) {
-                const double sm = S.k_sum[kid];
+
                 J.ws.peak[node] = S.k_peak[kid];
                 J.ws.xmin[node] = (int)tx0 + S.k_xmin[kid];
                 J.ws.xmax[node] = (int)tx0 + S.k_xmax[kid];
                 J.ws.ymin[node] = (int)ty0 + S.k_ymin[kid];
                 J.ws.ymax[node] = (int)ty0 + S.k_ymax[kid];
-                J.ws.sum[node] = sm;
-                J.ws.sx[node] = S.k_sx[kid] + (double)(int)tx0 * sm;
-                J.ws.sy[node] = S.k_sy[kid] + (double)(int)ty0 * sm;
+                for (int h = 0; h < 2; h++) {
+                    const long long sm = S.k_sum[kid][h];
+                    J.ws.sum[2 * node + h] = sm;
+                    J.ws.sx[2 * node + h] = S.k_sx[kid][h] + tx0 * sm;
+                    J.ws.sy[2 * node + h] = S.k_sy[kid][h] + ty0 * sm;
+                }
             }
         }
     }
@@ -730,55 +763,60 @@ __device__ __forceinline__ void gunite(int32_t* P, int a, int b) {
     }
 }
 
-__global__ void k_ccl_union(CclWs ws, int ntx, int nty) {
-    const int tx = blockIdx.x, ty = blockIdx.y, tile = ty * ntx + tx;
-    const int t = threadIdx.x;  // 128 threads
-    if (ty + 1 < nty) {  // bottom seam, including the diagonal corners
-        const int below = tile + ntx;
-        int a = __ldcg(ws.bbot + (int64_t)tile * T_TW + t);
-        if (a >= 0) {
-            for (int d = -1; d <= 1; d++) {
-                int j = t + d;
-                int b;
-                if (j < 0) b = (tx > 0) ? __ldcg(ws.btop + (int64_t)(below - 1) * T_TW + T_TW - 1) : -1;
-                else if (j >= T_TW) b = (tx + 1 < ntx) ? __ldcg(ws.btop + (int64_t)(below + 1) * T_TW) : -1;
-                else b = __ldcg(ws.btop + (int64_t)below * T_TW + j);
-                if (b >= 0) gunite(ws.parent, a, b);
+// ---- global phase, as per-unit bodies run by the persistent kernel below ----
+// seams of one tile: threads 0..127 the bottom seam (diagonal corners
+// included), threads 128..159 the right seam
+__device__ void ccl_union_tile(const CclWs& ws, int tile, int ntx, int nty) {
+    const int ty = tile / ntx, tx = tile - ty * ntx;
+    const int t = threadIdx.x;
+    if (t < T_TW) {
+        if (ty + 1 < nty) {
+            const int below = tile + ntx;
+            const int a = __ldcg(ws.bbot + (int64_t)tile * T_TW + t);
+            if (a >= 0) {
+                for (int d = -1; d <= 1; d++) {
+                    const int j = t + d;
+                    int b;
+                    if (j < 0) b = (tx > 0) ? __ldcg(ws.btop + (int64_t)(below - 1) * T_TW + T_TW - 1) : -1;
+                    else if (j >= T_TW) b = (tx + 1 < ntx) ? __ldcg(ws.btop + (int64_t)(below + 1) * T_TW) : -1;
+                    else b = __ldcg(ws.btop + (int64_t)below * T_TW + j);
+                    if (b >= 0) gunite(ws.parent, a, b);
+                }
             }
         }
-    }
-    if (tx + 1 < ntx && t < T_TH) {  // right seam
-        const int right = tile + 1;
-        int a = __ldcg(ws.brig + (int64_t)tile * T_TH + t);
-        if (a >= 0) {
-            for (int d = -1; d <= 1; d++) {
-                int i = t + d;
-                if (i < 0 || i >= T_TH) continue;
-                int b = __ldcg(ws.blef + (int64_t)right * T_TH + i);
-                if (b >= 0) gunite(ws.parent, a, b);
+    } else if (t < T_TW + T_TH) {
+        const int i0 = t - T_TW;
+        if (tx + 1 < ntx) {
+            const int right = tile + 1;
+            const int a = __ldcg(ws.brig + (int64_t)tile * T_TH + i0);
+            if (a >= 0) {
+                for (int d = -1; d <= 1; d++) {
+                    const int i = i0 + d;
+                    if (i < 0 || i >= T_TH) continue;
+                    const int b = __ldcg(ws.blef + (int64_t)right * T_TH + i);
+                    if (b >= 0) gunite(ws.parent, a, b);
+                }
             }
         }
     }
 }
 
-// fold every kept node into its root (grid-stride over the kept-node list)
-__global__ void k_ccl_resolve(CclWs ws) {
-    const int n = __ldcg(ws.counters);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const int node = ws.klist[t];
-        const int r = gfind(ws.parent, node);
-        if (r == node) continue;
-        ws.parent[node] = r;
-        atomicAdd(&ws.area[r], ws.area[node]);
-        atomicMin(&ws.first[r], ws.first[node]);
-        atomicMax(&ws.peak[r], ws.peak[node]);
-        atomicMin(&ws.xmin[r], ws.xmin[node]);
-        atomicMax(&ws.xmax[r], ws.xmax[node]);
-        atomicMin(&ws.ymin[r], ws.ymin[node]);
-        atomicMax(&ws.ymax[r], ws.ymax[node]);
-        atomicAdd(&ws.sum[r], ws.sum[node]);
-        atomicAdd(&ws.sx[r], ws.sx[node]);
-        atomicAdd(&ws.sy[r], ws.sy[node]);
+// fold kept node `node` into its root
+__device__ __forceinline__ void ccl_resolve_node(const CclWs& ws, int node) {
+    const int r = gfind(ws.parent, node);
+    if (r == node) return;
+    ws.parent[node] = r;
+    atomicAdd(&ws.area[r], ws.area[node]);
+    atomicMin(&ws.first[r], ws.first[node]);
+    atomicMax(&ws.peak[r], ws.peak[node]);
+    atomicMin(&ws.xmin[r], ws.xmin[node]);
+    atomicMax(&ws.xmax[r], ws.xmax[node]);
+    atomicMin(&ws.ymin[r], ws.ymin[node]);
+    atomicMax(&ws.ymax[r], ws.ymax[node]);
+    for (int h = 0; h < 2; h++) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ws.sum[2 * r + h]), (unsigned long long)ws.sum[2 * node + h]);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ws.sx[2 * r + h]), (unsigned long long)ws.sx[2 * node + h]);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ws.sy[2 * r + h]), (unsigned long long)ws.sy[2 * node + h]);
     }
 }
 
@@ -789,20 +827,25 @@ __global__ void k_ccl_resolve(CclWs ws) {
 //   (survivors of earlier tile rows) + (survivors of this tile row whose first
 //   pixel lies in an earlier row, or in the same row in an earlier tile)
 //   + (its rank among its home tile's survivors of that row) + 1.
-// k_ccl_count: one block per tile, ranks the tile's home survivors in kept-id
-// order and counts them per row; dropped roots get label 0.
-constexpr int CN_THREADS = 128;
-__global__ void __launch_bounds__(CN_THREADS) k_ccl_count(CclWs ws, int64_t W, int ntx, int min_area) {
-    __shared__ int cnt[T_TH];
-    __shared__ int wsum[CN_THREADS / 32];
-    const int tile = blockIdx.x, ty = tile / ntx, tx = tile - ty * ntx;
+// ccl_count_tile: ranks the tile's home survivors in kept-id order and counts
+// them per row; dropped roots get label 0.  Block-wide.
+constexpr int G_THREADS = 256, G_WARPS = G_THREADS / 32;
+struct GShared {
+    int cnt[T_TH];
+    int red[G_WARPS];
+    int carry;
+};
+constexpr int CT_WORDS = 8;   // CclWs::counters words before the per-tile-row counts
+
+__device__ void ccl_count_tile(const CclWs& ws, GShared& G, int tile, int64_t W, int ntx, int min_area) {
+    const int ty = tile / ntx, tx = tile - ty * ntx;
     const int64_t tx0 = (int64_t)tx * T_TW, ty0 = (int64_t)ty * T_TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < T_TH) cnt[threadIdx.x] = 0;
+    if (threadIdx.x < T_TH) G.cnt[threadIdx.x] = 0;
     __syncthreads();
     const int nk = __ldcg(ws.nkept + tile);
     int chunk0 = 0;
-    for (int base = 0; base < nk; base += CN_THREADS) {
+    for (int base = 0; base < nk; base += G_THREADS) {
         const int k = base + threadIdx.x;
         bool surv = false;
         int r = 0;
@@ -817,53 +860,49 @@ __global__ void __launch_bounds__(CN_THREADS) k_ccl_count(CclWs ws, int64_t W, i
             if (root == node && !big) ws.label[node] = 0;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, surv);
-        if (lane == 0) wsum[warp] = __popc(bal);
+        if (lane == 0) G.red[warp] = __popc(bal);
         __syncthreads();
         int before = chunk0, total = chunk0;
-        for (int w = 0; w < CN_THREADS / 32; w++) {
-            if (w < warp) before += wsum[w];
-            total += wsum[w];
+        for (int w = 0; w < G_WARPS; w++) {
+            if (w < warp) before += G.red[w];
+            total += G.red[w];
         }
         if (k < nk) ws.pk[tile * T_CAP + k] = surv ? before + __popc(bal & ((1u << lane) - 1u)) : -1;
-        if (surv) atomicAdd(&cnt[r], 1);
+        if (surv) atomicAdd(&G.cnt[r], 1);
         __syncthreads();
         chunk0 = total;
     }
-    if (threadIdx.x < T_TH) ws.rowcnt[tile * T_TH + threadIdx.x] = cnt[threadIdx.x];
+    if (threadIdx.x < T_TH) ws.rowcnt[tile * T_TH + threadIdx.x] = G.cnt[threadIdx.x];
     if (threadIdx.x == 0 && chunk0 > 0) atomicAdd(&ws.trcnt[ty], chunk0);
+    __syncthreads();
 }
 
-// k_ccl_scan: one block per tile row.  Exclusive scan of the (row, tile)
+// ccl_scan_row: one tile row, block-wide.  Exclusive scan of the (row, tile)
 // survivor counts in raster order; each (tile, row) entry of rowcnt is replaced
 // by the label offset of its survivors: (survivors of earlier tile rows) +
-// (scan value) - (the tile's survivors in earlier rows).
-constexpr int CL_THREADS = 256;
-__global__ void __launch_bounds__(CL_THREADS) k_ccl_scan(CclWs ws, int ntx, int nty, int32_t* n_src_dev) {
-    extern __shared__ int cl_smem[];
-    int* off = cl_smem;                   // [T_TH][ntx] counts, then their exclusive prefix
-    int* rstart = cl_smem + T_TH * ntx;   // [T_TH][ntx] survivors of the tile in earlier rows
-    __shared__ int red[CL_THREADS / 32];
-    __shared__ int carry;
-    const int ty = blockIdx.x;
+// (scan value) - (the tile's survivors in earlier rows).  `sm` holds 2 T_TH ntx ints.
+__device__ void ccl_scan_row(const CclWs& ws, GShared& G, int* sm, int ty, int ntx, int nty, int32_t* n_src_dev) {
+    int* off = sm;                   // [T_TH][ntx] counts, then their exclusive prefix
+    int* rstart = sm + T_TH * ntx;   // [T_TH][ntx] survivors of the tile in earlier rows
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int base = 0;  // survivors of earlier tile rows
-    for (int t = threadIdx.x; t < ty; t += CL_THREADS) base += __ldcg(ws.trcnt + t);
+    for (int t = threadIdx.x; t < ty; t += G_THREADS) base += __ldcg(ws.trcnt + t);
     base = __reduce_add_sync(0xffffffffu, base);
-    if (lane == 0) red[warp] = base;
-    for (int i = threadIdx.x; i < T_TH * ntx; i += CL_THREADS) {
+    if (lane == 0) G.red[warp] = base;
+    for (int i = threadIdx.x; i < T_TH * ntx; i += G_THREADS) {
         const int r = i / ntx, tx = i - r * ntx;
         off[i] = __ldcg(ws.rowcnt + (int64_t)(ty * ntx + tx) * T_TH + r);
     }
-    if (threadIdx.x == 0) carry = 0;
+    if (threadIdx.x == 0) G.carry = 0;
     __syncthreads();
     base = 0;
-    for (int w = 0; w < CL_THREADS / 32; w++) base += red[w];
-    for (int tx = threadIdx.x; tx < ntx; tx += CL_THREADS) {
+    for (int w = 0; w < G_WARPS; w++) base += G.red[w];
+    for (int tx = threadIdx.x; tx < ntx; tx += G_THREADS) {
         int acc = 0;
         for (int r = 0; r < T_TH; r++) { rstart[r * ntx + tx] = acc; acc += off[r * ntx + tx]; }
     }
     __syncthreads();
-    for (int c0 = 0; c0 < T_TH * ntx; c0 += CL_THREADS) {
+    for (int c0 = 0; c0 < T_TH * ntx; c0 += G_THREADS) {
         const int i = c0 + threadIdx.x;
         const int v = i < T_TH * ntx ? off[i] : 0;
         int inc = v;
@@ -872,81 +911,79 @@ __global__ void __launch_bounds__(CL_THREADS) k_ccl_scan(CclWs ws, int ntx, int 
             const int t = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += t;
         }
-        if (lane == 31) red[warp] = inc;
+        if (lane == 31) G.red[warp] = inc;
         __syncthreads();
-        int before = carry;
-        for (int w = 0; w < warp; w++) before += red[w];
+        int before = G.carry;
+        for (int w = 0; w < warp; w++) before += G.red[w];
         if (i < T_TH * ntx) off[i] = before + inc - v;
         __syncthreads();
-        if (threadIdx.x == CL_THREADS - 1) carry = before + inc;
+        if (threadIdx.x == G_THREADS - 1) G.carry = before + inc;
         __syncthreads();
     }
-    if (threadIdx.x == 0 && ty == nty - 1) *n_src_dev = base + carry;
-    for (int i = threadIdx.x; i < T_TH * ntx; i += CL_THREADS) {
+    if (threadIdx.x == 0 && ty == nty - 1) *n_src_dev = base + G.carry;
+    for (int i = threadIdx.x; i < T_TH * ntx; i += G_THREADS) {
         const int r = i / ntx, tx = i - r * ntx;
         ws.rowcnt[(int64_t)(ty * ntx + tx) * T_TH + r] = base + off[i] - rstart[i];
     }
+    __syncthreads();
 }
 
-// k_ccl_emit: one thread per kept node (all tiles): a home survivor writes its
-// component's label (offset + rank + 1) and catalog entry.
-__global__ void k_ccl_emit(CclWs ws, int32_t max_src, ipp_src_stats out) {
-    const int n = __ldcg(ws.counters);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const int node = __ldcg(ws.klist + t);
-        const int p = __ldcg(ws.pk + node);
-        if (p < 0) continue;
-        const int tile = node / T_CAP;
-        const int r = __ldcg(ws.lpos + node) / T_TW;
-        const int lab = __ldcg(ws.rowcnt + (int64_t)tile * T_TH + r) + p + 1;
-        const int root = __ldcg(ws.parent + node);
-        ws.label[root] = lab;
-        if (lab <= max_src) {
-            const int k = lab - 1;
-            const double sm = __ldcg(ws.sum + root);
-            out.area[k] = __ldcg(ws.area + root);
-            out.first[k] = (int64_t)__ldcg(ws.first + root);
-            out.xmin[k] = __ldcg(ws.xmin + root);
-            out.xmax[k] = __ldcg(ws.xmax + root);
-            out.ymin[k] = __ldcg(ws.ymin + root);
-            out.ymax[k] = __ldcg(ws.ymax + root);
-            out.peak[k] = fkey_inv(__ldcg(ws.peak + root));
-            out.flux[k] = (float)sm;
-            out.xbar[k] = (float)(__ldcg(ws.sx + root) / sm);
-            out.ybar[k] = (float)(__ldcg(ws.sy + root) / sm);
-        }
+// a home survivor writes its component's label (offset + rank + 1) and its
+// catalog entry
+__device__ __forceinline__ void ccl_emit_node(const CclWs& ws, int node, int32_t max_src, const ipp_src_stats& out) {
+    const int p = __ldcg(ws.pk + node);
+    if (p < 0) return;
+    const int tile = node / T_CAP;
+    const int r = __ldcg(ws.lpos + node) / T_TW;
+    const int lab = __ldcg(ws.rowcnt + (int64_t)tile * T_TH + r) + p + 1;
+    const int root = __ldcg(ws.parent + node);
+    ws.label[root] = lab;
+    if (lab <= max_src) {
+        const int k = lab - 1;
+        out.area[k] = __ldcg(ws.area + root);
+        out.first[k] = (int64_t)__ldcg(ws.first + root);
+        out.xmin[k] = __ldcg(ws.xmin + root);
+        out.xmax[k] = __ldcg(ws.xmax + root);
+        out.ymin[k] = __ldcg(ws.ymin + root);
+        out.ymax[k] = __ldcg(ws.ymax + root);
+        out.peak[k] = fkey_inv(__ldcg(ws.peak + root));
+        // flux and barycentre from the exact sums, in double-float
+        const df dsm = fx_value(ws.sum + 2 * root);
+        out.flux[k] = __fadd_rn(dsm.hi, dsm.lo);
+        const df bx = df_div(fx_value(ws.sx + 2 * root), dsm);
+        const df by = df_div(fx_value(ws.sy + 2 * root), dsm);
+        out.xbar[k] = __fadd_rn(bx.hi, bx.lo);
+        out.ybar[k] = __fadd_rn(by.hi, by.lo);
     }
 }
 
-// Second tile pass: expand the tile's runs into the label map (0 for
-// background and dropped components), writing every pixel once, coalesced.
-constexpr int TF_THREADS = 256;
-__global__ void __launch_bounds__(TF_THREADS) k_tile_final(CclWs ws, int64_t W, int64_t H, int ntx,
-                                                         int32_t* labels) {
-    __shared__ __align__(16) int32_t lab[T_TH][T_TW];
-    const int tx = blockIdx.x, ty = blockIdx.y, tile = ty * ntx + tx;
+// expand one tile's runs into the label map (0 for background and dropped
+// components), writing every pixel once, coalesced; `lab` holds T_TH x T_TW ints
+__device__ void ccl_final_tile(const CclWs& ws, int32_t* lab, int tile, int64_t W, int64_t H, int ntx,
+                               int32_t* labels) {
+    const int ty = tile / ntx, tx = tile - ty * ntx;
     const int64_t tx0 = (int64_t)tx * T_TW, ty0 = (int64_t)ty * T_TH;
-    int4* l4 = reinterpret_cast<int4*>(&lab[0][0]);
-    for (int t = threadIdx.x; t < T_TH * T_TW / 4; t += TF_THREADS) l4[t] = make_int4(0, 0, 0, 0);
+    int4* l4 = reinterpret_cast<int4*>(lab);
+    for (int t = threadIdx.x; t < T_TH * T_TW / 4; t += G_THREADS) l4[t] = make_int4(0, 0, 0, 0);
     __syncthreads();
-    const int nr = ws.nruns[tile];
-    for (int i = threadIdx.x; i < nr; i += TF_THREADS) {
+    const int nr = __ldcg(ws.nruns + tile);
+    for (int i = threadIdx.x; i < nr; i += G_THREADS) {
         const int node = __ldcg(ws.run_node + (int64_t)tile * T_RCAP + i);
         if (node < 0) continue;
         const int v = __ldcg(ws.label + __ldcg(ws.parent + node));
         if (v == 0) continue;
         const uint32_t rr = __ldcg(ws.runs + (int64_t)tile * T_RCAP + i);
         const int r = rr >> 16, st = (rr >> 8) & 0xff, en = rr & 0xff;
-        for (int c = st; c <= en; c++) lab[r][c] = v;
+        for (int c = st; c <= en; c++) lab[r * T_TW + c] = v;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t xc = tx0 + lane * 4;
     const bool vec = (W % 4 == 0) && (((uintptr_t)labels & 15) == 0) && (xc + 4 <= W);
-    for (int r = warp; r < T_TH; r += TF_THREADS / 32) {
+    for (int r = warp; r < T_TH; r += G_WARPS) {
         const int64_t y = ty0 + r;
         if (y >= H || xc >= W) continue;
-        const int4 o = *reinterpret_cast<const int4*>(&lab[r][lane * 4]);
+        const int4 o = *reinterpret_cast<const int4*>(&lab[r * T_TW + lane * 4]);
         if (vec) {
             *reinterpret_cast<int4*>(labels + y * W + xc) = o;
         } else {
@@ -956,6 +993,45 @@ __global__ void __launch_bounds__(TF_THREADS) k_tile_final(CclWs ws, int64_t W, 
                 if (xc + c < W) labels[y * W + xc + c] = vals[c];
         }
     }
+    __syncthreads();
+}
+
+
+// ---- the global phase: one launch per step ------------------------------------
+// (Folding these into one cooperative persistent kernel with grid-wide barriers
+// was measured slower: each barrier added 3-5 us, and a cooperative launch,
+// which needs all its blocks resident at once, stops the labeling of one frame
+// from overlapping the kernels of frames on other streams.)
+__global__ void __launch_bounds__(G_THREADS) k_ccl_union(CclWs ws, int ntx, int nty) {
+    ccl_union_tile(ws, blockIdx.x, ntx, nty);
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_ccl_resolve(CclWs ws) {
+    const int n = __ldcg(ws.counters);
+    for (int t = blockIdx.x * G_THREADS + threadIdx.x; t < n; t += gridDim.x * G_THREADS)
+        ccl_resolve_node(ws, __ldcg(ws.klist + t));
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_ccl_count(CclWs ws, int64_t W, int ntx, int min_area) {
+    __shared__ GShared G;
+    ccl_count_tile(ws, G, blockIdx.x, W, ntx, min_area);
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_ccl_scan(CclWs ws, int ntx, int nty, int32_t* n_src_dev) {
+    extern __shared__ __align__(16) int g_sm[];   // 2 T_TH ntx ints
+    __shared__ GShared G;
+    ccl_scan_row(ws, G, g_sm, blockIdx.x, ntx, nty, n_src_dev);
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_ccl_emit(CclWs ws, int32_t max_src, ipp_src_stats out) {
+    const int n = __ldcg(ws.counters);
+    for (int t = blockIdx.x * G_THREADS + threadIdx.x; t < n; t += gridDim.x * G_THREADS)
+        ccl_emit_node(ws, __ldcg(ws.klist + t), max_src, out);
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_tile_final(CclWs ws, int64_t W, int64_t H, int ntx, int32_t* labels) {
+    __shared__ __align__(16) int32_t lab[T_TH * T_TW];
+    ccl_final_tile(ws, lab, blockIdx.x, W, H, ntx, labels);
 }
 
 }  // namespace ipp
@@ -985,11 +1061,11 @@ static CclLayout ccl_layout(int64_t W, int64_t H) {
         (size_t)L.nodes * 4, (size_t)L.nodes * 4,              // parent, area
         (size_t)L.nodes * 8, (size_t)L.nodes * 4,              // first, peak
         (size_t)L.nodes * 4, (size_t)L.nodes * 4, (size_t)L.nodes * 4, (size_t)L.nodes * 4,  // bbox
-        (size_t)L.nodes * 8, (size_t)L.nodes * 8, (size_t)L.nodes * 8,  // sum sx sy
+        (size_t)L.nodes * 16, (size_t)L.nodes * 16, (size_t)L.nodes * 16,  // sum sx sy (integer pairs)
         (size_t)L.nodes * 4,                                   // label
         (size_t)L.ntiles * T_TW * 4, (size_t)L.ntiles * T_TW * 4,  // btop bbot
         (size_t)L.ntiles * T_TH * 4, (size_t)L.ntiles * T_TH * 4,  // blef brig
-        (size_t)(L.nty + 8) * 4,                               // counters + trcnt
+        (size_t)(L.nty + CT_WORDS) * 4,                        // counters + trcnt
         (size_t)L.nodes * 4,                                   // klist
         (size_t)L.nodes * 4, (size_t)L.nodes * 4,              // lpos, pk
         (size_t)cdiv(W, 32) * (size_t)H * 4,                   // detection bit rows
@@ -1017,16 +1093,16 @@ static CclWs ccl_ws(const CclLayout& L, void* ws) {
     w.xmax = (int32_t*)(b + L.off[9]);
     w.ymin = (int32_t*)(b + L.off[10]);
     w.ymax = (int32_t*)(b + L.off[11]);
-    w.sum = (double*)(b + L.off[12]);
-    w.sx = (double*)(b + L.off[13]);
-    w.sy = (double*)(b + L.off[14]);
+    w.sum = (long long*)(b + L.off[12]);
+    w.sx = (long long*)(b + L.off[13]);
+    w.sy = (long long*)(b + L.off[14]);
     w.label = (int32_t*)(b + L.off[15]);
     w.btop = (int32_t*)(b + L.off[16]);
     w.bbot = (int32_t*)(b + L.off[17]);
     w.blef = (int32_t*)(b + L.off[18]);
     w.brig = (int32_t*)(b + L.off[19]);
     w.counters = (int32_t*)(b + L.off[20]);
-    w.trcnt = w.counters + 8;
+    w.trcnt = w.counters + CT_WORDS;
     w.klist = (int32_t*)(b + L.off[21]);
     w.lpos = (int32_t*)(b + L.off[22]);
     w.pk = (int32_t*)(b + L.off[23]);
@@ -1077,7 +1153,7 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
     cudaFuncSetAttribute(k_tile_label_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileFull));
     dim3 tg(L.ntx, L.nty);
     // the kept-node counter, the overflow count and the per-tile-row counts start at zero
-    if (cudaMemsetAsync(w.counters, 0, (size_t)(L.nty + 8) * 4, s) != cudaSuccess) return ipp_check_launch("memset");
+    if (cudaMemsetAsync(w.counters, 0, (size_t)(L.nty + CT_WORDS) * 4, s) != cudaSuccess) return ipp_check_launch("memset");
     k_tile_label<<<tg, T_THREADS, sizeof(TileFast), s>>>(J);
     if (int e = ipp_check_launch("k_tile_label")) return e;
     {
@@ -1088,23 +1164,24 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
         k_tile_label_full<<<(unsigned)fg, T_THREADS, sizeof(TileFull), s>>>(J);
         if (int e = ipp_check_launch("k_tile_label_full")) return e;
     }
-    k_ccl_union<<<tg, 128, 0, s>>>(w, L.ntx, L.nty);
+    const unsigned nt = (unsigned)L.ntiles;
+    k_ccl_union<<<nt, G_THREADS, 0, s>>>(w, L.ntx, L.nty);
     if (int e = ipp_check_launch("k_ccl_union")) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned pg = (unsigned)std::max(sms, 1) * 8;  // persistent grid over the kept nodes
-    k_ccl_resolve<<<pg, 256, 0, s>>>(w);
+    const unsigned pg = (unsigned)std::max(sms, 1) * 4;  // grid-stride over the kept nodes
+    k_ccl_resolve<<<pg, G_THREADS, 0, s>>>(w);
     if (int e = ipp_check_launch("k_ccl_resolve")) return e;
-    k_ccl_count<<<(unsigned)L.ntiles, CN_THREADS, 0, s>>>(w, A.W, L.ntx, A.min_area);
+    k_ccl_count<<<nt, G_THREADS, 0, s>>>(w, A.W, L.ntx, A.min_area);
     if (int e = ipp_check_launch("k_ccl_count")) return e;
     const size_t lsm = (size_t)2 * T_TH * L.ntx * sizeof(int);
     if (lsm > 200 * 1024) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "frame too wide for the labeling pass");
     cudaFuncSetAttribute(k_ccl_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm);
-    k_ccl_scan<<<L.nty, CL_THREADS, lsm, s>>>(w, L.ntx, L.nty, A.n_src_dev);
+    k_ccl_scan<<<L.nty, G_THREADS, lsm, s>>>(w, L.ntx, L.nty, A.n_src_dev);
     if (int e = ipp_check_launch("k_ccl_scan")) return e;
-    k_ccl_emit<<<pg, 256, 0, s>>>(w, A.max_src, A.stats);
+    k_ccl_emit<<<pg, G_THREADS, 0, s>>>(w, A.max_src, A.stats);
     if (int e = ipp_check_launch("k_ccl_emit")) return e;
-    k_tile_final<<<tg, TF_THREADS, 0, s>>>(w, A.W, A.H, L.ntx, A.labels);
+    k_tile_final<<<nt, G_THREADS, 0, s>>>(w, A.W, A.H, L.ntx, A.labels);
     return ipp_check_launch("k_tile_final");
 }

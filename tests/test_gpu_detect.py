@@ -129,3 +129,4 @@ def test_mixed_dense_and_sparse_tiles(gpu, orc):
     sub = rng.uniform(0.5, 50.0, (H, W)).astype(np.float32)
     for min_area in (1, 5):
         _run_mask(gpu, orc, mask, sub, min_area)
+
