@@ -1909,7 +1909,8 @@ int orc_spline_map(const float* mesh, int64_t nx, int64_t ny, int32_t mesh_w, in
  *     below the detection threshold there; it is merged into the brighter
  *     object whose model is largest there (ties: smaller label), following
  *     merges to an object that is kept;
- *   kept objects are renumbered 1.. in the order of their labels.
+ *   kept objects are renumbered 1.. in the order of their labels (a label with
+ *     no pixel is no object and takes no number).
  * ------------------------------------------------------------------------- */
 /* Per-object statistics of the cleaning test (arrays of nobj + 1, index = label):
  * peak value and its raster index (-1 for an empty label), barycentre and second
@@ -1993,7 +1994,7 @@ int64_t orc_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H,
     for (int64_t i = 1; i <= n; i++) { int64_t r = i; while (into[r] != r) r = into[r]; root[i] = r; }
     int64_t* num = calloc(n + 1, sizeof(int64_t));
     int64_t k = 0;
-    for (int64_t i = 1; i <= n; i++) if (root[i] == i) num[i] = ++k;
+    for (int64_t i = 1; i <= n; i++) if (root[i] == i && pidx[i] >= 0) num[i] = ++k;  /* an empty label is no object */
     for (int64_t p = 0; p < W * H; p++) {
         const int32_t l = labels[p];
         out[p] = (l <= 0 || l > n) ? 0 : (int32_t)num[root[l]];

@@ -126,3 +126,14 @@ def test_object_statistics_brute_force(orc):
             cx, cy, x2, y2, xy = j.mean(), i.mean(), 1 / 12, 1 / 12, 0.0
         got = [st[k2][l] for k2 in ("cx", "cy", "x2", "y2", "xy")]
         assert np.allclose(got, [cx, cy, x2, y2, xy], rtol=1e-12, atol=1e-12)
+
+
+def test_empty_label_takes_no_number(orc):
+    """a label with no pixel is no object: the objects on either side of it are
+    numbered 1 and 2, and the count leaves it out"""
+    sub = np.zeros((10, 30), np.float32)
+    lab = np.zeros((10, 30), np.int32)
+    sub[5, 3], lab[5, 3] = 100.0, 1
+    sub[5, 25], lab[5, 25] = 100.0, 3     # label 2 has no pixel
+    out, k = orc.clean(sub, lab, 3, 10.0)
+    assert k == 2 and out[5, 3] == 1 and out[5, 25] == 2
