@@ -500,8 +500,17 @@ def main():
     # deblending of the same candidates (also a widening, timed beside the step)
     dbws = torch.empty(ipp.load().ipp_deblend_workspace_size(W, H, 65536), dtype=torch.uint8, device=dev)
     stages["deblend"] = timeit(lambda k: ipp.deblend(subbuf, lab, nsrc, st, max_src=65536, ws=dbws))
-    _, n_deb = ipp.deblend(subbuf, lab, nsrc, st, max_src=65536, ws=dbws)
+    d_map, n_deb = ipp.deblend(subbuf, lab, nsrc, st, max_src=65536, ws=dbws)
     deblended_objects = int(n_deb.item())
+    # cleaning of the deblended objects against the detection threshold (a
+    # widening, timed beside the step)
+    clws = torch.empty(ipp.load().ipp_clean_workspace_size(65536), dtype=torch.uint8, device=dev)
+    stages["clean"] = timeit(lambda k: ipp.clean(subbuf, d_map, n_deb, 65536, mesh_rms=mr, cfg=cfg, ws=clws))
+    cleaned_objects = int(ipp.clean(subbuf, d_map, n_deb, 65536, mesh_rms=mr, cfg=cfg, ws=clws)[1].item())
+    # the natural-spline background map in place of the Keys cubic (a widening)
+    spbuf = torch.empty_like(subbuf)
+    stages["bg_subtract_spline"] = timeit(lambda k: ipp.bg_subtract_spline(frames[k % 3], mb, cfg=cfg, out=spbuf))
+    del spbuf
     # gray-scale maps of the subtracted frame (a widening, timed beside the step):
     # four distinct input/output pairs rotate, 512 MiB in all, so that each call
     # reads its input from HBM, not L2
@@ -634,6 +643,7 @@ def main():
                        "parallelism": f"replicas x{ws} (independent frames), {L} streams per GPU",
                        "l2": "inputs larger than L2: 3 rotating 64 MiB frames"},
             "sources_per_s": src_per_s, "sources_per_frame": K, "deblended_objects_per_frame": deblended_objects,
+            "cleaned_objects_per_frame": cleaned_objects,
             "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": W * H * 4,
                     "pipelining": f"each step H2D + catalog + D2H on one of {L} lane streams",
                     "d2h_bytes_per_step": 4 + 3 * 4 * nmax},

@@ -16,6 +16,7 @@
  *   ipp_aperture_phot circular aperture photometry with a local sky annulus
  *                                                             (Sec. 2.2.5)
  *   ipp_deblend       multi-threshold deblending of the candidates (Sec. 2.2.5)
+ *   ipp_clean         cleaning of the deblended objects (Sec. 2.2.5)
  *   ipp_auto_phot     auto (Kron) photometry in an elliptical aperture (Sec. 2.2.5)
  *   ipp_stamp_cut     S x S stamps at the measured positions (input of the fit)
  *   ipp_psf_fit       batched Levenberg-Marquardt PSF fit of stamps
@@ -275,6 +276,22 @@ int ipp_bg_subtract(const void* img, int dtype, int64_t W, int64_t H, int64_t pi
                     const ipp_calib* cal, const float* mesh_bkg, const ipp_bg_params* p,
                     float* sub, int64_t sub_pitch, float* bkg_map, void* stream);
 
+/*
+ * ipp_bg_subtract_spline -- the natural-spline reading of Sec. 2.2.2's spline
+ * interpolation back to full resolution (the default reading is the Keys cubic
+ * of ipp_bg_subtract): B is the tensor product of 1-D natural cubic splines
+ * through the filtered mesh nodes (node positions as in ipp_bg_subtract, zero
+ * second derivative at the end nodes, beyond them the line with the end slope);
+ * sub = f - B.  Arguments as ipp_bg_subtract, plus a workspace of
+ * ipp_bg_spline_workspace_size() bytes, 256-byte aligned (the nodes' values
+ * and second derivatives).  FP32.
+ */
+size_t ipp_bg_spline_workspace_size(int64_t W, int64_t H, const ipp_bg_params* p);
+int ipp_bg_subtract_spline(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                           const ipp_calib* cal, const float* mesh_bkg, const ipp_bg_params* p,
+                           float* sub, int64_t sub_pitch, float* bkg_map, void* ws, size_t ws_bytes,
+                           void* stream);
+
 /* --------------------------------------------------------------- detection */
 /*
  * ipp_detect_label -- pixel detection and connection into candidates, with the
@@ -360,6 +377,48 @@ int ipp_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t H, i
                 const int32_t* n_src_dev, int32_t max_src, const ipp_src_stats* stats,
                 const ipp_deblend_params* p, int32_t* out_labels, int32_t* n_out_dev, void* ws,
                 size_t ws_bytes, void* stream);
+
+/*
+ * ipp_clean -- cleaning of the deblended objects (Sec. 2.2.5: an object that
+ * does not stand out from its neighbours is merged into them).  Reading, after
+ * SExtractor's cleaning:
+ *   per object, from its pixels of sub: the peak (largest value, first in
+ *     raster order on ties); the barycentre and second moments weighted by the
+ *     positive values (1/12 added to x2 and y2 when x2 y2 - xy^2 < 1/144; no
+ *     positive pixel: the unweighted centre, x2 = y2 = 1/12, xy = 0);
+ *   model of object j: peak_j (1 + r^2 / a^2)^-beta about its barycentre,
+ *     r^2 = (y2 dx^2 - 2 xy dx dy + x2 dy^2) / (x2 y2 - xy^2),
+ *     a^2 = 2 ln 2 / (2^(1/beta) - 1);
+ *   object i merges when its peak less the sum of the models of every brighter
+ *     object (larger peak; equal peaks: smaller label), summed in label order,
+ *     at its peak pixel is below the detection threshold there; the target is
+ *     the brighter object whose model is largest there (ties: smaller label),
+ *     merges followed to a kept object; kept objects are renumbered 1.. in label
+ *     order (a label with no pixel is no object and takes no number).
+ * The sums over pixels are exact (integer accumulators), so the result does not
+ * depend on the order of the atomics; the models and the test are FP32.
+ * Processes labels 1..min(*n_obj_dev, max_obj); other labels map to 0.
+ *   labels      device int32 map (pitch W), e.g. the output of ipp_deblend
+ *   thr_map     nullable device float threshold map (pitch W); when NULL the
+ *               threshold is max(dp->k rms(x, y), dp->thresh_abs), rms the Keys
+ *               interpolation of mesh_rms on the grid of bp (the detection
+ *               threshold of ipp_detect_label), or dp->thresh_abs when mesh_rms
+ *               is NULL too
+ *   beta        Moffat index of the model, > 0 [1]
+ *   out_labels  device int32[W*H] (pitch W): the cleaned map, 0 = background
+ *   n_out_dev   device int32[1]: the number of kept objects
+ *   ws          device workspace of ipp_clean_workspace_size(max_obj) bytes
+ *               (about 200 B per object), 256-byte aligned
+ * Sizes: frames below 2^31 pixels, narrower than 65536 pixels, objects below
+ * 2^24 pixels (range of the exact sums).
+ * Errors: INVALID_ARG for NULL inputs, beta <= 0, a small or misaligned
+ * workspace, or sizes out of range.
+ */
+size_t ipp_clean_workspace_size(int32_t max_obj);
+int ipp_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t pitch,
+              const int32_t* n_obj_dev, int32_t max_obj, const float* thr_map, const float* mesh_rms,
+              const ipp_bg_params* bp, const ipp_det_params* dp, float beta, int32_t* out_labels,
+              int32_t* n_out_dev, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * ipp_auto_phot -- auto (Kron) photometry; Sec. 2.2.5 lists auto photometry

@@ -24,7 +24,7 @@ from ._abi import (  # noqa: F401
     IppError, PSF_GAUSS, PSF_MOFFAT,
 )
 
-__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "deblend", "stamp_cut", "Batch",
+__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "deblend", "clean", "bg_subtract_spline", "stamp_cut", "Batch",
            "gray_transform", "hist_equalize", "zscale", "sub_apply", "wcs_map", "affine_fit", "reproject_affine", "align",
            "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
 
@@ -133,6 +133,27 @@ def bg_subtract(img, mesh_bkg, cfg: BgConfig | None = None, bkg_map=False, calib
     return (sub, bmap) if bkg_map else sub
 
 
+def bg_subtract_spline(img, mesh_bkg, cfg: BgConfig | None = None, bkg_map=False, calib=None, out=None, ws=None,
+                       **kw):
+    """Background-subtracted frame with the natural-spline map (ipp_bg_subtract_spline)."""
+    L = load()
+    cfg = _bgcfg(cfg, kw)
+    _need_cuda(img, "img")
+    _need_cuda(mesh_bkg, "mesh_bkg", torch.float32)
+    H, W = img.shape
+    dtype, cal = _frame(img, calib)
+    p = cfg.c()
+    sub = out if out is not None else torch.empty((H, W), dtype=torch.float32, device=img.device)
+    bmap = torch.empty_like(sub) if bkg_map else None
+    need = L.ipp_bg_spline_workspace_size(W, H, p)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=img.device)
+    _abi.check("ipp_bg_subtract_spline", L.ipp_bg_subtract_spline(
+        _ptr(img), dtype, W, H, img.stride(0), cal, _ptr(mesh_bkg.contiguous()), p, _ptr(sub),
+        sub.stride(0), _ptr(bmap), _ptr(ws), ws.numel(), _stream()))
+    return (sub, bmap) if bkg_map else sub
+
+
 _STAT_TYPES = dict(area=torch.int32, first=torch.int64, xmin=torch.int32, xmax=torch.int32,
                    ymin=torch.int32, ymax=torch.int32, peak=torch.float32, flux=torch.float32,
                    xbar=torch.float32, ybar=torch.float32)
@@ -232,6 +253,32 @@ def deblend(sub, labels, n_src, stats, nthresh=32, mincont=0.005, max_src=None, 
     _abi.check("ipp_deblend", L.ipp_deblend(
         _ptr(sub), _ptr(labels.contiguous()), W, H, sub.stride(0), _ptr(n_src), n, _stats_c(stats),
         _abi.DeblendParams(nthresh, mincont), _ptr(out), _ptr(n_out), _ptr(ws), ws.numel(), _stream()))
+    return out, n_out
+
+
+def clean(sub, labels, n_obj, max_obj, thr_map=None, mesh_rms=None, cfg: BgConfig | None = None, k=1.5,
+          thresh_abs=0.0, beta=1.0, ws=None, **kw):
+    """Cleaned label map and device object count (ipp_clean).  The threshold at an
+    object's peak is thr_map there, else max(k rms, thresh_abs) with rms the
+    Keys interpolation of mesh_rms on the grid of cfg, else thresh_abs."""
+    L = load()
+    cfg = _bgcfg(cfg, kw)
+    _need_cuda(sub, "sub", torch.float32)
+    _need_cuda(labels, "labels", torch.int32)
+    H, W = sub.shape
+    dev = sub.device
+    need = L.ipp_clean_workspace_size(max_obj)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    out = torch.empty((H, W), dtype=torch.int32, device=dev)
+    n_out = torch.empty(1, dtype=torch.int32, device=dev)
+    if thr_map is not None:
+        _need_cuda(thr_map, "thr_map", torch.float32)
+        thr_map = thr_map.contiguous()
+    _abi.check("ipp_clean", L.ipp_clean(
+        _ptr(sub), _ptr(labels.contiguous()), W, H, sub.stride(0), _ptr(n_obj), max_obj, _ptr(thr_map),
+        _ptr(None if mesh_rms is None else mesh_rms.contiguous()), cfg.c(), _abi.DetParams(k, thresh_abs, 1, 0),
+        float(beta), _ptr(out), _ptr(n_out), _ptr(ws), ws.numel(), _stream()))
     return out, n_out
 
 

@@ -94,6 +94,9 @@ PROTOTYPES = {
                          vp, vp, sz, vp], i32),
     "ipp_bg_estimate_noalloc": ([vp, i32, i64, i64, i64, vp, C.POINTER(Calib), C.POINTER(BgParams), vp, vp, vp,
                                  vp], i32),
+    "ipp_bg_spline_workspace_size": ([i64, i64, C.POINTER(BgParams)], C.c_size_t),
+    "ipp_bg_subtract_spline": ([vp, i32, i64, i64, i64, C.POINTER(Calib), vp, C.POINTER(BgParams), vp, i64, vp,
+                                vp, C.c_size_t, vp], i32),
     "ipp_bg_subtract": ([vp, i32, i64, i64, i64, C.POINTER(Calib), vp, C.POINTER(BgParams), vp, i64, vp, vp],
                         i32),
     "ipp_detect_label_workspace_size": ([i64, i64], sz),
@@ -105,6 +108,9 @@ PROTOTYPES = {
     "ipp_deblend_workspace_size": ([i64, i64, i32], sz),
     "ipp_deblend": ([vp, vp, i64, i64, i64, vp, i32, C.POINTER(SrcStats), C.POINTER(DeblendParams), vp, vp, vp, sz,
                      vp], i32),
+    "ipp_clean_workspace_size": ([i32], sz),
+    "ipp_clean": ([vp, vp, i64, i64, i64, vp, i32, vp, vp, C.POINTER(BgParams), C.POINTER(DetParams), C.c_float, vp,
+                   vp, vp, sz, vp], i32),
     "ipp_auto_phot": ([vp, vp, i64, i64, i64, vp, i32, C.POINTER(SrcStats), C.POINTER(AutoParams), vp, vp, vp,
                        vp, vp, vp], i32),
     "ipp_wcs_map": ([C.POINTER(Wcs), C.POINTER(Wcs), i64, i64, i32, vp, vp, vp], i32),

@@ -137,6 +137,35 @@ extern "C" int ipp_bg_subtract(const void* img, int dtype, int64_t W, int64_t H,
     return ipp_launch_bg_subtract(J, (cudaStream_t)stream);
 }
 
+extern "C" size_t ipp_bg_spline_workspace_size(int64_t W, int64_t H, const ipp_bg_params* p) {
+    if (!p || p->mesh_w < 1 || p->mesh_h < 1 || W <= 0 || H <= 0) return 0;
+    int nx, ny;
+    grid_of(W, H, p, &nx, &ny);
+    return ipp_spline_ws_bytes(nx, ny);
+}
+
+extern "C" int ipp_bg_subtract_spline(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                                      const ipp_calib* cal, const float* mesh_bkg, const ipp_bg_params* p,
+                                      float* sub, int64_t sub_pitch, float* bkg_map, void* ws, size_t ws_bytes,
+                                      void* stream) {
+    if (int e = check_frame(img, dtype, W, H, pitch, cal)) return e;
+    if (int e = check_bg(p)) return e;
+    REQUIRE(mesh_bkg && sub, "mesh_bkg / sub NULL");
+    REQUIRE(sub_pitch >= W, "sub_pitch < W");
+    const size_t need = ipp_bg_spline_workspace_size(W, H, p);
+    REQUIRE(ws && ws_bytes >= need && ((uintptr_t)ws & 255) == 0, "workspace of %zu bytes (256-byte aligned) needed",
+            need);
+    int nx, ny;
+    grid_of(W, H, p, &nx, &ny);
+    SubJob J;
+    J.img = img; J.dtype = dtype; J.W = W; J.H = H; J.pitch = pitch;
+    J.bias_map = cal ? cal->bias_map : nullptr; J.bias = cal ? cal->bias : 0.f;
+    J.inv_flat = cal ? cal->inv_flat : nullptr;
+    J.mesh = mesh_bkg; J.nx = nx; J.ny = ny; J.mesh_w = p->mesh_w; J.mesh_h = p->mesh_h;
+    J.sub = sub; J.sub_pitch = sub_pitch; J.bkg_map = bkg_map;
+    return ipp_launch_bg_subtract_spline(J, ws, (cudaStream_t)stream);
+}
+
 // ---- detection ------------------------------------------------------------------
 static int check_stats(const ipp_src_stats* st) {
     REQUIRE(st && st->area && st->first && st->xmin && st->xmax && st->ymin && st->ymax && st->peak &&
@@ -268,6 +297,37 @@ extern "C" int ipp_deblend(const float* sub, const int32_t* labels, int64_t W, i
     J.out = out_labels; J.n_out_dev = n_out_dev;
     ipp_deblend_ws_carve(W, H, max_src, ws, &J.ws);
     return ipp_launch_deblend(J, (cudaStream_t)stream);
+}
+
+// ---- cleaning -------------------------------------------------------------------------
+extern "C" size_t ipp_clean_workspace_size(int32_t max_obj) {
+    if (max_obj < 0) return 0;
+    return ipp_clean_ws_bytes(max_obj);
+}
+
+extern "C" int ipp_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t pitch,
+                         const int32_t* n_obj_dev, int32_t max_obj, const float* thr_map, const float* mesh_rms,
+                         const ipp_bg_params* bp, const ipp_det_params* dp, float beta, int32_t* out_labels,
+                         int32_t* n_out_dev, void* ws, size_t ws_bytes, void* stream) {
+    if (int e = check_frame(sub, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(labels && n_obj_dev && out_labels && n_out_dev && ws && dp, "NULL pointer");
+    REQUIRE(beta > 0.f && std::isfinite(beta), "beta must be > 0");
+    REQUIRE(max_obj >= 0, "max_obj < 0");
+    REQUIRE(W * H < (int64_t(1) << 31) && W < 65536, "cleaning needs a frame below 2^31 pixels, W < 65536");
+    REQUIRE(((uintptr_t)ws & 255) == 0, "workspace not 256-byte aligned");
+    REQUIRE(ws_bytes >= ipp_clean_ws_bytes(max_obj), "workspace too small");
+    int nx = 0, ny = 0;
+    float mw = 1.f, mh = 1.f;
+    if (!thr_map && mesh_rms) {
+        if (int e = check_bg(bp)) return e;
+        nx = (int)cdiv(W, bp->mesh_w);
+        ny = (int)cdiv(H, bp->mesh_h);
+        mw = (float)bp->mesh_w;
+        mh = (float)bp->mesh_h;
+    }
+    return ipp_launch_clean(sub, pitch, labels, W, H, n_obj_dev, max_obj, thr_map, thr_map ? nullptr : mesh_rms,
+                            nx, ny, mw, mh, dp->k, dp->thresh_abs, beta, out_labels, n_out_dev, ws,
+                            (cudaStream_t)stream);
 }
 
 // ---- image subtraction -----------------------------------------------------------------

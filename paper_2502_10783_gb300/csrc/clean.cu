@@ -1,0 +1,352 @@
+// clean.cu -- cleaning of the deblended objects (Sec. 2.2.5: each object is
+// tested against its neighbours, and one that does not stand out from them is
+// merged into them).  The reading, after SExtractor's cleaning:
+//   per object, from its pixels: the peak (largest value, first in raster order
+//   on ties), the barycentre and second moments weighted by the positive
+//   values (1/12 added to x2 and y2 when x2 y2 - xy^2 < 1/144; no positive
+//   pixel: the unweighted centre, x2 = y2 = 1/12, xy = 0);
+//   the model of object j at a pixel: peak_j (1 + r^2 / a^2)^-beta, r^2 the
+//   moments' elliptical radius (y2 dx^2 - 2 xy dx dy + x2 dy^2) / det, with
+//   a^2 = 2 ln 2 / (2^(1/beta) - 1) (the FWHM of the Gaussian of those moments);
+//   object i is spurious when its peak less the models of every brighter object
+//   (larger peak; equal peaks: smaller label) at its peak pixel is below the
+//   detection threshold there; it merges into the brighter object whose model
+//   is largest there (ties: the smaller label), merges followed to a kept
+//   object; kept objects are renumbered 1.. in label order (a label with no
+//   pixel is no object and takes no number).
+//
+// Kernels: per-pixel statistics with atomics (the peak as one 64-bit key; the
+// weighted sums as exact integer pairs, so the barycentres do not depend on the
+// order of the adds), per-object moments, the all-pairs test (a thread per
+// object, the other objects staged through shared memory in label order, as
+// the definition sums them), merge targets followed to their roots, a
+// label-order scan and the relabelled map.
+#include "jobs.cuh"
+
+namespace ipp {
+
+constexpr int CL_T = 256;
+
+// per-object workspace (arrays of max_obj + 1 entries; index = label)
+struct CleanWs {
+    unsigned long long* pkey;   // fkey(peak) << 32 | ~raster index (max = largest, then first)
+    long long* sw;              // [2 (n+1)] sum f over positive f (pairs in 2^-8 and 2^-40 units)
+    long long* swx;             // [2 (n+1)] sum f x (pairs in 2^-8 and 2^-32 units)
+    long long* swy;             // [2 (n+1)] sum f y
+    long long* cnt;             // pixel count, sum x, sum y (unweighted) [3 (n+1)]
+    long long* mom;             // [6 (n+1)] sum f dx^2, f dy^2, f dx dy about the barycentre (pairs)
+    float4* geo;                // cx, cy, peak, valid
+    float2* blo;                // the barycentre's remainders: cx + lo.x, cy + lo.y to ~2^-48
+    float4* ell;                // y2 / (det a^2), -2 xy / (det a^2), x2 / (det a^2), threshold at the peak
+    int32_t* into;              // merge target
+    int32_t* num;               // new label of a kept object
+};
+
+// where the detection threshold comes from: a map (pitch W), else the mesh rms
+// (k rms, floored at thresh_abs), else thresh_abs alone
+struct CleanThr {
+    const float* map;
+    const float* mesh_rms;
+    int nx, ny;
+    float mesh_w, mesh_h, k, thresh_abs;
+    int64_t W;
+};
+
+__device__ __forceinline__ int clean_n(const int32_t* n_dev, int32_t max_obj) {
+    return max(0, min(__ldg(n_dev), max_obj));
+}
+
+__global__ void __launch_bounds__(CL_T) k_clean_pix_a(const float* sub, int64_t pitch, const int32_t* labels,
+                                                      int64_t W, int64_t H, const int32_t* n_dev, int32_t max_obj,
+                                                      CleanWs ws) {
+    const int n = clean_n(n_dev, max_obj);
+    for (int64_t p = (int64_t)blockIdx.x * CL_T + threadIdx.x; p < W * H; p += (int64_t)gridDim.x * CL_T) {
+        const int l = __ldg(labels + p);
+        if (l <= 0 || l > n) continue;
+        const int64_t y = p / W, x = p - y * W;
+        const float f = __ldg(sub + y * pitch + x);
+        const unsigned long long key = ((unsigned long long)fkey(f) << 32) | (unsigned long long)(~(uint32_t)p);
+        atomicMax(ws.pkey + l, key);
+        atomicAdd(reinterpret_cast<unsigned long long*>(ws.cnt + 3 * l), 1ull);
+        atomicAdd(reinterpret_cast<unsigned long long*>(ws.cnt + 3 * l + 1), (unsigned long long)x);
+        atomicAdd(reinterpret_cast<unsigned long long*>(ws.cnt + 3 * l + 2), (unsigned long long)y);
+        if (f > 0.f) {
+            long long t[2];
+            fx_split(f, t);
+            // the coordinate-weighted residuals in 2^-32 units: |t1 >> 8| < 2^23,
+            // so x < 2^16 keeps 2^24 pixels of one object inside 64 bits
+            const long long r32 = t[1] >> 8;
+            atomicAdd(reinterpret_cast<unsigned long long*>(ws.sw + 2 * l), (unsigned long long)t[0]);
+            atomicAdd(reinterpret_cast<unsigned long long*>(ws.sw + 2 * l + 1), (unsigned long long)t[1]);
+            atomicAdd(reinterpret_cast<unsigned long long*>(ws.swx + 2 * l), (unsigned long long)(t[0] * x));
+            atomicAdd(reinterpret_cast<unsigned long long*>(ws.swx + 2 * l + 1), (unsigned long long)(r32 * x));
+            atomicAdd(reinterpret_cast<unsigned long long*>(ws.swy + 2 * l), (unsigned long long)(t[0] * y));
+            atomicAdd(reinterpret_cast<unsigned long long*>(ws.swy + 2 * l + 1), (unsigned long long)(r32 * y));
+        }
+    }
+}
+
+__device__ __forceinline__ df pair32_value(const long long* p) {
+    const df a = df_from_i64(__ldcg(p)), b = df_from_i64(__ldcg(p + 1));
+    return df_add(df_scale(a, 1.0f / 256.0f), df_scale(b, 1.0f / 4294967296.0f));
+}
+
+// barycentres (exact sums, double-float quotient)
+__global__ void __launch_bounds__(CL_T) k_clean_obj_a(const int32_t* n_dev, int32_t max_obj, CleanWs ws) {
+    const int n = clean_n(n_dev, max_obj);
+    for (int l = blockIdx.x * CL_T + threadIdx.x; l <= n; l += gridDim.x * CL_T) {
+        if (l == 0) continue;
+        const long long c = ws.cnt[3 * l];
+        float cx = 0.f, cy = 0.f, lx = 0.f, ly = 0.f;
+        const df sw = fx_value(ws.sw + 2 * l);
+        if (sw.hi > 0.f) {
+            const df bx = df_div(pair32_value(ws.swx + 2 * l), sw), by = df_div(pair32_value(ws.swy + 2 * l), sw);
+            cx = __fadd_rn(bx.hi, bx.lo);
+            cy = __fadd_rn(by.hi, by.lo);
+            lx = (bx.hi - cx) + bx.lo;
+            ly = (by.hi - cy) + by.lo;
+        } else if (c > 0) {
+            const df sx = df_from_i64(ws.cnt[3 * l + 1]), sy = df_from_i64(ws.cnt[3 * l + 2]), n = df_from_i64(c);
+            const df bx = df_div(sx, n), by = df_div(sy, n);
+            cx = __fadd_rn(bx.hi, bx.lo);
+            cy = __fadd_rn(by.hi, by.lo);
+            lx = (bx.hi - cx) + bx.lo;
+            ly = (by.hi - cy) + by.lo;
+        }
+        ws.blo[l] = make_float2(lx, ly);
+        const unsigned long long k = ws.pkey[l];
+        const float pk = c > 0 ? fkey_inv((uint32_t)(k >> 32)) : -INFINITY;
+        ws.geo[l] = make_float4(cx, cy, pk, c > 0 ? 1.f : 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(CL_T) k_clean_pix_b(const float* sub, int64_t pitch, const int32_t* labels,
+                                                      int64_t W, int64_t H, const int32_t* n_dev, int32_t max_obj,
+                                                      CleanWs ws) {
+    const int n = clean_n(n_dev, max_obj);
+    for (int64_t p = (int64_t)blockIdx.x * CL_T + threadIdx.x; p < W * H; p += (int64_t)gridDim.x * CL_T) {
+        const int l = __ldg(labels + p);
+        if (l <= 0 || l > n) continue;
+        const int64_t y = p / W, x = p - y * W;
+        const float f = __ldg(sub + y * pitch + x);
+        if (!(f > 0.f)) continue;
+        const float4 g = ws.geo[l];
+        const float2 lo = ws.blo[l];
+        const float dx = ((float)x - g.x) - lo.x, dy = ((float)y - g.y) - lo.y;
+        // exact sums of the FP32 terms: the moments do not depend on the order
+        fx_atomic_add(ws.mom + 6 * l, f * dx * dx);
+        fx_atomic_add(ws.mom + 6 * l + 2, f * dy * dy);
+        fx_atomic_add(ws.mom + 6 * l + 4, f * dx * dy);
+    }
+}
+
+// the detection threshold at pixel (x, y): max(k rms(x, y), thresh_abs), rms the
+// Keys interpolation of the mesh rms (nodes clamped at the grid's edges)
+__device__ float clean_thr_at(const CleanThr& T, int64_t x, int64_t y) {
+    if (T.map) return __ldg(T.map + y * T.W + x);
+    if (!T.mesh_rms) return T.thresh_abs;
+    const float u = ((float)x + 0.5f) / T.mesh_w - 0.5f, v = ((float)y + 0.5f) / T.mesh_h - 0.5f;
+    const float qf = floorf(u), pf = floorf(v);
+    float wx[4], wy[4];
+    keys_weights(u - qf, wx);
+    keys_weights(v - pf, wy);
+    const int q0 = (int)qf, p0 = (int)pf;
+    float acc = 0.f;
+    for (int a = 0; a < 4; a++) {
+        const int p = clampi(p0 - 1 + a, 0, T.ny - 1);
+        float r = 0.f;
+        for (int b = 0; b < 4; b++) r = fmaf(wx[b], __ldg(T.mesh_rms + p * T.nx + clampi(q0 - 1 + b, 0, T.nx - 1)), r);
+        acc = fmaf(wy[a], r, acc);
+    }
+    return fmaxf(T.k * acc, T.thresh_abs);
+}
+
+// moments, the model's inverse shape, and the threshold at the peak pixel
+__global__ void __launch_bounds__(CL_T) k_clean_obj_b(const int32_t* n_dev, int32_t max_obj, CleanWs ws,
+                                                      CleanThr T, float inv_a2) {
+    const int n = clean_n(n_dev, max_obj);
+    for (int l = blockIdx.x * CL_T + threadIdx.x; l <= n; l += gridDim.x * CL_T) {
+        if (l == 0) continue;
+        const df sw = fx_value(ws.sw + 2 * l);
+        float x2 = 1.0f / 12.0f, y2 = 1.0f / 12.0f, xy = 0.f;
+        if (sw.hi > 0.f) {
+            const df m0 = df_div(fx_value(ws.mom + 6 * l), sw), m1 = df_div(fx_value(ws.mom + 6 * l + 2), sw),
+                     m2 = df_div(fx_value(ws.mom + 6 * l + 4), sw);
+            x2 = __fadd_rn(m0.hi, m0.lo);
+            y2 = __fadd_rn(m1.hi, m1.lo);
+            xy = __fadd_rn(m2.hi, m2.lo);
+            if (x2 * y2 - xy * xy < 1.0f / 144.0f) { x2 += 1.0f / 12.0f; y2 += 1.0f / 12.0f; }
+        }
+        const float det = x2 * y2 - xy * xy;
+        const float k = inv_a2 / det;
+        float thr = T.thresh_abs;
+        if (ws.geo[l].w > 0.f) {
+            const uint32_t pix = ~(uint32_t)(ws.pkey[l] & 0xffffffffu);
+            thr = clean_thr_at(T, pix % (uint32_t)T.W, pix / (uint32_t)T.W);
+        }
+        ws.ell[l] = make_float4(y2 * k, -2.0f * xy * k, x2 * k, thr);
+    }
+}
+
+// the test of object i against every brighter object (a thread per object,
+// the objects j = 1..n staged through shared memory in label order)
+__global__ void __launch_bounds__(CL_T) k_clean_test(const int32_t* n_dev, int32_t max_obj, CleanWs ws, int64_t W,
+                                                     float beta) {
+    __shared__ float4 sg[CL_T], se[CL_T];
+    __shared__ float2 sl[CL_T];
+    const int n = clean_n(n_dev, max_obj);
+    const int i = blockIdx.x * CL_T + threadIdx.x + 1;
+    const bool act = i <= n;
+    float4 gi = act ? ws.geo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool valid = act && gi.w > 0.f;
+    float px = 0.f, py = 0.f;
+    if (valid) {
+        const uint32_t pix = ~(uint32_t)(ws.pkey[i] & 0xffffffffu);
+        py = (float)(pix / (uint32_t)W);
+        px = (float)(pix - (uint32_t)py * (uint32_t)W);
+    }
+    float sum = 0.f, best = -1.f;
+    int bj = -1;
+    const bool unit = beta == 1.0f;
+    for (int j0 = 1; j0 <= n; j0 += CL_T) {
+        __syncthreads();
+        const int jj = j0 + threadIdx.x;
+        if (jj <= n) { sg[threadIdx.x] = ws.geo[jj]; se[threadIdx.x] = ws.ell[jj]; sl[threadIdx.x] = ws.blo[jj]; }
+        __syncthreads();
+        if (!valid) continue;
+        const int m = min(CL_T, n - j0 + 1);
+        for (int t = 0; t < m; t++) {
+            const int j = j0 + t;
+            const float4 g = sg[t];
+            if (j == i || !(g.w > 0.f)) continue;
+            if (!(g.z > gi.z || (g.z == gi.z && j < i))) continue;
+            const float4 e = se[t];
+            const float dx = (px - g.x) - sl[t].x, dy = (py - g.y) - sl[t].y;
+            const float q = fmaf(e.x * dx, dx, fmaf(e.y * dx, dy, e.z * dy * dy));
+            const float mv = unit ? g.z / (1.0f + q) : g.z * expf(-beta * log1pf(q));
+            sum += mv;
+            if (mv > best) { best = mv; bj = j; }
+        }
+    }
+    if (act) ws.into[i] = (valid && bj > 0 && gi.z - sum < ws.ell[i].w) ? bj : i;
+}
+
+// merge targets followed to a kept object (each target is strictly brighter, so
+// a chain has at most n steps), then the label-order numbering of the kept ones
+// in one block; the count goes to n_out
+__global__ void __launch_bounds__(1024) k_clean_number(const int32_t* n_dev, int32_t max_obj, CleanWs ws,
+                                                       int32_t* n_out) {
+    __shared__ int red[32];
+    __shared__ int carry;
+    const int n = clean_n(n_dev, max_obj);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x + 1; i <= n; i += 1024) {
+        int r = i;
+        for (int s = 0; s <= n && ws.into[r] != r; s++) r = ws.into[r];
+        ws.num[i] = r;   // root for now
+    }
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 1; base <= n; base += 1024) {
+        const int i = base + threadIdx.x;
+        // a label with no pixel is no object: it takes no number
+        const int kept = (i <= n && ws.num[i] == i && ws.geo[i].w > 0.f) ? 1 : 0;
+        int inc = kept;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) red[warp] = inc;
+        __syncthreads();
+        int before = carry;
+        for (int w = 0; w < warp; w++) before += red[w];
+        __syncthreads();
+        // the new number of a kept object; others keep their root (negated, resolved below)
+        if (i <= n) ws.into[i] = kept ? before + inc : -ws.num[i];
+        if (threadIdx.x == 1023) carry = before + inc;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x + 1; i <= n; i += 1024) {
+        const int v = ws.into[i];
+        ws.num[i] = v > 0 ? v : 0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x + 1; i <= n; i += 1024) {
+        const int v = ws.into[i];
+        if (v < 0) ws.num[i] = ws.num[-v];
+    }
+    if (threadIdx.x == 0) *n_out = carry;
+}
+
+__global__ void __launch_bounds__(CL_T) k_clean_relabel(const int32_t* labels, int64_t npx, const int32_t* n_dev,
+                                                        int32_t max_obj, CleanWs ws, int32_t* out) {
+    const int n = clean_n(n_dev, max_obj);
+    for (int64_t p = (int64_t)blockIdx.x * CL_T + threadIdx.x; p < npx; p += (int64_t)gridDim.x * CL_T) {
+        const int l = __ldg(labels + p);
+        out[p] = (l <= 0 || l > n) ? 0 : ws.num[l];
+    }
+}
+
+}  // namespace ipp
+
+using namespace ipp;
+
+static size_t a256c(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t ipp_clean_ws_carve(int32_t max_obj, void* base, CleanWs* w) {
+    const size_t n = (size_t)max_obj + 1;
+    const size_t sz[] = {n * 8, n * 16, n * 16, n * 16, n * 24, n * 48, n * 16, n * 8, n * 16, n * 4, n * 4};
+    size_t off[11], o = 0;
+    for (int k = 0; k < 11; k++) { off[k] = o; o += a256c(sz[k]); }
+    if (base && w) {
+        unsigned char* b = static_cast<unsigned char*>(base);
+        w->pkey = (unsigned long long*)(b + off[0]);
+        w->sw = (long long*)(b + off[1]);
+        w->swx = (long long*)(b + off[2]);
+        w->swy = (long long*)(b + off[3]);
+        w->cnt = (long long*)(b + off[4]);
+        w->mom = (long long*)(b + off[5]);
+        w->geo = (float4*)(b + off[6]);
+        w->blo = (float2*)(b + off[7]);
+        w->ell = (float4*)(b + off[8]);
+        w->into = (int32_t*)(b + off[9]);
+        w->num = (int32_t*)(b + off[10]);
+    }
+    return o;
+}
+
+size_t ipp_clean_ws_bytes(int32_t max_obj) { return ipp_clean_ws_carve(max_obj, nullptr, nullptr); }
+
+int ipp_launch_clean(const float* sub, int64_t pitch, const int32_t* labels, int64_t W, int64_t H,
+                     const int32_t* n_dev, int32_t max_obj, const float* thr_map, const float* mesh_rms, int nx,
+                     int ny, float mesh_w, float mesh_h, float k, float thresh_abs, float beta, int32_t* out,
+                     int32_t* n_out, void* ws, cudaStream_t s) {
+    CleanWs w;
+    ipp_clean_ws_carve(max_obj, ws, &w);
+    // the accumulators start at zero (peak keys, sums, counts, moments)
+    const size_t acc = (size_t)((unsigned char*)w.geo - (unsigned char*)ws);
+    if (cudaMemsetAsync(ws, 0, acc, s) != cudaSuccess) return ipp_check_launch("clean memset");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t npx = W * H;
+    const unsigned pg = (unsigned)std::min<int64_t>((npx + CL_T - 1) / CL_T, (int64_t)std::max(sms, 1) * 16);
+    const unsigned og = (unsigned)std::max<int64_t>(1, ((int64_t)max_obj + CL_T) / CL_T);
+    const float a2 = (float)(2.0 * std::log(2.0) / (std::pow(2.0, 1.0 / beta) - 1.0));
+    k_clean_pix_a<<<pg, CL_T, 0, s>>>(sub, pitch, labels, W, H, n_dev, max_obj, w);
+    if (int e = ipp_check_launch("k_clean_pix_a")) return e;
+    k_clean_obj_a<<<og, CL_T, 0, s>>>(n_dev, max_obj, w);
+    if (int e = ipp_check_launch("k_clean_obj_a")) return e;
+    k_clean_pix_b<<<pg, CL_T, 0, s>>>(sub, pitch, labels, W, H, n_dev, max_obj, w);
+    if (int e = ipp_check_launch("k_clean_pix_b")) return e;
+    const CleanThr T{thr_map, mesh_rms, nx, ny, mesh_w, mesh_h, k, thresh_abs, W};
+    k_clean_obj_b<<<og, CL_T, 0, s>>>(n_dev, max_obj, w, T, 1.0f / a2);
+    if (int e = ipp_check_launch("k_clean_obj_b")) return e;
+    k_clean_test<<<og, CL_T, 0, s>>>(n_dev, max_obj, w, W, beta);
+    if (int e = ipp_check_launch("k_clean_test")) return e;
+    k_clean_number<<<1, 1024, 0, s>>>(n_dev, max_obj, w, n_out);
+    if (int e = ipp_check_launch("k_clean_number")) return e;
+    k_clean_relabel<<<pg, CL_T, 0, s>>>(labels, npx, n_dev, max_obj, w, out);
+    return ipp_check_launch("k_clean_relabel");
+}

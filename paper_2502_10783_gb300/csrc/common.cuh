@@ -105,6 +105,30 @@ IPP_D df df_from_i64(long long i) {
     return df_add_f(two_sum(c2 * 4398046511104.0f, c1 * 2097152.0f), c0);
 }
 
+// A float as two integers, v = c 2^-8 + f 2^-40 exactly for |v| >= 2^-17 (its
+// bits below 2^-40 are dropped otherwise): c = rint(v 2^8), and f the residual
+// v - c 2^-8 (|.| <= 2^-9, formed exactly in FP32) in units of 2^-40.  Sums of
+// such pairs are exact and order-independent; the c sums stay in range while
+// the totals stay below ~3.6e16 (values, or values times pixel coordinates).
+IPP_D void fx_split(float v, long long out[2]) {
+    const long long c = __float2ll_rn(v * 256.0f);
+    const float rsd = fabsf(v) < 65536.0f ? v - (float)c * (1.0f / 256.0f) : 0.0f;
+    out[0] = c;
+    out[1] = __float2ll_rn(rsd * 1099511627776.0f);
+}
+// the pair's value in double-float
+IPP_D df fx_value(const long long* p) {
+    const df a = df_from_i64(__ldcg(p)), b = df_from_i64(__ldcg(p + 1));
+    return df_add(df_scale(a, 1.0f / 256.0f), df_scale(b, 1.0f / 1099511627776.0f));
+}
+// add a float's pair to an integer-pair accumulator (global or shared memory)
+IPP_D void fx_atomic_add(long long* acc, float v) {
+    long long t[2];
+    fx_split(v, t);
+    atomicAdd(reinterpret_cast<unsigned long long*>(acc), (unsigned long long)t[0]);
+    atomicAdd(reinterpret_cast<unsigned long long*>(acc + 1), (unsigned long long)t[1]);
+}
+
 // Keys (1981) cubic-convolution weights, a = -1/2, for fractional offset s in
 // [0, 1): nodes at distances 1 + s, s, 1 - s, 2 - s.
 IPP_D void keys_weights(float s, float w[4]) {

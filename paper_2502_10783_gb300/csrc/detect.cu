@@ -111,22 +111,7 @@ using TileFull = TileShared<T_RCAP, KCAP_FULL>;
 
 constexpr int BORDER_BIT = 1 << 30;
 
-// A float as two integers, v = c 2^-8 + f 2^-40 exactly for |v| >= 2^-17 (its
-// bits below 2^-40 are dropped otherwise): c = rint(v 2^8), and f the residual
-// v - c 2^-8 (|.| <= 2^-9, formed exactly in FP32) in units of 2^-40.  Sums of
-// such pairs are exact and order-independent; the c sums stay in range while
-// the totals stay below ~3.6e16 (values, or values times pixel coordinates).
-__device__ __forceinline__ void fx_split(float v, long long out[2]) {
-    const long long c = __float2ll_rn(v * 256.0f);
-    const float rsd = fabsf(v) < 65536.0f ? v - (float)c * (1.0f / 256.0f) : 0.0f;
-    out[0] = c;
-    out[1] = __float2ll_rn(rsd * 1099511627776.0f);
-}
-// the pair's value in double-float
-__device__ __forceinline__ df fx_value(const long long* p) {
-    const df a = df_from_i64(__ldcg(p)), b = df_from_i64(__ldcg(p + 1));
-    return df_add(df_scale(a, 1.0f / 256.0f), df_scale(b, 1.0f / 1099511627776.0f));
-}
+
 static_assert(T_TH * T_WPR <= T_THREADS, "one thread per mask word");
 
 __device__ __forceinline__ int rfind(const int32_t* P, int x) {

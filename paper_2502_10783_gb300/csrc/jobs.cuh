@@ -154,6 +154,13 @@ struct FitJob {
 }  // namespace ipp
 
 int ipp_launch_mesh_stats(const ipp::MeshJob& J, cudaStream_t s);
+size_t ipp_spline_ws_bytes(int nx, int ny);
+int ipp_launch_bg_subtract_spline(const ipp::SubJob& J, void* ws, cudaStream_t s);
+size_t ipp_clean_ws_bytes(int32_t max_obj);
+int ipp_launch_clean(const float* sub, int64_t pitch, const int32_t* labels, int64_t W, int64_t H,
+                     const int32_t* n_dev, int32_t max_obj, const float* thr_map, const float* mesh_rms, int nx,
+                     int ny, float mesh_w, float mesh_h, float k, float thresh_abs, float beta, int32_t* out,
+                     int32_t* n_out, void* ws, cudaStream_t s);
 int ipp_launch_mesh_filter(const float* raw_bkg, const float* raw_rms, float* fill_bkg, float* fill_rms,
                            int nx, int ny, int fw, int fh, float* out_bkg, float* out_rms,
                            int32_t* status_dev, cudaStream_t s);
