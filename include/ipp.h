@@ -390,13 +390,15 @@ int ipp_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t H, i
  *     r^2 = (y2 dx^2 - 2 xy dx dy + x2 dy^2) / (x2 y2 - xy^2),
  *     a^2 = 2 ln 2 / (2^(1/beta) - 1);
  *   object i merges when its peak less the sum of the models of every brighter
- *     object (larger peak; equal peaks: smaller label), summed in label order,
- *     at its peak pixel is below the detection threshold there; the target is
+ *     object (larger peak; equal peaks: smaller label) at its peak pixel is
+ *     below the detection threshold there; the target is
  *     the brighter object whose model is largest there (ties: smaller label),
  *     merges followed to a kept object; kept objects are renumbered 1.. in label
  *     order (a label with no pixel is no object and takes no number).
  * The sums over pixels are exact (integer accumulators), so the result does not
- * depend on the order of the atomics; the models and the test are FP32.
+ * depend on the order of the atomics; the models are FP32, summed with a
+ * compensated (two-sum) accumulator in a fixed order (brightest first), so the
+ * result is the same from run to run.
  * Processes labels 1..min(*n_obj_dev, max_obj); other labels map to 0.
  *   labels      device int32 map (pitch W), e.g. the output of ipp_deblend
  *   thr_map     nullable device float threshold map (pitch W); when NULL the
@@ -408,11 +410,12 @@ int ipp_deblend(const float* sub, const int32_t* labels, int64_t W, int64_t H, i
  *   out_labels  device int32[W*H] (pitch W): the cleaned map, 0 = background
  *   n_out_dev   device int32[1]: the number of kept objects
  *   ws          device workspace of ipp_clean_workspace_size(max_obj) bytes
- *               (about 200 B per object), 256-byte aligned
+ *               (about 200 + 16 P / 4096 B per object, P the power of two at
+ *               or above max(max_obj, 2048)), 256-byte aligned
  * Sizes: frames below 2^31 pixels, narrower than 65536 pixels, objects below
  * 2^24 pixels (range of the exact sums).
- * Errors: INVALID_ARG for NULL inputs, beta <= 0, a small or misaligned
- * workspace, or sizes out of range.
+ * Errors: INVALID_ARG for NULL inputs, beta <= 0, max_obj above 2^24, a small
+ * or misaligned workspace, or sizes out of range.
  */
 size_t ipp_clean_workspace_size(int32_t max_obj);
 int ipp_clean(const float* sub, const int32_t* labels, int64_t W, int64_t H, int64_t pitch,

@@ -301,7 +301,7 @@ extern "C" int ipp_deblend(const float* sub, const int32_t* labels, int64_t W, i
 
 // ---- cleaning -------------------------------------------------------------------------
 extern "C" size_t ipp_clean_workspace_size(int32_t max_obj) {
-    if (max_obj < 0) return 0;
+    if (max_obj < 0 || max_obj > (1 << 24)) return 0;
     return ipp_clean_ws_bytes(max_obj);
 }
 
@@ -312,7 +312,7 @@ extern "C" int ipp_clean(const float* sub, const int32_t* labels, int64_t W, int
     if (int e = check_frame(sub, IPP_F32, W, H, pitch, nullptr)) return e;
     REQUIRE(labels && n_obj_dev && out_labels && n_out_dev && ws && dp, "NULL pointer");
     REQUIRE(beta > 0.f && std::isfinite(beta), "beta must be > 0");
-    REQUIRE(max_obj >= 0, "max_obj < 0");
+    REQUIRE(max_obj >= 0 && max_obj <= (1 << 24), "max_obj outside 0..2^24");
     REQUIRE(W * H < (int64_t(1) << 31) && W < 65536, "cleaning needs a frame below 2^31 pixels, W < 65536");
     REQUIRE(((uintptr_t)ws & 255) == 0, "workspace not 256-byte aligned");
     REQUIRE(ws_bytes >= ipp_clean_ws_bytes(max_obj), "workspace too small");

@@ -17,15 +17,20 @@
 //
 // Kernels: per-pixel statistics with atomics (the peak as one 64-bit key; the
 // weighted sums as exact integer pairs, so the barycentres do not depend on the
-// order of the adds), per-object moments, the all-pairs test (a thread per
-// object, the other objects staged through shared memory in label order, as
-// the definition sums them), merge targets followed to their roots, a
-// label-order scan and the relabelled map.
+// order of the adds), per-object moments, a bitonic sort of the objects by
+// brightness (so that the objects brighter than one are a prefix), the test
+// tiled over (object, chunk of brighter objects) blocks with compensated
+// partial sums combined in chunk order, merge targets followed to their roots,
+// a label-order scan and the relabelled map.
 #include "jobs.cuh"
 
 namespace ipp {
 
 constexpr int CL_T = 256;
+
+// one chunk's share of the test of one object: compensated sum of the models,
+// the largest model and its label
+struct __align__(16) CleanPart { float s_hi, s_lo, best; int bj; };
 
 // per-object workspace (arrays of max_obj + 1 entries; index = label)
 struct CleanWs {
@@ -40,6 +45,9 @@ struct CleanWs {
     float4* ell;                // y2 / (det a^2), -2 xy / (det a^2), x2 / (det a^2), threshold at the peak
     int32_t* into;              // merge target
     int32_t* num;               // new label of a kept object
+    unsigned long long* skey;   // [P] brightness sort keys
+    CleanPart* part;            // [nchunk][P] per-chunk partials of the test
+    int P;                      // sort size (a power of two >= max_obj, >= 2048)
 };
 
 // where the detection threshold comes from: a map (pitch W), else the mesh rms
@@ -188,47 +196,150 @@ __global__ void __launch_bounds__(CL_T) k_clean_obj_b(const int32_t* n_dev, int3
     }
 }
 
-// the test of object i against every brighter object (a thread per object,
-// the objects j = 1..n staged through shared memory in label order)
-__global__ void __launch_bounds__(CL_T) k_clean_test(const int32_t* n_dev, int32_t max_obj, CleanWs ws, int64_t W,
-                                                     float beta) {
-    __shared__ float4 sg[CL_T], se[CL_T];
-    __shared__ float2 sl[CL_T];
+// ---- brightness order ------------------------------------------------------
+// Sort key of label l: (~fkey(peak) << 32) | l, so that ascending keys run from
+// the brightest object down, equal peaks by label -- the "brighter" relation of
+// the test.  Empty labels and padding take the largest key and sort last.
+// Bitonic sort of P = 2^m keys: 2048-key blocks in shared memory, the strides
+// of 2048 and more in global passes.
+constexpr int BS_T = 1024, BS_N = 2 * BS_T;
+
+__global__ void __launch_bounds__(CL_T) k_clean_keys(const int32_t* n_dev, int32_t max_obj, CleanWs ws, int P) {
     const int n = clean_n(n_dev, max_obj);
-    const int i = blockIdx.x * CL_T + threadIdx.x + 1;
-    const bool act = i <= n;
-    float4 gi = act ? ws.geo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const bool valid = act && gi.w > 0.f;
-    float px = 0.f, py = 0.f;
-    if (valid) {
-        const uint32_t pix = ~(uint32_t)(ws.pkey[i] & 0xffffffffu);
-        py = (float)(pix / (uint32_t)W);
-        px = (float)(pix - (uint32_t)py * (uint32_t)W);
+    for (int r = blockIdx.x * CL_T + threadIdx.x; r < P; r += gridDim.x * CL_T) {
+        const int l = r + 1;
+        unsigned long long k = ~0ull;
+        if (l <= n && ws.geo[l].w > 0.f)
+            k = ((unsigned long long)(~fkey(ws.geo[l].z)) << 32) | (unsigned long long)(uint32_t)l;
+        ws.skey[r] = k;
     }
-    float sum = 0.f, best = -1.f;
-    int bj = -1;
-    const bool unit = beta == 1.0f;
-    for (int j0 = 1; j0 <= n; j0 += CL_T) {
-        __syncthreads();
-        const int jj = j0 + threadIdx.x;
-        if (jj <= n) { sg[threadIdx.x] = ws.geo[jj]; se[threadIdx.x] = ws.ell[jj]; sl[threadIdx.x] = ws.blo[jj]; }
-        __syncthreads();
-        if (!valid) continue;
-        const int m = min(CL_T, n - j0 + 1);
-        for (int t = 0; t < m; t++) {
-            const int j = j0 + t;
-            const float4 g = sg[t];
-            if (j == i || !(g.w > 0.f)) continue;
-            if (!(g.z > gi.z || (g.z == gi.z && j < i))) continue;
-            const float4 e = se[t];
-            const float dx = (px - g.x) - sl[t].x, dy = (py - g.y) - sl[t].y;
-            const float q = fmaf(e.x * dx, dx, fmaf(e.y * dx, dy, e.z * dy * dy));
-            const float mv = unit ? g.z / (1.0f + q) : g.z * expf(-beta * log1pf(q));
-            sum += mv;
-            if (mv > best) { best = mv; bj = j; }
+}
+
+__device__ __forceinline__ void bitonic_cas(unsigned long long& a, unsigned long long& b, bool up) {
+    if ((a > b) == up) { const unsigned long long t = a; a = b; b = t; }
+}
+
+// k in [k_lo, k_hi] (powers of two), strides below BS_N only; k_lo = 2 sorts the
+// block from scratch, k_lo = k_hi finishes one merge of size k
+__global__ void __launch_bounds__(BS_T) k_bitonic_local(unsigned long long* keys, int k_lo, int k_hi) {
+    __shared__ unsigned long long sk[BS_N];
+    const int base = blockIdx.x * BS_N;
+    sk[threadIdx.x] = keys[base + threadIdx.x];
+    sk[threadIdx.x + BS_T] = keys[base + threadIdx.x + BS_T];
+    __syncthreads();
+    for (int k = k_lo; k <= k_hi; k <<= 1) {
+        for (int j = min(k >> 1, BS_N >> 1); j > 0; j >>= 1) {
+            const int t = threadIdx.x;
+            const int i = 2 * t - (t & (j - 1));   // the lower element of this thread's pair
+            const bool up = ((base + i) & k) == 0;
+            bitonic_cas(sk[i], sk[i + j], up);
+            __syncthreads();
         }
     }
-    if (act) ws.into[i] = (valid && bj > 0 && gi.z - sum < ws.ell[i].w) ? bj : i;
+    keys[base + threadIdx.x] = sk[threadIdx.x];
+    keys[base + threadIdx.x + BS_T] = sk[threadIdx.x + BS_T];
+}
+
+__global__ void __launch_bounds__(CL_T) k_bitonic_global(unsigned long long* keys, int P, int k, int j) {
+    const int t = blockIdx.x * CL_T + threadIdx.x;
+    if (t >= P / 2) return;
+    const int i = 2 * t - (t & (j - 1));
+    const bool up = (i & k) == 0;
+    unsigned long long a = keys[i], b = keys[i + j];
+    if ((a > b) == up) { keys[i] = b; keys[i + j] = a; }
+}
+
+// ---- the test ----------------------------------------------------------------
+// In brightness order the objects brighter than the one of rank r are the ranks
+// 0..r-1.  Block (bi, bc): ranks [256 bi, 256 bi + 256) against the ranks of chunk
+// bc ([CL_JC bc, CL_JC (bc + 1))), staged through shared memory 256 at a time.
+// Each thread sums its models in rank order with a compensated (two-sum) FP32
+// accumulator and keeps the largest model (ties: the smaller label); the chunks'
+// partials are combined in chunk order by k_clean_decide, so the result does not
+// depend on the scheduling.
+constexpr int CL_JC = 4096;
+
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    const float t = hi + v;
+    const float bp = t - hi;
+    lo += (hi - (t - bp)) + (v - bp);
+    hi = t;
+}
+
+__global__ void __launch_bounds__(CL_T) k_clean_pairs(const int32_t* n_dev, int32_t max_obj, CleanWs ws, int64_t W,
+                                                      float beta, int nchunk) {
+    __shared__ float4 sg[CL_T], se[CL_T];
+    __shared__ float2 sl[CL_T];
+    __shared__ int sb[CL_T];
+    const int n = clean_n(n_dev, max_obj);
+    const int r0 = blockIdx.x * CL_T, c0 = blockIdx.y * CL_JC;
+    if (r0 >= n || c0 >= min(n, r0 + CL_T)) return;     // nothing brighter here
+    const int r = r0 + threadIdx.x;
+    const unsigned long long key = r < n ? ws.skey[r] : ~0ull;
+    const bool valid = key != ~0ull;
+    const int li = valid ? (int)(uint32_t)key : 0;
+    float px = 0.f, py = 0.f;
+    if (valid) {
+        const uint32_t pix = ~(uint32_t)(ws.pkey[li] & 0xffffffffu);
+        const uint32_t yy = pix / (uint32_t)W;
+        py = (float)yy;
+        px = (float)(pix - yy * (uint32_t)W);
+    }
+    float hi = 0.f, lo = 0.f, best = -1.f;
+    int bj = -1;
+    const bool unit = beta == 1.0f;
+    const int c1 = min(min(c0 + CL_JC, n), r0 + CL_T);
+    const int lim = valid ? min(c1, r) : c0;              // ranks c0..lim-1 are brighter than r
+    for (int t0 = c0; t0 < c1; t0 += CL_T) {
+        __syncthreads();
+        const int jr = t0 + threadIdx.x;
+        if (jr < c1) {
+            const unsigned long long kj = ws.skey[jr];
+            const int lj = kj != ~0ull ? (int)(uint32_t)kj : 0;
+            sb[threadIdx.x] = lj;
+            if (lj > 0) { sg[threadIdx.x] = ws.geo[lj]; se[threadIdx.x] = ws.ell[lj]; sl[threadIdx.x] = ws.blo[lj]; }
+        }
+        __syncthreads();
+        const int m = min(CL_T, lim - t0);
+        for (int t = 0; t < m; t++) {
+            const float4 g = sg[t], e = se[t];
+            const float2 o = sl[t];
+            const float dx = (px - g.x) - o.x, dy = (py - g.y) - o.y;
+            const float q = fmaf(e.x * dx, dx, fmaf(e.y * dx, dy, e.z * dy * dy));
+            const float mv = unit ? __fdividef(g.z, 1.0f + q) : g.z * expf(-beta * log1pf(q));
+            two_sum_acc(hi, lo, mv);
+            const int lj = sb[t];
+            if (mv > best || (mv == best && lj < bj)) { best = mv; bj = lj; }
+        }
+    }
+    if (r < n) ws.part[(size_t)blockIdx.y * ws.P + r] = CleanPart{hi, lo, best, bj};
+}
+
+// per rank: the chunks' partials in chunk order, the decision and the target
+__global__ void __launch_bounds__(CL_T) k_clean_decide(const int32_t* n_dev, int32_t max_obj, CleanWs ws) {
+    const int n = clean_n(n_dev, max_obj);
+    for (int r = blockIdx.x * CL_T + threadIdx.x; r < n; r += gridDim.x * CL_T) {
+        const unsigned long long key = ws.skey[r];
+        if (key == ~0ull) continue;
+        const int li = (int)(uint32_t)key;
+        float hi = 0.f, lo = 0.f, best = -1.f;
+        int bj = -1;
+        for (int c = 0; c * CL_JC < r; c++) {
+            const CleanPart p = ws.part[(size_t)c * ws.P + r];
+            two_sum_acc(hi, lo, p.s_hi);
+            lo += p.s_lo;
+            if (p.bj > 0 && (p.best > best || (p.best == best && p.bj < bj))) { best = p.best; bj = p.bj; }
+        }
+        const float sum = hi + lo;
+        const float4 g = ws.geo[li];
+        ws.into[li] = (bj > 0 && g.z - sum < ws.ell[li].w) ? bj : li;
+    }
+}
+
+__global__ void __launch_bounds__(CL_T) k_clean_into_init(const int32_t* n_dev, int32_t max_obj, CleanWs ws) {
+    const int n = clean_n(n_dev, max_obj);
+    for (int l = blockIdx.x * CL_T + threadIdx.x; l <= n; l += gridDim.x * CL_T) ws.into[l] = l;
 }
 
 // merge targets followed to a kept object (each target is strictly brighter, so
@@ -294,11 +405,21 @@ using namespace ipp;
 
 static size_t a256c(size_t x) { return (x + 255) & ~(size_t)255; }
 
+static int clean_sort_size(int32_t max_obj) {
+    int P = BS_N;
+    while (P < max_obj) P <<= 1;
+    return P;
+}
+
 static size_t ipp_clean_ws_carve(int32_t max_obj, void* base, CleanWs* w) {
     const size_t n = (size_t)max_obj + 1;
-    const size_t sz[] = {n * 8, n * 16, n * 16, n * 16, n * 24, n * 48, n * 16, n * 8, n * 16, n * 4, n * 4};
-    size_t off[11], o = 0;
-    for (int k = 0; k < 11; k++) { off[k] = o; o += a256c(sz[k]); }
+    const int P = clean_sort_size(max_obj);
+    const size_t nchunk = ((size_t)P + CL_JC - 1) / CL_JC;
+    const size_t sz[] = {n * 8, n * 16, n * 16, n * 16, n * 24, n * 48, n * 16, n * 8, n * 16, n * 4, n * 4,
+                         (size_t)P * 8, nchunk * P * sizeof(CleanPart)};
+    constexpr int NA = sizeof(sz) / sizeof(sz[0]);
+    size_t off[NA], o = 0;
+    for (int k = 0; k < NA; k++) { off[k] = o; o += a256c(sz[k]); }
     if (base && w) {
         unsigned char* b = static_cast<unsigned char*>(base);
         w->pkey = (unsigned long long*)(b + off[0]);
@@ -312,6 +433,9 @@ static size_t ipp_clean_ws_carve(int32_t max_obj, void* base, CleanWs* w) {
         w->ell = (float4*)(b + off[8]);
         w->into = (int32_t*)(b + off[9]);
         w->num = (int32_t*)(b + off[10]);
+        w->skey = (unsigned long long*)(b + off[11]);
+        w->part = (CleanPart*)(b + off[12]);
+        w->P = P;
     }
     return o;
 }
@@ -343,8 +467,28 @@ int ipp_launch_clean(const float* sub, int64_t pitch, const int32_t* labels, int
     const CleanThr T{thr_map, mesh_rms, nx, ny, mesh_w, mesh_h, k, thresh_abs, W};
     k_clean_obj_b<<<og, CL_T, 0, s>>>(n_dev, max_obj, w, T, 1.0f / a2);
     if (int e = ipp_check_launch("k_clean_obj_b")) return e;
-    k_clean_test<<<og, CL_T, 0, s>>>(n_dev, max_obj, w, W, beta);
-    if (int e = ipp_check_launch("k_clean_test")) return e;
+    k_clean_into_init<<<og, CL_T, 0, s>>>(n_dev, max_obj, w);
+    if (int e = ipp_check_launch("k_clean_into_init")) return e;
+    // brightness order: keys, 2048-key blocks sorted in shared memory, then the
+    // merges of 4096 keys and more
+    const int P = w.P;
+    k_clean_keys<<<(unsigned)(P / CL_T), CL_T, 0, s>>>(n_dev, max_obj, w, P);
+    if (int e = ipp_check_launch("k_clean_keys")) return e;
+    k_bitonic_local<<<(unsigned)(P / BS_N), BS_T, 0, s>>>(w.skey, 2, BS_N);
+    if (int e = ipp_check_launch("k_bitonic_local")) return e;
+    for (int kk = 2 * BS_N; kk <= P; kk <<= 1) {
+        for (int j = kk >> 1; j >= BS_N; j >>= 1) {
+            k_bitonic_global<<<(unsigned)(P / 2 / CL_T), CL_T, 0, s>>>(w.skey, P, kk, j);
+            if (int e = ipp_check_launch("k_bitonic_global")) return e;
+        }
+        k_bitonic_local<<<(unsigned)(P / BS_N), BS_T, 0, s>>>(w.skey, kk, kk);
+        if (int e = ipp_check_launch("k_bitonic_local")) return e;
+    }
+    const int nchunk = (P + CL_JC - 1) / CL_JC;
+    k_clean_pairs<<<dim3((unsigned)(P / CL_T), (unsigned)nchunk), CL_T, 0, s>>>(n_dev, max_obj, w, W, beta, nchunk);
+    if (int e = ipp_check_launch("k_clean_pairs")) return e;
+    k_clean_decide<<<og, CL_T, 0, s>>>(n_dev, max_obj, w);
+    if (int e = ipp_check_launch("k_clean_decide")) return e;
     k_clean_number<<<1, 1024, 0, s>>>(n_dev, max_obj, w, n_out);
     if (int e = ipp_check_launch("k_clean_number")) return e;
     k_clean_relabel<<<pg, CL_T, 0, s>>>(labels, npx, n_dev, max_obj, w, out);
