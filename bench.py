@@ -16,6 +16,7 @@ on a bounded 1024 x 1024 crop of the same field instead.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -531,6 +532,13 @@ def main():
     sub_ws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
     stages["sub_apply"] = timeit(
         lambda k: ipp.sub_apply(gin[k % 4], gin[(k + 1) % 4], sub_coef, out=gout[k % 4], ws=sub_ws))
+    # the fit of the same pair: 10 x 10 regions, 21 x 21 footprints, FP64 normal
+    # equations of the 49-function basis (297 unknowns) and their Cholesky solve
+    fit_ws = torch.empty(ipp.load().ipp_sub_fit_workspace_size(
+        100, 100, 10, 10, 3, np.array([6, 4, 2], np.int32).ctypes.data_as(ctypes.c_void_p), 2, 1),
+        dtype=torch.uint8, device=dev)
+    stages["sub_fit"] = timeit(lambda k: ipp.sub_fit(gin[k % 4], gin[(k + 1) % 4], ws=fit_ws), n=5)
+    sub_fit_status = int(ipp.sub_fit(gin[0], gin[1], ws=fit_ws)["status"].item())
     # image alignment of the subtracted frame onto a second exposure's pixel grid
     # (a widening): WCS mapping of a 32 px node grid, partial affine fit, bilinear
     # reprojection; same four rotating input/output pairs
@@ -569,7 +577,10 @@ def main():
     sub_flops = 2.0 * 441 * W * H + 2.0 * 49 * 441 * ((W + 20) // 21) * ((H + 20) // 21)
     subtraction = {"ms": stages["sub_apply"], "achieved_tflops": sub_flops / (stages["sub_apply"] / 1e3) / 1e12,
                    "flops_per_call": sub_flops, "kernels": "k_sub_basis + k_sub_apply (one block per 21 x 21 tile)",
-                   "workload": "survey_4k subtracted frame against a copy, 21 x 21 kernel, 49 basis functions"}
+                   "workload": "survey_4k subtracted frame against a copy, 21 x 21 kernel, 49 basis functions",
+                   "fit_ms": stages["sub_fit"], "fit_status": sub_fit_status,
+                   "fit_kernels": "k_sub_stamps + k_sub_compact + k_sub_conv + k_sub_gram + k_sub_assemble + "
+                                  "k_sub_chol (FP64; 10 x 10 regions, 297 unknowns)"}
     gb = 8 * W * H / (stages["reproject"] / 1e3) / 1e9
     align = {"ms": stages["align"], "reproject_ms": stages["reproject"], "reproject_bytes_per_px": 8,
              "reproject_achieved_gbs": gb, "reproject_frac_of_measured_hbm": gb / hbm,

@@ -610,6 +610,58 @@ int ipp_sub_apply(const float* I, const float* R, int64_t W, int64_t H, int64_t 
                   int64_t out_pitch, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * The fit of image subtraction (Sec. 2.2.4, Eqs. 8-10, HOTPANTS-style readings;
+ * the model and basis as ipp_sub_apply's, sig in FP64 here):
+ *   ipp_sub_stamps  candidate stamps: the frame is cut into nsx x nsy regions
+ *     (region (sx, sy) spans x in [sx W / nsx, (sx + 1) W / nsx), likewise y); in
+ *     each, med and MAD are the median (Eq. 1's mean of the middle pair for an
+ *     even count) of the template's finite pixels and of their FP64 |R - med|;
+ *     the candidate is the brightest template pixel (first in raster order among
+ *     equals) whose footprint (2 fh + 1)^2 in I and support (2 (fh + hw) + 1)^2
+ *     in R lie inside the frame and are finite, kept when R > med + nsig 1.4826
+ *     MAD (FP64).  Exact: the same candidates as a sequential evaluation.
+ *     cx, cy: device int32[nsx * nsy], the candidates in region order (row-major
+ *     over the regions); n_dev: device int32[1], their count.
+ *   ipp_sub_normal  the normal equations of the unweighted least-squares fit over
+ *     every footprint pixel of candidates 0 .. min(*n_dev, max_c) - 1: unknowns
+ *     c[n * ns + s] (kernel) then d[b] (background), design row of a pixel
+ *     [C_n P_s(candidate centre)] then [-P_b(pixel)], C_n = R (x) K_n, target I.
+ *     FP64 throughout (the scaled normal matrix has condition numbers ~1e11, so
+ *     FP32 entries would move the fitted model by percents); the convolutions
+ *     use the basis' separability.  A candidate whose support leaves the frame
+ *     contributes nothing.  AtA: device double[np * np] (full, symmetric), Atb:
+ *     device double[np], np = nb * ns + nb_bg.
+ *   ipp_sub_solve   Cholesky solve of AtA x = Atb in FP64, in place (AtA takes
+ *     L, Atb the solution); coef64 (double) and coef (float, the input of
+ *     ipp_sub_apply) receive the solution when not NULL; *status_dev = 0, or 1
+ *     when a pivot is not positive (no solution written).
+ *   ipp_sub_fit     the three in sequence on the frame's own candidates;
+ *     cx, cy, n_dev nullable (else the candidates are reported there).
+ * Workspace: ipp_sub_fit_workspace_size(max_c, nreg, ...) bytes, 256-byte
+ * aligned: max_c candidates (nsx * nsy for ipp_sub_fit, 0 for ipp_sub_stamps),
+ * nreg regions (nsx * nsy for ipp_sub_stamps and ipp_sub_fit, 0 for
+ * ipp_sub_normal).  Limits: nk 1..8, deg 0..8, sord 0..4, bord -1..4, frames
+ * below 2^31 pixels, at most 65536 regions; NOT_SUPPORTED when a footprint and
+ * basis need more shared memory than one block has (fh = hw = 10 with the
+ * 49-function basis takes 187 KB).
+ */
+size_t ipp_sub_fit_workspace_size(int32_t max_c, int32_t nreg, int32_t hw, int32_t fh, int32_t nk, const int32_t* deg,
+                                  int32_t sord, int32_t bord);
+int ipp_sub_stamps(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int32_t nsx, int32_t nsy,
+                   int32_t hw, int32_t fh, double nsig, int32_t* cx, int32_t* cy, int32_t* n_dev, void* ws,
+                   size_t ws_bytes, void* stream);
+int ipp_sub_normal(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, const int32_t* cx,
+                   const int32_t* cy, const int32_t* n_dev, int32_t max_c, int32_t hw, int32_t fh, int32_t nk,
+                   const double* sig, const int32_t* deg, int32_t sord, int32_t bord, double* AtA, double* Atb,
+                   void* ws, size_t ws_bytes, void* stream);
+int ipp_sub_solve(double* AtA, double* Atb, int32_t np, double* coef64, float* coef, int32_t* status_dev,
+                  void* stream);
+int ipp_sub_fit(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int32_t nsx, int32_t nsy,
+                double nsig, int32_t hw, int32_t fh, int32_t nk, const double* sig, const int32_t* deg, int32_t sord,
+                int32_t bord, double* coef64, float* coef, int32_t* cx, int32_t* cy, int32_t* n_dev,
+                int32_t* status_dev, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * ipp_stamp_cut -- S x S stamps of the subtracted frame around each source, the
  * input of the PSF fit (the paper fits no PSF; this cut is part of that
  * paper-silent reading of Sec. 2.2.5's photometry).  For source s < min(*n_src_dev,

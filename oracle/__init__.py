@@ -135,6 +135,7 @@ def lib():
             L.orc_affine_fit.argtypes = [vp, vp, vp, vp, i64, vp, vp]
             L.orc_reproject_affine.argtypes = [vp, i64, i64, vp, i64, i64, d, vp]
             L.orc_zscale.argtypes = [vp, i64, i64, i32, d, d, i32, vp, vp]
+            L.orc_chol_solve.argtypes = [vp, vp, i32]
             L.orc_clean.argtypes = [vp, vp, i64, i64, i64, vp, d, vp]
             L.orc_clean.restype = i64
             L.orc_clean_stats.argtypes = [vp, vp, i64, i64, i64] + [vp] * 7
@@ -590,3 +591,13 @@ def clean_stats(sub, labels, nobj):
                                  _p(out["cy"]), _p(out["x2"]), _p(out["y2"]), _p(out["xy"])) == 0
     out["peak_index"] = pidx
     return out
+
+
+def chol_solve(A, b):
+    """x with A x = b by the oracle's Cholesky (A symmetric positive definite);
+    ValueError when a pivot is not positive"""
+    A = np.array(A, np.float64, order="C", copy=True)
+    x = np.array(b, np.float64, copy=True)
+    if lib().orc_chol_solve(_p(A), _p(x), int(x.size)):
+        raise ValueError("not positive definite")
+    return x

@@ -1716,6 +1716,13 @@ static int chol_solve(double* A, double* b, int n) {
     return 0;
 }
 
+/* The Cholesky solve above as an entry point (A and b overwritten: L and x);
+ * ORC_INVALID_ARG when a pivot is not positive. */
+int orc_chol_solve(double* A, double* b, int32_t n) {
+    if (n < 1) return ORC_INVALID_ARG;
+    return chol_solve(A, b, n) ? ORC_INVALID_ARG : ORC_OK;
+}
+
 /* Normal equations of the fit: AtA (np x np, full, row-major) and Atb (np), the
  * unknowns ordered as the coefficients below; the design row of footprint pixel
  * p of candidate c is [C_n(p) P_s(c) for n, s] then [-P_b(p) for b], its target

@@ -24,7 +24,7 @@ from ._abi import (  # noqa: F401
     IppError, PSF_GAUSS, PSF_MOFFAT,
 )
 
-__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "deblend", "clean", "bg_subtract_spline", "stamp_cut", "Batch",
+__all__ = ["load", "bg_estimate", "bg_subtract", "detect_label", "centroid", "aperture_phot", "auto_phot", "deblend", "clean", "bg_subtract_spline", "sub_stamps", "sub_normal", "sub_solve", "sub_fit", "stamp_cut", "Batch",
            "gray_transform", "hist_equalize", "zscale", "sub_apply", "wcs_map", "affine_fit", "reproject_affine", "align",
            "extract", "Extractor", "psf_fit", "psf_model", "PSFModel", "BgConfig"]
 
@@ -323,6 +323,107 @@ def gray_transform(img, kind, lo, hi, a=1000.0, out=None):
         _ptr(img), W, H, img.stride(0), int(kind), float(lo), float(hi), float(a), _ptr(out), out.stride(0),
         _stream()))
     return out
+
+
+def _sub_basis_args(sig, deg, sord, bord):
+    sg = np.ascontiguousarray(sig, np.float64)
+    dg = np.ascontiguousarray(deg, np.int32)
+    nb = sum((int(d) + 1) * (int(d) + 2) // 2 for d in dg)
+    npar = nb * (sord + 1) * (sord + 2) // 2 + ((bord + 1) * (bord + 2) // 2 if bord >= 0 else 0)
+    return sg, dg, npar
+
+
+def _pair(img, tmpl):
+    _frame2d(img, "img")
+    _frame2d(tmpl, "tmpl")
+    if tmpl.shape != img.shape or tmpl.stride(0) != img.stride(0):
+        raise TypeError("img and tmpl must have the same shape and row pitch")
+
+
+def sub_stamps(img, tmpl, nsx=10, nsy=10, hw=10, fh=10, nsig=5.0, ws=None):
+    """Candidate stamp centres of the subtraction fit (ipp_sub_stamps): device
+    int32 cx, cy (nsx * nsy, the first n valid) and the device count n."""
+    L = load()
+    _pair(img, tmpl)
+    H, W = img.shape
+    dev = img.device
+    dg = np.zeros(1, np.int32)
+    need = L.ipp_sub_fit_workspace_size(0, nsx * nsy, int(hw), int(fh), 1, dg.ctypes.data_as(C.c_void_p), 0, -1)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    cx = torch.empty(nsx * nsy, dtype=torch.int32, device=dev)
+    cy = torch.empty_like(cx)
+    n = torch.empty(1, dtype=torch.int32, device=dev)
+    _abi.check("ipp_sub_stamps", L.ipp_sub_stamps(
+        _ptr(img), _ptr(tmpl), W, H, img.stride(0), int(nsx), int(nsy), int(hw), int(fh), float(nsig), _ptr(cx),
+        _ptr(cy), _ptr(n), _ptr(ws), ws.numel(), _stream()))
+    return cx, cy, n
+
+
+def sub_normal(img, tmpl, cx, cy, n, hw=10, fh=10, sig=(0.7, 1.5, 3.0), deg=(6, 4, 2), sord=2, bord=1, ws=None):
+    """Normal equations (AtA, Atb) of the subtraction fit over candidates
+    cx[:n], cy[:n] (ipp_sub_normal), FP64 device tensors."""
+    L = load()
+    _pair(img, tmpl)
+    H, W = img.shape
+    dev = img.device
+    sg, dg, npar = _sub_basis_args(sig, deg, sord, bord)
+    max_c = cx.numel()
+    need = L.ipp_sub_fit_workspace_size(max_c, 0, int(hw), int(fh), len(dg), dg.ctypes.data_as(C.c_void_p),
+                                        int(sord), int(bord))
+    if need == 0:
+        raise ValueError("bad basis description")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    AtA = torch.empty((npar, npar), dtype=torch.float64, device=dev)
+    Atb = torch.empty(npar, dtype=torch.float64, device=dev)
+    _abi.check("ipp_sub_normal", L.ipp_sub_normal(
+        _ptr(img), _ptr(tmpl), W, H, img.stride(0), _ptr(cx.contiguous()), _ptr(cy.contiguous()), _ptr(n), max_c,
+        int(hw), int(fh), len(dg), sg.ctypes.data_as(C.c_void_p), dg.ctypes.data_as(C.c_void_p), int(sord),
+        int(bord), _ptr(AtA), _ptr(Atb), _ptr(ws), ws.numel(), _stream()))
+    return AtA, Atb
+
+
+def sub_solve(AtA, Atb):
+    """Cholesky solve of the normal equations on the device (ipp_sub_solve);
+    overwrites AtA (L) and Atb; returns (coef64, coef32, status) device tensors."""
+    L = load()
+    npar = Atb.numel()
+    c64 = torch.empty(npar, dtype=torch.float64, device=Atb.device)
+    c32 = torch.empty(npar, dtype=torch.float32, device=Atb.device)
+    st = torch.empty(1, dtype=torch.int32, device=Atb.device)
+    _abi.check("ipp_sub_solve", L.ipp_sub_solve(_ptr(AtA), _ptr(Atb), npar, _ptr(c64), _ptr(c32), _ptr(st),
+                                                _stream()))
+    return c64, c32, st
+
+
+def sub_fit(img, tmpl, nsx=10, nsy=10, nsig=5.0, hw=10, fh=10, sig=(0.7, 1.5, 3.0), deg=(6, 4, 2), sord=2, bord=1,
+            ws=None):
+    """The subtraction fit on the device (ipp_sub_fit): dict of device tensors
+    coef64, coef (float, the input of sub_apply), cx, cy, n and status (0 =
+    solved, 1 = the normal matrix is not positive definite)."""
+    L = load()
+    _pair(img, tmpl)
+    H, W = img.shape
+    dev = img.device
+    sg, dg, npar = _sub_basis_args(sig, deg, sord, bord)
+    nreg = nsx * nsy
+    need = L.ipp_sub_fit_workspace_size(nreg, nreg, int(hw), int(fh), len(dg), dg.ctypes.data_as(C.c_void_p),
+                                        int(sord), int(bord))
+    if need == 0:
+        raise ValueError("bad basis description")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    o = dict(coef64=torch.empty(npar, dtype=torch.float64, device=dev),
+             coef=torch.empty(npar, dtype=torch.float32, device=dev),
+             cx=torch.empty(nreg, dtype=torch.int32, device=dev), cy=torch.empty(nreg, dtype=torch.int32, device=dev),
+             n=torch.empty(1, dtype=torch.int32, device=dev), status=torch.empty(1, dtype=torch.int32, device=dev))
+    _abi.check("ipp_sub_fit", L.ipp_sub_fit(
+        _ptr(img), _ptr(tmpl), W, H, img.stride(0), int(nsx), int(nsy), float(nsig), int(hw), int(fh), len(dg),
+        sg.ctypes.data_as(C.c_void_p), dg.ctypes.data_as(C.c_void_p), int(sord), int(bord), _ptr(o["coef64"]),
+        _ptr(o["coef"]), _ptr(o["cx"]), _ptr(o["cy"]), _ptr(o["n"]), _ptr(o["status"]), _ptr(ws), ws.numel(),
+        _stream()))
+    return o
 
 
 def sub_apply(img, tmpl, coef, hw=10, sig=(0.7, 1.5, 3.0), deg=(6, 4, 2), sord=2, bord=1, out=None, ws=None):

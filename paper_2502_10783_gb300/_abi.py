@@ -120,6 +120,13 @@ PROTOTYPES = {
     "ipp_zscale": ([vp, i64, i64, i64, C.POINTER(ZscaleParams), vp, vp, vp], i32),
     "ipp_sub_apply_workspace_size": ([i32, i32, vp], sz),
     "ipp_sub_apply": ([vp, vp, i64, i64, i64, i32, i32, vp, vp, vp, i32, i32, vp, i64, vp, sz, vp], i32),
+    "ipp_sub_fit_workspace_size": ([i32, i32, i32, i32, i32, vp, i32, i32], sz),
+    "ipp_sub_stamps": ([vp, vp, i64, i64, i64, i32, i32, i32, i32, C.c_double, vp, vp, vp, vp, sz, vp], i32),
+    "ipp_sub_normal": ([vp, vp, i64, i64, i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, i32, i32, vp, vp, vp, sz, vp],
+                       i32),
+    "ipp_sub_solve": ([vp, vp, i32, vp, vp, vp, vp], i32),
+    "ipp_sub_fit": ([vp, vp, i64, i64, i64, i32, i32, C.c_double, i32, i32, i32, vp, vp, i32, i32, vp, vp, vp, vp, vp,
+                     vp, vp, sz, vp], i32),
     "ipp_gray_transform": ([vp, i64, i64, i64, i32, f32, f32, f32, vp, i64, vp], i32),
     "ipp_hist_equalize_workspace_size": ([i32], sz),
     "ipp_hist_equalize": ([vp, i64, i64, i64, i32, vp, i64, vp, sz, vp], i32),

@@ -16,7 +16,7 @@ SRC = os.path.join(PKG, "csrc")
 INC = os.path.join(ROOT, "include")
 OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libipp.so")
-UNITS = ["bg", "detect", "phot", "psf", "api", "noalloc", "batch", "deblend", "gray", "align", "subtract", "spline", "clean"]
+UNITS = ["bg", "detect", "phot", "psf", "api", "noalloc", "batch", "deblend", "gray", "align", "subtract", "spline", "clean", "subfit"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC]
 

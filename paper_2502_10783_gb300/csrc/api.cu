@@ -367,6 +367,86 @@ extern "C" int ipp_sub_apply(const float* I, const float* R, int64_t W, int64_t 
                                 D, out_pitch, ws, (cudaStream_t)stream);
 }
 
+// ---- subtraction fit --------------------------------------------------------------------
+static int check_sub_fit_basis(int32_t hw, int32_t fh, int32_t nk, const double* sig, const int32_t* deg,
+                               int32_t sord, int32_t bord) {
+    REQUIRE(sig && deg, "NULL basis description");
+    REQUIRE(hw >= 0 && fh >= 0, "hw, fh must be >= 0");
+    REQUIRE(nk >= 1 && nk <= 8, "nk must be 1..8");
+    for (int k = 0; k < nk; k++)
+        REQUIRE(deg[k] >= 0 && deg[k] <= 8 && sig[k] > 0.0 && std::isfinite(sig[k]), "bad basis description");
+    REQUIRE(sord >= 0 && sord <= 4 && bord >= -1 && bord <= 4, "spatial order 0..4, background order -1..4");
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (ipp_subfit_smem(hw, fh, nk, deg, sord, bord) > (size_t)optin)
+        return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "footprint and basis need %zu B of shared memory (> %d)",
+                             ipp_subfit_smem(hw, fh, nk, deg, sord, bord), optin);
+    return IPP_OK;
+}
+
+extern "C" size_t ipp_sub_fit_workspace_size(int32_t max_c, int32_t nreg, int32_t hw, int32_t fh, int32_t nk,
+                                             const int32_t* deg, int32_t sord, int32_t bord) {
+    if (max_c < 0 || nreg < 0 || hw < 0 || fh < 0 || nk < 1 || nk > 8 || !deg || sord < 0 || sord > 4 ||
+        bord < -1 || bord > 4)
+        return 0;
+    for (int k = 0; k < nk; k++)
+        if (deg[k] < 0 || deg[k] > 8) return 0;
+    return ipp_subfit_ws_bytes(max_c, nreg, hw, fh, nk, deg, sord, bord);
+}
+
+extern "C" int ipp_sub_stamps(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int32_t nsx,
+                              int32_t nsy, int32_t hw, int32_t fh, double nsig, int32_t* cx, int32_t* cy,
+                              int32_t* n_dev, void* ws, size_t ws_bytes, void* stream) {
+    if (int e = check_frame(I, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(R && cx && cy && n_dev && ws, "NULL pointer");
+    REQUIRE(W * H < (int64_t(1) << 31), "frame of 2^31 pixels or more");
+    REQUIRE(nsx >= 1 && nsy >= 1 && (int64_t)nsx * nsy <= 65536, "regions: 1..65536");
+    REQUIRE(hw >= 0 && fh >= 0 && std::isfinite(nsig), "bad hw, fh or nsig");
+    REQUIRE(((uintptr_t)ws & 255) == 0 && ws_bytes >= (size_t)nsx * nsy * 8, "workspace too small or misaligned");
+    return ipp_launch_sub_stamps(I, R, W, H, pitch, nsx, nsy, hw, fh, nsig, cx, cy, n_dev, ws, (cudaStream_t)stream);
+}
+
+extern "C" int ipp_sub_normal(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, const int32_t* cx,
+                              const int32_t* cy, const int32_t* n_dev, int32_t max_c, int32_t hw, int32_t fh,
+                              int32_t nk, const double* sig, const int32_t* deg, int32_t sord, int32_t bord,
+                              double* AtA, double* Atb, void* ws, size_t ws_bytes, void* stream) {
+    if (int e = check_frame(I, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(R && cx && cy && n_dev && AtA && Atb && ws, "NULL pointer");
+    REQUIRE(max_c >= 0 && max_c <= 65536, "max_c must be 0..65536");
+    if (int e = check_sub_fit_basis(hw, fh, nk, sig, deg, sord, bord)) return e;
+    REQUIRE(((uintptr_t)ws & 255) == 0 && ws_bytes >= ipp_subfit_ws_bytes(max_c, 0, hw, fh, nk, deg, sord, bord),
+            "workspace too small or misaligned");
+    return ipp_launch_sub_normal(I, R, W, H, pitch, cx, cy, n_dev, max_c, 0, hw, fh, nk, sig, deg, sord, bord, AtA,
+                                 Atb, ws, (cudaStream_t)stream);
+}
+
+extern "C" int ipp_sub_solve(double* AtA, double* Atb, int32_t np, double* coef64, float* coef, int32_t* status_dev,
+                             void* stream) {
+    REQUIRE(AtA && Atb && status_dev, "NULL pointer");
+    REQUIRE(np >= 1 && np <= 8192, "np must be 1..8192");
+    return ipp_launch_sub_solve(AtA, Atb, np, coef64, coef, status_dev, (cudaStream_t)stream);
+}
+
+extern "C" int ipp_sub_fit(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int32_t nsx,
+                           int32_t nsy, double nsig, int32_t hw, int32_t fh, int32_t nk, const double* sig,
+                           const int32_t* deg, int32_t sord, int32_t bord, double* coef64, float* coef, int32_t* cx,
+                           int32_t* cy, int32_t* n_dev, int32_t* status_dev, void* ws, size_t ws_bytes,
+                           void* stream) {
+    if (int e = check_frame(I, IPP_F32, W, H, pitch, nullptr)) return e;
+    REQUIRE(R && status_dev && ws && (coef64 || coef), "NULL pointer");
+    REQUIRE(W * H < (int64_t(1) << 31), "frame of 2^31 pixels or more");
+    REQUIRE(nsx >= 1 && nsy >= 1 && (int64_t)nsx * nsy <= 65536, "regions: 1..65536");
+    REQUIRE(std::isfinite(nsig), "nsig not finite");
+    if (int e = check_sub_fit_basis(hw, fh, nk, sig, deg, sord, bord)) return e;
+    const int nreg = nsx * nsy;
+    REQUIRE(((uintptr_t)ws & 255) == 0 &&
+                ws_bytes >= ipp_subfit_ws_bytes(nreg, nreg, hw, fh, nk, deg, sord, bord),
+            "workspace too small or misaligned");
+    return ipp_launch_sub_fit(I, R, W, H, pitch, nsx, nsy, nsig, hw, fh, nk, sig, deg, sord, bord, coef64, coef, cx,
+                              cy, n_dev, status_dev, ws, (cudaStream_t)stream);
+}
+
 // ---- image alignment -------------------------------------------------------------------
 static int check_wcs(const ipp_wcs* w, bool need_inverse) {
     REQUIRE(w, "wcs NULL");

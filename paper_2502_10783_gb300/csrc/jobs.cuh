@@ -156,6 +156,21 @@ struct FitJob {
 int ipp_launch_mesh_stats(const ipp::MeshJob& J, cudaStream_t s);
 size_t ipp_spline_ws_bytes(int nx, int ny);
 int ipp_launch_bg_subtract_spline(const ipp::SubJob& J, void* ws, cudaStream_t s);
+size_t ipp_subfit_ws_bytes(int max_c, int nreg, int hw, int fh, int nk, const int32_t* deg, int sord, int bord);
+size_t ipp_subfit_smem(int hw, int fh, int nk, const int32_t* deg, int sord, int bord);
+int ipp_launch_sub_stamps(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int nsx, int nsy,
+                          int hw, int fh, double nsig, int32_t* cx, int32_t* cy, int32_t* n_dev, void* ws,
+                          cudaStream_t s);
+int ipp_launch_sub_normal(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, const int32_t* cx,
+                          const int32_t* cy, const int32_t* n_dev, int max_c, int nreg, int hw, int fh, int nk,
+                          const double* sig, const int32_t* deg, int sord, int bord, double* AtA, double* Atb,
+                          void* ws, cudaStream_t s);
+int ipp_launch_sub_solve(double* AtA, double* Atb, int np, double* coef64, float* coef, int32_t* status,
+                         cudaStream_t s);
+int ipp_launch_sub_fit(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int nsx, int nsy,
+                       double nsig, int hw, int fh, int nk, const double* sig, const int32_t* deg, int sord, int bord,
+                       double* coef64, float* coef, int32_t* cx_out, int32_t* cy_out, int32_t* n_out,
+                       int32_t* status, void* ws, cudaStream_t s);
 size_t ipp_clean_ws_bytes(int32_t max_obj);
 int ipp_launch_clean(const float* sub, int64_t pitch, const int32_t* labels, int64_t W, int64_t H,
                      const int32_t* n_dev, int32_t max_obj, const float* thr_map, const float* mesh_rms, int nx,

@@ -196,3 +196,15 @@ def test_normal_equations_match_an_explicit_design_matrix(orc):
     # and the fit solves them
     coef = orc.sub_fit(I, R, cx, cy, hw=hw, fh=fh, sig=sig, deg=deg, sord=sord, bord=bord)
     assert np.allclose(coef, np.linalg.lstsq(A, b, rcond=None)[0], rtol=1e-6, atol=1e-8)
+
+
+def test_chol_solve_against_lapack(orc):
+    """the oracle's Cholesky solve against LAPACK's (numpy) on a random SPD
+    system, and a matrix with a zero pivot is refused"""
+    rng = np.random.default_rng(12)
+    M = rng.normal(0, 1, (40, 40))
+    A = M @ M.T + 40 * np.eye(40)
+    b = rng.normal(0, 1, 40)
+    assert np.allclose(orc.chol_solve(A, b), np.linalg.solve(A, b), rtol=1e-12, atol=1e-14)
+    with pytest.raises(ValueError):
+        orc.chol_solve(np.zeros((3, 3)), np.ones(3))
