@@ -231,19 +231,34 @@ def batch_leg(ipp, synth, dev, n_frames, reps=5):
     tuner = ipp.Batch(frames, lanes=1, cfg=cfg, max_src=65536)
     best, lane_ms = tuner.autotune()
     tuner.close()
-    b = ipp.Batch(frames, lanes=best, cfg=cfg, max_src=65536)
-    b.run()
-    torch.cuda.synchronize(dev)
     gs = torch.cuda.Stream(dev)
+    # the stream form at its best lane count, plain and as a graph
+    b = ipp.Batch(frames, lanes=best, cfg=cfg, max_src=65536)
+    streams_ms = timed(lambda: b.run(gs), gs)
     b.capture(gs)
-    bat_ms = timed(lambda: b.launch(gs), gs)
+    streams_graph_ms = timed(lambda: b.launch(gs), gs)
     b.close()
+    del b
+    # the table form: one launch per stage over all frames, plain and as a graph
+    t = ipp.Batch(frames, cfg=cfg, max_src=65536, mode="table")
+    table_ms = timed(lambda: t.run(gs), gs)
+    t.capture(gs)
+    table_graph_ms = timed(lambda: t.launch(gs), gs)
+    table_ws_gb = t.ws.numel() / 1e9
+    t.close()
+    del t
     mpix = sum(f.numel() for f in frames) / 1e6
+    bat_ms = table_graph_ms
     return {"frames": n_frames, "mpix": mpix, "per_frame_ms": per_ms, "batched_ms": bat_ms,
-            "speedup": per_ms / bat_ms, "batched_mpix_per_s": mpix / (bat_ms / 1e3), "lanes": best,
+            "form": "table (one launch per stage over a device table of all frames), captured graph",
+            "speedup": per_ms / bat_ms, "batched_mpix_per_s": mpix / (bat_ms / 1e3),
+            "table_ms": table_ms, "table_graph_ms": table_graph_ms, "table_workspace_gb": table_ws_gb,
+            "streams_ms": streams_ms, "streams_graph_ms": streams_graph_ms, "lanes": best,
+            "table_vs_streams": min(streams_ms, streams_graph_ms) / bat_ms,
             "autotune_ms_lanes_1_2_4_8": lane_ms,
             "workload": f"{n_frames} frames 2048^2 / 4096^2 / 6144x6160, 2k-50k stars, sky 200-3000 ADU, "
-                        "mesh 128; per-frame ipp_extract vs captured batch graph"}
+                        "mesh 128; per-frame ipp_extract on one stream, the stream form at its autotuned "
+                        "lane count, and the table form"}
 
 
 def raw_stream_leg(ipp, synth, dev, n_steps, n_resident=4):
@@ -309,7 +324,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--psf-stamps", type=int, default=200000)
-    ap.add_argument("--batch-frames", type=int, default=12)
+    ap.add_argument("--batch-frames", type=int, default=64)
     ap.add_argument("--raw-frames", type=int, default=10)
     ap.add_argument("--lanes", type=int, default=4, help="CUDA streams that consecutive frames rotate over")
     ap.add_argument("--soak-steps", type=int, default=3000,

@@ -754,6 +754,35 @@ int ipp_batch_capture(ipp_batch b, const ipp_frame_desc* frames, int32_t n, cons
 int ipp_batch_launch(ipp_batch b, void* stream);
 
 /*
+ * The table form of the batch: one launch per stage for all frames.  The jobs
+ * of every frame (the same as ipp_extract's) are packed into a device table at
+ * the head of ws; each stage is a single launch over the frames' blocks, a block
+ * finding its frame by binary search over the frames' first blocks, and runs the
+ * per-frame kernel body -- so the outputs equal ipp_extract's bit for bit and a
+ * batch of n frames costs ~17 launches.  Frames keep separate scratch (ws holds
+ * them one after another), so every frame's stages can run at once.
+ *   ipp_batch_table_workspace_size  bytes of ws for these frames (the table plus
+ *                                   each frame's ipp_extract workspace)
+ *   ipp_batch_table_extract         enqueues the batch on `stream`; the table is
+ *                                   uploaded from the runner's pinned staging
+ *                                   buffer unless it equals the one uploaded to
+ *                                   this ws last (same frames and parameters)
+ *   ipp_batch_table_capture         uploads the table, then records the stages as
+ *                                   the runner's graph (ipp_batch_launch replays
+ *                                   it; the graph reads the table in ws, so ws is
+ *                                   not to be reused for another batch meanwhile)
+ * Limits: 1..1024 frames; the windowed centroid's box at most 15 px (fwhm_win
+ * up to ~3.5 px) -- NOT_SUPPORTED otherwise, where the stream form applies.
+ */
+size_t ipp_batch_table_workspace_size(const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp);
+int ipp_batch_table_extract(ipp_batch b, const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp,
+                            const ipp_det_params* dp, const ipp_cen_params* cp, const ipp_phot_params* pp,
+                            int32_t max_src, void* ws, size_t ws_bytes, void* stream);
+int ipp_batch_table_capture(ipp_batch b, const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp,
+                            const ipp_det_params* dp, const ipp_cen_params* cp, const ipp_phot_params* pp,
+                            int32_t max_src, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * ipp_batch_autotune -- times ipp_batch_extract on this batch for 1, 2, 4 and 8
  * lanes (two runs each after a warm-up, CUDA events on `stream`), and returns
  * the fastest lane count in *best_lanes and the times in ms_per_lanes[4]

@@ -651,13 +651,18 @@ class Extractor:
 class Batch:
     """The catalog path over a fixed list of frames of mixed sizes (ipp_batch_*):
     outputs preallocated per frame (self.outs, per-label statistics in
-    self.stats), frames spread over `lanes` CUDA streams.
-    run() enqueues the batch; capture() records it as one CUDA graph that
-    launch() replays (update the frames' contents in place between launches)."""
+    self.stats).  mode="table": one launch per stage for all frames, from a
+    device table of the frames' jobs (ipp_batch_table_*); mode="streams": the
+    frames spread over `lanes` CUDA streams.  run() enqueues the batch;
+    capture() records it as one CUDA graph that launch() replays (update the
+    frames' contents in place between launches)."""
 
     def __init__(self, frames, lanes=4, cfg: BgConfig | None = None, k=1.5, thresh_abs=0.0, min_area=5,
                  fwhm_win=3.0, cen_iter=16, tol2=1e-8, r_ap=5.0, r_in=8.0, r_out=12.0, min_ann=10,
-                 max_src=None, calib=None):
+                 max_src=None, calib=None, mode="streams"):
+        if mode not in ("streams", "table"):
+            raise ValueError("mode is 'streams' or 'table'")
+        self.mode = mode
         L = load()
         self.L = L
         self.cfg = cfg or BgConfig()
@@ -688,7 +693,12 @@ class Batch:
         self.pp = _abi.PhotParams(r_ap, r_in, r_out, min_ann)
         mw = max(f.shape[1] for f in self.frames)
         mh = max(f.shape[0] for f in self.frames)
-        need = L.ipp_batch_workspace_size(mw, mh, self.bp, _abi.IPP_BATCH_MAX_LANES)
+        if mode == "table":
+            need = L.ipp_batch_table_workspace_size(self.descs, self.n, self.bp)
+            if need == 0:
+                raise ValueError("bad batch for the table form")
+        else:
+            need = L.ipp_batch_workspace_size(mw, mh, self.bp, _abi.IPP_BATCH_MAX_LANES)
         self.ws = torch.empty(need, dtype=torch.uint8, device=dev)
         self.h = C.c_void_p()
         self.lanes = lanes
@@ -699,12 +709,19 @@ class Batch:
 
     def run(self, stream=None):
         s = stream.cuda_stream if stream is not None else _stream()
-        _abi.check("ipp_batch_extract", self.L.ipp_batch_extract(self.h, *self._args(), s))
+        if self.mode == "table":
+            _abi.check("ipp_batch_table_extract", self.L.ipp_batch_table_extract(self.h, *self._args(), s))
+        else:
+            _abi.check("ipp_batch_extract", self.L.ipp_batch_extract(self.h, *self._args(), s))
         return self.outs
 
     def capture(self, stream):
         """Record the batch as a CUDA graph (stream: a torch.cuda.Stream, not the default)."""
-        _abi.check("ipp_batch_capture", self.L.ipp_batch_capture(self.h, *self._args(), stream.cuda_stream))
+        if self.mode == "table":
+            _abi.check("ipp_batch_table_capture",
+                       self.L.ipp_batch_table_capture(self.h, *self._args(), stream.cuda_stream))
+        else:
+            _abi.check("ipp_batch_capture", self.L.ipp_batch_capture(self.h, *self._args(), stream.cuda_stream))
 
     def launch(self, stream=None):
         s = stream.cuda_stream if stream is not None else _stream()

@@ -140,6 +140,9 @@ PROTOTYPES = {
     "ipp_batch_extract": ([vp, C.POINTER(FrameDesc), i32] + _par + [vp, sz, vp], i32),
     "ipp_batch_capture": ([vp, C.POINTER(FrameDesc), i32] + _par + [vp, sz, vp], i32),
     "ipp_batch_launch": ([vp, vp], i32),
+    "ipp_batch_table_workspace_size": ([C.POINTER(FrameDesc), i32, C.POINTER(BgParams)], sz),
+    "ipp_batch_table_extract": ([vp, C.POINTER(FrameDesc), i32] + _par + [vp, sz, vp], i32),
+    "ipp_batch_table_capture": ([vp, C.POINTER(FrameDesc), i32] + _par + [vp, sz, vp], i32),
     "ipp_batch_autotune": ([C.POINTER(FrameDesc), i32] + _par + [vp, sz, vp, C.POINTER(i32), C.POINTER(f32)],
                            i32),
     "ipp_psf_fit": ([vp, i64, i32, vp, vp, C.POINTER(FitParams), vp, vp, vp, vp, vp], i32),

@@ -549,10 +549,14 @@ extern "C" size_t ipp_extract_workspace_size(int64_t W, int64_t H, const ipp_bg_
     return a256(ipp_bg_estimate_workspace_size(W, H, bp)) + ipp_ccl_workspace_size(W, H);
 }
 
-extern "C" int ipp_extract(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
-                           const ipp_calib* cal, const ipp_bg_params* bp, const ipp_det_params* dp,
-                           const ipp_cen_params* cp, const ipp_phot_params* pp, int32_t max_src,
-                           const ipp_catalog_out* out, void* ws, size_t ws_bytes, void* stream) {
+// The jobs of ipp_extract for one frame, after its argument checks: the mesh
+// statistics and filter, the fused subtraction / detection, the centroid and
+// the aperture photometry.  Shared by ipp_extract and the batched form, so the
+// two run the same arithmetic on the same workspace layout.
+int ipp_extract_jobs(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch, const ipp_calib* cal,
+                     const ipp_bg_params* bp, const ipp_det_params* dp, const ipp_cen_params* cp,
+                     const ipp_phot_params* pp, int32_t max_src, const ipp_catalog_out* out, void* ws,
+                     size_t ws_bytes, MeshJob* M, MeshFilterJob* F, DetectArgs* A, CenJob* C, PhotJob* P) {
     if (int e = check_frame(img, dtype, W, H, pitch, cal)) return e;
     if (int e = check_bg(bp)) return e;
     REQUIRE(dp && cp && pp && out, "NULL parameter struct");
@@ -561,38 +565,82 @@ extern "C" int ipp_extract(const void* img, int dtype, int64_t W, int64_t H, int
     if (int e = check_stats(&out->stats)) return e;
     REQUIRE(dp->min_area >= 1 && dp->k >= 0.f, "bad detection params");
     REQUIRE(dp->filter == 0 || dp->filter == 1, "detection filter must be 0 or 1");
-    REQUIRE(cp->fwhm_win > 0.f && cp->fwhm_win <= 16.f && cp->max_iter >= 1, "bad centroid params");
+    REQUIRE(cp->fwhm_win > 0.f && cp->fwhm_win <= 16.f && cp->max_iter >= 1 && cp->tol2 >= 0.f,
+            "bad centroid params");
     REQUIRE(pp->r_ap > 0.f && pp->r_ap <= 16.f && pp->r_out > pp->r_in && pp->r_in >= 0.f, "bad aperture params");
     REQUIRE(pp->r_out <= 16.f, "r_out above 16 px not supported");
     REQUIRE(max_src >= 0, "max_src < 0");
     size_t need = ipp_extract_workspace_size(W, H, bp);
     REQUIRE(ws && ws_bytes >= need, "workspace of %zu bytes needed", need);
-    cudaStream_t s = (cudaStream_t)stream;
     unsigned char* w = (unsigned char*)ws;
-    size_t bgws = a256(ipp_bg_estimate_workspace_size(W, H, bp));
-    if (int e = bg_estimate_impl(img, dtype, W, H, pitch, nullptr, cal, bp, out->mesh_bkg, out->mesh_rms,
-                                 nullptr, nullptr, out->status_dev, w, bgws, s))
-        return e;
+    const size_t bgws = a256(ipp_bg_estimate_workspace_size(W, H, bp));
+    int nx, ny;
+    grid_of(W, H, bp, &nx, &ny);
+    const size_t nb = a256((size_t)nx * ny * sizeof(float));
+    float* rb = (float*)(w + 0 * nb);
+    float* rr = (float*)(w + 1 * nb);
+    // mesh statistics (as ipp_bg_estimate)
+    memset(M, 0, sizeof(*M));
+    M->img = img; M->dtype = dtype; M->W = W; M->H = H; M->pitch = pitch; M->mask = nullptr;
+    M->bias_map = cal ? cal->bias_map : nullptr; M->bias = cal ? cal->bias : 0.f;
+    M->inv_flat = cal ? cal->inv_flat : nullptr;
+    M->mesh_w = bp->mesh_w; M->mesh_h = bp->mesh_h; M->nx = nx; M->ny = ny;
+    M->maxiters = bp->maxiters; M->min_valid = bp->min_valid; M->estimator = bp->estimator;
+    M->nsigma = bp->nsigma; M->mf = bp->median_factor; M->mnf = bp->mean_factor;
+    M->raw_bkg = rb; M->raw_rms = rr;
+    F->raw_bkg = rb; F->raw_rms = rr;
+    F->fill_bkg = (float*)(w + 2 * nb); F->fill_rms = (float*)(w + 3 * nb);
+    F->nx = nx; F->ny = ny; F->fw = bp->filter_w; F->fh = bp->filter_h;
+    F->out_bkg = out->mesh_bkg; F->out_rms = out->mesh_rms; F->status_dev = out->status_dev;
+    // fused subtraction, threshold and labeling
+    memset(A, 0, sizeof(*A));
+    A->mode = 2;
+    A->W = W; A->H = H; A->img = img; A->dtype = dtype; A->pitch = pitch;
+    A->bias_map = cal ? cal->bias_map : nullptr; A->bias = cal ? cal->bias : 0.f;
+    A->inv_flat = cal ? cal->inv_flat : nullptr;
+    A->mesh_bkg = out->mesh_bkg; A->sub = out->sub; A->sub_pitch = W; A->mesh_rms = out->mesh_rms;
+    A->nx = nx; A->ny = ny;
+    A->mesh_w = bp->mesh_w; A->mesh_h = bp->mesh_h;
+    A->k = dp->k; A->thresh_abs = dp->thresh_abs; A->min_area = dp->min_area; A->mask_in = nullptr;
+    A->filter = dp->filter;
+    A->labels = out->labels; A->n_src_dev = out->n_src_dev; A->max_src = max_src; A->stats = out->stats;
+    A->ws = w + bgws;
+    // centroid (as ipp_centroid) and aperture photometry (as ipp_aperture_phot)
+    memset(C, 0, sizeof(*C));
+    C->sub = out->sub; C->W = W; C->H = H; C->pitch = W; C->n_src_dev = out->n_src_dev; C->max_src = max_src;
+    C->x0 = out->stats.xbar; C->y0 = out->stats.ybar;
+    C->sw = (float)(cp->fwhm_win / 2.3548200450309493);
+    C->rad = 4.0f * C->sw;
+    C->tol2 = cp->tol2; C->max_iter = cp->max_iter;
+    C->x = out->x; C->y = out->y; C->niter = nullptr; C->flags = out->cen_flags;
+    memset(P, 0, sizeof(*P));
+    P->sub = out->sub; P->W = W; P->H = H; P->pitch = W; P->n_src_dev = out->n_src_dev; P->max_src = max_src;
+    P->x = out->x; P->y = out->y; P->r_ap = pp->r_ap; P->r_in = pp->r_in; P->r_out = pp->r_out;
+    P->min_ann = pp->min_ann;
+    P->flux = out->flux; P->sky = out->sky; P->area = out->area; P->n_ann = out->n_ann; P->flags = out->phot_flags;
+    return IPP_OK;
+}
+
+extern "C" int ipp_extract(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch,
+                           const ipp_calib* cal, const ipp_bg_params* bp, const ipp_det_params* dp,
+                           const ipp_cen_params* cp, const ipp_phot_params* pp, int32_t max_src,
+                           const ipp_catalog_out* out, void* ws, size_t ws_bytes, void* stream) {
+    MeshJob M;
+    MeshFilterJob F;
     DetectArgs A;
-    memset(&A, 0, sizeof(A));
-    A.mode = 2;
-    A.W = W; A.H = H; A.img = img; A.dtype = dtype; A.pitch = pitch;
-    A.bias_map = cal ? cal->bias_map : nullptr; A.bias = cal ? cal->bias : 0.f;
-    A.inv_flat = cal ? cal->inv_flat : nullptr;
-    A.mesh_bkg = out->mesh_bkg; A.sub = out->sub; A.sub_pitch = W; A.mesh_rms = out->mesh_rms;
-    grid_of(W, H, bp, &A.nx, &A.ny);
-    A.mesh_w = bp->mesh_w; A.mesh_h = bp->mesh_h;
-    A.k = dp->k; A.thresh_abs = dp->thresh_abs; A.min_area = dp->min_area; A.mask_in = nullptr;
-    A.filter = dp->filter;
-    A.labels = out->labels; A.n_src_dev = out->n_src_dev; A.max_src = max_src; A.stats = out->stats;
-    A.ws = w + bgws;
-    if (int e = ipp_launch_detect(A, s)) return e;
-    ipp_cen_params c = *cp;
-    if (int e = ipp_centroid(out->sub, W, H, W, out->n_src_dev, max_src, out->stats.xbar, out->stats.ybar, &c,
-                             out->x, out->y, nullptr, out->cen_flags, stream))
+    CenJob C;
+    PhotJob P;
+    if (int e = ipp_extract_jobs(img, dtype, W, H, pitch, cal, bp, dp, cp, pp, max_src, out, ws, ws_bytes, &M, &F,
+                                 &A, &C, &P))
         return e;
-    return ipp_aperture_phot(out->sub, W, H, W, out->n_src_dev, max_src, out->x, out->y, pp, out->flux,
-                             out->sky, out->area, out->n_ann, out->phot_flags, stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int e = ipp_launch_mesh_stats(M, s)) return e;
+    if (int e = ipp_launch_mesh_filter(F.raw_bkg, F.raw_rms, F.fill_bkg, F.fill_rms, F.nx, F.ny, F.fw, F.fh,
+                                       F.out_bkg, F.out_rms, F.status_dev, s))
+        return e;
+    if (int e = ipp_launch_detect(A, s)) return e;
+    if (int e = ipp_launch_centroid(C, s)) return e;
+    return ipp_launch_aperture(P, s);
 }
 
 // ---- PSF fit and differentiable model --------------------------------------------

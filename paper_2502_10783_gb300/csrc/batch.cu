@@ -1,9 +1,16 @@
-// batch.cu -- the catalog path over a batch of independent frames: a runner
-// that spreads frames over its own CUDA streams (largest frames first, each to
-// the least-loaded lane), fork/join with events around the caller's stream, an
-// optional CUDA graph of a whole batch, and a lane-count autotuner.
+// batch.cu -- the catalog path over a batch of independent frames, in two forms:
+//   streams: a runner that spreads frames over its own CUDA streams (largest
+//     frames first, each to the least-loaded lane), fork/join with events around
+//     the caller's stream, and a lane-count autotuner;
+//   table: one launch per stage for all frames -- a device table holds every
+//     frame's jobs, each block finds its frame by binary search over the
+//     frames' first blocks and runs the per-frame kernel body on it, so a batch
+//     of n frames costs the same ~17 launches as one frame and the stages'
+//     tails of small frames fill in behind large ones.
+// Either form can be recorded as one CUDA graph.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "jobs.cuh"
@@ -14,6 +21,13 @@ struct ipp_batch_s {
     cudaEvent_t fork = nullptr;
     cudaEvent_t join[IPP_BATCH_MAX_LANES] = {};
     cudaGraphExec_t exec = nullptr;
+    // table form: pinned staging of the device table, and what was uploaded last
+    unsigned char* stage = nullptr;
+    size_t stage_cap = 0;
+    cudaEvent_t staged = nullptr;    // the last upload has left the staging buffer
+    bool stage_busy = false;
+    std::vector<unsigned char> last;
+    const void* last_dev = nullptr;
 };
 
 namespace {
@@ -115,6 +129,8 @@ extern "C" int ipp_batch_destroy(ipp_batch b) {
         if (b->st[l]) cudaStreamDestroy(b->st[l]);
     }
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->staged) cudaEventDestroy(b->staged);
+    if (b->stage) cudaFreeHost(b->stage);
     delete b;
     return IPP_OK;
 }
@@ -197,4 +213,147 @@ extern "C" int ipp_batch_autotune(const ipp_frame_desc* frames, int32_t n, const
     cudaEventDestroy(e1);
     if (status == IPP_OK) *best_lanes = bl;
     return status;
+}
+
+
+// ---- table form -----------------------------------------------------------------
+namespace {
+
+size_t table_bytes(int32_t n) { return a256((size_t)n * 6144 + 65536); }
+
+// Builds the batch's table in the runner's pinned staging buffer, uploads it
+// to the head of ws unless it equals the table uploaded there last, and
+// enqueues the stages.  upload_only: stop after the upload (capture set-up).
+int run_table(ipp_batch b, const ipp_frame_desc* f, int32_t n, const ipp_bg_params* bp, const ipp_det_params* dp,
+              const ipp_cen_params* cp, const ipp_phot_params* pp, int32_t max_src, void* ws, size_t ws_bytes,
+              cudaStream_t s, bool upload_only, ipp::BgMultiPlan* bg_out, ipp::DetMultiPlan* det_out,
+              ipp::PhotMultiPlan* ph_out) {
+    using namespace ipp;
+    int64_t mw = 0, mh = 0;
+    if (int e = check_frames(f, n, &mw, &mh)) return e;
+    if (n == 0) return IPP_OK;
+    if (n > 1024) return ipp_set_error(IPP_ERR_INVALID_ARG, "at most 1024 frames in the table form");
+    if (!ws || ((uintptr_t)ws & 255)) return ipp_set_error(IPP_ERR_INVALID_ARG, "workspace NULL or misaligned");
+    const size_t tb = table_bytes(n);
+    std::vector<MeshJob> M(n);
+    std::vector<MeshFilterJob> F(n);
+    std::vector<DetectArgs> A(n);
+    std::vector<CenJob> C(n);
+    std::vector<PhotJob> P(n);
+    size_t off = tb;
+    for (int i = 0; i < n; i++) {
+        const size_t need = a256(ipp_extract_workspace_size(f[i].W, f[i].H, bp));
+        if (off + need > ws_bytes) return ipp_set_error(IPP_ERR_INVALID_ARG, "workspace too small at frame %d", i);
+        int st = ipp_extract_jobs(f[i].img, f[i].dtype, f[i].W, f[i].H, f[i].pitch, f[i].cal, bp, dp, cp, pp, max_src,
+                                  &f[i].out, (unsigned char*)ws + off, need, &M[i], &F[i], &A[i], &C[i], &P[i]);
+        if (st != IPP_OK) {
+            char msg[512];
+            snprintf(msg, sizeof(msg), "%s", ipp_last_error_detail());
+            return ipp_set_error(st, "frame %d: %s", i, msg);
+        }
+        off += need;
+    }
+    // the staging buffer is reused only once the previous upload has read it
+    if (b->stage_busy) {
+        cudaEventSynchronize(b->staged);
+        b->stage_busy = false;
+    }
+    if (b->stage_cap < tb) {
+        if (b->stage) cudaFreeHost(b->stage);
+        b->stage = nullptr;
+        b->stage_cap = 0;
+        if (cudaMallocHost(&b->stage, tb) != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "pinned table staging");
+        b->stage_cap = tb;
+    }
+    HostBlob hb;
+    hb.h = b->stage;
+    hb.cap = tb;
+    BgMultiPlan bgp;
+    DetMultiPlan dtp;
+    PhotMultiPlan php;
+    if (int e = ipp_bg_multi_pack(M.data(), F.data(), n, hb, &bgp)) return e;
+    if (int e = ipp_detect_multi_pack(A.data(), n, hb, &dtp)) return e;
+    if (int e = ipp_phot_multi_pack(C.data(), P.data(), n, hb, &php)) return e;
+    const unsigned char* dtab = static_cast<const unsigned char*>(ws);
+    const bool same = b->last_dev == ws && b->last.size() == hb.used && memcmp(b->last.data(), hb.h, hb.used) == 0;
+    if (!same) {
+        cudaError_t e = cudaMemcpyAsync(ws, hb.h, hb.used, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b->staged, s);
+        if (e != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+        b->stage_busy = true;
+        b->last.assign(hb.h, hb.h + hb.used);
+        b->last_dev = ws;
+    }
+    if (bg_out) *bg_out = bgp;
+    if (det_out) *det_out = dtp;
+    if (ph_out) *ph_out = php;
+    if (upload_only) return IPP_OK;
+    if (int e = ipp_bg_multi_launch(bgp, dtab, s)) return e;
+    if (int e = ipp_detect_multi_launch(dtp, dtab, s)) return e;
+    return ipp_phot_multi_launch(php, dtab, s);
+}
+
+int ensure_stage_event(ipp_batch b) {
+    if (b->staged) return IPP_OK;
+    if (cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess)
+        return ipp_set_error(IPP_ERR_CUDA, "event create");
+    return IPP_OK;
+}
+
+}  // namespace
+
+extern "C" size_t ipp_batch_table_workspace_size(const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp) {
+    if (!frames || !bp || n < 0 || n > 1024) return 0;
+    size_t t = table_bytes(n);
+    for (int i = 0; i < n; i++) {
+        if (frames[i].W <= 0 || frames[i].H <= 0) return 0;
+        t += a256(ipp_extract_workspace_size(frames[i].W, frames[i].H, bp));
+    }
+    return t;
+}
+
+extern "C" int ipp_batch_table_extract(ipp_batch b, const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp,
+                                       const ipp_det_params* dp, const ipp_cen_params* cp, const ipp_phot_params* pp,
+                                       int32_t max_src, void* ws, size_t ws_bytes, void* stream) {
+    if (!b) return ipp_set_error(IPP_ERR_INVALID_ARG, "batch runner NULL");
+    if (int e = ensure_stage_event(b)) return e;
+    return run_table(b, frames, n, bp, dp, cp, pp, max_src, ws, ws_bytes, (cudaStream_t)stream, false, nullptr,
+                     nullptr, nullptr);
+}
+
+extern "C" int ipp_batch_table_capture(ipp_batch b, const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp,
+                                       const ipp_det_params* dp, const ipp_cen_params* cp, const ipp_phot_params* pp,
+                                       int32_t max_src, void* ws, size_t ws_bytes, void* stream) {
+    if (!b) return ipp_set_error(IPP_ERR_INVALID_ARG, "batch runner NULL");
+    if (!stream) return ipp_set_error(IPP_ERR_INVALID_ARG, "capture needs a stream other than the legacy default");
+    if (int e = ensure_stage_event(b)) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the table is uploaded before the capture, so the graph holds only the stages
+    ipp::BgMultiPlan bgp;
+    ipp::DetMultiPlan dtp;
+    ipp::PhotMultiPlan php;
+    if (int e = run_table(b, frames, n, bp, dp, cp, pp, max_src, ws, ws_bytes, s, true, &bgp, &dtp, &php)) return e;
+    if (n == 0) return IPP_OK;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    const unsigned char* dtab = static_cast<const unsigned char*>(ws);
+    int status = ipp_bg_multi_launch(bgp, dtab, s);
+    if (status == IPP_OK) status = ipp_detect_multi_launch(dtp, dtab, s);
+    if (status == IPP_OK) status = ipp_phot_multi_launch(php, dtab, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (status != IPP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return status;
+    }
+    if (e != cudaSuccess || !g) return ipp_set_error(IPP_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = x;
+    // a later upload to the same workspace must not be skipped: the graph reads
+    // the table uploaded here, which stays in place
+    return IPP_OK;
 }

@@ -592,11 +592,10 @@ __device__ int warp0_finish(MeshShared& S, const MeshJob& J, const Stored& St, c
     return ST_SCAN;
 }
 
-__global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
+__device__ __forceinline__ void mesh_stats_body(const MeshJob& J, const int mesh) {
     __shared__ MeshShared S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    const int mesh = blockIdx.x;
     const int mx = mesh % J.nx, my = mesh / J.nx;
     MeshGeom G;
     G.img = J.img; G.dtype = J.dtype; G.pitch = J.pitch; G.W = J.W; G.mask = J.mask;
@@ -1063,6 +1062,8 @@ __global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) {
     }
 }
 
+__global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats(MeshJob J) { mesh_stats_body(J, blockIdx.x); }
+
 // ---------------------------------------------------------------------------
 // Invalid-mesh fill and median filter on the mesh grid.  An invalid node takes
 // the median of the valid nodes in the smallest (2k+1)^2 neighbourhood holding
@@ -1199,32 +1200,60 @@ __device__ __forceinline__ void window_median_any(const float* fb, const float* 
 
 // pass 1: fills into the caller's arrays.  Each block first checks
 // that the grid holds a valid node (a block-wide scan of raw_rms).
-__global__ void __launch_bounds__(MF_THREADS) k_mesh_fill(const float* raw_bkg, const float* raw_rms, int nx, int ny,
-                                                          float* fill_bkg, float* fill_rms, int32_t* status_dev) {
+__device__ __forceinline__ void mesh_fill_body(const float* raw_bkg, const float* raw_rms, int nx, int ny,
+                                               float* fill_bkg, float* fill_rms, int32_t* status_dev, int vb) {
     const int nn = nx * ny;
     int any = 0;
     for (int i = threadIdx.x; i < nn && !any; i += MF_THREADS) any |= raw_rms[i] >= 0.f;
     if (!__syncthreads_or(any)) {
-        const int id = blockIdx.x * MF_THREADS + threadIdx.x;
+        const int id = vb * MF_THREADS + threadIdx.x;
         if (id < nn) { fill_bkg[id] = 0.f; fill_rms[id] = -1.f; }  // -1: pass 2 writes zeros
         if (id == 0 && status_dev) *status_dev = IPP_ERR_NO_VALID_MESH;
         return;
     }
-    const int id = blockIdx.x * MF_THREADS + threadIdx.x;
+    const int id = vb * MF_THREADS + threadIdx.x;
     if (id >= nn) return;
     const int p = id / nx, q = id - p * nx;
     fill_node(raw_bkg, raw_rms, nx, ny, p, q, &fill_bkg[id], &fill_rms[id]);
     if (id == 0 && status_dev) *status_dev = IPP_OK;
 }
 
+__global__ void __launch_bounds__(MF_THREADS) k_mesh_fill(const float* raw_bkg, const float* raw_rms, int nx, int ny,
+                                                          float* fill_bkg, float* fill_rms, int32_t* status_dev) {
+    mesh_fill_body(raw_bkg, raw_rms, nx, ny, fill_bkg, fill_rms, status_dev, blockIdx.x);
+}
+
 // pass 2: window medians of the filled grids
-__global__ void __launch_bounds__(MF_THREADS) k_mesh_median(const float* fill_bkg, const float* fill_rms, int nx,
-                                                            int ny, int fw, int fh, float* out_bkg, float* out_rms) {
-    const int id = blockIdx.x * MF_THREADS + threadIdx.x;
+__device__ __forceinline__ void mesh_median_body(const float* fill_bkg, const float* fill_rms, int nx, int ny, int fw,
+                                                 int fh, float* out_bkg, float* out_rms, int vb) {
+    const int id = vb * MF_THREADS + threadIdx.x;
     if (id >= nx * ny) return;
     if (fill_rms[0] < 0.f) { out_bkg[id] = 0.f; out_rms[id] = 0.f; return; }  // no valid mesh (pass 1)
     const int p = id / nx, q = id - p * nx;
     window_median_any(fill_bkg, fill_rms, nx, ny, p, q, fw, fh, &out_bkg[id], &out_rms[id]);
+}
+
+__global__ void __launch_bounds__(MF_THREADS) k_mesh_median(const float* fill_bkg, const float* fill_rms, int nx,
+                                                            int ny, int fw, int fh, float* out_bkg, float* out_rms) {
+    mesh_median_body(fill_bkg, fill_rms, nx, ny, fw, fh, out_bkg, out_rms, blockIdx.x);
+}
+
+// ---- batched form: the same bodies over a table of frames ------------------
+__global__ void __launch_bounds__(MS_THREADS, 7) k_mesh_stats_multi(const MeshJob* J, const int* bs, int nf) {
+    const int f = frame_of(bs, nf, blockIdx.x);
+    mesh_stats_body(J[f], blockIdx.x - bs[f]);
+}
+
+__global__ void __launch_bounds__(MF_THREADS) k_mesh_fill_multi(const MeshFilterJob* J, const int* bs, int nf) {
+    const int f = frame_of(bs, nf, blockIdx.x);
+    const MeshFilterJob& F = J[f];
+    mesh_fill_body(F.raw_bkg, F.raw_rms, F.nx, F.ny, F.fill_bkg, F.fill_rms, F.status_dev, blockIdx.x - bs[f]);
+}
+
+__global__ void __launch_bounds__(MF_THREADS) k_mesh_median_multi(const MeshFilterJob* J, const int* bs, int nf) {
+    const int f = frame_of(bs, nf, blockIdx.x);
+    const MeshFilterJob& F = J[f];
+    mesh_median_body(F.fill_bkg, F.fill_rms, F.nx, F.ny, F.fw, F.fh, F.out_bkg, F.out_rms, blockIdx.x - bs[f]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1368,4 +1397,35 @@ int ipp_launch_bg_subtract(const SubJob& J, cudaStream_t s) {
     dim3 grid((unsigned)cdiv(J.W, BG_TW), (unsigned)cdiv(J.H, BG_TH));
     k_bg_subtract<<<grid, BG_THREADS, 0, s>>>(J);
     return ipp_check_launch("k_bg_subtract");
+}
+
+
+int ipp_bg_multi_pack(const MeshJob* J, const MeshFilterJob* F, int nf, HostBlob& hb, BgMultiPlan* p) {
+    int nb[1024];
+    if (nf < 1 || nf > 1024) return ipp_set_error(IPP_ERR_INVALID_ARG, "1..1024 frames");
+    for (int f = 0; f < nf; f++) {
+        if (J[f].mesh_w * J[f].mesh_h > 16384)
+            return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "mesh area %d > 16384", J[f].mesh_w * J[f].mesh_h);
+        nb[f] = J[f].nx * J[f].ny;
+    }
+    p->stats = ipp_put_stage(hb, J, nb, nf);
+    for (int f = 0; f < nf; f++) nb[f] = (F[f].nx * F[f].ny + MF_THREADS - 1) / MF_THREADS;
+    p->fill = ipp_put_stage(hb, F, nb, nf);
+    p->median = p->fill;
+    p->nf = nf;
+    return hb.ok() ? IPP_OK : ipp_set_error(IPP_ERR_INVALID_ARG, "batch table overflow");
+}
+
+int ipp_bg_multi_launch(const BgMultiPlan& p, const unsigned char* t, cudaStream_t s) {
+    cudaFuncSetAttribute(k_mesh_stats_multi, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    k_mesh_stats_multi<<<(unsigned)p.stats.total, MS_THREADS, 0, s>>>(
+        reinterpret_cast<const MeshJob*>(t + p.stats.jobs), reinterpret_cast<const int*>(t + p.stats.bs), p.nf);
+    if (int e = ipp_check_launch("k_mesh_stats_multi")) return e;
+    const MeshFilterJob* F = reinterpret_cast<const MeshFilterJob*>(t + p.fill.jobs);
+    const int* bs = reinterpret_cast<const int*>(t + p.fill.bs);
+    k_mesh_fill_multi<<<(unsigned)p.fill.total, MF_THREADS, 0, s>>>(F, bs, p.nf);
+    if (int e = ipp_check_launch("k_mesh_fill_multi")) return e;
+    k_mesh_median_multi<<<(unsigned)p.median.total, MF_THREADS, 0, s>>>(F, bs, p.nf);
+    return ipp_check_launch("k_mesh_median_multi");
 }

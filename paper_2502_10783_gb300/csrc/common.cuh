@@ -139,6 +139,18 @@ IPP_D void keys_weights(float s, float w[4]) {
     w[3] = 0.5f * s3 - 0.5f * s2;
 }
 
+// Frame of virtual block b in a multi-frame launch: bs[f] is the first block of
+// frame f (bs[0] = 0, bs[nf] = the total); frames without blocks are skipped.
+IPP_D int frame_of(const int* bs, int nf, int b) {
+    int lo = 0, hi = nf - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(bs + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 IPP_HD int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 IPP_HD int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

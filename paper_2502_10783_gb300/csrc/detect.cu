@@ -19,6 +19,7 @@
 // expands the runs into the label map, writing every pixel once.  Nothing
 // depends on the tile shape but the work split.
 #include <algorithm>
+#include <vector>
 
 #include "jobs.cuh"
 
@@ -220,9 +221,9 @@ __device__ void tile_union(SH& S) {
 
 constexpr int ST_TH = 32, ST_TW = 128, ST_THREADS = 256;
 
-__global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh(SubThreshJob J) {
+__device__ __forceinline__ void sub_thresh_body(const SubThreshJob& J, int bx, int by) {
     __shared__ float cvb[ST_TH][T_NQ], cvr[ST_TH][T_NQ];
-    const int64_t tx0 = (int64_t)blockIdx.x * ST_TW, ty0 = (int64_t)blockIdx.y * ST_TH;
+    const int64_t tx0 = (int64_t)bx * ST_TW, ty0 = (int64_t)by * ST_TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // per row: vertical interpolation of the node columns this tile reads
     const int qa = (int)floorf(((float)(int)tx0 + 0.5f) / J.mesh_w - 0.5f) - 1;
@@ -358,6 +359,10 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh(SubThreshJob J) {
     }
 }
 
+__global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh(SubThreshJob J) {
+    sub_thresh_body(J, blockIdx.x, blockIdx.y);
+}
+
 // Same pass with the horizontal Keys interpolation in polynomial form: per tile
 // row and node interval q0 the four (row-interpolated) node values give
 // B(t) = c0 + c1 t + c2 t^2 + c3 t^3, t = u - q0 (relative to the reference
@@ -371,10 +376,10 @@ __device__ __forceinline__ float4 keys_poly(float d0, float d1, float d2, float 
                        0.5f * (d3 - d0) + 1.5f * (d1 - d2));
 }
 
-__global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh_poly(SubThreshJob J) {
+__device__ __forceinline__ void sub_thresh_poly_body(const SubThreshJob& J, int bx, int by) {
     __shared__ float cvb[ST_TH][T_NQ], cvr[ST_TH][T_NQ];
     __shared__ float4 pb[ST_TH][ST_NINT], pr[ST_TH][ST_NINT];
-    const int64_t tx0 = (int64_t)blockIdx.x * ST_TW, ty0 = (int64_t)blockIdx.y * ST_TH;
+    const int64_t tx0 = (int64_t)bx * ST_TW, ty0 = (int64_t)by * ST_TH;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int qa = (int)floorf(((float)(int)tx0 + 0.5f) / J.mesh_w - 0.5f) - 1;
     const int qz = (int)floorf(((float)((int)tx0 + ST_TW - 1) + 0.5f) / J.mesh_w - 0.5f) + 2;
@@ -513,6 +518,10 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh_poly(SubThreshJob 
         const int64_t wcol = (xc >> 5);
         if ((lane & 7) == 0 && y < J.H && wcol < J.mw) J.mask[y * J.mw + wcol] = wv;
     }
+}
+
+__global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh_poly(SubThreshJob J) {
+    sub_thresh_poly_body(J, blockIdx.x, blockIdx.y);
 }
 
 // One tile, all threads of the block.  Returns false, having written nothing
@@ -711,24 +720,27 @@ __device__ bool tile_label_body(const TileJob& J, SH& S, int tile) {
 
 // Common pass: one tile per block with the small capacities; tiles that do not
 // fit are listed for the full pass.
-__global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) {
+__device__ __forceinline__ void tile_label_fast(const TileJob& J, int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileFast& S = *reinterpret_cast<TileFast*>(smem_raw);
-    const int tile = blockIdx.y * J.ntx + blockIdx.x;
     if (!tile_label_body(J, S, tile) && threadIdx.x == 0) {
         const int slot = atomicAdd(&J.ws.counters[1], 1);
         J.ws.ovf[slot] = tile;
     }
 }
 
+__global__ void __launch_bounds__(T_THREADS) k_tile_label(TileJob J) { tile_label_fast(J, blockIdx.y * J.ntx + blockIdx.x); }
+
 // Full pass over the listed tiles (any mask fits: T_RCAP is the most runs a
 // tile can have).
-__global__ void __launch_bounds__(T_THREADS) k_tile_label_full(TileJob J) {
+__device__ __forceinline__ void tile_label_full(const TileJob& J, int vb, int nvb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileFull& S = *reinterpret_cast<TileFull*>(smem_raw);
     const int n = __ldcg(J.ws.counters + 1);
-    for (int i = blockIdx.x; i < n; i += gridDim.x) tile_label_body(J, S, __ldcg(J.ws.ovf + i));
+    for (int i = vb; i < n; i += nvb) tile_label_body(J, S, __ldcg(J.ws.ovf + i));
 }
+
+__global__ void __launch_bounds__(T_THREADS) k_tile_label_full(TileJob J) { tile_label_full(J, blockIdx.x, gridDim.x); }
 
 // ------------------------------------------------------------ global phase
 __device__ __forceinline__ int gfind(int32_t* P, int x) {
@@ -1019,6 +1031,100 @@ __global__ void __launch_bounds__(G_THREADS) k_tile_final(CclWs ws, int64_t W, i
     ccl_final_tile(ws, lab, blockIdx.x, W, H, ntx, labels);
 }
 
+// ---- batched form: the same bodies over a table of frames ------------------
+struct CclJob {
+    CclWs ws;
+    int ntx, nty;
+    int64_t W, H;
+    int min_area;
+    int32_t* n_src_dev;
+    int32_t max_src;
+    ipp_src_stats stats;
+    int32_t* labels;
+};
+struct ZeroJob {
+    int32_t* p;
+    int words;
+};
+
+#define IPP_MULTI_FRAME(bs, nf) \
+    const int f_ = frame_of(bs, nf, blockIdx.x); \
+    const int vb = blockIdx.x - bs[f_], nvb = bs[f_ + 1] - bs[f_];
+
+__global__ void __launch_bounds__(256) k_zero_multi(const ZeroJob* Z, const int* bs, int nf) {
+    IPP_MULTI_FRAME(bs, nf)
+    (void)vb; (void)nvb;
+    for (int i = threadIdx.x; i < Z[f_].words; i += 256) Z[f_].p[i] = 0;
+}
+
+__global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh_poly_multi(const SubThreshJob* T, const int* bs, int nf) {
+    IPP_MULTI_FRAME(bs, nf)
+    (void)nvb;
+    const int gx = (int)cdiv(T[f_].W, ST_TW);
+    sub_thresh_poly_body(T[f_], vb % gx, vb / gx);
+}
+
+__global__ void __launch_bounds__(ST_THREADS, 4) k_sub_thresh_multi(const SubThreshJob* T, const int* bs, int nf) {
+    IPP_MULTI_FRAME(bs, nf)
+    (void)nvb;
+    const int gx = (int)cdiv(T[f_].W, ST_TW);
+    sub_thresh_body(T[f_], vb % gx, vb / gx);
+}
+
+__global__ void __launch_bounds__(T_THREADS) k_tile_label_multi(const TileJob* J, const int* bs, int nf) {
+    IPP_MULTI_FRAME(bs, nf)
+    (void)nvb;
+    tile_label_fast(J[f_], vb);
+}
+
+__global__ void __launch_bounds__(T_THREADS) k_tile_label_full_multi(const TileJob* J, const int* bs, int nf) {
+    IPP_MULTI_FRAME(bs, nf)
+    tile_label_full(J[f_], vb, nvb);
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_ccl_union_multi(const CclJob* C, const int* bs, int nf) {
+    IPP_MULTI_FRAME(bs, nf)
+    (void)nvb;
+    ccl_union_tile(C[f_].ws, vb, C[f_].ntx, C[f_].nty);
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_ccl_resolve_multi(const CclJob* C, const int* bs, int nf) {
+    IPP_MULTI_FRAME(bs, nf)
+    const CclWs& ws = C[f_].ws;
+    const int n = __ldcg(ws.counters);
+    for (int t = vb * G_THREADS + threadIdx.x; t < n; t += nvb * G_THREADS) ccl_resolve_node(ws, __ldcg(ws.klist + t));
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_ccl_count_multi(const CclJob* C, const int* bs, int nf) {
+    __shared__ GShared G;
+    IPP_MULTI_FRAME(bs, nf)
+    (void)nvb;
+    ccl_count_tile(C[f_].ws, G, vb, C[f_].W, C[f_].ntx, C[f_].min_area);
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_ccl_scan_multi(const CclJob* C, const int* bs, int nf) {
+    extern __shared__ __align__(16) int g_sm[];   // 2 T_TH ntx ints of the widest frame
+    __shared__ GShared G;
+    IPP_MULTI_FRAME(bs, nf)
+    (void)nvb;
+    ccl_scan_row(C[f_].ws, G, g_sm, vb, C[f_].ntx, C[f_].nty, C[f_].n_src_dev);
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_ccl_emit_multi(const CclJob* C, const int* bs, int nf) {
+    IPP_MULTI_FRAME(bs, nf)
+    const CclJob& c = C[f_];
+    const int n = __ldcg(c.ws.counters);
+    for (int t = vb * G_THREADS + threadIdx.x; t < n; t += nvb * G_THREADS)
+        ccl_emit_node(c.ws, __ldcg(c.ws.klist + t), c.max_src, c.stats);
+}
+
+__global__ void __launch_bounds__(G_THREADS) k_tile_final_multi(const CclJob* C, const int* bs, int nf) {
+    __shared__ __align__(16) int32_t lab[T_TH * T_TW];
+    IPP_MULTI_FRAME(bs, nf)
+    (void)nvb;
+    ccl_final_tile(C[f_].ws, lab, vb, C[f_].W, C[f_].H, C[f_].ntx, C[f_].labels);
+}
+
 }  // namespace ipp
 
 // ------------------------------------------------------------------ host side
@@ -1169,4 +1275,104 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
     if (int e = ipp_check_launch("k_ccl_emit")) return e;
     k_tile_final<<<nt, G_THREADS, 0, s>>>(w, A.W, A.H, L.ntx, A.labels);
     return ipp_check_launch("k_tile_final");
+}
+
+// ---- batched form: tables and launches ----------------------------------------
+int ipp_detect_multi_pack(const DetectArgs* A, int nf, HostBlob& hb, DetMultiPlan* p) {
+    if (nf < 1 || nf > 1024) return ipp_set_error(IPP_ERR_INVALID_ARG, "1..1024 frames");
+    std::vector<SubThreshJob> T(nf), Tf(nf);
+    std::vector<TileJob> J(nf);
+    std::vector<CclJob> C(nf);
+    std::vector<ZeroJob> Z(nf);
+    std::vector<int> nb(nf);
+    int max_ntx = 0;
+    p->poly = true;
+    p->filter = A[0].filter != 0;
+    for (int f = 0; f < nf; f++) {
+        const DetectArgs& a = A[f];
+        if (a.mode == MODE_MASK) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "batched detection from a mask");
+        if ((a.filter != 0) != p->filter) return ipp_set_error(IPP_ERR_INVALID_ARG, "mixed detection filters");
+        const CclLayout L = ccl_layout(a.W, a.H);
+        if (L.nodes >= (int64_t)INT32_MAX) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "frame too large");
+        const CclWs w = ccl_ws(L, a.ws);
+        SubThreshJob& t = T[f];
+        t.W = a.W; t.H = a.H; t.fused = a.mode == MODE_FUSED;
+        t.img = a.img; t.dtype = a.dtype; t.pitch = a.pitch;
+        t.bias_map = a.bias_map; t.bias = a.bias; t.inv_flat = a.inv_flat;
+        t.mesh_bkg = a.mesh_bkg; t.sub = a.sub; t.sub_pitch = a.sub_pitch;
+        t.mesh_rms = a.mesh_rms; t.nx = a.nx; t.ny = a.ny; t.mesh_w = a.mesh_w; t.mesh_h = a.mesh_h;
+        t.k = a.k; t.thresh_abs = a.thresh_abs; t.filter = false;
+        t.mask = (uint32_t*)((unsigned char*)a.ws + L.off[24]);
+        t.mw = (int)cdiv(a.W, 32);
+        Tf[f] = t;
+        Tf[f].fused = false;
+        Tf[f].filter = true;
+        p->poly = p->poly && a.mesh_w >= 16;
+        TileJob& j = J[f];
+        j.W = a.W; j.H = a.H; j.ntx = L.ntx; j.nty = L.nty;
+        j.sub = a.sub; j.sub_pitch = a.sub_pitch; j.mw = t.mw; j.min_area = a.min_area;
+        j.ws = w; j.mask = t.mask;
+        CclJob& c = C[f];
+        c.ws = w; c.ntx = L.ntx; c.nty = L.nty; c.W = a.W; c.H = a.H; c.min_area = a.min_area;
+        c.n_src_dev = a.n_src_dev; c.max_src = a.max_src; c.stats = a.stats; c.labels = a.labels;
+        Z[f].p = w.counters;
+        Z[f].words = L.nty + CT_WORDS;
+        max_ntx = std::max(max_ntx, L.ntx);
+    }
+    for (int f = 0; f < nf; f++) nb[f] = 1;
+    p->zero = ipp_put_stage(hb, Z.data(), nb.data(), nf);
+    for (int f = 0; f < nf; f++) nb[f] = (int)(cdiv(T[f].W, ST_TW) * cdiv(T[f].H, ST_TH));
+    p->thresh = ipp_put_stage(hb, T.data(), nb.data(), nf);
+    if (p->filter) p->filt = ipp_put_stage(hb, Tf.data(), nb.data(), nf);
+    for (int f = 0; f < nf; f++) nb[f] = J[f].ntx * J[f].nty;
+    p->tile = ipp_put_stage(hb, J.data(), nb.data(), nf);
+    for (int f = 0; f < nf; f++) nb[f] = std::min(J[f].ntx * J[f].nty, 8);
+    p->tile_full = ipp_put_stage(hb, J.data(), nb.data(), nf);
+    for (int f = 0; f < nf; f++) nb[f] = C[f].ntx * C[f].nty;
+    p->unions = ipp_put_stage(hb, C.data(), nb.data(), nf);
+    p->count = p->unions;
+    p->fin = p->unions;
+    for (int f = 0; f < nf; f++) nb[f] = std::max(1, (C[f].ntx * C[f].nty + 3) / 4);
+    p->resolve = ipp_put_stage(hb, C.data(), nb.data(), nf);
+    p->emit = p->resolve;
+    for (int f = 0; f < nf; f++) nb[f] = C[f].nty;
+    p->scan = ipp_put_stage(hb, C.data(), nb.data(), nf);
+    p->scan_smem = (size_t)2 * T_TH * max_ntx * sizeof(int);
+    if (p->scan_smem > 200 * 1024) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "frame too wide for the labeling pass");
+    p->nf = nf;
+    return hb.ok() ? IPP_OK : ipp_set_error(IPP_ERR_INVALID_ARG, "batch table overflow");
+}
+
+int ipp_detect_multi_launch(const DetMultiPlan& p, const unsigned char* t, cudaStream_t s) {
+#define IPP_TAB(st, T) reinterpret_cast<const T*>(t + p.st.jobs), reinterpret_cast<const int*>(t + p.st.bs), p.nf
+    cudaFuncSetAttribute(k_tile_label_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileFast));
+    cudaFuncSetAttribute(k_tile_label_full_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileFull));
+    cudaFuncSetAttribute(k_ccl_scan_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.scan_smem);
+    k_zero_multi<<<(unsigned)p.zero.total, 256, 0, s>>>(IPP_TAB(zero, ZeroJob));
+    if (int e = ipp_check_launch("k_zero_multi")) return e;
+    if (p.poly) k_sub_thresh_poly_multi<<<(unsigned)p.thresh.total, ST_THREADS, 0, s>>>(IPP_TAB(thresh, SubThreshJob));
+    else k_sub_thresh_multi<<<(unsigned)p.thresh.total, ST_THREADS, 0, s>>>(IPP_TAB(thresh, SubThreshJob));
+    if (int e = ipp_check_launch("k_sub_thresh_multi")) return e;
+    if (p.filter) {
+        k_sub_thresh_multi<<<(unsigned)p.filt.total, ST_THREADS, 0, s>>>(IPP_TAB(filt, SubThreshJob));
+        if (int e = ipp_check_launch("k_sub_thresh_multi (filtered)")) return e;
+    }
+    k_tile_label_multi<<<(unsigned)p.tile.total, T_THREADS, sizeof(TileFast), s>>>(IPP_TAB(tile, TileJob));
+    if (int e = ipp_check_launch("k_tile_label_multi")) return e;
+    k_tile_label_full_multi<<<(unsigned)p.tile_full.total, T_THREADS, sizeof(TileFull), s>>>(
+        IPP_TAB(tile_full, TileJob));
+    if (int e = ipp_check_launch("k_tile_label_full_multi")) return e;
+    k_ccl_union_multi<<<(unsigned)p.unions.total, G_THREADS, 0, s>>>(IPP_TAB(unions, CclJob));
+    if (int e = ipp_check_launch("k_ccl_union_multi")) return e;
+    k_ccl_resolve_multi<<<(unsigned)p.resolve.total, G_THREADS, 0, s>>>(IPP_TAB(resolve, CclJob));
+    if (int e = ipp_check_launch("k_ccl_resolve_multi")) return e;
+    k_ccl_count_multi<<<(unsigned)p.count.total, G_THREADS, 0, s>>>(IPP_TAB(count, CclJob));
+    if (int e = ipp_check_launch("k_ccl_count_multi")) return e;
+    k_ccl_scan_multi<<<(unsigned)p.scan.total, G_THREADS, p.scan_smem, s>>>(IPP_TAB(scan, CclJob));
+    if (int e = ipp_check_launch("k_ccl_scan_multi")) return e;
+    k_ccl_emit_multi<<<(unsigned)p.emit.total, G_THREADS, 0, s>>>(IPP_TAB(emit, CclJob));
+    if (int e = ipp_check_launch("k_ccl_emit_multi")) return e;
+    k_tile_final_multi<<<(unsigned)p.fin.total, G_THREADS, 0, s>>>(IPP_TAB(fin, CclJob));
+#undef IPP_TAB
+    return ipp_check_launch("k_tile_final_multi");
 }

@@ -1,6 +1,7 @@
 // jobs.cuh -- argument bundles passed from the C ABI (api.cu) to the kernel
 // launchers of each translation unit, and the launchers' declarations.
 #pragma once
+#include <string.h>
 #include "common.cuh"
 
 namespace ipp {
@@ -152,6 +153,77 @@ struct FitJob {
 };
 
 }  // namespace ipp
+
+// ---- the batched form: one launch per stage over a device table of frames ----
+// A stage's table holds one job per frame and bs[nf + 1], the first virtual
+// block of each frame; blocks find their frame by binary search (frame_of).
+namespace ipp {
+struct MeshFilterJob {
+    const float* raw_bkg;
+    const float* raw_rms;
+    float* fill_bkg;
+    float* fill_rms;
+    int nx, ny, fw, fh;
+    float* out_bkg;
+    float* out_rms;
+    int32_t* status_dev;
+};
+
+// host staging of a batch's device table (16-byte aligned entries)
+struct HostBlob {
+    unsigned char* h = nullptr;
+    size_t used = 0, cap = 0;
+    size_t put(const void* p, size_t bytes) {
+        used = (used + 15) & ~(size_t)15;
+        if (used + bytes > cap) { used = cap + 1; return 0; }   // overflow: the caller checks ok()
+        memcpy(h + used, p, bytes);
+        const size_t o = used;
+        used += bytes;
+        return o;
+    }
+    bool ok() const { return used <= cap; }
+};
+
+struct StageRef {
+    size_t jobs = 0, bs = 0;   // offsets of the job array and of bs[] in the table
+    int total = 0;             // virtual blocks over all frames
+};
+
+struct BgMultiPlan { StageRef stats, fill, median; int nf = 0; };
+struct DetMultiPlan {
+    StageRef zero, thresh, filt, tile, tile_full, unions, resolve, count, scan, emit, fin;
+    int nf = 0;
+    bool poly = true, filter = false;
+    size_t scan_smem = 0;
+};
+struct PhotMultiPlan { StageRef cen, ap; int nf = 0; size_t ap_smem = 0; };
+}  // namespace ipp
+
+template <class T>
+ipp::StageRef ipp_put_stage(ipp::HostBlob& hb, const T* jobs, const int* nblk, int nf) {
+    ipp::StageRef r;
+    r.jobs = hb.put(jobs, sizeof(T) * (size_t)nf);
+    int bs[1025];
+    bs[0] = 0;
+    for (int f = 0; f < nf && f < 1024; f++) bs[f + 1] = bs[f] + nblk[f];
+    r.bs = hb.put(bs, sizeof(int) * (size_t)(nf + 1));
+    r.total = bs[nf];
+    return r;
+}
+
+int ipp_extract_jobs(const void* img, int dtype, int64_t W, int64_t H, int64_t pitch, const ipp_calib* cal,
+                     const ipp_bg_params* bp, const ipp_det_params* dp, const ipp_cen_params* cp,
+                     const ipp_phot_params* pp, int32_t max_src, const ipp_catalog_out* out, void* ws,
+                     size_t ws_bytes, ipp::MeshJob* M, ipp::MeshFilterJob* F, ipp::DetectArgs* A, ipp::CenJob* C,
+                     ipp::PhotJob* P);
+int ipp_bg_multi_pack(const ipp::MeshJob* J, const ipp::MeshFilterJob* F, int nf, ipp::HostBlob& hb,
+                      ipp::BgMultiPlan* p);
+int ipp_bg_multi_launch(const ipp::BgMultiPlan& p, const unsigned char* dtab, cudaStream_t s);
+int ipp_detect_multi_pack(const ipp::DetectArgs* A, int nf, ipp::HostBlob& hb, ipp::DetMultiPlan* p);
+int ipp_detect_multi_launch(const ipp::DetMultiPlan& p, const unsigned char* dtab, cudaStream_t s);
+int ipp_phot_multi_pack(const ipp::CenJob* C, const ipp::PhotJob* P, int nf, ipp::HostBlob& hb,
+                        ipp::PhotMultiPlan* p);
+int ipp_phot_multi_launch(const ipp::PhotMultiPlan& p, const unsigned char* dtab, cudaStream_t s);
 
 int ipp_launch_mesh_stats(const ipp::MeshJob& J, cudaStream_t s);
 size_t ipp_spline_ws_bytes(int nx, int ny);

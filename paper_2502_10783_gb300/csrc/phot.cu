@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "jobs.cuh"
 
@@ -132,12 +133,12 @@ __global__ void __launch_bounds__(P_THREADS) k_centroid(CenJob J) {
 // rule as k_centroid; about a third of its instructions per pass.
 constexpr int CR_BOX = 15;  // box of 2R + 1 <= 15 pixels (rad < 7.5)
 
-__global__ void __launch_bounds__(P_THREADS) k_centroid_rows(CenJob J) {
+__device__ __forceinline__ void centroid_rows_body(const CenJob& J, int vb, int nvb) {
     __shared__ float4 colv[P_THREADS / 16][CR_BOX];
     const int lane = threadIdx.x & 31, sub = lane & 15, half = threadIdx.x >> 4;
     const unsigned hmask = 0xffffu << (lane & 16);
-    const int gid = (blockIdx.x * P_THREADS + threadIdx.x) >> 4;
-    const int ng = (gridDim.x * P_THREADS) >> 4;
+    const int gid = (vb * P_THREADS + threadIdx.x) >> 4;
+    const int ng = (nvb * P_THREADS) >> 4;
     const int n = min(*J.n_src_dev, J.max_src);
     const float rad2 = J.rad * J.rad;
     const float inv2s2 = 1.0f / (2.0f * J.sw * J.sw);
@@ -218,6 +219,8 @@ __global__ void __launch_bounds__(P_THREADS) k_centroid_rows(CenJob J) {
         }
     }
 }
+
+__global__ void __launch_bounds__(P_THREADS) k_centroid_rows(CenJob J) { centroid_rows_body(J, blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------- aperture
 // Area of the disk of radius r centred at (cx, cy) -- coordinates relative to
@@ -532,7 +535,7 @@ __device__ __forceinline__ float grid_pixel_area(const float* tab, int R1, int d
     return fminf(fmaxf(area, 0.f), 1.f);
 }
 
-__global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
+__device__ __forceinline__ void aperture_body(const PhotJob& J, int vb, int nvb) {
     extern __shared__ float ann_dyn[];        // [P_WARPS][J.ann_cap] annulus values
     __shared__ float cand[P_WARPS][32];
     __shared__ int hist[P_WARPS][32];
@@ -543,8 +546,8 @@ __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
     __shared__ int16_t l_ap[ANN_CAP], l_ann[ANN_CAP];  // aperture: inner pixels, then edge pixels
     __shared__ int n_lists[3];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int gw = (blockIdx.x * P_THREADS + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * P_THREADS) >> 5;
+    const int gw = (vb * P_THREADS + threadIdx.x) >> 5;
+    const int nw = (nvb * P_THREADS) >> 5;
     const int n = min(*J.n_src_dev, J.max_src);
     float* buf = ann_dyn + (size_t)wib * J.ann_cap;
     const float Wf = (float)(int)J.W, Hf = (float)(int)J.H;
@@ -672,6 +675,19 @@ __global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) {
             if (J.flags) J.flags[s] = fl;
         }
     }
+}
+
+__global__ void __launch_bounds__(P_THREADS) k_aperture(PhotJob J) { aperture_body(J, blockIdx.x, gridDim.x); }
+
+// batched form: the same bodies over a table of frames
+__global__ void __launch_bounds__(P_THREADS) k_centroid_rows_multi(const CenJob* J, const int* bs, int nf) {
+    const int f = frame_of(bs, nf, blockIdx.x);
+    centroid_rows_body(J[f], blockIdx.x - bs[f], bs[f + 1] - bs[f]);
+}
+
+__global__ void __launch_bounds__(P_THREADS) k_aperture_multi(const PhotJob* J, const int* bs, int nf) {
+    const int f = frame_of(bs, nf, blockIdx.x);
+    aperture_body(J[f], blockIdx.x - bs[f], bs[f + 1] - bs[f]);
 }
 
 // Stamp cut: one thread per stamp pixel, grid-stride over the device-resident
@@ -931,11 +947,9 @@ int ipp_launch_centroid(const CenJob& J, cudaStream_t s) {
     return ipp_check_launch("k_centroid");
 }
 
-int ipp_launch_aperture(const PhotJob& J0, cudaStream_t s) {
-    if (J0.r_out > (float)ANN_MAXR) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "r_out above %d px", ANN_MAXR);
-    // annulus buffer per warp: the number of pixels whose centre can lie in the
-    // annulus for a centre within 1/2 px of the anchor (same test as the device list)
-    PhotJob J = J0;
+// annulus buffer per warp: the number of pixels whose centre can lie in the
+// annulus for a centre within 1/2 px of the anchor (same test as the device list)
+static int annulus_cap(const PhotJob& J) {
     const float rin2 = (float)((double)J.r_in * (double)J.r_in), rout2 = (float)((double)J.r_out * (double)J.r_out);
     const int R2 = (int)floorf(J.r_out + 0.5f);
     int cap = 0;
@@ -945,7 +959,13 @@ int ipp_launch_aperture(const PhotJob& J0, cudaStream_t s) {
             const float c = fabsf((float)dj) + 0.5f, d = fabsf((float)di) + 0.5f;
             cap += (a * a + b * b < rout2 * 1.0001f && c * c + d * d >= rin2 * 0.9999f);
         }
-    J.ann_cap = cap + 32;  // slack for host/device rounding differences of the test
+    return cap + 32;  // slack for host/device rounding differences of the test
+}
+
+int ipp_launch_aperture(const PhotJob& J0, cudaStream_t s) {
+    if (J0.r_out > (float)ANN_MAXR) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "r_out above %d px", ANN_MAXR);
+    PhotJob J = J0;
+    J.ann_cap = annulus_cap(J);
     const size_t dyn = (size_t)P_WARPS * J.ann_cap * sizeof(float);
     cudaFuncSetAttribute(k_aperture, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     k_aperture<<<resident_blocks(k_aperture, dyn), P_THREADS, dyn, s>>>(J);
@@ -967,4 +987,37 @@ int ipp_launch_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pitch, 
     k_stamp_cut<<<(unsigned)blocks, P_THREADS, 0, s>>>(sub, W, H, pitch, n_src_dev, max_src, x, y, S, stamps,
                                                         weights, origin, flags);
     return ipp_check_launch("k_stamp_cut");
+}
+
+
+// ---- batched form: tables and launches ----------------------------------------
+// Per frame, blocks in proportion to its area (one per 64 K pixels, at least
+// one), each striding over the frame's device-resident source count.
+int ipp_phot_multi_pack(const CenJob* C, const PhotJob* P, int nf, HostBlob& hb, PhotMultiPlan* p) {
+    if (nf < 1 || nf > 1024) return ipp_set_error(IPP_ERR_INVALID_ARG, "1..1024 frames");
+    std::vector<PhotJob> Pj(P, P + nf);
+    std::vector<int> nb(nf);
+    for (int f = 0; f < nf; f++) {
+        const int R = (int)floorf(C[f].rad + 0.5f);
+        if (2 * R + 1 > CR_BOX) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "batched centroid window above 15 px");
+        if (P[f].r_out > (float)ANN_MAXR) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "r_out above %d px", ANN_MAXR);
+        Pj[f].ann_cap = annulus_cap(P[f]);
+        if (Pj[f].ann_cap != Pj[0].ann_cap) return ipp_set_error(IPP_ERR_INVALID_ARG, "mixed aperture params");
+        nb[f] = (int)std::max<int64_t>(1, (C[f].W * C[f].H) >> 16);
+    }
+    p->cen = ipp_put_stage(hb, C, nb.data(), nf);
+    p->ap = ipp_put_stage(hb, Pj.data(), nb.data(), nf);
+    p->ap_smem = (size_t)P_WARPS * Pj[0].ann_cap * sizeof(float);
+    p->nf = nf;
+    return hb.ok() ? IPP_OK : ipp_set_error(IPP_ERR_INVALID_ARG, "batch table overflow");
+}
+
+int ipp_phot_multi_launch(const PhotMultiPlan& p, const unsigned char* t, cudaStream_t s) {
+    k_centroid_rows_multi<<<(unsigned)p.cen.total, P_THREADS, 0, s>>>(
+        reinterpret_cast<const CenJob*>(t + p.cen.jobs), reinterpret_cast<const int*>(t + p.cen.bs), p.nf);
+    if (int e = ipp_check_launch("k_centroid_rows_multi")) return e;
+    cudaFuncSetAttribute(k_aperture_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.ap_smem);
+    k_aperture_multi<<<(unsigned)p.ap.total, P_THREADS, p.ap_smem, s>>>(
+        reinterpret_cast<const PhotJob*>(t + p.ap.jobs), reinterpret_cast<const int*>(t + p.ap.bs), p.nf);
+    return ipp_check_launch("k_aperture_multi");
 }
