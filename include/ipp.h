@@ -758,9 +758,12 @@ int ipp_batch_launch(ipp_batch b, void* stream);
  * of every frame (the same as ipp_extract's) are packed into a device table at
  * the head of ws; each stage is a single launch over the frames' blocks, a block
  * finding its frame by binary search over the frames' first blocks, and runs the
- * per-frame kernel body -- so the outputs equal ipp_extract's bit for bit and a
- * batch of n frames costs ~17 launches.  Frames keep separate scratch (ws holds
- * them one after another), so every frame's stages can run at once.
+ * per-frame kernel body -- so the outputs equal ipp_extract's bit for bit.  The
+ * frames are split into one group per lane of the runner (largest first, to the
+ * least-loaded lane); each group is a table of its own whose ~17 launches go to
+ * the lane's stream, so the stages of different groups overlap (a memory-bound
+ * stage of one group beside a compute-bound one of another).  Frames keep
+ * separate scratch (ws holds them one after another).
  *   ipp_batch_table_workspace_size  bytes of ws for these frames (the table plus
  *                                   each frame's ipp_extract workspace)
  *   ipp_batch_table_extract         enqueues the batch on `stream`; the table is

@@ -2,11 +2,11 @@
 //   streams: a runner that spreads frames over its own CUDA streams (largest
 //     frames first, each to the least-loaded lane), fork/join with events around
 //     the caller's stream, and a lane-count autotuner;
-//   table: one launch per stage for all frames -- a device table holds every
-//     frame's jobs, each block finds its frame by binary search over the
-//     frames' first blocks and runs the per-frame kernel body on it, so a batch
-//     of n frames costs the same ~17 launches as one frame and the stages'
-//     tails of small frames fill in behind large ones.
+//   table: one launch per stage for a group of frames -- a device table holds
+//     every frame's jobs, each block finds its frame by binary search over the
+//     frames' first blocks and runs the per-frame kernel body on it; the frames
+//     are split into one group per lane, each group's ~17 launches on the
+//     lane's stream, so stages of different groups overlap.
 // Either form can be recorded as one CUDA graph.
 #include <algorithm>
 #include <cstdio>
@@ -219,15 +219,40 @@ extern "C" int ipp_batch_autotune(const ipp_frame_desc* frames, int32_t n, const
 // ---- table form -----------------------------------------------------------------
 namespace {
 
-size_t table_bytes(int32_t n) { return a256((size_t)n * 6144 + 65536); }
+size_t table_bytes(int32_t n) { return a256((size_t)n * 6144 + 65536 * IPP_BATCH_MAX_LANES); }
 
 // Builds the batch's table in the runner's pinned staging buffer, uploads it
 // to the head of ws unless it equals the table uploaded there last, and
 // enqueues the stages.  upload_only: stop after the upload (capture set-up).
+struct TablePlan {
+    int nf = 0;
+    ipp::BgMultiPlan bg;
+    ipp::DetMultiPlan det;
+    ipp::PhotMultiPlan ph;
+};
+
+// the groups' stages, each on its lane's stream, forked from and joined to s
+int launch_table(ipp_batch b, const TablePlan* plans, const unsigned char* dtab, cudaStream_t s) {
+    cudaError_t e = cudaEventRecord(b->fork, s);
+    for (int l = 0; l < b->lanes && e == cudaSuccess; l++) e = cudaStreamWaitEvent(b->st[l], b->fork, 0);
+    if (e != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "table fork: %s", cudaGetErrorString(e));
+    int status = IPP_OK;
+    for (int l = 0; l < b->lanes && status == IPP_OK; l++) {
+        if (plans[l].nf == 0) continue;
+        status = ipp_bg_multi_launch(plans[l].bg, dtab, b->st[l]);
+        if (status == IPP_OK) status = ipp_detect_multi_launch(plans[l].det, dtab, b->st[l]);
+        if (status == IPP_OK) status = ipp_phot_multi_launch(plans[l].ph, dtab, b->st[l]);
+    }
+    for (int l = 0; l < b->lanes; l++) {   // joined also after an error (a capture stays well formed)
+        cudaEventRecord(b->join[l], b->st[l]);
+        cudaStreamWaitEvent(s, b->join[l], 0);
+    }
+    return status;
+}
+
 int run_table(ipp_batch b, const ipp_frame_desc* f, int32_t n, const ipp_bg_params* bp, const ipp_det_params* dp,
               const ipp_cen_params* cp, const ipp_phot_params* pp, int32_t max_src, void* ws, size_t ws_bytes,
-              cudaStream_t s, bool upload_only, ipp::BgMultiPlan* bg_out, ipp::DetMultiPlan* det_out,
-              ipp::PhotMultiPlan* ph_out) {
+              cudaStream_t s, bool upload_only, TablePlan* plans) {
     using namespace ipp;
     int64_t mw = 0, mh = 0;
     if (int e = check_frames(f, n, &mw, &mh)) return e;
@@ -265,16 +290,30 @@ int run_table(ipp_batch b, const ipp_frame_desc* f, int32_t n, const ipp_bg_para
         if (cudaMallocHost(&b->stage, tb) != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "pinned table staging");
         b->stage_cap = tb;
     }
+    // frames in groups, one per lane (largest first to the least-loaded lane),
+    // each group a table of its own on the lane's stream: the stages of one
+    // group overlap those of the others
+    const std::vector<int> lane = assign_lanes(f, n, b->lanes);
     HostBlob hb;
     hb.h = b->stage;
     hb.cap = tb;
-    BgMultiPlan bgp;
-    DetMultiPlan dtp;
-    PhotMultiPlan php;
-    if (int e = ipp_bg_multi_pack(M.data(), F.data(), n, hb, &bgp)) return e;
-    if (int e = ipp_detect_multi_pack(A.data(), n, hb, &dtp)) return e;
-    if (int e = ipp_phot_multi_pack(C.data(), P.data(), n, hb, &php)) return e;
-    const unsigned char* dtab = static_cast<const unsigned char*>(ws);
+    for (int l = 0; l < b->lanes; l++) {
+        std::vector<MeshJob> gM;
+        std::vector<MeshFilterJob> gF;
+        std::vector<DetectArgs> gA;
+        std::vector<CenJob> gC;
+        std::vector<PhotJob> gP;
+        for (int i = 0; i < n; i++) {
+            if (lane[i] != l) continue;
+            gM.push_back(M[i]); gF.push_back(F[i]); gA.push_back(A[i]); gC.push_back(C[i]); gP.push_back(P[i]);
+        }
+        TablePlan& tp = plans[l];
+        tp.nf = (int)gM.size();
+        if (tp.nf == 0) continue;
+        if (int e = ipp_bg_multi_pack(gM.data(), gF.data(), tp.nf, hb, &tp.bg)) return e;
+        if (int e = ipp_detect_multi_pack(gA.data(), tp.nf, hb, &tp.det)) return e;
+        if (int e = ipp_phot_multi_pack(gC.data(), gP.data(), tp.nf, hb, &tp.ph)) return e;
+    }
     const bool same = b->last_dev == ws && b->last.size() == hb.used && memcmp(b->last.data(), hb.h, hb.used) == 0;
     if (!same) {
         cudaError_t e = cudaMemcpyAsync(ws, hb.h, hb.used, cudaMemcpyHostToDevice, s);
@@ -284,13 +323,8 @@ int run_table(ipp_batch b, const ipp_frame_desc* f, int32_t n, const ipp_bg_para
         b->last.assign(hb.h, hb.h + hb.used);
         b->last_dev = ws;
     }
-    if (bg_out) *bg_out = bgp;
-    if (det_out) *det_out = dtp;
-    if (ph_out) *ph_out = php;
     if (upload_only) return IPP_OK;
-    if (int e = ipp_bg_multi_launch(bgp, dtab, s)) return e;
-    if (int e = ipp_detect_multi_launch(dtp, dtab, s)) return e;
-    return ipp_phot_multi_launch(php, dtab, s);
+    return launch_table(b, plans, static_cast<const unsigned char*>(ws), s);
 }
 
 int ensure_stage_event(ipp_batch b) {
@@ -317,8 +351,8 @@ extern "C" int ipp_batch_table_extract(ipp_batch b, const ipp_frame_desc* frames
                                        int32_t max_src, void* ws, size_t ws_bytes, void* stream) {
     if (!b) return ipp_set_error(IPP_ERR_INVALID_ARG, "batch runner NULL");
     if (int e = ensure_stage_event(b)) return e;
-    return run_table(b, frames, n, bp, dp, cp, pp, max_src, ws, ws_bytes, (cudaStream_t)stream, false, nullptr,
-                     nullptr, nullptr);
+    TablePlan plans[IPP_BATCH_MAX_LANES];
+    return run_table(b, frames, n, bp, dp, cp, pp, max_src, ws, ws_bytes, (cudaStream_t)stream, false, plans);
 }
 
 extern "C" int ipp_batch_table_capture(ipp_batch b, const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp,
@@ -329,17 +363,12 @@ extern "C" int ipp_batch_table_capture(ipp_batch b, const ipp_frame_desc* frames
     if (int e = ensure_stage_event(b)) return e;
     cudaStream_t s = (cudaStream_t)stream;
     // the table is uploaded before the capture, so the graph holds only the stages
-    ipp::BgMultiPlan bgp;
-    ipp::DetMultiPlan dtp;
-    ipp::PhotMultiPlan php;
-    if (int e = run_table(b, frames, n, bp, dp, cp, pp, max_src, ws, ws_bytes, s, true, &bgp, &dtp, &php)) return e;
+    TablePlan plans[IPP_BATCH_MAX_LANES];
+    if (int e = run_table(b, frames, n, bp, dp, cp, pp, max_src, ws, ws_bytes, s, true, plans)) return e;
     if (n == 0) return IPP_OK;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return ipp_set_error(IPP_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
-    const unsigned char* dtab = static_cast<const unsigned char*>(ws);
-    int status = ipp_bg_multi_launch(bgp, dtab, s);
-    if (status == IPP_OK) status = ipp_detect_multi_launch(dtp, dtab, s);
-    if (status == IPP_OK) status = ipp_phot_multi_launch(php, dtab, s);
+    const int status = launch_table(b, plans, static_cast<const unsigned char*>(ws), s);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s, &g);
     if (status != IPP_OK) {

@@ -23,6 +23,8 @@
 // patterns, the MAD on the FP64 differences the definition takes.
 #include <math.h>
 
+#include <algorithm>
+
 #include "jobs.cuh"
 
 namespace ipp {
@@ -85,34 +87,53 @@ __device__ unsigned long long block_min_u64(unsigned long long v, unsigned long 
     return m;
 }
 
-// Key of a region element for the order statistics: mode 0, the template value
-// (fkey, in the upper 32 bits); mode 1, the FP64 |R - med| (its bit pattern,
-// monotone for non-negative doubles).  Non-finite values have no key.
-__device__ __forceinline__ bool stamp_key(const StampRegion& g, int t, int mode, double med, unsigned long long* k) {
+// Keys of a region's finite values for the order statistics, as unsigned
+// 64-bit integers ordered like the quantities they stand for:
+//   mode 0: the value, fkey(v);
+//   mode 1: |v - med| exactly, as the integer |v 2^-e0 - med 2^-e0| -- every value
+//     and med are multiples of 2^e0 (e0: one below the smallest ulp in the
+//     region), so the difference is exact and its FP64 rounding is the FP64
+//     subtraction's, without the narrow FP64 pipe in the per-element work;
+//   mode 2: the bit pattern of the FP64 |v - med| (when the region's range does
+//     not fit 62 bits at scale 2^e0).
+struct KeySpec {
+    int mode;
+    int e0;
+    double med;
+    long long imed;
+};
+
+__device__ __forceinline__ bool stamp_key(const StampRegion& g, int t, const KeySpec& ks, unsigned long long* k) {
     int x, y;
     const float v = reg_r(g, t, &x, &y);
     if (!isfinite(v)) return false;
-    if (mode == 0) *k = (unsigned long long)fkey(v) << 32;
-    else *k = (unsigned long long)__double_as_longlong(fabs((double)v - med));
+    if (ks.mode == 0) {
+        *k = fkey(v);
+    } else if (ks.mode == 1) {
+        const long long d = __float2ll_rz(ldexpf(v, -ks.e0)) - ks.imed;
+        *k = (unsigned long long)(d < 0 ? -d : d);
+    } else {
+        *k = (unsigned long long)__double_as_longlong(fabs((double)v - ks.med));
+    }
     return true;
 }
 
-// The k-th smallest key (0-based) among the region's keys of the given mode:
-// radix selection, 8 bits a pass from the top, per-warp histograms in shared
-// memory (hist: SS_W x 256 counters).  Mode 0 needs the upper 32 bits only.
-__device__ unsigned long long block_select(const StampRegion& g, int mode, double med, long long k,
-                                           unsigned int* hist, long long* red, int* sdig, long long* sbelow) {
-    unsigned long long prefix = 0;
-    const int lo_shift = mode == 0 ? 32 : 0;
+// The k-th smallest key (0-based) of the region: radix selection, 8 bits a
+// pass from bit top + 7 down, every key sharing the bits above top with
+// prefix0; per-warp histograms in shared memory (hist: SS_W x 256 counters).
+__device__ unsigned long long block_select(const StampRegion& g, const KeySpec& ks, long long k, int top,
+                                           unsigned long long prefix0, unsigned int* hist, int* sdig,
+                                           long long* sbelow) {
+    unsigned long long prefix = prefix0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int shift = 56; shift >= lo_shift; shift -= 8) {
+    for (int shift = top; shift >= 0; shift -= 8) {
         for (int t = threadIdx.x; t < SS_W * 256; t += SS_T) hist[t] = 0;
         __syncthreads();
         for (int base = 0; base < g.n; base += SS_T) {
             const int t = base + threadIdx.x;
             unsigned long long key = 0;
-            bool ok = t < g.n && stamp_key(g, t, mode, med, &key);
-            if (ok && shift < 56) ok = (key >> (shift + 8)) == prefix;
+            bool ok = t < g.n && stamp_key(g, t, ks, &key);
+            if (ok && shift + 8 < 64) ok = (key >> (shift + 8)) == prefix;
             const unsigned dig = ok ? (unsigned)((key >> shift) & 255u) : 256u;
             const unsigned m = __match_any_sync(0xffffffffu, dig);
             if (ok && lane == __ffs(m) - 1) atomicAdd(&hist[warp * 256 + dig], (unsigned)__popc(m));
@@ -152,18 +173,17 @@ __device__ unsigned long long block_select(const StampRegion& g, int mode, doubl
         k -= *sbelow;
         __syncthreads();
     }
-    (void)red;
-    return prefix << lo_shift;
+    return prefix;
 }
 
 // (count of keys <= kk, smallest key > kk) over the region
-__device__ void block_count_next(const StampRegion& g, int mode, double med, unsigned long long kk, long long* cnt,
+__device__ void block_count_next(const StampRegion& g, const KeySpec& ks, unsigned long long kk, long long* cnt,
                                  unsigned long long* next, long long* red, unsigned long long* redu) {
     long long c = 0;
     unsigned long long nx = ~0ull;
     for (int t = threadIdx.x; t < g.n; t += SS_T) {
         unsigned long long key;
-        if (!stamp_key(g, t, mode, med, &key)) continue;
+        if (!stamp_key(g, t, ks, &key)) continue;
         if (key <= kk) c++;
         else if (key < nx) nx = key;
     }
@@ -171,16 +191,21 @@ __device__ void block_count_next(const StampRegion& g, int mode, double med, uns
     *next = block_min_u64(nx, redu);
 }
 
-// the two middle order statistics (k0 = (n - 1) / 2, k1 = n / 2) as keys
-__device__ void block_middle(const StampRegion& g, int mode, double med, long long n, unsigned int* hist,
-                             long long* red, unsigned long long* redu, int* sdig, long long* sbelow,
-                             unsigned long long* a, unsigned long long* b) {
+// the two middle order statistics (k0 = (n - 1) / 2, k1 = n / 2) as keys, for
+// keys in [kmin, kmax]: the radix passes start at the highest byte where kmin
+// and kmax differ
+__device__ void block_middle(const StampRegion& g, const KeySpec& ks, long long n, unsigned long long kmin,
+                             unsigned long long kmax, unsigned int* hist, long long* red, unsigned long long* redu,
+                             int* sdig, long long* sbelow, unsigned long long* a, unsigned long long* b) {
     const long long k0 = (n - 1) / 2, k1 = n / 2;
-    *a = block_select(g, mode, med, k0, hist, red, sdig, sbelow);
+    const unsigned long long dif = kmin ^ kmax;
+    const int top = dif ? ((63 - __clzll((long long)dif)) & ~7) : 0;
+    const unsigned long long prefix0 = top + 8 < 64 ? kmin >> (top + 8) : 0ull;
+    *a = block_select(g, ks, k0, top, prefix0, hist, sdig, sbelow);
     if (k1 == k0) { *b = *a; return; }
     long long cle;
     unsigned long long nx;
-    block_count_next(g, mode, med, *a, &cle, &nx, red, redu);
+    block_count_next(g, ks, *a, &cle, &nx, red, redu);
     *b = cle > k1 ? *a : nx;
 }
 
@@ -212,24 +237,56 @@ __global__ void __launch_bounds__(SS_T) k_sub_stamps(const float* I, const float
     g.rw = (int)((sx + 1) * W / nsx) - g.x0;
     g.rh = (int)((sy + 1) * H / nsy) - g.y0;
     g.n = g.rw * g.rh;
-    // the finite values: count, median (Eq. 1's even-count mean of the middle pair)
+    // the finite values: count, key range, smallest ulp exponent, largest |v|
     long long c = 0;
+    unsigned long long kmin = ~0ull, kmax = 0, emin = ~0ull, amax = 0;
     for (int t = threadIdx.x; t < g.n; t += SS_T) {
         int x, y;
-        if (isfinite(reg_r(g, t, &x, &y))) c++;
+        const float v = reg_r(g, t, &x, &y);
+        if (!isfinite(v)) continue;
+        c++;
+        const unsigned long long k = fkey(v);
+        kmin = k < kmin ? k : kmin;
+        kmax = k > kmax ? k : kmax;
+        const uint32_t bits = __float_as_uint(v) & 0x7fffffffu, be = bits >> 23;
+        const unsigned long long ue = be ? be : 1u;      // ulp 2^(be - 150), denormals as be = 1
+        emin = ue < emin ? ue : emin;
+        amax = bits > amax ? bits : amax;
     }
     const long long n = block_sum_ll(c, red);
     if (n == 0) {
         if (threadIdx.x == 0) reg_out[blockIdx.x] = make_int2(-1, -1);
         return;
     }
+    kmin = block_min_u64(kmin, redu);
+    kmax = block_max_u64(kmax, redu);
+    emin = block_min_u64(emin, redu);
+    amax = block_max_u64(amax, redu);
+    // median (Eq. 1's even-count mean of the middle pair)
+    KeySpec ks{0, 0, 0.0, 0};
     unsigned long long ka, kb;
-    block_middle(g, 0, 0.0, n, hist, red, redu, &sdig, &sbelow, &ka, &kb);
-    const double va = (double)fkey_inv((uint32_t)(ka >> 32)), vb = (double)fkey_inv((uint32_t)(kb >> 32));
+    block_middle(g, ks, n, kmin, kmax, hist, red, redu, &sdig, &sbelow, &ka, &kb);
+    const double va = (double)fkey_inv((uint32_t)ka), vb = (double)fkey_inv((uint32_t)kb);
     const double med = (n & 1) ? vb : __dmul_rn(0.5, __dadd_rn(va, vb));
-    block_middle(g, 1, med, n, hist, red, redu, &sdig, &sbelow, &ka, &kb);
-    const double da = __longlong_as_double((long long)ka), db = __longlong_as_double((long long)kb);
-    const double mad = (n & 1) ? db : __dmul_rn(0.5, __dadd_rn(da, db));
+    // MAD: exact integer differences at scale 2^e0 when they fit 62 bits
+    ks.med = med;
+    ks.e0 = (int)emin - 150 - 1;
+    const double span = ldexp((double)__uint_as_float((uint32_t)amax) + fabs(med), -ks.e0);
+    double mad;
+    if (span < 4.6e18) {
+        ks.mode = 1;
+        ks.imed = __double2ll_rz(ldexp(med, -ks.e0));
+        const unsigned long long top =
+            (unsigned long long)ldexp((double)__uint_as_float((uint32_t)amax) + fabs(med), -ks.e0) + 1ull;
+        block_middle(g, ks, n, 0ull, top, hist, red, redu, &sdig, &sbelow, &ka, &kb);
+        const double da = ldexp((double)ka, ks.e0), db = ldexp((double)kb, ks.e0);
+        mad = (n & 1) ? db : __dmul_rn(0.5, __dadd_rn(da, db));
+    } else {
+        ks.mode = 2;
+        block_middle(g, ks, n, 0ull, ~0ull, hist, red, redu, &sdig, &sbelow, &ka, &kb);
+        const double da = __longlong_as_double((long long)ka), db = __longlong_as_double((long long)kb);
+        mad = (n & 1) ? db : __dmul_rn(0.5, __dadd_rn(da, db));
+    }
     const double sgm = __dmul_rn(1.4826, mad);
     const double thr = __dadd_rn(med, __dmul_rn(nsig, sgm));
     // the brightest eligible pixel: arg-max rounds over the keys below the last
@@ -497,36 +554,41 @@ __global__ void __launch_bounds__(256) k_sub_assemble(SubFitJob J) {
     }
 }
 
-// Cholesky solve of AtA x = Atb in place (one block; L in the lower triangle,
-// the solution in Atb).  Column by column: warp 0 forms the pivot, then the
-// warps take the rows below it, the lanes splitting each dot product.  A pivot
-// that is not positive sets *status = 1 and leaves the system unsolved.
-__global__ void __launch_bounds__(1024) k_sub_chol(double* A, double* b, int n, double* x64, float* x32,
-                                                   int32_t* status) {
-    __shared__ double piv;
+// Cholesky solve of AtA x = Atb in place, blocked and right-looking: for each
+// panel of CB columns, the diagonal block is factored in shared memory
+// (k_chol_diag), the rows below it are solved against it (k_chol_trsm, a warp
+// per row), and the trailing lower triangle takes the panel's rank-CB update
+// (k_chol_syrk, a 32 x 32 tile per block).  Then the two triangular solves,
+// CB rows at a time (k_chol_solve).  FP64 throughout.  A pivot that is not
+// positive sets *status = 1; the later kernels then leave everything as is.
+constexpr int CB = 32;
+
+__global__ void k_chol_init(int32_t* status) { *status = 0; }
+
+__global__ void __launch_bounds__(256) k_chol_diag(double* A, int n, int k0, int32_t* status) {
+    __shared__ double D[CB][CB + 1];
     __shared__ int fail;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (__ldcg(status)) return;
+    const int b = min(CB, n - k0);
+    for (int t = threadIdx.x; t < b * b; t += 256) {
+        const int i = t / b, j = t - i * b;
+        D[i][j] = A[(size_t)(k0 + i) * n + k0 + j];
+    }
     if (threadIdx.x == 0) fail = 0;
-    for (int j = 0; j < n; j++) {
-        if (warp == 0) {
-            double s = 0.0;
-            for (int k = lane; k < j; k += 32) s = fma(A[(size_t)j * n + k], A[(size_t)j * n + k], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) {
-                const double d = A[(size_t)j * n + j] - s;
-                if (!(d > 0.0)) fail = 1;
-                piv = d > 0.0 ? sqrt(d) : 1.0;
-                A[(size_t)j * n + j] = piv;
-            }
+    __syncthreads();
+    for (int j = 0; j < b; j++) {
+        if (threadIdx.x == 0) {
+            const double d = D[j][j];
+            if (!(d > 0.0)) fail = 1;
+            D[j][j] = d > 0.0 ? sqrt(d) : 1.0;
         }
         __syncthreads();
         if (fail) break;
-        const double d = piv;
-        for (int i = j + 1 + warp; i < n; i += 32) {
-            double s = 0.0;
-            for (int k = lane; k < j; k += 32) s = fma(A[(size_t)i * n + k], A[(size_t)j * n + k], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) A[(size_t)i * n + j] = (A[(size_t)i * n + j] - s) / d;
+        for (int i = j + 1 + threadIdx.x; i < b; i += 256) D[i][j] /= D[j][j];
+        __syncthreads();
+        for (int t = threadIdx.x; t < b * b; t += 256) {          // trailing update inside the block
+            const int i = t / b, c = t - i * b;
+            if (i > j && c > j && c <= i) D[i][c] -= D[i][j] * D[c][j];
         }
         __syncthreads();
     }
@@ -534,26 +596,118 @@ __global__ void __launch_bounds__(1024) k_sub_chol(double* A, double* b, int n, 
         if (threadIdx.x == 0) *status = 1;
         return;
     }
-    if (warp != 0) return;
-    for (int i = 0; i < n; i++) {                          // L y = b
-        double s = 0.0;
-        for (int k = lane; k < i; k += 32) s = fma(A[(size_t)i * n + k], b[k], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) b[i] = (b[i] - s) / A[(size_t)i * n + i];
-        __syncwarp();
+    for (int t = threadIdx.x; t < b * b; t += 256) {
+        const int i = t / b, j = t - i * b;
+        if (j <= i) A[(size_t)(k0 + i) * n + k0 + j] = D[i][j];
     }
-    for (int i = n - 1; i >= 0; i--) {                     // L' x = y
-        double s = 0.0;
-        for (int k = i + 1 + lane; k < n; k += 32) s = fma(A[(size_t)k * n + i], b[k], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) b[i] = (b[i] - s) / A[(size_t)i * n + i];
-        __syncwarp();
+}
+
+// rows i >= k0 + CB: L21[i] = A21[i] L11^-T, one warp per row (lane j holds column j)
+__global__ void __launch_bounds__(256) k_chol_trsm(double* A, int n, int k0, const int32_t* status) {
+    __shared__ double L[CB][CB + 1];
+    if (__ldcg(status)) return;
+    const int b = min(CB, n - k0);
+    for (int t = threadIdx.x; t < b * b; t += 256) {
+        const int i = t / b, j = t - i * b;
+        L[i][j] = j <= i ? A[(size_t)(k0 + i) * n + k0 + j] : 0.0;
     }
-    for (int i = lane; i < n; i += 32) {
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = k0 + b + blockIdx.x * 8 + warp; i < n; i += gridDim.x * 8) {
+        double a = lane < b ? A[(size_t)i * n + k0 + lane] : 0.0;
+        double x = 0.0;
+        for (int j = 0; j < b; j++) {
+            const double xj = __shfl_sync(0xffffffffu, lane == j ? a / L[j][j] : 0.0, j);
+            if (lane == j) x = xj;
+            if (lane > j) a -= xj * L[lane][j];
+        }
+        if (lane < b) A[(size_t)i * n + k0 + lane] = x;
+    }
+}
+
+// trailing update of the lower triangle from row / column k0 + CB on: tile
+// (ti, tc), ti >= tc, of 32 x 32, A[i][c] -= sum_m L[i][k0 + m] L[c][k0 + m]
+__global__ void __launch_bounds__(256) k_chol_syrk(double* A, int n, int k0, const int32_t* status) {
+    __shared__ double Li[32][CB + 1], Lc[32][CB + 1];
+    if (__ldcg(status)) return;
+    const int r0 = k0 + CB;
+    const int t = blockIdx.x;
+    int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while (ti * (ti + 1) / 2 > t) ti--;
+    while ((ti + 1) * (ti + 2) / 2 <= t) ti++;
+    const int tc = t - ti * (ti + 1) / 2;
+    const int i0 = r0 + ti * 32, c0 = r0 + tc * 32;
+    for (int q = threadIdx.x; q < 32 * CB; q += 256) {
+        const int r = q / CB, m = q - r * CB;
+        Li[r][m] = i0 + r < n ? A[(size_t)(i0 + r) * n + k0 + m] : 0.0;
+        Lc[r][m] = c0 + r < n ? A[(size_t)(c0 + r) * n + k0 + m] : 0.0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+        const int r = q >> 5, c = q & 31;
+        const int i = i0 + r, cc = c0 + c;
+        if (i >= n || cc >= n || cc > i) continue;
+        double acc = 0.0;
+        for (int m = 0; m < CB; m++) acc = fma(Li[r][m], Lc[c][m], acc);
+        A[(size_t)i * n + cc] -= acc;
+    }
+}
+
+// L y = b, then L' x = y, CB rows at a time: the block's warps first take the
+// dot products with the part already solved (a warp per row), then warp 0
+// solves the CB x CB triangle.  The solution goes to b (and x64 / x32).
+__global__ void __launch_bounds__(1024) k_chol_solve(const double* A, double* b, int n, double* x64, float* x32,
+                                                     const int32_t* status) {
+    __shared__ double part[CB];
+    if (__ldcg(status)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r0 = 0; r0 < n; r0 += CB) {                 // forward
+        const int bsz = min(CB, n - r0);
+        if (warp < bsz) {
+            const int i = r0 + warp;
+            double s = 0.0;
+            for (int k = lane; k < r0; k += 32) s = fma(A[(size_t)i * n + k], b[k], s);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) part[warp] = b[i] - s;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double y = lane < bsz ? part[lane] : 0.0, x = 0.0;
+            for (int j = 0; j < bsz; j++) {
+                const double xj = __shfl_sync(0xffffffffu, lane == j ? y / A[(size_t)(r0 + j) * n + r0 + j] : 0.0, j);
+                if (lane == j) x = xj;
+                if (lane > j && lane < bsz) y -= A[(size_t)(r0 + lane) * n + r0 + j] * xj;
+            }
+            if (lane < bsz) b[r0 + lane] = x;
+        }
+        __syncthreads();
+    }
+    const int nblk = (n + CB - 1) / CB;
+    for (int blk = nblk - 1; blk >= 0; blk--) {          // backward with L'
+        const int r0 = blk * CB, bsz = min(CB, n - r0);
+        if (warp < bsz) {
+            const int i = r0 + warp;
+            double s = 0.0;
+            for (int k = r0 + bsz + lane; k < n; k += 32) s = fma(A[(size_t)k * n + i], b[k], s);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) part[warp] = b[i] - s;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double y = lane < bsz ? part[lane] : 0.0, x = 0.0;
+            for (int j = bsz - 1; j >= 0; j--) {
+                const double xj = __shfl_sync(0xffffffffu, lane == j ? y / A[(size_t)(r0 + j) * n + r0 + j] : 0.0, j);
+                if (lane == j) x = xj;
+                if (lane < j) y -= A[(size_t)(r0 + j) * n + r0 + lane] * xj;
+            }
+            if (lane < bsz) b[r0 + lane] = x;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += 1024) {
         if (x64) x64[i] = b[i];
         if (x32) x32[i] = (float)b[i];
     }
-    if (lane == 0) *status = 0;
 }
 
 }  // namespace ipp
@@ -663,8 +817,21 @@ int ipp_launch_sub_normal(const float* I, const float* R, int64_t W, int64_t H, 
 
 int ipp_launch_sub_solve(double* AtA, double* Atb, int np, double* coef64, float* coef, int32_t* status,
                          cudaStream_t s) {
-    k_sub_chol<<<1, 1024, 0, s>>>(AtA, Atb, np, coef64, coef, status);
-    return ipp_check_launch("k_sub_chol");
+    k_chol_init<<<1, 1, 0, s>>>(status);
+    if (int e = ipp_check_launch("k_chol_init")) return e;
+    for (int k0 = 0; k0 < np; k0 += CB) {
+        k_chol_diag<<<1, 256, 0, s>>>(AtA, np, k0, status);
+        if (int e = ipp_check_launch("k_chol_diag")) return e;
+        const int rest = np - k0 - CB;
+        if (rest <= 0) break;
+        k_chol_trsm<<<(unsigned)std::min((rest + 7) / 8, 152), 256, 0, s>>>(AtA, np, k0, status);
+        if (int e = ipp_check_launch("k_chol_trsm")) return e;
+        const int nt = (rest + 31) / 32;
+        k_chol_syrk<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(AtA, np, k0, status);
+        if (int e = ipp_check_launch("k_chol_syrk")) return e;
+    }
+    k_chol_solve<<<1, 1024, 0, s>>>(AtA, Atb, np, coef64, coef, status);
+    return ipp_check_launch("k_chol_solve");
 }
 
 int ipp_launch_sub_fit(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int nsx, int nsy,
