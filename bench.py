@@ -596,7 +596,8 @@ def main():
                    "workload": "survey_4k subtracted frame against a copy, 21 x 21 kernel, 49 basis functions",
                    "fit_ms": stages["sub_fit"], "fit_status": sub_fit_status,
                    "fit_kernels": "k_sub_stamps + k_sub_compact + k_sub_conv + k_sub_gram + k_sub_assemble + "
-                                  "k_sub_chol (FP64; 10 x 10 regions, 297 unknowns)"}
+                                  "blocked Cholesky k_chol_diag / k_chol_trsm / k_chol_syrk per 32-column panel + "
+                                  "k_chol_solve (FP64; 10 x 10 regions, 297 unknowns)"}
     gb = 8 * W * H / (stages["reproject"] / 1e3) / 1e9
     align = {"ms": stages["align"], "reproject_ms": stages["reproject"], "reproject_bytes_per_px": 8,
              "reproject_achieved_gbs": gb, "reproject_frac_of_measured_hbm": gb / hbm,
