@@ -44,7 +44,8 @@ struct CleanWs {
     float2* blo;                // the barycentre's remainders: cx + lo.x, cy + lo.y to ~2^-48
     float4* ell;                // y2 / (det a^2), -2 xy / (det a^2), x2 / (det a^2), threshold at the peak
     int32_t* into;              // merge target
-    int32_t* num;               // new label of a kept object
+    int32_t* num;               // the kept object a label's merges lead to
+    int32_t* tcount;            // kept objects per tile of 1024 labels
     unsigned long long* skey;   // [P] brightness sort keys
     CleanPart* part;            // [nchunk][P] per-chunk partials of the test
     int P;                      // sort size (a power of two >= max_obj, >= 2048)
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(CL_T) k_bitonic_global(unsigned long long* key
 // In brightness order the objects brighter than the one of rank r are the ranks
 // 0..r-1.  Block (bi, bc): ranks [256 bi, 256 bi + 256) against the ranks of chunk
 // bc ([CL_JC bc, CL_JC (bc + 1))), staged through shared memory 256 at a time.
-// Each thread sums its models in rank order with a compensated (two-sum) FP32
+// Each thread sums its models in rank order with a compensated (Kahan) FP32
 // accumulator and keeps the largest model (ties: the smaller label); the chunks'
 // partials are combined in chunk order by k_clean_decide, so the result does not
 // depend on the scheduling.
@@ -267,11 +268,20 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
     hi = t;
 }
 
+// Kahan-compensated accumulation: the total is s - c (error bound 2 eps of the
+// sum of magnitudes, whatever the order of the terms)
+__device__ __forceinline__ void kahan_acc(float& s, float& c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <bool UNIT>
 __global__ void __launch_bounds__(CL_T) k_clean_pairs(const int32_t* n_dev, int32_t max_obj, CleanWs ws, int64_t W,
-                                                      float beta, int nchunk) {
-    __shared__ float4 sg[CL_T], se[CL_T];
-    __shared__ float2 sl[CL_T];
-    __shared__ int sb[CL_T];
+                                                      float beta) {
+    __shared__ float4 sa[CL_T], sq[CL_T];   // (cx, cy, peak, lo.x), (y2', -2 xy', x2', lo.y) of object rank t
+    __shared__ int sb[CL_T];                // its label
     const int n = clean_n(n_dev, max_obj);
     const int r0 = blockIdx.x * CL_T, c0 = blockIdx.y * CL_JC;
     if (r0 >= n || c0 >= min(n, r0 + CL_T)) return;     // nothing brighter here
@@ -286,9 +296,8 @@ __global__ void __launch_bounds__(CL_T) k_clean_pairs(const int32_t* n_dev, int3
         py = (float)yy;
         px = (float)(pix - yy * (uint32_t)W);
     }
-    float hi = 0.f, lo = 0.f, best = -1.f;
+    float sum = 0.f, comp = 0.f, best = -1.f;
     int bj = -1;
-    const bool unit = beta == 1.0f;
     const int c1 = min(min(c0 + CL_JC, n), r0 + CL_T);
     const int lim = valid ? min(c1, r) : c0;              // ranks c0..lim-1 are brighter than r
     for (int t0 = c0; t0 < c1; t0 += CL_T) {
@@ -298,22 +307,29 @@ __global__ void __launch_bounds__(CL_T) k_clean_pairs(const int32_t* n_dev, int3
             const unsigned long long kj = ws.skey[jr];
             const int lj = kj != ~0ull ? (int)(uint32_t)kj : 0;
             sb[threadIdx.x] = lj;
-            if (lj > 0) { sg[threadIdx.x] = ws.geo[lj]; se[threadIdx.x] = ws.ell[lj]; sl[threadIdx.x] = ws.blo[lj]; }
+            if (lj > 0) {
+                const float4 g = ws.geo[lj], e = ws.ell[lj];
+                const float2 o = ws.blo[lj];
+                sa[threadIdx.x] = make_float4(g.x, g.y, g.z, o.x);
+                sq[threadIdx.x] = make_float4(e.x, e.y, e.z, o.y);
+            }
         }
         __syncthreads();
         const int m = min(CL_T, lim - t0);
         for (int t = 0; t < m; t++) {
-            const float4 g = sg[t], e = se[t];
-            const float2 o = sl[t];
-            const float dx = (px - g.x) - o.x, dy = (py - g.y) - o.y;
-            const float q = fmaf(e.x * dx, dx, fmaf(e.y * dx, dy, e.z * dy * dy));
-            const float mv = unit ? __fdividef(g.z, 1.0f + q) : g.z * expf(-beta * log1pf(q));
-            two_sum_acc(hi, lo, mv);
-            const int lj = sb[t];
-            if (mv > best || (mv == best && lj < bj)) { best = mv; bj = lj; }
+            const float4 a = sa[t], e = sq[t];
+            const float dx = (px - a.x) - a.w, dy = (py - a.y) - e.w;
+            // r^2 / a^2 = dx (y2' dx - 2 xy' dy) + x2' dy^2
+            const float q = fmaf(dx, fmaf(e.x, dx, e.y * dy), e.z * dy * dy);
+            const float mv = UNIT ? __fdividef(a.z, 1.0f + q) : a.z * expf(-beta * log1pf(q));
+            kahan_acc(sum, comp, mv);
+            if (mv >= best) {                              // ties to the smaller label (rare)
+                const int lj = sb[t];
+                if (mv > best || lj < bj) { best = mv; bj = lj; }
+            }
         }
     }
-    if (r < n) ws.part[(size_t)blockIdx.y * ws.P + r] = CleanPart{hi, lo, best, bj};
+    if (r < n) ws.part[(size_t)blockIdx.y * ws.P + r] = CleanPart{sum, -comp, best, bj};
 }
 
 // per rank: the chunks' partials in chunk order, the decision and the target
@@ -343,51 +359,56 @@ __global__ void __launch_bounds__(CL_T) k_clean_into_init(const int32_t* n_dev, 
 }
 
 // merge targets followed to a kept object (each target is strictly brighter, so
-// a chain has at most n steps), then the label-order numbering of the kept ones
-// in one block; the count goes to n_out
-__global__ void __launch_bounds__(1024) k_clean_number(const int32_t* n_dev, int32_t max_obj, CleanWs ws,
-                                                       int32_t* n_out) {
-    __shared__ int red[32];
-    __shared__ int carry;
+// a chain has at most n steps): num[i] = that object
+__global__ void __launch_bounds__(CL_T) k_clean_root(const int32_t* n_dev, int32_t max_obj, CleanWs ws) {
     const int n = clean_n(n_dev, max_obj);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x + 1; i <= n; i += 1024) {
+    for (int i = blockIdx.x * CL_T + threadIdx.x + 1; i <= n; i += gridDim.x * CL_T) {
         int r = i;
         for (int s = 0; s <= n && ws.into[r] != r; s++) r = ws.into[r];
-        ws.num[i] = r;   // root for now
+        ws.num[i] = r;
     }
-    if (threadIdx.x == 0) carry = 0;
+}
+
+// kept objects (their own root, holding pixels) per tile of 1024 labels
+__global__ void __launch_bounds__(1024) k_clean_count(const int32_t* n_dev, int32_t max_obj, CleanWs ws) {
+    const int n = clean_n(n_dev, max_obj);
+    const int i = blockIdx.x * 1024 + threadIdx.x + 1;
+    const int kept = (i <= n && ws.num[i] == i && ws.geo[i].w > 0.f) ? 1 : 0;
+    const int c = __syncthreads_count(kept);
+    if (threadIdx.x == 0) ws.tcount[blockIdx.x] = c;
+}
+
+// new numbers 1.. in label order: a tile's offset is the sum of the counts
+// before it; a block scan inside.  The number of a kept object replaces its
+// (self) target in into[]; the count goes to n_out.
+__global__ void __launch_bounds__(1024) k_clean_assign(const int32_t* n_dev, int32_t max_obj, CleanWs ws,
+                                                       int32_t* n_out) {
+    __shared__ int red[32];
+    const int n = clean_n(n_dev, max_obj);
+    const int tile = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (tile * 1024 >= max(n, 1)) return;
+    int off = 0;
+    for (int t = threadIdx.x; t < tile; t += 1024) off += ws.tcount[t];
+    for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+    if (lane == 0) red[warp] = off;
     __syncthreads();
-    for (int base = 1; base <= n; base += 1024) {
-        const int i = base + threadIdx.x;
-        // a label with no pixel is no object: it takes no number
-        const int kept = (i <= n && ws.num[i] == i && ws.geo[i].w > 0.f) ? 1 : 0;
-        int inc = kept;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
-        }
-        if (lane == 31) red[warp] = inc;
-        __syncthreads();
-        int before = carry;
-        for (int w = 0; w < warp; w++) before += red[w];
-        __syncthreads();
-        // the new number of a kept object; others keep their root (negated, resolved below)
-        if (i <= n) ws.into[i] = kept ? before + inc : -ws.num[i];
-        if (threadIdx.x == 1023) carry = before + inc;
-        __syncthreads();
-    }
-    for (int i = threadIdx.x + 1; i <= n; i += 1024) {
-        const int v = ws.into[i];
-        ws.num[i] = v > 0 ? v : 0;
-    }
+    off = 0;
+    for (int w = 0; w < 32; w++) off += red[w];
     __syncthreads();
-    for (int i = threadIdx.x + 1; i <= n; i += 1024) {
-        const int v = ws.into[i];
-        if (v < 0) ws.num[i] = ws.num[-v];
+    const int i = tile * 1024 + threadIdx.x + 1;
+    const int kept = (i <= n && ws.num[i] == i && ws.geo[i].w > 0.f) ? 1 : 0;
+    int inc = kept;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
     }
-    if (threadIdx.x == 0) *n_out = carry;
+    if (lane == 31) red[warp] = inc;
+    __syncthreads();
+    int before = off;
+    for (int w = 0; w < warp; w++) before += red[w];
+    if (kept) ws.into[i] = before + inc;
+    // the tile holding label n (or tile 0 when there is none) reports the count
+    if (threadIdx.x == 1023 && tile == (n > 0 ? (n - 1) / 1024 : 0)) *n_out = before + inc;
 }
 
 __global__ void __launch_bounds__(CL_T) k_clean_relabel(const int32_t* labels, int64_t npx, const int32_t* n_dev,
@@ -395,7 +416,7 @@ __global__ void __launch_bounds__(CL_T) k_clean_relabel(const int32_t* labels, i
     const int n = clean_n(n_dev, max_obj);
     for (int64_t p = (int64_t)blockIdx.x * CL_T + threadIdx.x; p < npx; p += (int64_t)gridDim.x * CL_T) {
         const int l = __ldg(labels + p);
-        out[p] = (l <= 0 || l > n) ? 0 : ws.num[l];
+        out[p] = (l <= 0 || l > n) ? 0 : ws.into[ws.num[l]];   // the number of the object's kept root
     }
 }
 
@@ -416,7 +437,7 @@ static size_t ipp_clean_ws_carve(int32_t max_obj, void* base, CleanWs* w) {
     const int P = clean_sort_size(max_obj);
     const size_t nchunk = ((size_t)P + CL_JC - 1) / CL_JC;
     const size_t sz[] = {n * 8, n * 16, n * 16, n * 16, n * 24, n * 48, n * 16, n * 8, n * 16, n * 4, n * 4,
-                         (size_t)P * 8, nchunk * P * sizeof(CleanPart)};
+                         (size_t)P * 8, nchunk * P * sizeof(CleanPart), (n / 1024 + 1) * 4};
     constexpr int NA = sizeof(sz) / sizeof(sz[0]);
     size_t off[NA], o = 0;
     for (int k = 0; k < NA; k++) { off[k] = o; o += a256c(sz[k]); }
@@ -435,6 +456,7 @@ static size_t ipp_clean_ws_carve(int32_t max_obj, void* base, CleanWs* w) {
         w->num = (int32_t*)(b + off[10]);
         w->skey = (unsigned long long*)(b + off[11]);
         w->part = (CleanPart*)(b + off[12]);
+        w->tcount = (int32_t*)(b + off[13]);
         w->P = P;
     }
     return o;
@@ -485,12 +507,19 @@ int ipp_launch_clean(const float* sub, int64_t pitch, const int32_t* labels, int
         if (int e = ipp_check_launch("k_bitonic_local")) return e;
     }
     const int nchunk = (P + CL_JC - 1) / CL_JC;
-    k_clean_pairs<<<dim3((unsigned)(P / CL_T), (unsigned)nchunk), CL_T, 0, s>>>(n_dev, max_obj, w, W, beta, nchunk);
+    const dim3 pg2((unsigned)(P / CL_T), (unsigned)nchunk);
+    if (beta == 1.0f) k_clean_pairs<true><<<pg2, CL_T, 0, s>>>(n_dev, max_obj, w, W, beta);
+    else k_clean_pairs<false><<<pg2, CL_T, 0, s>>>(n_dev, max_obj, w, W, beta);
     if (int e = ipp_check_launch("k_clean_pairs")) return e;
     k_clean_decide<<<og, CL_T, 0, s>>>(n_dev, max_obj, w);
     if (int e = ipp_check_launch("k_clean_decide")) return e;
-    k_clean_number<<<1, 1024, 0, s>>>(n_dev, max_obj, w, n_out);
-    if (int e = ipp_check_launch("k_clean_number")) return e;
+    k_clean_root<<<og, CL_T, 0, s>>>(n_dev, max_obj, w);
+    if (int e = ipp_check_launch("k_clean_root")) return e;
+    const unsigned ntile = (unsigned)(max_obj / 1024 + 1);
+    k_clean_count<<<ntile, 1024, 0, s>>>(n_dev, max_obj, w);
+    if (int e = ipp_check_launch("k_clean_count")) return e;
+    k_clean_assign<<<ntile, 1024, 0, s>>>(n_dev, max_obj, w, n_out);
+    if (int e = ipp_check_launch("k_clean_assign")) return e;
     k_clean_relabel<<<pg, CL_T, 0, s>>>(labels, npx, n_dev, max_obj, w, out);
     return ipp_check_launch("k_clean_relabel");
 }
