@@ -266,7 +266,7 @@ def batch_leg(ipp, synth, dev, n_frames, reps=5, shapes=None, mesh=128, star_sca
             "table_ms": table_ms, "table_graph_ms": table_graph_ms, "table_workspace_gb": table_ws_gb,
             "table_lanes": tbest, "table_ms_lanes_1_2_4_8": [table_lane_ms[k] for k in (1, 2, 4, 8)],
             "streams_ms": streams_ms, "streams_graph_ms": streams_graph_ms, "lanes": best,
-            "table_vs_streams": min(streams_ms, streams_graph_ms) / bat_ms,
+            "table_vs_streams": min(streams_ms, streams_graph_ms) / min(table_ms, table_graph_ms),
             "autotune_ms_lanes_1_2_4_8": lane_ms,
             "workload": f"{n_frames} frames of {sorted(set(shapes))}, {2000 * star_scale:g}-{50000 * star_scale:g} "
                         "stars, sky 200-3000 ADU, "
