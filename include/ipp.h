@@ -114,6 +114,9 @@ typedef struct {
 #define IPP_GRAY_POWER 2
 #define IPP_GRAY_EXP 3
 
+#define IPP_INTERP_KEYS 0
+#define IPP_INTERP_SPLINE 1
+
 #define IPP_PSF_MOFFAT 0
 #define IPP_PSF_GAUSS 1
 
@@ -124,7 +127,13 @@ typedef struct {
     int32_t maxiters;           /* clip passes [10] */
     int32_t min_valid;          /* usable pixels for a valid mesh [100] */
     int32_t estimator;          /* IPP_EST_* [IPP_EST_SIGMA] */
-    int32_t reserved;           /* must be 0 */
+    int32_t interp;             /* IPP_INTERP_KEYS [default]: Keys cubic convolution of the nodes;
+                                   IPP_INTERP_SPLINE: the natural tensor-product spline (the map of
+                                   ipp_bg_subtract_spline), used by ipp_extract for both the
+                                   background and the rms of the threshold; calls that interpolate
+                                   without a spline workspace (ipp_bg_subtract, ipp_detect_label,
+                                   ipp_clean from mesh_rms, the table form of the batch) return
+                                   IPP_ERR_NOT_SUPPORTED for it */
     double nsigma;              /* clip half-width in sigma [3] */
     double median_factor;       /* Eq. 4 [2.5] */
     double mean_factor;         /* Eq. 4 [1.5] */

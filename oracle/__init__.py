@@ -411,17 +411,27 @@ def psf_fit(stamps, init=None, weights=None, model=PSF_MOFFAT, beta=2.5, max_ite
 
 # ----------------------------------------------------------- whole path
 def catalog(img, mesh=64, filter_size=3, k=1.5, min_area=5, fwhm_win=3.0,
-            r_ap=5.0, r_in=8.0, r_out=12.0, mask_in=None):
-    """The whole per-frame path a1..a6 on one float32 frame."""
+            r_ap=5.0, r_in=8.0, r_out=12.0, mask_in=None, interp="keys"):
+    """The whole per-frame path a1..a6 on one float32 frame.  interp="spline"
+    takes the natural-spline map (spline_map) for the background and for the
+    rms of the threshold: sub = float32(img - B), detected where
+    sub > k rms(x, y) -- the same definitions, the other interpolant."""
     bkg, rms, st = bg_estimate(img, mesh=mesh, filter_size=filter_size)
-    sub, _ = bg_subtract(img, bkg, mesh)
-    m = threshold(sub, rms, mesh, k) if mask_in is None else mask_in
+    if interp == "spline":
+        H, W = img.shape
+        B = spline_map(bkg, mesh, W, H)
+        sub = (_f32(img).astype(np.float64) - B).astype(np.float32)
+        R = spline_map(rms, mesh, W, H)
+        m = (sub.astype(np.float64) > k * R).astype(np.uint8) if mask_in is None else mask_in
+    else:
+        sub, _ = bg_subtract(img, bkg, mesh)
+        m = threshold(sub, rms, mesh, k) if mask_in is None else mask_in
     labels, K, stats = label(m, sub, min_area)
     x, y, it, cfl = centroid(sub, stats["xbar"].astype(np.float32),
                              stats["ybar"].astype(np.float32), fwhm_win)
     ph = aperture(sub, x.astype(np.float32), y.astype(np.float32), r_ap, r_in, r_out)
     return dict(bkg=bkg, rms=rms, mesh_stats=st, sub=sub, mask=m, labels=labels, K=K,
-                stats=stats, x=x, y=y, cen_iter=it, cen_flags=cfl, **ph)
+                stats=stats, x=x, y=y, cen_iter=it, cen_flags=cfl, interp=interp, **ph)
 
 
 def wcs_pix2world(w, x, y):

@@ -61,11 +61,14 @@ class BgConfig:
     estimator: int = EST_SIGMA
     median_factor: float = 2.5
     mean_factor: float = 1.5
+    interp: str = "keys"    # "keys" (Keys cubic convolution) or "spline" (natural tensor spline)
 
     def c(self):
+        if self.interp not in ("keys", "spline"):
+            raise ValueError("interp is 'keys' or 'spline'")
         return _abi.BgParams(self.mesh, self.mesh_h or self.mesh, self.filter_size, self.filter_size,
-                             self.maxiters, self.min_valid, self.estimator, 0, self.nsigma,
-                             self.median_factor, self.mean_factor)
+                             self.maxiters, self.min_valid, self.estimator, int(self.interp == "spline"),
+                             self.nsigma, self.median_factor, self.mean_factor)
 
     def grid(self, W, H):
         mh = self.mesh_h or self.mesh
@@ -748,7 +751,7 @@ class Batch:
 
 
 _BG_KEYS = ("mesh", "mesh_h", "filter_size", "maxiters", "min_valid", "nsigma", "estimator",
-            "median_factor", "mean_factor")
+            "median_factor", "mean_factor", "interp")
 
 
 def extract(img, cfg: BgConfig | None = None, calib=None, **kw):

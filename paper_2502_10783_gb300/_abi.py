@@ -25,7 +25,7 @@ vp, i32, i64, f32, f64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_do
 
 class BgParams(C.Structure):
     _fields_ = [("mesh_w", i32), ("mesh_h", i32), ("filter_w", i32), ("filter_h", i32),
-                ("maxiters", i32), ("min_valid", i32), ("estimator", i32), ("reserved", i32),
+                ("maxiters", i32), ("min_valid", i32), ("estimator", i32), ("interp", i32),
                 ("nsigma", f64), ("median_factor", f64), ("mean_factor", f64)]
 
 

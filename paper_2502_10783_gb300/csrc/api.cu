@@ -124,6 +124,7 @@ extern "C" int ipp_bg_subtract(const void* img, int dtype, int64_t W, int64_t H,
                                float* sub, int64_t sub_pitch, float* bkg_map, void* stream) {
     if (int e = check_frame(img, dtype, W, H, pitch, cal)) return e;
     if (int e = check_bg(p)) return e;
+    if (int e = check_keys_only(p, "ipp_bg_subtract")) return e;
     REQUIRE(mesh_bkg && sub, "mesh_bkg / sub NULL");
     REQUIRE(sub_pitch >= W, "sub_pitch < W");
     int nx, ny;
@@ -189,6 +190,7 @@ extern "C" int ipp_detect_label(const float* sub, int64_t W, int64_t H, int64_t 
     REQUIRE(dp->filter == 0 || dp->filter == 1, "detection filter must be 0 or 1");
     if (!mask_in) {
         if (int e = check_bg(bp)) return e;
+        if (int e = check_keys_only(bp, "ipp_detect_label")) return e;
         REQUIRE(mesh_rms, "mesh_rms NULL (needed without mask_in)");
         REQUIRE(dp->k >= 0.f, "k must be >= 0");
     }
@@ -320,6 +322,7 @@ extern "C" int ipp_clean(const float* sub, const int32_t* labels, int64_t W, int
     float mw = 1.f, mh = 1.f;
     if (!thr_map && mesh_rms) {
         if (int e = check_bg(bp)) return e;
+        if (int e = check_keys_only(bp, "ipp_clean (threshold from mesh_rms)")) return e;
         nx = (int)cdiv(W, bp->mesh_w);
         ny = (int)cdiv(H, bp->mesh_h);
         mw = (float)bp->mesh_w;
@@ -544,9 +547,17 @@ extern "C" int ipp_stamp_cut(const float* sub, int64_t W, int64_t H, int64_t pit
 }
 
 // ---- fused frame ---------------------------------------------------------------------
+// ipp_extract's workspace: the mesh statistics' scratch, the labeling's, then
+// the spline node tables of the mesh bkg and rms (used with interp = spline)
+static size_t extract_spline_off(int64_t W, int64_t H, const ipp_bg_params* bp) {
+    return a256(ipp_bg_estimate_workspace_size(W, H, bp)) + a256(ipp_ccl_workspace_size(W, H));
+}
+
 extern "C" size_t ipp_extract_workspace_size(int64_t W, int64_t H, const ipp_bg_params* bp) {
-    if (!bp) return 0;
-    return a256(ipp_bg_estimate_workspace_size(W, H, bp)) + ipp_ccl_workspace_size(W, H);
+    if (!bp || bp->mesh_w < 1 || bp->mesh_h < 1) return 0;
+    int nx, ny;
+    grid_of(W, H, bp, &nx, &ny);
+    return extract_spline_off(W, H, bp) + 2 * a256(ipp_spline_ws_bytes(nx, ny));
 }
 
 // The jobs of ipp_extract for one frame, after its argument checks: the mesh
@@ -605,6 +616,13 @@ int ipp_extract_jobs(const void* img, int dtype, int64_t W, int64_t H, int64_t p
     A->filter = dp->filter;
     A->labels = out->labels; A->n_src_dev = out->n_src_dev; A->max_src = max_src; A->stats = out->stats;
     A->ws = w + bgws;
+    A->interp = bp->interp;
+    if (bp->interp == IPP_INTERP_SPLINE) {
+        if (dp->filter) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "detection filter with the spline reading");
+        const size_t so = extract_spline_off(W, H, bp);
+        A->bnodes = reinterpret_cast<const float4*>(w + so);
+        A->rnodes = reinterpret_cast<const float4*>(w + so + a256(ipp_spline_ws_bytes(nx, ny)));
+    }
     // centroid (as ipp_centroid) and aperture photometry (as ipp_aperture_phot)
     memset(C, 0, sizeof(*C));
     C->sub = out->sub; C->W = W; C->H = H; C->pitch = W; C->n_src_dev = out->n_src_dev; C->max_src = max_src;
@@ -638,6 +656,10 @@ extern "C" int ipp_extract(const void* img, int dtype, int64_t W, int64_t H, int
     if (int e = ipp_launch_mesh_filter(F.raw_bkg, F.raw_rms, F.fill_bkg, F.fill_rms, F.nx, F.ny, F.fw, F.fh,
                                        F.out_bkg, F.out_rms, F.status_dev, s))
         return e;
+    if (A.interp == IPP_INTERP_SPLINE) {   // node tables of the filtered grids
+        if (int e = ipp_launch_spline_nodes(F.out_bkg, F.nx, F.ny, (void*)A.bnodes, s)) return e;
+        if (int e = ipp_launch_spline_nodes(F.out_rms, F.nx, F.ny, (void*)A.rnodes, s)) return e;
+    }
     if (int e = ipp_launch_detect(A, s)) return e;
     if (int e = ipp_launch_centroid(C, s)) return e;
     return ipp_launch_aperture(P, s);

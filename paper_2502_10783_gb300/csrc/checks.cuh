@@ -25,5 +25,13 @@ static inline int check_bg(const ipp_bg_params* p) {
     REQUIRE(p->min_valid >= 1, "min_valid must be >= 1");
     REQUIRE(p->estimator >= 0 && p->estimator <= 3, "unknown estimator %d", p->estimator);
     REQUIRE(p->nsigma > 0, "nsigma must be > 0");
+    REQUIRE(p->interp == IPP_INTERP_KEYS || p->interp == IPP_INTERP_SPLINE, "unknown interp %d", p->interp);
+    return IPP_OK;
+}
+
+// calls that interpolate with Keys only
+static inline int check_keys_only(const ipp_bg_params* p, const char* what) {
+    if (p && p->interp != IPP_INTERP_KEYS)
+        return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "%s interpolates with Keys only (interp = spline)", what);
     return IPP_OK;
 }

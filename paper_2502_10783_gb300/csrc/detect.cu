@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "jobs.cuh"
+#include "spline.cuh"
 
 namespace ipp {
 
@@ -1031,6 +1032,49 @@ __global__ void __launch_bounds__(G_THREADS) k_tile_final(CclWs ws, int64_t W, i
     ccl_final_tile(ws, lab, blockIdx.x, W, H, ntx, labels);
 }
 
+// The same pass with the natural-spline reading of the interpolation (the
+// interp option of the mesh parameters): B and rms from the node tables
+// {f, Mx, My, Mxy} of the filtered mesh grids (k_spline_nodes), a thread per 4
+// pixels of a row, 8 rows per 256-thread block; the mask nibbles of 8 lanes
+// make one 32-bit word.
+__global__ void __launch_bounds__(256) k_sub_thresh_spline(SubThreshJob T, const float4* nb, const float4* nr) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t y = (int64_t)blockIdx.y * 8 + warp;
+    if (y >= T.H) return;                                   // uniform over the warp
+    const int64_t x0 = ((int64_t)blockIdx.x * 32 + lane) * 4;
+    const float v = ((float)y + 0.5f) / T.mesh_h - 0.5f;
+    unsigned nib = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const int64_t x = x0 + c;
+        if (x >= T.W) break;
+        const float u = ((float)x + 0.5f) / T.mesh_w - 0.5f;
+        float s;
+        if (T.fused) {
+            float f;
+            if (T.dtype == IPP_F32) {
+                f = __ldg(reinterpret_cast<const float*>(T.img) + y * T.pitch + x);
+            } else {
+                const float raw = (float)__ldg(reinterpret_cast<const uint16_t*>(T.img) + y * T.pitch + x);
+                const float b = T.bias_map ? __ldg(T.bias_map + y * T.W + x) : T.bias;
+                f = (raw - b) * __ldg(T.inv_flat + y * T.W + x);
+            }
+            s = f - spline_at(nb, T.nx, T.ny, u, v);
+            T.sub[y * T.sub_pitch + x] = s;
+        } else {
+            s = T.sub[y * T.sub_pitch + x];
+        }
+        const float thr = fmaxf(T.k * spline_at(nr, T.nx, T.ny, u, v), T.thresh_abs);
+        if (s > thr) nib |= 1u << c;
+    }
+    unsigned word = nib << (4 * (lane & 7));
+    word |= __shfl_xor_sync(0xffffffffu, word, 1);
+    word |= __shfl_xor_sync(0xffffffffu, word, 2);
+    word |= __shfl_xor_sync(0xffffffffu, word, 4);
+    const int64_t wi = (x0 >> 5);
+    if ((lane & 7) == 0 && wi < T.mw) T.mask[y * T.mw + wi] = word;
+}
+
 // ---- batched form: the same bodies over a table of frames ------------------
 struct CclJob {
     CclWs ws;
@@ -1228,8 +1272,16 @@ int ipp_launch_detect(const DetectArgs& A, cudaStream_t s) {
         T.mask = (uint32_t*)((unsigned char*)A.ws + L.off[24]);
         T.mw = J.mw;
         dim3 sg((unsigned)cdiv(A.W, ST_TW), (unsigned)cdiv(A.H, ST_TH));
-        if (A.mesh_w >= 16) k_sub_thresh_poly<<<sg, ST_THREADS, 0, s>>>(T);
-        else k_sub_thresh<<<sg, ST_THREADS, 0, s>>>(T);
+        if (A.interp == 1) {
+            if (A.filter) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "detection filter with the spline reading");
+            if (!A.bnodes || !A.rnodes) return ipp_set_error(IPP_ERR_INVALID_ARG, "spline node tables missing");
+            dim3 spg((unsigned)cdiv(A.W, 128), (unsigned)cdiv(A.H, 8));
+            k_sub_thresh_spline<<<spg, 256, 0, s>>>(T, A.bnodes, A.rnodes);
+        } else if (A.mesh_w >= 16) {
+            k_sub_thresh_poly<<<sg, ST_THREADS, 0, s>>>(T);
+        } else {
+            k_sub_thresh<<<sg, ST_THREADS, 0, s>>>(T);
+        }
         if (int e = ipp_check_launch("k_sub_thresh")) return e;
         if (A.filter) {  // detection filter: threshold again, on the smoothed sub just written
             SubThreshJob Tf = T;
@@ -1291,6 +1343,7 @@ int ipp_detect_multi_pack(const DetectArgs* A, int nf, HostBlob& hb, DetMultiPla
     for (int f = 0; f < nf; f++) {
         const DetectArgs& a = A[f];
         if (a.mode == MODE_MASK) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "batched detection from a mask");
+        if (a.interp != 0) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "the table form with the spline reading");
         if ((a.filter != 0) != p->filter) return ipp_set_error(IPP_ERR_INVALID_ARG, "mixed detection filters");
         const CclLayout L = ccl_layout(a.W, a.H);
         if (L.nodes >= (int64_t)INT32_MAX) return ipp_set_error(IPP_ERR_NOT_SUPPORTED, "frame too large");

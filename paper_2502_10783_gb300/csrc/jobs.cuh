@@ -133,6 +133,9 @@ struct DetectArgs {
     int32_t max_src;
     ipp_src_stats stats;
     void* ws;
+    int interp;                 // IPP_INTERP_KEYS or IPP_INTERP_SPLINE
+    const float4* bnodes;       // spline node tables of the mesh bkg and rms (interp = spline)
+    const float4* rnodes;
 };
 
 struct FitJob {
@@ -228,6 +231,7 @@ int ipp_phot_multi_launch(const ipp::PhotMultiPlan& p, const unsigned char* dtab
 int ipp_launch_mesh_stats(const ipp::MeshJob& J, cudaStream_t s);
 size_t ipp_spline_ws_bytes(int nx, int ny);
 int ipp_launch_bg_subtract_spline(const ipp::SubJob& J, void* ws, cudaStream_t s);
+int ipp_launch_spline_nodes(const float* mesh, int nx, int ny, void* ws, cudaStream_t s);
 size_t ipp_subfit_ws_bytes(int max_c, int nreg, int hw, int fh, int nk, const int32_t* deg, int sord, int bord);
 size_t ipp_subfit_smem(int hw, int fh, int nk, const int32_t* deg, int sord, int bord);
 int ipp_launch_sub_stamps(const float* I, const float* R, int64_t W, int64_t H, int64_t pitch, int nsx, int nsy,

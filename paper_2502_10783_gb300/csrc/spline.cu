@@ -12,6 +12,7 @@
 // a thread per node row or column); k_bg_subtract_spline then evaluates the map
 // at each pixel from its cell's sixteen numbers and writes f - B.
 #include "jobs.cuh"
+#include "spline.cuh"
 
 namespace ipp {
 
@@ -69,50 +70,6 @@ __global__ void __launch_bounds__(SP_THREADS) k_spline_nodes(const float* mesh, 
     }
 }
 
-// A 1-D natural spline at offset b from node k: (f0, M0) value and second
-// derivative at node k, (f1, M1) at node k + 1; the cubic between them, and
-// beyond the first (below) or last (above) node the line with the end slope.
-__device__ __forceinline__ float nat_piece(float f0, float M0, float f1, float M1, float b) {
-    const float a = 1.0f - b;
-    return fmaf(a, f0, b * f1) + ((a * a * a - a) * M0 + (b * b * b - b) * M1) * (1.0f / 6.0f);
-}
-__device__ __forceinline__ float nat_eval(float f0, float M0, float f1, float M1, float b, bool below, bool above) {
-    if (below) return f0 + b * ((f1 - f0) - (2.0f * M0 + M1) * (1.0f / 6.0f));            // b < 0
-    if (above) return f1 + (b - 1.0f) * ((f1 - f0) + (M0 + 2.0f * M1) * (1.0f / 6.0f));  // b > 1
-    return nat_piece(f0, M0, f1, M1, b);
-}
-
-// cell and offset along one axis: node k (0 <= k <= n - 2) and b = u - k, with
-// the flags for u beyond the first or last node; n = 1 gives k = 0, b = 0
-__device__ __forceinline__ void nat_cell(float u, int n, int* k, float* b, bool* below, bool* above) {
-    if (n < 2) { *k = 0; *b = 0.f; *below = *above = false; return; }
-    const int kk = min(max((int)floorf(u), 0), n - 2);
-    *k = kk;
-    *b = u - (float)kk;
-    *below = u < 0.f;
-    *above = u > (float)(n - 1);
-}
-
-__device__ __forceinline__ float spline_at(const float4* nodes, int nx, int ny, float u, float v) {
-    int q, p;
-    float bx, by;
-    bool xb, xa, yb, ya;
-    nat_cell(u, nx, &q, &bx, &xb, &xa);
-    nat_cell(v, ny, &p, &by, &yb, &ya);
-    const int q1 = min(q + 1, nx - 1), p1 = min(p + 1, ny - 1);
-    float R[2], Ry[2];
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
-        const int pp = s ? p1 : p;
-        const float4 A = __ldg(nodes + pp * nx + q), B = __ldg(nodes + pp * nx + q1);
-        if (nx < 2) { R[s] = A.x; Ry[s] = A.z; continue; }
-        R[s] = nat_eval(A.x, A.y, B.x, B.y, bx, xb, xa);     // along x: values with Mx
-        Ry[s] = nat_eval(A.z, A.w, B.z, B.w, bx, xb, xa);    // along x: My with Mxy
-    }
-    if (ny < 2) return R[0];
-    return nat_eval(R[0], Ry[0], R[1], Ry[1], by, yb, ya);   // along y
-}
-
 __device__ __forceinline__ float spline_pix(const SubJob& J, int64_t y, int64_t x) {
     if (J.dtype == IPP_F32) return __ldg(reinterpret_cast<const float*>(J.img) + y * J.pitch + x);
     const float raw = (float)__ldg(reinterpret_cast<const uint16_t*>(J.img) + y * J.pitch + x);
@@ -164,6 +121,15 @@ using namespace ipp;
 size_t ipp_spline_ws_bytes(int nx, int ny) {
     const size_t n = (size_t)nx * ny;
     return ((n * sizeof(float4) + 255) & ~(size_t)255) + (n + nx + ny) * sizeof(float);
+}
+
+// the node table of an nx x ny grid at the head of ws (ipp_spline_ws_bytes)
+int ipp_launch_spline_nodes(const float* mesh, int nx, int ny, void* ws, cudaStream_t s) {
+    const size_t n = (size_t)nx * ny;
+    float4* nodes = static_cast<float4*>(ws);
+    float* scratch = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + ((n * sizeof(float4) + 255) & ~(size_t)255));
+    k_spline_nodes<<<1, SP_THREADS, 0, s>>>(mesh, nx, ny, nodes, scratch);
+    return ipp_check_launch("k_spline_nodes");
 }
 
 int ipp_launch_bg_subtract_spline(const SubJob& J, void* ws, cudaStream_t s) {

@@ -48,10 +48,11 @@ def _comp_index(labels, K):
     return [idx[starts[i]:starts[i + 1]] for i in range(K)]
 
 
-def borderline(orc, osub, gsub, orms, mesh, W, H, k=1.5):
+def borderline(orc, osub, gsub, orms, mesh, W, H, k=1.5, interp="keys"):
     """pixels whose oracle value lies within the two sides' rounding of the
     threshold: |osub - k rms| <= |gsub - osub| + 2e-5 k rms + 1e-6"""
-    thr = k * orc.interp_map(orms, mesh, W, H)
+    rmap = orc.spline_map if interp == "spline" else orc.interp_map
+    thr = k * rmap(orms, mesh, W, H)
     dev = np.abs(gsub.astype(np.float64) - osub.astype(np.float64))
     return np.abs(osub.astype(np.float64) - thr) <= dev + 2e-5 * np.abs(thr) + 1e-6
 
@@ -112,7 +113,7 @@ def assert_catalog(orc, img, oc, g, gstats, mesh, r_ap=5.0, r_in=8.0, r_out=12.0
     assert np.all(np.abs(gsub.astype(np.float64) - osub) <= sub_tol), "subtracted frame"
 
     gK, oK = int(g["n_src"]), int(oc["K"])
-    near = borderline(orc, osub, gsub, oc["rms"], mesh, W, H, k)
+    near = borderline(orc, osub, gsub, oc["rms"], mesh, W, H, k, oc.get("interp", "keys"))
     pairs, o_bad, g_bad = match_components(oc["labels"], oK, g["labels"], gK, near)
     assert len(pairs) == oK - o_bad == gK - g_bad, (len(pairs), oK, o_bad, gK, g_bad)
     io, ig = pairs[:, 0], pairs[:, 1]
@@ -162,10 +163,16 @@ def assert_catalog(orc, img, oc, g, gstats, mesh, r_ap=5.0, r_in=8.0, r_out=12.0
     # frames that differ by at most dsub; the centroid moves by at most
     # 2 * sum(w |dsub| |x_i - x|) / sum(w sub), bounded here by the window's
     # pixel count times dsub times its radius over the window flux.
+    # A window that ends more than its radius from its seed has run off its
+    # source (a faint source beside a brighter one or a gradient): its end point
+    # is not a continuous function of the frame near the source, and frames that
+    # differ by dsub can send it to different places.  Such windows are compared
+    # on identical inputs above, exactly, and left out here.
     ox, oy, ocf = oc["x"][io], oc["y"][io], oc["cen_flags"][io]
-    conv2 = ((ocf & FLAG_WIN_NOT_CONVERGED) == 0) & ((gcf & FLAG_WIN_NOT_CONVERGED) == 0)
     sw = 3.0 / 2.3548200450309493
     rad = 4 * sw
+    ran = np.hypot(ox - ost["xbar"][io], oy - ost["ybar"][io]) > rad
+    conv2 = ((ocf & FLAG_WIN_NOT_CONVERGED) == 0) & ((gcf & FLAG_WIN_NOT_CONVERGED) == 0) & ~ran
     wflux = np.abs(ost["sum"][io]) + 1.0
     shift = 2 * np.pi * rad ** 2 * dsub.max() * rad / wflux
     tol2 = 3e-4 + 2 * float_ulp(ox) + shift
@@ -184,4 +191,4 @@ def assert_catalog(orc, img, oc, g, gstats, mesh, r_ap=5.0, r_in=8.0, r_out=12.0
     fl_tol = 1e-5 * oscale + 2 * oc["area"][io] * dsub.max() + pos_err * 4 * oscale
     assert np.all(np.abs(g["flux"][ig] - oc["flux"][io])[ok] <= fl_tol[ok]), "end-to-end flux"
     return dict(matched=len(pairs), oK=oK, gK=gK, o_unclean=o_bad, g_unclean=g_bad,
-                near=int(near.sum()), end_to_end=int(ok.sum()))
+                near=int(near.sum()), end_to_end=int(ok.sum()), ran_off=int(ran.sum()))

@@ -80,6 +80,16 @@ def test_host_side_validation(L):
     # empty batch is a no-op
     assert L.ipp_psf_fit(fake, 0, 15, None, None, _abi.FitParams(0, 2.5, 50, 1e-3), fake, fake, None, None,
                          None) == 0
+    # the spline reading: an unknown interp is refused; calls that interpolate with
+    # Keys only answer NOT_SUPPORTED before anything is enqueued
+    assert L.ipp_bg_subtract(fake, 0, 100, 100, 100, None, fake, _abi.BgParams(64, 64, 3, 3, 10, 100, 0, 7, 3.0,
+                             2.5, 1.5), fake, 100, None, None) == _abi.IPP_ERR_INVALID_ARG
+    ps = _abi.BgParams(64, 64, 3, 3, 10, 100, 0, 1, 3.0, 2.5, 1.5)
+    assert L.ipp_bg_subtract(fake, 0, 100, 100, 100, None, fake, ps, fake, 100, None,
+                             None) == _abi.IPP_ERR_NOT_SUPPORTED
+    st_ok = _abi.SrcStats(*([0x1000] * 10))
+    assert L.ipp_detect_label(fake, 100, 100, 100, fake, ps, d1, None, fake, fake, 10, st_ok, fake, 1 << 30,
+                              None) == _abi.IPP_ERR_NOT_SUPPORTED
 
 
 def test_workspace_queries(L):
@@ -90,4 +100,7 @@ def test_workspace_queries(L):
     b = L.ipp_detect_label_workspace_size(1000, 1000)
     assert a > b > 0
     assert L.ipp_extract_workspace_size(4096, 4096, p) >= a
+    # the spline node tables of the mesh bkg and rms are part of it, whatever interp says
+    ps = _abi.BgParams(128, 128, 3, 3, 10, 100, 0, 1, 3.0, 2.5, 1.5)
+    assert L.ipp_extract_workspace_size(4096, 4096, ps) == L.ipp_extract_workspace_size(4096, 4096, p)
     assert L.ipp_detect_label_workspace_size(0, 10) == 0

@@ -141,3 +141,24 @@ def test_table_rejects_wide_centroid_window(gpu):
     with pytest.raises(Exception):
         b.run()
     b.close()
+
+
+def test_spline_reading_in_both_forms(gpu):
+    """interp = spline: the stream form runs it (through ipp_extract, equal to the
+    per-frame call); the table form answers NOT_SUPPORTED"""
+    frames = _frames()[:3]
+    cfg = gpu.BgConfig(mesh=64, interp="spline")
+    ref = []
+    for f in frames:
+        ex = gpu.Extractor(f.shape[1], f.shape[0], cfg, max_src=4096)
+        ref.append({k: v.clone() for k, v in ex(f).items()})
+    b = gpu.Batch(frames, lanes=2, cfg=cfg, max_src=4096)
+    b.run()
+    torch.cuda.synchronize()
+    for o, r in zip(b.outs, ref):
+        _same(o, r)
+    b.close()
+    t = gpu.Batch(frames, cfg=cfg, max_src=4096, mode="table")
+    with pytest.raises(Exception):
+        t.run()
+    t.close()

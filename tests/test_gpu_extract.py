@@ -44,6 +44,45 @@ def test_extract_parity(gpu, orc, which):
     assert s["matched"] >= 0.97 * s["oK"], s
 
 
+@pytest.mark.parametrize("which", ["gradient_1k", "ragged"])
+def test_extract_spline_parity(gpu, orc, which):
+    """the catalog path with the natural-spline reading (interp = spline): the
+    fused pass takes the background and the threshold's rms from the node tables
+    of the filtered grids; the oracle composes its spline map with the same
+    threshold, labeling, centroid and aperture"""
+    if which == "gradient_1k":
+        img, _ = synth.frame_gradient_1k(1001)
+        mesh = 64
+    else:
+        img, _ = synth.tiny_frame(517, 389, 77, n_stars=40, sky=500.0, flux=(3.0, 4.5))
+        mesh = 32
+    oc = orc.catalog(img, mesh=mesh, interp="spline")
+    out = gpu.extract(dev(img), mesh=mesh, interp="spline")
+    torch.cuda.synchronize()
+    g, st = host_catalog(out)
+    s = assert_catalog(orc, img, oc, g, st, mesh)
+    assert s["matched"] >= 0.97 * s["oK"], s
+    # the spline map differs from the Keys map, so the two catalogs' frames differ
+    ok = gpu.extract(dev(img), mesh=mesh)
+    assert not np.array_equal(host(ok["sub"]), g["sub"])
+
+
+def test_extract_spline_u16(gpu, orc):
+    """the spline reading on a raw uint16 frame with bias and flat fused into the read"""
+    if not hasattr(torch, "uint16"):
+        pytest.skip("torch without uint16")
+    raw, flat, _ = synth.raw_calibrated_4k(5301, W=517, H=389, n_stars=30)
+    f = orc.calibrate(raw, flat, bias=500.0)
+    oc = orc.catalog(f, mesh=32, interp="spline")
+    inv = dev((1.0 / flat.astype(np.float64)).astype(np.float32))
+    traw = torch.from_numpy(raw.view(np.int16)).cuda().view(torch.uint16)
+    out = gpu.extract(traw, calib=(inv, 500.0), mesh=32, interp="spline")
+    torch.cuda.synchronize()
+    g, st = host_catalog(out)
+    s = assert_catalog(orc, f, oc, g, st, 32)
+    assert s["matched"] >= 0.97 * s["oK"], s
+
+
 def test_extract_repeatable(gpu):
     """two runs over the same frame give identical outputs, bit for bit: the
     component sums are integers (fixed point), so the order of the atomic

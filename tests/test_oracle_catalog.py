@@ -50,3 +50,19 @@ def test_catalog_vs_truth_1k(orc):
     expect = tr.flux[m[k]] * (1 - math.exp(-25 / (2 * s * s)))
     dmag = -2.5 * np.log10(out["flux"][k] / expect)
     assert np.mean(np.abs(dmag) < 0.04) > 0.95
+
+
+def test_spline_reading_of_the_catalog(orc):
+    """the catalog with the natural-spline map: a constant sky is subtracted
+    exactly (the spline of equal nodes is that value everywhere, the linear
+    extension included) and nothing is detected; on a sky with stars the
+    subtracted frame equals the frame less the oracle's spline map"""
+    import synth
+    f = np.full((200, 300), 500.0, np.float32)
+    c = orc.catalog(f, mesh=32, interp="spline")
+    assert c["K"] == 0 and np.all(c["sub"] == 0.0)
+    img, _ = synth.tiny_frame(300, 200, 5, n_stars=8, sky=400.0)
+    c = orc.catalog(img, mesh=32, interp="spline")
+    B = orc.spline_map(c["bkg"], 32, 300, 200)
+    assert np.array_equal(c["sub"], (img.astype(np.float64) - B).astype(np.float32))
+    assert c["K"] >= 4
