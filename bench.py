@@ -540,6 +540,11 @@ def main():
     spbuf = torch.empty_like(subbuf)
     stages["bg_subtract_spline"] = timeit(lambda k: ipp.bg_subtract_spline(frames[k % 3], mb, cfg=cfg, out=spbuf))
     del spbuf
+    # the whole catalog path with the spline reading (interp = spline)
+    cfg_sp = ipp.BgConfig(mesh=cfg.mesh, interp="spline")
+    ex_sp = ipp.Extractor(W, H, cfg_sp, device=dev, max_src=65536)
+    stages["extract_spline"] = timeit(lambda k: ex_sp(frames[k % 3]))
+    del ex_sp
     # gray-scale maps of the subtracted frame (a widening, timed beside the step):
     # four distinct input/output pairs rotate, 512 MiB in all, so that each call
     # reads its input from HBM, not L2
