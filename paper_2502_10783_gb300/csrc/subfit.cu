@@ -120,7 +120,8 @@ __device__ __forceinline__ bool stamp_key(const StampRegion& g, int t, const Key
 
 // The k-th smallest key (0-based) of the region: radix selection, 8 bits a
 // pass from bit top + 7 down, every key sharing the bits above top with
-// prefix0; per-warp histograms in shared memory (hist: SS_W x 256 counters).
+// prefix0; per-warp histograms in shared memory (hist: SS_W x 256 counters),
+// fed by per-thread run lengths of equal digits.
 __device__ unsigned long long block_select(const StampRegion& g, const KeySpec& ks, long long k, int top,
                                            unsigned long long prefix0, unsigned int* hist, int* sdig,
                                            long long* sbelow) {
@@ -129,15 +130,25 @@ __device__ unsigned long long block_select(const StampRegion& g, const KeySpec& 
     for (int shift = top; shift >= 0; shift -= 8) {
         for (int t = threadIdx.x; t < SS_W * 256; t += SS_T) hist[t] = 0;
         __syncthreads();
-        for (int base = 0; base < g.n; base += SS_T) {
-            const int t = base + threadIdx.x;
+        // each thread counts runs of equal digits over its elements (the region's
+        // keys mostly share their high digits) and adds a run to its warp's
+        // histogram when the digit changes
+        unsigned cur = 256u, run = 0u;
+        for (int t = threadIdx.x; t < g.n; t += SS_T) {
             unsigned long long key = 0;
-            bool ok = t < g.n && stamp_key(g, t, ks, &key);
+            bool ok = stamp_key(g, t, ks, &key);
             if (ok && shift + 8 < 64) ok = (key >> (shift + 8)) == prefix;
-            const unsigned dig = ok ? (unsigned)((key >> shift) & 255u) : 256u;
-            const unsigned m = __match_any_sync(0xffffffffu, dig);
-            if (ok && lane == __ffs(m) - 1) atomicAdd(&hist[warp * 256 + dig], (unsigned)__popc(m));
+            if (!ok) continue;
+            const unsigned dig = (unsigned)((key >> shift) & 255u);
+            if (dig == cur) {
+                run++;
+            } else {
+                if (run) atomicAdd(&hist[warp * 256 + cur], run);
+                cur = dig;
+                run = 1u;
+            }
         }
+        if (run) atomicAdd(&hist[warp * 256 + cur], run);
         __syncthreads();
         // totals per digit (thread b < 256), then warp 0 finds the digit of rank k
         if (threadIdx.x < 256) {
