@@ -578,6 +578,7 @@ __global__ void k_chol_init(int32_t* status) { *status = 0; }
 
 __global__ void __launch_bounds__(256) k_chol_diag(double* A, int n, int k0, int32_t* status) {
     __shared__ double D[CB][CB + 1];
+    __shared__ double rinv;
     __shared__ int fail;
     if (__ldcg(status)) return;
     const int b = min(CB, n - k0);
@@ -591,11 +592,13 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, int n, int k0, int
         if (threadIdx.x == 0) {
             const double d = D[j][j];
             if (!(d > 0.0)) fail = 1;
-            D[j][j] = d > 0.0 ? sqrt(d) : 1.0;
+            const double r = d > 0.0 ? sqrt(d) : 1.0;
+            D[j][j] = r;
+            rinv = 1.0 / r;
         }
         __syncthreads();
         if (fail) break;
-        for (int i = j + 1 + threadIdx.x; i < b; i += 256) D[i][j] /= D[j][j];
+        for (int i = j + 1 + threadIdx.x; i < b; i += 256) D[i][j] *= rinv;
         __syncthreads();
         for (int t = threadIdx.x; t < b * b; t += 256) {          // trailing update inside the block
             const int i = t / b, c = t - i * b;
@@ -667,13 +670,26 @@ __global__ void __launch_bounds__(256) k_chol_syrk(double* A, int n, int k0, con
 // L y = b, then L' x = y, CB rows at a time: the block's warps first take the
 // dot products with the part already solved (a warp per row), then warp 0
 // solves the CB x CB triangle.  The solution goes to b (and x64 / x32).
+// the CB x CB diagonal block of L at r0 (bsz rows) in shared memory, and the
+// reciprocals of its diagonal, for the sequential part of a solve step
+__device__ __forceinline__ void chol_stage_block(const double* A, int n, int r0, int bsz, double (*Ld)[CB + 1],
+                                                 double* rd) {
+    for (int t = threadIdx.x; t < bsz * bsz; t += 1024) {
+        const int i = t / bsz, j = t - i * bsz;
+        Ld[i][j] = A[(size_t)(r0 + i) * n + r0 + j];
+    }
+    if (threadIdx.x < bsz) rd[threadIdx.x] = 1.0 / A[(size_t)(r0 + threadIdx.x) * n + r0 + threadIdx.x];
+}
+
 __global__ void __launch_bounds__(1024) k_chol_solve(const double* A, double* b, int n, double* x64, float* x32,
                                                      const int32_t* status) {
-    __shared__ double part[CB];
+    __shared__ double part[CB], rd[CB];
+    __shared__ double Ld[CB][CB + 1];
     if (__ldcg(status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r0 = 0; r0 < n; r0 += CB) {                 // forward
         const int bsz = min(CB, n - r0);
+        chol_stage_block(A, n, r0, bsz, Ld, rd);
         if (warp < bsz) {
             const int i = r0 + warp;
             double s = 0.0;
@@ -685,9 +701,9 @@ __global__ void __launch_bounds__(1024) k_chol_solve(const double* A, double* b,
         if (warp == 0) {
             double y = lane < bsz ? part[lane] : 0.0, x = 0.0;
             for (int j = 0; j < bsz; j++) {
-                const double xj = __shfl_sync(0xffffffffu, lane == j ? y / A[(size_t)(r0 + j) * n + r0 + j] : 0.0, j);
+                const double xj = __shfl_sync(0xffffffffu, y * rd[j], j);
                 if (lane == j) x = xj;
-                if (lane > j && lane < bsz) y -= A[(size_t)(r0 + lane) * n + r0 + j] * xj;
+                if (lane > j && lane < bsz) y -= Ld[lane][j] * xj;
             }
             if (lane < bsz) b[r0 + lane] = x;
         }
@@ -696,6 +712,7 @@ __global__ void __launch_bounds__(1024) k_chol_solve(const double* A, double* b,
     const int nblk = (n + CB - 1) / CB;
     for (int blk = nblk - 1; blk >= 0; blk--) {          // backward with L'
         const int r0 = blk * CB, bsz = min(CB, n - r0);
+        chol_stage_block(A, n, r0, bsz, Ld, rd);
         if (warp < bsz) {
             const int i = r0 + warp;
             double s = 0.0;
@@ -707,9 +724,9 @@ __global__ void __launch_bounds__(1024) k_chol_solve(const double* A, double* b,
         if (warp == 0) {
             double y = lane < bsz ? part[lane] : 0.0, x = 0.0;
             for (int j = bsz - 1; j >= 0; j--) {
-                const double xj = __shfl_sync(0xffffffffu, lane == j ? y / A[(size_t)(r0 + j) * n + r0 + j] : 0.0, j);
+                const double xj = __shfl_sync(0xffffffffu, y * rd[j], j);
                 if (lane == j) x = xj;
-                if (lane < j) y -= A[(size_t)(r0 + j) * n + r0 + lane] * xj;
+                if (lane < j) y -= Ld[j][lane] * xj;
             }
             if (lane < bsz) b[r0 + lane] = x;
         }
