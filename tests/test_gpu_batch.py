@@ -162,3 +162,26 @@ def test_spline_reading_in_both_forms(gpu):
     with pytest.raises(Exception):
         t.run()
     t.close()
+
+
+def test_table_raw_u16_with_bias_map(gpu):
+    """raw uint16 frames with a bias map and a flat fused into every read, in the
+    table form and per frame: every output equal bit for bit"""
+    from test_gpu_extract import _raw_u16, _u16_tensor
+    frames = []
+    calib = None
+    for i in range(3):
+        raw, flat, bm = _raw_u16(6100 + i, W=640, H=480, n_stars=80, with_bias_map=True)
+        frames.append(_u16_tensor(raw))
+        if calib is None:   # one calibration for the batch (the frames share the flat and the bias map)
+            calib = (dev((1.0 / flat.astype(np.float64)).astype(np.float32)), 500.0, dev(bm))
+    ref = []
+    for f in frames:
+        ex = gpu.Extractor(640, 480, gpu.BgConfig(mesh=64), max_src=4096)
+        ref.append({k: v.clone() for k, v in ex(f, calib).items()})
+    b = gpu.Batch(frames, cfg=gpu.BgConfig(mesh=64), max_src=4096, mode="table", calib=calib)
+    b.run()
+    torch.cuda.synchronize()
+    for o, r in zip(b.outs, ref):
+        _same(o, r)
+    b.close()
