@@ -652,7 +652,11 @@ int ipp_sub_apply(const float* I, const float* R, int64_t W, int64_t H, int64_t 
  * ipp_sub_normal).  Limits: nk 1..8, deg 0..8, sord 0..4, bord -1..4, frames
  * below 2^31 pixels, at most 65536 regions; NOT_SUPPORTED when a footprint and
  * basis need more shared memory than one block has (fh = hw = 10 with the
- * 49-function basis takes 187 KB).
+ * 49-function basis takes 187 KB).  Errors: INVALID_ARG for NULL pointers, a
+ * basis or orders out of range, non-finite sig or nsig, or a small or
+ * misaligned workspace, all before anything is enqueued; the workspace query
+ * returns 0 for arguments out of range.  A singular normal matrix is not an
+ * error of the call: it is *status_dev = 1 on the device.
  */
 size_t ipp_sub_fit_workspace_size(int32_t max_c, int32_t nreg, int32_t hw, int32_t fh, int32_t nk, const int32_t* deg,
                                   int32_t sord, int32_t bord);
@@ -784,7 +788,12 @@ int ipp_batch_launch(ipp_batch b, void* stream);
  *                                   it; the graph reads the table in ws, so ws is
  *                                   not to be reused for another batch meanwhile)
  * Limits: 1..1024 frames; the windowed centroid's box at most 15 px (fwhm_win
- * up to ~3.5 px) -- NOT_SUPPORTED otherwise, where the stream form applies.
+ * up to ~3.5 px), the Keys reading (interp = IPP_INTERP_KEYS) -- NOT_SUPPORTED
+ * otherwise, where the stream form applies.
+ * Errors: INVALID_ARG for a bad frame (its index in ipp_last_error_detail()), a
+ * NULL or misaligned workspace or one too small for these frames, before
+ * anything is enqueued; otherwise as ipp_extract.  The workspace query returns
+ * 0 for a bad frame list.
  */
 size_t ipp_batch_table_workspace_size(const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp);
 int ipp_batch_table_extract(ipp_batch b, const ipp_frame_desc* frames, int32_t n, const ipp_bg_params* bp,
