@@ -339,7 +339,7 @@ def main():
     ap.add_argument("--psf-stamps", type=int, default=200000)
     ap.add_argument("--batch-frames", type=int, default=64)
     ap.add_argument("--raw-frames", type=int, default=10)
-    ap.add_argument("--lanes", type=int, default=4, help="CUDA streams that consecutive frames rotate over")
+    ap.add_argument("--lanes", type=int, default=8, help="CUDA streams that consecutive frames rotate over")
     ap.add_argument("--soak-steps", type=int, default=3000,
                     help="steps run under the clock sampler before the timed ones (>= 1 s)")
     ap.add_argument("--cfg1-steps", type=int, default=200, help="1024^2 frames of the small-field line")
